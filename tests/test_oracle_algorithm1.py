@@ -1,0 +1,209 @@
+"""Pins for the FP64 oracle of Algorithm 1 (CPU only).
+
+Each test checks the oracle against something other than itself: hand-counted
+values from the paper's definitions (tests/golden), closed forms, the paper's
+theorems used as statistical envelopes, the acceptance desiderata of Sec. 1.1,
+and brute force (full SVD) on small inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import algorithm1 as alg
+from oracle import rng
+from paper_2105_07388_gb300 import workloads as wl
+
+
+def test_r1_ladder(golden):
+    for s, r1 in golden("r1_ladder.txt"):
+        assert alg.r1_of_s(int(s)) == int(r1)
+        assert alg.oversampled(int(r1)) <= int(s) < alg.oversampled(int(r1) + 1)
+
+
+def test_round_half_away():
+    assert alg.oversampled(5) == 6          # 5.5 -> 6
+    assert alg.oversampled(15) == 17        # 16.5 -> 17
+    assert alg.oversampled(465) == 512      # 511.5 -> 512
+    assert alg.oversampled(0) == 0
+
+
+def test_numerical_rank_definition(golden):
+    for fam, n, eps, rank in golden("spectra_ranks.txt"):
+        sig = wl.spectrum(fam, int(n)).numpy()
+        assert alg.numerical_rank(sig, float(eps)) == int(rank)
+
+
+def test_readoff_threshold_and_gap():
+    sig = np.array([1.0, 0.5, 1e-5, 1e-6, 5e-7])
+    ro = alg.readoff(sig, 1e-4)
+    assert ro.rank == 2 and ro.gap_index == 2 and ro.gap_ratio == pytest.approx(5e4)
+    # ties at the threshold count as below it (Definition 1 uses <=)
+    ro = alg.readoff(np.array([2.0, 1.0, 2e-4, 1e-9]), 1e-4)
+    assert ro.rank == 2
+    # no value below tau among the trusted ones -> not converged
+    ro = alg.readoff(np.array([1.0, 0.9, 0.8]), 1e-4)
+    assert ro.rank is None and ro.gap_index == 2   # 0.9/0.8 > 1/0.9
+    # a zero after a positive value is an infinite gap; the zero matrix has rank 0
+    ro = alg.readoff(np.array([1.0, 1e-3, 0.0, 0.0]), 1e-6)
+    assert ro.rank == 2 and ro.gap_index == 2 and math.isinf(ro.gap_ratio)
+    ro = alg.readoff(np.zeros(5), 1e-3)
+    assert ro.rank == 0
+    # a given ||A|| replaces sigma^_1
+    ro = alg.readoff(np.array([1.0, 0.5, 0.01]), 0.1, norm_a=10.0)
+    assert ro.rank == 0
+
+
+def test_nested_core_prefix():
+    # Appending: the core at width s is the leading 2s x s block of the core at 2s.
+    A = np.random.default_rng(1).standard_normal((96, 40))
+    for kind in (alg.GAUSSIAN, alg.SRHT):
+        c8 = alg.core(A, 8, kind, seed=5)
+        c16 = alg.core(A, 16, kind, seed=5)
+        assert np.allclose(c16[:16, :8], c8, rtol=1e-13, atol=1e-12)
+
+
+def test_sketch_of_identity_is_the_embedding():
+    # A = I: A X = X, so the right sketch returns the generated columns.
+    n = 64
+    ax = alg.right_sketch(np.eye(n), 16, alg.GAUSSIAN, seed=9, col0=8)
+    assert np.array_equal(ax, rng.gaussian_x(n, 16, seed=9, col0=8))
+
+
+def test_sketch_of_rank_one():
+    # A = u v^T: every column of A X is u (v^T x_j), so sigma_2.. vanish and
+    # sigma_1(A X) = |u| |X^T v|.
+    r = np.random.default_rng(2)
+    u, v = r.standard_normal(50), r.standard_normal(30)
+    A = np.outer(u, v)
+    X = rng.gaussian_x(30, 8, seed=4)
+    sv = np.linalg.svd(alg.right_sketch(A, 8, alg.GAUSSIAN, seed=4), compute_uv=False)
+    assert sv[0] == pytest.approx(np.linalg.norm(u) * np.linalg.norm(X.T @ v), rel=1e-12)
+    assert sv[1] < 1e-12 * sv[0]
+
+
+def test_theorem4_expectation_envelope():
+    # Theorem 4 (Eq. ineqGauss): 1 - sqrt(i/r) <= E sigma_i(AX)/sigma_i(A)
+    #   <= 1 + sqrt((r-i+1)/r) + sigma_{r+1}/sigma_i (1 + sqrt((n-r)/r)).
+    m, n, r = 200, 120, 16
+    sig = wl.spectrum("fp", n)
+    A = wl.haar_matrix(m, n, sig, seed=3).numpy()
+    s = sig.numpy()
+    ratios = []
+    for seed in range(60):
+        ax = alg.right_sketch(A, r, alg.GAUSSIAN, seed=1000 + seed) / np.sqrt(r)
+        ratios.append(np.linalg.svd(ax, compute_uv=False) / s[:r])
+    mean = np.mean(ratios, axis=0)
+    for i in range(1, r + 1):
+        lo = 1 - np.sqrt(i / r)
+        hi = 1 + np.sqrt((r - i + 1) / r) + s[r] / s[i - 1] * (1 + np.sqrt((n - r) / r))
+        assert lo - 0.05 <= mean[i - 1] <= hi + 0.05, (i, lo, mean[i - 1], hi)
+
+
+def test_left_sketch_preserves_all_singular_values():
+    # Sec. 4: for tall-skinny B, sigma_i(Y B)/sigma_i(B) = O(1) for ALL i.  With a
+    # Gaussian Y of 2 r1 rows the ratios lie near [1 - 1/sqrt2, 1 + 1/sqrt2]
+    # (Theorem 3 applied to Y Q); the SRTT obeys Corollary 6 in the same sense.
+    r1 = 32
+    B = np.random.default_rng(4).standard_normal((2048, r1)) * np.logspace(0, -8, r1)
+    sb = np.linalg.svd(B, compute_uv=False)
+    for kind in (alg.GAUSSIAN, alg.SRHT):
+        yb = alg.left_sketch(B, 2 * r1, kind, seed=6) / np.sqrt(2 * r1)
+        ratio = np.linalg.svd(yb, compute_uv=False) / sb
+        assert np.all(ratio > 0.2) and np.all(ratio < 1.9), (kind, ratio.min(), ratio.max())
+
+
+@pytest.mark.parametrize("kind", [alg.GAUSSIAN, alg.SRHT])
+def test_exact_rank_on_clear_gap(kind):
+    # Sec. 1.1: with a clear gap sigma_r >> eps ||A|| >> sigma_{r+1} the estimate is exact.
+    m, n = 400, 300
+    for rank, seed in ((5, 0), (23, 1), (50, 2)):
+        sig = wl.spectrum("step", n, rank=rank, tail_scale=1e-9)
+        A = wl.haar_matrix(m, n, sig, seed=seed).numpy()
+        res = alg.rank_estimate(A, 1e-4, kind=kind, seed=seed + 10)
+        assert res.converged and res.rank == rank
+        assert res.rank == alg.numerical_rank(np.linalg.svd(A, compute_uv=False), 1e-4)
+        # gap index lands on the gap as well
+        assert res.gap_index == rank
+
+
+def test_gapped_family_A_G_reduced():
+    # A_G of Sec. 6 with blocks of 12 instead of 100 (n = 200): every eps between two
+    # levels returns the exact rank (Sec. 6.1: gaps are identified).
+    n = 200
+    sig = wl.spectrum("gaps", n, block=12)
+    A = wl.haar_matrix(300, n, sig, seed=7).numpy()
+    exact = np.linalg.svd(A, compute_uv=False)
+    for eps, want in ((1e-2, 12), (1e-6, 24), (1e-10, 36)):
+        res = alg.rank_estimate(A, eps, kind=alg.GAUSSIAN, seed=3)
+        assert res.converged and res.rank == want == alg.numerical_rank(exact, eps)
+
+
+@pytest.mark.parametrize("fam,eps", [("sp", 1e-2), ("fp", 1e-4), ("se", 1e-1), ("fe", 1e-6)])
+def test_acceptance_desiderata(fam, eps):
+    # Sec. 1.1: sigma_{r^+1}(A) < 10 eps ||A|| and sigma_{r^}(A) > 0.1 eps ||A||
+    # (Sec. 6.2 reports these always held); checked over several seeds.
+    n = 400
+    sig = wl.spectrum(fam, n)
+    A = wl.haar_matrix(500, n, sig, seed=1).numpy()
+    s = sig.numpy()
+    for seed in range(4):
+        res = alg.rank_estimate(A, eps, kind=alg.GAUSSIAN, seed=seed, s_max=256)
+        assert res.converged
+        r = res.rank
+        assert s[r] < 10 * eps * s[0]
+        assert r == 0 or s[r - 1] > 0.1 * eps * s[0]
+
+
+def test_brute_force_small():
+    # Full SVD brute force on small gapped inputs of odd shapes.
+    for (m, n, rank, seed) in ((33, 17, 3, 0), (57, 40, 9, 1), (129, 100, 31, 2)):
+        sig = wl.spectrum("step", n, rank=rank, tail_scale=1e-10)
+        A = wl.haar_matrix(m, n, sig, seed=seed).numpy()
+        exact = alg.numerical_rank(np.linalg.svd(A, compute_uv=False), 1e-5)
+        res = alg.rank_estimate(A, 1e-5, seed=seed)
+        assert exact == rank and res.rank == rank
+
+
+def test_transposed_input():
+    sig = wl.spectrum("step", 60, rank=6, tail_scale=1e-9)
+    A = wl.haar_matrix(150, 60, sig, seed=5).numpy()
+    r1 = alg.rank_estimate(A, 1e-4, seed=2)
+    r2 = alg.rank_estimate(A.T.copy(), 1e-4, seed=2)
+    assert r2.transposed and not r1.transposed
+    assert r1.rank == r2.rank == 6
+    assert np.allclose(r1.sigma, r2.sigma, rtol=1e-12)
+
+
+def test_doubling_and_lower_bound():
+    # rank 40 needs r1 >= 41: s = 8, 16, 32 are too small, s = 64 (r1 = 58) suffices.
+    sig = wl.spectrum("step", 200, rank=40, tail_scale=1e-9)
+    A = wl.haar_matrix(300, 200, sig, seed=6).numpy()
+    res = alg.rank_estimate(A, 1e-4, seed=1)
+    assert res.converged and res.rank == 40 and res.final_s == 64 and res.passes == 4
+    assert [h[0] for h in res.history] == [8, 16, 32, 64]
+    # capped at s_max = 32: r1(32) = 29 is returned as a lower bound
+    res = alg.rank_estimate(A, 1e-4, seed=1, s_max=32)
+    assert not res.converged and res.rank == 29 and res.final_s == 32
+
+
+def test_zero_and_argument_errors():
+    res = alg.rank_estimate(np.zeros((40, 20)), 1e-3)
+    assert res.rank == 0 and res.converged
+    with pytest.raises(ValueError):
+        alg.rank_estimate(np.ones((4, 4)), 0.0)
+    with pytest.raises(ValueError):
+        alg.rank_estimate(np.full((20, 20), np.nan), 1e-3)
+    with pytest.raises(ValueError):
+        alg.rank_estimate(np.ones((20, 20)), 1e-3, s0=12)
+    with pytest.raises(ValueError):
+        alg.rank_estimate(np.ones((8, 8)), 1e-3, kind=alg.SRHT)   # 2 s0 > m_pad
+
+
+def test_scaling_constant():
+    # With X = G/sqrt(s) and Y = G/sqrt(2s) the sketched sigma of a matrix with
+    # orthonormal columns concentrate around 1 (embedding matrices, Sec. 1 notation).
+    Q = wl.haar_orthonormal(4000, 10, seed=3).numpy() @ wl.haar_orthonormal(10, 10, 4).numpy().T
+    sig = alg.sketched_sigma(Q, 64, alg.GAUSSIAN, seed=3)[:10]
+    assert np.all(sig > 0.6) and np.all(sig < 1.5)
