@@ -1,0 +1,314 @@
+"""Benchmark: randomized numerical-rank estimation (Algorithm 1) on one GB300.
+
+Workload (default): the large single matrix, m = 65536, n = 16384, FP32 (4 GiB),
+A = U diag(sigma) V^T with U, V products of 8 seeded Householder reflectors and
+random signs; sigma_i = 1 (i <= 200), then 1e-6 / i; eps = 1e-4; Gaussian X and
+Y; s = 8, 16, ..., 256 by doubling (6 passes over A, true rank 200).
+
+One step = one full rank estimate (generator, right sketch, left sketch,
+small-core singular values, read-off, doubling loop) over the resident matrix.
+value = sketch GB/s = (bytes of A x passes over A) / step time, with A larger
+than L2 (no flush needed).  e2e = the same metric through the host-buffer entry
+point (host->device copy of A inside the timed region).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on
+a bounded row sample of the same workload, on the host cores.
+Multi-GPU: independent replicas, one matrix per rank, no collective on the data
+path ("weak" scaling); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "large": dict(m=65536, n=16384, rank=200, eps=1e-4, seed=1, sketch_seed=12345),
+    "small": dict(m=2048, n=1024, rank=40, eps=1e-4, seed=0, sketch_seed=12345),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--kind", default="gaussian", choices=["gaussian", "srht"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if "Active" in v
+                          and "Not" not in v})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+def build_matrix(w, device):
+    import torch
+    from paper_2105_07388_gb300 import workloads as wl
+    if w["m"] >= 16384:
+        sig = wl.spectrum("step", w["n"], rank=w["rank"], tail_scale=1e-6)
+        A = wl.householder_matrix(w["m"], w["n"], sig, seed=w["seed"], device=device)
+    else:
+        sig = wl.spectrum("decade10", w["n"])
+        A = wl.haar_matrix(w["m"], w["n"], sig, seed=w["seed"], device=device).to(torch.float32)
+    torch.cuda.synchronize() if device != "cpu" else None
+    return A
+
+
+def cpu_oracle_run(A_host: np.ndarray, w, kind: int, budget_s: float = 20.0):
+    """Time the FP64 oracle on a bounded row sample; returns (GB/s, info)."""
+    from oracle import algorithm1 as alg
+    m = A_host.shape[0]
+    rows = min(m, 2048)
+    t0 = time.perf_counter()
+    total_bytes = 0.0
+    runs = 0
+    while True:
+        sample = A_host[:rows].astype(np.float64)
+        t1 = time.perf_counter()
+        res = alg.rank_estimate(sample, w["eps"], kind=kind, seed=w["sketch_seed"], s_max=512)
+        dt = time.perf_counter() - t1
+        total_bytes += 4.0 * rows * A_host.shape[1] * res.passes
+        runs += 1
+        if time.perf_counter() - t0 > budget_s * 0.5 or rows >= m:
+            break
+        if dt < budget_s / 8:
+            rows = min(m, rows * 2)
+    el = time.perf_counter() - t0
+    return total_bytes / el / 1e9, {"rows": rows, "cols": A_host.shape[1], "runs": runs,
+                                     "seconds": el, "passes": res.passes}
+
+
+def main():
+    args = parse()
+    w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    kind_code = 0 if args.kind == "gaussian" else 1
+    cfg = {"workload": f"single matrix {w['m']}x{w['n']} FP32, sigma=1 (i<=200) then 1e-6/i, "
+                       f"eps={w['eps']}, {args.kind} X and Y, s=8..256 doubling"
+           if args.workload == "large" else
+           f"single matrix {w['m']}x{w['n']}, sigma=10^-(i-1)/10, eps={w['eps']}",
+           "m": w["m"], "n": w["n"], "dtype_A": "f32", "eps": w["eps"], "sketch": args.kind,
+           "precision": args.precision, "l2": "inputs larger than L2 (4 GiB A), no flush",
+           "parallelism": f"replicas x{args.gpus}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import torch
+        A = build_matrix(w, "cuda" if torch.cuda.is_available() else "cpu")
+        A_host = A.cpu().numpy()
+        del A
+        for _ in range(args.warmup):
+            cpu_oracle_run(A_host, w, kind_code, budget_s=2.0)
+        vals = []
+        info = None
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            v, info = cpu_oracle_run(A_host, w, kind_code, budget_s=8.0)
+            vals.append(v)
+        el = time.perf_counter() - t0
+        value = float(np.mean(vals))
+        line = {"impl": "reference", "metric": "sketch GB/s (A read once, % of HBM peak); "
+                "rank estimates/s vs plain at same ranks", "value": value, "unit": "GB/s",
+                "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": el / max(args.steps, 1) * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": cfg,
+                "cpu_baseline": {"kind": "oracle", "value": value, "unit": "GB/s",
+                                 "cores": os.cpu_count(),
+                                 "sample": f"first {info['rows']} rows x {info['cols']} of A, "
+                                           f"full doubling ladder ({info['passes']} passes)"},
+                "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2105_07388_gb300 import build as _b
+    from paper_2105_07388_gb300 import rankest as rk
+    _b.build()
+    A = build_matrix(w, "cuda")
+    m, n = A.shape
+    prec = rk.RE_PREC_FP32 if args.precision == "fp32" else rk.RE_PREC_BF16X3
+    h = rk.re_create(local, rk.make_opts(precision=prec))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return rk.re_rank_estimate(h, A, w["eps"], kind_code, w["sketch_seed"], stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        res, sig = step()
+    torch.cuda.synchronize()
+    rk.re_stats_enable(h, True)
+    rk.re_stats_reset(h)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res, sig = step()
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    st = rk.re_stats_get(h)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    passes = res.passes
+    a_bytes = 4.0 * m * n
+    value = a_bytes * passes * world / (ms * 1e-3) / 1e9
+    hbm, bf16, src = peaks()
+    clocks = clk.summary()
+
+    # roofline of the dominant stage
+    stage_ms = {"right": st.right_ms, "left": st.left_ms, "svd": st.svd_ms, "other": st.other_ms}
+    dominant = max(stage_ms, key=stage_ms.get)
+    right_avg_ms = st.right_ms / max(st.right_launches, 1)
+    right_gbs = st.right_bytes / max(st.right_launches, 1) / (right_avg_ms * 1e-3) / 1e9
+    right_tflops = st.right_flops / (st.right_ms * 1e-3) / 1e12 if st.right_ms else 0.0
+    sm_mhz = clocks["sm_mhz"] or 1900.0
+    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    if args.kind == "gaussian" and args.precision == "fp32":
+        alu_frac = right_tflops / fp32_peak_tflops
+    else:
+        alu_frac = 0.0
+    hbm_frac = right_gbs / hbm
+    if alu_frac > hbm_frac:
+        roof = {"kernel": "right sketch (FP32 SIMT)", "bound": "alu", "achieved": right_tflops,
+                "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": alu_frac,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock under load",
+                "hbm_achieved_gbs": right_gbs, "hbm_frac": hbm_frac}
+    else:
+        roof = {"kernel": "right sketch", "bound": "hbm", "achieved": right_gbs, "peak": hbm,
+                "unit": "GB/s", "frac": hbm_frac, "peak_source": f"{src} hbm_gbs"}
+    roof["traffic"] = None
+    roof["dominant_stage"] = dominant
+    roof["stage_ms_per_step"] = {k: v / args.steps for k, v in stage_ms.items()}
+
+    line = {"metric": "sketch GB/s (A read once, % of HBM peak); rank estimates/s vs plain at same ranks",
+            "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": cfg, "hbm_frac_of_step": value / world / hbm,
+            "rank_estimates_per_s": world * 1e3 / ms,
+            "result": {"rank": res.rank, "final_s": res.final_s, "passes": passes,
+                       "flags": res.flags},
+            "gpu_launches": int(st.launches), "roofline": roof, "clocks": clocks}
+
+    if not args.no_e2e:
+        Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        Ah.copy_(A)
+        Ah_np = Ah.numpy()
+        rk.re_rank_estimate_host(h, Ah_np, w["eps"], kind_code, w["sketch_seed"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_steps = max(1, min(args.steps, 5))
+        for _ in range(e_steps):
+            r2, s2 = rk.re_rank_estimate_host(h, Ah_np, w["eps"], kind_code, w["sketch_seed"])
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+        line["e2e"] = {"value": a_bytes * r2.passes / (e_ms * 1e-3) / 1e9, "unit": "GB/s",
+                       "ms_per_step": e_ms, "h2d_bytes_per_step": int(a_bytes),
+                       "d2h_bytes_per_step": int(r2.passes * 40 + 8 * r2.n_sigma)}
+        del Ah
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        A_host = A.cpu().numpy()
+        v, info = cpu_oracle_run(A_host, w, kind_code, budget_s=20.0)
+        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"first {info['rows']} rows x {info['cols']} of A, "
+                                          f"full doubling ladder, {info['runs']} runs in "
+                                          f"{info['seconds']:.1f} s"}
+    rk.re_destroy(h)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * rankest.h - C ABI of librankest.so, a GB300 (sm_103a) implementation of the
+ * randomized numerical-rank estimator of Meier & Nakatsukasa, "Fast Randomized
+ * Numerical Rank Estimation for Numerically Low-Rank Matrices".
+ *
+ * The estimator (Algorithm 1, Sec. 5) forms the two-sided sketch Y*A*X of an
+ * m x n matrix A (m >= n, Notation in Sec. 1): the right sketch A*X with an
+ * n x s embedding X (Gaussian, Sec. 3.4, or a subsampled randomized Hadamard
+ * transform, Eq. (Theta) in Sec. 4), the left sketch Y*(A*X) with a 2s x m
+ * embedding Y ("randomized approximate orthogonalization", Sec. 4), the
+ * singular values of the small 2s x s core (step 7), and the read-off of the
+ * eps-rank (Definition 1, Sec. 1.1) from the threshold eps*||A|| and the gap
+ * sigma_i / sigma_{i+1} (step 8), growing s by doubling and appending until the
+ * threshold is crossed (step 8; Sec. 5 on the choice of r1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Return value: RE_OK (0) or a negative RE_ERR_* code.  On error nothing is
+ *   written to caller outputs except where stated; re_last_error() gives a
+ *   one-line message.
+ * - A is row-major with leading dimension ld >= n (elements), FP32 or FP64
+ *   (dtype RE_F32 / RE_F64).  FP64 input is rounded to FP32 as it is loaded.
+ *   When m < n the estimate is taken on A^T (same eps-rank); results then carry
+ *   RE_TRANSPOSED and "rows" below means the longer dimension.
+ * - Device pointers are CUDA device memory of the handle's device; host
+ *   pointers are ordinary (pageable or pinned) host memory.  The caller owns
+ *   every buffer it passes; the library never frees them.
+ * - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Work is stream-ordered; calls returning host values synchronise the stream.
+ * - Sketch widths s are multiples of 8.  The ladder is s0, 2 s0, 4 s0, ...
+ *   <= s_max; at width s the first r1(s) = max{r : round(1.1 r) <= s} sketched
+ *   singular values are trusted (Algorithm 1 step 1 and Sec. 3.3's 10%
+ *   oversampling), r2 = 2 s (step 4).
+ * - Random embeddings are never passed in: they are drawn from a counter-based
+ *   generator keyed by `seed` (Philox4x32-10, Box-Muller normals rounded to BF16,
+ *   Feistel sampling for the SRHT), so a given seed always gives the same X and
+ *   Y and larger widths append columns/rows to smaller ones.
+ * - A handle is used by one host thread at a time.
+ */
+#ifndef RANKEST_H
+#define RANKEST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RE_OK 0
+#define RE_ERR_ARG (-1)         /* invalid argument (null pointer, ld < n, eps not in (0,1), bad s) */
+#define RE_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define RE_ERR_NONFINITE (-3)   /* A holds NaN or Inf (detected in the sketch) */
+#define RE_ERR_TIMEOUT (-4)     /* a bounded device wait expired */
+#define RE_ERR_NOMEM (-5)       /* device workspace allocation failed */
+#define RE_ERR_UNSUPPORTED (-6) /* valid request this build does not handle */
+
+/* element types of A */
+#define RE_F32 0
+#define RE_F64 1
+
+/* embedding kinds (Sec. 3.4) */
+#define RE_GAUSSIAN 0 /* iid N(0,1) entries, scaled by 1/sqrt(width) */
+#define RE_SRHT 1     /* sqrt(N/r) S H D, H Sylvester Hadamard on the zero-padded dimension */
+
+/* arithmetic of the Gaussian right sketch */
+#define RE_PREC_FP32 0   /* FP32 FMA on CUDA cores */
+#define RE_PREC_BF16X3 1 /* A split into three BF16 terms, tensor cores (tcgen05), FP32 accumulation */
+
+/* result flags */
+#define RE_CONVERGED 1u        /* some trusted sigma^_{i+1} <= eps ||A|| was found */
+#define RE_LOWER_BOUND_ONLY 2u /* the ladder ended first: rank = r1(final s) is a lower bound (Sec. 5) */
+#define RE_TRANSPOSED 4u       /* m < n: the estimate was taken on A^T */
+
+typedef struct re_handle_* re_handle;
+
+/* Options (all plain values).  re_opts_default() fills the defaults given here. */
+typedef struct {
+    int s0;          /* initial X width, multiple of 8 (default 8) */
+    int s_max;       /* largest X width, <= 512 (default 512) */
+    int precision;   /* RE_PREC_* for the Gaussian right sketch (default RE_PREC_FP32) */
+    int y_kind;      /* left embedding kind; -1 = same as the right one (default -1) */
+    double norm_a;   /* > 0: use as ||A|| in the threshold; otherwise sigma^_1 (step 8) */
+    int learned;     /* 1: let the sketch-size proposal network pick the next width (default 0) */
+    int reserved[7];
+} re_opts;
+
+/* Outcome of one estimate.  sigma values go to a separate caller buffer. */
+typedef struct {
+    int rank;          /* eps-rank estimate r^ (or r1 with RE_LOWER_BOUND_ONLY) */
+    int gap_index;     /* argmax_{1<=i<r1} sigma^_i / sigma^_{i+1}, smallest i on ties */
+    double gap_ratio;  /* that ratio (+inf when sigma^_{i+1} = 0 < sigma^_i) */
+    double tau;        /* the threshold eps * ||A|| used */
+    int n_sigma;       /* r1(final_s): number of trusted sketched singular values */
+    int final_s;       /* X width of the last step */
+    int passes;        /* passes over A (sketch steps) */
+    uint32_t flags;    /* RE_CONVERGED | RE_LOWER_BOUND_ONLY | RE_TRANSPOSED */
+    int status;        /* per-estimate status (batched calls): RE_OK or RE_ERR_* */
+    int reserved[3];
+} re_result;
+
+/* One block of a batched estimate: a device matrix, row-major. */
+typedef struct {
+    const void* ptr;
+    int64_t m, n, ld;
+} re_block;
+
+/* Per-handle counters for measurement: kernel launches made by the library and,
+ * when timing is enabled, CUDA-event time of each stage on the caller's stream.
+ * right_bytes / right_flops are the algorithmic bytes (A read once, X read,
+ * AX written) and flops of the right-sketch launches that were timed. */
+typedef struct {
+    int64_t launches;        /* kernels launched by this handle since the last reset */
+    int64_t right_launches;  /* right-sketch kernel launches timed */
+    double right_ms;         /* their summed device time */
+    double right_bytes;      /* their algorithmic bytes */
+    double right_flops;      /* their algorithmic flops */
+    double left_ms;          /* left-sketch kernels (with the split-K reduction) */
+    double svd_ms;           /* small-core singular values */
+    double other_ms;         /* generator and read-off kernels */
+    int64_t passes;          /* sketch passes over A */
+    int64_t reserved[4];
+} re_stats;
+
+/* Library version as major*10000 + minor*100 + patch. */
+int re_version(void);
+
+/* Message for the last error on this host thread (static storage). */
+const char* re_last_error(void);
+
+/* Fill *opts with the defaults above. */
+void re_opts_default(re_opts* opts);
+
+/* Create a handle on CUDA device `device`.  opts may be NULL (defaults).  The
+ * handle owns its device workspace, which grows on demand and is freed by
+ * re_destroy. */
+int re_create(re_handle* out, int device, const re_opts* opts);
+int re_destroy(re_handle h);
+int re_set_opts(re_handle h, const re_opts* opts);
+
+/* Measurement counters (see re_stats).  Timing adds CUDA events around each
+ * stage; it is off by default.  re_stats_get synchronises nothing: it reports
+ * stages whose read-off step has completed. */
+int re_stats_enable(re_handle h, int timing_on);
+int re_stats_reset(re_handle h);
+int re_stats_get(re_handle h, re_stats* out);
+
+/*
+ * Algorithm 1 with doubling (Sec. 5): estimate rank_eps(A).
+ *   A          device pointer, m x n row-major, leading dimension ld.
+ *   eps        relative tolerance in (0, 1) (Definition 1).
+ *   sketch_kind RE_GAUSSIAN or RE_SRHT (right embedding; left per opts.y_kind).
+ *   seed       generator key for X and Y.
+ *   sigma_out  host buffer of sigma_cap doubles, receives the first
+ *              min(n_sigma, sigma_cap) scaled sketched singular values
+ *              sigma_i(Y A X) (descending); may be NULL when sigma_cap = 0.
+ *   out        host result.
+ * Synchronises `stream` before returning.  A is only read.
+ */
+int re_rank_estimate(re_handle h, const void* A, int dtype, int64_t m, int64_t n, int64_t ld,
+                     double eps, int sketch_kind, uint64_t seed,
+                     double* sigma_out, int sigma_cap, re_result* out, void* stream);
+
+/* As re_rank_estimate, but A is a HOST pointer: the call copies A to the
+ * handle's device workspace (host->device inside the call) and reads back only
+ * the result and sigma. */
+int re_rank_estimate_host(re_handle h, const void* A_host, int dtype, int64_t m, int64_t n,
+                          int64_t ld, double eps, int sketch_kind, uint64_t seed,
+                          double* sigma_out, int sigma_cap, re_result* out, void* stream);
+
+/*
+ * One appending sketch step (Algorithm 1 steps 2-6), for callers that reuse A*X
+ * (randomized SVD / rangefinder, Sec. 5.1).  With k0 = col0:
+ *   AX   device FP32, rows x ld_ax row-major (rows = max(m, n)); columns
+ *        k0 .. k0+s-1 receive the UNSCALED right sketch A*G[:, k0:k0+s] (Gaussian G
+ *        entries, or D H S^T entries +-1 for RE_SRHT).  Columns < k0 must hold
+ *        earlier columns from the same seed when core is non-NULL.
+ *   core optional device FP64, (2 (k0+s)) x ld_core row-major: on entry its
+ *        leading 2 k0 x k0 block holds the previous unscaled core; on return the
+ *        leading 2(k0+s) x (k0+s) block holds Y[0:2(k0+s)] * A * X[:, 0:k0+s].
+ *        NULL skips the left sketch.
+ * Scaling by 1/sqrt(width) is left to the caller.  col0 and s are multiples of 8.
+ */
+int re_sketch_apply(re_handle h, const void* A, int dtype, int64_t m, int64_t n, int64_t ld,
+                    int col0, int s, int sketch_kind, uint64_t seed,
+                    float* AX, int64_t ld_ax, double* core, int64_t ld_core, void* stream);
+
+/*
+ * Step 7 alone: the singular values of a device FP64 r2 x s matrix (row-major,
+ * leading dimension ld), descending, written to the device FP64 array sigma
+ * (s entries), unscaled.  r2 >= s >= 1, s <= 512.
+ */
+int re_core_sigma(re_handle h, const double* core, int r2, int s, int64_t ld,
+                  double* sigma, void* stream);
+
+/*
+ * The embeddings themselves, for tests and for callers that want X or Y
+ * explicitly (the estimator never materialises them this way):
+ *   re_embedding_x: out (device FP32, n x s row-major) = columns col0.. of the
+ *                   unscaled X (n = number of columns of the oriented A).
+ *   re_embedding_y: out (device FP32, r2 x m row-major) = rows row0.. of the
+ *                   unscaled Y (m = number of rows of the oriented A).
+ */
+int re_embedding_x(re_handle h, int kind, uint64_t seed, int64_t n, int col0, int s,
+                   float* out, void* stream);
+int re_embedding_y(re_handle h, int kind, uint64_t seed, int64_t m, int row0, int r2,
+                   float* out, void* stream);
+
+/*
+ * Batched Algorithm 1 over `count` independent blocks (e.g. the off-diagonal
+ * blocks of a hierarchical matrix, Sec. 1).  blocks is a HOST array of device
+ * matrices; out (host, count entries) receives one result each; sigma_out
+ * (host, count x sigma_cap, may be NULL) the trusted sigma of each.  Every block
+ * uses seed + block index.  Per-block argument errors are reported in
+ * out[i].status; the call itself fails only on launch or allocation errors.
+ */
+int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int dtype,
+                             double eps, int sketch_kind, uint64_t seed,
+                             double* sigma_out, int sigma_cap, re_result* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RANKEST_H */

@@ -1,0 +1,600 @@
+// C ABI of librankest: handles, workspace, and the host side of Algorithm 1
+// (Sec. 5): the adaptive loop that grows the sketch width by doubling and
+// appending columns of X / rows of Y until the read-off of step 8 finds a
+// trusted sketched singular value below eps*||A||.  Every numerical step runs
+// in this library's kernels; the host only launches them and reads back a
+// 40-byte read-off record per step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return RE_ERR_CUDA;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+enum Stage { kStageRight = 0, kStageLeft = 1, kStageSvd = 2, kStageOther = 3 };
+
+struct PendingTiming {
+    int stage;
+    cudaEvent_t a, b;
+    double bytes, flops;
+};
+
+struct re_handle_ {
+    int device = 0;
+    re_opts opts{};
+    bool timing = false;
+    re_stats stats{};
+    std::vector<PendingTiming> pending;
+    std::vector<cudaEvent_t> event_pool;
+    DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status;
+    re::DevReadoff* h_ro = nullptr;   // pinned
+    double* h_sigma = nullptr;        // pinned, 1024 doubles
+    int sm_count = 0;
+};
+
+namespace {
+
+cudaEvent_t take_event(re_handle h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Stage timing on the caller's stream: begin() returns an event recorded before
+// the stage's launches, end() records the closing event.  Timings are resolved
+// after the next stream synchronisation.
+cudaEvent_t stage_begin(re_handle h, cudaStream_t st) {
+    if (!h->timing) return nullptr;
+    cudaEvent_t a = take_event(h);
+    cudaEventRecord(a, st);
+    return a;
+}
+
+void stage_end(re_handle h, cudaStream_t st, cudaEvent_t a, int stage, double bytes = 0.0,
+               double flops = 0.0) {
+    if (!h->timing || !a) return;
+    cudaEvent_t b = take_event(h);
+    cudaEventRecord(b, st);
+    h->pending.push_back(PendingTiming{stage, a, b, bytes, flops});
+}
+
+void resolve_timings(re_handle h) {
+    for (const PendingTiming& p : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        switch (p.stage) {
+            case kStageRight:
+                h->stats.right_ms += ms;
+                h->stats.right_launches += 1;
+                h->stats.right_bytes += p.bytes;
+                h->stats.right_flops += p.flops;
+                break;
+            case kStageLeft: h->stats.left_ms += ms; break;
+            case kStageSvd: h->stats.svd_ms += ms; break;
+            default: h->stats.other_ms += ms; break;
+        }
+        h->event_pool.push_back(p.a);
+        h->event_pool.push_back(p.b);
+    }
+    h->pending.clear();
+}
+
+int ensure(DevBuf& b, size_t bytes) {
+    if (bytes <= b.cap) return RE_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RE_ERR_NOMEM, "device workspace allocation failed");
+    }
+    b.cap = want;
+    return RE_OK;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+int round_half_away_11_10(int r) { return (2 * 11 * r + 10) / 20; }
+
+// r1(s): largest r with round(1.1 r) <= s (Algorithm 1 step 1; 10% oversampling of Sec. 3.3).
+int r1_of_s(int s) {
+    int r = 1;
+    while (round_half_away_11_10(r + 1) <= s) ++r;
+    return r;
+}
+
+struct Plan {
+    re::MatView A;
+    int kind;     // right embedding
+    int ykind;    // left embedding
+    int cap;      // largest admissible width
+    int64_t n_pad, m_pad;
+    int nbits, mbits;
+};
+
+int make_plan(const void* A, int dtype, int64_t m, int64_t n, int64_t ld, int kind, int ykind,
+              int s_max, Plan* p) {
+    if (!A) return fail(RE_ERR_ARG, "A is NULL");
+    if (dtype != RE_F32 && dtype != RE_F64) return fail(RE_ERR_ARG, "dtype must be RE_F32 or RE_F64");
+    if (m <= 0 || n <= 0) return fail(RE_ERR_ARG, "m and n must be positive");
+    if (ld < n) return fail(RE_ERR_ARG, "ld < n");
+    if (m > INT32_MAX || n > INT32_MAX) return fail(RE_ERR_ARG, "dimension too large");
+    if (kind != RE_GAUSSIAN && kind != RE_SRHT) return fail(RE_ERR_ARG, "unknown sketch kind");
+    if (ykind != RE_GAUSSIAN && ykind != RE_SRHT) return fail(RE_ERR_ARG, "unknown left sketch kind");
+    p->A.ptr = A;
+    p->A.dtype = dtype;
+    p->A.trans = m < n;
+    p->A.rows = std::max(m, n);
+    p->A.cols = std::min(m, n);
+    p->A.ld = ld;
+    p->kind = kind;
+    p->ykind = ykind;
+    p->nbits = re::pow2_bits(p->A.cols);
+    p->mbits = re::pow2_bits(p->A.rows);
+    p->n_pad = int64_t(1) << p->nbits;
+    p->m_pad = int64_t(1) << p->mbits;
+    int64_t cap = s_max;
+    if (kind == RE_SRHT) cap = std::min<int64_t>(cap, p->n_pad);
+    if (ykind == RE_SRHT) cap = std::min<int64_t>(cap, p->m_pad / 2);
+    p->cap = (int)cap;
+    return RE_OK;
+}
+
+// Algorithmic bytes of one right-sketch launch: A read once, X read (x_bytes per
+// entry, 0 when generated in place), AX written.
+double right_bytes(const Plan& P, int cnt, int x_bytes) {
+    const double a_elem = P.A.dtype == RE_F32 ? 4.0 : 8.0;
+    return a_elem * (double)P.A.rows * (double)P.A.cols + (double)x_bytes * P.A.cols * cnt +
+           4.0 * (double)P.A.rows * cnt;
+}
+
+struct Step {
+    int passes = 0;
+    int final_s = 0;
+    re::DevReadoff ro{};
+};
+
+// Right sketch columns [c0, c0+cnt) of the oriented A into AX (row-major, ld_ax).
+int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, float* AX,
+                  int64_t ld_ax, cudaStream_t st) {
+    cudaError_t e;
+    if (P.kind == RE_GAUSSIAN) {
+        if (h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A)) {
+            const int64_t kpad = (P.A.cols + 63) / 64 * 64;
+            if (int r = ensure(h->xt, sizeof(uint16_t) * (size_t)kpad * cnt + 1024)) return r;
+            if (int r = ensure(h->status, 64)) return r;
+            cudaEvent_t g = stage_begin(h, st);
+            e = re::launch_gauss_xt_bf16(seed, P.A.cols, kpad, c0, cnt, static_cast<uint16_t*>(h->xt.p),
+                                         kpad, st);
+            if (e != cudaSuccess) return cuda_fail(e, "generate X");
+            stage_end(h, st, g, kStageOther);
+            cudaEvent_t a = stage_begin(h, st);
+            e = re::launch_right_tc(P.A, static_cast<const uint16_t*>(h->xt.p), kpad, cnt,
+                                    AX + c0, ld_ax, static_cast<int*>(h->status.p) + 4, st);
+            if (e != cudaSuccess) return cuda_fail(e, "right sketch (tensor cores)");
+            stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 2), 3.0 * 2.0 * P.A.rows * P.A.cols * cnt);
+            h->stats.launches += 2;
+            return RE_OK;
+        }
+        if (h->opts.precision == RE_PREC_BF16X3)
+            return fail(RE_ERR_UNSUPPORTED, "BF16x3 tensor-core sketch unavailable for this input");
+        if (int r = ensure(h->x, sizeof(float) * (size_t)P.A.cols * cnt)) return r;
+        cudaEvent_t g = stage_begin(h, st);
+        e = re::launch_gauss_x(seed, P.A.cols, c0, cnt, static_cast<float*>(h->x.p), cnt, st);
+        if (e != cudaSuccess) return cuda_fail(e, "generate X");
+        stage_end(h, st, g, kStageOther);
+        cudaEvent_t a = stage_begin(h, st);
+        e = re::launch_right_simt(P.A, static_cast<const float*>(h->x.p), cnt, cnt, AX + c0, ld_ax, st);
+        if (e != cudaSuccess) return cuda_fail(e, "right sketch (FP32)");
+        stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 4), 2.0 * P.A.rows * P.A.cols * cnt);
+        h->stats.launches += 2;
+        return RE_OK;
+    }
+    // SRHT: signs of the padded n and sampled columns pi_X(c0 .. c0+cnt-1)
+    if (int r = ensure(h->dx, sizeof(uint32_t) * (size_t)(P.n_pad / 32 + 1))) return r;
+    if (int r = ensure(h->px, sizeof(int) * (size_t)cnt)) return r;
+    cudaEvent_t g = stage_begin(h, st);
+    e = re::launch_sign_bits(seed, re::kStreamDX, P.A.cols, static_cast<uint32_t*>(h->dx.p), st);
+    if (e == cudaSuccess)
+        e = re::launch_perm(seed, re::kStreamPX, P.nbits, c0, cnt, static_cast<int*>(h->px.p), st);
+    stage_end(h, st, g, kStageOther);
+    cudaEvent_t a = stage_begin(h, st);
+    if (e == cudaSuccess)
+        e = re::launch_right_srht(P.A, static_cast<const uint32_t*>(h->dx.p),
+                                  static_cast<const int*>(h->px.p), cnt, AX + c0, ld_ax, st);
+    if (e != cudaSuccess) return cuda_fail(e, "right sketch (SRHT)");
+    stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 0),
+              (double)P.A.rows * (double)P.n_pad * (double)P.nbits);
+    h->stats.launches += 3;
+    return RE_OK;
+}
+
+// Left-sketch blocks after AX columns [c0, c1) were added: rows [2 c0, 2 c1) x cols
+// [0, c0) and rows [0, 2 c1) x cols [c0, c1) of core (FP64 row-major, ld_core).
+int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const float* AX,
+                int64_t ld_ax, double* core, int64_t ld_core, cudaStream_t st) {
+    const int64_t M = P.A.rows;
+    if (P.ykind == RE_SRHT) {
+        if (int r = ensure(h->dy, sizeof(uint32_t) * (size_t)(P.m_pad / 32 + 1))) return r;
+        if (int r = ensure(h->py, sizeof(int) * (size_t)(2 * c1))) return r;
+        cudaEvent_t g = stage_begin(h, st);
+        cudaError_t e = re::launch_sign_bits(seed, re::kStreamDY, M, static_cast<uint32_t*>(h->dy.p), st);
+        if (e == cudaSuccess)
+            e = re::launch_perm(seed, re::kStreamPY, P.mbits, 0, 2 * c1, static_cast<int*>(h->py.p), st);
+        if (e != cudaSuccess) return cuda_fail(e, "left embedding");
+        stage_end(h, st, g, kStageOther);
+        h->stats.launches += 2;
+    }
+    const size_t need = std::max(re::left_part_floats(M, 2 * (c1 - c0), c0),
+                                 re::left_part_floats(M, 2 * c1, c1 - c0));
+    if (int r = ensure(h->part, sizeof(float) * need)) return r;
+    cudaError_t e = cudaSuccess;
+    cudaEvent_t a = stage_begin(h, st);
+    if (c0 > 0)
+        e = re::launch_left(P.ykind, seed, AX, ld_ax, M, 2 * c0, 2 * (c1 - c0), 0, c0,
+                            static_cast<const uint32_t*>(h->dy.p), static_cast<const int*>(h->py.p),
+                            static_cast<float*>(h->part.p), h->part.cap / sizeof(float), core,
+                            ld_core, st);
+    if (e == cudaSuccess)
+        e = re::launch_left(P.ykind, seed, AX, ld_ax, M, 0, 2 * c1, c0, c1 - c0,
+                            static_cast<const uint32_t*>(h->dy.p), static_cast<const int*>(h->py.p),
+                            static_cast<float*>(h->part.p), h->part.cap / sizeof(float), core,
+                            ld_core, st);
+    if (e != cudaSuccess) return cuda_fail(e, "left sketch");
+    stage_end(h, st, a, kStageLeft);
+    h->stats.launches += c0 > 0 ? 4 : 2;
+    return RE_OK;
+}
+
+// Algorithm 1 with doubling on an already validated plan.
+int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* sigma_out,
+                 int sigma_cap, re_result* out, cudaStream_t st) {
+    const re_opts& o = h->opts;
+    if (o.s0 > P.cap) return fail(RE_ERR_ARG, "initial sketch width exceeds the admissible width");
+    int smax = o.s0;
+    while (smax * 2 <= P.cap) smax *= 2;
+    const int64_t M = P.A.rows;
+    if (int r = ensure(h->ax, sizeof(float) * (size_t)M * smax)) return r;
+    if (int r = ensure(h->core, sizeof(double) * (size_t)2 * smax * smax)) return r;
+    if (int r = ensure(h->sigma, sizeof(double) * (size_t)smax)) return r;
+    if (int r = ensure(h->sigma_scaled, sizeof(double) * (size_t)smax)) return r;
+    if (int r = ensure(h->svdws, re::svd_workspace_bytes(2 * smax, smax))) return r;
+    if (int r = ensure(h->ro, sizeof(re::DevReadoff))) return r;
+    if (int r = ensure(h->status, 64)) return r;
+    float* AX = static_cast<float*>(h->ax.p);
+    double* core = static_cast<double*>(h->core.p);
+    int* status = static_cast<int*>(h->status.p);
+    const double scale_base = 1.0;
+    (void)scale_base;
+
+    int s_prev = 0, s = o.s0, passes = 0;
+    re::DevReadoff ro{};
+    int r1 = 0;
+    for (;;) {
+        if (int r = right_columns(h, P, seed, s_prev, s - s_prev, AX, smax, st)) return r;
+        if (int r = left_blocks(h, P, seed, s_prev, s, AX, smax, core, smax, st)) return r;
+        cudaEvent_t a = stage_begin(h, st);
+        cudaError_t e = re::launch_core_sigma(core, 2 * s, s, smax, h->svdws.p,
+                                              static_cast<double*>(h->sigma.p), status, st);
+        if (e != cudaSuccess) return cuda_fail(e, "core singular values");
+        stage_end(h, st, a, kStageSvd);
+        r1 = std::min(r1_of_s(s), s);
+        const double scale = 1.0 / std::sqrt((double)s * (double)(2 * s));
+        e = re::launch_readoff(static_cast<const double*>(h->sigma.p), r1, scale, eps, o.norm_a,
+                               status, static_cast<re::DevReadoff*>(h->ro.p),
+                               static_cast<double*>(h->sigma_scaled.p), st);
+        if (e != cudaSuccess) return cuda_fail(e, "read-off");
+        e = cudaMemcpyAsync(h->h_ro, h->ro.p, sizeof(re::DevReadoff), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "read-off copy");
+        h->stats.launches += 2;
+        resolve_timings(h);
+        ro = *h->h_ro;
+        ++passes;
+        h->stats.passes += 1;
+        if (ro.status != RE_OK) return fail(ro.status, "non-finite values in A or its sketch");
+        if (ro.rank >= 0) break;
+        if (2 * s > smax || r1 >= P.A.cols) break;
+        s_prev = s;
+        s *= 2;
+    }
+    const int ncopy = std::min(r1, std::max(sigma_cap, 0));
+    if (sigma_out && ncopy > 0) {
+        cudaError_t e = cudaMemcpyAsync(sigma_out, h->sigma_scaled.p, sizeof(double) * ncopy,
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "sigma copy");
+    }
+    std::memset(out, 0, sizeof(*out));
+    const bool conv = ro.rank >= 0;
+    out->rank = conv ? ro.rank : r1;
+    out->gap_index = ro.gap_index;
+    out->gap_ratio = ro.gap_ratio;
+    out->tau = ro.tau;
+    out->n_sigma = r1;
+    out->final_s = s;
+    out->passes = passes;
+    out->flags = (conv ? RE_CONVERGED : RE_LOWER_BOUND_ONLY) | (P.A.trans ? RE_TRANSPOSED : 0u);
+    out->status = RE_OK;
+    return RE_OK;
+}
+
+int check_opts(const re_opts* o) {
+    if (o->s0 < 8 || o->s0 % 8 != 0) return fail(RE_ERR_ARG, "s0 must be a positive multiple of 8");
+    if (o->s_max < o->s0) return fail(RE_ERR_ARG, "s_max < s0");
+    if (o->s_max > 512) return fail(RE_ERR_ARG, "s_max above 512");
+    if (o->precision != RE_PREC_FP32 && o->precision != RE_PREC_BF16X3)
+        return fail(RE_ERR_ARG, "unknown precision");
+    if (o->y_kind < -1 || o->y_kind > RE_SRHT) return fail(RE_ERR_ARG, "unknown y_kind");
+    return RE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int re_version(void) { return 100; }
+
+const char* re_last_error(void) { return g_last_error.c_str(); }
+
+void re_opts_default(re_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->s0 = 8;
+    o->s_max = 512;
+    o->precision = RE_PREC_FP32;
+    o->y_kind = -1;
+    o->norm_a = 0.0;
+    o->learned = 0;
+}
+
+int re_create(re_handle* out, int device, const re_opts* opts) {
+    if (!out) return fail(RE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    re_opts o;
+    re_opts_default(&o);
+    if (opts) o = *opts;
+    if (int r = check_opts(&o)) return r;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(RE_ERR_ARG, "no such device");
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    re_handle h = new re_handle_();
+    h->device = device;
+    h->opts = o;
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+    e = cudaMallocHost(reinterpret_cast<void**>(&h->h_ro), sizeof(re::DevReadoff));
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->h_sigma), 1024 * sizeof(double));
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "pinned host buffers");
+    }
+    *out = h;
+    return RE_OK;
+}
+
+int re_destroy(re_handle h) {
+    if (!h) return RE_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    DevBuf* bufs[] = {&h->x, &h->xt, &h->ax, &h->part, &h->core, &h->sigma, &h->sigma_scaled,
+                      &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status};
+    for (DevBuf* b : bufs) release(*b);
+    resolve_timings(h);
+    for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+    if (h->h_ro) cudaFreeHost(h->h_ro);
+    if (h->h_sigma) cudaFreeHost(h->h_sigma);
+    delete h;
+    return RE_OK;
+}
+
+int re_stats_enable(re_handle h, int timing_on) {
+    if (!h) return fail(RE_ERR_ARG, "NULL handle");
+    h->timing = timing_on != 0;
+    return RE_OK;
+}
+
+int re_stats_reset(re_handle h) {
+    if (!h) return fail(RE_ERR_ARG, "NULL handle");
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    resolve_timings(h);
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    return RE_OK;
+}
+
+int re_stats_get(re_handle h, re_stats* out) {
+    if (!h || !out) return fail(RE_ERR_ARG, "NULL argument");
+    *out = h->stats;
+    return RE_OK;
+}
+
+int re_set_opts(re_handle h, const re_opts* opts) {
+    if (!h || !opts) return fail(RE_ERR_ARG, "NULL argument");
+    if (int r = check_opts(opts)) return r;
+    h->opts = *opts;
+    return RE_OK;
+}
+
+int re_rank_estimate(re_handle h, const void* A, int dtype, int64_t m, int64_t n, int64_t ld,
+                     double eps, int sketch_kind, uint64_t seed, double* sigma_out, int sigma_cap,
+                     re_result* out, void* stream) {
+    if (!h || !out) return fail(RE_ERR_ARG, "NULL handle or result");
+    if (!(eps > 0.0 && eps < 1.0)) return fail(RE_ERR_ARG, "eps must lie in (0, 1)");
+    if (sigma_cap > 0 && !sigma_out) return fail(RE_ERR_ARG, "sigma_out is NULL");
+    cudaSetDevice(h->device);
+    const int ykind = h->opts.y_kind < 0 ? sketch_kind : h->opts.y_kind;
+    Plan P;
+    if (int r = make_plan(A, dtype, m, n, ld, sketch_kind, ykind, h->opts.s_max, &P)) return r;
+    return run_estimate(h, P, eps, seed, sigma_out, sigma_cap, out,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int re_rank_estimate_host(re_handle h, const void* A_host, int dtype, int64_t m, int64_t n,
+                          int64_t ld, double eps, int sketch_kind, uint64_t seed, double* sigma_out,
+                          int sigma_cap, re_result* out, void* stream) {
+    if (!h || !out || !A_host) return fail(RE_ERR_ARG, "NULL argument");
+    if (m <= 0 || n <= 0 || ld < n) return fail(RE_ERR_ARG, "bad shape");
+    if (dtype != RE_F32 && dtype != RE_F64) return fail(RE_ERR_ARG, "bad dtype");
+    cudaSetDevice(h->device);
+    const size_t es = dtype == RE_F32 ? 4 : 8;
+    if (int r = ensure(h->acopy, es * (size_t)m * n)) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpy2DAsync(h->acopy.p, es * n, A_host, es * ld, es * n, m,
+                                      cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "host to device copy of A");
+    return re_rank_estimate(h, h->acopy.p, dtype, m, n, n, eps, sketch_kind, seed, sigma_out,
+                            sigma_cap, out, stream);
+}
+
+int re_sketch_apply(re_handle h, const void* A, int dtype, int64_t m, int64_t n, int64_t ld,
+                    int col0, int s, int sketch_kind, uint64_t seed, float* AX, int64_t ld_ax,
+                    double* core, int64_t ld_core, void* stream) {
+    if (!h || !AX) return fail(RE_ERR_ARG, "NULL argument");
+    if (col0 < 0 || col0 % 8 != 0 || s <= 0 || s % 8 != 0)
+        return fail(RE_ERR_ARG, "col0 and s must be multiples of 8, s > 0");
+    if (ld_ax < col0 + s) return fail(RE_ERR_ARG, "ld_ax < col0 + s");
+    if (core && ld_core < col0 + s) return fail(RE_ERR_ARG, "ld_core < col0 + s");
+    cudaSetDevice(h->device);
+    const int ykind = h->opts.y_kind < 0 ? sketch_kind : h->opts.y_kind;
+    Plan P;
+    if (int r = make_plan(A, dtype, m, n, ld, sketch_kind, ykind, 1 << 30, &P)) return r;
+    if (sketch_kind == RE_SRHT && col0 + s > P.n_pad)
+        return fail(RE_ERR_ARG, "SRHT width exceeds the padded dimension");
+    if (core && ykind == RE_SRHT && 2 * (int64_t)(col0 + s) > P.m_pad)
+        return fail(RE_ERR_ARG, "SRHT left width exceeds the padded dimension");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (int r = right_columns(h, P, seed, col0, s, AX, ld_ax, st)) return r;
+    if (core) {
+        if (int r = left_blocks(h, P, seed, col0, col0 + s, AX, ld_ax, core, ld_core, st)) return r;
+    }
+    return RE_OK;
+}
+
+int re_core_sigma(re_handle h, const double* core, int r2, int s, int64_t ld, double* sigma,
+                  void* stream) {
+    if (!h || !core || !sigma) return fail(RE_ERR_ARG, "NULL argument");
+    if (s < 1 || s > 512 || r2 < s || ld < s) return fail(RE_ERR_ARG, "need 1 <= s <= 512, r2 >= s, ld >= s");
+    cudaSetDevice(h->device);
+    if (int r = ensure(h->svdws, re::svd_workspace_bytes(r2, s))) return r;
+    if (int r = ensure(h->status, 64)) return r;
+    cudaError_t e = re::launch_core_sigma(core, r2, s, ld, h->svdws.p, sigma,
+                                          static_cast<int*>(h->status.p),
+                                          static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "core singular values");
+    return RE_OK;
+}
+
+int re_embedding_x(re_handle h, int kind, uint64_t seed, int64_t n, int col0, int s, float* out,
+                   void* stream) {
+    if (!h || !out || n <= 0 || col0 < 0 || s <= 0) return fail(RE_ERR_ARG, "bad argument");
+    if (kind == RE_GAUSSIAN && (col0 % 4 != 0)) return fail(RE_ERR_ARG, "col0 must be a multiple of 4");
+    cudaSetDevice(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (kind == RE_GAUSSIAN) {
+        e = re::launch_gauss_x(seed, n, col0, s, out, s, st);
+    } else if (kind == RE_SRHT) {
+        const int bits = re::pow2_bits(n);
+        if (col0 + s > (int64_t(1) << bits)) return fail(RE_ERR_ARG, "SRHT width exceeds the padded dimension");
+        if (int r = ensure(h->dx, sizeof(uint32_t) * (size_t)((int64_t(1) << bits) / 32 + 1))) return r;
+        if (int r = ensure(h->px, sizeof(int) * (size_t)s)) return r;
+        e = re::launch_sign_bits(seed, re::kStreamDX, n, static_cast<uint32_t*>(h->dx.p), st);
+        if (e == cudaSuccess) e = re::launch_perm(seed, re::kStreamPX, bits, col0, s, static_cast<int*>(h->px.p), st);
+        if (e == cudaSuccess)
+            e = re::launch_srtt_x_dense(n, s, static_cast<const uint32_t*>(h->dx.p),
+                                        static_cast<const int*>(h->px.p), out, s, st);
+    } else {
+        return fail(RE_ERR_ARG, "unknown kind");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "embedding X");
+    return RE_OK;
+}
+
+int re_embedding_y(re_handle h, int kind, uint64_t seed, int64_t m, int row0, int r2, float* out,
+                   void* stream) {
+    if (!h || !out || m <= 0 || row0 < 0 || r2 <= 0) return fail(RE_ERR_ARG, "bad argument");
+    if (kind == RE_GAUSSIAN && (row0 % 4 != 0)) return fail(RE_ERR_ARG, "row0 must be a multiple of 4");
+    cudaSetDevice(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (kind == RE_GAUSSIAN) {
+        e = re::launch_gauss_y(seed, m, row0, r2, out, m, st);
+    } else if (kind == RE_SRHT) {
+        const int bits = re::pow2_bits(m);
+        if (row0 + r2 > (int64_t(1) << bits)) return fail(RE_ERR_ARG, "SRHT height exceeds the padded dimension");
+        if (int r = ensure(h->dy, sizeof(uint32_t) * (size_t)((int64_t(1) << bits) / 32 + 1))) return r;
+        if (int r = ensure(h->py, sizeof(int) * (size_t)r2)) return r;
+        e = re::launch_sign_bits(seed, re::kStreamDY, m, static_cast<uint32_t*>(h->dy.p), st);
+        if (e == cudaSuccess) e = re::launch_perm(seed, re::kStreamPY, bits, row0, r2, static_cast<int*>(h->py.p), st);
+        if (e == cudaSuccess)
+            e = re::launch_srtt_y_dense(m, r2, static_cast<const uint32_t*>(h->dy.p),
+                                        static_cast<const int*>(h->py.p), out, m, st);
+    } else {
+        return fail(RE_ERR_ARG, "unknown kind");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "embedding Y");
+    return RE_OK;
+}
+
+int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int dtype, double eps,
+                             int sketch_kind, uint64_t seed, double* sigma_out, int sigma_cap,
+                             re_result* out, void* stream) {
+    if (!h || (count > 0 && (!blocks || !out))) return fail(RE_ERR_ARG, "NULL argument");
+    if (count < 0) return fail(RE_ERR_ARG, "count < 0");
+    if (!(eps > 0.0 && eps < 1.0)) return fail(RE_ERR_ARG, "eps must lie in (0, 1)");
+    for (int i = 0; i < count; ++i) {
+        double* so = sigma_out ? sigma_out + (size_t)i * std::max(sigma_cap, 0) : nullptr;
+        const int r = re_rank_estimate(h, blocks[i].ptr, dtype, blocks[i].m, blocks[i].n, blocks[i].ld,
+                                       eps, sketch_kind, seed + (uint64_t)i, so,
+                                       so ? sigma_cap : 0, &out[i], stream);
+        if (r != RE_OK) {
+            if (r == RE_ERR_CUDA || r == RE_ERR_NOMEM) return r;
+            std::memset(&out[i], 0, sizeof(out[i]));
+            out[i].status = r;
+        }
+    }
+    return RE_OK;
+}
+
+}  // extern "C"

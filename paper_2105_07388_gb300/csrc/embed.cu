@@ -1,0 +1,166 @@
+// Random embeddings X and Y drawn from the counter-based generator (common.cuh):
+// Gaussian G (Sec. 1 notation; Sec. 3.4) and the SRTT ingredients D and S of
+// Eq. (Theta) (Sec. 4).  The Gaussian right embedding is written once per sketch
+// step into a small buffer (n x s, L2-resident) that the right-sketch kernels
+// stream; the left embedding Y is generated inside the left-sketch kernel and
+// is only written out here for re_embedding_y.
+#include "common.cuh"
+#include "internal.h"
+
+namespace re {
+
+namespace {
+
+// One thread per (row k, column group g): X[k][4g+t] = normal t of Philox(k, g, GX).
+__global__ void gauss_x_kernel(uint64_t seed, int64_t n, int g0, int ng, int col0, int s, float* X,
+                               int64_t ldx) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * ng) return;
+    const int64_t k = idx / ng;
+    const int g = g0 + (int)(idx % ng);
+    float z[4];
+    normals4((uint32_t)k, (uint32_t)g, kStreamGX, seed, z);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int j = 4 * g + t - col0;
+        if (j >= 0 && j < s) X[k * ldx + j] = z[t];
+    }
+}
+
+// Transposed BF16 copy for the tensor-core path: Xt[j][k] (k contiguous); rows
+// k in [n, n_alloc) are zero so full K tiles can be read past the edge.
+__global__ void gauss_xt_bf16_kernel(uint64_t seed, int64_t n, int64_t n_alloc, int g0, int ng,
+                                     int col0, int s, uint16_t* Xt, int64_t ldt) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_alloc * ng) return;
+    const int64_t k = idx % n_alloc;
+    const int g = g0 + (int)(idx / n_alloc);
+    float z[4] = {0.f, 0.f, 0.f, 0.f};
+    if (k < n) normals4((uint32_t)k, (uint32_t)g, kStreamGX, seed, z);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int j = 4 * g + t - col0;
+        if (j >= 0 && j < s) Xt[(int64_t)j * ldt + k] = (uint16_t)(__float_as_uint(z[t]) >> 16);
+    }
+}
+
+__global__ void gauss_y_kernel(uint64_t seed, int64_t m, int g0, int ng, int row0, int r2, float* Y,
+                               int64_t ldy) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * ng) return;
+    const int64_t i = idx % m;
+    const int g = g0 + (int)(idx / m);
+    float z[4];
+    normals4((uint32_t)i, (uint32_t)g, kStreamGY, seed, z);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int q = 4 * g + t - row0;
+        if (q >= 0 && q < r2) Y[(int64_t)q * ldy + i] = z[t];
+    }
+}
+
+// words[w] bit b  <=>  d_{32w+b} = -1; Philox(j/128, 0, stream, 0) supplies j mod 128.
+__global__ void sign_bits_kernel(uint64_t seed, uint32_t stream, int64_t nwords, int64_t count,
+                                 uint32_t* words) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwords) return;
+    const U4 r = philox((uint32_t)(w >> 2), 0u, stream, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const int sel = (int)(w & 3);
+    uint32_t v = sel == 0 ? r.x : sel == 1 ? r.y : sel == 2 ? r.z : r.w;
+    const int64_t first = w * 32;
+    if (first + 32 > count) {
+        const int keep = (int)(count - first);
+        v = keep <= 0 ? 0u : (keep >= 32 ? v : (v & ((1u << keep) - 1u)));
+    }
+    words[w] = v;
+}
+
+__global__ void perm_kernel(uint64_t seed, uint32_t stream, int bits, int k0, int cnt, int* out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    out[k] = (int)feistel((uint32_t)(k0 + k), bits, stream, seed);
+}
+
+__global__ void srtt_x_dense_kernel(int64_t n, int s, const uint32_t* dbits, const int* cols,
+                                    float* X, int64_t ldx) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * s) return;
+    const int64_t k = idx / s;
+    const int j = (int)(idx % s);
+    const uint32_t par = (__popcll((unsigned long long)(k & (int64_t)cols[j])) & 1) ^
+                         ((dbits[k >> 5] >> (k & 31)) & 1u);
+    X[k * ldx + j] = par ? -1.0f : 1.0f;
+}
+
+__global__ void srtt_y_dense_kernel(int64_t m, int r2, const uint32_t* dbits, const int* rows,
+                                    float* Y, int64_t ldy) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * r2) return;
+    const int q = (int)(idx / m);
+    const int64_t i = idx % m;
+    const uint32_t par = (__popcll((unsigned long long)(i & (int64_t)rows[q])) & 1) ^
+                         ((dbits[i >> 5] >> (i & 31)) & 1u);
+    Y[(int64_t)q * ldy + i] = par ? -1.0f : 1.0f;
+}
+
+inline unsigned blocks_for(int64_t total, int threads) {
+    return (unsigned)((total + threads - 1) / threads);
+}
+
+}  // namespace
+
+cudaError_t launch_gauss_x(uint64_t seed, int64_t n, int col0, int s, float* X, int64_t ldx,
+                           cudaStream_t st) {
+    if (n <= 0 || s <= 0) return cudaSuccess;
+    const int g0 = col0 / 4, g1 = (col0 + s + 3) / 4, ng = g1 - g0;
+    gauss_x_kernel<<<blocks_for(n * ng, 256), 256, 0, st>>>(seed, n, g0, ng, col0, s, X, ldx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_xt_bf16(uint64_t seed, int64_t n, int64_t n_alloc, int col0, int s,
+                                 uint16_t* Xt, int64_t ldt, cudaStream_t st) {
+    if (n_alloc <= 0 || s <= 0) return cudaSuccess;
+    const int g0 = col0 / 4, g1 = (col0 + s + 3) / 4, ng = g1 - g0;
+    gauss_xt_bf16_kernel<<<blocks_for(n_alloc * ng, 256), 256, 0, st>>>(seed, n, n_alloc, g0, ng,
+                                                                         col0, s, Xt, ldt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_y(uint64_t seed, int64_t m, int row0, int r2, float* Y, int64_t ldy,
+                           cudaStream_t st) {
+    if (m <= 0 || r2 <= 0) return cudaSuccess;
+    const int g0 = row0 / 4, g1 = (row0 + r2 + 3) / 4, ng = g1 - g0;
+    gauss_y_kernel<<<blocks_for(m * ng, 256), 256, 0, st>>>(seed, m, g0, ng, row0, r2, Y, ldy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sign_bits(uint64_t seed, uint32_t stream, int64_t count, uint32_t* words,
+                             cudaStream_t st) {
+    const int64_t nwords = (count + 31) / 32;
+    if (nwords <= 0) return cudaSuccess;
+    sign_bits_kernel<<<blocks_for(nwords, 256), 256, 0, st>>>(seed, stream, nwords, count, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perm(uint64_t seed, uint32_t stream, int bits, int k0, int cnt, int* out,
+                        cudaStream_t st) {
+    if (cnt <= 0) return cudaSuccess;
+    perm_kernel<<<blocks_for(cnt, 256), 256, 0, st>>>(seed, stream, bits, k0, cnt, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_srtt_x_dense(int64_t n, int s, const uint32_t* dbits, const int* cols, float* X,
+                                int64_t ldx, cudaStream_t st) {
+    if (n <= 0 || s <= 0) return cudaSuccess;
+    srtt_x_dense_kernel<<<blocks_for(n * s, 256), 256, 0, st>>>(n, s, dbits, cols, X, ldx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_srtt_y_dense(int64_t m, int r2, const uint32_t* dbits, const int* rows, float* Y,
+                                int64_t ldy, cudaStream_t st) {
+    if (m <= 0 || r2 <= 0) return cudaSuccess;
+    srtt_y_dense_kernel<<<blocks_for(m * r2, 256), 256, 0, st>>>(m, r2, dbits, rows, Y, ldy);
+    return cudaGetLastError();
+}
+
+}  // namespace re

@@ -1,0 +1,91 @@
+// Internal interfaces between the translation units of librankest (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rankest.h"
+
+namespace re {
+
+// Oriented view of the caller's matrix: rows >= cols.  Element (r, c) of the
+// oriented matrix sits at A[r*ld + c] (plain) or A[c*ld + r] (transposed).
+struct MatView {
+    const void* ptr;
+    int dtype;      // RE_F32 / RE_F64
+    int64_t rows;   // m' = max(m, n)
+    int64_t cols;   // n' = min(m, n)
+    int64_t ld;
+    bool trans;
+};
+
+// ---- embeddings (embed.cu) ----------------------------------------------------
+// X columns [col0, col0+s) as FP32, row-major n x ldx.
+cudaError_t launch_gauss_x(uint64_t seed, int64_t n, int col0, int s, float* X, int64_t ldx,
+                           cudaStream_t st);
+// X columns [col0, col0+s) as BF16 bits, column-major (s rows of n): Xt[j*ldt + k].
+cudaError_t launch_gauss_xt_bf16(uint64_t seed, int64_t n, int64_t n_alloc, int col0, int s,
+                                 uint16_t* Xt, int64_t ldt, cudaStream_t st);
+// Y rows [row0, row0+r2) as FP32, row-major r2 x ldy.
+cudaError_t launch_gauss_y(uint64_t seed, int64_t m, int row0, int r2, float* Y, int64_t ldy,
+                           cudaStream_t st);
+// SRTT sign bits: bit j of words[j/32] set <=> d_j = -1, j < count (stream DX or DY).
+cudaError_t launch_sign_bits(uint64_t seed, uint32_t stream, int64_t count, uint32_t* words,
+                             cudaStream_t st);
+// SRTT sampled indices pi(k0 .. k0+cnt-1) on `bits` bits (stream PX or PY).
+cudaError_t launch_perm(uint64_t seed, uint32_t stream, int bits, int k0, int cnt, int* out,
+                        cudaStream_t st);
+// Dense SRTT X / Y entries (+-1) for re_embedding_x/y.
+cudaError_t launch_srtt_x_dense(int64_t n, int s, const uint32_t* dbits, const int* cols, float* X,
+                                int64_t ldx, cudaStream_t st);
+cudaError_t launch_srtt_y_dense(int64_t m, int r2, const uint32_t* dbits, const int* rows, float* Y,
+                                int64_t ldy, cudaStream_t st);
+
+// ---- right sketch, FP32 SIMT (sketch_simt.cu) -------------------------------------
+// C[:, 0:s] (row-major, ldc) = A_oriented * X[:, 0:s], X FP32 row-major n' x ldx.
+cudaError_t launch_right_simt(const MatView& A, const float* X, int64_t ldx, int s, float* C,
+                              int64_t ldc, cudaStream_t st);
+
+// ---- left sketch (sketch_simt.cu) ---------------------------------------------
+// core[row0+r][col0+c] (FP64, ld_core) = sum_i Y[row0+r][i] * AX[i][col0+c] for
+// r < R, c < S, i < M.  Y Gaussian (kind RE_GAUSSIAN) or SRTT from dbits/perm
+// (perm holds pi_Y(q) for q in [0, row0+R)).  `part` is FP32 scratch of
+// part_cap floats.
+cudaError_t launch_left(int kind, uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0,
+                        int R, int col0, int S, const uint32_t* dbits, const int* perm,
+                        float* part, size_t part_cap, double* core, int64_t ld_core,
+                        cudaStream_t st);
+size_t left_part_floats(int64_t M, int R, int S);
+
+// ---- right sketch, SRHT (sketch_srht.cu) --------------------------------------
+// C[:, 0:s] = A_oriented * D H S^T with sampled Hadamard columns cols[0..s).
+cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int* cols, int s,
+                              float* C, int64_t ldc, cudaStream_t st);
+
+// ---- right sketch, BF16x3 tensor cores (sketch_tc.cu) ------------------------------
+bool tc_supported(const MatView& A);
+cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, int s, float* C,
+                            int64_t ldc, int* err_flag, cudaStream_t st);
+
+// ---- small core singular values (core_svd.cu) ----------------------------------
+size_t svd_workspace_bytes(int r2, int s);
+// sigma (FP64, s entries, descending, unscaled) of core (FP64 row-major r2 x s, ld).
+// status (device int): 0 ok, RE_ERR_NONFINITE if core has NaN/Inf.
+cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws,
+                              double* sigma, int* status, cudaStream_t st);
+
+// Device read-off (step 8).  Writes DevReadoff to `out`.
+struct DevReadoff {
+    int rank;        // -1 when not converged
+    int gap_index;
+    double gap_ratio;
+    double tau;
+    int status;
+    int pad;
+};
+cudaError_t launch_readoff(const double* sigma, int r1, double scale, double eps, double norm_a,
+                           const int* status_in, DevReadoff* out, double* sigma_scaled,
+                           cudaStream_t st);
+
+}  // namespace re

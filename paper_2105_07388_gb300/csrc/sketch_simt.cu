@@ -1,0 +1,416 @@
+// FP32 CUDA-core kernels of the two-sided sketch Y*A*X (Algorithm 1 steps 3 and 6).
+//
+//  * right_simt: A*X (step 3) for a Gaussian X held as an FP32 n x s buffer.
+//    A is streamed once per column tile; 128-row x BN-column CTA tiles, K steps
+//    of 32, A staged through registers into a k-major shared tile so that each
+//    thread runs an 8 x TN outer product per k.  FP64 input is rounded to FP32
+//    as it is loaded.  Transposed orientation (m < n) reads A by columns.
+//  * left_sketch: Y*(A X) (step 6) as split-K partial products over the long
+//    dimension m, with Y generated on the fly (Gaussian from the counter-based
+//    generator, or SRTT entries d_i (-1)^popcount(pi(q) & i)), reduced in FP64
+//    in a fixed order.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace re {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 32;
+constexpr int kThreads = 256;
+
+template <int BN>
+struct SimtShape;
+template <> struct SimtShape<128> { static constexpr int TN = 8, TM = 8; };
+template <> struct SimtShape<64> { static constexpr int TN = 4, TM = 8; };
+template <> struct SimtShape<32> { static constexpr int TN = 2, TM = 8; };
+template <> struct SimtShape<16> { static constexpr int TN = 1, TM = 8; };
+template <> struct SimtShape<8> { static constexpr int TN = 1, TM = 4; };
+
+template <typename TA>
+__device__ __forceinline__ float ld_as_f32(const TA* p) {
+    return (float)__ldg(p);
+}
+
+// Loads of one A tile into registers (16 values per thread), non-transposed:
+// thread t holds row (t & 127), k range [16 (t >> 7), +16).
+template <typename TA, bool TRANS>
+struct ATile {
+    float v[16];
+
+    __device__ __forceinline__ void load(const TA* __restrict__ A, int64_t lda, int64_t M,
+                                         int64_t N, int64_t m0, int64_t k0, bool vec) {
+        const int t = threadIdx.x;
+        if (!TRANS) {
+            const int64_t r = m0 + (t & 127);
+            const int64_t kb = k0 + 16 * (t >> 7);
+            if constexpr (sizeof(TA) == 4) {
+                if (vec && r < M && kb + 16 <= N) {
+                    const float4* p = reinterpret_cast<const float4*>(A + r * lda + kb);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 w = __ldg(p + q);
+                        v[4 * q + 0] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+                    }
+                    return;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                v[q] = (r < M && kb + q < N) ? ld_as_f32(A + r * lda + kb + q) : 0.0f;
+        } else {
+            // oriented (r, c) = A[c * lda + r]; thread t: c = k0 + (t >> 3), r range [16 (t & 7), +16)
+            const int64_t c = k0 + (t >> 3);
+            const int64_t rb = m0 + 16 * (t & 7);
+            if constexpr (sizeof(TA) == 4) {
+                if (vec && c < N && rb + 16 <= M) {
+                    const float4* p = reinterpret_cast<const float4*>(A + c * lda + rb);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 w = __ldg(p + q);
+                        v[4 * q + 0] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+                    }
+                    return;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                v[q] = (c < N && rb + q < M) ? ld_as_f32(A + c * lda + rb + q) : 0.0f;
+        }
+    }
+
+    // shared tile layout: As[k][m] with row pitch kBM + 4
+    __device__ __forceinline__ void store(float* As) const {
+        const int t = threadIdx.x;
+        if (!TRANS) {
+            const int r = t & 127;
+            const int kb = 16 * (t >> 7);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) As[(kb + q) * (kBM + 4) + r] = v[q];
+        } else {
+            const int c = t >> 3;
+            const int rb = 16 * (t & 7);
+            float4* p = reinterpret_cast<float4*>(As + c * (kBM + 4) + rb);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    }
+};
+
+template <int BN>
+struct XTile {
+    static constexpr int PER = BN / 8;   // floats per thread (32 x BN tile, 256 threads)
+    float v[PER];
+
+    __device__ __forceinline__ void load(const float* __restrict__ X, int64_t ldx, int64_t N,
+                                         int64_t k0, int n0) {
+        const int t = threadIdx.x;
+        const int64_t k = k0 + (t >> 3);
+        const int c = n0 + (t & 7) * PER;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) v[q] = (k < N) ? __ldg(X + k * ldx + c + q) : 0.0f;
+    }
+
+    __device__ __forceinline__ void store(float* Bs) const {
+        const int t = threadIdx.x;
+        const int k = t >> 3;
+        const int c = (t & 7) * PER;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) Bs[k * BN + c + q] = v[q];
+    }
+};
+
+template <int BN, bool TRANS, typename TA>
+__global__ void __launch_bounds__(kThreads) right_simt_kernel(const TA* __restrict__ A, int64_t lda,
+                                                              int64_t M, int64_t N,
+                                                              const float* __restrict__ X,
+                                                              int64_t ldx, float* __restrict__ C,
+                                                              int64_t ldc, int vec) {
+    using S = SimtShape<BN>;
+    constexpr int TN = S::TN, TM = S::TM;
+    constexpr int TX = BN / TN;
+    extern __shared__ float4 smem_raw[];
+    float* As = reinterpret_cast<float*>(smem_raw);              // 2 x kBK x (kBM+4)
+    float* Bs = As + 2 * kBK * (kBM + 4);                        // 2 x kBK x BN
+
+    const int n0 = blockIdx.x * BN;
+    const int64_t m0 = (int64_t)blockIdx.y * kBM;
+    const int tx = threadIdx.x % TX;
+    const int ty = threadIdx.x / TX;
+
+    float acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
+
+    ATile<TA, TRANS> at;
+    XTile<BN> xt;
+    const int64_t KT = (N + kBK - 1) / kBK;
+    at.load(A, lda, M, N, m0, 0, vec != 0);
+    xt.load(X, ldx, N, 0, n0);
+    at.store(As);
+    xt.store(Bs);
+    __syncthreads();
+
+    for (int64_t kt = 0; kt < KT; ++kt) {
+        const int buf = (int)(kt & 1);
+        const bool more = kt + 1 < KT;
+        if (more) {
+            at.load(A, lda, M, N, m0, (kt + 1) * kBK, vec != 0);
+            xt.load(X, ldx, N, (kt + 1) * kBK, n0);
+        }
+        const float* as = As + buf * kBK * (kBM + 4);
+        const float* bs = Bs + buf * kBK * BN;
+#pragma unroll 8
+        for (int k = 0; k < kBK; ++k) {
+            float a[TM], b[TN];
+            const float* ap = as + k * (kBM + 4) + ty * TM;
+#pragma unroll
+            for (int i = 0; i < TM; i += 4) {
+                const float4 w = *reinterpret_cast<const float4*>(ap + i);
+                a[i] = w.x; a[i + 1] = w.y; a[i + 2] = w.z; a[i + 3] = w.w;
+            }
+            const float* bp = bs + k * BN + tx * TN;
+            if constexpr (TN >= 4) {
+#pragma unroll
+                for (int j = 0; j < TN; j += 4) {
+                    const float4 w = *reinterpret_cast<const float4*>(bp + j);
+                    b[j] = w.x; b[j + 1] = w.y; b[j + 2] = w.z; b[j + 3] = w.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < TN; ++j) b[j] = bp[j];
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (more) {
+            at.store(As + (buf ^ 1) * kBK * (kBM + 4));
+            xt.store(Bs + (buf ^ 1) * kBK * BN);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t r = m0 + ty * TM + i;
+        if (r >= M) continue;
+        float* cp = C + r * ldc + n0 + tx * TN;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cp[j] = acc[i][j];
+    }
+}
+
+template <int BN, bool TRANS, typename TA>
+cudaError_t launch_right_simt_t(const MatView& A, const float* X, int64_t ldx, int s, float* C,
+                                int64_t ldc, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (2 * kBK * (kBM + 4) + 2 * kBK * BN);
+    auto kern = right_simt_kernel<BN, TRANS, TA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int vec = ((reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0 && (A.ld & 3) == 0) ? 1 : 0;
+    dim3 grid((unsigned)(s / BN), (unsigned)((A.rows + kBM - 1) / kBM));
+    kern<<<grid, kThreads, smem, st>>>(static_cast<const TA*>(A.ptr), A.ld, A.rows, A.cols, X, ldx,
+                                        C, ldc, vec);
+    return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t dispatch_right(const MatView& A, const float* X, int64_t ldx, int s, float* C,
+                           int64_t ldc, cudaStream_t st) {
+    if (A.dtype == RE_F32) {
+        return A.trans ? launch_right_simt_t<BN, true, float>(A, X, ldx, s, C, ldc, st)
+                       : launch_right_simt_t<BN, false, float>(A, X, ldx, s, C, ldc, st);
+    }
+    return A.trans ? launch_right_simt_t<BN, true, double>(A, X, ldx, s, C, ldc, st)
+                   : launch_right_simt_t<BN, false, double>(A, X, ldx, s, C, ldc, st);
+}
+
+// ---------------------------------------------------------------------------
+// Left sketch: part[split][r][c] = sum over the split's rows i of Y[row0+r][i] AX[i][col0+c].
+constexpr int kLR = 64;     // rows of Y per tile
+constexpr int kLK = 32;     // i per k step
+
+template <int LC, int KIND>
+__global__ void __launch_bounds__(256) left_kernel(uint64_t seed, const float* __restrict__ AX,
+                                                   int64_t ldax, int64_t M, int row0, int R,
+                                                   int col0, int S, int64_t chunk,
+                                                   const uint32_t* __restrict__ dbits,
+                                                   const int* __restrict__ perm,
+                                                   float* __restrict__ part) {
+    constexpr int TC = LC / 16;           // columns per thread
+    __shared__ __align__(16) float Ys[kLK][kLR];
+    __shared__ __align__(16) float Xs[kLK][LC];
+    const int ct = blockIdx.x, rt = blockIdx.y, split = blockIdx.z;
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;           // 16 x 16 threads, 4 rows x TC cols each
+    const int64_t i_begin = (int64_t)split * chunk;
+    const int64_t i_end = min(M, i_begin + chunk);
+    const int qbase = row0 + rt * kLR;                // first Y row of this tile (multiple of 8)
+
+    float acc[4][TC];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < TC; ++b) acc[a][b] = 0.0f;
+
+    int my_perm[4];
+    if (KIND == RE_SRHT) {
+        // each thread generates 8 entries per k step: rows 4*(tid&15)+e? use a fixed map below
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = qbase + (tid & 15) * 4 + e;
+            my_perm[e] = (q - row0 < R) ? perm[q] : 0;
+        }
+    }
+
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += kLK) {
+        // ---- Y tile: Ys[k][r] = Y[qbase + r][i0 + k]
+        if (KIND == RE_GAUSSIAN) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = tid & 31;
+                const int g = (tid >> 5) + 8 * h;        // 16 groups of 4 rows
+                const int64_t i = i0 + k;
+                float z[4] = {0.f, 0.f, 0.f, 0.f};
+                if (i < i_end && qbase + 4 * g - row0 < R)
+                    normals4((uint32_t)i, (uint32_t)((qbase >> 2) + g), kStreamGY, seed, z);
+                *reinterpret_cast<float4*>(&Ys[k][4 * g]) = make_float4(z[0], z[1], z[2], z[3]);
+            }
+        } else {
+            // thread: rows 4*(tid&15) .. +3, k = (tid >> 4) and (tid >> 4) + 16
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = (tid >> 4) + 16 * h;
+                const int64_t i = i0 + k;
+                float y[4];
+                const uint32_t di = (i < i_end) ? ((dbits[i >> 5] >> (i & 31)) & 1u) : 0u;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int q = qbase + (tid & 15) * 4 + e;
+                    const uint32_t par = (__popcll((unsigned long long)(i & (int64_t)my_perm[e])) & 1) ^ di;
+                    y[e] = (i < i_end && q - row0 < R) ? (par ? -1.0f : 1.0f) : 0.0f;
+                }
+                *reinterpret_cast<float4*>(&Ys[k][(tid & 15) * 4]) = make_float4(y[0], y[1], y[2], y[3]);
+            }
+        }
+        // ---- AX tile: Xs[k][c] = AX[i0 + k][col0 + ct*LC + c]
+        {
+            constexpr int PER = LC * kLK / 256;
+            const int k = tid / (LC / PER);
+            const int cb = (tid % (LC / PER)) * PER;
+            const int64_t i = i0 + k;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int c = ct * LC + cb + q;
+                Xs[k][cb + q] = (i < i_end && c < S) ? __ldg(AX + i * ldax + col0 + c) : 0.0f;
+            }
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kLK; ++k) {
+            const float4 yv = *reinterpret_cast<const float4*>(&Ys[k][ty * 4]);
+            const float y[4] = {yv.x, yv.y, yv.z, yv.w};
+            float x[TC];
+#pragma unroll
+            for (int b = 0; b < TC; b += 4) {
+                const float4 w = *reinterpret_cast<const float4*>(&Xs[k][tx * TC + b]);
+                x[b] = w.x; x[b + 1] = w.y; x[b + 2] = w.z; x[b + 3] = w.w;
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < TC; ++b) acc[a][b] = fmaf(y[a], x[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+    // part layout: [split][R][S]
+    float* out = part + (int64_t)split * R * S;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = rt * kLR + ty * 4 + a;
+        if (r >= R) continue;
+#pragma unroll
+        for (int b = 0; b < TC; ++b) {
+            const int c = ct * LC + tx * TC + b;
+            if (c < S) out[(int64_t)r * S + c] = acc[a][b];
+        }
+    }
+}
+
+__global__ void left_reduce_kernel(const float* __restrict__ part, int splits, int R, int S,
+                                   int row0, int col0, double* __restrict__ core, int64_t ld_core) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)R * S) return;
+    double sum = 0.0;
+    for (int p = 0; p < splits; ++p) sum += (double)part[(int64_t)p * R * S + idx];
+    const int r = (int)(idx / S), c = (int)(idx % S);
+    core[(int64_t)(row0 + r) * ld_core + col0 + c] = sum;
+}
+
+int left_splits(int64_t M, int R, int S, int64_t* chunk_out) {
+    const int tiles = ((R + kLR - 1) / kLR) * ((S + 63) / 64);
+    int splits = (int)std::max<int64_t>(1, std::min<int64_t>((M + 1023) / 1024, (4 * 152 + tiles - 1) / tiles));
+    int64_t chunk = (M + splits - 1) / splits;
+    chunk = (chunk + kLK - 1) / kLK * kLK;
+    splits = (int)((M + chunk - 1) / chunk);
+    *chunk_out = chunk;
+    return splits;
+}
+
+}  // namespace
+
+cudaError_t launch_right_simt(const MatView& A, const float* X, int64_t ldx, int s, float* C,
+                              int64_t ldc, cudaStream_t st) {
+    if (s <= 0 || A.rows <= 0) return cudaSuccess;
+    if ((A.rows + kBM - 1) / kBM > 65535) return cudaErrorInvalidConfiguration;
+    if (s % 128 == 0) return dispatch_right<128>(A, X, ldx, s, C, ldc, st);
+    if (s % 64 == 0) return dispatch_right<64>(A, X, ldx, s, C, ldc, st);
+    if (s % 32 == 0) return dispatch_right<32>(A, X, ldx, s, C, ldc, st);
+    if (s % 16 == 0) return dispatch_right<16>(A, X, ldx, s, C, ldc, st);
+    return dispatch_right<8>(A, X, ldx, s, C, ldc, st);
+}
+
+size_t left_part_floats(int64_t M, int R, int S) {
+    int64_t chunk;
+    const int splits = left_splits(M, R, S, &chunk);
+    return (size_t)splits * R * S;
+}
+
+cudaError_t launch_left(int kind, uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0,
+                        int R, int col0, int S, const uint32_t* dbits, const int* perm,
+                        float* part, size_t part_cap, double* core, int64_t ld_core,
+                        cudaStream_t st) {
+    if (R <= 0 || S <= 0) return cudaSuccess;
+    int64_t chunk;
+    const int splits = left_splits(M, R, S, &chunk);
+    if ((size_t)splits * R * S > part_cap) return cudaErrorInvalidValue;
+    const bool wide = S >= 128;
+    dim3 grid((unsigned)((S + (wide ? 127 : 63)) / (wide ? 128 : 64)), (unsigned)((R + kLR - 1) / kLR),
+              (unsigned)splits);
+    if (kind == RE_GAUSSIAN) {
+        if (wide)
+            left_kernel<128, RE_GAUSSIAN><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, dbits, perm, part);
+        else
+            left_kernel<64, RE_GAUSSIAN><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, dbits, perm, part);
+    } else {
+        if (wide)
+            left_kernel<128, RE_SRHT><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, dbits, perm, part);
+        else
+            left_kernel<64, RE_SRHT><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, dbits, perm, part);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)R * S;
+    left_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, splits, R, S, row0, col0,
+                                                                         core, ld_core);
+    return cudaGetLastError();
+}
+
+}  // namespace re

@@ -1,0 +1,211 @@
+// Right sketch with a subsampled randomized Hadamard transform (Sec. 3.4, SRTT;
+// Eq. (Theta) of Sec. 4 applied from the right: X = D H S^T over the dimension
+// n_pad = 2^ceil(log2 n) with A zero padded, Sec. 4 on zero padding):
+//
+//     AX[r, k] = sum_j A[r, j] d_j H[j, pi(k)],   H[j, c] = (-1)^popcount(j & c).
+//
+// Each row is transformed by a fast Walsh-Hadamard transform (O(n log n) per
+// row, the cost quoted for SRTTs in Sec. 3.4) and the s sampled outputs are
+// gathered.  A row of 2^L values is held by T = 2^floor(L/2) threads with
+// E = 2^L / T values each in registers:
+//   phase A  coalesced load, index = r*T + j (thread j, register r); the
+//            butterflies over the register index cover bits [log T, L);
+//   transpose through shared memory with an XOR swizzle (conflict-free both ways);
+//   phase B  index = j*E + r; butterflies over register offsets < T cover bits
+//            [0, log T);
+//   gather   the sampled outputs pi(k) from shared memory.
+// Because H_{2N}[i, c] = H_N[i, c] for i, c < N and padded inputs are zero, a
+// transform longer than n_pad gives the same sampled values, so four kernel
+// sizes (2^8, 2^10, 2^12, 2^14) serve every n <= 16384.  Longer rows
+// (n <= 32768) use a shared-memory-only transform, one row per CTA.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace re {
+
+namespace {
+
+template <typename TA>
+__device__ __forceinline__ float load_oriented(const TA* A, int64_t lda, int64_t r, int64_t c,
+                                               bool trans) {
+    return trans ? (float)__ldg(A + c * lda + r) : (float)__ldg(A + r * lda + c);
+}
+
+template <int E, int H_LIMIT>
+__device__ __forceinline__ void fwht_regs(float (&x)[E]) {
+#pragma unroll
+    for (int h = 1; h < H_LIMIT; h <<= 1) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if ((r & h) == 0) {
+                const float a = x[r], b = x[r + h];
+                x[r] = a + b;
+                x[r + h] = a - b;
+            }
+        }
+    }
+}
+
+template <int LOGN, bool TRANS, typename TA>
+__global__ void __launch_bounds__(128) srht_reg_kernel(const TA* __restrict__ A, int64_t lda,
+                                                       int64_t M, int64_t N,
+                                                       const uint32_t* __restrict__ dbits,
+                                                       const int* __restrict__ cols, int s,
+                                                       float* __restrict__ C, int64_t ldc) {
+    constexpr int NP = 1 << LOGN;
+    constexpr int LOGT = LOGN / 2;
+    constexpr int T = 1 << LOGT;
+    constexpr int LOGE = LOGN - LOGT;
+    constexpr int E = 1 << LOGE;
+    constexpr int G = 128 / T;                        // rows per CTA iteration
+    constexpr int PITCH = NP + (T < 32 ? 16 : 0);
+    constexpr int XMASK = (E < 32 ? E : 32) - 1;
+    extern __shared__ float4 smem4[];
+    float* buf = reinterpret_cast<float*>(smem4);     // G x PITCH
+    uint32_t* sd = reinterpret_cast<uint32_t*>(buf + G * PITCH);
+    int* scol = reinterpret_cast<int*>(sd + NP / 32);
+
+    const int64_t nwords = (N + 31) / 32;
+    for (int w = threadIdx.x; w < NP / 32; w += blockDim.x) sd[w] = (w < nwords) ? dbits[w] : 0u;
+    for (int k = threadIdx.x; k < s; k += blockDim.x) scol[k] = cols[k];
+    __syncthreads();
+
+    const int g = threadIdx.x / T;
+    const int j = threadIdx.x % T;
+    float* gb = buf + g * PITCH;
+    auto phys = [](int idx) { return idx ^ ((idx >> LOGE) & XMASK); };
+
+    for (int64_t row0 = (int64_t)blockIdx.x * G; row0 < M; row0 += (int64_t)gridDim.x * G) {
+        const int64_t row = row0 + g;
+        const bool live = row < M;
+        float x[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int idx = r * T + j;
+            float v = 0.0f;
+            if (live && idx < N) {
+                v = load_oriented(A, lda, row, idx, TRANS);
+                if ((sd[idx >> 5] >> (idx & 31)) & 1u) v = -v;
+            }
+            x[r] = v;
+        }
+        fwht_regs<E, E>(x);
+#pragma unroll
+        for (int r = 0; r < E; ++r) gb[phys(r * T + j)] = x[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < E; ++r) x[r] = gb[phys(j * E + r)];
+        __syncthreads();
+        fwht_regs<E, T>(x);
+#pragma unroll
+        for (int r = 0; r < E; ++r) gb[phys(j * E + r)] = x[r];
+        __syncthreads();
+        if (live) {
+            for (int k = j; k < s; k += T) C[row * ldc + k] = gb[phys(scol[k])];
+        }
+        __syncthreads();
+    }
+}
+
+// Rows longer than 2^14: whole row in shared memory, radix-2 stages.
+template <bool TRANS, typename TA>
+__global__ void __launch_bounds__(1024) srht_smem_kernel(const TA* __restrict__ A, int64_t lda,
+                                                         int64_t M, int64_t N, int logn,
+                                                         const uint32_t* __restrict__ dbits,
+                                                         const int* __restrict__ cols, int s,
+                                                         float* __restrict__ C, int64_t ldc) {
+    extern __shared__ float4 smem4[];
+    float* buf = reinterpret_cast<float*>(smem4);
+    const int np = 1 << logn;
+    for (int64_t row = blockIdx.x; row < M; row += gridDim.x) {
+        for (int idx = threadIdx.x; idx < np; idx += blockDim.x) {
+            float v = 0.0f;
+            if (idx < N) {
+                v = load_oriented(A, lda, row, idx, TRANS);
+                if ((__ldg(dbits + (idx >> 5)) >> (idx & 31)) & 1u) v = -v;
+            }
+            buf[idx] = v;
+        }
+        __syncthreads();
+        for (int h = 1; h < np; h <<= 1) {
+            for (int b = threadIdx.x; b < np / 2; b += blockDim.x) {
+                const int lo = (b / h) * 2 * h + (b % h);
+                const float a = buf[lo], c = buf[lo + h];
+                buf[lo] = a + c;
+                buf[lo + h] = a - c;
+            }
+            __syncthreads();
+        }
+        for (int k = threadIdx.x; k < s; k += blockDim.x) C[row * ldc + k] = buf[cols[k]];
+        __syncthreads();
+    }
+}
+
+int g_sm_count = 0;
+
+int sm_count() {
+    if (!g_sm_count) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (!g_sm_count) g_sm_count = 148;
+    }
+    return g_sm_count;
+}
+
+template <int LOGN, bool TRANS, typename TA>
+cudaError_t launch_reg(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
+                       int64_t ldc, cudaStream_t st) {
+    constexpr int NP = 1 << LOGN;
+    constexpr int T = 1 << (LOGN / 2);
+    constexpr int G = 128 / T;
+    constexpr int PITCH = NP + (T < 32 ? 16 : 0);
+    const size_t smem = sizeof(float) * (size_t)G * PITCH + sizeof(uint32_t) * (NP / 32) +
+                        sizeof(int) * (size_t)s;
+    auto k = srht_reg_kernel<LOGN, TRANS, TA>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t groups = (A.rows + G - 1) / G;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)std::max(per_sm, 1) * sm_count()));
+    k<<<(unsigned)grid, 128, smem, st>>>(static_cast<const TA*>(A.ptr), A.ld, A.rows, A.cols, dbits,
+                                         cols, s, C, ldc);
+    return cudaGetLastError();
+}
+
+template <bool TRANS, typename TA>
+cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
+                          int64_t ldc, cudaStream_t st) {
+    const int need = pow2_bits(A.cols);
+    if (need <= 8) return launch_reg<8, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
+    if (need <= 10) return launch_reg<10, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
+    if (need <= 12) return launch_reg<12, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
+    if (need <= 14) return launch_reg<14, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
+    if (need > 15) return cudaErrorNotSupported;
+    const size_t smem = sizeof(float) << need;
+    auto k = srht_smem_kernel<TRANS, TA>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(A.rows, (int64_t)sm_count() * 1);
+    k<<<(unsigned)grid, 1024, smem, st>>>(static_cast<const TA*>(A.ptr), A.ld, A.rows, A.cols, need,
+                                          dbits, cols, s, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int* cols, int s,
+                              float* C, int64_t ldc, cudaStream_t st) {
+    if (s <= 0 || A.rows <= 0) return cudaSuccess;
+    if (A.dtype == RE_F32)
+        return A.trans ? launch_srht_t<true, float>(A, dbits, cols, s, C, ldc, st)
+                       : launch_srht_t<false, float>(A, dbits, cols, s, C, ldc, st);
+    return A.trans ? launch_srht_t<true, double>(A, dbits, cols, s, C, ldc, st)
+                   : launch_srht_t<false, double>(A, dbits, cols, s, C, ldc, st);
+}
+
+}  // namespace re

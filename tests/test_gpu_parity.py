@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: integer and index results bit-exact (generator outputs, sampled Hadamard
+columns, ranks on inputs with a clear gap); floating point within tolerances
+derived from FP32 arithmetic (stated per test); sketched singular values within
+1e-4 * sigma^_1 of the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import algorithm1 as alg
+from oracle import rng
+from paper_2105_07388_gb300 import rankest as rk
+from paper_2105_07388_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+SIGMA_TOL = 1e-4          # |sigma_gpu - sigma_oracle| <= 1e-4 sigma^_1 (FP32 path)
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2105_07388_gb300 import build
+    build.build()
+    hd = rk.re_create(0)
+    yield hd
+    rk.re_destroy(hd)
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def ranks_agree(gpu_rank, orc, tol):
+    """Ranks equal, or the oracle has a trusted sigma within tol of its threshold
+    (then both answers are legitimate: the decision is within FP32 noise)."""
+    if gpu_rank == orc.rank:
+        return True
+    tau = orc.sigma[0] * orc._eps
+    return bool(np.any(np.abs(orc.sigma - tau) <= tol))
+
+
+def oracle_estimate(A, eps, kind, seed, **kw):
+    res = alg.rank_estimate(A, eps, kind=kind, seed=seed, **kw)
+    res._eps = eps
+    return res
+
+
+# ---------------------------------------------------------------------------
+# generator: bit-exact
+@pytest.mark.parametrize("n,col0,s", [(1000, 0, 64), (37, 8, 16), (4099, 24, 40)])
+def test_gaussian_x_bit_exact(h, n, col0, s):
+    out = torch.empty(n, s, dtype=torch.float32, device="cuda")
+    rk.re_embedding_x(h, rk.RE_GAUSSIAN, 12345, n, col0, s, out)
+    ref = rng.gaussian_x(n, s, 12345, col0).astype(np.float32)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("m,row0,r2", [(2048, 0, 128), (333, 16, 48)])
+def test_gaussian_y_bit_exact(h, m, row0, r2):
+    out = torch.empty(r2, m, dtype=torch.float32, device="cuda")
+    rk.re_embedding_y(h, rk.RE_GAUSSIAN, 777, m, row0, r2, out)
+    ref = rng.gaussian_y(r2, m, 777, row0).astype(np.float32)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("n,col0,s", [(1000, 0, 64), (16384, 8, 32), (5, 0, 8)])
+def test_srtt_x_exact(h, n, col0, s):
+    out = torch.empty(n, s, dtype=torch.float32, device="cuda")
+    rk.re_embedding_x(h, rk.RE_SRHT, 99, n, col0, s, out)
+    assert np.array_equal(out.cpu().numpy(), rng.srtt_x(n, s, 99, col0))
+
+
+@pytest.mark.parametrize("m,row0,r2", [(3000, 0, 64), (64, 8, 48)])
+def test_srtt_y_exact(h, m, row0, r2):
+    out = torch.empty(r2, m, dtype=torch.float32, device="cuda")
+    rk.re_embedding_y(h, rk.RE_SRHT, 5, m, row0, r2, out)
+    assert np.array_equal(out.cpu().numpy(), rng.srtt_y(r2, m, 5, row0))
+
+
+# ---------------------------------------------------------------------------
+# right and left sketches: FP32 error bounds against the FP64 oracle
+def _right_bound(Ao, X):
+    # |fl(A X) - A X| <= gamma_n |A| |X|; FP32 accumulation in K steps of 32 with
+    # about n/32 + 32 roundings per entry -> 2 (n/32 + 32) u |A||X| is generous.
+    n = Ao.shape[1]
+    return 2.0 * (n / 32 + 32) * U32 * (np.abs(Ao) @ np.abs(X)) + 1e-30
+
+
+@pytest.mark.parametrize("m,n,dtype,kind", [
+    (1000, 777, torch.float32, rk.RE_GAUSSIAN),
+    (300, 1100, torch.float32, rk.RE_GAUSSIAN),     # m < n: A^T is sketched
+    (513, 129, torch.float64, rk.RE_GAUSSIAN),
+    (1000, 777, torch.float32, rk.RE_SRHT),
+    (257, 3000, torch.float32, rk.RE_SRHT),
+    (700, 9000, torch.float32, rk.RE_SRHT),        # transposed
+    (9100, 9000, torch.float32, rk.RE_SRHT),       # 2^14-point register transform
+    (333, 20000, torch.float32, rk.RE_SRHT),       # shared-memory transform (2^15)
+])
+def test_right_sketch_parity(h, m, n, dtype, kind):
+    gen = np.random.default_rng(m * 7 + n)
+    A = gen.standard_normal((m, n))
+    Ad = dev(A, dtype)
+    A_used = Ad.double().cpu().numpy()                   # the values the GPU sees
+    Ao, _ = alg.orient(A_used)
+    rows, cols = Ao.shape
+    for col0, s in ((0, 16), (16, 48)):
+        AX = torch.zeros(rows, 64, dtype=torch.float32, device="cuda")
+        rk.re_sketch_apply(h, Ad, col0, s, kind, 4242, AX)
+        ref = alg.right_sketch(Ao.astype(np.float32).astype(np.float64), s, kind, 4242, col0)
+        X = alg.embeddings(kind, cols, rows, s, 4242, col0=col0, r2=0)[0]
+        got = AX[:, col0:col0 + s].double().cpu().numpy()
+        assert np.all(np.abs(got - ref) <= _right_bound(Ao.astype(np.float32).astype(np.float64), X))
+        assert np.all(AX[:, :col0].cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("kind", [rk.RE_GAUSSIAN, rk.RE_SRHT])
+def test_core_parity_with_appending(h, kind):
+    m, n = 2000, 700
+    A = np.random.default_rng(3).standard_normal((m, n)).astype(np.float32)
+    Ad = dev(A)
+    AX = torch.zeros(m, 32, dtype=torch.float32, device="cuda")
+    core = torch.zeros(64, 32, dtype=torch.float64, device="cuda")
+    rk.re_sketch_apply(h, Ad, 0, 16, kind, 31, AX, core)
+    rk.re_sketch_apply(h, Ad, 16, 16, kind, 31, AX, core)
+    A64 = A.astype(np.float64)
+    ref = alg.core(A64, 32, kind, 31)
+    X, Y = alg.embeddings(kind, n, m, 32, 31)
+    bound = 4.0 * (m / 32 + n / 32 + 64) * U32 * (np.abs(Y) @ np.abs(A64) @ np.abs(X))
+    got = core.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+def test_core_sigma_against_lapack(h):
+    for (r2, s, seed) in ((16, 8, 0), (128, 64, 1), (256, 128, 2), (512, 256, 3), (37, 29, 4)):
+        gen = np.random.default_rng(seed)
+        U, _ = np.linalg.qr(gen.standard_normal((r2, s)))
+        V, _ = np.linalg.qr(gen.standard_normal((s, s)))
+        sv = np.logspace(0, -9, s)
+        C = (U * sv) @ V.T
+        sig = torch.zeros(s, dtype=torch.float64, device="cuda")
+        rk.re_core_sigma(h, dev(C, torch.float64), sig)
+        got = sig.cpu().numpy()
+        ref = np.linalg.svd(C, compute_uv=False)
+        assert np.all(np.diff(got) <= 0)
+        assert np.max(np.abs(got - ref)) <= 2e-6 * ref[0], (r2, s, np.max(np.abs(got - ref)))
+
+
+# ---------------------------------------------------------------------------
+# end-to-end Algorithm 1
+def check_estimate(h, A_host, eps, kind, seed, dtype=torch.float32, exact=True, **kw):
+    Ad = dev(A_host, dtype)
+    A_used = Ad.double().cpu().numpy()
+    if dtype == torch.float64:
+        A_used = A_used.astype(np.float32).astype(np.float64)   # FP64 input is read as FP32
+    res, sig = rk.re_rank_estimate(h, Ad, eps, kind, seed)
+    orc = oracle_estimate(A_used, eps, kind, seed, **kw)
+    assert res.final_s == orc.final_s or not exact
+    n = min(len(sig), len(orc.sigma))
+    assert np.max(np.abs(sig[:n] - orc.sigma[:n])) <= SIGMA_TOL * orc.sigma[0]
+    tol = SIGMA_TOL * orc.sigma[0]
+    if exact:
+        assert res.rank == orc.rank
+    else:
+        assert ranks_agree(res.rank, orc, tol)
+    assert bool(res.flags & rk.RE_CONVERGED) == orc.converged
+    assert bool(res.flags & rk.RE_TRANSPOSED) == orc.transposed
+    return res, orc
+
+
+def test_small_fp64_decade_spectrum(h):
+    # 2048 x 1024 FP64, sigma_i = 10^{-(i-1)/10} (i <= 60) then 1e-12, eps = 1e-4:
+    # sigma_41 sits exactly on the threshold, so +-1 is legitimate near it.
+    sig = wl.spectrum("decade10", 1024)
+    A = wl.haar_matrix(2048, 1024, sig, seed=0).numpy()
+    res, orc = check_estimate(h, A, 1e-4, rk.RE_GAUSSIAN, 12345, dtype=torch.float64, exact=False)
+    assert res.final_s == 64 and res.passes == 4
+    assert abs(res.rank - 40) <= 1
+
+
+@pytest.mark.parametrize("kind", [rk.RE_GAUSSIAN, rk.RE_SRHT])
+@pytest.mark.parametrize("m,n,rank", [(1500, 600, 37), (600, 1500, 37), (4096, 4096, 120),
+                                      (333, 257, 5), (2000, 1000, 0)])
+def test_clear_gap_exact_rank(h, kind, m, n, rank):
+    k = min(m, n)
+    sig = wl.spectrum("step", k, rank=rank, tail_scale=1e-9) if rank else torch.full((k,), 1e-30)
+    A = wl.haar_matrix(m, n, sig, seed=rank + m).numpy()
+    if rank == 0:
+        A = np.zeros((m, n))
+    res, orc = check_estimate(h, A, 1e-4, kind, 7 + rank)
+    assert res.rank == rank
+
+
+@pytest.mark.parametrize("fam,eps", [("fe", 1e-6), ("fp", 1e-4), ("sp", 1e-2)])
+def test_ungapped_families(h, fam, eps):
+    sig = wl.spectrum(fam, 800)
+    A = wl.haar_matrix(1200, 800, sig, seed=11).numpy()
+    res, orc = check_estimate(h, A, eps, rk.RE_GAUSSIAN, 3, exact=False)
+    s = sig.numpy()
+    r = res.rank
+    assert s[r] < 10 * eps * s[0] and (r == 0 or s[r - 1] > 0.1 * eps * s[0])
+
+
+def test_tiny_and_ragged(h):
+    for (m, n, rank) in ((33, 17, 3), (17, 33, 3), (100, 1, 1), (257, 129, 20)):
+        sig = wl.spectrum("step", min(m, n), rank=rank, tail_scale=1e-10)
+        A = wl.haar_matrix(m, n, sig, seed=m).numpy()
+        res, orc = check_estimate(h, A, 1e-5, rk.RE_GAUSSIAN, 1)
+        assert res.rank == rank
+
+
+def test_lower_bound_when_capped(h):
+    sig = wl.spectrum("step", 500, rank=100, tail_scale=1e-9)
+    A = wl.haar_matrix(900, 500, sig, seed=1).numpy()
+    o = rk.make_opts(s_max=64)
+    rk.re_set_opts(h, o)
+    try:
+        res, sig_g = rk.re_rank_estimate(h, dev(A), 1e-4, rk.RE_GAUSSIAN, 2)
+    finally:
+        rk.re_set_opts(h, rk.re_opts_default())
+    assert res.flags & rk.RE_LOWER_BOUND_ONLY and res.rank == 58 and res.final_s == 64
+
+
+def test_host_entry_point_matches_device(h):
+    sig = wl.spectrum("step", 512, rank=30, tail_scale=1e-9)
+    A = wl.haar_matrix(1024, 512, sig, seed=4).numpy().astype(np.float32)
+    r1, s1 = rk.re_rank_estimate(h, dev(A), 1e-4, rk.RE_GAUSSIAN, 9)
+    r2, s2 = rk.re_rank_estimate_host(h, A, 1e-4, rk.RE_GAUSSIAN, 9)
+    assert r1.rank == r2.rank == 30 and np.array_equal(s1, s2)
+
+
+def test_errors(h):
+    A = torch.ones(64, 32, device="cuda")
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_rank_estimate(h, A, 0.0)
+    assert e.value.code == rk.RE_ERR_ARG
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_rank_estimate(h, A, 1e-3, m=64, n=32, ld=16, dtype=rk.RE_F32)
+    assert e.value.code == rk.RE_ERR_ARG
+    B = torch.randn(300, 200, device="cuda")
+    B[17, 3] = float("nan")
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_rank_estimate(h, B, 1e-3)
+    assert e.value.code == rk.RE_ERR_NONFINITE
+    B[17, 3] = float("inf")
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_rank_estimate(h, B, 1e-3)
+    assert e.value.code == rk.RE_ERR_NONFINITE
+    # the handle still works after an error
+    res, _ = rk.re_rank_estimate(h, torch.zeros(64, 32, device="cuda"), 1e-3)
+    assert res.rank == 0
+
+
+def test_batched_kernel_blocks(h):
+    shapes = wl.kernel_block_sizes(6, seed=3, lo=256, hi=1024)
+    blocks = [wl.kernel_block(m, n, seed=100 + i).cuda() for i, (m, n) in enumerate(shapes)]
+    res, sig = rk.re_rank_estimate_batched(h, blocks, 1e-6, rk.RE_GAUSSIAN, 500, sigma_cap=512)
+    for i, B in enumerate(blocks):
+        orc = oracle_estimate(B.double().cpu().numpy(), 1e-6, alg.GAUSSIAN, 500 + i)
+        assert res[i].status == 0
+        n = min(res[i].n_sigma, len(orc.sigma))
+        assert np.max(np.abs(sig[i, :n] - orc.sigma[:n])) <= SIGMA_TOL * orc.sigma[0]
+        assert ranks_agree(res[i].rank, orc, SIGMA_TOL * orc.sigma[0])
