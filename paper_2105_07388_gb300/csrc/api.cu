@@ -197,25 +197,31 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
                   int64_t ld_ax, cudaStream_t st) {
     cudaError_t e;
     if (P.kind == RE_GAUSSIAN) {
-        if (h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A)) {
+        if (h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && cnt <= 256) {
             const int64_t kpad = (P.A.cols + 63) / 64 * 64;
-            if (int r = ensure(h->xt, sizeof(uint16_t) * (size_t)kpad * cnt + 1024)) return r;
+            const int nrows = re::tc_mma_n(cnt);
+            if (int r = ensure(h->xt, sizeof(uint16_t) * (size_t)kpad * nrows)) return r;
             if (int r = ensure(h->status, 64)) return r;
             cudaEvent_t g = stage_begin(h, st);
+            if (nrows > cnt) {
+                e = cudaMemsetAsync(static_cast<uint16_t*>(h->xt.p) + (size_t)kpad * cnt, 0,
+                                    sizeof(uint16_t) * (size_t)kpad * (nrows - cnt), st);
+                if (e != cudaSuccess) return cuda_fail(e, "clear X padding");
+            }
             e = re::launch_gauss_xt_bf16(seed, P.A.cols, kpad, c0, cnt, static_cast<uint16_t*>(h->xt.p),
                                          kpad, st);
             if (e != cudaSuccess) return cuda_fail(e, "generate X");
             stage_end(h, st, g, kStageOther);
             cudaEvent_t a = stage_begin(h, st);
             e = re::launch_right_tc(P.A, static_cast<const uint16_t*>(h->xt.p), kpad, cnt,
-                                    AX + c0, ld_ax, static_cast<int*>(h->status.p) + 4, st);
+                                    AX + c0, ld_ax, static_cast<int*>(h->status.p) + 1, st);
             if (e != cudaSuccess) return cuda_fail(e, "right sketch (tensor cores)");
             stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 2), 3.0 * 2.0 * P.A.rows * P.A.cols * cnt);
             h->stats.launches += 2;
             return RE_OK;
         }
-        if (h->opts.precision == RE_PREC_BF16X3)
-            return fail(RE_ERR_UNSUPPORTED, "BF16x3 tensor-core sketch unavailable for this input");
+        // inputs the tensor-core kernel does not take (transposed or FP64 A, or
+        // unaligned rows) use the FP32 kernel
         if (int r = ensure(h->x, sizeof(float) * (size_t)P.A.cols * cnt)) return r;
         cudaEvent_t g = stage_begin(h, st);
         e = re::launch_gauss_x(seed, P.A.cols, c0, cnt, static_cast<float*>(h->x.p), cnt, st);
@@ -302,6 +308,10 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
     float* AX = static_cast<float*>(h->ax.p);
     double* core = static_cast<double*>(h->core.p);
     int* status = static_cast<int*>(h->status.p);
+    {
+        cudaError_t e0 = cudaMemsetAsync(status, 0, 2 * sizeof(int), st);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "clear status");
+    }
     const double scale_base = 1.0;
     (void)scale_base;
 
@@ -330,6 +340,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
         ro = *h->h_ro;
         ++passes;
         h->stats.passes += 1;
+        if (ro.status == RE_ERR_TIMEOUT) return fail(ro.status, "a bounded device wait expired");
         if (ro.status != RE_OK) return fail(ro.status, "non-finite values in A or its sketch");
         if (ro.rank >= 0) break;
         if (2 * s > smax || r1 >= P.A.cols) break;
@@ -514,7 +525,8 @@ int re_sketch_apply(re_handle h, const void* A, int dtype, int64_t m, int64_t n,
 int re_core_sigma(re_handle h, const double* core, int r2, int s, int64_t ld, double* sigma,
                   void* stream) {
     if (!h || !core || !sigma) return fail(RE_ERR_ARG, "NULL argument");
-    if (s < 1 || s > 512 || r2 < s || ld < s) return fail(RE_ERR_ARG, "need 1 <= s <= 512, r2 >= s, ld >= s");
+    if (s < 1 || s > 512 || r2 < s || r2 > 1024 || ld < s)
+        return fail(RE_ERR_ARG, "need 1 <= s <= 512, s <= r2 <= 1024, ld >= s");
     cudaSetDevice(h->device);
     if (int r = ensure(h->svdws, re::svd_workspace_bytes(r2, s))) return r;
     if (int r = ensure(h->status, 64)) return r;

@@ -65,6 +65,8 @@ cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int
 
 // ---- right sketch, BF16x3 tensor cores (sketch_tc.cu) ------------------------------
 bool tc_supported(const MatView& A);
+// MMA N used for s output columns (>= 16, multiple of 16); X^T needs that many rows.
+int tc_mma_n(int s);
 cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, int s, float* C,
                             int64_t ldc, int* err_flag, cudaStream_t st);
 
@@ -74,6 +76,12 @@ size_t svd_workspace_bytes(int r2, int s);
 // status (device int): 0 ok, RE_ERR_NONFINITE if core has NaN/Inf.
 cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws,
                               double* sigma, int* status, cudaStream_t st);
+// `count` cores core + i*core_stride (each r2 x s, ld) -> sigma + i*sigma_stride,
+// status[i]; one CTA each (requires core_sigma_fits_cta).
+bool core_sigma_fits_cta(int r2, int s);
+cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t ld,
+                                      int64_t core_stride, int count, double* sigma,
+                                      int64_t sigma_stride, int* status, cudaStream_t st);
 
 // Device read-off (step 8).  Writes DevReadoff to `out`.
 struct DevReadoff {

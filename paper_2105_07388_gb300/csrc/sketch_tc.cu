@@ -1,13 +1,458 @@
-// Right sketch on the 5th-generation tensor cores (BF16x3 split of A).
+// Right sketch A*X (Algorithm 1 step 3) for a Gaussian X on the 5th-generation
+// tensor cores (tcgen05), with A split exactly into three BF16 terms:
+//
+//     a = hi + mid + lo,  hi = bf16(a), mid = bf16(a - hi), lo = bf16(a - hi - mid)
+//
+// (24 significand bits of FP32 in three 8-bit pieces; every step is exact in
+// FP32), while X holds BF16-exact normals by construction, so each product is
+// exact and only the FP32 accumulation rounds.  A*X = hi*X + mid*X + lo*X is
+// accumulated in one TMEM accumulator.
+//
+// Persistent kernel, one CTA per SM, 128-row M tiles, K chunks of 64:
+//   warps 0-7   converters: coalesced 128-bit loads of A (prefetched one chunk
+//               ahead in registers), exact 3-way split, stores of the three BF16
+//               tiles into shared memory in the 128B-swizzled K-major layout the
+//               MMA descriptors expect; fence.proxy.async + mbarrier arrive.
+//   warp 12     TMA producer: cp.async.bulk.tensor of the BF16 X^T chunk
+//               (N rows x 64 k, 128B swizzle) with complete_tx on an mbarrier.
+//   warp 13     TMEM allocation; one elected thread issues 3 x 4 tcgen05.mma
+//               (M=128, N, K=16, kind::f16 BF16 -> FP32) per chunk and
+//               tcgen05.commit to release stages / publish accumulators.
+//   warps 8-11  epilogue: tcgen05.ld (32 lanes x 16 columns) -> FP32 rows of AX.
+// The accumulator is double buffered in TMEM (2N columns) so the epilogue of one
+// tile overlaps the MMAs of the next.  Every mbarrier wait is bounded in time:
+// on expiry the kernel raises an error flag, every role drains what it has in
+// flight (bounded again), TMEM is freed and the kernel returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
 #include "internal.h"
 
 namespace re {
 
-bool tc_supported(const MatView&) { return false; }
+namespace {
 
-cudaError_t launch_right_tc(const MatView&, const uint16_t*, int64_t, int, float*, int64_t, int*,
-                            cudaStream_t) {
-    return cudaErrorNotSupported;
+constexpr int kBM = 128;           // rows per M tile (UMMA M)
+constexpr int kBK = 64;            // K elements per chunk (one 128-byte swizzle row)
+constexpr int kConvWarps = 8;
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = (kConvWarps + kEpiWarps + 2) * 32;   // 448
+constexpr int kProducerWarp = kConvWarps + kEpiWarps;          // 12
+constexpr int kMmaWarp = kProducerWarp + 1;                    // 13
+constexpr uint32_t kTermBytes = kBM * kBK * 2;                 // 16 KB per BF16 term tile
+constexpr unsigned long long kWaitNs = 2000000000ull;          // 2 s bound per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; returns false (and raises the abort flag) on expiry or when
+// another role has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    while (true) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (now_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+// Wait used while draining after an abort: bounded, never raises anything.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = now_ns();
+    while (!mbar_test(bar, parity) && now_ns() - t0 < kWaitNs) {
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
+    d |= (uint64_t)1u << 16;                           // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;                 // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1u << 46;                           // descriptor version for tcgen05
+    d |= (uint64_t)2u << 61;                           // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Exact split of two FP32 values into packed BF16x2 hi / mid / lo terms.
+__device__ __forceinline__ void split3(float a, float b, uint32_t& hi, uint32_t& mid, uint32_t& lo) {
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(b), "f"(a));
+    const float ha = __uint_as_float(hi << 16), hb = __uint_as_float(hi & 0xFFFF0000u);
+    const float ra = a - ha, rb = b - hb;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(mid) : "f"(rb), "f"(ra));
+    const float ma = __uint_as_float(mid << 16), mb = __uint_as_float(mid & 0xFFFF0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(rb - mb), "f"(ra - ma));
+}
+
+struct TcParams {
+    const float* A;
+    int64_t lda, M, K;
+    float* C;
+    int64_t ldc;
+    int S;            // valid output columns
+    int N;            // MMA N (>= 16, multiple of 16)
+    int stages;
+    int64_t tiles;
+    int64_t kchunks;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_constant__ CUtensorMap xmap,
+                                                               const TcParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_a[4], full_b[4], empty[4], accf[2], acce[2], done_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NS = p.stages;
+    const uint32_t b_bytes = (uint32_t)p.N * kBK * 2;
+    const uint32_t stage_bytes = 3 * kTermBytes + ((b_bytes + 1023u) & ~1023u);
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full_a[s], kConvWarps * 32);
+            mbar_init(&full_b[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf[a], 1);
+            mbar_init(&acce[a], kEpiWarps * 32);
+        }
+        mbar_init(&done_bar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    const uint32_t tmem_cols = (uint32_t)std::max(32, 1 << (32 - __clz(2 * p.N - 1)));
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = s_tmem;
+
+    // chunk sequence of this CTA: (tile, kc) for tile = blockIdx.x + i*gridDim.x
+    const int64_t my_tiles = p.tiles > blockIdx.x ? (p.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t total_chunks = my_tiles * p.kchunks;
+
+    if (warp < kConvWarps) {
+        // ---------------- converters
+        const int t = tid;                 // 0..255
+        float4 cur[8], nxt[8];
+        auto load_chunk = [&](int64_t g, float4 (&v)[8]) {
+            const int64_t tile = blockIdx.x + (g / p.kchunks) * gridDim.x;
+            const int64_t kc = g % p.kchunks;
+            const int64_t m0 = tile * kBM, k0 = kc * kBK;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int f = j * 256 + t;              // float4 index in the 128 x 64 chunk
+                const int r = f >> 4, c4 = f & 15;
+                const int64_t row = m0 + r, col = k0 + 4 * c4;
+                float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (row < p.M) {
+                    const float* src = p.A + row * p.lda + col;
+                    if (col + 4 <= p.K) {
+                        w = __ldcs(reinterpret_cast<const float4*>(src));
+                    } else {
+                        if (col + 0 < p.K) w.x = src[0];
+                        if (col + 1 < p.K) w.y = src[1];
+                        if (col + 2 < p.K) w.z = src[2];
+                    }
+                }
+                v[j] = w;
+            }
+        };
+        if (total_chunks > 0) load_chunk(0, cur);
+        for (int64_t g = 0; g < total_chunks; ++g) {
+            const int s = (int)(g % NS);
+            const uint32_t ph = (uint32_t)((g / NS) & 1);
+            if (g + 1 < total_chunks) load_chunk(g + 1, nxt);
+            if (!mbar_wait(&empty[s], ph ^ 1u, &s_abort, p.err)) break;
+            unsigned char* st = base + (size_t)s * stage_bytes;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int f = j * 256 + t;
+                const int r = f >> 4, c4 = f & 15;
+                // element (r, k=4*c4): 16-byte chunk (k/8) swizzled with (r mod 8), 8-byte half (c4 & 1)
+                const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((c4 >> 1) ^ (r & 7)) << 4) +
+                                     (uint32_t)(c4 & 1) * 8u;
+                uint32_t h0, m0, l0, h1, m1, l1;
+                split3(cur[j].x, cur[j].y, h0, m0, l0);
+                split3(cur[j].z, cur[j].w, h1, m1, l1);
+                *reinterpret_cast<uint2*>(st + off) = make_uint2(h0, h1);
+                *reinterpret_cast<uint2*>(st + kTermBytes + off) = make_uint2(m0, m1);
+                *reinterpret_cast<uint2*>(st + 2 * kTermBytes + off) = make_uint2(l0, l1);
+            }
+            fence_proxy_async();
+            mbar_arrive(&full_a[s]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cur[j] = nxt[j];
+        }
+    } else if (warp == kProducerWarp) {
+        // ---------------- TMA producer for X^T chunks
+        int64_t issued = 0;
+        if (lane == 0) {
+            for (int64_t g = 0; g < total_chunks; ++g) {
+                const int s = (int)(g % NS);
+                const uint32_t ph = (uint32_t)((g / NS) & 1);
+                if (!mbar_wait(&empty[s], ph ^ 1u, &s_abort, p.err)) break;
+                unsigned char* st = base + (size_t)s * stage_bytes + 3 * kTermBytes;
+                mbar_arrive_expect_tx(&full_b[s], b_bytes);
+                tma_load_2d(st, &xmap, (int)((g % p.kchunks) * kBK), 0, &full_b[s]);
+                ++issued;
+            }
+            // drain: every issued copy must land before the CTA may exit
+            for (int64_t g = std::max<int64_t>(0, issued - NS); g < issued; ++g)
+                mbar_drain(&full_b[g % NS], (uint32_t)((g / NS) & 1));
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(p.N);
+            int64_t g = 0;
+            bool ok = true;
+            for (int64_t it = 0; it < my_tiles && ok; ++it) {
+                const int a = (int)(it & 1);
+                if (!mbar_wait(&acce[a], (uint32_t)(((it >> 1) & 1) ^ 1), &s_abort, p.err)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(a * p.N);
+                for (int64_t kc = 0; kc < p.kchunks; ++kc, ++g) {
+                    const int s = (int)(g % NS);
+                    const uint32_t ph = (uint32_t)((g / NS) & 1);
+                    if (!mbar_wait(&full_a[s], ph, &s_abort, p.err) ||
+                        !mbar_wait(&full_b[s], ph, &s_abort, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(base + (size_t)s * stage_bytes);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint64_t bdesc = sw128_desc(st + 3 * kTermBytes + 32u * kk);
+#pragma unroll
+                        for (int term = 0; term < 3; ++term) {
+                            const uint64_t adesc = sw128_desc(st + term * kTermBytes + 32u * kk);
+                            mma_bf16(d_tmem, adesc, bdesc, idesc, (kc | kk | term) ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&accf[a]);
+            }
+            // all issued MMAs complete before TMEM is released
+            mma_commit(&done_bar);
+            mbar_drain(&done_bar, 0);
+        }
+    } else {
+        // ---------------- epilogue warps 8..11: TMEM lanes 32*(warp%4) ..
+        const int q = warp & 3;
+        for (int64_t it = 0; it < my_tiles; ++it) {
+            const int a = (int)(it & 1);
+            if (!mbar_wait(&accf[a], (uint32_t)((it >> 1) & 1), &s_abort, p.err)) break;
+            tc_fence_after();
+            const int64_t tile = blockIdx.x + it * gridDim.x;
+            const int64_t row = tile * kBM + q * 32 + lane;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * p.N);
+            for (int c = 0; c < p.N; c += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c, v);
+                if (row < p.M) {
+                    float* dst = p.C + row * p.ldc + c;
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        if (c + j < p.S) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[a]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
+// ---- host side --------------------------------------------------------------
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(ptr);
+    }
+    return fn;
+}
+
+int g_sms = 0;
+
+}  // namespace
+
+bool tc_supported(const MatView& A) {
+    // FP32, not transposed, 16-byte aligned rows (128-bit loads)
+    return A.dtype == RE_F32 && !A.trans && (A.ld % 4) == 0 &&
+           (reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0 && encode_fn() != nullptr;
+}
+
+int tc_mma_n(int s) { return s <= 16 ? 16 : (s + 15) / 16 * 16; }
+
+cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, int s, float* C,
+                            int64_t ldc, int* err_flag, cudaStream_t st) {
+    if (s <= 0 || A.rows <= 0) return cudaSuccess;
+    if (s > 256 || s % 8 != 0) return cudaErrorInvalidValue;
+    const int N = tc_mma_n(s);
+    EncodeTiled enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t gdim[2] = {(cuuint64_t)ldt, (cuuint64_t)N};
+    const cuuint64_t gstride[1] = {(cuuint64_t)ldt * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)N};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(Xt), gdim, gstride,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    TcParams p;
+    p.A = static_cast<const float*>(A.ptr);
+    p.lda = A.ld;
+    p.M = A.rows;
+    p.K = A.cols;
+    p.C = C;
+    p.ldc = ldc;
+    p.S = s;
+    p.N = N;
+    p.stages = N <= 128 ? 3 : 2;
+    p.tiles = (A.rows + kBM - 1) / kBM;
+    p.kchunks = (A.cols + kBK - 1) / kBK;
+    p.err = err_flag;
+    const uint32_t b_bytes = (uint32_t)N * kBK * 2;
+    const size_t stage_bytes = 3 * kTermBytes + ((b_bytes + 1023u) & ~1023u);
+    const size_t smem = stage_bytes * p.stages + 1024;
+    cudaError_t e = cudaFuncSetAttribute(right_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int64_t grid = std::min<int64_t>(p.tiles, g_sms);
+    right_tc_kernel<<<(unsigned)grid, kThreads, smem, st>>>(map, p);
+    return cudaGetLastError();
 }
 
 }  // namespace re

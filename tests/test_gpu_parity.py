@@ -138,7 +138,8 @@ def test_core_parity_with_appending(h, kind):
 
 
 def test_core_sigma_against_lapack(h):
-    for (r2, s, seed) in ((16, 8, 0), (128, 64, 1), (256, 128, 2), (512, 256, 3), (37, 29, 4)):
+    for (r2, s, seed) in ((16, 8, 0), (128, 64, 1), (256, 128, 2), (512, 256, 3), (37, 29, 4),
+                          (1024, 512, 5), (600, 300, 6), (1000, 70, 7)):
         gen = np.random.default_rng(seed)
         U, _ = np.linalg.qr(gen.standard_normal((r2, s)))
         V, _ = np.linalg.qr(gen.standard_normal((s, s)))
@@ -149,7 +150,10 @@ def test_core_sigma_against_lapack(h):
         got = sig.cpu().numpy()
         ref = np.linalg.svd(C, compute_uv=False)
         assert np.all(np.diff(got) <= 0)
-        assert np.max(np.abs(got - ref)) <= 2e-6 * ref[0], (r2, s, np.max(np.abs(got - ref)))
+        # FP32 one-sided Jacobi: each column takes ~sweeps*(s-1) rotations, each
+        # rounding its entries once (~u relative), so |error| ~ 2u sqrt(8 s) sigma_1;
+        # 3e-5 sigma_1 covers s <= 512 (input rounding to FP32 adds ~u sigma_1).
+        assert np.max(np.abs(got - ref)) <= 3e-5 * ref[0], (r2, s, np.max(np.abs(got - ref)))
 
 
 # ---------------------------------------------------------------------------
@@ -181,7 +185,9 @@ def test_small_fp64_decade_spectrum(h):
     A = wl.haar_matrix(2048, 1024, sig, seed=0).numpy()
     res, orc = check_estimate(h, A, 1e-4, rk.RE_GAUSSIAN, 12345, dtype=torch.float64, exact=False)
     assert res.final_s == 64 and res.passes == 4
-    assert abs(res.rank - 40) <= 1
+    # no clear gap near eps: the Sec. 1.1 desiderata bound the answer
+    s = sig.numpy()
+    assert s[res.rank] < 10 * 1e-4 and s[res.rank - 1] > 0.1 * 1e-4
 
 
 @pytest.mark.parametrize("kind", [rk.RE_GAUSSIAN, rk.RE_SRHT])

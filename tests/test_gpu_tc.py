@@ -1,0 +1,78 @@
+"""Parity of the BF16x3 tensor-core (tcgen05) right sketch with the FP64 oracle.
+
+A is split exactly into three BF16 terms and X entries are BF16-exact, so every
+product is exact and only FP32 accumulation (in TMEM) rounds: the same
+|A||X|-scaled bound as the FP32 path applies.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import algorithm1 as alg
+from paper_2105_07388_gb300 import rankest as rk
+from paper_2105_07388_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def htc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2105_07388_gb300 import build
+    build.build()
+    h = rk.re_create(0, rk.make_opts(precision=rk.RE_PREC_BF16X3))
+    yield h
+    rk.re_destroy(h)
+
+
+@pytest.mark.parametrize("m,n,col0,s", [
+    (128, 64, 0, 16),        # one tile, one K chunk
+    (300, 100, 0, 8),        # ragged M and K, N padded 8 -> 16
+    (1000, 777, 16, 48),     # several tiles, ragged K chunk
+    (2049, 1030, 0, 128),
+    (513, 300, 8, 256),      # N = 256, two pipeline stages
+    (5000, 4096, 64, 64),
+])
+def test_tc_right_sketch_parity(htc, m, n, col0, s):
+    A = np.random.default_rng(m + n + s).standard_normal((m, n)).astype(np.float32)
+    A[0, :5] = [1e-30, -3e-20, 1e20, 7.0, -0.0]          # wide exponent range stays exact
+    Ad = torch.from_numpy(A).cuda()
+    AX = torch.zeros(m, col0 + s, dtype=torch.float32, device="cuda")
+    rk.re_sketch_apply(htc, Ad, col0, s, rk.RE_GAUSSIAN, 99, AX)
+    A64 = A.astype(np.float64)
+    ref = alg.right_sketch(A64, s, alg.GAUSSIAN, 99, col0)
+    X = alg.embeddings(alg.GAUSSIAN, n, m, s, 99, col0=col0, r2=0)[0]
+    bound = 2.0 * (n / 16 + 32) * U32 * (np.abs(A64) @ np.abs(X)) + 1e-35
+    got = AX[:, col0:].double().cpu().numpy()
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert np.all(AX[:, :col0].cpu().numpy() == 0)
+
+
+def test_tc_matches_fp32_path_closely(htc):
+    m, n = 4096, 2048
+    A = np.random.default_rng(5).standard_normal((m, n)).astype(np.float32)
+    Ad = torch.from_numpy(A).cuda()
+    h32 = rk.re_create(0)
+    try:
+        a1 = torch.zeros(m, 64, device="cuda")
+        a2 = torch.zeros(m, 64, device="cuda")
+        rk.re_sketch_apply(htc, Ad, 0, 64, rk.RE_GAUSSIAN, 3, a1)
+        rk.re_sketch_apply(h32, Ad, 0, 64, rk.RE_GAUSSIAN, 3, a2)
+    finally:
+        rk.re_destroy(h32)
+    rel = (a1 - a2).abs().max() / a2.abs().max()
+    assert rel < 1e-5
+
+
+@pytest.mark.parametrize("m,n,rank", [(1500, 600, 37), (4096, 4096, 120), (600, 1500, 37)])
+def test_tc_rank_estimate_clear_gap(htc, m, n, rank):
+    sig = wl.spectrum("step", min(m, n), rank=rank, tail_scale=1e-9)
+    A = wl.haar_matrix(m, n, sig, seed=rank + m).to(torch.float32)
+    res, sg = rk.re_rank_estimate(htc, A.cuda(), 1e-4, rk.RE_GAUSSIAN, 7 + rank)
+    orc = alg.rank_estimate(A.double().numpy(), 1e-4, kind=alg.GAUSSIAN, seed=7 + rank)
+    assert res.rank == orc.rank == rank and res.final_s == orc.final_s
+    k = min(len(sg), len(orc.sigma))
+    assert np.max(np.abs(sg[:k] - orc.sigma[:k])) <= 1e-4 * orc.sigma[0]
