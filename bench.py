@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     "large": dict(m=65536, n=16384, rank=200, eps=1e-4, seed=1, sketch_seed=12345),
+    "medium": dict(m=16384, n=16384, rank=200, eps=1e-4, seed=1, sketch_seed=12345),
     "small": dict(m=2048, n=1024, rank=40, eps=1e-4, seed=0, sketch_seed=12345),
 }
 
@@ -156,7 +157,7 @@ def main():
     kind_code = 0 if args.kind == "gaussian" else 1
     cfg = {"workload": f"single matrix {w['m']}x{w['n']} FP32, sigma=1 (i<=200) then 1e-6/i, "
                        f"eps={w['eps']}, {args.kind} X and Y, s=8..256 doubling"
-           if args.workload == "large" else
+           if args.workload in ("large", "medium") else
            f"single matrix {w['m']}x{w['n']}, sigma=10^-(i-1)/10, eps={w['eps']}",
            "m": w["m"], "n": w["n"], "dtype_A": "f32", "eps": w["eps"], "sketch": args.kind,
            "precision": args.precision, "l2": "inputs larger than L2 (4 GiB A), no flush",

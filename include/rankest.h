@@ -97,7 +97,8 @@ typedef struct {
     int passes;        /* passes over A (sketch steps) */
     uint32_t flags;    /* RE_CONVERGED | RE_LOWER_BOUND_ONLY | RE_TRANSPOSED */
     int status;        /* per-estimate status (batched calls): RE_OK or RE_ERR_* */
-    int reserved[3];
+    int svd_sweeps;    /* Jacobi sweeps used by the last small-core singular value step */
+    int reserved[2];
 } re_result;
 
 /* One block of a batched estimate: a device matrix, row-major. */

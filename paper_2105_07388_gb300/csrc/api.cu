@@ -309,7 +309,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
     double* core = static_cast<double*>(h->core.p);
     int* status = static_cast<int*>(h->status.p);
     {
-        cudaError_t e0 = cudaMemsetAsync(status, 0, 2 * sizeof(int), st);
+        cudaError_t e0 = cudaMemsetAsync(status, 0, 4 * sizeof(int), st);
         if (e0 != cudaSuccess) return cuda_fail(e0, "clear status");
     }
     const double scale_base = 1.0;
@@ -365,6 +365,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
     out->passes = passes;
     out->flags = (conv ? RE_CONVERGED : RE_LOWER_BOUND_ONLY) | (P.A.trans ? RE_TRANSPOSED : 0u);
     out->status = RE_OK;
+    out->svd_sweeps = ro.sweeps;
     return RE_OK;
 }
 

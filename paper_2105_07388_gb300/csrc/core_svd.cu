@@ -40,6 +40,9 @@ constexpr int kSvdThreads = 512;
 constexpr int kMaxSweeps = 40;
 constexpr float kU = 5.9604644775390625e-08f;        // 2^-24
 constexpr float kAbsFloor = 1e-14f;                  // (1e-7)^2 of max column norm^2
+// A sweep whose largest rotated |cos| is below kStopFactor * u * sqrt(n) only
+// rotated pairs at the FP32 rounding level of the dot products: stop there.
+constexpr float kStopFactor = 32.f;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -70,12 +73,18 @@ __device__ __forceinline__ float group_sum(float v) {
 // Jacobi rotation of columns a, b (length n) by a group of kG lanes; returns 1 if
 // this group rotated.  Every lane of the warp must call it (the reductions use
 // full-warp shuffles); inactive groups pass active = false.
+// n is a multiple of kG (columns are zero padded); the four groups of a warp
+// start their traversal kG*g elements apart so that, with column strides that
+// are multiples of 32 floats, they touch disjoint shared-memory banks.
 __device__ __forceinline__ int rotate_pair(bool active, float* a, float* b, int n, float tol,
-                                           float floor_abs) {
+                                           float floor_abs, float* meas) {
     const int gl = threadIdx.x & (kG - 1);
+    const int J = n / kG;
+    const int j0 = J > 0 ? ((threadIdx.x >> 3) & 3) % J : 0;
     float al = 0.f, be = 0.f, ga = 0.f;
     if (active) {
-        for (int i = gl; i < n; i += kG) {
+        for (int jj = 0, j = j0; jj < J; ++jj, j = (j + 1 == J) ? 0 : j + 1) {
+            const int i = j * kG + gl;
             const float x = a[i], y = b[i];
             al = fmaf(x, x, al);
             be = fmaf(y, y, be);
@@ -87,12 +96,14 @@ __device__ __forceinline__ int rotate_pair(bool active, float* a, float* b, int 
     ga = group_sum(ga);
     const float ag = fabsf(ga);
     if (!active || !(ag > tol * sqrtf(al) * sqrtf(be)) || !(ag > floor_abs)) return 0;
+    *meas = ag / (sqrtf(al) * sqrtf(be));
     const float zeta = (be - al) / (ga + ga);
     const float tt = fabsf(zeta) > 1e15f ? 0.5f / zeta
                                          : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
     const float c = 1.f / sqrtf(1.f + tt * tt);
     const float sn = c * tt;
-    for (int i = gl; i < n; i += kG) {
+    for (int jj = 0, j = j0; jj < J; ++jj, j = (j + 1 == J) ? 0 : j + 1) {
+        const int i = j * kG + gl;
         const float x = a[i], y = b[i];
         a[i] = fmaf(c, x, -sn * y);
         b[i] = fmaf(sn, x, c * y);
@@ -157,11 +168,13 @@ __global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
     extern __shared__ __align__(16) unsigned char smem[];
     core += (int64_t)blockIdx.x * core_stride;
     sigma += (int64_t)blockIdx.x * sigma_stride;
+    const int sp = (s + 31) / 32 * 32;                  // padded column length of R^T
     float* W = reinterpret_cast<float*>(smem);          // r2 x s, column-major
-    float* Rt = W + (size_t)r2 * s;                     // s x s, column c = row c of R
+    float* Rt = W + (size_t)r2 * s;                     // sp x s, column c = row c of R
     __shared__ double s_norm[512];
     __shared__ float s_tau, s_red[32];
     __shared__ int s_bad, s_flag;
+    __shared__ unsigned int s_meas;
     __shared__ unsigned long long s_dmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
@@ -218,9 +231,9 @@ __global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
         __syncthreads();
     }
     // R^T: column c of Rt = row c of R = W[j][c] for j >= c
-    for (int64_t idx = tid; idx < (int64_t)s * s; idx += blockDim.x) {
-        const int c = (int)(idx / s), j = (int)(idx % s);
-        Rt[(size_t)c * s + j] = j >= c ? W[(size_t)j * r2 + c] : 0.f;
+    for (int64_t idx = tid; idx < (int64_t)s * sp; idx += blockDim.x) {
+        const int c = (int)(idx / sp), j = (int)(idx % sp);
+        Rt[(size_t)c * sp + j] = (j >= c && j < s) ? W[(size_t)j * r2 + c] : 0.f;
     }
     __syncthreads();
 
@@ -231,11 +244,14 @@ __global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
         float amax = 0.f;
         for (int j = warp; j < s; j += nwarps) {
             float a = 0.f;
-            for (int i = lane; i < s; i += 32) a = fmaf(Rt[(size_t)j * s + i], Rt[(size_t)j * s + i], a);
+            for (int i = lane; i < sp; i += 32) a = fmaf(Rt[(size_t)j * sp + i], Rt[(size_t)j * sp + i], a);
             amax = fmaxf(amax, warp_sum(a));
         }
         if (lane == 0) s_red[warp] = amax;
-        if (tid == 0) s_flag = 0;
+        if (tid == 0) {
+            s_flag = 0;
+            s_meas = 0u;
+        }
         __syncthreads();
         if (warp == 0) {
             const float v = warp_max(lane < nwarps ? s_red[lane] : 0.f);
@@ -257,18 +273,26 @@ __global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
                     qq = max(c1, c2);
                     act = qq < s;
                 }
-                if (rotate_pair(act, Rt + (size_t)p * s, Rt + (size_t)qq * s, s, tol, floor_abs) &&
-                    (tid & (kG - 1)) == 0)
+                float meas = 0.f;
+                if (rotate_pair(act, Rt + (size_t)p * sp, Rt + (size_t)qq * sp, sp, tol, floor_abs, &meas) &&
+                    (tid & (kG - 1)) == 0) {
                     s_flag = 1;
+                    atomicMax(&s_meas, __float_as_uint(meas));
+                }
             }
             __syncthreads();
         }
         const int any = s_flag;
+        const float worst = __uint_as_float(s_meas);
         __syncthreads();
-        if (!any) break;
+        if (!any || worst < kStopFactor * kU * sqrtf((float)s)) {
+            if (tid == 0 && blockIdx.x == 0 && sigma_stride == 0) status[2] = sweep + 1;
+            break;
+        }
+        if (tid == 0 && blockIdx.x == 0 && sigma_stride == 0) status[2] = sweep + 1;
     }
     for (int j = warp; j < s; j += nwarps) {
-        const double nv = col_norm(Rt + (size_t)j * s, s);
+        const double nv = col_norm(Rt + (size_t)j * sp, sp);
         if (lane == 0) s_norm[j] = nv;
     }
     __syncthreads();
@@ -288,13 +312,15 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
     const int nloc = (s + CL - 1) / CL;
+    const int sp = (s + 31) / 32 * 32;                         // padded column length of R^T
     float* W = reinterpret_cast<float*>(smem);                // nloc x r2 (column-major)
     float* slot0 = W + (size_t)nloc * r2;                     // b columns of R^T (length s)
-    float* slot1 = slot0 + (size_t)b * s;
-    float* vbuf = slot1 + (size_t)b * s;                      // 2 x r2 Householder vectors
+    float* slot1 = slot0 + (size_t)b * sp;
+    float* vbuf = slot1 + (size_t)b * sp;                     // 2 x r2 Householder vectors
     __shared__ float s_tau[2];
     __shared__ int s_block[2];
     __shared__ int s_count, s_bad;
+    __shared__ unsigned int s_meas;
     __shared__ float s_fmax;
     __shared__ unsigned long long s_dmax;
     __shared__ double s_norm[512];
@@ -307,6 +333,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         s_bad = 0;
         s_dmax = 0ull;
         s_count = 0;
+        s_meas = 0u;
     }
     __syncthreads();
     {
@@ -388,14 +415,14 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         s_block[0] = k;
         s_block[1] = P2 - 1 - k;
     }
-    for (int64_t idx = tid; idx < 2 * (int64_t)b * s; idx += blockDim.x) {
-        const int sl = (int)(idx / ((int64_t)b * s));
-        const int64_t off = idx % ((int64_t)b * s);
-        const int jj = (int)(off / s), col = (int)(off % s);     // entry col of R^T column c
+    for (int64_t idx = tid; idx < 2 * (int64_t)b * sp; idx += blockDim.x) {
+        const int sl = (int)(idx / ((int64_t)b * sp));
+        const int64_t off = idx % ((int64_t)b * sp);
+        const int jj = (int)(off / sp), col = (int)(off % sp);   // entry col of R^T column c
         const int blk = sl == 0 ? k : P2 - 1 - k;
         const int c = blk * b + jj;                              // = row c of R
         float val = 0.f;
-        if (c < s && col >= c) {
+        if (c < s && col >= c && col < s) {
             const float* src = cluster.map_shared_rank(W, col % CL);
             val = src[(size_t)(col / CL) * r2 + c];
         }
@@ -406,13 +433,13 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
     // ---- blocked Jacobi on R^T (length-s columns)
     const float tol = 4.f * kU * sqrtf((float)s);
     float stage[kPullRegs];
-    const int per_thread = (2 * b * s + kSvdThreads - 1) / kSvdThreads;
+    const int per_thread = (2 * b * sp + kSvdThreads - 1) / kSvdThreads;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         float amax = 0.f;
         for (int q = warp; q < 2 * b; q += nwarps) {
-            const float* a = slot0 + (size_t)q * s;
+            const float* a = slot0 + (size_t)q * sp;
             float acc = 0.f;
-            for (int i = lane; i < s; i += 32) acc = fmaf(a[i], a[i], acc);
+            for (int i = lane; i < sp; i += 32) acc = fmaf(a[i], a[i], acc);
             amax = fmaxf(amax, warp_sum(acc));
         }
         if (lane == 0) s_red[warp] = amax;
@@ -446,10 +473,14 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
                             const int p = min(c1, c2), qq = max(c1, c2);
                             act = qq < b;
                             float* bs = sl == 0 ? slot0 : slot1;
-                            pa = bs + (size_t)p * s;
-                            pb = bs + (size_t)qq * s;
+                            pa = bs + (size_t)p * sp;
+                            pb = bs + (size_t)qq * sp;
                         }
-                        if (rotate_pair(act, pa, pb, s, tol, floor_abs) && leader) rotated = 1;
+                        float meas = 0.f;
+                        if (rotate_pair(act, pa, pb, sp, tol, floor_abs, &meas) && leader) {
+                            rotated = 1;
+                            atomicMax(&s_meas, __float_as_uint(meas));
+                        }
                     }
                     __syncthreads();
                 }
@@ -460,9 +491,12 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
                     const int j = base + grp;
                     const bool act = j < b;
                     const int jj = act ? (j + u) % b : 0;
-                    if (rotate_pair(act, slot0 + (size_t)(act ? j : 0) * s, slot1 + (size_t)jj * s, s, tol,
-                                    floor_abs) && leader)
+                    float meas = 0.f;
+                    if (rotate_pair(act, slot0 + (size_t)(act ? j : 0) * sp, slot1 + (size_t)jj * sp, sp, tol,
+                                    floor_abs, &meas) && leader) {
                         rotated = 1;
+                        atomicMax(&s_meas, __float_as_uint(meas));
+                    }
                 }
                 __syncthreads();
             }
@@ -479,13 +513,13 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
 #pragma unroll
             for (int q = 0; q < kPullRegs; ++q) {
                 const int64_t idx = (int64_t)q * kSvdThreads + tid;
-                if (q < per_thread && idx < 2 * (int64_t)b * s) {
-                    const int sl = (int)(idx / ((int64_t)b * s));
-                    const int64_t off = idx % ((int64_t)b * s);
+                if (q < per_thread && idx < 2 * (int64_t)b * sp) {
+                    const int sl = (int)(idx / ((int64_t)b * sp));
+                    const int64_t off = idx % ((int64_t)b * sp);
                     const int src = sl == 0 ? src0 : src1;
                     if (src >= 0) {
                         const float* rs = cluster.map_shared_rank(slot0, cta_of(src));
-                        stage[q] = rs[(size_t)slot_of(src) * b * s + off];
+                        stage[q] = rs[(size_t)slot_of(src) * b * sp + off];
                     } else {
                         stage[q] = slot0[off];
                     }
@@ -495,7 +529,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
 #pragma unroll
             for (int q = 0; q < kPullRegs; ++q) {
                 const int64_t idx = (int64_t)q * kSvdThreads + tid;
-                if (q < per_thread && idx < 2 * (int64_t)b * s) slot0[idx] = stage[q];
+                if (q < per_thread && idx < 2 * (int64_t)b * sp) slot0[idx] = stage[q];
             }
             if (tid == 0) {
                 s_block[0] = nb0;
@@ -505,17 +539,25 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         }
         cluster.sync();
         int total = 0;
-        for (int r = 0; r < CL; ++r) total += *cluster.map_shared_rank(&s_count, r);
+        float worst = 0.f;
+        for (int r = 0; r < CL; ++r) {
+            total += *cluster.map_shared_rank(&s_count, r);
+            worst = fmaxf(worst, __uint_as_float(*cluster.map_shared_rank(&s_meas, r)));
+        }
         cluster.sync();
-        if (tid == 0) s_count = 0;
+        if (tid == 0) {
+            s_count = 0;
+            s_meas = 0u;
+        }
         __syncthreads();
-        if (total == 0) break;
+        if (k == 0 && tid == 0) status[2] = sweep + 1;
+        if (total == 0 || worst < kStopFactor * kU * sqrtf((float)s)) break;
     }
     // ---- norms gathered in CTA 0
     for (int q = warp; q < 2 * b; q += nwarps) {
         const int sl = q / b, j = q % b;
         const int c = s_block[sl] * b + j;
-        const double nv = col_norm(slot0 + (size_t)q * s, s);
+        const double nv = col_norm(slot0 + (size_t)q * sp, sp);
         if (lane == 0 && c < s) *cluster.map_shared_rank(&s_norm[c], 0) = nv;
     }
     cluster.sync();
@@ -528,8 +570,9 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
 size_t cluster_smem(int CL, int r2, int s, int* b_out) {
     const int nloc = (s + CL - 1) / CL;
     const int b = (s + 2 * CL - 1) / (2 * CL);
+    const size_t sp = (size_t)(s + 31) / 32 * 32;
     *b_out = b;
-    return sizeof(float) * ((size_t)nloc * r2 + 2 * (size_t)b * s + 2 * (size_t)r2);
+    return sizeof(float) * ((size_t)nloc * r2 + 2 * (size_t)b * sp + 2 * (size_t)r2);
 }
 
 template <int CL>
@@ -537,7 +580,7 @@ cudaError_t launch_cluster_sigma(const double* core, int r2, int s, int64_t ld, 
                                  int* status, cudaStream_t st) {
     int b = 0;
     const size_t smem = cluster_smem(CL, r2, s, &b);
-    if (2 * (size_t)b * s > (size_t)kPullRegs * kSvdThreads) return cudaErrorInvalidValue;
+    if (2 * (size_t)b * ((s + 31) / 32 * 32) > (size_t)kPullRegs * kSvdThreads) return cudaErrorInvalidValue;
     auto kern = core_sigma_cluster_kernel<CL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -570,7 +613,7 @@ __global__ void readoff_kernel(const double* __restrict__ sigma, int r1, double 
     // by the tensor-core right sketch when one of its bounded waits expired
     r.status = status_in ? status_in[0] : RE_OK;
     if (status_in && status_in[1]) r.status = RE_ERR_TIMEOUT;
-    r.pad = 0;
+    r.sweeps = status_in ? status_in[2] : 0;
     for (int i = 0; i < r1; ++i) sigma_scaled[i] = sigma[i] * scale;
     const double ref = norm_a > 0.0 ? norm_a : sigma_scaled[0];
     r.tau = eps * ref;
@@ -601,7 +644,10 @@ __global__ void readoff_kernel(const double* __restrict__ sigma, int r1, double 
 
 constexpr size_t kSmemLimit = 210 * 1024;
 
-size_t cta_smem(int r2, int s) { return sizeof(float) * ((size_t)r2 * s + (size_t)s * s); }
+size_t cta_smem(int r2, int s) {
+    const size_t sp = (size_t)(s + 31) / 32 * 32;
+    return sizeof(float) * ((size_t)r2 * s + sp * s);
+}
 
 }  // namespace
 
@@ -629,9 +675,10 @@ cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, voi
     if (cta_smem(r2, s) <= kSmemLimit)
         return launch_core_sigma_batched(core, r2, s, ld, 0, 1, sigma, 0, status, st);
     int b = 0;
-    if (cluster_smem(8, r2, s, &b) <= kSmemLimit && 2 * (size_t)b * s <= (size_t)kPullRegs * kSvdThreads)
+    const size_t sp = (size_t)(s + 31) / 32 * 32;
+    if (cluster_smem(8, r2, s, &b) <= kSmemLimit && 2 * (size_t)b * sp <= (size_t)kPullRegs * kSvdThreads)
         return launch_cluster_sigma<8>(core, r2, s, ld, sigma, status, st);
-    if (cluster_smem(16, r2, s, &b) <= kSmemLimit && 2 * (size_t)b * s <= (size_t)kPullRegs * kSvdThreads)
+    if (cluster_smem(16, r2, s, &b) <= kSmemLimit && 2 * (size_t)b * sp <= (size_t)kPullRegs * kSvdThreads)
         return launch_cluster_sigma<16>(core, r2, s, ld, sigma, status, st);
     return cudaErrorInvalidValue;
 }

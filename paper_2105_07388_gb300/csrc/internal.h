@@ -90,7 +90,7 @@ struct DevReadoff {
     double gap_ratio;
     double tau;
     int status;
-    int pad;
+    int sweeps;      // Jacobi sweeps of the small-core step (status_in[2])
 };
 cudaError_t launch_readoff(const double* sigma, int r1, double scale, double eps, double norm_a,
                            const int* status_in, DevReadoff* out, double* sigma_scaled,

@@ -9,13 +9,14 @@
 // accumulated in one TMEM accumulator.
 //
 // Persistent kernel, one CTA per SM, 128-row M tiles, K chunks of 64:
-//   warps 0-7   converters: coalesced 128-bit loads of A (prefetched one chunk
-//               ahead in registers), exact 3-way split, stores of the three BF16
-//               tiles into shared memory in the 128B-swizzled K-major layout the
-//               MMA descriptors expect; fence.proxy.async + mbarrier arrive.
-//   warp 12     TMA producer: cp.async.bulk.tensor of the BF16 X^T chunk
-//               (N rows x 64 k, 128B swizzle) with complete_tx on an mbarrier.
-//   warp 13     TMEM allocation; one elected thread issues 3 x 4 tcgen05.mma
+//   warp 12     TMA producer of A: FP32 half chunks (128 rows x 32 k, 128B
+//               swizzle, zero fill past the edges) into a 3-4 deep ring, so
+//               48-64 KB of A are in flight per SM.
+//   warp 13     TMA producer of X^T: BF16 chunk (N rows x 64 k, 128B swizzle).
+//   warps 0-7   converters: read two FP32 half chunks from shared memory, split
+//               exactly into three BF16 tiles written in the 128B-swizzled
+//               K-major layout of the MMA descriptors; fence.proxy.async, arrive.
+//   warp 14     TMEM allocation; one elected thread issues 3 x 4 tcgen05.mma
 //               (M=128, N, K=16, kind::f16 BF16 -> FP32) per chunk and
 //               tcgen05.commit to release stages / publish accumulators.
 //   warps 8-11  epilogue: tcgen05.ld (32 lanes x 16 columns) -> FP32 rows of AX.
@@ -39,10 +40,13 @@ constexpr int kBM = 128;           // rows per M tile (UMMA M)
 constexpr int kBK = 64;            // K elements per chunk (one 128-byte swizzle row)
 constexpr int kConvWarps = 8;
 constexpr int kEpiWarps = 4;
-constexpr int kThreads = (kConvWarps + kEpiWarps + 2) * 32;   // 448
-constexpr int kProducerWarp = kConvWarps + kEpiWarps;          // 12
-constexpr int kMmaWarp = kProducerWarp + 1;                    // 13
+constexpr int kThreads = (kConvWarps + kEpiWarps + 3) * 32;   // 480
+constexpr int kAProdWarp = kConvWarps + kEpiWarps;             // 12
+constexpr int kBProdWarp = kAProdWarp + 1;                     // 13
+constexpr int kMmaWarp = kBProdWarp + 1;                       // 14
 constexpr uint32_t kTermBytes = kBM * kBK * 2;                 // 16 KB per BF16 term tile
+constexpr uint32_t kHalfBytes = kBM * 32 * 4;                  // 16 KB FP32 half chunk
+constexpr int kSplitStages = 2;
 constexpr unsigned long long kWaitNs = 2000000000ull;          // 2 s bound per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -187,31 +191,39 @@ struct TcParams {
     int64_t ldc;
     int S;            // valid output columns
     int N;            // MMA N (>= 16, multiple of 16)
-    int stages;
+    int astages;      // FP32 half-chunk ring depth
     int64_t tiles;
     int64_t kchunks;
     int* err;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_constant__ CUtensorMap xmap,
+__global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_constant__ CUtensorMap amap,
+                                                               const __grid_constant__ CUtensorMap xmap,
                                                                const TcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full_a[4], full_b[4], empty[4], accf[2], acce[2], done_bar;
+    __shared__ __align__(8) uint64_t a_full[4], a_empty[4];
+    __shared__ __align__(8) uint64_t full_a[kSplitStages], full_b[kSplitStages], empty[kSplitStages];
+    __shared__ __align__(8) uint64_t accf[2], acce[2], done_bar;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int NS = p.stages;
+    const int NA = p.astages;
     const uint32_t b_bytes = (uint32_t)p.N * kBK * 2;
     const uint32_t stage_bytes = 3 * kTermBytes + ((b_bytes + 1023u) & ~1023u);
-    unsigned char* base = reinterpret_cast<unsigned char*>(
+    unsigned char* abuf = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* sbuf = abuf + (size_t)NA * kHalfBytes;
 
     if (tid == 0) {
-        for (int s = 0; s < NS; ++s) {
-            mbar_init(&full_a[s], kConvWarps * 32);
-            mbar_init(&full_b[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int i = 0; i < NA; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], kConvWarps * 32);
+        }
+        for (int i = 0; i < kSplitStages; ++i) {
+            mbar_init(&full_a[i], kConvWarps * 32);
+            mbar_init(&full_b[i], 1);
+            mbar_init(&empty[i], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&accf[a], 1);
@@ -240,74 +252,77 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     const int64_t total_chunks = my_tiles * p.kchunks;
 
     if (warp < kConvWarps) {
-        // ---------------- converters
-        const int t = tid;                 // 0..255
-        float4 cur[8], nxt[8];
-        auto load_chunk = [&](int64_t g, float4 (&v)[8]) {
-            const int64_t tile = blockIdx.x + (g / p.kchunks) * gridDim.x;
-            const int64_t kc = g % p.kchunks;
-            const int64_t m0 = tile * kBM, k0 = kc * kBK;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int f = j * 256 + t;              // float4 index in the 128 x 64 chunk
-                const int r = f >> 4, c4 = f & 15;
-                const int64_t row = m0 + r, col = k0 + 4 * c4;
-                float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (row < p.M) {
-                    const float* src = p.A + row * p.lda + col;
-                    if (col + 4 <= p.K) {
-                        w = __ldcs(reinterpret_cast<const float4*>(src));
-                    } else {
-                        if (col + 0 < p.K) w.x = src[0];
-                        if (col + 1 < p.K) w.y = src[1];
-                        if (col + 2 < p.K) w.z = src[2];
-                    }
-                }
-                v[j] = w;
-            }
-        };
-        if (total_chunks > 0) load_chunk(0, cur);
+        // ---------------- converters: FP32 half chunks -> three BF16 tiles
         for (int64_t g = 0; g < total_chunks; ++g) {
-            const int s = (int)(g % NS);
-            const uint32_t ph = (uint32_t)((g / NS) & 1);
-            if (g + 1 < total_chunks) load_chunk(g + 1, nxt);
-            if (!mbar_wait(&empty[s], ph ^ 1u, &s_abort, p.err)) break;
-            unsigned char* st = base + (size_t)s * stage_bytes;
+            const int s = (int)(g % kSplitStages);
+            if (!mbar_wait(&empty[s], (uint32_t)((g / kSplitStages) & 1) ^ 1u, &s_abort, p.err)) break;
+            unsigned char* st = sbuf + (size_t)s * stage_bytes;
+            bool ok = true;
+            for (int h = 0; h < 2; ++h) {
+                const int64_t hg = 2 * g + h;
+                const int as = (int)(hg % NA);
+                if (!mbar_wait(&a_full[as], (uint32_t)((hg / NA) & 1), &s_abort, p.err)) {
+                    ok = false;
+                    break;
+                }
+                const unsigned char* src = abuf + (size_t)as * kHalfBytes;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int f = j * 256 + t;
-                const int r = f >> 4, c4 = f & 15;
-                // element (r, k=4*c4): 16-byte chunk (k/8) swizzled with (r mod 8), 8-byte half (c4 & 1)
-                const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((c4 >> 1) ^ (r & 7)) << 4) +
-                                     (uint32_t)(c4 & 1) * 8u;
-                uint32_t h0, m0, l0, h1, m1, l1;
-                split3(cur[j].x, cur[j].y, h0, m0, l0);
-                split3(cur[j].z, cur[j].w, h1, m1, l1);
-                *reinterpret_cast<uint2*>(st + off) = make_uint2(h0, h1);
-                *reinterpret_cast<uint2*>(st + kTermBytes + off) = make_uint2(m0, m1);
-                *reinterpret_cast<uint2*>(st + 2 * kTermBytes + off) = make_uint2(l0, l1);
+                for (int j = 0; j < 4; ++j) {
+                    // rows {0,1,4,5} or {2,3,6,7} of an 8-row atom per instruction: the
+                    // swizzled 8-byte stores of the four rows fall in two bank halves
+                    const int gg = warp + 8 * j;
+                    const int sel = lane >> 3, c4 = lane & 7;
+                    const int roff = (sel & 1) * 4 + (sel >> 1);
+                    const int r = 8 * (gg >> 1) + 2 * (gg & 1) + roff;
+                    const float4 v = *reinterpret_cast<const float4*>(src + r * 128 + ((c4 ^ (r & 7)) << 4));
+                    const int chunk16 = 4 * h + (c4 >> 1);
+                    const uint32_t off = (uint32_t)r * 128u + ((uint32_t)(chunk16 ^ (r & 7)) << 4) +
+                                         (uint32_t)(c4 & 1) * 8u;
+                    uint32_t h0, m0, l0, h1, m1, l1;
+                    split3(v.x, v.y, h0, m0, l0);
+                    split3(v.z, v.w, h1, m1, l1);
+                    *reinterpret_cast<uint2*>(st + off) = make_uint2(h0, h1);
+                    *reinterpret_cast<uint2*>(st + kTermBytes + off) = make_uint2(m0, m1);
+                    *reinterpret_cast<uint2*>(st + 2 * kTermBytes + off) = make_uint2(l0, l1);
+                }
+                mbar_arrive(&a_empty[as]);
             }
+            if (!ok) break;
             fence_proxy_async();
             mbar_arrive(&full_a[s]);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) cur[j] = nxt[j];
         }
-    } else if (warp == kProducerWarp) {
-        // ---------------- TMA producer for X^T chunks
-        int64_t issued = 0;
+    } else if (warp == kAProdWarp) {
+        // ---------------- TMA producer of A half chunks
         if (lane == 0) {
-            for (int64_t g = 0; g < total_chunks; ++g) {
-                const int s = (int)(g % NS);
-                const uint32_t ph = (uint32_t)((g / NS) & 1);
-                if (!mbar_wait(&empty[s], ph ^ 1u, &s_abort, p.err)) break;
-                unsigned char* st = base + (size_t)s * stage_bytes + 3 * kTermBytes;
-                mbar_arrive_expect_tx(&full_b[s], b_bytes);
-                tma_load_2d(st, &xmap, (int)((g % p.kchunks) * kBK), 0, &full_b[s]);
+            int64_t issued = 0;
+            for (int64_t hg = 0; hg < 2 * total_chunks; ++hg) {
+                const int as = (int)(hg % NA);
+                if (!mbar_wait(&a_empty[as], (uint32_t)((hg / NA) & 1) ^ 1u, &s_abort, p.err)) break;
+                const int64_t g = hg >> 1;
+                const int64_t tile = blockIdx.x + (g / p.kchunks) * gridDim.x;
+                const int64_t kc = g % p.kchunks;
+                mbar_arrive_expect_tx(&a_full[as], kHalfBytes);
+                tma_load_2d(abuf + (size_t)as * kHalfBytes, &amap, (int)(kc * kBK + 32 * (hg & 1)),
+                            (int)(tile * kBM), &a_full[as]);
                 ++issued;
             }
-            // drain: every issued copy must land before the CTA may exit
-            for (int64_t g = std::max<int64_t>(0, issued - NS); g < issued; ++g)
-                mbar_drain(&full_b[g % NS], (uint32_t)((g / NS) & 1));
+            for (int64_t hg = std::max<int64_t>(0, issued - NA); hg < issued; ++hg)
+                mbar_drain(&a_full[hg % NA], (uint32_t)((hg / NA) & 1));
+        }
+    } else if (warp == kBProdWarp) {
+        // ---------------- TMA producer of X^T chunks
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t g = 0; g < total_chunks; ++g) {
+                const int s = (int)(g % kSplitStages);
+                if (!mbar_wait(&empty[s], (uint32_t)((g / kSplitStages) & 1) ^ 1u, &s_abort, p.err)) break;
+                mbar_arrive_expect_tx(&full_b[s], b_bytes);
+                tma_load_2d(sbuf + (size_t)s * stage_bytes + 3 * kTermBytes, &xmap, (int)((g % p.kchunks) * kBK), 0,
+                            &full_b[s]);
+                ++issued;
+            }
+            for (int64_t g = std::max<int64_t>(0, issued - kSplitStages); g < issued; ++g)
+                mbar_drain(&full_b[g % kSplitStages], (uint32_t)((g / kSplitStages) & 1));
         }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer
@@ -321,15 +336,15 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(a * p.N);
                 for (int64_t kc = 0; kc < p.kchunks; ++kc, ++g) {
-                    const int s = (int)(g % NS);
-                    const uint32_t ph = (uint32_t)((g / NS) & 1);
+                    const int s = (int)(g % kSplitStages);
+                    const uint32_t ph = (uint32_t)((g / kSplitStages) & 1);
                     if (!mbar_wait(&full_a[s], ph, &s_abort, p.err) ||
                         !mbar_wait(&full_b[s], ph, &s_abort, p.err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = smem_u32(base + (size_t)s * stage_bytes);
+                    const uint32_t st = smem_u32(sbuf + (size_t)s * stage_bytes);
 #pragma unroll
                     for (int kk = 0; kk < kBK / 16; ++kk) {
                         const uint64_t bdesc = sw128_desc(st + 3 * kTermBytes + 32u * kk);
@@ -404,8 +419,9 @@ int g_sms = 0;
 }  // namespace
 
 bool tc_supported(const MatView& A) {
-    // FP32, not transposed, 16-byte aligned rows (128-bit loads)
-    return A.dtype == RE_F32 && !A.trans && (A.ld % 4) == 0 &&
+    // FP32, not transposed, TMA-compatible (16-byte aligned base and row pitch),
+    // at least one full tile in each dimension
+    return A.dtype == RE_F32 && !A.trans && (A.ld % 4) == 0 && A.rows >= kBM && A.cols >= kBK &&
            (reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0 && encode_fn() != nullptr;
 }
 
@@ -427,6 +443,15 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // A: FP32 (K, M) with row pitch ld; boxes of 32 k x 128 rows, zero fill past the edges
+    CUtensorMap amap;
+    const cuuint64_t adim[2] = {(cuuint64_t)A.cols, (cuuint64_t)A.rows};
+    const cuuint64_t astride[1] = {(cuuint64_t)A.ld * 4};
+    const cuuint32_t abox[2] = {32u, (cuuint32_t)kBM};
+    r = enc(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(A.ptr), adim, astride, abox, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     TcParams p;
     p.A = static_cast<const float*>(A.ptr);
     p.lda = A.ld;
@@ -436,13 +461,13 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
     p.ldc = ldc;
     p.S = s;
     p.N = N;
-    p.stages = N <= 128 ? 3 : 2;
+    p.astages = N <= 128 ? 4 : 3;
     p.tiles = (A.rows + kBM - 1) / kBM;
     p.kchunks = (A.cols + kBK - 1) / kBK;
     p.err = err_flag;
     const uint32_t b_bytes = (uint32_t)N * kBK * 2;
     const size_t stage_bytes = 3 * kTermBytes + ((b_bytes + 1023u) & ~1023u);
-    const size_t smem = stage_bytes * p.stages + 1024;
+    const size_t smem = (size_t)kHalfBytes * p.astages + stage_bytes * kSplitStages + 1024;
     cudaError_t e = cudaFuncSetAttribute(right_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (!g_sms) {
@@ -451,7 +476,7 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
         cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int64_t grid = std::min<int64_t>(p.tiles, g_sms);
-    right_tc_kernel<<<(unsigned)grid, kThreads, smem, st>>>(map, p);
+    right_tc_kernel<<<(unsigned)grid, kThreads, smem, st>>>(amap, map, p);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ class re_result(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int), ("gap_index", ctypes.c_int), ("gap_ratio", ctypes.c_double),
                 ("tau", ctypes.c_double), ("n_sigma", ctypes.c_int), ("final_s", ctypes.c_int),
                 ("passes", ctypes.c_int), ("flags", ctypes.c_uint32), ("status", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("svd_sweeps", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
