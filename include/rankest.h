@@ -222,6 +222,29 @@ int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int
                              double eps, int sketch_kind, uint64_t seed,
                              double* sigma_out, int sigma_cap, re_result* out, void* stream);
 
+/*
+ * The Gaussian sketch step of re_sketch_apply without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that may not
+ * allocate device memory -- code running inside a CUDA stream capture (where
+ * cudaMalloc would break the capture), applications whose device memory is owned
+ * by their own pool or caching allocator, and real-time paths where an
+ * allocation's latency or failure is not acceptable.  It needs no handle.
+ *   Arguments and outputs are those of re_sketch_apply with sketch_kind =
+ *   RE_GAUSSIAN and FP32 arithmetic (AX columns col0..col0+s-1 unscaled; the
+ *   optional FP64 core appended in place).
+ *   Scratch (the generated X columns and the left sketch's split-K partial sums)
+ *   lives in one 16 MiB static device array that every GPU loading the library
+ *   holds until exit; calls needing more (about min(m,n)*s + 2(col0+s)*s*splits
+ *   floats > 4 Mi) return RE_ERR_ARG.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the array: calls that overlap on the GPU race on it and must
+ *   be serialised by the caller.  Nothing in it needs to start at zero.
+ */
+int re_sketch_apply_noalloc(const void* A, int dtype, int64_t m, int64_t n, int64_t ld, int col0,
+                            int s, uint64_t seed, float* AX, int64_t ld_ax, double* core,
+                            int64_t ld_core, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

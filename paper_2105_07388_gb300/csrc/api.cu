@@ -56,6 +56,10 @@ struct re_handle_ {
     int sm_count = 0;
 };
 
+namespace re {
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace re
+
 namespace {
 
 cudaEvent_t take_event(re_handle h) {

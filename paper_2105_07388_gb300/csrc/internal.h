@@ -9,6 +9,9 @@
 
 namespace re {
 
+// Records msg as the thread's last error (re_last_error) and returns code.
+int set_last_error(int code, const char* msg);
+
 // Oriented view of the caller's matrix: rows >= cols.  Element (r, c) of the
 // oriented matrix sits at A[r*ld + c] (plain) or A[c*ld + r] (transposed).
 struct MatView {

@@ -102,6 +102,8 @@ _SIGS = {
     "re_embedding_y": (_I, [_VP, _I, _U64, _I64, _I, _I, _VP, _VP]),
     "re_rank_estimate_batched": (_I, [_VP, ctypes.POINTER(re_block), _I, _I, _D, _I, _U64, _VP,
                                       _I, ctypes.POINTER(re_result), _VP]),
+    "re_sketch_apply_noalloc": (_I, [_VP, _I, _I64, _I64, _I64, _I, _I, _U64, _VP, _I64, _VP, _I64,
+                                     _VP]),
 }
 
 # Symbols declared in include/rankest.h; tests check that the library exports all of them.
@@ -278,3 +280,13 @@ def re_rank_estimate_batched(h: int, blocks, eps: float, sketch_kind: int = RE_G
                                           sig.ctypes.data if sig is not None else None,
                                           sigma_cap, res, _stream(stream)))
     return [res[i] for i in range(count)], sig
+
+
+def re_sketch_apply_noalloc(A, col0: int, s: int, seed: int, AX, core=None, stream=None) -> None:
+    """Gaussian sketch step without device allocation (static 16 MiB scratch, no handle)."""
+    m, n = A.shape
+    assert A.stride(1) == 1 and AX.stride(1) == 1
+    ld_core = core.stride(0) if core is not None else 0
+    _check(lib().re_sketch_apply_noalloc(_ptr(A), _dtype_code(A), m, n, A.stride(0), col0, s, seed,
+                                         _ptr(AX), AX.stride(0), _ptr(core), ld_core,
+                                         _stream(stream)))
