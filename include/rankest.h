@@ -217,6 +217,10 @@ int re_embedding_y(re_handle h, int kind, uint64_t seed, int64_t m, int row0, in
  * (host, count x sigma_cap, may be NULL) the trusted sigma of each.  Every block
  * uses seed + block index.  Per-block argument errors are reported in
  * out[i].status; the call itself fails only on launch or allocation errors.
+ * FP32 blocks with Gaussian embeddings run level-synchronously (all active
+ * blocks advance one ladder width per level; widths up to min(s_max, 128)) as
+ * ONE captured CUDA graph, replayed for repeated identical batches; other
+ * cases run one estimate per block.  Synchronises `stream`.
  */
 int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int dtype,
                              double eps, int sketch_kind, uint64_t seed,

@@ -51,6 +51,7 @@ struct re_handle_ {
     std::vector<PendingTiming> pending;
     std::vector<cudaEvent_t> event_pool;
     DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status;
+    re::BatchedState* batched = nullptr;
     re::DevReadoff* h_ro = nullptr;   // pinned
     double* h_sigma = nullptr;        // pinned, 1024 doubles
     int sm_count = 0;
@@ -436,6 +437,7 @@ int re_destroy(re_handle h) {
     DevBuf* bufs[] = {&h->x, &h->xt, &h->ax, &h->part, &h->core, &h->sigma, &h->sigma_scaled,
                       &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status};
     for (DevBuf* b : bufs) release(*b);
+    re::batched_destroy(h->batched);
     resolve_timings(h);
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     if (h->h_ro) cudaFreeHost(h->h_ro);
@@ -600,6 +602,16 @@ int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int
     if (!h || (count > 0 && (!blocks || !out))) return fail(RE_ERR_ARG, "NULL argument");
     if (count < 0) return fail(RE_ERR_ARG, "count < 0");
     if (!(eps > 0.0 && eps < 1.0)) return fail(RE_ERR_ARG, "eps must lie in (0, 1)");
+    if (count == 0) return RE_OK;
+    cudaSetDevice(h->device);
+    const int ykind = h->opts.y_kind < 0 ? sketch_kind : h->opts.y_kind;
+    if (dtype == RE_F32 && sketch_kind == RE_GAUSSIAN && ykind == RE_GAUSSIAN && !h->opts.learned) {
+        // one graph launch over all blocks (level-synchronous batched kernels)
+        return re::batched_estimate(&h->batched, h->opts, blocks, count, eps, seed, sigma_out,
+                                    sigma_out ? sigma_cap : 0, out, static_cast<cudaStream_t>(stream),
+                                    &h->stats.launches);
+    }
+    // other element types / embeddings: one estimate per block
     for (int i = 0; i < count; ++i) {
         double* so = sigma_out ? sigma_out + (size_t)i * std::max(sigma_cap, 0) : nullptr;
         const int r = re_rank_estimate(h, blocks[i].ptr, dtype, blocks[i].m, blocks[i].n, blocks[i].ld,

@@ -1,0 +1,475 @@
+// Batched Algorithm 1 (Sec. 5) over many independent blocks, e.g. the
+// off-diagonal blocks of a hierarchical matrix (Sec. 1 motivates rank
+// estimation for low-rank off-diagonal blocks).
+//
+// Level-synchronous: every still-active block advances together through the
+// sketch-width ladder s = s0, 2 s0, ..., one level at a time, and each level is
+// a fixed sequence of batched kernels over all blocks:
+//   generator     X_b columns [s_prev, s) for every active block (own seed each)
+//   right sketch  one CTA per (block, row tile) work item (FP32 CUDA cores)
+//   left sketch   one CTA per (block, 64 x 64 core tile), Y_b generated on the fly
+//   core sigma    one CTA per block (QR + one-sided Jacobi in shared memory)
+//   read-off      one thread per block; converged blocks, and blocks that reached
+//                 their largest width, retire by clearing their active flag
+// Inactive blocks cost each kernel only a flag test.  The whole ladder is
+// captured once into a CUDA graph and replayed for identical batches, so an
+// estimate of thousands of uneven blocks is one graph launch with no host
+// round trips.  The right sketch's tile height (64 or 128 rows) is chosen per
+// sketch width by timing both on the batch at hand (autotuner, cached per
+// handle and width).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace re {
+
+namespace {
+
+struct DBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 256));
+        if (e == cudaSuccess) cap = std::max<size_t>(bytes, 256);
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+__device__ __forceinline__ int find_prefix(const int64_t* prefix, int count, int64_t item) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void init_active_kernel(const int* valid, int* active, int* status, int count) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count) return;
+    active[b] = valid[b];
+    status[b] = 0;
+}
+
+// X_b[k][j] (row-major, ld = s) for columns [col0, col0 + s) of every active block.
+__global__ void gauss_x_batched_kernel(const BatchDesc* __restrict__ d, int count,
+                                       const int64_t* __restrict__ col_prefix,
+                                       const int* __restrict__ active, int col0, int s,
+                                       float* __restrict__ Xpool) {
+    const int ng = s / 4;
+    const int64_t total = col_prefix[count] * ng;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t krow = idx / ng;
+        const int b = find_prefix(col_prefix, count, krow);
+        if (!active[b]) continue;
+        const int64_t k = krow - col_prefix[b];
+        const int g = (int)(idx % ng);
+        float z[4];
+        normals4((uint32_t)k, (uint32_t)(col0 / 4 + g), kStreamGX, d[b].seed, z);
+        float* X = Xpool + d[b].x_off + k * s + 4 * g;
+        *reinterpret_cast<float4*>(X) = make_float4(z[0], z[1], z[2], z[3]);
+    }
+}
+
+// core_b[row0 + r][col0 + c] = sum_i Y_b[row0 + r][i] AX_b[i][col0 + c] over all
+// rows i of block b; one CTA per (block, 64 x 64 tile), FP32 accumulation.
+constexpr int kLT = 64;
+constexpr int kLK = 32;
+
+__global__ void __launch_bounds__(256) left_batched_kernel(
+    const BatchDesc* __restrict__ d, const int* __restrict__ active, const float* __restrict__ AXpool,
+    int64_t ldax, double* __restrict__ corepool, int64_t core_stride, int ld_core, int row0, int R,
+    int col0, int S, int tiles_c) {
+    __shared__ __align__(16) float Ys[kLK][kLT + 4];
+    __shared__ __align__(16) float Xs[kLK][kLT];
+    const int b = blockIdx.x;
+    if (!active[b]) return;
+    const BatchDesc D = d[b];
+    const int rt = blockIdx.y / tiles_c, ct = blockIdx.y % tiles_c;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int qbase = row0 + rt * kLT;
+    const float* AX = AXpool + D.ax_off;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+    for (int64_t i0 = 0; i0 < D.rows; i0 += kLK) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = tid & 31;
+            const int g = (tid >> 5) + 8 * h;
+            const int64_t i = i0 + k;
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+            if (i < D.rows && qbase + 4 * g - row0 < R)
+                normals4((uint32_t)i, (uint32_t)((qbase >> 2) + g), kStreamGY, D.seed, z);
+            *reinterpret_cast<float4*>(&Ys[k][4 * g]) = make_float4(z[0], z[1], z[2], z[3]);
+        }
+        {
+            const int k = tid >> 3, cb = (tid & 7) * 8;
+            const int64_t i = i0 + k;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = ct * kLT + cb + q;
+                Xs[k][cb + q] = (i < D.rows && c < S) ? __ldg(AX + i * ldax + col0 + c) : 0.f;
+            }
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kLK; ++k) {
+            const float4 yv = *reinterpret_cast<const float4*>(&Ys[k][ty * 4]);
+            const float4 xv = *reinterpret_cast<const float4*>(&Xs[k][tx * 4]);
+            const float y[4] = {yv.x, yv.y, yv.z, yv.w};
+            const float x[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(y[a], x[c], acc[a][c]);
+        }
+        __syncthreads();
+    }
+    double* core = corepool + (int64_t)b * core_stride;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = rt * kLT + ty * 4 + a;
+        if (r >= R) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int cc = ct * kLT + tx * 4 + c;
+            if (cc < S) core[(int64_t)(row0 + r) * ld_core + col0 + cc] = (double)acc[a][c];
+        }
+    }
+}
+
+// Read-off for every active block at width s (Algorithm 1 step 8); retires blocks.
+__global__ void readoff_batched_kernel(const BatchDesc* __restrict__ d, int count, int* active,
+                                       const double* __restrict__ sigma, int64_t sstride, int s, int r1,
+                                       double scale, double eps, double norm_a, int* status,
+                                       DevReadoff* out, double* sigma_scaled, int* final_s) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count || !active[b]) return;
+    const double* sg = sigma + (int64_t)b * sstride;
+    double* ss = sigma_scaled + (int64_t)b * sstride;
+    DevReadoff r;
+    r.status = status[b];
+    r.sweeps = 0;
+    for (int i = 0; i < r1; ++i) ss[i] = sg[i] * scale;
+    const double ref = norm_a > 0.0 ? norm_a : ss[0];
+    r.tau = eps * ref;
+    r.rank = -1;
+    for (int i = 0; i < r1; ++i)
+        if (ss[i] <= r.tau) {
+            r.rank = i;
+            break;
+        }
+    int gi = 1;
+    double gr = r1 >= 2 ? -1.0 : 1.0;
+    for (int i = 1; i < r1; ++i) {
+        const double a = ss[i - 1], c = ss[i];
+        const double ratio = c > 0.0 ? a / c : (a > 0.0 ? INFINITY : 1.0);
+        if (ratio > gr) {
+            gr = ratio;
+            gi = i;
+        }
+    }
+    r.gap_index = gi;
+    r.gap_ratio = gr;
+    out[b] = r;
+    final_s[b] = s;
+    if (r.status != RE_OK || r.rank >= 0 || 2 * s > d[b].smax || r1 >= d[b].cols) active[b] = 0;
+}
+
+int r1_of(int s) {
+    int r = 1;
+    while ((2 * 11 * (r + 1) + 10) / 20 <= s) ++r;
+    return r;
+}
+
+}  // namespace
+
+struct BatchedState {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+    DBuf ax, x, core, sigma, sscaled, status, out, active, valid, descs, pre128, pre64, colpre, finals;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> key;
+    int bm_for[16] = {0};
+    int64_t launches_per_run = 0;
+};
+
+void batched_destroy(BatchedState* st) {
+    if (!st) return;
+    if (st->exec) cudaGraphExecDestroy(st->exec);
+    DBuf* bufs[] = {&st->ax, &st->x, &st->core, &st->sigma, &st->sscaled, &st->status, &st->out,
+                    &st->active, &st->valid, &st->descs, &st->pre128, &st->pre64, &st->colpre, &st->finals};
+    for (DBuf* b : bufs) b->release();
+    if (st->ev_in) cudaEventDestroy(st->ev_in);
+    if (st->ev_out) cudaEventDestroy(st->ev_out);
+    if (st->t0) cudaEventDestroy(st->t0);
+    if (st->t1) cudaEventDestroy(st->t1);
+    if (st->stream) cudaStreamDestroy(st->stream);
+    delete st;
+}
+
+int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* blocks, int count, double eps,
+                     uint64_t seed, double* sigma_out, int sigma_cap, re_result* out, cudaStream_t ustream,
+                     int64_t* launches) {
+    if (!*pst) {
+        BatchedState* st = new BatchedState();
+        if (cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&st->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&st->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&st->t0) != cudaSuccess || cudaEventCreate(&st->t1) != cudaSuccess) {
+            batched_destroy(st);
+            return set_last_error(RE_ERR_CUDA, "batched: stream/event creation failed");
+        }
+        *pst = st;
+    }
+    BatchedState* st = *pst;
+    const int s0 = o.s0;
+    const int scap = std::min(o.s_max, 128);
+    // ---- host descriptors
+    std::vector<BatchDesc> hd(count);
+    std::vector<int> valid(count, 0);
+    std::vector<int64_t> pre128(count + 1, 0), pre64(count + 1, 0), colpre(count + 1, 0);
+    int S_MAX = 0;
+    for (int i = 0; i < count; ++i) {
+        const re_block& B = blocks[i];
+        BatchDesc& D = hd[i];
+        std::memset(&D, 0, sizeof(D));
+        const bool ok = B.ptr && B.m > 0 && B.n > 0 && B.ld >= B.n && B.m <= INT32_MAX && B.n <= INT32_MAX;
+        if (ok) {
+            D.A = static_cast<const float*>(B.ptr);
+            D.ld = B.ld;
+            D.trans = B.m < B.n;
+            D.rows = std::max(B.m, B.n);
+            D.cols = std::min(B.m, B.n);
+            int sm = s0;
+            while (sm * 2 <= scap) sm *= 2;
+            D.smax = sm;
+            S_MAX = std::max(S_MAX, sm);
+            valid[i] = 1;
+        }
+        D.seed = seed + (uint64_t)i;
+    }
+    if (S_MAX == 0) S_MAX = s0;
+    const int SNEW = std::max(s0, S_MAX / 2);
+    int64_t ax_total = 0, x_total = 0;
+    for (int i = 0; i < count; ++i) {
+        BatchDesc& D = hd[i];
+        D.ax_off = ax_total;
+        D.x_off = x_total;
+        ax_total += D.rows * S_MAX;
+        x_total += (D.cols * SNEW + 63) / 64 * 64;
+        pre128[i + 1] = pre128[i] + (valid[i] ? (D.rows + 127) / 128 : 0);
+        pre64[i + 1] = pre64[i] + (valid[i] ? (D.rows + 63) / 64 : 0);
+        colpre[i + 1] = colpre[i] + (valid[i] ? D.cols : 0);
+    }
+    const int64_t core_stride = 2LL * S_MAX * S_MAX;
+    cudaError_t e = cudaSuccess;
+    auto ens = [&](DBuf& b, size_t bytes) {
+        if (e == cudaSuccess) e = b.ensure(bytes);
+    };
+    ens(st->ax, sizeof(float) * (size_t)std::max<int64_t>(ax_total, 1));
+    ens(st->x, sizeof(float) * (size_t)std::max<int64_t>(x_total, 1));
+    ens(st->core, sizeof(double) * (size_t)core_stride * count);
+    ens(st->sigma, sizeof(double) * (size_t)S_MAX * count);
+    ens(st->sscaled, sizeof(double) * (size_t)S_MAX * count);
+    ens(st->status, sizeof(int) * (size_t)count);
+    ens(st->out, sizeof(DevReadoff) * (size_t)count);
+    ens(st->active, sizeof(int) * (size_t)count);
+    ens(st->valid, sizeof(int) * (size_t)count);
+    ens(st->descs, sizeof(BatchDesc) * (size_t)count);
+    ens(st->pre128, sizeof(int64_t) * (size_t)(count + 1));
+    ens(st->pre64, sizeof(int64_t) * (size_t)(count + 1));
+    ens(st->colpre, sizeof(int64_t) * (size_t)(count + 1));
+    ens(st->finals, sizeof(int) * (size_t)count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_last_error(RE_ERR_NOMEM, "batched: device workspace allocation failed");
+    }
+    // cache key: everything the captured graph depends on
+    std::vector<unsigned char> key;
+    auto put = [&](const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        key.insert(key.end(), c, c + n);
+    };
+    put(&count, sizeof(count));
+    put(&eps, sizeof(eps));
+    put(&o, sizeof(o));
+    put(hd.data(), sizeof(BatchDesc) * hd.size());
+    put(valid.data(), sizeof(int) * valid.size());
+    const void* pools[] = {st->ax.p, st->x.p, st->core.p, st->sigma.p, st->sscaled.p, st->status.p,
+                           st->out.p, st->active.p, st->finals.p};
+    put(pools, sizeof(pools));
+
+    cudaStream_t bs = st->stream;
+    BatchDesc* dd = st->descs.as<BatchDesc>();
+    int* active = st->active.as<int>();
+    int* status = st->status.as<int>();
+    if (!st->exec || key != st->key) {
+        if (st->exec) {
+            cudaGraphExecDestroy(st->exec);
+            st->exec = nullptr;
+        }
+        e = cudaMemcpy(dd, hd.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(st->valid.p, valid.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(st->pre128.p, pre128.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(st->pre64.p, pre64.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(st->colpre.p, colpre.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: descriptor upload failed");
+        // ---- autotune the right-sketch tile height for each width of the ladder
+        {
+            init_active_kernel<<<(count + 255) / 256, 256, 0, bs>>>(st->valid.as<int>(), active, status, count);
+            for (int s_prev = 0, s = s0; s <= S_MAX; s_prev = s, s *= 2) {
+                const int sn = s - s_prev;
+                const int slot = 31 - __builtin_clz((unsigned)sn);
+                if (st->bm_for[slot]) continue;
+                gauss_x_batched_kernel<<<1024, 256, 0, bs>>>(dd, count, st->colpre.as<int64_t>(), active, s_prev, sn,
+                                                            st->x.as<float>());
+                float best = 1e30f;
+                int best_bm = 128;
+                for (int bm : {128, 64}) {
+                    const int64_t* pre = bm == 128 ? st->pre128.as<int64_t>() : st->pre64.as<int64_t>();
+                    const int64_t items = bm == 128 ? pre128[count] : pre64[count];
+                    for (int rep = 0; rep < 2; ++rep) {     // first run warms up
+                        cudaEventRecord(st->t0, bs);
+                        e = launch_right_simt_batched(dd, count, pre, items, active, st->x.as<float>(), sn,
+                                                      st->ax.as<float>(), S_MAX, s_prev, bm, bs);
+                        cudaEventRecord(st->t1, bs);
+                        if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: autotune launch failed");
+                        cudaEventSynchronize(st->t1);
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, st->t0, st->t1);
+                    if (ms < best) {
+                        best = ms;
+                        best_bm = bm;
+                    }
+                }
+                st->bm_for[slot] = best_bm;
+            }
+            e = cudaStreamSynchronize(bs);
+            if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: autotune failed");
+        }
+        // ---- capture the whole ladder
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: begin capture failed");
+        int64_t nl = 0;
+        init_active_kernel<<<(count + 255) / 256, 256, 0, bs>>>(st->valid.as<int>(), active, status, count);
+        ++nl;
+        for (int s_prev = 0, s = s0; s <= S_MAX && e == cudaSuccess; s_prev = s, s *= 2) {
+            const int sn = s - s_prev;
+            const int bm = st->bm_for[31 - __builtin_clz((unsigned)sn)] == 64 ? 64 : 128;
+            gauss_x_batched_kernel<<<1024, 256, 0, bs>>>(dd, count, st->colpre.as<int64_t>(), active, s_prev, sn,
+                                                        st->x.as<float>());
+            e = launch_right_simt_batched(dd, count, bm == 128 ? st->pre128.as<int64_t>() : st->pre64.as<int64_t>(),
+                                          bm == 128 ? pre128[count] : pre64[count], active, st->x.as<float>(), sn,
+                                          st->ax.as<float>(), S_MAX, s_prev, bm, bs);
+            nl += 2;
+            if (e != cudaSuccess) break;
+            if (s_prev > 0) {
+                const int R = 2 * sn, S = s_prev;
+                const int tr = (R + kLT - 1) / kLT, tc = (S + kLT - 1) / kLT;
+                left_batched_kernel<<<dim3(count, tr * tc), 256, 0, bs>>>(dd, active, st->ax.as<float>(), S_MAX,
+                                                                          st->core.as<double>(), core_stride, S_MAX,
+                                                                          2 * s_prev, R, 0, S, tc);
+                ++nl;
+            }
+            {
+                const int R = 2 * s, S = sn;
+                const int tr = (R + kLT - 1) / kLT, tc = (S + kLT - 1) / kLT;
+                left_batched_kernel<<<dim3(count, tr * tc), 256, 0, bs>>>(dd, active, st->ax.as<float>(), S_MAX,
+                                                                          st->core.as<double>(), core_stride, S_MAX, 0,
+                                                                          R, s_prev, S, tc);
+                ++nl;
+            }
+            e = launch_core_sigma_batched(st->core.as<double>(), 2 * s, s, S_MAX, core_stride, count,
+                                          st->sigma.as<double>(), S_MAX, status, bs, active);
+            ++nl;
+            if (e != cudaSuccess) break;
+            readoff_batched_kernel<<<(count + 127) / 128, 128, 0, bs>>>(
+                dd, count, active, st->sigma.as<double>(), S_MAX, s, std::min(r1_of(s), s),
+                1.0 / std::sqrt((double)s * (double)(2 * s)), eps, o.norm_a, status, st->out.as<DevReadoff>(),
+                st->sscaled.as<double>(), st->finals.as<int>());
+            ++nl;
+        }
+        cudaError_t ec = cudaStreamEndCapture(bs, &graph);
+        if (e == cudaSuccess) e = ec;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&st->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st->exec = nullptr;
+            return set_last_error(RE_ERR_CUDA, "batched: graph capture failed");
+        }
+        st->key = key;
+        st->launches_per_run = nl;
+    }
+    // ---- one graph launch, ordered after the caller's stream
+    e = cudaEventRecord(st->ev_in, ustream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, st->ev_in, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(st->exec, bs);
+    if (e == cudaSuccess) e = cudaEventRecord(st->ev_out, bs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ustream, st->ev_out, 0);
+    if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: graph launch failed");
+    *launches += st->launches_per_run;
+    std::vector<DevReadoff> ro(count);
+    std::vector<int> fin(count);
+    e = cudaMemcpyAsync(ro.data(), st->out.p, sizeof(DevReadoff) * count, cudaMemcpyDeviceToHost, ustream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fin.data(), st->finals.p, sizeof(int) * count, cudaMemcpyDeviceToHost, ustream);
+    std::vector<double> sg;
+    if (e == cudaSuccess && sigma_out && sigma_cap > 0) {
+        sg.resize((size_t)count * S_MAX);
+        e = cudaMemcpyAsync(sg.data(), st->sscaled.p, sizeof(double) * sg.size(), cudaMemcpyDeviceToHost, ustream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ustream);
+    if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: result copy failed");
+    for (int i = 0; i < count; ++i) {
+        re_result& R = out[i];
+        std::memset(&R, 0, sizeof(R));
+        if (!valid[i]) {
+            R.status = RE_ERR_ARG;
+            continue;
+        }
+        const int s = fin[i];
+        const int r1 = std::min(r1_of(s), s);
+        const bool conv = ro[i].rank >= 0;
+        R.status = ro[i].status == RE_OK ? RE_OK : ro[i].status;
+        R.rank = conv ? ro[i].rank : r1;
+        R.gap_index = ro[i].gap_index;
+        R.gap_ratio = ro[i].gap_ratio;
+        R.tau = ro[i].tau;
+        R.n_sigma = r1;
+        R.final_s = s;
+        int passes = 0;
+        for (int t = s0; t <= s; t *= 2) ++passes;
+        R.passes = passes;
+        R.flags = (conv ? RE_CONVERGED : RE_LOWER_BOUND_ONLY) | (hd[i].trans ? RE_TRANSPOSED : 0u);
+        if (!sg.empty()) {
+            const int nc = std::min(r1, sigma_cap);
+            for (int j = 0; j < nc; ++j) sigma_out[(size_t)i * sigma_cap + j] = sg[(size_t)i * S_MAX + j];
+        }
+    }
+    return RE_OK;
+}
+
+}  // namespace re

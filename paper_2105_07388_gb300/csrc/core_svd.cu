@@ -22,6 +22,7 @@
 // use a cluster of 8 or 16 CTAs: the QR is column-cyclic with the Householder
 // vector broadcast over distributed shared memory, and Jacobi is blocked (two
 // column blocks per CTA, blocks rotating through the cluster each round).
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -60,55 +61,73 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Lanes per column pair in a Jacobi rotation: a warp works on four pairs at once
-// (three-level reductions, four independent dependency chains).
-constexpr int kG = 8;
-
-__device__ __forceinline__ float group_sum(float v) {
-#pragma unroll
-    for (int o = kG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Jacobi rotation of columns a, b (length n) by a group of kG lanes; returns 1 if
-// this group rotated.  Every lane of the warp must call it (the reductions use
-// full-warp shuffles); inactive groups pass active = false.
-// n is a multiple of kG (columns are zero padded); the four groups of a warp
-// start their traversal kG*g elements apart so that, with column strides that
-// are multiples of 32 floats, they touch disjoint shared-memory banks.
+// Jacobi rotation of columns a, b (length n, a multiple of 4*G, 16-byte
+// aligned) by a group of G consecutive lanes; returns 1 if this group rotated
+// (and stores |cos| of the pair in *meas).  Every lane of the warp must call it
+// (the reductions use full-warp shuffles); inactive groups pass active = false.
+// Each group reads 4*G contiguous floats per step with 128-bit accesses, so a
+// group of 8 lanes is exactly one shared-memory wavefront.  The rotation
+// parameters use the fast reciprocal square root and division: their rounding
+// only perturbs the angle, and c*c + s*s stays 1 to a few ulp.
+template <int G>
 __device__ __forceinline__ int rotate_pair(bool active, float* a, float* b, int n, float tol,
                                            float floor_abs, float* meas) {
-    const int gl = threadIdx.x & (kG - 1);
-    const int J = n / kG;
-    const int j0 = J > 0 ? ((threadIdx.x >> 3) & 3) % J : 0;
+    const int gl = threadIdx.x & (G - 1);
     float al = 0.f, be = 0.f, ga = 0.f;
     if (active) {
-        for (int jj = 0, j = j0; jj < J; ++jj, j = (j + 1 == J) ? 0 : j + 1) {
-            const int i = j * kG + gl;
-            const float x = a[i], y = b[i];
-            al = fmaf(x, x, al);
-            be = fmaf(y, y, be);
-            ga = fmaf(x, y, ga);
+        for (int i = 4 * gl; i < n; i += 4 * G) {
+            const float4 x = *reinterpret_cast<const float4*>(a + i);
+            const float4 y = *reinterpret_cast<const float4*>(b + i);
+            al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
+            be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
+            ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
         }
     }
-    al = group_sum(al);
-    be = group_sum(be);
-    ga = group_sum(ga);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+    }
     const float ag = fabsf(ga);
-    if (!active || !(ag > tol * sqrtf(al) * sqrtf(be)) || !(ag > floor_abs)) return 0;
-    *meas = ag / (sqrtf(al) * sqrtf(be));
-    const float zeta = (be - al) / (ga + ga);
-    const float tt = fabsf(zeta) > 1e15f ? 0.5f / zeta
-                                         : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-    const float c = 1.f / sqrtf(1.f + tt * tt);
+    const float nab = sqrtf(al) * sqrtf(be);
+    if (!active || !(ag > tol * nab) || !(ag > floor_abs)) return 0;
+    *meas = __fdividef(ag, nab);
+    const float zeta = __fdividef(be - al, ga + ga);
+    const float az = fabsf(zeta);
+    float tt;
+    if (az > 1e15f) {
+        tt = __fdividef(0.5f, zeta);
+    } else {
+        const float q = fmaf(zeta, zeta, 1.f);
+        tt = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
+    }
+    const float c = rsqrtf(fmaf(tt, tt, 1.f));
     const float sn = c * tt;
-    for (int jj = 0, j = j0; jj < J; ++jj, j = (j + 1 == J) ? 0 : j + 1) {
-        const int i = j * kG + gl;
-        const float x = a[i], y = b[i];
-        a[i] = fmaf(c, x, -sn * y);
-        b[i] = fmaf(sn, x, c * y);
+    for (int i = 4 * gl; i < n; i += 4 * G) {
+        float4 x = *reinterpret_cast<float4*>(a + i);
+        float4 y = *reinterpret_cast<float4*>(b + i);
+        const float4 xa = x;
+        x.x = fmaf(c, xa.x, -sn * y.x);
+        x.y = fmaf(c, xa.y, -sn * y.y);
+        x.z = fmaf(c, xa.z, -sn * y.z);
+        x.w = fmaf(c, xa.w, -sn * y.w);
+        y.x = fmaf(sn, xa.x, c * y.x);
+        y.y = fmaf(sn, xa.y, c * y.y);
+        y.z = fmaf(sn, xa.z, c * y.z);
+        y.w = fmaf(sn, xa.w, c * y.w);
+        *reinterpret_cast<float4*>(a + i) = x;
+        *reinterpret_cast<float4*>(b + i) = y;
     }
     return 1;
+}
+
+// Position i of the round-robin (circle) schedule on P players in round t.
+__device__ __forceinline__ int circle_player(int i, int t, int P) {
+    if (i == 0) return 0;
+    int x = i - 1 + t;
+    if (x >= P - 1) x -= P - 1;
+    return 1 + x;
 }
 
 // FP64-accumulated norm of a length-n column (one warp).
@@ -164,13 +183,15 @@ __device__ __forceinline__ float householder(float* x, int L) {
 // (core_stride / sigma_stride apart) so one launch serves a batch.
 __global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
     const double* __restrict__ core, int r2, int s, int64_t ld, int64_t core_stride,
-    double* __restrict__ sigma, int64_t sigma_stride, int* __restrict__ status) {
+    double* __restrict__ sigma, int64_t sigma_stride, int* __restrict__ status,
+    const int* __restrict__ active) {
     extern __shared__ __align__(16) unsigned char smem[];
+    if (active && !active[blockIdx.x]) return;
     core += (int64_t)blockIdx.x * core_stride;
     sigma += (int64_t)blockIdx.x * sigma_stride;
     const int sp = (s + 31) / 32 * 32;                  // padded column length of R^T
     float* W = reinterpret_cast<float*>(smem);          // r2 x s, column-major
-    float* Rt = W + (size_t)r2 * s;                     // sp x s, column c = row c of R
+    float* Rt = W + ((size_t)r2 * s + 31) / 32 * 32;    // sp x s, column c = row c of R (128-B aligned)
     __shared__ double s_norm[512];
     __shared__ float s_tau, s_red[32];
     __shared__ int s_bad, s_flag;
@@ -259,23 +280,22 @@ __global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
         }
         __syncthreads();
         const float floor_abs = kAbsFloor * s_red[0];
-        const int grp = tid / kG, ngrp = blockDim.x / kG;
+        constexpr int G = 8;
+        const int grp = tid / G, ngrp = blockDim.x / G;
         for (int t = 0; t < P - 1; ++t) {
             for (int base = 0; base < P / 2; base += ngrp) {
                 const int q = base + grp;
                 int p = 0, qq = 0;
                 bool act = q < P / 2;
                 if (act) {
-                    const int i1 = q, i2 = P - 1 - q;
-                    const int c1 = (i1 == 0) ? 0 : 1 + (i1 - 1 + t) % (P - 1);
-                    const int c2 = (i2 == 0) ? 0 : 1 + (i2 - 1 + t) % (P - 1);
+                    const int c1 = circle_player(q, t, P), c2 = circle_player(P - 1 - q, t, P);
                     p = min(c1, c2);
                     qq = max(c1, c2);
                     act = qq < s;
                 }
                 float meas = 0.f;
-                if (rotate_pair(act, Rt + (size_t)p * sp, Rt + (size_t)qq * sp, sp, tol, floor_abs, &meas) &&
-                    (tid & (kG - 1)) == 0) {
+                if (rotate_pair<G>(act, Rt + (size_t)p * sp, Rt + (size_t)qq * sp, sp, tol, floor_abs, &meas) &&
+                    (tid & (G - 1)) == 0) {
                     s_flag = 1;
                     atomicMax(&s_meas, __float_as_uint(meas));
                 }
@@ -302,7 +322,6 @@ __global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
 
 // ---------------------------------------------------------------------------
 // Cluster version.  Column j of the core lives in CTA j % CL (local column j / CL).
-constexpr int kPullRegs = 32;       // per-thread staging for a block exchange
 
 template <int CL>
 __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
@@ -312,13 +331,14 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
     const int nloc = (s + CL - 1) / CL;
-    const int sp = (s + 31) / 32 * 32;                         // padded column length of R^T
-    float* W = reinterpret_cast<float*>(smem);                // nloc x r2 (column-major)
-    float* slot0 = W + (size_t)nloc * r2;                     // b columns of R^T (length s)
-    float* slot1 = slot0 + (size_t)b * sp;
-    float* vbuf = slot1 + (size_t)b * sp;                     // 2 x r2 Householder vectors
+    const int sp = (s + 127) / 128 * 128;                      // padded column length of R^T
+    const size_t set_floats = 2 * (size_t)b * sp;              // two blocks of b columns
+    const size_t r1_floats = (max((size_t)nloc * r2, set_floats) + 31) / 32 * 32;
+    float* W = reinterpret_cast<float*>(smem);                // QR: nloc x r2 (column-major)
+    float* vbuf = W + r1_floats;                              // 2 x r2 Householder vectors
+    float* sets[2] = {vbuf + (2 * (size_t)r2 + 31) / 32 * 32, W};   // Jacobi ping-pong (set 1 reuses W)
     __shared__ float s_tau[2];
-    __shared__ int s_block[2];
+    __shared__ int s_block[2][2];                             // [set][slot] block ids
     __shared__ int s_count, s_bad;
     __shared__ unsigned int s_meas;
     __shared__ float s_fmax;
@@ -412,9 +432,10 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
 
     // ---- gather the two R^T column blocks of this CTA (positions k and P2-1-k)
     if (tid == 0) {
-        s_block[0] = k;
-        s_block[1] = P2 - 1 - k;
+        s_block[0][0] = k;
+        s_block[0][1] = P2 - 1 - k;
     }
+    float* slot0 = sets[0];
     for (int64_t idx = tid; idx < 2 * (int64_t)b * sp; idx += blockDim.x) {
         const int sl = (int)(idx / ((int64_t)b * sp));
         const int64_t off = idx % ((int64_t)b * sp);
@@ -430,14 +451,13 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
     }
     cluster.sync();
 
-    // ---- blocked Jacobi on R^T (length-s columns)
+    // ---- blocked Jacobi on R^T (length-sp columns, zero padded)
     const float tol = 4.f * kU * sqrtf((float)s);
-    float stage[kPullRegs];
-    const int per_thread = (2 * b * sp + kSvdThreads - 1) / kSvdThreads;
+    int cur = 0;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         float amax = 0.f;
         for (int q = warp; q < 2 * b; q += nwarps) {
-            const float* a = slot0 + (size_t)q * sp;
+            const float* a = sets[cur] + (size_t)q * sp;
             float acc = 0.f;
             for (int i = lane; i < sp; i += 32) acc = fmaf(a[i], a[i], acc);
             amax = fmaxf(amax, warp_sum(acc));
@@ -453,9 +473,12 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         for (int r = 0; r < CL; ++r) gm = fmaxf(gm, *cluster.map_shared_rank(&s_fmax, r));
         const float floor_abs = kAbsFloor * gm;
         for (int t = 0; t < P2 - 1; ++t) {
+            float* c0 = sets[cur];
+            float* c1 = c0 + (size_t)b * sp;
             int rotated = 0;
-            const int grp = tid / kG, ngrp = blockDim.x / kG;
-            const bool leader = (tid & (kG - 1)) == 0;
+            constexpr int G = 32;                  // one warp per pair: few pairs per round
+            const int grp = tid / G, ngrp = blockDim.x / G;
+            const bool leader = (tid & (G - 1)) == 0;
             if (t == 0) {
                 // pairs inside each block (circle ordering on b columns)
                 const int P = b + (b & 1);
@@ -463,21 +486,19 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
                     for (int base = 0; base < P; base += ngrp) {
                         const int q = base + grp;
                         bool act = q < P;
-                        float* pa = slot0;
-                        float* pb = slot0;
+                        float* pa = c0;
+                        float* pb = c0;
                         if (act) {
                             const int sl = q / (P / 2), kq = q % (P / 2);
-                            const int i1 = kq, i2 = P - 1 - kq;
-                            const int c1 = (i1 == 0) ? 0 : 1 + (i1 - 1 + u) % (P - 1);
-                            const int c2 = (i2 == 0) ? 0 : 1 + (i2 - 1 + u) % (P - 1);
-                            const int p = min(c1, c2), qq = max(c1, c2);
+                            const int e1 = circle_player(kq, u, P), e2 = circle_player(P - 1 - kq, u, P);
+                            const int p = min(e1, e2), qq = max(e1, e2);
                             act = qq < b;
-                            float* bs = sl == 0 ? slot0 : slot1;
+                            float* bs = sl == 0 ? c0 : c1;
                             pa = bs + (size_t)p * sp;
                             pb = bs + (size_t)qq * sp;
                         }
                         float meas = 0.f;
-                        if (rotate_pair(act, pa, pb, sp, tol, floor_abs, &meas) && leader) {
+                        if (rotate_pair<G>(act, pa, pb, sp, tol, floor_abs, &meas) && leader) {
                             rotated = 1;
                             atomicMax(&s_meas, __float_as_uint(meas));
                         }
@@ -490,10 +511,11 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
                 for (int base = 0; base < b; base += ngrp) {
                     const int j = base + grp;
                     const bool act = j < b;
-                    const int jj = act ? (j + u) % b : 0;
+                    int jj = act ? j + u : 0;
+                    if (jj >= b) jj -= b;
                     float meas = 0.f;
-                    if (rotate_pair(act, slot0 + (size_t)(act ? j : 0) * sp, slot1 + (size_t)jj * sp, sp, tol,
-                                    floor_abs, &meas) && leader) {
+                    if (rotate_pair<G>(act, c0 + (size_t)(act ? j : 0) * sp, c1 + (size_t)jj * sp, sp, tol,
+                                       floor_abs, &meas) && leader) {
                         rotated = 1;
                         atomicMax(&s_meas, __float_as_uint(meas));
                     }
@@ -501,40 +523,34 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
                 __syncthreads();
             }
             if (rotated) atomicAdd(&s_count, 1);
-            // tournament positions 1..P2-1 move up by one; pull the new blocks
+            // tournament positions 1..P2-1 move up by one: pull the new blocks from
+            // the current set of their source CTAs into this CTA's other set
             cluster.sync();
             const int src0 = (k == 0) ? -1 : (k == 1 ? P2 - 1 : k - 1);
             const int src1 = P2 - 2 - k;
             auto cta_of = [](int pos) { return pos < CL ? pos : P2 - 1 - pos; };
             auto slot_of = [](int pos) { return pos < CL ? 0 : 1; };
-            int nb0 = s_block[0];
-            const int nb1 = cluster.map_shared_rank(&s_block[0], cta_of(src1))[slot_of(src1)];
-            if (src0 >= 0) nb0 = cluster.map_shared_rank(&s_block[0], cta_of(src0))[slot_of(src0)];
-#pragma unroll
-            for (int q = 0; q < kPullRegs; ++q) {
-                const int64_t idx = (int64_t)q * kSvdThreads + tid;
-                if (q < per_thread && idx < 2 * (int64_t)b * sp) {
-                    const int sl = (int)(idx / ((int64_t)b * sp));
-                    const int64_t off = idx % ((int64_t)b * sp);
-                    const int src = sl == 0 ? src0 : src1;
-                    if (src >= 0) {
-                        const float* rs = cluster.map_shared_rank(slot0, cta_of(src));
-                        stage[q] = rs[(size_t)slot_of(src) * b * sp + off];
-                    } else {
-                        stage[q] = slot0[off];
-                    }
+            const int nxt = cur ^ 1;
+            const int n4 = b * sp / 4;
+            for (int sl = 0; sl < 2; ++sl) {
+                const int src = sl == 0 ? src0 : src1;
+                const float4* from;
+                if (src >= 0) {
+                    const float* rs = cluster.map_shared_rank(sets[cur], cta_of(src));
+                    from = reinterpret_cast<const float4*>(rs + (size_t)slot_of(src) * b * sp);
+                } else {
+                    from = reinterpret_cast<const float4*>(sets[cur]);
                 }
-            }
-            cluster.sync();
-#pragma unroll
-            for (int q = 0; q < kPullRegs; ++q) {
-                const int64_t idx = (int64_t)q * kSvdThreads + tid;
-                if (q < per_thread && idx < 2 * (int64_t)b * sp) slot0[idx] = stage[q];
+                float4* to = reinterpret_cast<float4*>(sets[nxt] + (size_t)sl * b * sp);
+                for (int i = tid; i < n4; i += blockDim.x) to[i] = from[i];
             }
             if (tid == 0) {
-                s_block[0] = nb0;
-                s_block[1] = nb1;
+                s_block[nxt][0] = src0 >= 0
+                                      ? cluster.map_shared_rank(&s_block[cur][0], cta_of(src0))[slot_of(src0)]
+                                      : s_block[cur][0];
+                s_block[nxt][1] = cluster.map_shared_rank(&s_block[cur][0], cta_of(src1))[slot_of(src1)];
             }
+            cur = nxt;
             __syncthreads();
         }
         cluster.sync();
@@ -553,10 +569,11 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         if (k == 0 && tid == 0) status[2] = sweep + 1;
         if (total == 0 || worst < kStopFactor * kU * sqrtf((float)s)) break;
     }
+    slot0 = sets[cur];
     // ---- norms gathered in CTA 0
     for (int q = warp; q < 2 * b; q += nwarps) {
         const int sl = q / b, j = q % b;
-        const int c = s_block[sl] * b + j;
+        const int c = s_block[cur][sl] * b + j;
         const double nv = col_norm(slot0 + (size_t)q * sp, sp);
         if (lane == 0 && c < s) *cluster.map_shared_rank(&s_norm[c], 0) = nv;
     }
@@ -570,9 +587,11 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
 size_t cluster_smem(int CL, int r2, int s, int* b_out) {
     const int nloc = (s + CL - 1) / CL;
     const int b = (s + 2 * CL - 1) / (2 * CL);
-    const size_t sp = (size_t)(s + 31) / 32 * 32;
+    const size_t sp = (size_t)(s + 127) / 128 * 128;
+    const size_t set_floats = 2 * (size_t)b * sp;
     *b_out = b;
-    return sizeof(float) * ((size_t)nloc * r2 + 2 * (size_t)b * sp + 2 * (size_t)r2);
+    return sizeof(float) * ((std::max((size_t)nloc * r2, set_floats) + 31) / 32 * 32 +
+                            (2 * (size_t)r2 + 31) / 32 * 32 + set_floats);
 }
 
 template <int CL>
@@ -580,7 +599,6 @@ cudaError_t launch_cluster_sigma(const double* core, int r2, int s, int64_t ld, 
                                  int* status, cudaStream_t st) {
     int b = 0;
     const size_t smem = cluster_smem(CL, r2, s, &b);
-    if (2 * (size_t)b * ((s + 31) / 32 * 32) > (size_t)kPullRegs * kSvdThreads) return cudaErrorInvalidValue;
     auto kern = core_sigma_cluster_kernel<CL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -646,7 +664,7 @@ constexpr size_t kSmemLimit = 210 * 1024;
 
 size_t cta_smem(int r2, int s) {
     const size_t sp = (size_t)(s + 31) / 32 * 32;
-    return sizeof(float) * ((size_t)r2 * s + sp * s);
+    return sizeof(float) * (((size_t)r2 * s + 31) / 32 * 32 + sp * s);
 }
 
 }  // namespace
@@ -657,14 +675,15 @@ bool core_sigma_fits_cta(int r2, int s) { return cta_smem(r2, s) <= kSmemLimit; 
 
 cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t ld,
                                       int64_t core_stride, int count, double* sigma,
-                                      int64_t sigma_stride, int* status, cudaStream_t st) {
+                                      int64_t sigma_stride, int* status, cudaStream_t st,
+                                      const int* active) {
     const size_t sm = cta_smem(r2, s);
     if (sm > kSmemLimit || count <= 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(core_sigma_cta_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     core_sigma_cta_kernel<<<count, kSvdThreads, sm, st>>>(core, r2, s, ld, core_stride, sigma,
-                                                          sigma_stride, status);
+                                                          sigma_stride, status, active);
     return cudaGetLastError();
 }
 
@@ -675,11 +694,8 @@ cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, voi
     if (cta_smem(r2, s) <= kSmemLimit)
         return launch_core_sigma_batched(core, r2, s, ld, 0, 1, sigma, 0, status, st);
     int b = 0;
-    const size_t sp = (size_t)(s + 31) / 32 * 32;
-    if (cluster_smem(8, r2, s, &b) <= kSmemLimit && 2 * (size_t)b * sp <= (size_t)kPullRegs * kSvdThreads)
-        return launch_cluster_sigma<8>(core, r2, s, ld, sigma, status, st);
-    if (cluster_smem(16, r2, s, &b) <= kSmemLimit && 2 * (size_t)b * sp <= (size_t)kPullRegs * kSvdThreads)
-        return launch_cluster_sigma<16>(core, r2, s, ld, sigma, status, st);
+    if (cluster_smem(8, r2, s, &b) <= kSmemLimit) return launch_cluster_sigma<8>(core, r2, s, ld, sigma, status, st);
+    if (cluster_smem(16, r2, s, &b) <= kSmemLimit) return launch_cluster_sigma<16>(core, r2, s, ld, sigma, status, st);
     return cudaErrorInvalidValue;
 }
 

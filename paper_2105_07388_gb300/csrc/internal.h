@@ -23,6 +23,18 @@ struct MatView {
     bool trans;
 };
 
+// One block of a batched estimate, as the batched kernels see it (device array).
+struct BatchDesc {
+    const float* A;     // FP32, oriented view as in MatView
+    int64_t ld;
+    int64_t rows, cols; // rows >= cols
+    int trans;
+    int smax;           // largest sketch width for this block
+    int64_t ax_off;     // offset (floats) of this block's AX region (rows x ldax) in the AX pool
+    int64_t x_off;      // offset (floats) of this block's X region (cols x xs) in the X pool
+    uint64_t seed;
+};
+
 // ---- embeddings (embed.cu) ----------------------------------------------------
 // X columns [col0, col0+s) as FP32, row-major n x ldx.
 cudaError_t launch_gauss_x(uint64_t seed, int64_t n, int col0, int s, float* X, int64_t ldx,
@@ -61,6 +73,13 @@ cudaError_t launch_left(int kind, uint64_t seed, const float* AX, int64_t ldax, 
                         cudaStream_t st);
 size_t left_part_floats(int64_t M, int R, int S);
 
+// Batched right sketch: for every active block b and each of its BM-row tiles
+// (tile_prefix[b] .. tile_prefix[b+1]-1 are b's work items), AX_b[:, col0:col0+s]
+// = A_b X_b with X_b (cols x s, ld s) at Xpool + x_off.  BM is 64 or 128.
+cudaError_t launch_right_simt_batched(const BatchDesc* d, int count, const int64_t* tile_prefix,
+                                      int64_t items, const int* active, const float* Xpool, int s,
+                                      float* AXpool, int64_t ldax, int col0, int bm, cudaStream_t st);
+
 // ---- right sketch, SRHT (sketch_srht.cu) --------------------------------------
 // C[:, 0:s] = A_oriented * D H S^T with sampled Hadamard columns cols[0..s).
 cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int* cols, int s,
@@ -84,7 +103,8 @@ cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, voi
 bool core_sigma_fits_cta(int r2, int s);
 cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t ld,
                                       int64_t core_stride, int count, double* sigma,
-                                      int64_t sigma_stride, int* status, cudaStream_t st);
+                                      int64_t sigma_stride, int* status, cudaStream_t st,
+                                      const int* active = nullptr);
 
 // Device read-off (step 8).  Writes DevReadoff to `out`.
 struct DevReadoff {
@@ -98,5 +118,15 @@ struct DevReadoff {
 cudaError_t launch_readoff(const double* sigma, int r1, double scale, double eps, double norm_a,
                            const int* status_in, DevReadoff* out, double* sigma_scaled,
                            cudaStream_t st);
+
+// ---- batched estimate (batched.cu) --------------------------------------------
+struct BatchedState;
+// Level-synchronous batched Algorithm 1 (FP32 input, Gaussian X and Y); state is
+// created on first use and owned by the handle.  launches is incremented by the
+// number of kernels in one replay of the captured graph.
+int batched_estimate(BatchedState** st, const re_opts& o, const re_block* blocks, int count,
+                     double eps, uint64_t seed, double* sigma_out, int sigma_cap, re_result* out,
+                     cudaStream_t stream, int64_t* launches);
+void batched_destroy(BatchedState* st);
 
 }  // namespace re

@@ -35,23 +35,26 @@ __device__ __forceinline__ float ld_as_f32(const TA* p) {
     return (float)__ldg(p);
 }
 
-// Loads of one A tile into registers (16 values per thread), non-transposed:
-// thread t holds row (t & 127), k range [16 (t >> 7), +16).
-template <typename TA, bool TRANS>
+// Loads of one BM x 32 A tile into registers (BM/8 values per thread).
+// Non-transposed: thread t holds row (t % BM), k range [(t / BM) * BM/8, + BM/8).
+// Transposed (oriented (r, c) = A[c * lda + r]): thread t holds k = t / 8 and
+// rows [(t % 8) * BM/8, + BM/8).
+template <typename TA, bool TRANS, int BM>
 struct ATile {
-    float v[16];
+    static constexpr int PER = BM / 8;
+    float v[PER];
 
     __device__ __forceinline__ void load(const TA* __restrict__ A, int64_t lda, int64_t M,
                                          int64_t N, int64_t m0, int64_t k0, bool vec) {
         const int t = threadIdx.x;
         if (!TRANS) {
-            const int64_t r = m0 + (t & 127);
-            const int64_t kb = k0 + 16 * (t >> 7);
+            const int64_t r = m0 + (t % BM);
+            const int64_t kb = k0 + PER * (t / BM);
             if constexpr (sizeof(TA) == 4) {
-                if (vec && r < M && kb + 16 <= N) {
+                if (vec && r < M && kb + PER <= N) {
                     const float4* p = reinterpret_cast<const float4*>(A + r * lda + kb);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < PER / 4; ++q) {
                         const float4 w = __ldg(p + q);
                         v[4 * q + 0] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
                     }
@@ -59,17 +62,16 @@ struct ATile {
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < PER; ++q)
                 v[q] = (r < M && kb + q < N) ? ld_as_f32(A + r * lda + kb + q) : 0.0f;
         } else {
-            // oriented (r, c) = A[c * lda + r]; thread t: c = k0 + (t >> 3), r range [16 (t & 7), +16)
             const int64_t c = k0 + (t >> 3);
-            const int64_t rb = m0 + 16 * (t & 7);
+            const int64_t rb = m0 + PER * (t & 7);
             if constexpr (sizeof(TA) == 4) {
-                if (vec && c < N && rb + 16 <= M) {
+                if (vec && c < N && rb + PER <= M) {
                     const float4* p = reinterpret_cast<const float4*>(A + c * lda + rb);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < PER / 4; ++q) {
                         const float4 w = __ldg(p + q);
                         v[4 * q + 0] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
                     }
@@ -77,25 +79,25 @@ struct ATile {
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < PER; ++q)
                 v[q] = (c < N && rb + q < M) ? ld_as_f32(A + c * lda + rb + q) : 0.0f;
         }
     }
 
-    // shared tile layout: As[k][m] with row pitch kBM + 4
+    // shared tile layout: As[k][m] with row pitch BM + 4
     __device__ __forceinline__ void store(float* As) const {
         const int t = threadIdx.x;
         if (!TRANS) {
-            const int r = t & 127;
-            const int kb = 16 * (t >> 7);
+            const int r = t % BM;
+            const int kb = PER * (t / BM);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) As[(kb + q) * (kBM + 4) + r] = v[q];
+            for (int q = 0; q < PER; ++q) As[(kb + q) * (BM + 4) + r] = v[q];
         } else {
             const int c = t >> 3;
-            const int rb = 16 * (t & 7);
-            float4* p = reinterpret_cast<float4*>(As + c * (kBM + 4) + rb);
+            const int rb = PER * (t & 7);
+            float4* p = reinterpret_cast<float4*>(As + c * (BM + 4) + rb);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            for (int q = 0; q < PER / 4; ++q) p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
     }
 };
@@ -123,21 +125,21 @@ struct XTile {
     }
 };
 
-template <int BN, bool TRANS, typename TA>
-__global__ void __launch_bounds__(kThreads) right_simt_kernel(const TA* __restrict__ A, int64_t lda,
-                                                              int64_t M, int64_t N,
-                                                              const float* __restrict__ X,
-                                                              int64_t ldx, float* __restrict__ C,
-                                                              int64_t ldc, int vec) {
+// One BM x BN output tile of A*X (FP32 FMA): rows m0.., columns n0.. of C.
+// smem: 2 x 32 x (BM+4) floats for A, then 2 x 32 x BN floats for X.
+template <int BN, bool TRANS, typename TA, int BM>
+__device__ __forceinline__ void simt_tile(const TA* __restrict__ A, int64_t lda, int64_t M, int64_t N,
+                                          const float* __restrict__ X, int64_t ldx,
+                                          float* __restrict__ C, int64_t ldc, int64_t m0, int n0,
+                                          bool vec, float* smem) {
     using S = SimtShape<BN>;
-    constexpr int TN = S::TN, TM = S::TM;
+    constexpr int TN = S::TN;
     constexpr int TX = BN / TN;
-    extern __shared__ float4 smem_raw[];
-    float* As = reinterpret_cast<float*>(smem_raw);              // 2 x kBK x (kBM+4)
-    float* Bs = As + 2 * kBK * (kBM + 4);                        // 2 x kBK x BN
-
-    const int n0 = blockIdx.x * BN;
-    const int64_t m0 = (int64_t)blockIdx.y * kBM;
+    constexpr int TY = kThreads / TX;
+    constexpr int TM = BM / TY;
+    static_assert(TM % 4 == 0 || TM == 2, "row fragment");
+    float* As = smem;                                // 2 x kBK x (BM+4)
+    float* Bs = As + 2 * kBK * (BM + 4);             // 2 x kBK x BN
     const int tx = threadIdx.x % TX;
     const int ty = threadIdx.x / TX;
 
@@ -147,10 +149,10 @@ __global__ void __launch_bounds__(kThreads) right_simt_kernel(const TA* __restri
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
 
-    ATile<TA, TRANS> at;
+    ATile<TA, TRANS, BM> at;
     XTile<BN> xt;
     const int64_t KT = (N + kBK - 1) / kBK;
-    at.load(A, lda, M, N, m0, 0, vec != 0);
+    at.load(A, lda, M, N, m0, 0, vec);
     xt.load(X, ldx, N, 0, n0);
     at.store(As);
     xt.store(Bs);
@@ -160,19 +162,24 @@ __global__ void __launch_bounds__(kThreads) right_simt_kernel(const TA* __restri
         const int buf = (int)(kt & 1);
         const bool more = kt + 1 < KT;
         if (more) {
-            at.load(A, lda, M, N, m0, (kt + 1) * kBK, vec != 0);
+            at.load(A, lda, M, N, m0, (kt + 1) * kBK, vec);
             xt.load(X, ldx, N, (kt + 1) * kBK, n0);
         }
-        const float* as = As + buf * kBK * (kBM + 4);
+        const float* as = As + buf * kBK * (BM + 4);
         const float* bs = Bs + buf * kBK * BN;
 #pragma unroll 8
         for (int k = 0; k < kBK; ++k) {
             float a[TM], b[TN];
-            const float* ap = as + k * (kBM + 4) + ty * TM;
+            const float* ap = as + k * (BM + 4) + ty * TM;
+            if constexpr (TM >= 4) {
 #pragma unroll
-            for (int i = 0; i < TM; i += 4) {
-                const float4 w = *reinterpret_cast<const float4*>(ap + i);
-                a[i] = w.x; a[i + 1] = w.y; a[i + 2] = w.z; a[i + 3] = w.w;
+                for (int i = 0; i < TM; i += 4) {
+                    const float4 w = *reinterpret_cast<const float4*>(ap + i);
+                    a[i] = w.x; a[i + 1] = w.y; a[i + 2] = w.z; a[i + 3] = w.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < TM; ++i) a[i] = ap[i];
             }
             const float* bp = bs + k * BN + tx * TN;
             if constexpr (TN >= 4) {
@@ -191,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) right_simt_kernel(const TA* __restri
                 for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
         if (more) {
-            at.store(As + (buf ^ 1) * kBK * (kBM + 4));
+            at.store(As + (buf ^ 1) * kBK * (BM + 4));
             xt.store(Bs + (buf ^ 1) * kBK * BN);
         }
         __syncthreads();
@@ -204,6 +211,75 @@ __global__ void __launch_bounds__(kThreads) right_simt_kernel(const TA* __restri
         float* cp = C + r * ldc + n0 + tx * TN;
 #pragma unroll
         for (int j = 0; j < TN; ++j) cp[j] = acc[i][j];
+    }
+}
+
+template <int BN, bool TRANS, typename TA>
+__global__ void __launch_bounds__(kThreads) right_simt_kernel(const TA* __restrict__ A, int64_t lda,
+                                                              int64_t M, int64_t N,
+                                                              const float* __restrict__ X,
+                                                              int64_t ldx, float* __restrict__ C,
+                                                              int64_t ldc, int vec) {
+    extern __shared__ float4 smem_raw[];
+    simt_tile<BN, TRANS, TA, kBM>(A, lda, M, N, X, ldx, C, ldc, (int64_t)blockIdx.y * kBM,
+                                  (int)blockIdx.x * BN, vec != 0, reinterpret_cast<float*>(smem_raw));
+}
+
+// Batched: one CTA per (block, BM-row tile) work item.
+__device__ __forceinline__ int find_block(const int64_t* prefix, int count, int64_t item) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int BN, int BM>
+__global__ void __launch_bounds__(kThreads) right_simt_batched_kernel(
+    const BatchDesc* __restrict__ d, int count, const int64_t* __restrict__ tile_prefix,
+    const int* __restrict__ active, const float* __restrict__ Xpool, int s,
+    float* __restrict__ AXpool, int64_t ldax, int col0) {
+    extern __shared__ float4 smem_raw[];
+    const int64_t item = blockIdx.x;
+    const int b = find_block(tile_prefix, count, item);
+    if (!active[b]) return;
+    const BatchDesc D = d[b];
+    const int64_t m0 = (item - tile_prefix[b]) * BM;
+    const bool vec = ((reinterpret_cast<uintptr_t>(D.A) & 15) == 0) && ((D.ld & 3) == 0);
+    const float* X = Xpool + D.x_off;
+    float* C = AXpool + D.ax_off + col0;
+    float* sm = reinterpret_cast<float*>(smem_raw);
+    if (D.trans)
+        simt_tile<BN, true, float, BM>(D.A, D.ld, D.rows, D.cols, X, s, C, ldax, m0, 0, vec, sm);
+    else
+        simt_tile<BN, false, float, BM>(D.A, D.ld, D.rows, D.cols, X, s, C, ldax, m0, 0, vec, sm);
+}
+
+template <int BN, int BM>
+cudaError_t launch_batched_t(const BatchDesc* d, int count, const int64_t* tile_prefix, int64_t items,
+                             const int* active, const float* Xpool, int s, float* AXpool, int64_t ldax,
+                             int col0, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (2 * kBK * (BM + 4) + 2 * kBK * BN);
+    auto kern = right_simt_batched_kernel<BN, BM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)items, kThreads, smem, st>>>(d, count, tile_prefix, active, Xpool, s, AXpool, ldax, col0);
+    return cudaGetLastError();
+}
+
+template <int BM>
+cudaError_t dispatch_batched(const BatchDesc* d, int count, const int64_t* tile_prefix, int64_t items,
+                             const int* active, const float* Xpool, int s, float* AXpool, int64_t ldax,
+                             int col0, cudaStream_t st) {
+    switch (s) {
+        case 8: return launch_batched_t<8, BM>(d, count, tile_prefix, items, active, Xpool, s, AXpool, ldax, col0, st);
+        case 16: return launch_batched_t<16, BM>(d, count, tile_prefix, items, active, Xpool, s, AXpool, ldax, col0, st);
+        case 32: return launch_batched_t<32, BM>(d, count, tile_prefix, items, active, Xpool, s, AXpool, ldax, col0, st);
+        case 64: return launch_batched_t<64, BM>(d, count, tile_prefix, items, active, Xpool, s, AXpool, ldax, col0, st);
+        case 128: return launch_batched_t<128, BM>(d, count, tile_prefix, items, active, Xpool, s, AXpool, ldax, col0, st);
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -375,6 +451,14 @@ cudaError_t launch_right_simt(const MatView& A, const float* X, int64_t ldx, int
     if (s % 32 == 0) return dispatch_right<32>(A, X, ldx, s, C, ldc, st);
     if (s % 16 == 0) return dispatch_right<16>(A, X, ldx, s, C, ldc, st);
     return dispatch_right<8>(A, X, ldx, s, C, ldc, st);
+}
+
+cudaError_t launch_right_simt_batched(const BatchDesc* d, int count, const int64_t* tile_prefix,
+                                      int64_t items, const int* active, const float* Xpool, int s,
+                                      float* AXpool, int64_t ldax, int col0, int bm, cudaStream_t st) {
+    if (items <= 0) return cudaSuccess;
+    if (bm == 64) return dispatch_batched<64>(d, count, tile_prefix, items, active, Xpool, s, AXpool, ldax, col0, st);
+    return dispatch_batched<128>(d, count, tile_prefix, items, active, Xpool, s, AXpool, ldax, col0, st);
 }
 
 size_t left_part_floats(int64_t M, int R, int S) {

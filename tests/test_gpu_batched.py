@@ -1,0 +1,96 @@
+"""Batched Algorithm 1 (one captured graph over many uneven blocks) against the
+FP64 oracle run block by block, and against the single-matrix entry point."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import algorithm1 as alg
+from paper_2105_07388_gb300 import rankest as rk
+from paper_2105_07388_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+SIGMA_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2105_07388_gb300 import build
+    build.build()
+    hd = rk.re_create(0, rk.make_opts(s_max=128))
+    yield hd
+    rk.re_destroy(hd)
+
+
+def _agree(rank, orc, eps):
+    if rank == orc.rank:
+        return True
+    tau = eps * orc.sigma[0]
+    return bool(np.any(np.abs(orc.sigma - tau) <= SIGMA_TOL * orc.sigma[0]))
+
+
+def test_batched_gapped_blocks_exact(h):
+    # clear gaps, uneven and transposed shapes: ranks identical to the oracle's
+    specs = [(300, 257, 5), (257, 700, 12), (1024, 1024, 40), (900, 300, 1), (333, 333, 70),
+             (2000, 600, 100), (600, 2000, 3), (512, 256, 0)]
+    blocks, mats = [], []
+    for i, (m, n, r) in enumerate(specs):
+        k = min(m, n)
+        if r == 0:
+            A = torch.zeros(m, n, dtype=torch.float64)
+        else:
+            A = wl.haar_matrix(m, n, wl.spectrum("step", k, rank=r, tail_scale=1e-9), seed=i)
+        A32 = A.to(torch.float32)
+        blocks.append(A32.cuda())
+        mats.append(A32.double().numpy())
+    res, sig = rk.re_rank_estimate_batched(h, blocks, 1e-4, rk.RE_GAUSSIAN, 900, sigma_cap=128)
+    for i, (m, n, r) in enumerate(specs):
+        orc = alg.rank_estimate(mats[i], 1e-4, kind=alg.GAUSSIAN, seed=900 + i, s_max=128)
+        assert res[i].status == 0
+        assert res[i].rank == orc.rank == r, (i, res[i].rank, orc.rank)
+        assert res[i].final_s == orc.final_s and res[i].passes == orc.passes
+        k = min(res[i].n_sigma, len(orc.sigma))
+        assert np.max(np.abs(sig[i, :k] - orc.sigma[:k])) <= SIGMA_TOL * max(orc.sigma[0], 1e-300)
+        assert bool(res[i].flags & rk.RE_TRANSPOSED) == (m < n)
+
+
+def test_batched_kernel_blocks_and_replay(h):
+    shapes = wl.kernel_block_sizes(24, seed=11, lo=256, hi=2048)
+    blocks = [wl.kernel_block(m, n, seed=300 + i).cuda() for i, (m, n) in enumerate(shapes)]
+    r1, s1 = rk.re_rank_estimate_batched(h, blocks, 1e-6, rk.RE_GAUSSIAN, 77, sigma_cap=128)
+    r2, s2 = rk.re_rank_estimate_batched(h, blocks, 1e-6, rk.RE_GAUSSIAN, 77, sigma_cap=128)   # graph replay
+    assert [x.rank for x in r1] == [x.rank for x in r2] and np.array_equal(s1, s2)
+    for i, B in enumerate(blocks):
+        orc = alg.rank_estimate(B.double().cpu().numpy(), 1e-6, kind=alg.GAUSSIAN, seed=77 + i, s_max=128)
+        k = min(r1[i].n_sigma, len(orc.sigma))
+        assert r1[i].final_s == orc.final_s or _agree(r1[i].rank, orc, 1e-6)
+        if r1[i].final_s == orc.final_s:
+            assert np.max(np.abs(s1[i, :k] - orc.sigma[:k])) <= SIGMA_TOL * orc.sigma[0]
+        assert _agree(r1[i].rank, orc, 1e-6)
+
+
+def test_batched_matches_single_matrix_path(h):
+    specs = [(1500, 700, 33), (700, 1500, 60), (800, 800, 9)]
+    blocks = []
+    for i, (m, n, r) in enumerate(specs):
+        A = wl.haar_matrix(m, n, wl.spectrum("step", min(m, n), rank=r, tail_scale=1e-9), seed=40 + i)
+        blocks.append(A.to(torch.float32).cuda())
+    res, sig = rk.re_rank_estimate_batched(h, blocks, 1e-4, rk.RE_GAUSSIAN, 5, sigma_cap=128)
+    for i, B in enumerate(blocks):
+        one, s1 = rk.re_rank_estimate(h, B, 1e-4, rk.RE_GAUSSIAN, 5 + i)
+        assert one.rank == res[i].rank == specs[i][2] and one.final_s == res[i].final_s
+        k = min(len(s1), res[i].n_sigma)
+        assert np.max(np.abs(s1[:k] - sig[i, :k])) <= SIGMA_TOL * s1[0]
+
+
+def test_batched_invalid_block_reported(h):
+    good = wl.haar_matrix(400, 300, wl.spectrum("step", 300, rank=7, tail_scale=1e-9), seed=1).to(torch.float32).cuda()
+    arr = (rk.re_block * 2)()
+    arr[0].ptr, arr[0].m, arr[0].n, arr[0].ld = good.data_ptr(), 400, 300, 300
+    arr[1].ptr, arr[1].m, arr[1].n, arr[1].ld = good.data_ptr(), 400, 300, 100       # ld < n
+    out = (rk.re_result * 2)()
+    rc = rk.lib().re_rank_estimate_batched(h, arr, 2, rk.RE_F32, 1e-4, rk.RE_GAUSSIAN, 3, None, 0, out, None)
+    assert rc == 0
+    assert out[0].status == 0 and out[0].rank == 7
+    assert out[1].status == rk.RE_ERR_ARG
