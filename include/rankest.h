@@ -227,6 +227,42 @@ int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int
                              double* sigma_out, int sigma_cap, re_result* out, void* stream);
 
 /*
+ * Sketch-size proposal network (answers the question left open in the paper's
+ * discussion, Sec. 7: choosing a new r1 from the information of a first run).
+ * An 18 -> 128 -> 128 -> 12 ReLU network maps features of an s = 16 first sketch
+ * (the 14 trusted log10(sigma^_i / (eps sigma^_1)), log10 rows, log10 cols,
+ * log10(1/eps), and the log decay of the last seven trusted values) to a width
+ * class c (width 8 * 2^c).  With opts.learned = 1, re_rank_estimate sketches to
+ * s = 16, asks the network for s*, appends straight to s*, and checks the
+ * read-off on the nested leading core blocks at s = 8, 16, 32, ..., s* in
+ * order: the result equals the plain doubling ladder's whenever s* is at least
+ * its final width, and doubling continues from s* otherwise.  Weights are used
+ * in BF16 with FP32 accumulation (FP32 master copies, Adam).  All compute runs
+ * in this library's kernels.  Parameter layout: W1 (128x18), b1, W2 (128x128),
+ * b2, W3 (12x128), b3, row-major, RE_MLP_PARAMS floats.
+ */
+#define RE_MLP_IN 18
+#define RE_MLP_OUT 12
+#define RE_MLP_PARAMS 20492
+int re_mlp_init(re_handle h, uint64_t seed);                        /* deterministic He-uniform init */
+int re_mlp_set_params(re_handle h, const float* params, int count); /* host -> device */
+int re_mlp_get_params(re_handle h, float* params, int count);       /* device -> host */
+/* Versioned file: magic "REMLPv1", parameter count, Adam step, parameters and
+ * both Adam moments (training resumes where it stopped). */
+int re_mlp_save(re_handle h, const char* path);
+int re_mlp_load(re_handle h, const char* path);
+/* classes (host, count) = argmax of the logits of X (host, count x 18); logits may be NULL */
+int re_mlp_predict(re_handle h, const float* X, int count, int* classes, float* logits);
+/* gradient (host, RE_MLP_PARAMS) and value of the mean softmax cross-entropy at (X, y) */
+int re_mlp_grad(re_handle h, const float* X, const int* y, int count, float* grad, float* loss);
+/* Adam training on (X, y) (host arrays); epoch_loss (host, epochs entries) may be NULL */
+int re_mlp_train(re_handle h, const float* X, const int* y, int count, int epochs, int batch, float lr,
+                 float weight_decay, uint64_t seed, float* epoch_loss);
+/* the 18 features of the s = 16 first sketch of a device matrix (Gaussian X, Y) */
+int re_mlp_features(re_handle h, const void* A, int dtype, int64_t m, int64_t n, int64_t ld, double eps,
+                    uint64_t seed, float* features);
+
+/*
  * The Gaussian sketch step of re_sketch_apply without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that may not
  * allocate device memory -- code running inside a CUDA stream capture (where

@@ -52,6 +52,10 @@ struct re_handle_ {
     std::vector<cudaEvent_t> event_pool;
     DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status;
     re::BatchedState* batched = nullptr;
+    // sketch-size proposal network: parameters, Adam moments, gradient, scratch
+    DevBuf mlp_P, mlp_M, mlp_V, mlp_G, mlp_X, mlp_y, mlp_logits, mlp_keep, mlp_cls, mlp_feat, mlp_loss;
+    int mlp_step = 0;
+    bool mlp_ready = false;
     re::DevReadoff* h_ro = nullptr;   // pinned
     double* h_sigma = nullptr;        // pinned, 1024 doubles
     int sm_count = 0;
@@ -295,11 +299,64 @@ int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const
     return RE_OK;
 }
 
-// Algorithm 1 with doubling on an already validated plan.
-int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* sigma_out,
-                 int sigma_cap, re_result* out, cudaStream_t st) {
+// Singular values and read-off of the leading 2s x s block of the core (the
+// core at width s, by the nested-prefix property of the appended embeddings).
+int check_width(re_handle h, const Plan& P, int s, int smax, double eps, re::DevReadoff* ro, int* r1_out,
+                cudaStream_t st) {
+    double* core = static_cast<double*>(h->core.p);
+    int* status = static_cast<int*>(h->status.p);
+    cudaEvent_t a = stage_begin(h, st);
+    cudaError_t e = re::launch_core_sigma(core, 2 * s, s, smax, h->svdws.p, static_cast<double*>(h->sigma.p),
+                                          status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "core singular values");
+    stage_end(h, st, a, kStageSvd);
+    const int r1 = std::min(r1_of_s(s), s);
+    const double scale = 1.0 / std::sqrt((double)s * (double)(2 * s));
+    e = re::launch_readoff(static_cast<const double*>(h->sigma.p), r1, scale, eps, h->opts.norm_a, status,
+                           static_cast<re::DevReadoff*>(h->ro.p), static_cast<double*>(h->sigma_scaled.p), st);
+    if (e != cudaSuccess) return cuda_fail(e, "read-off");
+    e = cudaMemcpyAsync(h->h_ro, h->ro.p, sizeof(re::DevReadoff), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "read-off copy");
+    h->stats.launches += 2;
+    resolve_timings(h);
+    *ro = *h->h_ro;
+    *r1_out = r1;
+    if (ro->status == RE_ERR_TIMEOUT) return fail(ro->status, "a bounded device wait expired");
+    if (ro->status != RE_OK) return fail(ro->status, "non-finite values in A or its sketch");
+    return RE_OK;
+}
+
+// Proposal network: class of the width at which the read-off is expected to
+// succeed, from the trusted sigma of the s = 16 core (sigma_scaled).
+int propose_width(re_handle h, const Plan& P, double eps, int* cls, cudaStream_t st) {
+    if (int r = ensure(h->mlp_feat, sizeof(float) * re::kMlpIn)) return r;
+    if (int r = ensure(h->mlp_logits, sizeof(float) * re::kMlpOut)) return r;
+    if (int r = ensure(h->mlp_cls, sizeof(int))) return r;
+    cudaError_t e = re::mlp_features(static_cast<const double*>(h->sigma_scaled.p), eps, P.A.rows, P.A.cols,
+                                     static_cast<float*>(h->mlp_feat.p), st);
+    if (e == cudaSuccess)
+        e = re::mlp_forward(static_cast<const float*>(h->mlp_P.p), static_cast<const float*>(h->mlp_feat.p), 1,
+                            static_cast<float*>(h->mlp_logits.p), nullptr, st);
+    if (e == cudaSuccess) e = re::mlp_argmax(static_cast<const float*>(h->mlp_logits.p), 1, static_cast<int*>(h->mlp_cls.p), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cls, h->mlp_cls.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "proposal network");
+    h->stats.launches += 3;
+    return RE_OK;
+}
+
+// Algorithm 1 with doubling on an already validated plan.  With the proposal
+// network enabled, the first pass goes straight to s = 16, the network picks a
+// target width s*, one more pass appends up to s*, and the read-off is checked
+// on the nested leading blocks at every ladder width up to s* in order -- so the
+// answer is the plain ladder's whenever s* is at least the plain final width;
+// otherwise doubling continues from s*.
+int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* sigma_out, int sigma_cap,
+                 re_result* out, cudaStream_t st) {
     const re_opts& o = h->opts;
     if (o.s0 > P.cap) return fail(RE_ERR_ARG, "initial sketch width exceeds the admissible width");
+    if (o.learned && !h->mlp_ready) return fail(RE_ERR_ARG, "learned proposal requested but no network is loaded");
     int smax = o.s0;
     while (smax * 2 <= P.cap) smax *= 2;
     const int64_t M = P.A.rows;
@@ -312,43 +369,50 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
     if (int r = ensure(h->status, 64)) return r;
     float* AX = static_cast<float*>(h->ax.p);
     double* core = static_cast<double*>(h->core.p);
-    int* status = static_cast<int*>(h->status.p);
     {
-        cudaError_t e0 = cudaMemsetAsync(status, 0, 4 * sizeof(int), st);
+        cudaError_t e0 = cudaMemsetAsync(h->status.p, 0, 4 * sizeof(int), st);
         if (e0 != cudaSuccess) return cuda_fail(e0, "clear status");
     }
-    const double scale_base = 1.0;
-    (void)scale_base;
-
-    int s_prev = 0, s = o.s0, passes = 0;
-    re::DevReadoff ro{};
-    int r1 = 0;
-    for (;;) {
-        if (int r = right_columns(h, P, seed, s_prev, s - s_prev, AX, smax, st)) return r;
-        if (int r = left_blocks(h, P, seed, s_prev, s, AX, smax, core, smax, st)) return r;
-        cudaEvent_t a = stage_begin(h, st);
-        cudaError_t e = re::launch_core_sigma(core, 2 * s, s, smax, h->svdws.p,
-                                              static_cast<double*>(h->sigma.p), status, st);
-        if (e != cudaSuccess) return cuda_fail(e, "core singular values");
-        stage_end(h, st, a, kStageSvd);
-        r1 = std::min(r1_of_s(s), s);
-        const double scale = 1.0 / std::sqrt((double)s * (double)(2 * s));
-        e = re::launch_readoff(static_cast<const double*>(h->sigma.p), r1, scale, eps, o.norm_a,
-                               status, static_cast<re::DevReadoff*>(h->ro.p),
-                               static_cast<double*>(h->sigma_scaled.p), st);
-        if (e != cudaSuccess) return cuda_fail(e, "read-off");
-        e = cudaMemcpyAsync(h->h_ro, h->ro.p, sizeof(re::DevReadoff), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(e, "read-off copy");
-        h->stats.launches += 2;
-        resolve_timings(h);
-        ro = *h->h_ro;
-        ++passes;
+    auto sketch_to = [&](int c0, int c1) -> int {
+        if (int r = right_columns(h, P, seed, c0, c1 - c0, AX, smax, st)) return r;
+        if (int r = left_blocks(h, P, seed, c0, c1, AX, smax, core, smax, st)) return r;
         h->stats.passes += 1;
-        if (ro.status == RE_ERR_TIMEOUT) return fail(ro.status, "a bounded device wait expired");
-        if (ro.status != RE_OK) return fail(ro.status, "non-finite values in A or its sketch");
-        if (ro.rank >= 0) break;
-        if (2 * s > smax || r1 >= P.A.cols) break;
+        return RE_OK;
+    };
+    int s_prev = 0, s = o.s0, passes = 0, r1 = 0;
+    re::DevReadoff ro{};
+    bool done = false;
+    if (o.learned && o.s0 == 8 && smax >= 16) {
+        if (int r = sketch_to(0, 16)) return r;
+        passes = 1;
+        for (int w = 8; w <= 16 && !done; w *= 2) {
+            if (int r = check_width(h, P, w, smax, eps, &ro, &r1, st)) return r;
+            s = w;
+            done = ro.rank >= 0 || r1 >= P.A.cols;
+        }
+        if (!done && smax >= 32) {
+            int cls = 0;
+            if (int r = propose_width(h, P, eps, &cls, st)) return r;
+            const int target = std::min(smax, std::max(32, 8 << std::min(std::max(cls, 0), 11)));
+            if (int r = sketch_to(16, target)) return r;
+            passes = 2;
+            for (int w = 32; w <= target && !done; w *= 2) {
+                if (int r = check_width(h, P, w, smax, eps, &ro, &r1, st)) return r;
+                s = w;
+                done = ro.rank >= 0 || r1 >= P.A.cols;
+            }
+        }
+        if (!done) {
+            if (2 * s > smax) done = true;
+            s_prev = s;
+            s *= 2;
+        }
+    }
+    while (!done) {
+        if (int r = sketch_to(s_prev, s)) return r;
+        ++passes;
+        if (int r = check_width(h, P, s, smax, eps, &ro, &r1, st)) return r;
+        if (ro.rank >= 0 || 2 * s > smax || r1 >= P.A.cols) break;
         s_prev = s;
         s *= 2;
     }
@@ -381,6 +445,7 @@ int check_opts(const re_opts* o) {
     if (o->precision != RE_PREC_FP32 && o->precision != RE_PREC_BF16X3)
         return fail(RE_ERR_ARG, "unknown precision");
     if (o->y_kind < -1 || o->y_kind > RE_SRHT) return fail(RE_ERR_ARG, "unknown y_kind");
+    if (o->learned != 0 && o->learned != 1) return fail(RE_ERR_ARG, "learned must be 0 or 1");
     return RE_OK;
 }
 
@@ -435,7 +500,9 @@ int re_destroy(re_handle h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&h->x, &h->xt, &h->ax, &h->part, &h->core, &h->sigma, &h->sigma_scaled,
-                      &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status};
+                      &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status,
+                      &h->mlp_P, &h->mlp_M, &h->mlp_V, &h->mlp_G, &h->mlp_X, &h->mlp_y,
+                      &h->mlp_logits, &h->mlp_keep, &h->mlp_cls, &h->mlp_feat, &h->mlp_loss};
     for (DevBuf* b : bufs) release(*b);
     re::batched_destroy(h->batched);
     resolve_timings(h);
@@ -623,6 +690,242 @@ int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int
             out[i].status = r;
         }
     }
+    return RE_OK;
+}
+
+}  // extern "C"
+
+// ---- sketch-size proposal network --------------------------------------------
+namespace {
+
+int mlp_alloc(re_handle h) {
+    const size_t P = sizeof(float) * re::kMlpParams;
+    if (int r = ensure(h->mlp_P, P)) return r;
+    if (int r = ensure(h->mlp_M, P)) return r;
+    if (int r = ensure(h->mlp_V, P)) return r;
+    if (int r = ensure(h->mlp_G, P)) return r;
+    if (int r = ensure(h->mlp_loss, sizeof(float))) return r;
+    return RE_OK;
+}
+
+int mlp_batch_buffers(re_handle h, int count) {
+    if (int r = ensure(h->mlp_X, sizeof(float) * re::kMlpIn * (size_t)count)) return r;
+    if (int r = ensure(h->mlp_y, sizeof(int) * (size_t)count)) return r;
+    if (int r = ensure(h->mlp_logits, sizeof(float) * re::kMlpOut * (size_t)count)) return r;
+    if (int r = ensure(h->mlp_keep, sizeof(float) * 2 * re::kMlpHidden * (size_t)count)) return r;
+    if (int r = ensure(h->mlp_cls, sizeof(int) * (size_t)count)) return r;
+    return RE_OK;
+}
+
+const char kMagic[8] = {'R', 'E', 'M', 'L', 'P', 'v', '1', 0};
+
+}  // namespace
+
+extern "C" {
+
+int re_mlp_init(re_handle h, uint64_t seed) {
+    if (!h) return fail(RE_ERR_ARG, "NULL handle");
+    cudaSetDevice(h->device);
+    if (int r = mlp_alloc(h)) return r;
+    std::vector<float> p(re::kMlpParams);
+    re::mlp_init_host(p.data(), seed);
+    cudaError_t e = cudaMemcpy(h->mlp_P.p, p.data(), sizeof(float) * p.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->mlp_M.p, 0, sizeof(float) * re::kMlpParams);
+    if (e == cudaSuccess) e = cudaMemset(h->mlp_V.p, 0, sizeof(float) * re::kMlpParams);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp init");
+    h->mlp_step = 0;
+    h->mlp_ready = true;
+    return RE_OK;
+}
+
+int re_mlp_set_params(re_handle h, const float* params, int count) {
+    if (!h || !params || count != re::kMlpParams) return fail(RE_ERR_ARG, "need RE_MLP_PARAMS parameters");
+    cudaSetDevice(h->device);
+    if (int r = mlp_alloc(h)) return r;
+    cudaError_t e = cudaMemcpy(h->mlp_P.p, params, sizeof(float) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp set params");
+    h->mlp_ready = true;
+    return RE_OK;
+}
+
+int re_mlp_get_params(re_handle h, float* params, int count) {
+    if (!h || !params || count != re::kMlpParams) return fail(RE_ERR_ARG, "need RE_MLP_PARAMS parameters");
+    if (!h->mlp_ready) return fail(RE_ERR_ARG, "no network");
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaMemcpy(params, h->mlp_P.p, sizeof(float) * count, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp get params");
+    return RE_OK;
+}
+
+int re_mlp_save(re_handle h, const char* path) {
+    if (!h || !path) return fail(RE_ERR_ARG, "NULL argument");
+    if (!h->mlp_ready) return fail(RE_ERR_ARG, "no network");
+    cudaSetDevice(h->device);
+    std::vector<float> buf(3 * (size_t)re::kMlpParams);
+    cudaError_t e = cudaMemcpy(buf.data(), h->mlp_P.p, sizeof(float) * re::kMlpParams, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data() + re::kMlpParams, h->mlp_M.p, sizeof(float) * re::kMlpParams, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data() + 2 * re::kMlpParams, h->mlp_V.p, sizeof(float) * re::kMlpParams, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp save copy");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(RE_ERR_ARG, "cannot open file for writing");
+    const int32_t hdr[2] = {re::kMlpParams, h->mlp_step};
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(RE_ERR_ARG, "write failed");
+    return RE_OK;
+}
+
+int re_mlp_load(re_handle h, const char* path) {
+    if (!h || !path) return fail(RE_ERR_ARG, "NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(RE_ERR_ARG, "cannot open file");
+    char magic[8];
+    int32_t hdr[2];
+    std::vector<float> buf(3 * (size_t)re::kMlpParams);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == re::kMlpParams &&
+              std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return fail(RE_ERR_ARG, "not a proposal-network file of this version");
+    cudaSetDevice(h->device);
+    if (int r = mlp_alloc(h)) return r;
+    cudaError_t e = cudaMemcpy(h->mlp_P.p, buf.data(), sizeof(float) * re::kMlpParams, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->mlp_M.p, buf.data() + re::kMlpParams, sizeof(float) * re::kMlpParams, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->mlp_V.p, buf.data() + 2 * re::kMlpParams, sizeof(float) * re::kMlpParams, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp load copy");
+    h->mlp_step = hdr[1];
+    h->mlp_ready = true;
+    return RE_OK;
+}
+
+int re_mlp_predict(re_handle h, const float* X, int count, int* classes, float* logits) {
+    if (!h || (count > 0 && (!X || !classes))) return fail(RE_ERR_ARG, "NULL argument");
+    if (!h->mlp_ready) return fail(RE_ERR_ARG, "no network");
+    if (count <= 0) return RE_OK;
+    cudaSetDevice(h->device);
+    if (int r = mlp_batch_buffers(h, count)) return r;
+    cudaError_t e = cudaMemcpy(h->mlp_X.p, X, sizeof(float) * re::kMlpIn * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = re::mlp_forward(static_cast<float*>(h->mlp_P.p), static_cast<float*>(h->mlp_X.p), count,
+                            static_cast<float*>(h->mlp_logits.p), nullptr, nullptr);
+    if (e == cudaSuccess) e = re::mlp_argmax(static_cast<float*>(h->mlp_logits.p), count, static_cast<int*>(h->mlp_cls.p), nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(classes, h->mlp_cls.p, sizeof(int) * count, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && logits)
+        e = cudaMemcpy(logits, h->mlp_logits.p, sizeof(float) * re::kMlpOut * count, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp predict");
+    return RE_OK;
+}
+
+int re_mlp_grad(re_handle h, const float* X, const int* y, int count, float* grad, float* loss) {
+    if (!h || !X || !y || !grad || count <= 0) return fail(RE_ERR_ARG, "bad argument");
+    if (!h->mlp_ready) return fail(RE_ERR_ARG, "no network");
+    for (int i = 0; i < count; ++i)
+        if (y[i] < 0 || y[i] >= re::kMlpOut) return fail(RE_ERR_ARG, "label out of range");
+    cudaSetDevice(h->device);
+    if (int r = mlp_batch_buffers(h, count)) return r;
+    float* G = static_cast<float*>(h->mlp_G.p);
+    cudaError_t e = cudaMemcpy(h->mlp_X.p, X, sizeof(float) * re::kMlpIn * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->mlp_y.p, y, sizeof(int) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(G, 0, sizeof(float) * re::kMlpParams);
+    if (e == cudaSuccess) e = cudaMemset(h->mlp_loss.p, 0, sizeof(float));
+    if (e == cudaSuccess)
+        e = re::mlp_forward(static_cast<float*>(h->mlp_P.p), static_cast<float*>(h->mlp_X.p), count,
+                            static_cast<float*>(h->mlp_logits.p), static_cast<float*>(h->mlp_keep.p), nullptr);
+    if (e == cudaSuccess)
+        e = re::mlp_backward(static_cast<float*>(h->mlp_P.p), static_cast<float*>(h->mlp_X.p),
+                             static_cast<int*>(h->mlp_y.p), count, static_cast<float*>(h->mlp_logits.p),
+                             static_cast<float*>(h->mlp_keep.p), G, static_cast<float*>(h->mlp_loss.p), nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(grad, G, sizeof(float) * re::kMlpParams, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && loss) e = cudaMemcpy(loss, h->mlp_loss.p, sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp grad");
+    return RE_OK;
+}
+
+int re_mlp_train(re_handle h, const float* X, const int* y, int count, int epochs, int batch, float lr,
+                 float weight_decay, uint64_t seed, float* epoch_loss) {
+    if (!h || !X || !y || count <= 0 || epochs <= 0 || batch <= 0 || !(lr > 0.f))
+        return fail(RE_ERR_ARG, "bad argument");
+    if (!h->mlp_ready) return fail(RE_ERR_ARG, "no network (re_mlp_init or re_mlp_load first)");
+    for (int i = 0; i < count; ++i)
+        if (y[i] < 0 || y[i] >= re::kMlpOut) return fail(RE_ERR_ARG, "label out of range");
+    cudaSetDevice(h->device);
+    const int B = std::min(batch, count);
+    if (int r = mlp_batch_buffers(h, B)) return r;
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::vector<float> xb((size_t)B * re::kMlpIn);
+    std::vector<int> yb(B);
+    float* G = static_cast<float*>(h->mlp_G.p);
+    float* P = static_cast<float*>(h->mlp_P.p);
+    uint64_t rng = seed * 6364136223846793005ull + 1442695040888963407ull;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int i = count - 1; i > 0; --i) {           // Fisher-Yates with a 64-bit LCG
+            rng = rng * 6364136223846793005ull + 1442695040888963407ull;
+            const int j = (int)((rng >> 33) % (uint64_t)(i + 1));
+            std::swap(order[i], order[j]);
+        }
+        double ep_loss = 0.0;
+        int nb = 0;
+        cudaError_t e = cudaMemset(h->mlp_loss.p, 0, sizeof(float));
+        for (int b0 = 0; b0 + B <= count && e == cudaSuccess; b0 += B, ++nb) {
+            for (int k = 0; k < B; ++k) {
+                std::memcpy(&xb[(size_t)k * re::kMlpIn], X + (size_t)order[b0 + k] * re::kMlpIn, sizeof(float) * re::kMlpIn);
+                yb[k] = y[order[b0 + k]];
+            }
+            e = cudaMemcpy(h->mlp_X.p, xb.data(), sizeof(float) * xb.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(h->mlp_y.p, yb.data(), sizeof(int) * B, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemset(G, 0, sizeof(float) * re::kMlpParams);
+            if (e == cudaSuccess)
+                e = re::mlp_forward(P, static_cast<float*>(h->mlp_X.p), B, static_cast<float*>(h->mlp_logits.p),
+                                    static_cast<float*>(h->mlp_keep.p), nullptr);
+            if (e == cudaSuccess)
+                e = re::mlp_backward(P, static_cast<float*>(h->mlp_X.p), static_cast<int*>(h->mlp_y.p), B,
+                                     static_cast<float*>(h->mlp_logits.p), static_cast<float*>(h->mlp_keep.p), G,
+                                     static_cast<float*>(h->mlp_loss.p), nullptr);
+            if (e == cudaSuccess)
+                e = re::mlp_adam(P, G, static_cast<float*>(h->mlp_M.p), static_cast<float*>(h->mlp_V.p), lr,
+                                 ++h->mlp_step, weight_decay, nullptr);
+        }
+        float tot = 0.f;
+        if (e == cudaSuccess) e = cudaMemcpy(&tot, h->mlp_loss.p, sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "mlp train");
+        ep_loss = nb > 0 ? tot / nb : 0.0;
+        if (epoch_loss) epoch_loss[ep] = (float)ep_loss;
+    }
+    return RE_OK;
+}
+
+int re_mlp_features(re_handle h, const void* A, int dtype, int64_t m, int64_t n, int64_t ld, double eps,
+                    uint64_t seed, float* features) {
+    if (!h || !features) return fail(RE_ERR_ARG, "NULL argument");
+    if (!(eps > 0.0 && eps < 1.0)) return fail(RE_ERR_ARG, "eps must lie in (0, 1)");
+    cudaSetDevice(h->device);
+    const int ykind = RE_GAUSSIAN;
+    Plan P;
+    if (int r = make_plan(A, dtype, m, n, ld, RE_GAUSSIAN, ykind, 16, &P)) return r;
+    if (P.cap < 16) return fail(RE_ERR_ARG, "matrix too small for the s = 16 first sketch");
+    cudaStream_t st = nullptr;
+    const int64_t M = P.A.rows;
+    if (int r = ensure(h->ax, sizeof(float) * (size_t)M * 16)) return r;
+    if (int r = ensure(h->core, sizeof(double) * 2 * 16 * 16)) return r;
+    if (int r = ensure(h->sigma, sizeof(double) * 16)) return r;
+    if (int r = ensure(h->sigma_scaled, sizeof(double) * 16)) return r;
+    if (int r = ensure(h->ro, sizeof(re::DevReadoff))) return r;
+    if (int r = ensure(h->status, 64)) return r;
+    if (int r = ensure(h->mlp_feat, sizeof(float) * re::kMlpIn)) return r;
+    cudaError_t e0 = cudaMemsetAsync(h->status.p, 0, 4 * sizeof(int), st);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "clear status");
+    float* AX = static_cast<float*>(h->ax.p);
+    if (int r = right_columns(h, P, seed, 0, 16, AX, 16, st)) return r;
+    if (int r = left_blocks(h, P, seed, 0, 16, AX, 16, static_cast<double*>(h->core.p), 16, st)) return r;
+    re::DevReadoff ro;
+    int r1 = 0;
+    if (int r = check_width(h, P, 16, 16, eps, &ro, &r1, st)) return r;
+    cudaError_t e = re::mlp_features(static_cast<const double*>(h->sigma_scaled.p), eps, P.A.rows, P.A.cols,
+                                     static_cast<float*>(h->mlp_feat.p), st);
+    if (e == cudaSuccess) e = cudaMemcpy(features, h->mlp_feat.p, sizeof(float) * re::kMlpIn, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "features");
     return RE_OK;
 }
 

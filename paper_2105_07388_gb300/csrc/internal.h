@@ -119,6 +119,20 @@ cudaError_t launch_readoff(const double* sigma, int r1, double scale, double eps
                            const int* status_in, DevReadoff* out, double* sigma_scaled,
                            cudaStream_t st);
 
+// ---- sketch-size proposal network (mlp.cu) -----------------------------------
+constexpr int kMlpIn = 18, kMlpHidden = 128, kMlpOut = 12;
+constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden +
+                           kMlpOut * kMlpHidden + kMlpOut;
+// logits (count x 12); keep (count x 256 activations) may be NULL for inference
+cudaError_t mlp_forward(const float* P, const float* X, int count, float* logits, float* keep, cudaStream_t st);
+// G += d(mean cross-entropy)/dP; *loss += mean loss
+cudaError_t mlp_backward(const float* P, const float* X, const int* y, int count, const float* logits,
+                         const float* keep, float* G, float* loss, cudaStream_t st);
+cudaError_t mlp_adam(float* P, const float* G, float* M, float* V, float lr, int step, float wd, cudaStream_t st);
+cudaError_t mlp_argmax(const float* logits, int count, int* cls, cudaStream_t st);
+cudaError_t mlp_features(const double* sigma16, double eps, int64_t rows, int64_t cols, float* f, cudaStream_t st);
+void mlp_init_host(float* P, uint64_t seed);
+
 // ---- batched estimate (batched.cu) --------------------------------------------
 struct BatchedState;
 // Level-synchronous batched Algorithm 1 (FP32 input, Gaussian X and Y); state is

@@ -30,6 +30,10 @@ RE_SRHT = 1
 RE_PREC_FP32 = 0
 RE_PREC_BF16X3 = 1
 
+RE_MLP_IN = 18
+RE_MLP_OUT = 12
+RE_MLP_PARAMS = 20492
+
 RE_CONVERGED = 1
 RE_LOWER_BOUND_ONLY = 2
 RE_TRANSPOSED = 4
@@ -104,6 +108,15 @@ _SIGS = {
                                       _I, ctypes.POINTER(re_result), _VP]),
     "re_sketch_apply_noalloc": (_I, [_VP, _I, _I64, _I64, _I64, _I, _I, _U64, _VP, _I64, _VP, _I64,
                                      _VP]),
+    "re_mlp_init": (_I, [_VP, _U64]),
+    "re_mlp_set_params": (_I, [_VP, _VP, _I]),
+    "re_mlp_get_params": (_I, [_VP, _VP, _I]),
+    "re_mlp_save": (_I, [_VP, ctypes.c_char_p]),
+    "re_mlp_load": (_I, [_VP, ctypes.c_char_p]),
+    "re_mlp_predict": (_I, [_VP, _VP, _I, _VP, _VP]),
+    "re_mlp_grad": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
+    "re_mlp_train": (_I, [_VP, _VP, _VP, _I, _I, _I, ctypes.c_float, ctypes.c_float, _U64, _VP]),
+    "re_mlp_features": (_I, [_VP, _VP, _I, _I64, _I64, _I64, _D, _U64, _VP]),
 }
 
 # Symbols declared in include/rankest.h; tests check that the library exports all of them.
@@ -290,3 +303,62 @@ def re_sketch_apply_noalloc(A, col0: int, s: int, seed: int, AX, core=None, stre
     _check(lib().re_sketch_apply_noalloc(_ptr(A), _dtype_code(A), m, n, A.stride(0), col0, s, seed,
                                          _ptr(AX), AX.stride(0), _ptr(core), ld_core,
                                          _stream(stream)))
+
+
+# ---- sketch-size proposal network ---------------------------------------------
+def re_mlp_init(h: int, seed: int = 0) -> None:
+    _check(lib().re_mlp_init(h, seed))
+
+
+def re_mlp_set_params(h: int, params) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().re_mlp_set_params(h, p.ctypes.data, p.size))
+
+
+def re_mlp_get_params(h: int) -> np.ndarray:
+    p = np.zeros(RE_MLP_PARAMS, dtype=np.float32)
+    _check(lib().re_mlp_get_params(h, p.ctypes.data, p.size))
+    return p
+
+
+def re_mlp_save(h: int, path: str) -> None:
+    _check(lib().re_mlp_save(h, path.encode()))
+
+
+def re_mlp_load(h: int, path: str) -> None:
+    _check(lib().re_mlp_load(h, path.encode()))
+
+
+def re_mlp_predict(h: int, X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n = X.shape[0]
+    cls = np.zeros(n, dtype=np.int32)
+    logits = np.zeros((n, RE_MLP_OUT), dtype=np.float32)
+    _check(lib().re_mlp_predict(h, X.ctypes.data, n, cls.ctypes.data, logits.ctypes.data))
+    return cls, logits
+
+
+def re_mlp_grad(h: int, X, y):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    g = np.zeros(RE_MLP_PARAMS, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(lib().re_mlp_grad(h, X.ctypes.data, y.ctypes.data, X.shape[0], g.ctypes.data, loss.ctypes.data))
+    return float(loss[0]), g
+
+
+def re_mlp_train(h: int, X, y, epochs: int = 10, batch: int = 256, lr: float = 1e-3,
+                 weight_decay: float = 0.0, seed: int = 0) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    losses = np.zeros(epochs, dtype=np.float32)
+    _check(lib().re_mlp_train(h, X.ctypes.data, y.ctypes.data, X.shape[0], epochs, batch, lr,
+                              weight_decay, seed, losses.ctypes.data))
+    return losses
+
+
+def re_mlp_features(h: int, A, eps: float, seed: int) -> np.ndarray:
+    m, n = A.shape
+    f = np.zeros(RE_MLP_IN, dtype=np.float32)
+    _check(lib().re_mlp_features(h, _ptr(A), _dtype_code(A), m, n, A.stride(0), eps, seed, f.ctypes.data))
+    return f
