@@ -46,9 +46,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--kind", default="gaussian", choices=["gaussian", "srht"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batched", type=int, default=1)
+    ap.add_argument("--batched-count", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -209,8 +211,8 @@ def main():
     h = rk.re_create(local, rk.make_opts(precision=prec))
     stream = torch.cuda.current_stream()
 
-    def step():
-        return rk.re_rank_estimate(h, A, w["eps"], kind_code, w["sketch_seed"], stream=stream)
+    def step(hd=h):
+        return rk.re_rank_estimate(hd, A, w["eps"], kind_code, w["sketch_seed"], stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         res, sig = step()
@@ -244,28 +246,32 @@ def main():
     hbm, bf16, src = peaks()
     clocks = clk.summary()
 
-    # roofline of the dominant stage
+    # roofline of the right sketch (the dominant stage; stage split reported too)
     stage_ms = {"right": st.right_ms, "left": st.left_ms, "svd": st.svd_ms, "other": st.other_ms}
     dominant = max(stage_ms, key=stage_ms.get)
     right_avg_ms = st.right_ms / max(st.right_launches, 1)
     right_gbs = st.right_bytes / max(st.right_launches, 1) / (right_avg_ms * 1e-3) / 1e9
     right_tflops = st.right_flops / (st.right_ms * 1e-3) / 1e12 if st.right_ms else 0.0
     sm_mhz = clocks["sm_mhz"] or 1900.0
-    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     if args.kind == "gaussian" and args.precision == "fp32":
-        alu_frac = right_tflops / fp32_peak_tflops
+        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        alu_frac = right_tflops / fp32_peak
     else:
-        alu_frac = 0.0
+        fp32_peak, alu_frac = None, 0.0
     hbm_frac = right_gbs / hbm
     if alu_frac > hbm_frac:
         roof = {"kernel": "right sketch (FP32 SIMT)", "bound": "alu", "achieved": right_tflops,
-                "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": alu_frac,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu_frac,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock under load",
                 "hbm_achieved_gbs": right_gbs, "hbm_frac": hbm_frac}
     else:
-        roof = {"kernel": "right sketch", "bound": "hbm", "achieved": right_gbs, "peak": hbm,
-                "unit": "GB/s", "frac": hbm_frac, "peak_source": f"{src} hbm_gbs"}
+        roof = {"kernel": "right sketch (" + ("BF16x3 tcgen05" if args.precision == "bf16x3" else args.kind) + ")",
+                "bound": "hbm", "achieved": right_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
+                "peak_source": f"{src} hbm_gbs",
+                "tensor_tflops_achieved": right_tflops if args.precision == "bf16x3" else None}
     roof["traffic"] = None
+    roof["algorithmic_bytes_per_launch"] = st.right_bytes / max(st.right_launches, 1)
+    roof["launches"] = int(st.right_launches)
     roof["dominant_stage"] = dominant
     roof["stage_ms_per_step"] = {k: v / args.steps for k, v in stage_ms.items()}
 
@@ -274,10 +280,45 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "hbm_frac_of_step": value / world / hbm,
-            "rank_estimates_per_s": world * 1e3 / ms,
             "result": {"rank": res.rank, "final_s": res.final_s, "passes": passes,
                        "flags": res.flags},
             "gpu_launches": int(st.launches), "roofline": roof, "clocks": clocks}
+
+    # rank estimates per second of the single-matrix forms, at identical ranks
+    forms = {}
+    K = max(1, min(args.steps, 5))
+
+    def time_form(hd, learned=False):
+        if learned:
+            rk.re_set_opts(hd, rk.make_opts(precision=rk.RE_PREC_BF16X3, learned=1))
+        r, _ = step(hd)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            r, _ = step(hd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / K
+
+    forms_ok = True
+    h32 = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_FP32))
+    r32, ms32 = time_form(h32)
+    rk.re_destroy(h32)
+    forms["plain_fp32"] = {"estimates_per_s": 1e3 / ms32, "ms": ms32, "rank": r32.rank, "passes": r32.passes}
+    forms["bf16x3"] = {"estimates_per_s": 1e3 / ms, "ms": ms, "rank": res.rank, "passes": passes}
+    weights = os.path.join(ROOT, "paper_2105_07388_gb300", "proposal.remlp")
+    if os.path.exists(weights) and args.kind == "gaussian":
+        hl = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_BF16X3))
+        rk.re_mlp_load(hl, weights)
+        rl, msl = time_form(hl, learned=True)
+        rk.re_destroy(hl)
+        forms["learned_bf16x3"] = {"estimates_per_s": 1e3 / msl, "ms": msl, "rank": rl.rank, "passes": rl.passes}
+    forms_ok = len({f["rank"] for f in forms.values()}) == 1
+    line["rank_estimates_per_s"] = {k: v["estimates_per_s"] for k, v in forms.items()}
+    line["forms"] = forms
+    line["forms_identical_ranks"] = forms_ok
 
     if not args.no_e2e:
         Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
@@ -296,6 +337,9 @@ def main():
                        "d2h_bytes_per_step": int(r2.passes * 40 + 8 * r2.n_sigma)}
         del Ah
 
+    if args.batched and world == 1:
+        line["batched"] = bench_batched(rk, local, stream, args)
+
     if rank == 0 and world == 1 and not args.no_cpu:
         A_host = A.cpu().numpy()
         v, info = cpu_oracle_run(A_host, w, kind_code, budget_s=20.0)
@@ -309,6 +353,58 @@ def main():
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_batched(rk, local, stream, args):
+    """4096 off-diagonal kernel blocks K_ij = 1/|x_i - y_j| (sizes uniform in
+    [256, 4096]), eps = 1e-6: one captured-graph batched estimate per step, and
+    the plain per-matrix FP32 form (one re_rank_estimate per block) on a sample."""
+    import torch
+    from paper_2105_07388_gb300 import workloads as wl
+    count = args.batched_count
+    shapes = wl.kernel_block_sizes(count, seed=7)
+    blocks = [wl.kernel_block(m, n, seed=10_000 + i, device="cuda") for i, (m, n) in enumerate(shapes)]
+    torch.cuda.synchronize()
+    total_bytes = 4.0 * sum(m * n for m, n in shapes)
+    hb = rk.re_create(local, rk.make_opts(s_max=128))
+    rk.re_stats_enable(hb, False)
+    res, _ = rk.re_rank_estimate_batched(hb, blocks, 1e-6, rk.RE_GAUSSIAN, 500, stream=stream)   # autotune + capture
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        res, _ = rk.re_rank_estimate_batched(hb, blocks, 1e-6, rk.RE_GAUSSIAN, 500, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    passes = sum(r.passes for r in res)
+    read_bytes = sum(4.0 * shapes[i][0] * shapes[i][1] * res[i].passes for i in range(count))
+    # plain per-matrix form on a sample of blocks, same seeds and widths
+    sample = list(range(0, count, max(1, count // 128)))
+    hp = rk.re_create(local, rk.make_opts(s_max=128))
+    same = 0
+    rk.re_rank_estimate(hp, blocks[sample[0]], 1e-6, rk.RE_GAUSSIAN, 500 + sample[0], stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in sample:
+        r, _ = rk.re_rank_estimate(hp, blocks[i], 1e-6, rk.RE_GAUSSIAN, 500 + i, stream=stream)
+        same += int(r.rank == res[i].rank)
+    torch.cuda.synchronize()
+    plain_ms_each = (time.perf_counter() - t0) * 1e3 / len(sample)
+    rk.re_destroy(hp)
+    rk.re_destroy(hb)
+    del blocks
+    torch.cuda.empty_cache()
+    return {"workload": f"{count} kernel blocks 1/|x-y|, m,n ~ U[256,4096], eps=1e-6, Gaussian, s<=128",
+            "blocks_bytes": total_bytes, "ms_per_batch": ms,
+            "rank_estimates_per_s": count * 1e3 / ms,
+            "sketch_gbs": read_bytes / (ms * 1e-3) / 1e9,
+            "mean_passes": passes / count,
+            "plain_per_matrix_estimates_per_s": 1e3 / plain_ms_each,
+            "plain_sample": len(sample), "plain_same_rank_fraction": same / len(sample),
+            "speedup_vs_plain": (count * 1e3 / ms) / (1e3 / plain_ms_each)}
 
 
 if __name__ == "__main__":

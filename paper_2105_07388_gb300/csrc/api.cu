@@ -206,6 +206,12 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
                   int64_t ld_ax, cudaStream_t st) {
     cudaError_t e;
     if (P.kind == RE_GAUSSIAN) {
+        if (h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && cnt > 256) {
+            // the tensor-core kernel takes at most 256 columns (one MMA N) per pass
+            for (int c = 0; c < cnt; c += 256)
+                if (int r = right_columns(h, P, seed, c0 + c, std::min(256, cnt - c), AX, ld_ax, st)) return r;
+            return RE_OK;
+        }
         if (h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && cnt <= 256) {
             const int64_t kpad = (P.A.cols + 63) / 64 * 64;
             const int nrows = re::tc_mma_n(cnt);
@@ -302,12 +308,21 @@ int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const
 // Singular values and read-off of the leading 2s x s block of the core (the
 // core at width s, by the nested-prefix property of the appended embeddings).
 int check_width(re_handle h, const Plan& P, int s, int smax, double eps, re::DevReadoff* ro, int* r1_out,
-                cudaStream_t st) {
+                cudaStream_t st, bool may_skip = false) {
     double* core = static_cast<double*>(h->core.p);
     int* status = static_cast<int*>(h->status.p);
+    const int r1c = std::min(r1_of_s(s), s);
+    // at widths that are not the last, a certified "not converged" skips the
+    // Jacobi sweeps; the margin 4 max(eps, 1e-5) keeps the decision clear of the
+    // FP32 sweeps' absolute error (about 3e-5 sigma_1), and ||A|| from opts is
+    // not used there (the certificate compares with sigma_1 of the core)
+    const bool skip_ok = may_skip && h->opts.norm_a <= 0.0 && r1c < P.A.cols;
+    const float ratio = (float)(4.0 * std::max(eps, 1e-5));
+    cudaError_t e = cudaMemsetAsync(status + 3, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
     cudaEvent_t a = stage_begin(h, st);
-    cudaError_t e = re::launch_core_sigma(core, 2 * s, s, smax, h->svdws.p, static_cast<double*>(h->sigma.p),
-                                          status, st);
+    e = re::launch_core_sigma(core, 2 * s, s, smax, h->svdws.p, static_cast<double*>(h->sigma.p), status, st,
+                              skip_ok ? r1c : 0, ratio);
     if (e != cudaSuccess) return cuda_fail(e, "core singular values");
     stage_end(h, st, a, kStageSvd);
     const int r1 = std::min(r1_of_s(s), s);
@@ -386,7 +401,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
         if (int r = sketch_to(0, 16)) return r;
         passes = 1;
         for (int w = 8; w <= 16 && !done; w *= 2) {
-            if (int r = check_width(h, P, w, smax, eps, &ro, &r1, st)) return r;
+            if (int r = check_width(h, P, w, smax, eps, &ro, &r1, st, 2 * w <= smax)) return r;
             s = w;
             done = ro.rank >= 0 || r1 >= P.A.cols;
         }
@@ -394,24 +409,31 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
             int cls = 0;
             if (int r = propose_width(h, P, eps, &cls, st)) return r;
             const int target = std::min(smax, std::max(32, 8 << std::min(std::max(cls, 0), 11)));
-            if (int r = sketch_to(16, target)) return r;
+            // one pass appends the right sketch up to the proposed width; the core
+            // is extended one ladder width at a time, only as far as the checks go
+            if (int r = right_columns(h, P, seed, 16, target - 16, AX, smax, st)) return r;
+            h->stats.passes += 1;
             passes = 2;
             for (int w = 32; w <= target && !done; w *= 2) {
-                if (int r = check_width(h, P, w, smax, eps, &ro, &r1, st)) return r;
+                if (int r = left_blocks(h, P, seed, w / 2, w, AX, smax, core, smax, st)) return r;
+                if (int r = check_width(h, P, w, smax, eps, &ro, &r1, st, 2 * w <= smax)) return r;
                 s = w;
                 done = ro.rank >= 0 || r1 >= P.A.cols;
             }
         }
         if (!done) {
-            if (2 * s > smax) done = true;
-            s_prev = s;
-            s *= 2;
+            if (2 * s > smax) {
+                done = true;          // ladder exhausted at s: r1(s) is a lower bound
+            } else {
+                s_prev = s;
+                s *= 2;
+            }
         }
     }
     while (!done) {
         if (int r = sketch_to(s_prev, s)) return r;
         ++passes;
-        if (int r = check_width(h, P, s, smax, eps, &ro, &r1, st)) return r;
+        if (int r = check_width(h, P, s, smax, eps, &ro, &r1, st, 2 * s <= smax)) return r;
         if (ro.rank >= 0 || 2 * s > smax || r1 >= P.A.cols) break;
         s_prev = s;
         s *= 2;

@@ -37,7 +37,8 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kSvdThreads = 512;
+constexpr int kSvdThreads = 512;      // cluster kernel
+constexpr int kCtaThreads = 1024;     // one-CTA kernel: 64 column pairs x 16 lanes
 constexpr int kMaxSweeps = 40;
 constexpr float kU = 5.9604644775390625e-08f;        // 2^-24
 constexpr float kAbsFloor = 1e-14f;                  // (1e-7)^2 of max column norm^2
@@ -73,16 +74,22 @@ template <int G>
 __device__ __forceinline__ int rotate_pair(bool active, float* a, float* b, int n, float tol,
                                            float floor_abs, float* meas) {
     const int gl = threadIdx.x & (G - 1);
-    float al = 0.f, be = 0.f, ga = 0.f;
+    float al = 0.f, be = 0.f, ga = 0.f, al2 = 0.f, be2 = 0.f, ga2 = 0.f;
     if (active) {
         for (int i = 4 * gl; i < n; i += 4 * G) {
             const float4 x = *reinterpret_cast<const float4*>(a + i);
             const float4 y = *reinterpret_cast<const float4*>(b + i);
-            al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
-            be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
-            ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
+            al = fmaf(x.x, x.x, fmaf(x.y, x.y, al));
+            al2 = fmaf(x.z, x.z, fmaf(x.w, x.w, al2));
+            be = fmaf(y.x, y.x, fmaf(y.y, y.y, be));
+            be2 = fmaf(y.z, y.z, fmaf(y.w, y.w, be2));
+            ga = fmaf(x.x, y.x, fmaf(x.y, y.y, ga));
+            ga2 = fmaf(x.z, y.z, fmaf(x.w, y.w, ga2));
         }
     }
+    al += al2;
+    be += be2;
+    ga += ga2;
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
         al += __shfl_xor_sync(0xffffffffu, al, o);
@@ -181,15 +188,15 @@ __device__ __forceinline__ float householder(float* x, int L) {
 // One CTA per core: core -> shared memory (column-major, scaled), QR in place,
 // R^T -> second region, Jacobi on R^T, norms.  blockIdx.x selects the core
 // (core_stride / sigma_stride apart) so one launch serves a batch.
-__global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
+__global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     const double* __restrict__ core, int r2, int s, int64_t ld, int64_t core_stride,
     double* __restrict__ sigma, int64_t sigma_stride, int* __restrict__ status,
-    const int* __restrict__ active) {
+    const int* __restrict__ active, int cert_r1, float cert_ratio) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (active && !active[blockIdx.x]) return;
     core += (int64_t)blockIdx.x * core_stride;
     sigma += (int64_t)blockIdx.x * sigma_stride;
-    const int sp = (s + 31) / 32 * 32;                  // padded column length of R^T
+    const int sp = (s + 63) / 64 * 64;                  // padded column length of R^T (4 x 16 lanes)
     float* W = reinterpret_cast<float*>(smem);          // r2 x s, column-major
     float* Rt = W + ((size_t)r2 * s + 31) / 32 * 32;    // sp x s, column c = row c of R (128-B aligned)
     __shared__ double s_norm[512];
@@ -251,6 +258,67 @@ __global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
         }
         __syncthreads();
     }
+    // Certificate of non-convergence (used at intermediate ladder widths only):
+    // sigma_r1(core) >= sigma_min(R11) >= 1 / ||R11^{-1}||_F (column interlacing)
+    // and sigma_1(core) <= ||R||_F; when the lower bound exceeds cert_ratio times
+    // the upper bound, the read-off cannot succeed at this width and the Jacobi
+    // sweeps are skipped (status[3] = 1; sigma is not written).
+    if (cert_r1 > 0 && cert_r1 <= s) {
+        __shared__ float s_fro, s_inv;
+        __shared__ int s_zero;
+        if (tid == 0) {
+            s_fro = 0.f;
+            s_inv = 0.f;
+            s_zero = 0;
+        }
+        __syncthreads();
+        float fro = 0.f;
+        for (int64_t idx = tid; idx < (int64_t)s * s; idx += blockDim.x) {
+            const int j = (int)(idx / s), i = (int)(idx % s);
+            if (i <= j) {
+                const float v = W[(size_t)j * r2 + i];
+                fro = fmaf(v, v, fro);
+            }
+        }
+        fro = warp_sum(fro);
+        if (lane == 0) atomicAdd(&s_fro, fro);
+        // columns of R11^{-1} by back substitution, one warp per column
+        float* x = Rt + (size_t)warp * sp;             // Rt is free until the transpose below
+        float inv = 0.f;
+        for (int j = warp; j < cert_r1; j += nwarps) {
+            const float rjj = W[(size_t)j * r2 + j];
+            if (rjj == 0.f) {
+                if (lane == 0) s_zero = 1;
+                continue;
+            }
+            if (lane == 0) x[j] = 1.f / rjj;
+            __syncwarp();
+            float acc = lane == 0 ? x[j] * x[j] : 0.f;
+            for (int i = j - 1; i >= 0; --i) {
+                float t = 0.f;
+                for (int k = i + 1 + lane; k <= j; k += 32) t = fmaf(W[(size_t)k * r2 + i], x[k], t);
+                t = warp_sum(t);
+                const float rii = W[(size_t)i * r2 + i];
+                const float xi = rii != 0.f ? -t / rii : INFINITY;
+                if (lane == 0) {
+                    x[i] = xi;
+                    acc = fmaf(xi, xi, acc);
+                }
+                __syncwarp();
+            }
+            inv += acc;
+        }
+        if (lane == 0) atomicAdd(&s_inv, inv);
+        __syncthreads();
+        const bool certified = s_zero == 0 && isfinite(s_inv) && s_inv > 0.f &&
+                               1.f / sqrtf(s_inv) > cert_ratio * sqrtf(s_fro);
+        __syncthreads();
+        if (certified) {
+            if (tid == 0 && sigma_stride == 0) status[3] = 1;
+            if (tid == 0) status[blockIdx.x] = RE_OK;
+            return;
+        }
+    }
     // R^T: column c of Rt = row c of R = W[j][c] for j >= c
     for (int64_t idx = tid; idx < (int64_t)s * sp; idx += blockDim.x) {
         const int c = (int)(idx / sp), j = (int)(idx % sp);
@@ -280,7 +348,7 @@ __global__ void __launch_bounds__(kSvdThreads) core_sigma_cta_kernel(
         }
         __syncthreads();
         const float floor_abs = kAbsFloor * s_red[0];
-        constexpr int G = 8;
+        constexpr int G = 16;
         const int grp = tid / G, ngrp = blockDim.x / G;
         for (int t = 0; t < P - 1; ++t) {
             for (int base = 0; base < P / 2; base += ngrp) {
@@ -631,6 +699,16 @@ __global__ void readoff_kernel(const double* __restrict__ sigma, int r1, double 
     // by the tensor-core right sketch when one of its bounded waits expired
     r.status = status_in ? status_in[0] : RE_OK;
     if (status_in && status_in[1]) r.status = RE_ERR_TIMEOUT;
+    if (status_in && status_in[3]) {
+        // the core step certified that no trusted sigma^ reaches the threshold
+        r.sweeps = 0;
+        r.rank = -1;
+        r.gap_index = 0;
+        r.gap_ratio = 0.0;
+        r.tau = 0.0;
+        *out = r;
+        return;
+    }
     r.sweeps = status_in ? status_in[2] : 0;
     for (int i = 0; i < r1; ++i) sigma_scaled[i] = sigma[i] * scale;
     const double ref = norm_a > 0.0 ? norm_a : sigma_scaled[0];
@@ -663,7 +741,7 @@ __global__ void readoff_kernel(const double* __restrict__ sigma, int r1, double 
 constexpr size_t kSmemLimit = 210 * 1024;
 
 size_t cta_smem(int r2, int s) {
-    const size_t sp = (size_t)(s + 31) / 32 * 32;
+    const size_t sp = (size_t)(s + 63) / 64 * 64;
     return sizeof(float) * (((size_t)r2 * s + 31) / 32 * 32 + sp * s);
 }
 
@@ -676,23 +754,24 @@ bool core_sigma_fits_cta(int r2, int s) { return cta_smem(r2, s) <= kSmemLimit; 
 cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t ld,
                                       int64_t core_stride, int count, double* sigma,
                                       int64_t sigma_stride, int* status, cudaStream_t st,
-                                      const int* active) {
+                                      const int* active, int cert_r1, float cert_ratio) {
     const size_t sm = cta_smem(r2, s);
     if (sm > kSmemLimit || count <= 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(core_sigma_cta_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    core_sigma_cta_kernel<<<count, kSvdThreads, sm, st>>>(core, r2, s, ld, core_stride, sigma,
-                                                          sigma_stride, status, active);
+    core_sigma_cta_kernel<<<count, kCtaThreads, sm, st>>>(core, r2, s, ld, core_stride, sigma,
+                                                          sigma_stride, status, active, cert_r1, cert_ratio);
     return cudaGetLastError();
 }
 
 cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void*, double* sigma,
-                              int* status, cudaStream_t st) {
+                              int* status, cudaStream_t st, int cert_r1, float cert_ratio) {
     if (s <= 0) return cudaSuccess;
     if (s > 512) return cudaErrorInvalidValue;
     if (cta_smem(r2, s) <= kSmemLimit)
-        return launch_core_sigma_batched(core, r2, s, ld, 0, 1, sigma, 0, status, st);
+        return launch_core_sigma_batched(core, r2, s, ld, 0, 1, sigma, 0, status, st, nullptr, cert_r1,
+                                         cert_ratio);
     int b = 0;
     if (cluster_smem(8, r2, s, &b) <= kSmemLimit) return launch_cluster_sigma<8>(core, r2, s, ld, sigma, status, st);
     if (cluster_smem(16, r2, s, &b) <= kSmemLimit) return launch_cluster_sigma<16>(core, r2, s, ld, sigma, status, st);

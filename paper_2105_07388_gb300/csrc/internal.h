@@ -96,15 +96,19 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
 size_t svd_workspace_bytes(int r2, int s);
 // sigma (FP64, s entries, descending, unscaled) of core (FP64 row-major r2 x s, ld).
 // status (device int): 0 ok, RE_ERR_NONFINITE if core has NaN/Inf.
+// With cert_r1 > 0 the one-CTA path first tries to certify that sigma_{cert_r1}
+// exceeds cert_ratio * sigma_1 (then status[3] = 1 and sigma is left unwritten).
 cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws,
-                              double* sigma, int* status, cudaStream_t st);
+                              double* sigma, int* status, cudaStream_t st, int cert_r1 = 0,
+                              float cert_ratio = 0.f);
 // `count` cores core + i*core_stride (each r2 x s, ld) -> sigma + i*sigma_stride,
 // status[i]; one CTA each (requires core_sigma_fits_cta).
 bool core_sigma_fits_cta(int r2, int s);
 cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t ld,
                                       int64_t core_stride, int count, double* sigma,
                                       int64_t sigma_stride, int* status, cudaStream_t st,
-                                      const int* active = nullptr);
+                                      const int* active = nullptr, int cert_r1 = 0,
+                                      float cert_ratio = 0.f);
 
 // Device read-off (step 8).  Writes DevReadoff to `out`.
 struct DevReadoff {

@@ -108,12 +108,12 @@ struct XTile {
     float v[PER];
 
     __device__ __forceinline__ void load(const float* __restrict__ X, int64_t ldx, int64_t N,
-                                         int64_t k0, int n0) {
+                                         int64_t k0, int n0, int ncols) {
         const int t = threadIdx.x;
         const int64_t k = k0 + (t >> 3);
         const int c = n0 + (t & 7) * PER;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) v[q] = (k < N) ? __ldg(X + k * ldx + c + q) : 0.0f;
+        for (int q = 0; q < PER; ++q) v[q] = (k < N && c + q < ncols) ? __ldg(X + k * ldx + c + q) : 0.0f;
     }
 
     __device__ __forceinline__ void store(float* Bs) const {
@@ -131,7 +131,7 @@ template <int BN, bool TRANS, typename TA, int BM>
 __device__ __forceinline__ void simt_tile(const TA* __restrict__ A, int64_t lda, int64_t M, int64_t N,
                                           const float* __restrict__ X, int64_t ldx,
                                           float* __restrict__ C, int64_t ldc, int64_t m0, int n0,
-                                          bool vec, float* smem) {
+                                          bool vec, float* smem, int ncols) {
     using S = SimtShape<BN>;
     constexpr int TN = S::TN;
     constexpr int TX = BN / TN;
@@ -153,7 +153,7 @@ __device__ __forceinline__ void simt_tile(const TA* __restrict__ A, int64_t lda,
     XTile<BN> xt;
     const int64_t KT = (N + kBK - 1) / kBK;
     at.load(A, lda, M, N, m0, 0, vec);
-    xt.load(X, ldx, N, 0, n0);
+    xt.load(X, ldx, N, 0, n0, ncols);
     at.store(As);
     xt.store(Bs);
     __syncthreads();
@@ -163,7 +163,7 @@ __device__ __forceinline__ void simt_tile(const TA* __restrict__ A, int64_t lda,
         const bool more = kt + 1 < KT;
         if (more) {
             at.load(A, lda, M, N, m0, (kt + 1) * kBK, vec);
-            xt.load(X, ldx, N, (kt + 1) * kBK, n0);
+            xt.load(X, ldx, N, (kt + 1) * kBK, n0, ncols);
         }
         const float* as = As + buf * kBK * (BM + 4);
         const float* bs = Bs + buf * kBK * BN;
@@ -210,7 +210,8 @@ __device__ __forceinline__ void simt_tile(const TA* __restrict__ A, int64_t lda,
         if (r >= M) continue;
         float* cp = C + r * ldc + n0 + tx * TN;
 #pragma unroll
-        for (int j = 0; j < TN; ++j) cp[j] = acc[i][j];
+        for (int j = 0; j < TN; ++j)
+            if (n0 + tx * TN + j < ncols) cp[j] = acc[i][j];
     }
 }
 
@@ -219,10 +220,10 @@ __global__ void __launch_bounds__(kThreads) right_simt_kernel(const TA* __restri
                                                               int64_t M, int64_t N,
                                                               const float* __restrict__ X,
                                                               int64_t ldx, float* __restrict__ C,
-                                                              int64_t ldc, int vec) {
+                                                              int64_t ldc, int vec, int ncols) {
     extern __shared__ float4 smem_raw[];
     simt_tile<BN, TRANS, TA, kBM>(A, lda, M, N, X, ldx, C, ldc, (int64_t)blockIdx.y * kBM,
-                                  (int)blockIdx.x * BN, vec != 0, reinterpret_cast<float*>(smem_raw));
+                                  (int)blockIdx.x * BN, vec != 0, reinterpret_cast<float*>(smem_raw), ncols);
 }
 
 // Batched: one CTA per (block, BM-row tile) work item.
@@ -252,9 +253,9 @@ __global__ void __launch_bounds__(kThreads) right_simt_batched_kernel(
     float* C = AXpool + D.ax_off + col0;
     float* sm = reinterpret_cast<float*>(smem_raw);
     if (D.trans)
-        simt_tile<BN, true, float, BM>(D.A, D.ld, D.rows, D.cols, X, s, C, ldax, m0, 0, vec, sm);
+        simt_tile<BN, true, float, BM>(D.A, D.ld, D.rows, D.cols, X, s, C, ldax, m0, 0, vec, sm, s);
     else
-        simt_tile<BN, false, float, BM>(D.A, D.ld, D.rows, D.cols, X, s, C, ldax, m0, 0, vec, sm);
+        simt_tile<BN, false, float, BM>(D.A, D.ld, D.rows, D.cols, X, s, C, ldax, m0, 0, vec, sm, s);
 }
 
 template <int BN, int BM>
@@ -291,9 +292,9 @@ cudaError_t launch_right_simt_t(const MatView& A, const float* X, int64_t ldx, i
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int vec = ((reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0 && (A.ld & 3) == 0) ? 1 : 0;
-    dim3 grid((unsigned)(s / BN), (unsigned)((A.rows + kBM - 1) / kBM));
+    dim3 grid((unsigned)((s + BN - 1) / BN), (unsigned)((A.rows + kBM - 1) / kBM));
     kern<<<grid, kThreads, smem, st>>>(static_cast<const TA*>(A.ptr), A.ld, A.rows, A.cols, X, ldx,
-                                        C, ldc, vec);
+                                        C, ldc, vec, s);
     return cudaGetLastError();
 }
 
@@ -446,10 +447,13 @@ cudaError_t launch_right_simt(const MatView& A, const float* X, int64_t ldx, int
                               int64_t ldc, cudaStream_t st) {
     if (s <= 0 || A.rows <= 0) return cudaSuccess;
     if ((A.rows + kBM - 1) / kBM > 65535) return cudaErrorInvalidConfiguration;
-    if (s % 128 == 0) return dispatch_right<128>(A, X, ldx, s, C, ldc, st);
-    if (s % 64 == 0) return dispatch_right<64>(A, X, ldx, s, C, ldc, st);
-    if (s % 32 == 0) return dispatch_right<32>(A, X, ldx, s, C, ldc, st);
-    if (s % 16 == 0) return dispatch_right<16>(A, X, ldx, s, C, ldc, st);
+    // one launch for any width: 128-wide column tiles (the last one masked) from
+    // 128 columns up, otherwise the narrowest tile that covers all columns; the
+    // column tiles of a row block run back to back, so A streams from HBM once
+    if (s >= 128 || s > 64) return dispatch_right<128>(A, X, ldx, s, C, ldc, st);
+    if (s > 32) return dispatch_right<64>(A, X, ldx, s, C, ldc, st);
+    if (s > 16) return dispatch_right<32>(A, X, ldx, s, C, ldc, st);
+    if (s > 8) return dispatch_right<16>(A, X, ldx, s, C, ldc, st);
     return dispatch_right<8>(A, X, ldx, s, C, ldc, st);
 }
 
