@@ -10,19 +10,24 @@
 //
 // Persistent kernel, one CTA per SM, 128-row M tiles, K chunks of 64:
 //   warp 12     TMA producer of A: FP32 half chunks (128 rows x 32 k, 128B
-//               swizzle, zero fill past the edges) into a 3-4 deep ring, so
-//               48-64 KB of A are in flight per SM.
+//               swizzle, zero fill past the edges) into an 8 deep ring, so up
+//               to 128 KB of A are in flight per SM.
 //   warp 13     TMA producer of X^T: BF16 chunk (N rows x 64 k, 128B swizzle).
-//   warps 0-7   converters: read two FP32 half chunks from shared memory, split
-//               exactly into three BF16 tiles written in the 128B-swizzled
-//               K-major layout of the MMA descriptors; fence.proxy.async, arrive.
+//   warps 0-7   converters: warp (q, h) reads, for row 32q + lane, the 32 FP32
+//               values of half h of a chunk (conflict-free 16-byte loads of the
+//               swizzled tile), splits them exactly into three BF16 terms and
+//               writes them to TMEM (tcgen05.st, lanes 32q..32q+31), where the
+//               MMA takes them as its A operand.  The split terms never touch
+//               shared memory, which then carries only the TMA writes, the
+//               converter reads and the MMA's reads of X^T.
 //   warp 14     TMEM allocation; one elected thread issues 3 x 4 tcgen05.mma
-//               (M=128, N, K=16, kind::f16 BF16 -> FP32) per chunk and
-//               tcgen05.commit to release stages / publish accumulators.
+//               (M=128, N, K=16, kind::f16 BF16 -> FP32, A from TMEM) per chunk
+//               and tcgen05.commit to release stages / publish accumulators.
 //   warps 8-11  epilogue: tcgen05.ld (32 lanes x 16 columns) -> FP32 rows of AX.
-// The accumulator is double buffered in TMEM (2N columns) so the epilogue of one
-// tile overlaps the MMAs of the next.  Every mbarrier wait is bounded in time:
-// on expiry the kernel raises an error flag, every role drains what it has in
+// TMEM (512 columns): accumulators in [0, 256) -- double buffered for N <= 128
+// so the epilogue of one tile overlaps the MMAs of the next -- and two A stages
+// of 96 columns from column 256.  Every mbarrier wait is bounded in time: on
+// expiry the kernel raises an error flag, every role drains what it has in
 // flight (bounded again), TMEM is freed and the kernel returns.
 #include <cuda.h>
 
@@ -44,9 +49,15 @@ constexpr int kThreads = (kConvWarps + kEpiWarps + 3) * 32;   // 480
 constexpr int kAProdWarp = kConvWarps + kEpiWarps;             // 12
 constexpr int kBProdWarp = kAProdWarp + 1;                     // 13
 constexpr int kMmaWarp = kBProdWarp + 1;                       // 14
-constexpr uint32_t kTermBytes = kBM * kBK * 2;                 // 16 KB per BF16 term tile
+constexpr int kHalfWarps = kConvWarps / 2;                     // converter warps per half chunk
 constexpr uint32_t kHalfBytes = kBM * 32 * 4;                  // 16 KB FP32 half chunk
-constexpr int kSplitStages = 2;
+constexpr int kMaxAStages = 8;                                 // FP32 half-chunk ring depth
+constexpr int kStages = 2;                                     // TMEM A stages = X^T stages
+// TMEM columns: accumulators at [0, 256) (two N <= 128 buffers, or one N = 256),
+// then kStages A stages of 3 terms x 32 columns (64 k of BF16 pairs)
+constexpr uint32_t kAStageCol = 256;
+constexpr uint32_t kTmemCols = 512;
+static_assert(kAStageCol + 96 * kStages <= kTmemCols, "TMEM budget");
 constexpr unsigned long long kWaitNs = 2000000000ull;          // 2 s bound per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -136,12 +147,22 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (TMEM) += A (TMEM, 128 lanes x 8 columns of BF16 pairs) * B (shared memory descriptor)
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
     asm volatile(
         "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p; }" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
         : "memory");
 }
 
@@ -201,26 +222,27 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
                                                                const __grid_constant__ CUtensorMap xmap,
                                                                const TcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t a_full[4], a_empty[4];
-    __shared__ __align__(8) uint64_t full_a[kSplitStages], full_b[kSplitStages], empty[kSplitStages];
+    __shared__ __align__(8) uint64_t a_full[kMaxAStages], a_empty[kMaxAStages];
+    __shared__ __align__(8) uint64_t full_a[kStages], full_b[kStages], empty[kStages];
     __shared__ __align__(8) uint64_t accf[2], acce[2], done_bar;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NA = p.astages;
+    const int nacc = p.N <= 128 ? 2 : 1;            // accumulator buffers in TMEM
     const uint32_t b_bytes = (uint32_t)p.N * kBK * 2;
-    const uint32_t stage_bytes = 3 * kTermBytes + ((b_bytes + 1023u) & ~1023u);
+    const uint32_t b_stage = (b_bytes + 1023u) & ~1023u;
     unsigned char* abuf = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    unsigned char* sbuf = abuf + (size_t)NA * kHalfBytes;
+    unsigned char* bbuf = abuf + (size_t)NA * kHalfBytes;
 
     if (tid == 0) {
         for (int i = 0; i < NA; ++i) {
             mbar_init(&a_full[i], 1);
-            mbar_init(&a_empty[i], kConvWarps * 32);
+            mbar_init(&a_empty[i], kHalfWarps * 32);
         }
-        for (int i = 0; i < kSplitStages; ++i) {
+        for (int i = 0; i < kStages; ++i) {
             mbar_init(&full_a[i], kConvWarps * 32);
             mbar_init(&full_b[i], 1);
             mbar_init(&empty[i], 1);
@@ -234,11 +256,10 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
-    const uint32_t tmem_cols = (uint32_t)std::max(32, 1 << (32 - __clz(2 * p.N - 1)));
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_tmem)),
-                     "r"(tmem_cols)
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -252,43 +273,42 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     const int64_t total_chunks = my_tiles * p.kchunks;
 
     if (warp < kConvWarps) {
-        // ---------------- converters: FP32 half chunks -> three BF16 tiles
+        // ---------------- converters: warp (q, h) owns TMEM lanes 32q.. (rows 32q + lane)
+        // and half h of every chunk; one FP32 row segment of 32 k per thread.
+        const int q = warp & 3, h = warp >> 2;
+        const int r = 32 * q + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         for (int64_t g = 0; g < total_chunks; ++g) {
-            const int s = (int)(g % kSplitStages);
-            if (!mbar_wait(&empty[s], (uint32_t)((g / kSplitStages) & 1) ^ 1u, &s_abort, p.err)) break;
-            unsigned char* st = sbuf + (size_t)s * stage_bytes;
-            bool ok = true;
-            for (int h = 0; h < 2; ++h) {
-                const int64_t hg = 2 * g + h;
-                const int as = (int)(hg % NA);
-                if (!mbar_wait(&a_full[as], (uint32_t)((hg / NA) & 1), &s_abort, p.err)) {
-                    ok = false;
-                    break;
-                }
-                const unsigned char* src = abuf + (size_t)as * kHalfBytes;
+            const int s = (int)(g % kStages);
+            // the warp leaves together (tcgen05.st is a warp-wide instruction)
+            bool ok = mbar_wait(&empty[s], (uint32_t)((g / kStages) & 1) ^ 1u, &s_abort, p.err);
+            const int64_t hg = 2 * g + h;
+            const int as = (int)(hg % NA);
+            if (ok) ok = mbar_wait(&a_full[as], (uint32_t)((hg / NA) & 1), &s_abort, p.err);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            // row r of the 128B-swizzled half tile: 16-byte chunk c sits at slot c ^ (r & 7);
+            // the 32 rows of a warp cover every bank four times per load (no conflicts)
+            const unsigned char* src = abuf + (size_t)as * kHalfBytes + (size_t)r * 128;
+            float4 v[8];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    // rows {0,1,4,5} or {2,3,6,7} of an 8-row atom per instruction: the
-                    // swizzled 8-byte stores of the four rows fall in two bank halves
-                    const int gg = warp + 8 * j;
-                    const int sel = lane >> 3, c4 = lane & 7;
-                    const int roff = (sel & 1) * 4 + (sel >> 1);
-                    const int r = 8 * (gg >> 1) + 2 * (gg & 1) + roff;
-                    const float4 v = *reinterpret_cast<const float4*>(src + r * 128 + ((c4 ^ (r & 7)) << 4));
-                    const int chunk16 = 4 * h + (c4 >> 1);
-                    const uint32_t off = (uint32_t)r * 128u + ((uint32_t)(chunk16 ^ (r & 7)) << 4) +
-                                         (uint32_t)(c4 & 1) * 8u;
-                    uint32_t h0, m0, l0, h1, m1, l1;
-                    split3(v.x, v.y, h0, m0, l0);
-                    split3(v.z, v.w, h1, m1, l1);
-                    *reinterpret_cast<uint2*>(st + off) = make_uint2(h0, h1);
-                    *reinterpret_cast<uint2*>(st + kTermBytes + off) = make_uint2(m0, m1);
-                    *reinterpret_cast<uint2*>(st + 2 * kTermBytes + off) = make_uint2(l0, l1);
-                }
-                mbar_arrive(&a_empty[as]);
+            for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const float4*>(src + ((c ^ (r & 7)) << 4));
+            mbar_arrive(&a_empty[as]);
+            uint32_t hi[16], mid[16], lo[16];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                split3(v[c].x, v[c].y, hi[2 * c], mid[2 * c], lo[2 * c]);
+                split3(v[c].z, v[c].w, hi[2 * c + 1], mid[2 * c + 1], lo[2 * c + 1]);
             }
-            if (!ok) break;
-            fence_proxy_async();
+            tc_fence_after();
+            // A operand layout in TMEM (M = 128): lane = row, 32-bit column = two
+            // consecutive k (lower k in the low half); term t of stage s starts at
+            // column kAStageCol + 96 s + 32 t, half h at +16 h
+            const uint32_t col = kAStageCol + 96u * (uint32_t)s + 16u * (uint32_t)h;
+            tmem_st16(lane_base + col, hi);
+            tmem_st16(lane_base + col + 32u, mid);
+            tmem_st16(lane_base + col + 64u, lo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
             mbar_arrive(&full_a[s]);
         }
     } else if (warp == kAProdWarp) {
@@ -314,45 +334,44 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
         if (lane == 0) {
             int64_t issued = 0;
             for (int64_t g = 0; g < total_chunks; ++g) {
-                const int s = (int)(g % kSplitStages);
-                if (!mbar_wait(&empty[s], (uint32_t)((g / kSplitStages) & 1) ^ 1u, &s_abort, p.err)) break;
+                const int s = (int)(g % kStages);
+                if (!mbar_wait(&empty[s], (uint32_t)((g / kStages) & 1) ^ 1u, &s_abort, p.err)) break;
                 mbar_arrive_expect_tx(&full_b[s], b_bytes);
-                tma_load_2d(sbuf + (size_t)s * stage_bytes + 3 * kTermBytes, &xmap, (int)((g % p.kchunks) * kBK), 0,
-                            &full_b[s]);
+                tma_load_2d(bbuf + (size_t)s * b_stage, &xmap, (int)((g % p.kchunks) * kBK), 0, &full_b[s]);
                 ++issued;
             }
-            for (int64_t g = std::max<int64_t>(0, issued - kSplitStages); g < issued; ++g)
-                mbar_drain(&full_b[g % kSplitStages], (uint32_t)((g / kSplitStages) & 1));
+            for (int64_t g = std::max<int64_t>(0, issued - kStages); g < issued; ++g)
+                mbar_drain(&full_b[g % kStages], (uint32_t)((g / kStages) & 1));
         }
     } else if (warp == kMmaWarp) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer: A terms from TMEM, X^T from shared memory
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(p.N);
             int64_t g = 0;
             bool ok = true;
             for (int64_t it = 0; it < my_tiles && ok; ++it) {
-                const int a = (int)(it & 1);
-                if (!mbar_wait(&acce[a], (uint32_t)(((it >> 1) & 1) ^ 1), &s_abort, p.err)) break;
+                const int a = (int)(it % nacc);
+                if (!mbar_wait(&acce[a], (uint32_t)(((it / nacc) & 1) ^ 1), &s_abort, p.err)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(a * p.N);
                 for (int64_t kc = 0; kc < p.kchunks; ++kc, ++g) {
-                    const int s = (int)(g % kSplitStages);
-                    const uint32_t ph = (uint32_t)((g / kSplitStages) & 1);
+                    const int s = (int)(g % kStages);
+                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
                     if (!mbar_wait(&full_a[s], ph, &s_abort, p.err) ||
                         !mbar_wait(&full_b[s], ph, &s_abort, p.err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = smem_u32(sbuf + (size_t)s * stage_bytes);
+                    const uint32_t bst = smem_u32(bbuf + (size_t)s * b_stage);
+                    const uint32_t ast = tmem_base + kAStageCol + 96u * (uint32_t)s;
 #pragma unroll
                     for (int kk = 0; kk < kBK / 16; ++kk) {
-                        const uint64_t bdesc = sw128_desc(st + 3 * kTermBytes + 32u * kk);
+                        const uint64_t bdesc = sw128_desc(bst + 32u * kk);
 #pragma unroll
-                        for (int term = 0; term < 3; ++term) {
-                            const uint64_t adesc = sw128_desc(st + term * kTermBytes + 32u * kk);
-                            mma_bf16(d_tmem, adesc, bdesc, idesc, (kc | kk | term) ? 1u : 0u);
-                        }
+                        for (int term = 0; term < 3; ++term)
+                            mma_bf16_ts(d_tmem, ast + 32u * term + 8u * kk, bdesc, idesc,
+                                        (kc | kk | term) ? 1u : 0u);
                     }
                     mma_commit(&empty[s]);
                 }
@@ -363,11 +382,12 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
             mbar_drain(&done_bar, 0);
         }
     } else {
-        // ---------------- epilogue warps 8..11: TMEM lanes 32*(warp%4) ..
+        // ---------------- epilogue warps: TMEM lanes 32*(warp%4) ..
         const int q = warp & 3;
         for (int64_t it = 0; it < my_tiles; ++it) {
-            const int a = (int)(it & 1);
-            if (!mbar_wait(&accf[a], (uint32_t)((it >> 1) & 1), &s_abort, p.err)) break;
+            const int a = (int)(it % nacc);
+            const bool ok = mbar_wait(&accf[a], (uint32_t)((it / nacc) & 1), &s_abort, p.err);
+            if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.ld is warp-wide
             tc_fence_after();
             const int64_t tile = blockIdx.x + it * gridDim.x;
             const int64_t row = tile * kBM + q * 32 + lane;
@@ -391,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     __syncthreads();
     tc_fence_after();
     if (warp == kMmaWarp) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
                      : "memory");
     }
 }
@@ -461,13 +481,12 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
     p.ldc = ldc;
     p.S = s;
     p.N = N;
-    p.astages = N <= 128 ? 4 : 3;
+    p.astages = kMaxAStages;           // 128 KB of A in flight per SM
     p.tiles = (A.rows + kBM - 1) / kBM;
     p.kchunks = (A.cols + kBK - 1) / kBK;
     p.err = err_flag;
     const uint32_t b_bytes = (uint32_t)N * kBK * 2;
-    const size_t stage_bytes = 3 * kTermBytes + ((b_bytes + 1023u) & ~1023u);
-    const size_t smem = (size_t)kHalfBytes * p.astages + stage_bytes * kSplitStages + 1024;
+    const size_t smem = (size_t)kHalfBytes * p.astages + ((b_bytes + 1023u) & ~1023u) * kStages + 1024;
     cudaError_t e = cudaFuncSetAttribute(right_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (!g_sms) {
