@@ -206,13 +206,16 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
                   int64_t ld_ax, cudaStream_t st) {
     cudaError_t e;
     if (P.kind == RE_GAUSSIAN) {
-        if (h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && cnt > 256) {
+        // the tensor-core kernel writes AX rows with 16-byte stores
+        const bool tc = h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && (ld_ax % 4) == 0 &&
+                        (reinterpret_cast<uintptr_t>(AX + c0) & 15) == 0;
+        if (tc && cnt > 256) {
             // the tensor-core kernel takes at most 256 columns (one MMA N) per pass
             for (int c = 0; c < cnt; c += 256)
                 if (int r = right_columns(h, P, seed, c0 + c, std::min(256, cnt - c), AX, ld_ax, st)) return r;
             return RE_OK;
         }
-        if (h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && cnt <= 256) {
+        if (tc) {
             const int64_t kpad = (P.A.cols + 63) / 64 * 64;
             const int nrows = re::tc_mma_n(cnt);
             if (int r = ensure(h->xt, sizeof(uint16_t) * (size_t)kpad * nrows)) return r;
@@ -235,8 +238,8 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
             h->stats.launches += 2;
             return RE_OK;
         }
-        // inputs the tensor-core kernel does not take (transposed or FP64 A, or
-        // unaligned rows) use the FP32 kernel
+        // inputs the tensor-core kernel does not take (transposed or FP64 A,
+        // unaligned rows of A or AX) use the FP32 kernel
         if (int r = ensure(h->x, sizeof(float) * (size_t)P.A.cols * cnt)) return r;
         cudaEvent_t g = stage_begin(h, st);
         e = re::launch_gauss_x(seed, P.A.cols, c0, cnt, static_cast<float*>(h->x.p), cnt, st);

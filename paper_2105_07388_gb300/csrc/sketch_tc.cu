@@ -268,9 +268,17 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     tc_fence_after();
     const uint32_t tmem_base = s_tmem;
 
-    // chunk sequence of this CTA: (tile, kc) for tile = blockIdx.x + i*gridDim.x
-    const int64_t my_tiles = p.tiles > blockIdx.x ? (p.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t total_chunks = my_tiles * p.kchunks;
+    // Stream-K schedule: the tiles x kchunks chunks (tile-major) are cut into
+    // gridDim.x equal contiguous ranges; this CTA owns [c_begin, c_end).  A range
+    // is never shorter than a tile (gridDim.x <= tiles), so a tile is shared by
+    // at most two CTAs; both add their partial sums onto the zeroed output.
+    const int64_t K = p.kchunks;
+    const int64_t c_total = p.tiles * K;
+    const int64_t c_begin = (int64_t)blockIdx.x * c_total / gridDim.x;
+    const int64_t c_end = ((int64_t)blockIdx.x + 1) * c_total / gridDim.x;
+    const int64_t total_chunks = c_end - c_begin;
+    const int64_t t_first = c_begin / K;
+    const int64_t nseg = total_chunks > 0 ? (c_end - 1) / K - t_first + 1 : 0;
 
     if (warp < kConvWarps) {
         // ---------------- converters: warp (q, h) owns TMEM lanes 32q.. (rows 32q + lane)
@@ -318,9 +326,9 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
             for (int64_t hg = 0; hg < 2 * total_chunks; ++hg) {
                 const int as = (int)(hg % NA);
                 if (!mbar_wait(&a_empty[as], (uint32_t)((hg / NA) & 1) ^ 1u, &s_abort, p.err)) break;
-                const int64_t g = hg >> 1;
-                const int64_t tile = blockIdx.x + (g / p.kchunks) * gridDim.x;
-                const int64_t kc = g % p.kchunks;
+                const int64_t c = c_begin + (hg >> 1);
+                const int64_t tile = c / K;
+                const int64_t kc = c % K;
                 mbar_arrive_expect_tx(&a_full[as], kHalfBytes);
                 tma_load_2d(abuf + (size_t)as * kHalfBytes, &amap, (int)(kc * kBK + 32 * (hg & 1)),
                             (int)(tile * kBM), &a_full[as]);
@@ -337,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
                 const int s = (int)(g % kStages);
                 if (!mbar_wait(&empty[s], (uint32_t)((g / kStages) & 1) ^ 1u, &s_abort, p.err)) break;
                 mbar_arrive_expect_tx(&full_b[s], b_bytes);
-                tma_load_2d(bbuf + (size_t)s * b_stage, &xmap, (int)((g % p.kchunks) * kBK), 0, &full_b[s]);
+                tma_load_2d(bbuf + (size_t)s * b_stage, &xmap, (int)(((c_begin + g) % K) * kBK), 0, &full_b[s]);
                 ++issued;
             }
             for (int64_t g = std::max<int64_t>(0, issued - kStages); g < issued; ++g)
@@ -349,12 +357,14 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
             const uint32_t idesc = idesc_bf16(p.N);
             int64_t g = 0;
             bool ok = true;
-            for (int64_t it = 0; it < my_tiles && ok; ++it) {
-                const int a = (int)(it % nacc);
-                if (!mbar_wait(&acce[a], (uint32_t)(((it / nacc) & 1) ^ 1), &s_abort, p.err)) break;
+            for (int64_t j = 0; j < nseg && ok; ++j) {
+                const int a = (int)(j % nacc);
+                if (!mbar_wait(&acce[a], (uint32_t)(((j / nacc) & 1) ^ 1), &s_abort, p.err)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(a * p.N);
-                for (int64_t kc = 0; kc < p.kchunks; ++kc, ++g) {
+                const int64_t t0 = (t_first + j) * K;
+                const int64_t k0 = std::max(c_begin, t0) - t0, k1 = std::min(c_end, t0 + K) - t0;
+                for (int64_t kc = k0; kc < k1; ++kc, ++g) {
                     const int s = (int)(g % kStages);
                     const uint32_t ph = (uint32_t)((g / kStages) & 1);
                     if (!mbar_wait(&full_a[s], ph, &s_abort, p.err) ||
@@ -371,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
 #pragma unroll
                         for (int term = 0; term < 3; ++term)
                             mma_bf16_ts(d_tmem, ast + 32u * term + 8u * kk, bdesc, idesc,
-                                        (kc | kk | term) ? 1u : 0u);
+                                        (kc != k0 || kk || term) ? 1u : 0u);
                     }
                     mma_commit(&empty[s]);
                 }
@@ -384,12 +394,15 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     } else {
         // ---------------- epilogue warps: TMEM lanes 32*(warp%4) ..
         const int q = warp & 3;
-        for (int64_t it = 0; it < my_tiles; ++it) {
-            const int a = (int)(it % nacc);
-            const bool ok = mbar_wait(&accf[a], (uint32_t)((it / nacc) & 1), &s_abort, p.err);
+        for (int64_t j = 0; j < nseg; ++j) {
+            const int a = (int)(j % nacc);
+            const bool ok = mbar_wait(&accf[a], (uint32_t)((j / nacc) & 1), &s_abort, p.err);
             if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.ld is warp-wide
             tc_fence_after();
-            const int64_t tile = blockIdx.x + it * gridDim.x;
+            const int64_t tile = t_first + j;
+            // a tile shared with a neighbouring CTA: add onto the zeroed output (two
+            // addends onto +0 give the same sum in either order)
+            const bool shared = std::max(c_begin, tile * K) != tile * K || std::min(c_end, tile * K + K) != tile * K + K;
             const int64_t row = tile * kBM + q * 32 + lane;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * p.N);
             for (int c = 0; c < p.N; c += 16) {
@@ -398,8 +411,12 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
                 if (row < p.M) {
                     float* dst = p.C + row * p.ldc + c;
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        if (c + j < p.S) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    for (int i = 0; i < 16; i += 4) {
+                        if (c + i >= p.S) continue;
+                        const float4 w = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                        if (shared) atomicAdd(reinterpret_cast<float4*>(dst + i), w);
+                        else *reinterpret_cast<float4*>(dst + i) = w;
+                    }
                 }
             }
             tc_fence_before();
@@ -413,6 +430,23 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
                      : "memory");
+    }
+}
+
+// Zero the output rows of every tile that two CTAs share (the tile holding the
+// start of range b, b = 1 .. G-1, unless the range starts on a tile boundary).
+__global__ void tc_zero_shared_tiles(float* __restrict__ C, int64_t ldc, int64_t M, int S, int64_t tiles,
+                                     int64_t kchunks, int G) {
+    const int64_t b = (int64_t)blockIdx.x + 1;
+    const int64_t c = b * (tiles * kchunks) / G;
+    if (c % kchunks == 0) return;
+    const int64_t tile = c / kchunks;
+    const int64_t r0 = tile * kBM;
+    const int64_t rows = std::min<int64_t>(kBM, M - r0);
+    const int q4 = S / 4;
+    for (int64_t i = threadIdx.x; i < rows * q4; i += blockDim.x) {
+        const int64_t r = r0 + i / q4;
+        *reinterpret_cast<float4*>(C + r * ldc + 4 * (i % q4)) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -495,6 +529,11 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
         cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int64_t grid = std::min<int64_t>(p.tiles, g_sms);
+    if (grid > 1 && p.tiles % grid != 0) {
+        tc_zero_shared_tiles<<<(unsigned)(grid - 1), 256, 0, st>>>(C, ldc, A.rows, s, p.tiles, p.kchunks, (int)grid);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     right_tc_kernel<<<(unsigned)grid, kThreads, smem, st>>>(amap, map, p);
     return cudaGetLastError();
 }

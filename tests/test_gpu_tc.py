@@ -34,6 +34,8 @@ def htc():
     (2049, 1030, 0, 128),
     (513, 300, 8, 256),      # N = 256, two pipeline stages
     (5000, 4096, 64, 64),
+    (19584, 1024, 0, 32),    # 153 row tiles on 152 SMs: tiles shared by two CTAs
+    (20400, 1000, 8, 128),   # 160 tiles, ragged last tile and K chunk, shared tiles
 ])
 def test_tc_right_sketch_parity(htc, m, n, col0, s):
     A = np.random.default_rng(m + n + s).standard_normal((m, n)).astype(np.float32)
@@ -76,3 +78,17 @@ def test_tc_rank_estimate_clear_gap(htc, m, n, rank):
     assert res.rank == orc.rank == rank and res.final_s == orc.final_s
     k = min(len(sg), len(orc.sigma))
     assert np.max(np.abs(sg[:k] - orc.sigma[:k])) <= 1e-4 * orc.sigma[0]
+
+
+def test_tc_shared_tiles_deterministic(htc):
+    """Tiles split between two CTAs are summed by two additions onto zero: the
+    result is the same bit pattern on every call."""
+    m, n, s = 39000, 1100, 64                 # 305 row tiles: most CTAs share a tile
+    A = torch.from_numpy(np.random.default_rng(11).standard_normal((m, n)).astype(np.float32)).cuda()
+    outs = []
+    for _ in range(3):
+        AX = torch.full((m, s), float("nan"), dtype=torch.float32, device="cuda")
+        rk.re_sketch_apply(htc, A, 0, s, rk.RE_GAUSSIAN, 21, AX)
+        outs.append(AX)
+    assert torch.isfinite(outs[0]).all()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
