@@ -31,6 +31,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# measured DRAM traffic / algorithmic bytes of right_tc_kernel (ncu, 16384x16384, N=32)
+TC_TRAFFIC_PER_ALGO_BYTE = 1.0012
+
 WORKLOADS = {
     "large": dict(m=65536, n=16384, rank=200, eps=1e-4, seed=1, sketch_seed=12345),
     "medium": dict(m=16384, n=16384, rank=200, eps=1e-4, seed=1, sketch_seed=12345),
@@ -269,7 +272,11 @@ def main():
                 "bound": "hbm", "achieved": right_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
                 "peak_source": f"{src} hbm_gbs",
                 "tensor_tflops_achieved": right_tflops if args.precision == "bf16x3" else None}
-    roof["traffic"] = None
+    # DRAM bytes per launch from an ncu capture of this kernel (dram__bytes_read.sum +
+    # dram__bytes_write.sum on a 16384x16384 launch, profiles/right_tc_kernel_16384x16384.md),
+    # expressed per algorithmic byte and scaled to this launch; only for the kernel it was taken on
+    roof["traffic"] = (TC_TRAFFIC_PER_ALGO_BYTE * st.right_bytes / max(st.right_launches, 1)
+                       if args.precision == "bf16x3" and args.kind == "gaussian" else None)
     roof["algorithmic_bytes_per_launch"] = st.right_bytes / max(st.right_launches, 1)
     roof["launches"] = int(st.right_launches)
     roof["dominant_stage"] = dominant

@@ -231,11 +231,12 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
             if (e != cudaSuccess) return cuda_fail(e, "generate X");
             stage_end(h, st, g, kStageOther);
             cudaEvent_t a = stage_begin(h, st);
+            int nl = 0;
             e = re::launch_right_tc(P.A, static_cast<const uint16_t*>(h->xt.p), kpad, cnt,
-                                    AX + c0, ld_ax, static_cast<int*>(h->status.p) + 1, st);
+                                    AX + c0, ld_ax, static_cast<int*>(h->status.p) + 1, st, &nl);
             if (e != cudaSuccess) return cuda_fail(e, "right sketch (tensor cores)");
             stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 2), 3.0 * 2.0 * P.A.rows * P.A.cols * cnt);
-            h->stats.launches += 2;
+            h->stats.launches += 1 + nl;
             return RE_OK;
         }
         // inputs the tensor-core kernel does not take (transposed or FP64 A,

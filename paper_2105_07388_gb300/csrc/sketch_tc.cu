@@ -482,7 +482,7 @@ bool tc_supported(const MatView& A) {
 int tc_mma_n(int s) { return s <= 16 ? 16 : (s + 15) / 16 * 16; }
 
 cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, int s, float* C,
-                            int64_t ldc, int* err_flag, cudaStream_t st) {
+                            int64_t ldc, int* err_flag, cudaStream_t st, int* launches) {
     if (s <= 0 || A.rows <= 0) return cudaSuccess;
     if (s > 256 || s % 8 != 0) return cudaErrorInvalidValue;
     const int N = tc_mma_n(s);
@@ -533,8 +533,10 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
         tc_zero_shared_tiles<<<(unsigned)(grid - 1), 256, 0, st>>>(C, ldc, A.rows, s, p.tiles, p.kchunks, (int)grid);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        if (launches) ++*launches;
     }
     right_tc_kernel<<<(unsigned)grid, kThreads, smem, st>>>(amap, map, p);
+    if (launches) ++*launches;
     return cudaGetLastError();
 }
 
