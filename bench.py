@@ -327,6 +327,33 @@ def main():
     line["forms"] = forms
     line["forms_identical_ranks"] = forms_ok
 
+    if args.kind == "gaussian":
+        # the SRHT right sketch (register FWHT, one pass of A per append) on the same
+        # matrix; its rank is reported, not compared: on this coherent U, V the sampled
+        # Hadamard columns alias and the SRHT estimate may fall short of the true rank
+        hs = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_FP32))
+        rs, _ = rk.re_rank_estimate(hs, A, w["eps"], 1, w["sketch_seed"], stream=stream)
+        torch.cuda.synchronize()
+        rk.re_stats_enable(hs, True)
+        rk.re_stats_reset(hs)
+        es0 = torch.cuda.Event(enable_timing=True)
+        es1 = torch.cuda.Event(enable_timing=True)
+        es0.record(stream)
+        for _ in range(K):
+            rs, _ = rk.re_rank_estimate(hs, A, w["eps"], 1, w["sketch_seed"], stream=stream)
+        es1.record(stream)
+        torch.cuda.synchronize()
+        ss = rk.re_stats_get(hs)
+        rk.re_destroy(hs)
+        ms_s = es0.elapsed_time(es1) / K
+        gbs = ss.right_bytes / (ss.right_ms * 1e-3) / 1e9 if ss.right_ms else 0.0
+        line["srht"] = {"estimates_per_s": 1e3 / ms_s, "ms": ms_s, "rank": rs.rank, "final_s": rs.final_s,
+                        "passes": rs.passes, "flags": rs.flags,
+                        "right_sketch_gbs": gbs, "right_sketch_frac": gbs / hbm,
+                        "right_ms_per_step": ss.right_ms / K,
+                        "stage_ms_per_step": {"right": ss.right_ms / K, "left": ss.left_ms / K,
+                                              "svd": ss.svd_ms / K, "other": ss.other_ms / K}}
+
     if not args.no_e2e:
         Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
         Ah.copy_(A)

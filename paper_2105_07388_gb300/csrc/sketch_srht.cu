@@ -143,6 +143,126 @@ __global__ void __launch_bounds__(1024) srht_smem_kernel(const TA* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 rows with n_pad = 2^L, L = 12..14, aligned and not transposed: T = 2^(L-5)
+// threads per row, 32 values per thread, three register phases joined by two
+// shared-memory transposes (logical index bits in registers per phase):
+//   phase 1  bits {0, 1} and [L-3, L): coalesced float4 loads, r*4T + 4j + q
+//   phase 2  bits [2, 7):  thread = (idx >> 7, idx & 3)
+//   phase 3  bits [7, L-3) of the register bits [7, 12): thread = (idx >> 12, idx & 127)
+// Shared memory holds the row with its 16-byte chunks XOR-swizzled inside each
+// 512-byte block by the block index, which makes the float4 stores of phase 1
+// and the scalar loads and stores of phases 2 and 3 conflict-free.  Butterflies
+// run two at a time with packed FP32x2 add/sub (round to nearest, as scalar).
+__device__ __forceinline__ int phys_sw(int idx) {
+    const int B = idx >> 7;
+    return (B << 7) | ((((idx >> 2) & 31) ^ (B & 7)) << 2) | (idx & 3);
+}
+
+__device__ __forceinline__ void bfly2(float& a0, float& a1, float& b0, float& b1) {
+    unsigned long long A, B, S, D;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b0), "f"(b1));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(S) : "l"(A), "l"(B));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(D) : "l"(A), "l"(B));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(S));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(b0), "=f"(b1) : "l"(D));
+}
+
+// butterflies over register-index bit H (a power of two) of 32 values
+template <int H>
+__device__ __forceinline__ void stage32(float (&x)[32]) {
+    if constexpr (H == 1) {
+#pragma unroll
+        for (int r = 0; r < 32; r += 4) bfly2(x[r], x[r + 2], x[r + 1], x[r + 3]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 32; r += 2)
+            if ((r & H) == 0) bfly2(x[r], x[r + 1], x[r + H], x[r + H + 1]);
+    }
+}
+
+template <int NB>   // the first NB register-index bits
+__device__ __forceinline__ void fwht32(float (&x)[32]) {
+    if constexpr (NB > 0) stage32<1>(x);
+    if constexpr (NB > 1) stage32<2>(x);
+    if constexpr (NB > 2) stage32<4>(x);
+    if constexpr (NB > 3) stage32<8>(x);
+    if constexpr (NB > 4) stage32<16>(x);
+}
+
+template <int L>
+__global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_vec_kernel(const float* __restrict__ A, int64_t lda,
+                                                                int64_t M, int64_t N,
+                                                                const uint32_t* __restrict__ dbits,
+                                                                const int* __restrict__ cols, int s,
+                                                                float* __restrict__ C, int64_t ldc) {
+    constexpr int T = 1 << (L - 5);
+    constexpr int NP = 1 << L;
+    extern __shared__ float4 smem4[];
+    float* buf = reinterpret_cast<float*>(smem4);          // NP floats, swizzled
+    int* scol = reinterpret_cast<int*>(buf + NP);
+    for (int k = threadIdx.x; k < s; k += T) scol[k] = cols[k];
+    const int j = threadIdx.x;
+    const int64_t nwords = (N + 31) / 32;
+    __syncthreads();
+
+    for (int64_t row = blockIdx.x; row < M; row += gridDim.x) {
+        const float* Ar = A + row * lda;
+        float x[32];
+        // phase 1: register e = 4 r + q  <->  logical bits (q: 0, 1; r: L-3 .. L-1)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int idx = r * 4 * T + 4 * j;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (idx + 3 < N) {
+                v = __ldg(reinterpret_cast<const float4*>(Ar + idx));
+            } else if (idx < N) {
+                v.x = __ldg(Ar + idx);
+                if (idx + 1 < N) v.y = __ldg(Ar + idx + 1);
+                if (idx + 2 < N) v.z = __ldg(Ar + idx + 2);
+            }
+            const uint32_t w = (idx >> 5) < nwords ? __ldg(dbits + (idx >> 5)) >> (idx & 31) : 0u;
+            x[4 * r + 0] = __uint_as_float(__float_as_uint(v.x) ^ ((w & 1u) << 31));
+            x[4 * r + 1] = __uint_as_float(__float_as_uint(v.y) ^ (((w >> 1) & 1u) << 31));
+            x[4 * r + 2] = __uint_as_float(__float_as_uint(v.z) ^ (((w >> 2) & 1u) << 31));
+            x[4 * r + 3] = __uint_as_float(__float_as_uint(v.w) ^ (((w >> 3) & 1u) << 31));
+        }
+        fwht32<5>(x);
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            *reinterpret_cast<float4*>(buf + phys_sw(r * 4 * T + 4 * j)) =
+                make_float4(x[4 * r], x[4 * r + 1], x[4 * r + 2], x[4 * r + 3]);
+        __syncthreads();
+        // phase 2: register c <-> logical bits 2..6
+        {
+            const int base = (j >> 2) * 128 + (j & 3);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) x[c] = buf[phys_sw(base + 4 * c)];
+            fwht32<5>(x);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) buf[phys_sw(base + 4 * c)] = x[c];
+        }
+        __syncthreads();
+        // phase 3: register k <-> logical bits 7..11, butterflies on bits 7 .. L-4
+        {
+            const int base = (j >> 7) * 4096 + (j & 127);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) x[k] = buf[phys_sw(base + 128 * k)];
+            fwht32<L - 10>(x);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) buf[phys_sw(base + 128 * k)] = x[k];
+        }
+        __syncthreads();
+        for (int k = j; k < s; k += T) C[row * ldc + k] = buf[phys_sw(scol[k])];
+        __syncthreads();
+    }
+}
+
+template <int L>
+cudaError_t launch_vec(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
+                       int64_t ldc, cudaStream_t st);
+
 int g_sm_count = 0;
 
 int sm_count() {
@@ -153,6 +273,23 @@ int sm_count() {
         if (!g_sm_count) g_sm_count = 148;
     }
     return g_sm_count;
+}
+
+template <int L>
+cudaError_t launch_vec(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
+                       int64_t ldc, cudaStream_t st) {
+    constexpr int T = 1 << (L - 5);
+    const size_t smem = sizeof(float) * ((size_t)1 << L) + sizeof(int) * (size_t)s;
+    auto k = srht_vec_kernel<L>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(A.rows, (int64_t)std::max(per_sm, 1) * sm_count()));
+    k<<<(unsigned)grid, T, smem, st>>>(static_cast<const float*>(A.ptr), A.ld, A.rows, A.cols, dbits, cols, s,
+                                       C, ldc);
+    return cudaGetLastError();
 }
 
 template <int LOGN, bool TRANS, typename TA>
@@ -181,6 +318,13 @@ template <bool TRANS, typename TA>
 cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
                           int64_t ldc, cudaStream_t st) {
     const int need = pow2_bits(A.cols);
+    if constexpr (!TRANS && sizeof(TA) == 4) {
+        if (need >= 12 && need <= 14 && (A.ld % 4) == 0 && (reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0) {
+            if (need == 12) return launch_vec<12>(A, dbits, cols, s, C, ldc, st);
+            if (need == 13) return launch_vec<13>(A, dbits, cols, s, C, ldc, st);
+            return launch_vec<14>(A, dbits, cols, s, C, ldc, st);
+        }
+    }
     if (need <= 8) return launch_reg<8, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
     if (need <= 10) return launch_reg<10, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
     if (need <= 12) return launch_reg<12, TRANS, TA>(A, dbits, cols, s, C, ldc, st);

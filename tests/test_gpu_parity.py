@@ -100,7 +100,10 @@ def _right_bound(Ao, X):
     (1000, 777, torch.float32, rk.RE_SRHT),
     (257, 3000, torch.float32, rk.RE_SRHT),
     (700, 9000, torch.float32, rk.RE_SRHT),        # transposed
-    (9100, 9000, torch.float32, rk.RE_SRHT),       # 2^14-point register transform
+    (9100, 9000, torch.float32, rk.RE_SRHT),       # 2^14-point vectorised transform
+    (3001, 2500, torch.float32, rk.RE_SRHT),       # 2^12, ragged row
+    (5003, 4100, torch.float32, rk.RE_SRHT),       # 2^13
+    (2000, 4097, torch.float32, rk.RE_SRHT),       # row pitch not a multiple of 4: scalar kernel
     (333, 20000, torch.float32, rk.RE_SRHT),       # shared-memory transform (2^15)
 ])
 def test_right_sketch_parity(h, m, n, dtype, kind):
