@@ -62,29 +62,35 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Jacobi rotation of columns a, b (length n, a multiple of 4*G, 16-byte
-// aligned) by a group of G consecutive lanes; returns 1 if this group rotated
-// (and stores |cos| of the pair in *meas).  Every lane of the warp must call it
-// (the reductions use full-warp shuffles); inactive groups pass active = false.
-// Each group reads 4*G contiguous floats per step with 128-bit accesses, so a
-// group of 8 lanes is exactly one shared-memory wavefront.  The rotation
-// parameters use the fast reciprocal square root and division: their rounding
-// only perturbs the angle, and c*c + s*s stays 1 to a few ulp.
-template <int G>
-__device__ __forceinline__ int rotate_pair(bool active, float* a, float* b, int n, float tol,
-                                           float floor_abs, float* meas) {
+// Jacobi rotation of columns a, b (length 4*G*NV, 16-byte aligned) by a group
+// of G consecutive lanes; each lane holds NV float4 of each column in registers
+// (elements 4 (gl + G v) .. +3), so the columns are read once and written once.
+// Every lane of the warp must call it (the reductions use full-warp shuffles);
+// inactive groups pass active = false.  A pair is rotated when
+// |a.b| > tol |a| |b| and |a.b| > floor_abs; then rotated is set and meas_max
+// takes max(|cos|).  The rotation parameters use the fast reciprocal square
+// root and division: their rounding only perturbs the angle, and c^2 + s^2
+// stays 1 to a few ulp.
+template <int G, int NV>
+__device__ __forceinline__ void jacobi_pair(bool active, float* a, float* b, float tol2, float floor_abs,
+                                            float& meas_max, int& rotated) {
     const int gl = threadIdx.x & (G - 1);
+    float4 x[NV], y[NV];
     float al = 0.f, be = 0.f, ga = 0.f, al2 = 0.f, be2 = 0.f, ga2 = 0.f;
     if (active) {
-        for (int i = 4 * gl; i < n; i += 4 * G) {
-            const float4 x = *reinterpret_cast<const float4*>(a + i);
-            const float4 y = *reinterpret_cast<const float4*>(b + i);
-            al = fmaf(x.x, x.x, fmaf(x.y, x.y, al));
-            al2 = fmaf(x.z, x.z, fmaf(x.w, x.w, al2));
-            be = fmaf(y.x, y.x, fmaf(y.y, y.y, be));
-            be2 = fmaf(y.z, y.z, fmaf(y.w, y.w, be2));
-            ga = fmaf(x.x, y.x, fmaf(x.y, y.y, ga));
-            ga2 = fmaf(x.z, y.z, fmaf(x.w, y.w, ga2));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            x[v] = *reinterpret_cast<const float4*>(a + 4 * (gl + G * v));
+            y[v] = *reinterpret_cast<const float4*>(b + 4 * (gl + G * v));
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            al = fmaf(x[v].x, x[v].x, fmaf(x[v].y, x[v].y, al));
+            al2 = fmaf(x[v].z, x[v].z, fmaf(x[v].w, x[v].w, al2));
+            be = fmaf(y[v].x, y[v].x, fmaf(y[v].y, y[v].y, be));
+            be2 = fmaf(y[v].z, y[v].z, fmaf(y[v].w, y[v].w, be2));
+            ga = fmaf(x[v].x, y[v].x, fmaf(x[v].y, y[v].y, ga));
+            ga2 = fmaf(x[v].z, y[v].z, fmaf(x[v].w, y[v].w, ga2));
         }
     }
     al += al2;
@@ -97,9 +103,12 @@ __device__ __forceinline__ int rotate_pair(bool active, float* a, float* b, int 
         ga += __shfl_xor_sync(0xffffffffu, ga, o);
     }
     const float ag = fabsf(ga);
-    const float nab = sqrtf(al) * sqrtf(be);
-    if (!active || !(ag > tol * nab) || !(ag > floor_abs)) return 0;
-    *meas = __fdividef(ag, nab);
+    const float ab = al * be;
+    // ga^2 > tol^2 al be  <=>  |ga| > tol |a| |b|  (pairs below the absolute floor are
+    // skipped first, so al be cannot have underflowed for a rotated pair)
+    if (!active || !(ag > floor_abs) || !(ga * ga > tol2 * ab)) return;
+    rotated = 1;
+    meas_max = fmaxf(meas_max, ag * rsqrtf(ab));
     const float zeta = __fdividef(be - al, ga + ga);
     const float az = fabsf(zeta);
     float tt;
@@ -111,22 +120,32 @@ __device__ __forceinline__ int rotate_pair(bool active, float* a, float* b, int 
     }
     const float c = rsqrtf(fmaf(tt, tt, 1.f));
     const float sn = c * tt;
-    for (int i = 4 * gl; i < n; i += 4 * G) {
-        float4 x = *reinterpret_cast<float4*>(a + i);
-        float4 y = *reinterpret_cast<float4*>(b + i);
-        const float4 xa = x;
-        x.x = fmaf(c, xa.x, -sn * y.x);
-        x.y = fmaf(c, xa.y, -sn * y.y);
-        x.z = fmaf(c, xa.z, -sn * y.z);
-        x.w = fmaf(c, xa.w, -sn * y.w);
-        y.x = fmaf(sn, xa.x, c * y.x);
-        y.y = fmaf(sn, xa.y, c * y.y);
-        y.z = fmaf(sn, xa.z, c * y.z);
-        y.w = fmaf(sn, xa.w, c * y.w);
-        *reinterpret_cast<float4*>(a + i) = x;
-        *reinterpret_cast<float4*>(b + i) = y;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const float4 xa = x[v], ya = y[v];
+        x[v].x = fmaf(c, xa.x, -sn * ya.x);
+        x[v].y = fmaf(c, xa.y, -sn * ya.y);
+        x[v].z = fmaf(c, xa.z, -sn * ya.z);
+        x[v].w = fmaf(c, xa.w, -sn * ya.w);
+        y[v].x = fmaf(sn, xa.x, c * ya.x);
+        y[v].y = fmaf(sn, xa.y, c * ya.y);
+        y[v].z = fmaf(sn, xa.z, c * ya.z);
+        y[v].w = fmaf(sn, xa.w, c * ya.w);
+        *reinterpret_cast<float4*>(a + 4 * (gl + G * v)) = x[v];
+        *reinterpret_cast<float4*>(b + 4 * (gl + G * v)) = y[v];
     }
-    return 1;
+}
+
+// Warp-wide OR of `rotated` and max of `meas` folded into shared flags (one
+// atomic per warp).
+__device__ __forceinline__ void fold_sweep_flags(int rotated, float meas, int* s_any, unsigned int* s_meas) {
+    const int any = __any_sync(0xffffffffu, rotated);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) meas = fmaxf(meas, __shfl_xor_sync(0xffffffffu, meas, o));
+    if ((threadIdx.x & 31) == 0 && any) {
+        atomicOr(s_any, 1);
+        atomicMax(s_meas, __float_as_uint(meas));
+    }
 }
 
 // Position i of the round-robin (circle) schedule on P players in round t.
@@ -188,6 +207,7 @@ __device__ __forceinline__ float householder(float* x, int L) {
 // One CTA per core: core -> shared memory (column-major, scaled), QR in place,
 // R^T -> second region, Jacobi on R^T, norms.  blockIdx.x selects the core
 // (core_stride / sigma_stride apart) so one launch serves a batch.
+template <int NV>
 __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     const double* __restrict__ core, int r2, int s, int64_t ld, int64_t core_stride,
     double* __restrict__ sigma, int64_t sigma_stride, int* __restrict__ status,
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     if (active && !active[blockIdx.x]) return;
     core += (int64_t)blockIdx.x * core_stride;
     sigma += (int64_t)blockIdx.x * sigma_stride;
-    const int sp = (s + 63) / 64 * 64;                  // padded column length of R^T (4 x 16 lanes)
+    const int sp = 64 * NV;                             // padded column length of R^T (4 x 16 lanes x NV)
     float* W = reinterpret_cast<float*>(smem);          // r2 x s, column-major
     float* Rt = W + ((size_t)r2 * s + 31) / 32 * 32;    // sp x s, column c = row c of R (128-B aligned)
     __shared__ double s_norm[512];
@@ -350,6 +370,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
         const float floor_abs = kAbsFloor * s_red[0];
         constexpr int G = 16;
         const int grp = tid / G, ngrp = blockDim.x / G;
+        int rotated = 0;
+        float meas = 0.f;
         for (int t = 0; t < P - 1; ++t) {
             for (int base = 0; base < P / 2; base += ngrp) {
                 const int q = base + grp;
@@ -361,15 +383,13 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
                     qq = max(c1, c2);
                     act = qq < s;
                 }
-                float meas = 0.f;
-                if (rotate_pair<G>(act, Rt + (size_t)p * sp, Rt + (size_t)qq * sp, sp, tol, floor_abs, &meas) &&
-                    (tid & (G - 1)) == 0) {
-                    s_flag = 1;
-                    atomicMax(&s_meas, __float_as_uint(meas));
-                }
+                jacobi_pair<G, NV>(act, Rt + (size_t)p * sp, Rt + (size_t)qq * sp, tol * tol, floor_abs, meas,
+                                   rotated);
             }
             __syncthreads();
         }
+        fold_sweep_flags(rotated, meas, &s_flag, &s_meas);
+        __syncthreads();
         const int any = s_flag;
         const float worst = __uint_as_float(s_meas);
         __syncthreads();
@@ -391,7 +411,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
 // ---------------------------------------------------------------------------
 // Cluster version.  Column j of the core lives in CTA j % CL (local column j / CL).
 
-template <int CL>
+template <int CL, int NV>
 __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
     const double* __restrict__ core, int r2, int s, int64_t ld, int b, double* __restrict__ sigma,
     int* __restrict__ status) {
@@ -399,7 +419,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
     const int nloc = (s + CL - 1) / CL;
-    const int sp = (s + 127) / 128 * 128;                      // padded column length of R^T
+    const int sp = 128 * NV;                                   // padded column length of R^T
     const size_t set_floats = 2 * (size_t)b * sp;              // two blocks of b columns
     const size_t r1_floats = (max((size_t)nloc * r2, set_floats) + 31) / 32 * 32;
     float* W = reinterpret_cast<float*>(smem);                // QR: nloc x r2 (column-major)
@@ -540,13 +560,13 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         float gm = 0.f;
         for (int r = 0; r < CL; ++r) gm = fmaxf(gm, *cluster.map_shared_rank(&s_fmax, r));
         const float floor_abs = kAbsFloor * gm;
+        int rotated = 0;
+        float meas = 0.f;
         for (int t = 0; t < P2 - 1; ++t) {
             float* c0 = sets[cur];
             float* c1 = c0 + (size_t)b * sp;
-            int rotated = 0;
             constexpr int G = 32;                  // one warp per pair: few pairs per round
             const int grp = tid / G, ngrp = blockDim.x / G;
-            const bool leader = (tid & (G - 1)) == 0;
             if (t == 0) {
                 // pairs inside each block (circle ordering on b columns)
                 const int P = b + (b & 1);
@@ -565,11 +585,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
                             pa = bs + (size_t)p * sp;
                             pb = bs + (size_t)qq * sp;
                         }
-                        float meas = 0.f;
-                        if (rotate_pair<G>(act, pa, pb, sp, tol, floor_abs, &meas) && leader) {
-                            rotated = 1;
-                            atomicMax(&s_meas, __float_as_uint(meas));
-                        }
+                        jacobi_pair<G, NV>(act, pa, pb, tol * tol, floor_abs, meas, rotated);
                     }
                     __syncthreads();
                 }
@@ -581,16 +597,11 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
                     const bool act = j < b;
                     int jj = act ? j + u : 0;
                     if (jj >= b) jj -= b;
-                    float meas = 0.f;
-                    if (rotate_pair<G>(act, c0 + (size_t)(act ? j : 0) * sp, c1 + (size_t)jj * sp, sp, tol,
-                                       floor_abs, &meas) && leader) {
-                        rotated = 1;
-                        atomicMax(&s_meas, __float_as_uint(meas));
-                    }
+                    jacobi_pair<G, NV>(act, c0 + (size_t)(act ? j : 0) * sp, c1 + (size_t)jj * sp, tol * tol,
+                                       floor_abs, meas, rotated);
                 }
                 __syncthreads();
             }
-            if (rotated) atomicAdd(&s_count, 1);
             // tournament positions 1..P2-1 move up by one: pull the new blocks from
             // the current set of their source CTAs into this CTA's other set
             cluster.sync();
@@ -621,6 +632,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
             cur = nxt;
             __syncthreads();
         }
+        fold_sweep_flags(rotated, meas, &s_count, &s_meas);
         cluster.sync();
         int total = 0;
         float worst = 0.f;
@@ -662,12 +674,12 @@ size_t cluster_smem(int CL, int r2, int s, int* b_out) {
                             (2 * (size_t)r2 + 31) / 32 * 32 + set_floats);
 }
 
-template <int CL>
-cudaError_t launch_cluster_sigma(const double* core, int r2, int s, int64_t ld, double* sigma,
-                                 int* status, cudaStream_t st) {
+template <int CL, int NV>
+cudaError_t launch_cluster_sigma_nv(const double* core, int r2, int s, int64_t ld, double* sigma,
+                                    int* status, cudaStream_t st) {
     int b = 0;
     const size_t smem = cluster_smem(CL, r2, s, &b);
-    auto kern = core_sigma_cluster_kernel<CL>;
+    auto kern = core_sigma_cluster_kernel<CL, NV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (CL > 8) {
@@ -687,6 +699,18 @@ cudaError_t launch_cluster_sigma(const double* core, int r2, int s, int64_t ld, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, core, r2, s, ld, b, sigma, status);
+}
+
+template <int CL>
+cudaError_t launch_cluster_sigma(const double* core, int r2, int s, int64_t ld, double* sigma,
+                                 int* status, cudaStream_t st) {
+    switch ((s + 127) / 128) {
+        case 1: return launch_cluster_sigma_nv<CL, 1>(core, r2, s, ld, sigma, status, st);
+        case 2: return launch_cluster_sigma_nv<CL, 2>(core, r2, s, ld, sigma, status, st);
+        case 3: return launch_cluster_sigma_nv<CL, 3>(core, r2, s, ld, sigma, status, st);
+        case 4: return launch_cluster_sigma_nv<CL, 4>(core, r2, s, ld, sigma, status, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // Step 8 (device): scaled sigma, threshold rank, gap index.
@@ -757,11 +781,18 @@ cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t
                                       const int* active, int cert_r1, float cert_ratio) {
     const size_t sm = cta_smem(r2, s);
     if (sm > kSmemLimit || count <= 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(core_sigma_cta_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto kern = core_sigma_cta_kernel<1>;
+    switch ((s + 63) / 64) {
+        case 1: kern = core_sigma_cta_kernel<1>; break;
+        case 2: kern = core_sigma_cta_kernel<2>; break;
+        case 3: kern = core_sigma_cta_kernel<3>; break;
+        case 4: kern = core_sigma_cta_kernel<4>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    core_sigma_cta_kernel<<<count, kCtaThreads, sm, st>>>(core, r2, s, ld, core_stride, sigma,
-                                                          sigma_stride, status, active, cert_r1, cert_ratio);
+    kern<<<count, kCtaThreads, sm, st>>>(core, r2, s, ld, core_stride, sigma, sigma_stride, status, active,
+                                         cert_r1, cert_ratio);
     return cudaGetLastError();
 }
 
