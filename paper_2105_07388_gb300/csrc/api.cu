@@ -288,21 +288,25 @@ int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const
         stage_end(h, st, g, kStageOther);
         h->stats.launches += 2;
     }
-    const size_t need = std::max(re::left_part_floats(M, 2 * (c1 - c0), c0),
-                                 re::left_part_floats(M, 2 * c1, c1 - c0));
+    const size_t need = std::max({re::left_part_floats(M, 2 * (c1 - c0), c0),
+                                  re::left_part_floats(M, 2 * c1, c1 - c0),
+                                  re::left_tc_part_floats(M, 2 * (c1 - c0), c0),
+                                  re::left_tc_part_floats(M, 2 * c1, c1 - c0)});
     if (int r = ensure(h->part, sizeof(float) * need)) return r;
+    if (int r = ensure(h->status, 64)) return r;
+    int* tmo = static_cast<int*>(h->status.p) + 1;     // bounded-wait expiry flag of the tensor-core kernels
     cudaError_t e = cudaSuccess;
     cudaEvent_t a = stage_begin(h, st);
     if (c0 > 0)
         e = re::launch_left(P.ykind, seed, AX, ld_ax, M, 2 * c0, 2 * (c1 - c0), 0, c0,
                             static_cast<const uint32_t*>(h->dy.p), static_cast<const int*>(h->py.p),
                             static_cast<float*>(h->part.p), h->part.cap / sizeof(float), core,
-                            ld_core, st);
+                            ld_core, st, tmo);
     if (e == cudaSuccess)
         e = re::launch_left(P.ykind, seed, AX, ld_ax, M, 0, 2 * c1, c0, c1 - c0,
                             static_cast<const uint32_t*>(h->dy.p), static_cast<const int*>(h->py.p),
                             static_cast<float*>(h->part.p), h->part.cap / sizeof(float), core,
-                            ld_core, st);
+                            ld_core, st, tmo);
     if (e != cudaSuccess) return cuda_fail(e, "left sketch");
     stage_end(h, st, a, kStageLeft);
     h->stats.launches += c0 > 0 ? 4 : 2;

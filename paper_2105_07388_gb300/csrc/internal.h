@@ -67,11 +67,22 @@ cudaError_t launch_right_simt(const MatView& A, const float* X, int64_t ldx, int
 // r < R, c < S, i < M.  Y Gaussian (kind RE_GAUSSIAN) or SRTT from dbits/perm
 // (perm holds pi_Y(q) for q in [0, row0+R)).  `part` is FP32 scratch of
 // part_cap floats.
+// With a non-null err_flag (a device word that a bounded wait sets on expiry),
+// Gaussian blocks of aligned AX run on the tensor cores (left_tc.cu); otherwise,
+// and when `part` is too small for that kernel's split count, on CUDA cores.
 cudaError_t launch_left(int kind, uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0,
                         int R, int col0, int S, const uint32_t* dbits, const int* perm,
                         float* part, size_t part_cap, double* core, int64_t ld_core,
-                        cudaStream_t st);
+                        cudaStream_t st, int* err_flag = nullptr);
 size_t left_part_floats(int64_t M, int R, int S);
+
+// ---- left sketch on the tensor cores (left_tc.cu) -----------------------------
+bool left_tc_supported(const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0, int S);
+size_t left_tc_part_floats(int64_t M, int R, int S);
+// FP32 split-K partials part[split][R][S] of the block; *splits_out = splits used.
+cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0, int R,
+                                    int col0, int S, float* part, size_t part_cap, int* err_flag, int* splits_out,
+                                    cudaStream_t st);
 
 // Batched right sketch: for every active block b and each of its BM-row tiles
 // (tile_prefix[b] .. tile_prefix[b+1]-1 are b's work items), AX_b[:, col0:col0+s]

@@ -1,0 +1,358 @@
+// Left sketch on the tensor cores (Algorithm 1 steps 4-6 for a Gaussian Y): a
+// block of the core Y (AX), computed transposed so that AX is the MMA's A
+// operand.  For an M tile of 128 AX columns c, an N tile of up to 256 Y rows q
+// and a range of AX rows i (split-K):
+//
+//     D[c][q] = sum_i AX[i][c] Y[q][i]
+//
+// AX (FP32) is split exactly into three BF16 terms (as in the right sketch) and
+// written to TMEM; the entries of Y are BF16-exact normals, generated on the fly
+// from Philox straight into the 128B-swizzled K-major layout of the B operand
+// (Y never exists in HBM).  Products are exact; the FP32 accumulation in TMEM is
+// the only rounding.  Each CTA writes its FP32 partial block, and the split-K
+// partials are summed in FP64 in a fixed order afterwards.
+//
+// Warp roles (576 threads, one CTA per SM):
+//   warps 0-7    converters: warp (q, h) owns TMEM lanes 32q.. (AX columns
+//                32q + lane of the M tile) and half h (32 rows) of each 64-row
+//                chunk: 32 loads of the row-major tile (consecutive lanes read
+//                consecutive columns), exact split, three tcgen05.st.
+//   warps 8-15   Y generators: a task is 16 Y rows x 64 i; each lane makes 8
+//                Philox calls (4 rows x 8 consecutive i) and writes four 16-byte
+//                rows segments; warps 8-11 then run the epilogue.
+//   warp 16      TMA producer of AX half chunks (32 rows x up to 128 columns,
+//                FP32, zero fill past the last row / column).
+//   warp 17      TMEM allocation and the MMA issuer (A from TMEM, B from smem).
+// Every mbarrier wait is bounded in time (on expiry: error flag, drain, free
+// TMEM, return).
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace re {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kLBM = 128;                    // AX columns per M tile (TMEM lanes)
+constexpr int kLBK = 64;                     // AX rows per chunk
+constexpr int kLConv = 8;                    // warps 0-7
+constexpr int kLGen = 8;                     // warps 8-15
+constexpr int kLEpi = 4;                     // warps 8-11
+constexpr int kLProdWarp = kLConv + kLGen;   // 16
+constexpr int kLMmaWarp = kLProdWarp + 1;    // 17
+constexpr int kLThreads = (kLMmaWarp + 1) * 32;
+constexpr int kLAStages = 4;                 // FP32 half-chunk ring
+constexpr int kLStages = 2;                  // TMEM A stages = Y stages
+constexpr uint32_t kLAStageCol = 256;        // TMEM: D in [0, N), A stages from column 256
+constexpr uint32_t kLTmemCols = 512;
+static_assert(kLAStageCol + 96 * kLStages <= kLTmemCols, "TMEM budget");
+
+struct LeftTcParams {
+    uint64_t seed;
+    int64_t M;          // AX rows
+    int row0;           // first Y row of the block (a multiple of 4)
+    int R;              // Y rows in the block
+    int S;              // AX columns in the block
+    int boxw;           // AX columns per TMA box (min(128, S))
+    int N;              // MMA N (multiple of 16, <= 256)
+    int n_tiles, m_tiles, splits;
+    int64_t chunk;      // AX rows per split (a multiple of 64)
+    float* part;        // [splits][R][S]
+    int* err;
+};
+
+__global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_constant__ CUtensorMap amap,
+                                                               const LeftTcParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t a_full[kLAStages], a_empty[kLAStages];
+    __shared__ __align__(8) uint64_t full_a[kLStages], full_b[kLStages], empty[kLStages];
+    __shared__ __align__(8) uint64_t accf, done_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles = p.n_tiles * p.m_tiles;
+    const int split = blockIdx.x / tiles;
+    const int nt = (blockIdx.x % tiles) / p.m_tiles;
+    const int mt = blockIdx.x % p.m_tiles;
+    const int64_t i_begin = (int64_t)split * p.chunk;
+    const int64_t i_end = std::min<int64_t>(p.M, i_begin + p.chunk);
+    const int64_t nchunks = i_end > i_begin ? (i_end - i_begin + kLBK - 1) / kLBK : 0;
+    const uint32_t half_bytes = (uint32_t)p.boxw * 32u * 4u;
+    const uint32_t y_stage = ((uint32_t)p.N * 128u + 1023u) & ~1023u;
+    unsigned char* abuf = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* ybuf = abuf + (size_t)kLAStages * ((kLBM * 32 * 4 + 1023) & ~1023);
+
+    if (tid == 0) {
+        for (int i = 0; i < kLAStages; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], (kLConv / 2) * 32);
+        }
+        for (int i = 0; i < kLStages; ++i) {
+            mbar_init(&full_a[i], kLConv * 32);
+            mbar_init(&full_b[i], kLGen * 32);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&accf, 1);
+        mbar_init(&done_bar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == kLMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kLTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = s_tmem;
+
+    if (warp < kLConv) {
+        // ---------------- converters: column c = 32q + lane, rows 32h .. 32h+31 of each chunk
+        const int q = warp & 3, h = warp >> 2;
+        const int c = 32 * q + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        for (int64_t g = 0; g < nchunks; ++g) {
+            const int s = (int)(g % kLStages);
+            bool ok = mbar_wait(&empty[s], (uint32_t)((g / kLStages) & 1) ^ 1u, &s_abort, p.err);
+            const int64_t hg = 2 * g + h;
+            const int as = (int)(hg % kLAStages);
+            if (ok) ok = mbar_wait(&a_full[as], (uint32_t)((hg / kLAStages) & 1), &s_abort, p.err);
+            if (!__all_sync(0xffffffffu, ok)) break;     // tcgen05.st is warp-wide
+            const float* src = reinterpret_cast<const float*>(abuf + (size_t)as * ((kLBM * 32 * 4 + 1023) & ~1023));
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = c < p.boxw ? src[i * p.boxw + c] : 0.f;
+            mbar_arrive(&a_empty[as]);
+            uint32_t hi[16], mid[16], lo[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) split3(v[2 * i], v[2 * i + 1], hi[i], mid[i], lo[i]);
+            tc_fence_after();
+            const uint32_t col = kLAStageCol + 96u * (uint32_t)s + 16u * (uint32_t)h;
+            tmem_st16(lane_base + col, hi);
+            tmem_st16(lane_base + col + 32u, mid);
+            tmem_st16(lane_base + col + 64u, lo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(&full_a[s]);
+        }
+    } else if (warp < kLConv + kLGen) {
+        // ---------------- Y generators: task = 16 rows x 64 i of the B tile
+        const int gw = warp - kLConv;
+        const int j = lane & 7;                  // 8 consecutive i (one 16-byte segment)
+        const int rows_here = std::min(p.N, p.R - nt * p.N);
+        const uint32_t q4_base = (uint32_t)((p.row0 + nt * p.N) >> 2);
+        bool ok = true;
+        for (int64_t g = 0; g < nchunks && ok; ++g) {
+            const int s = (int)(g % kLStages);
+            if (!mbar_wait(&empty[s], (uint32_t)((g / kLStages) & 1) ^ 1u, &s_abort, p.err)) {
+                ok = false;
+                break;
+            }
+            unsigned char* yb = ybuf + (size_t)s * y_stage;
+            const int64_t i0 = i_begin + g * kLBK + 8 * j;
+            for (int t = gw; t < p.N / 16; t += kLGen) {
+                const int grp = 4 * t + (lane >> 3);          // local group of 4 rows
+                float z[8][4];
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const int64_t i = i0 + kk;
+                    if (4 * grp < rows_here && i < p.M) {
+                        normals4((uint32_t)i, q4_base + (uint32_t)grp, kStreamGY, p.seed, z[kk]);
+                    } else {
+                        z[kk][0] = z[kk][1] = z[kk][2] = z[kk][3] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int ql = 4 * grp + e;
+                    const bool live = ql < rows_here;
+                    uint32_t w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        w[u] = live ? ((__float_as_uint(z[2 * u][e]) >> 16) | (__float_as_uint(z[2 * u + 1][e]) & 0xFFFF0000u))
+                                    : 0u;
+                    *reinterpret_cast<uint4*>(yb + (size_t)ql * 128 + ((j ^ (ql & 7)) << 4)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(&full_b[s]);
+        }
+        if (warp < kLConv + kLEpi) {
+            // ---------------- epilogue: lane c of the M tile, N columns of D
+            const int q = warp & 3;
+            const bool done = nchunks > 0 && mbar_wait(&accf, 0u, &s_abort, p.err);
+            if (__all_sync(0xffffffffu, done)) {
+                tc_fence_after();
+                const int c = 32 * q + lane;
+                const int cg = mt * kLBM + c;
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16);
+                for (int col = 0; col < p.N; col += 16) {
+                    float v[16];
+                    tmem_ld16(taddr + (uint32_t)col, v);
+                    if (cg < p.S) {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int r = nt * p.N + col + u;
+                            if (r < p.R) p.part[((int64_t)split * p.R + r) * p.S + cg] = v[u];
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == kLProdWarp) {
+        // ---------------- TMA producer of AX half chunks
+        if (lane == 0) {
+            const uint32_t a_stage = (kLBM * 32 * 4 + 1023) & ~1023;
+            int64_t issued = 0;
+            for (int64_t hg = 0; hg < 2 * nchunks; ++hg) {
+                const int as = (int)(hg % kLAStages);
+                if (!mbar_wait(&a_empty[as], (uint32_t)((hg / kLAStages) & 1) ^ 1u, &s_abort, p.err)) break;
+                mbar_arrive_expect_tx(&a_full[as], half_bytes);
+                tma_load_2d(abuf + (size_t)as * a_stage, &amap, mt * kLBM, (int)(i_begin + 32 * hg), &a_full[as]);
+                ++issued;
+            }
+            for (int64_t hg = std::max<int64_t>(0, issued - kLAStages); hg < issued; ++hg)
+                mbar_drain(&a_full[hg % kLAStages], (uint32_t)((hg / kLAStages) & 1));
+        }
+    } else {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(p.N);
+            bool ok = true;
+            for (int64_t g = 0; g < nchunks; ++g) {
+                const int s = (int)(g % kLStages);
+                const uint32_t ph = (uint32_t)((g / kLStages) & 1);
+                if (!mbar_wait(&full_a[s], ph, &s_abort, p.err) || !mbar_wait(&full_b[s], ph, &s_abort, p.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t bst = smem_u32(ybuf + (size_t)s * y_stage);
+                const uint32_t ast = tmem_base + kLAStageCol + 96u * (uint32_t)s;
+#pragma unroll
+                for (int kk = 0; kk < kLBK / 16; ++kk) {
+                    const uint64_t bdesc = sw128_desc(bst + 32u * kk);
+#pragma unroll
+                    for (int term = 0; term < 3; ++term)
+                        mma_bf16_ts(tmem_base, ast + 32u * term + 8u * kk, bdesc, idesc, (g | kk | term) ? 1u : 0u);
+                }
+                mma_commit(&empty[s]);
+            }
+            if (ok && nchunks > 0) mma_commit(&accf);
+            mma_commit(&done_bar);
+            mbar_drain(&done_bar, 0);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kLMmaWarp) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kLTmemCols)
+                     : "memory");
+    }
+}
+
+int g_left_sms = 0;
+
+int left_sms() {
+    if (!g_left_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_left_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (!g_left_sms) g_left_sms = 148;
+    }
+    return g_left_sms;
+}
+
+struct LeftTcPlan {
+    int N, n_tiles, m_tiles, splits;
+    int64_t chunk;
+};
+
+LeftTcPlan left_tc_plan(int64_t M, int R, int S, size_t part_cap) {
+    LeftTcPlan pl;
+    pl.N = std::min(256, (R + 15) / 16 * 16);
+    pl.n_tiles = (R + pl.N - 1) / pl.N;
+    pl.m_tiles = (S + kLBM - 1) / kLBM;
+    const int tiles = pl.n_tiles * pl.m_tiles;
+    int64_t splits = std::max<int64_t>(1, std::min<int64_t>((M + kLBK - 1) / kLBK, (left_sms() + tiles - 1) / tiles));
+    if (part_cap > 0) splits = std::min<int64_t>(splits, (int64_t)(part_cap / ((size_t)R * S)));
+    splits = std::max<int64_t>(splits, 1);
+    int64_t chunk = (M + splits - 1) / splits;
+    chunk = (chunk + kLBK - 1) / kLBK * kLBK;
+    pl.chunk = chunk;
+    pl.splits = (int)((M + chunk - 1) / chunk);
+    return pl;
+}
+
+}  // namespace
+
+bool left_tc_supported(const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0, int S) {
+    return encode_fn() != nullptr && M >= 32 && R >= 1 && S >= 4 && (S % 4) == 0 && (row0 % 4) == 0 &&
+           (ldax % 4) == 0 && (reinterpret_cast<uintptr_t>(AX + col0) & 15) == 0;
+}
+
+size_t left_tc_part_floats(int64_t M, int R, int S) {
+    const LeftTcPlan pl = left_tc_plan(M, R, S, 0);
+    return (size_t)pl.splits * R * S;
+}
+
+cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0, int R,
+                                    int col0, int S, float* part, size_t part_cap, int* err_flag, int* splits_out,
+                                    cudaStream_t st) {
+    const LeftTcPlan pl = left_tc_plan(M, R, S, part_cap);
+    if ((size_t)pl.splits * R * S > part_cap) return cudaErrorInvalidValue;
+    EncodeTiled enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const int boxw = std::min(kLBM, S);
+    CUtensorMap amap;
+    const cuuint64_t dim[2] = {(cuuint64_t)S, (cuuint64_t)M};
+    const cuuint64_t stride[1] = {(cuuint64_t)ldax * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)boxw, 32u};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(AX + col0), dim, stride, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    LeftTcParams p;
+    p.seed = seed;
+    p.M = M;
+    p.row0 = row0;
+    p.R = R;
+    p.S = S;
+    p.boxw = boxw;
+    p.N = pl.N;
+    p.n_tiles = pl.n_tiles;
+    p.m_tiles = pl.m_tiles;
+    p.splits = pl.splits;
+    p.chunk = pl.chunk;
+    p.part = part;
+    p.err = err_flag;
+    const size_t a_stage = (kLBM * 32 * 4 + 1023) & ~1023;
+    const size_t y_stage = ((size_t)pl.N * 128 + 1023) & ~(size_t)1023;
+    const size_t smem = a_stage * kLAStages + y_stage * kLStages + 1024;
+    cudaError_t e = cudaFuncSetAttribute(left_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (int64_t)pl.splits * pl.n_tiles * pl.m_tiles;
+    if (grid > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    left_tc_kernel<<<(unsigned)grid, kLThreads, smem, st>>>(amap, p);
+    *splits_out = pl.splits;
+    return cudaGetLastError();
+}
+
+}  // namespace re

@@ -140,6 +140,29 @@ def test_core_parity_with_appending(h, kind):
     assert np.all(np.abs(got - ref) <= bound)
 
 
+@pytest.mark.parametrize("m,n,c0,c1", [
+    (3001, 900, 0, 8),          # 16 x 8 core block
+    (4099, 1200, 64, 136),      # appended: 144 x 64 and 272 x 72 blocks (two N tiles)
+    (2500, 700, 128, 288),      # 320 x 128 and 576 x 160 blocks (three N tiles, two M tiles)
+])
+def test_core_blocks_parity(h, m, n, c0, c1):
+    """Left-sketch blocks of every shape the append step produces, against the
+    FP64 oracle's core at the final width."""
+    A = np.random.default_rng(m + c1).standard_normal((m, n)).astype(np.float32)
+    Ad = dev(A)
+    AX = torch.zeros(m, c1, dtype=torch.float32, device="cuda")
+    core = torch.zeros(2 * c1, c1, dtype=torch.float64, device="cuda")
+    if c0 > 0:
+        rk.re_sketch_apply(h, Ad, 0, c0, rk.RE_GAUSSIAN, 57, AX, core)
+    rk.re_sketch_apply(h, Ad, c0, c1 - c0, rk.RE_GAUSSIAN, 57, AX, core)
+    A64 = A.astype(np.float64)
+    ref = alg.core(A64, c1, rk.RE_GAUSSIAN, 57)
+    X, Y = alg.embeddings(rk.RE_GAUSSIAN, n, m, c1, 57)
+    bound = 4.0 * (m / 32 + n / 32 + 64) * U32 * (np.abs(Y) @ np.abs(A64) @ np.abs(X))
+    got = core.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
+
+
 def test_core_sigma_against_lapack(h):
     for (r2, s, seed) in ((16, 8, 0), (128, 64, 1), (256, 128, 2), (512, 256, 3), (37, 29, 4),
                           (1024, 512, 5), (600, 300, 6), (1000, 70, 7)):
