@@ -13,13 +13,12 @@
 // partials are summed in FP64 in a fixed order afterwards.
 //
 // Warp roles (576 threads, one CTA per SM):
-//   warps 0-7    converters: warp (q, h) owns TMEM lanes 32q.. (AX columns
-//                32q + lane of the M tile) and half h (32 rows) of each 64-row
-//                chunk: 32 loads of the row-major tile (consecutive lanes read
-//                consecutive columns), exact split, three tcgen05.st.
-//   warps 8-15   Y generators: a task is 16 Y rows x 64 i; each lane makes 8
-//                Philox calls (4 rows x 8 consecutive i) and writes four 16-byte
-//                rows segments; warps 8-11 then run the epilogue.
+//   warps 0-15   workers: for each 64-row chunk, warp w first generates its
+//                share of Y (groups of 4 Y rows x 64 i: lane l makes the 2 Philox
+//                calls of i = 2l, 2l+1 and writes one 4-byte word per row), then
+//                converts 16 rows of AX for the TMEM lanes 32 (w & 3) .. (AX
+//                columns of the M tile): loads of the row-major tile, exact split,
+//                three tcgen05.st of 8 columns; warps 0-3 then run the epilogue.
 //   warp 16      TMA producer of AX half chunks (32 rows x up to 128 columns,
 //                FP32, zero fill past the last row / column).
 //   warp 17      TMEM allocation and the MMA issuer (A from TMEM, B from smem).
@@ -42,10 +41,8 @@ using namespace tc;
 
 constexpr int kLBM = 128;                    // AX columns per M tile (TMEM lanes)
 constexpr int kLBK = 64;                     // AX rows per chunk
-constexpr int kLConv = 8;                    // warps 0-7
-constexpr int kLGen = 8;                     // warps 8-15
-constexpr int kLEpi = 4;                     // warps 8-11
-constexpr int kLProdWarp = kLConv + kLGen;   // 16
+constexpr int kLWork = 16;                   // worker warps 0-15
+constexpr int kLProdWarp = kLWork;           // 16
 constexpr int kLMmaWarp = kLProdWarp + 1;    // 17
 constexpr int kLThreads = (kLMmaWarp + 1) * 32;
 constexpr int kLAStages = 4;                 // FP32 half-chunk ring
@@ -72,7 +69,7 @@ __global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_cons
                                                                const LeftTcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t a_full[kLAStages], a_empty[kLAStages];
-    __shared__ __align__(8) uint64_t full_a[kLStages], full_b[kLStages], empty[kLStages];
+    __shared__ __align__(8) uint64_t full[kLStages], empty[kLStages];
     __shared__ __align__(8) uint64_t accf, done_bar;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
@@ -94,11 +91,10 @@ __global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_cons
     if (tid == 0) {
         for (int i = 0; i < kLAStages; ++i) {
             mbar_init(&a_full[i], 1);
-            mbar_init(&a_empty[i], (kLConv / 2) * 32);
+            mbar_init(&a_empty[i], (kLWork / 2) * 32);
         }
         for (int i = 0; i < kLStages; ++i) {
-            mbar_init(&full_a[i], kLConv * 32);
-            mbar_init(&full_b[i], kLGen * 32);
+            mbar_init(&full[i], kLWork * 32);
             mbar_init(&empty[i], 1);
         }
         mbar_init(&accf, 1);
@@ -119,90 +115,77 @@ __global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_cons
     tc_fence_after();
     const uint32_t tmem_base = s_tmem;
 
-    if (warp < kLConv) {
-        // ---------------- converters: column c = 32q + lane, rows 32h .. 32h+31 of each chunk
-        const int q = warp & 3, h = warp >> 2;
+    if (warp < kLWork) {
+        // ---------------- workers
+        const int q = warp & 3, r4 = warp >> 2;        // TMEM lane quarter, 16-row quarter of a chunk
+        const int h = r4 >> 1, roff = (r4 & 1) * 16;   // A half holding those rows, offset inside it
         const int c = 32 * q + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        const int rows_here = std::min(p.N, p.R - nt * p.N);
+        const uint32_t q4_base = (uint32_t)((p.row0 + nt * p.N) >> 2);
+        const int chunk16 = lane >> 2;                 // 16-byte segment of a Y row
+        const uint32_t in_seg = (uint32_t)(lane & 3) * 4u;
         for (int64_t g = 0; g < nchunks; ++g) {
             const int s = (int)(g % kLStages);
             bool ok = mbar_wait(&empty[s], (uint32_t)((g / kLStages) & 1) ^ 1u, &s_abort, p.err);
-            const int64_t hg = 2 * g + h;
-            const int as = (int)(hg % kLAStages);
-            if (ok) ok = mbar_wait(&a_full[as], (uint32_t)((hg / kLAStages) & 1), &s_abort, p.err);
-            if (!__all_sync(0xffffffffu, ok)) break;     // tcgen05.st is warp-wide
-            const float* src = reinterpret_cast<const float*>(abuf + (size_t)as * ((kLBM * 32 * 4 + 1023) & ~1023));
-            float v[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = c < p.boxw ? src[i * p.boxw + c] : 0.f;
-            mbar_arrive(&a_empty[as]);
-            uint32_t hi[16], mid[16], lo[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) split3(v[2 * i], v[2 * i + 1], hi[i], mid[i], lo[i]);
-            tc_fence_after();
-            const uint32_t col = kLAStageCol + 96u * (uint32_t)s + 16u * (uint32_t)h;
-            tmem_st16(lane_base + col, hi);
-            tmem_st16(lane_base + col + 32u, mid);
-            tmem_st16(lane_base + col + 64u, lo);
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            tc_fence_before();
-            mbar_arrive(&full_a[s]);
-        }
-    } else if (warp < kLConv + kLGen) {
-        // ---------------- Y generators: task = 16 rows x 64 i of the B tile
-        const int gw = warp - kLConv;
-        const int j = lane & 7;                  // 8 consecutive i (one 16-byte segment)
-        const int rows_here = std::min(p.N, p.R - nt * p.N);
-        const uint32_t q4_base = (uint32_t)((p.row0 + nt * p.N) >> 2);
-        bool ok = true;
-        for (int64_t g = 0; g < nchunks && ok; ++g) {
-            const int s = (int)(g % kLStages);
-            if (!mbar_wait(&empty[s], (uint32_t)((g / kLStages) & 1) ^ 1u, &s_abort, p.err)) {
-                ok = false;
-                break;
-            }
+            if (!__all_sync(0xffffffffu, ok)) break;
+            // Y share: groups of 4 rows
             unsigned char* yb = ybuf + (size_t)s * y_stage;
-            const int64_t i0 = i_begin + g * kLBK + 8 * j;
-            for (int t = gw; t < p.N / 16; t += kLGen) {
-                const int grp = 4 * t + (lane >> 3);          // local group of 4 rows
-                float z[8][4];
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    const int64_t i = i0 + kk;
-                    if (4 * grp < rows_here && i < p.M) {
-                        normals4((uint32_t)i, q4_base + (uint32_t)grp, kStreamGY, p.seed, z[kk]);
-                    } else {
-                        z[kk][0] = z[kk][1] = z[kk][2] = z[kk][3] = 0.f;
-                    }
+            const int64_t i0 = i_begin + g * kLBK + 2 * lane;
+            for (int grp = warp; grp < p.N / 4; grp += kLWork) {
+                float z0[4], z1[4];
+                if (4 * grp < rows_here && i0 < p.M) {
+                    normals4((uint32_t)i0, q4_base + (uint32_t)grp, kStreamGY, p.seed, z0);
+                } else {
+                    z0[0] = z0[1] = z0[2] = z0[3] = 0.f;
+                }
+                if (4 * grp < rows_here && i0 + 1 < p.M) {
+                    normals4((uint32_t)(i0 + 1), q4_base + (uint32_t)grp, kStreamGY, p.seed, z1);
+                } else {
+                    z1[0] = z1[1] = z1[2] = z1[3] = 0.f;
                 }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int ql = 4 * grp + e;
-                    const bool live = ql < rows_here;
-                    uint32_t w[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        w[u] = live ? ((__float_as_uint(z[2 * u][e]) >> 16) | (__float_as_uint(z[2 * u + 1][e]) & 0xFFFF0000u))
-                                    : 0u;
-                    *reinterpret_cast<uint4*>(yb + (size_t)ql * 128 + ((j ^ (ql & 7)) << 4)) =
-                        make_uint4(w[0], w[1], w[2], w[3]);
+                    const uint32_t w = ql < rows_here
+                                           ? ((__float_as_uint(z0[e]) >> 16) | (__float_as_uint(z1[e]) & 0xFFFF0000u))
+                                           : 0u;
+                    *reinterpret_cast<uint32_t*>(yb + (size_t)ql * 128 + ((chunk16 ^ (ql & 7)) << 4) + in_seg) = w;
                 }
             }
             fence_proxy_async();
-            mbar_arrive(&full_b[s]);
+            // AX share: rows roff .. roff+15 of half h, column c
+            const int64_t hg = 2 * g + h;
+            const int as = (int)(hg % kLAStages);
+            ok = mbar_wait(&a_full[as], (uint32_t)((hg / kLAStages) & 1), &s_abort, p.err);
+            if (!__all_sync(0xffffffffu, ok)) break;     // tcgen05.st is warp-wide
+            const float* src = reinterpret_cast<const float*>(abuf + (size_t)as * ((kLBM * 32 * 4 + 1023) & ~1023));
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = c < p.boxw ? src[(roff + i) * p.boxw + c] : 0.f;
+            mbar_arrive(&a_empty[as]);
+            uint32_t hi[8], mid[8], lo[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) split3(v[2 * i], v[2 * i + 1], hi[i], mid[i], lo[i]);
+            tc_fence_after();
+            // A stage layout: term t at column kLAStageCol + 96 s + 32 t, K pair k/2 at +k/2
+            const uint32_t col = kLAStageCol + 96u * (uint32_t)s + 8u * (uint32_t)r4;
+            tmem_st8(lane_base + col, hi);
+            tmem_st8(lane_base + col + 32u, mid);
+            tmem_st8(lane_base + col + 64u, lo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(&full[s]);
         }
-        if (warp < kLConv + kLEpi) {
+        if (warp < 4) {
             // ---------------- epilogue: lane c of the M tile, N columns of D
-            const int q = warp & 3;
             const bool done = nchunks > 0 && mbar_wait(&accf, 0u, &s_abort, p.err);
             if (__all_sync(0xffffffffu, done)) {
                 tc_fence_after();
-                const int c = 32 * q + lane;
                 const int cg = mt * kLBM + c;
-                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16);
                 for (int col = 0; col < p.N; col += 16) {
                     float v[16];
-                    tmem_ld16(taddr + (uint32_t)col, v);
+                    tmem_ld16(lane_base + (uint32_t)col, v);
                     if (cg < p.S) {
 #pragma unroll
                         for (int u = 0; u < 16; ++u) {
@@ -236,7 +219,7 @@ __global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_cons
             for (int64_t g = 0; g < nchunks; ++g) {
                 const int s = (int)(g % kLStages);
                 const uint32_t ph = (uint32_t)((g / kLStages) & 1);
-                if (!mbar_wait(&full_a[s], ph, &s_abort, p.err) || !mbar_wait(&full_b[s], ph, &s_abort, p.err)) {
+                if (!mbar_wait(&full[s], ph, &s_abort, p.err)) {
                     ok = false;
                     break;
                 }

@@ -421,14 +421,29 @@ __global__ void __launch_bounds__(256) left_kernel(uint64_t seed, const float* _
     }
 }
 
-__global__ void left_reduce_kernel(const float* __restrict__ part, int splits, int R, int S,
-                                   int row0, int col0, double* __restrict__ core, int64_t ld_core) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)R * S) return;
+// core block = sum of the split-K partials, in FP64 and in a fixed order: a CTA
+// owns 32 consecutive outputs (one per lane, so every load is a 128-byte line),
+// warp w sums splits w, w+8, w+16, ..., and the 8 warp sums are added in warp
+// order (the result does not depend on scheduling).
+__global__ void __launch_bounds__(256) left_reduce_kernel(const float* __restrict__ part, int splits, int R,
+                                                          int S, int row0, int col0, double* __restrict__ core,
+                                                          int64_t ld_core) {
+    __shared__ double s_sum[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t total = (int64_t)R * S;
+    const int64_t idx = (int64_t)blockIdx.x * 32 + lane;
     double sum = 0.0;
-    for (int p = 0; p < splits; ++p) sum += (double)part[(int64_t)p * R * S + idx];
-    const int r = (int)(idx / S), c = (int)(idx % S);
-    core[(int64_t)(row0 + r) * ld_core + col0 + c] = sum;
+    if (idx < total)
+        for (int p = w; p < splits; p += 8) sum += (double)part[(int64_t)p * total + idx];
+    s_sum[w][lane] = sum;
+    __syncthreads();
+    if (w == 0 && idx < total) {
+        double t = s_sum[0][lane];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) t += s_sum[u][lane];
+        const int r = (int)(idx / S), c = (int)(idx % S);
+        core[(int64_t)(row0 + r) * ld_core + col0 + c] = t;
+    }
 }
 
 int left_splits(int64_t M, int R, int S, int64_t* chunk_out) {
@@ -483,8 +498,8 @@ cudaError_t launch_left(int kind, uint64_t seed, const float* AX, int64_t ldax, 
                                                 &tsplits, st);
         if (e != cudaSuccess) return e;
         const int64_t total = (int64_t)R * S;
-        left_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, tsplits, R, S, row0, col0,
-                                                                             core, ld_core);
+        left_reduce_kernel<<<(unsigned)((total + 31) / 32), 256, 0, st>>>(part, tsplits, R, S, row0, col0,
+                                                                                 core, ld_core);
         return cudaGetLastError();
     }
     int64_t chunk;
@@ -507,8 +522,8 @@ cudaError_t launch_left(int kind, uint64_t seed, const float* AX, int64_t ldax, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)R * S;
-    left_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, splits, R, S, row0, col0,
-                                                                         core, ld_core);
+    left_reduce_kernel<<<(unsigned)((total + 31) / 32), 256, 0, st>>>(part, splits, R, S, row0, col0,
+                                                                             core, ld_core);
     return cudaGetLastError();
 }
 
