@@ -203,11 +203,76 @@ __device__ __forceinline__ float householder(float* x, int L) {
     return tau;
 }
 
+// Register-resident versions for a column of length L <= 32*E (one warp; lane
+// l holds entries l, l+32, ..., masked past L).  householder_regs: reflector of
+// x = col[0..L) with the same arithmetic as householder(); v (v[0] = 1) goes to
+// col[1..), beta to col[0]; returns tau.
+template <int E>
+__device__ __forceinline__ float householder_regs(float* col, int L) {
+    const int lane = threadIdx.x & 31;
+    float x[E];
+    float ss = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        x[e] = i < L ? col[i] : 0.f;
+        if (i >= 1) ss = fmaf(x[e], x[e], ss);
+    }
+    ss = warp_sum(ss);
+    const float x0 = __shfl_sync(0xffffffffu, x[0], 0);
+    float tau = 0.f, beta = x0;
+    if (ss > 0.f) {
+        const float nrm = sqrtf(fmaf(x0, x0, ss));
+        beta = -copysignf(nrm, x0);
+        tau = (beta - x0) / beta;
+        const float scale = 1.f / (x0 - beta);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = lane + 32 * e;
+            if (i >= 1 && i < L) col[i] = x[e] * scale;
+        }
+    }
+    if (lane == 0) col[0] = beta;
+    __syncwarp();
+    return tau;
+}
+
+// Load v (v[0] = 1, entries 1..L-1 from vsrc) into registers.
+template <int E>
+__device__ __forceinline__ void load_reflector(const float* vsrc, int L, float (&v)[E]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        v[e] = i < L ? (i == 0 ? 1.f : vsrc[i]) : 0.f;
+    }
+}
+
+// c <- (I - tau v v^T) c for one column of length L (one warp).
+template <int E>
+__device__ __forceinline__ void apply_reflector(const float (&v)[E], float tau, float* c, int L) {
+    const int lane = threadIdx.x & 31;
+    float x[E];
+    float w = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        x[e] = i < L ? c[i] : 0.f;
+        w = fmaf(v[e], x[e], w);
+    }
+    w = warp_sum(w) * tau;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        if (i < L) c[i] = fmaf(-w, v[e], x[e]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // One CTA per core: core -> shared memory (column-major, scaled), QR in place,
 // R^T -> second region, Jacobi on R^T, norms.  blockIdx.x selects the core
 // (core_stride / sigma_stride apart) so one launch serves a batch.
-template <int NV>
+template <int NV, int E>
 __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     const double* __restrict__ core, int r2, int s, int64_t ld, int64_t core_stride,
     double* __restrict__ sigma, int64_t sigma_stride, int* __restrict__ status,
@@ -258,23 +323,21 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     }
     __syncthreads();
 
-    // Householder QR: column k's reflector, then the trailing columns
+    // Householder QR: column k's reflector, then the trailing columns (reflector
+    // and each column held in registers, r2 <= 32 E)
     for (int k = 0; k < s; ++k) {
         float* colk = W + (size_t)k * r2 + k;
+        const int L = r2 - k;
         if (warp == 0) {
-            const float tau = householder(colk, r2 - k);
+            const float tau = householder_regs<E>(colk, L);
             if (lane == 0) s_tau = tau;
         }
         __syncthreads();
         const float tau = s_tau;
-        if (tau != 0.f) {
-            for (int j = k + 1 + warp; j < s; j += nwarps) {
-                float* cj = W + (size_t)j * r2 + k;
-                float w = 0.f;
-                for (int i = lane; i < r2 - k; i += 32) w = fmaf(i == 0 ? 1.f : colk[i], cj[i], w);
-                w = warp_sum(w) * tau;
-                for (int i = lane; i < r2 - k; i += 32) cj[i] = fmaf(-w, i == 0 ? 1.f : colk[i], cj[i]);
-            }
+        if (tau != 0.f && k + 1 + warp < s) {
+            float v[E];
+            load_reflector<E>(colk, L, v);
+            for (int j = k + 1 + warp; j < s; j += nwarps) apply_reflector<E>(v, tau, W + (size_t)j * r2 + k, L);
         }
         __syncthreads();
     }
@@ -411,7 +474,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
 // ---------------------------------------------------------------------------
 // Cluster version.  Column j of the core lives in CTA j % CL (local column j / CL).
 
-template <int CL, int NV>
+template <int CL, int NV, int E>
 __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
     const double* __restrict__ core, int r2, int s, int64_t ld, int b, double* __restrict__ sigma,
     int* __restrict__ status) {
@@ -490,7 +553,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         if (k == owner) {
             float* colk = W + (size_t)jl * r2 + kk;
             if (warp == 0) {
-                const float tau = householder(colk, L);
+                const float tau = householder_regs<E>(colk, L);
                 if (lane == 0) s_tau[buf] = tau;
             }
             __syncthreads();
@@ -504,15 +567,12 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         cluster.sync();
         const float tau = s_tau[buf];
         const float* v = vbuf + (size_t)buf * r2;
-        if (tau != 0.f) {
-            const int first = (kk + 1 - k + CL - 1) / CL;     // smallest jl with jl*CL + k > kk
-            for (int j2 = first + warp; j2 < nloc; j2 += nwarps) {
-                float* cj = W + (size_t)j2 * r2 + kk;
-                float w = 0.f;
-                for (int i = lane; i < L; i += 32) w = fmaf(v[i], cj[i], w);
-                w = warp_sum(w) * tau;
-                for (int i = lane; i < L; i += 32) cj[i] = fmaf(-w, v[i], cj[i]);
-            }
+        const int first = (kk + 1 - k + CL - 1) / CL;         // smallest jl with jl*CL + k > kk
+        if (tau != 0.f && first + warp < nloc) {
+            float vr[E];
+            load_reflector<E>(v, L, vr);
+            for (int j2 = first + warp; j2 < nloc; j2 += nwarps)
+                apply_reflector<E>(vr, tau, W + (size_t)j2 * r2 + kk, L);
         }
         __syncthreads();
     }
@@ -674,12 +734,12 @@ size_t cluster_smem(int CL, int r2, int s, int* b_out) {
                             (2 * (size_t)r2 + 31) / 32 * 32 + set_floats);
 }
 
-template <int CL, int NV>
+template <int CL, int NV, int E>
 cudaError_t launch_cluster_sigma_nv(const double* core, int r2, int s, int64_t ld, double* sigma,
                                     int* status, cudaStream_t st) {
     int b = 0;
     const size_t smem = cluster_smem(CL, r2, s, &b);
-    auto kern = core_sigma_cluster_kernel<CL, NV>;
+    auto kern = core_sigma_cluster_kernel<CL, NV, E>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (CL > 8) {
@@ -701,14 +761,25 @@ cudaError_t launch_cluster_sigma_nv(const double* core, int r2, int s, int64_t l
     return cudaLaunchKernelEx(&cfg, kern, core, r2, s, ld, b, sigma, status);
 }
 
+template <int CL, int NV>
+cudaError_t launch_cluster_sigma_e(const double* core, int r2, int s, int64_t ld, double* sigma, int* status,
+                                   cudaStream_t st) {
+    // column length r2 <= 32 E; this kernel only takes cores that do not fit one CTA (r2 > 128)
+    const int e = (r2 + 31) / 32;
+    if (e <= 8) return launch_cluster_sigma_nv<CL, NV, 8>(core, r2, s, ld, sigma, status, st);
+    if (e <= 16) return launch_cluster_sigma_nv<CL, NV, 16>(core, r2, s, ld, sigma, status, st);
+    if (e <= 32) return launch_cluster_sigma_nv<CL, NV, 32>(core, r2, s, ld, sigma, status, st);
+    return cudaErrorInvalidValue;
+}
+
 template <int CL>
 cudaError_t launch_cluster_sigma(const double* core, int r2, int s, int64_t ld, double* sigma,
                                  int* status, cudaStream_t st) {
     switch ((s + 127) / 128) {
-        case 1: return launch_cluster_sigma_nv<CL, 1>(core, r2, s, ld, sigma, status, st);
-        case 2: return launch_cluster_sigma_nv<CL, 2>(core, r2, s, ld, sigma, status, st);
-        case 3: return launch_cluster_sigma_nv<CL, 3>(core, r2, s, ld, sigma, status, st);
-        case 4: return launch_cluster_sigma_nv<CL, 4>(core, r2, s, ld, sigma, status, st);
+        case 1: return launch_cluster_sigma_e<CL, 1>(core, r2, s, ld, sigma, status, st);
+        case 2: return launch_cluster_sigma_e<CL, 2>(core, r2, s, ld, sigma, status, st);
+        case 3: return launch_cluster_sigma_e<CL, 3>(core, r2, s, ld, sigma, status, st);
+        case 4: return launch_cluster_sigma_e<CL, 4>(core, r2, s, ld, sigma, status, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -773,6 +844,35 @@ size_t cta_smem(int r2, int s) {
 
 size_t svd_workspace_bytes(int, int) { return 256; }
 
+namespace {
+
+using CtaKernel = void (*)(const double*, int, int, int64_t, int64_t, double*, int64_t, int*, const int*, int,
+                           float);
+
+template <int NV>
+CtaKernel cta_kernel_e(int e) {
+    if (e <= 1) return core_sigma_cta_kernel<NV, 1>;
+    if (e <= 2) return core_sigma_cta_kernel<NV, 2>;
+    if (e <= 4) return core_sigma_cta_kernel<NV, 4>;
+    if (e <= 8) return core_sigma_cta_kernel<NV, 8>;
+    if (e <= 16) return core_sigma_cta_kernel<NV, 16>;
+    if (e <= 32) return core_sigma_cta_kernel<NV, 32>;
+    return nullptr;
+}
+
+// instance for R^T column length 64 NV and core height r2 <= 32 e
+CtaKernel cta_kernel_for(int nv, int e) {
+    switch (nv) {
+        case 1: return cta_kernel_e<1>(e);
+        case 2: return cta_kernel_e<2>(e);
+        case 3: return cta_kernel_e<3>(e);
+        case 4: return cta_kernel_e<4>(e);
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
 bool core_sigma_fits_cta(int r2, int s) { return cta_smem(r2, s) <= kSmemLimit; }
 
 cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t ld,
@@ -781,14 +881,8 @@ cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t
                                       const int* active, int cert_r1, float cert_ratio) {
     const size_t sm = cta_smem(r2, s);
     if (sm > kSmemLimit || count <= 0) return cudaErrorInvalidValue;
-    auto kern = core_sigma_cta_kernel<1>;
-    switch ((s + 63) / 64) {
-        case 1: kern = core_sigma_cta_kernel<1>; break;
-        case 2: kern = core_sigma_cta_kernel<2>; break;
-        case 3: kern = core_sigma_cta_kernel<3>; break;
-        case 4: kern = core_sigma_cta_kernel<4>; break;
-        default: return cudaErrorInvalidValue;
-    }
+    auto kern = cta_kernel_for((s + 63) / 64, (r2 + 31) / 32);
+    if (!kern) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     kern<<<count, kCtaThreads, sm, st>>>(core, r2, s, ld, core_stride, sigma, sigma_stride, status, active,
