@@ -60,8 +60,9 @@ __device__ __forceinline__ int find_prefix(const int64_t* prefix, int count, int
     return lo;
 }
 
-__global__ void init_active_kernel(const int* valid, int* active, int* status, int count) {
+__global__ void init_active_kernel(const int* valid, int* active, int* status, int count, int* tcerr) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0 && tcerr) *tcerr = 0;
     if (b >= count) return;
     active[b] = valid[b];
     status[b] = 0;
@@ -162,13 +163,14 @@ __global__ void __launch_bounds__(256) left_batched_kernel(
 __global__ void readoff_batched_kernel(const BatchDesc* __restrict__ d, int count, int* active,
                                        const double* __restrict__ sigma, int64_t sstride, int s, int r1,
                                        double scale, double eps, double norm_a, int* status,
-                                       DevReadoff* out, double* sigma_scaled, int* final_s) {
+                                       DevReadoff* out, double* sigma_scaled, int* final_s, const int* tcerr) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= count || !active[b]) return;
     const double* sg = sigma + (int64_t)b * sstride;
     double* ss = sigma_scaled + (int64_t)b * sstride;
     DevReadoff r;
-    r.status = status[b];
+    // a bounded wait of the tensor-core sketch expired: every block reports it
+    r.status = (tcerr && *tcerr) ? RE_ERR_TIMEOUT : status[b];
     r.sweeps = 0;
     for (int i = 0; i < r1; ++i) ss[i] = sg[i] * scale;
     const double ref = norm_a > 0.0 ? norm_a : ss[0];
@@ -207,7 +209,7 @@ int r1_of(int s) {
 struct BatchedState {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
-    DBuf ax, x, core, sigma, sscaled, status, out, active, valid, descs, pre128, pre64, colpre, finals;
+    DBuf ax, x, xt, tcerr, actpre, core, sigma, sscaled, status, out, active, valid, descs, pre128, pre64, colpre, finals;
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned char> key;
     int bm_for[16] = {0};
@@ -217,7 +219,7 @@ struct BatchedState {
 void batched_destroy(BatchedState* st) {
     if (!st) return;
     if (st->exec) cudaGraphExecDestroy(st->exec);
-    DBuf* bufs[] = {&st->ax, &st->x, &st->core, &st->sigma, &st->sscaled, &st->status, &st->out,
+    DBuf* bufs[] = {&st->ax, &st->x, &st->xt, &st->tcerr, &st->actpre, &st->core, &st->sigma, &st->sscaled, &st->status, &st->out,
                     &st->active, &st->valid, &st->descs, &st->pre128, &st->pre64, &st->colpre, &st->finals};
     for (DBuf* b : bufs) b->release();
     if (st->ev_in) cudaEventDestroy(st->ev_in);
@@ -271,13 +273,20 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
     }
     if (S_MAX == 0) S_MAX = s0;
     const int SNEW = std::max(s0, S_MAX / 2);
-    int64_t ax_total = 0, x_total = 0;
+    // BF16x3 split products on the tensor cores (X^T pool of tc_mma_n rows per block),
+    // otherwise FP32 CUDA cores with an autotuned tile height
+    const bool use_tc = o.precision == RE_PREC_BF16X3;
+    const int NXT = tc_mma_n(SNEW);
+    int64_t ax_total = 0, x_total = 0, xt_total = 0;
     for (int i = 0; i < count; ++i) {
         BatchDesc& D = hd[i];
         D.ax_off = ax_total;
         D.x_off = x_total;
+        D.kpad = (D.cols + 63) / 64 * 64;
+        D.xt_off = xt_total;
         ax_total += D.rows * S_MAX;
         x_total += (D.cols * SNEW + 63) / 64 * 64;
+        if (use_tc && valid[i]) xt_total += (int64_t)NXT * D.kpad;
         pre128[i + 1] = pre128[i] + (valid[i] ? (D.rows + 127) / 128 : 0);
         pre64[i + 1] = pre64[i] + (valid[i] ? (D.rows + 63) / 64 : 0);
         colpre[i + 1] = colpre[i] + (valid[i] ? D.cols : 0);
@@ -288,7 +297,13 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
         if (e == cudaSuccess) e = b.ensure(bytes);
     };
     ens(st->ax, sizeof(float) * (size_t)std::max<int64_t>(ax_total, 1));
-    ens(st->x, sizeof(float) * (size_t)std::max<int64_t>(x_total, 1));
+    if (use_tc) {
+        ens(st->xt, sizeof(uint16_t) * (size_t)std::max<int64_t>(xt_total, 1));
+        ens(st->tcerr, sizeof(int));
+        ens(st->actpre, sizeof(int64_t) * (size_t)(count + 1));
+    } else {
+        ens(st->x, sizeof(float) * (size_t)std::max<int64_t>(x_total, 1));
+    }
     ens(st->core, sizeof(double) * (size_t)core_stride * count);
     ens(st->sigma, sizeof(double) * (size_t)S_MAX * count);
     ens(st->sscaled, sizeof(double) * (size_t)S_MAX * count);
@@ -316,8 +331,8 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
     put(&o, sizeof(o));
     put(hd.data(), sizeof(BatchDesc) * hd.size());
     put(valid.data(), sizeof(int) * valid.size());
-    const void* pools[] = {st->ax.p, st->x.p, st->core.p, st->sigma.p, st->sscaled.p, st->status.p,
-                           st->out.p, st->active.p, st->finals.p};
+    const void* pools[] = {st->ax.p, st->x.p, st->xt.p, st->tcerr.p, st->actpre.p, st->core.p, st->sigma.p, st->sscaled.p,
+                           st->status.p, st->out.p, st->active.p, st->finals.p};
     put(pools, sizeof(pools));
 
     cudaStream_t bs = st->stream;
@@ -336,8 +351,10 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
         if (e == cudaSuccess) e = cudaMemcpy(st->colpre.p, colpre.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: descriptor upload failed");
         // ---- autotune the right-sketch tile height for each width of the ladder
-        {
-            init_active_kernel<<<(count + 255) / 256, 256, 0, bs>>>(st->valid.as<int>(), active, status, count);
+        // (CUDA-core path; the candidates differ only in tiling, not in arithmetic)
+        if (!use_tc) {
+            init_active_kernel<<<(count + 255) / 256, 256, 0, bs>>>(st->valid.as<int>(), active, status, count,
+                                                                    nullptr);
             for (int s_prev = 0, s = s0; s <= S_MAX; s_prev = s, s *= 2) {
                 const int sn = s - s_prev;
                 const int slot = 31 - __builtin_clz((unsigned)sn);
@@ -374,16 +391,26 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
         e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: begin capture failed");
         int64_t nl = 0;
-        init_active_kernel<<<(count + 255) / 256, 256, 0, bs>>>(st->valid.as<int>(), active, status, count);
+        int* tcerr = use_tc ? st->tcerr.as<int>() : nullptr;
+        init_active_kernel<<<(count + 255) / 256, 256, 0, bs>>>(st->valid.as<int>(), active, status, count, tcerr);
         ++nl;
         for (int s_prev = 0, s = s0; s <= S_MAX && e == cudaSuccess; s_prev = s, s *= 2) {
             const int sn = s - s_prev;
-            const int bm = st->bm_for[31 - __builtin_clz((unsigned)sn)] == 64 ? 64 : 128;
-            gauss_x_batched_kernel<<<1024, 256, 0, bs>>>(dd, count, st->colpre.as<int64_t>(), active, s_prev, sn,
-                                                        st->x.as<float>());
-            e = launch_right_simt_batched(dd, count, bm == 128 ? st->pre128.as<int64_t>() : st->pre64.as<int64_t>(),
-                                          bm == 128 ? pre128[count] : pre64[count], active, st->x.as<float>(), sn,
-                                          st->ax.as<float>(), S_MAX, s_prev, bm, bs);
+            if (use_tc) {
+                e = launch_gauss_xt_batched(dd, count, active, s_prev, sn, tc_mma_n(sn), st->xt.as<uint16_t>(), bs);
+                if (e == cudaSuccess) e = launch_compact_tiles(dd, count, active, st->actpre.as<int64_t>(), bs);
+                if (e == cudaSuccess)
+                    e = launch_right_tc_batched(dd, count, st->actpre.as<int64_t>(), pre128[count],
+                                                st->xt.as<uint16_t>(), sn, st->ax.as<float>(), S_MAX, s_prev, tcerr, bs);
+                ++nl;
+            } else {
+                const int bm = st->bm_for[31 - __builtin_clz((unsigned)sn)] == 64 ? 64 : 128;
+                gauss_x_batched_kernel<<<1024, 256, 0, bs>>>(dd, count, st->colpre.as<int64_t>(), active, s_prev, sn,
+                                                            st->x.as<float>());
+                e = launch_right_simt_batched(dd, count, bm == 128 ? st->pre128.as<int64_t>() : st->pre64.as<int64_t>(),
+                                              bm == 128 ? pre128[count] : pre64[count], active, st->x.as<float>(), sn,
+                                              st->ax.as<float>(), S_MAX, s_prev, bm, bs);
+            }
             nl += 2;
             if (e != cudaSuccess) break;
             if (s_prev > 0) {
@@ -409,7 +436,7 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
             readoff_batched_kernel<<<(count + 127) / 128, 128, 0, bs>>>(
                 dd, count, active, st->sigma.as<double>(), S_MAX, s, std::min(r1_of(s), s),
                 1.0 / std::sqrt((double)s * (double)(2 * s)), eps, o.norm_a, status, st->out.as<DevReadoff>(),
-                st->sscaled.as<double>(), st->finals.as<int>());
+                st->sscaled.as<double>(), st->finals.as<int>(), tcerr);
             ++nl;
         }
         cudaError_t ec = cudaStreamEndCapture(bs, &graph);

@@ -1,0 +1,490 @@
+// Batched right sketch on the tensor cores: AX_b = A_b X_b for thousands of
+// independent blocks (Algorithm 1 step 3 per block), BF16x3 exactly as the
+// single-matrix kernel (A split into three BF16 terms in TMEM, X BF16-exact,
+// FP32 accumulation).  Work items are the 128-row tiles of the active blocks;
+// one persistent CTA per SM walks its items and K chunks in one pipeline.
+//
+// Blocks come with any row pitch (a kernel block of n columns has ld = n), which
+// TMA cannot address, so the tiles are fetched with asynchronous 4-byte copies
+// (cp.async) straight into the 128B-swizzled layout the converters read:
+//   warps 12-15  A producers: per half chunk (128 rows x 32 k), copies of 16,
+//             8 or 4 bytes (the widest the block's row starts allow), coalesced
+//             along k into the 128B-swizzled row layout for row-major blocks, or
+//             along rows into a k-major tile for blocks stored transposed; zero
+//             fill past the block's edges; completion tracked by the stage's
+//             mbarrier (cp.async.mbarrier.arrive.noinc).
+//   warp 16   X^T producer: 16-byte copies of the BF16 X^T chunk (N rows x 64 k).
+//   warps 0-7 converters (either tile layout), warp 17 MMA issuer, warps 8-11
+//             epilogue: as in the single-matrix kernel.
+// Every mbarrier wait is bounded in time (on expiry: error flag, drain, free
+// TMEM, return).
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace re {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;
+constexpr int kConvWarps = 8;
+constexpr int kEpiWarps = 4;
+constexpr int kAProdWarps = 4;
+constexpr int kAProdWarp = kConvWarps + kEpiWarps;             // 12..15
+constexpr int kBProdWarp = kAProdWarp + kAProdWarps;           // 16
+constexpr int kMmaWarp = kBProdWarp + 1;                       // 17
+constexpr int kThreads = (kMmaWarp + 1) * 32;                  // 576
+constexpr uint32_t kHalfBytes = kBM * 32 * 4;                  // 16 KB FP32 half chunk
+constexpr int kAStages = 8;
+constexpr int kStages = 2;
+constexpr uint32_t kAStageCol = 256;
+constexpr uint32_t kTmemCols = 512;
+
+__device__ __forceinline__ int find_block(const int64_t* prefix, int count, int64_t item) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// W-byte asynchronous copy (W = 4, 8, 16) of which src_bytes come from global, the rest zero
+template <int W>
+__device__ __forceinline__ void cp_async_w(uint32_t dst, const void* src, uint32_t src_bytes) {
+    if constexpr (W == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(W), "r"(src_bytes)
+                     : "memory");
+}
+
+// Copy width for a block: the widest of 16, 8, 4 bytes that every row start allows.
+__device__ __forceinline__ int copy_width(const float* A, int64_t ld) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(A);
+    if ((a & 15) == 0 && (ld & 3) == 0) return 16;
+    if ((a & 7) == 0 && (ld & 1) == 0) return 8;
+    return 4;
+}
+
+// One half chunk (rows row0.., k0..k0+31) of a row-major block into the 128B-swizzled
+// layout (row r at r*128, 16-byte chunk c at c ^ (r & 7)); this warp copies rows
+// rbase .. rbase+31; lanes cover (row, W-byte segment) pairs.  Rows past the block
+// are zero-filled in a second loop, so the main loop has no row test.
+template <int W>
+__device__ __forceinline__ void load_rows(const BatchDesc& D, int64_t row0, int64_t k0, int rbase, uint32_t dst0) {
+    constexpr int SEG = 128 / W;                  // segments per 128-byte row
+    constexpr int RPI = 32 / SEG;                 // rows per warp instruction
+    const int lane = threadIdx.x & 31;
+    const int seg = lane % SEG;
+    const int64_t k = k0 + seg * (W / 4);
+    const int64_t kleft = D.cols - k;             // columns left from k
+    const uint32_t nb = kleft >= W / 4 ? (uint32_t)W : (kleft > 0 ? (uint32_t)kleft * 4u : 0u);
+    const uint32_t byte = (uint32_t)seg * W;      // byte offset inside the 128-byte row
+    const int nvalid = (int)std::max<int64_t>(0, std::min<int64_t>(32, D.rows - (row0 + rbase)));
+    int i = lane / SEG;
+    const float* src = D.A + (row0 + rbase + i) * D.ld + (nb ? k : 0);
+    const int64_t step = (int64_t)RPI * D.ld;
+#pragma unroll 4
+    for (; i < nvalid; i += RPI, src += step) {
+        const int rr = rbase + i;
+        const uint32_t dst = dst0 + (uint32_t)rr * 128u + (((byte >> 4) ^ (uint32_t)(rr & 7)) << 4) + (byte & 15u);
+        cp_async_w<W>(dst, nb ? src : D.A, nb);
+    }
+    for (; i < 32; i += RPI) {
+        const int rr = rbase + i;
+        const uint32_t dst = dst0 + (uint32_t)rr * 128u + (((byte >> 4) ^ (uint32_t)(rr & 7)) << 4) + (byte & 15u);
+        cp_async_w<W>(dst, D.A, 0u);
+    }
+}
+
+// One half chunk of a block stored transposed (oriented (row, k) = A[k * ld + row])
+// into a k-major tile: k row kk at kk*512, 128 oriented rows contiguous; this warp
+// copies k rows kbase .. kbase+7, lanes over W-byte segments of each.
+template <int W>
+__device__ __forceinline__ void load_cols(const BatchDesc& D, int64_t row0, int64_t k0, int kbase, uint32_t dst0) {
+    constexpr int SEG = 512 / W;                  // segments per 512-byte k row
+    constexpr int PER = W / 4;                    // floats per segment
+    const int lane = threadIdx.x & 31;
+    const int64_t rleft0 = D.rows - row0;         // oriented rows left from row0
+    for (int kk = kbase; kk < kbase + 8; ++kk) {
+        const int64_t k = k0 + kk;
+        const bool kin = k < D.cols;
+        const float* rowp = D.A + (kin ? k : 0) * D.ld + row0;
+        const uint32_t dk = dst0 + (uint32_t)kk * 512u;
+#pragma unroll
+        for (int sg = lane; sg < SEG; sg += 32) {
+            const int64_t rl = rleft0 - (int64_t)sg * PER;
+            const uint32_t nb = !kin ? 0u : (rl >= PER ? (uint32_t)W : (rl > 0 ? (uint32_t)rl * 4u : 0u));
+            cp_async_w<W>(dk + (uint32_t)sg * W, nb ? rowp + sg * PER : D.A, nb);
+        }
+    }
+}
+
+// the mbarrier receives one arrival when all prior cp.async of this thread land
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct TcBatchParams {
+    const BatchDesc* d;
+    int count;
+    const int64_t* pre;       // prefix of the active blocks' 128-row tiles (count + 1 entries)
+    const uint16_t* xt;       // X^T pool
+    int N;                    // MMA N (rows of each block's X^T)
+    int S;                    // valid output columns
+    float* ax;
+    int64_t ldax;
+    int col0;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcBatchParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t a_full[kAStages], a_empty[kAStages];
+    __shared__ __align__(8) uint64_t full_a[kStages], full_b[kStages], empty[kStages];
+    __shared__ __align__(8) uint64_t accf[2], acce[2], done_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t items = p.pre[p.count];      // tiles of the active blocks (set on the device)
+    const uint32_t b_stage = ((uint32_t)p.N * 128u + 1023u) & ~1023u;
+    unsigned char* abuf = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* bbuf = abuf + (size_t)kAStages * kHalfBytes;
+
+    if (tid == 0) {
+        for (int i = 0; i < kAStages; ++i) {
+            mbar_init(&a_full[i], kAProdWarps * 32);
+            mbar_init(&a_empty[i], (kConvWarps / 2) * 32);   // the 4 converter warps of that half
+        }
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full_a[i], kConvWarps * 32);
+            mbar_init(&full_b[i], 32);
+            mbar_init(&empty[i], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accf[a], 1);
+            mbar_init(&acce[a], kEpiWarps * 32);
+        }
+        mbar_init(&done_bar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = s_tmem;
+
+    if (warp < kConvWarps) {
+        // ---------------- converters (as in the single-matrix kernel)
+        const int q = warp & 3, h = warp >> 2;
+        const int r = 32 * q + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        int64_t g = 0;
+        bool ok = true;
+        for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+            const int b = find_block(p.pre, p.count, it);
+            const int64_t kch = p.d[b].kpad / kBK;
+            const bool trans = p.d[b].trans != 0;
+            for (int64_t kc = 0; kc < kch; ++kc, ++g) {
+                const int s = (int)(g % kStages);
+                ok = mbar_wait(&empty[s], (uint32_t)((g / kStages) & 1) ^ 1u, &s_abort, p.err);
+                const int64_t hg = 2 * g + h;
+                const int as = (int)(hg % kAStages);
+                if (ok) ok = mbar_wait(&a_full[as], (uint32_t)((hg / kAStages) & 1), &s_abort, p.err);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                const unsigned char* tile = abuf + (size_t)as * kHalfBytes;
+                float4 v[8];
+                if (!trans) {
+                    const unsigned char* src = tile + (size_t)r * 128;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const float4*>(src + ((c ^ (r & 7)) << 4));
+                } else {
+                    // k-major tile: column r (consecutive lanes read consecutive words)
+                    const float* src = reinterpret_cast<const float*>(tile) + r;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        v[c] = make_float4(src[(4 * c) * 128], src[(4 * c + 1) * 128], src[(4 * c + 2) * 128],
+                                           src[(4 * c + 3) * 128]);
+                }
+                mbar_arrive(&a_empty[as]);
+                uint32_t hi[16], mid[16], lo[16];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    split3(v[c].x, v[c].y, hi[2 * c], mid[2 * c], lo[2 * c]);
+                    split3(v[c].z, v[c].w, hi[2 * c + 1], mid[2 * c + 1], lo[2 * c + 1]);
+                }
+                tc_fence_after();
+                const uint32_t col = kAStageCol + 96u * (uint32_t)s + 16u * (uint32_t)h;
+                tmem_st16(lane_base + col, hi);
+                tmem_st16(lane_base + col + 32u, mid);
+                tmem_st16(lane_base + col + 64u, lo);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                mbar_arrive(&full_a[s]);
+            }
+        }
+    } else if (warp >= kAProdWarp && warp < kAProdWarp + kAProdWarps) {
+        // ---------------- A producers: W-byte cp.async (W from the block's alignment)
+        const int pw = warp - kAProdWarp;
+        int64_t hg = 0;
+        bool ok = true;
+        for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+            const int b = find_block(p.pre, p.count, it);
+            const BatchDesc D = p.d[b];
+            const int64_t row0 = (it - p.pre[b]) * kBM;
+            const int64_t kch = D.kpad / kBK;
+            const int w = copy_width(D.A, D.ld);
+            for (int64_t kc = 0; kc < kch && ok; ++kc) {
+                for (int h = 0; h < 2; ++h, ++hg) {
+                    const int as = (int)(hg % kAStages);
+                    ok = mbar_wait(&a_empty[as], (uint32_t)((hg / kAStages) & 1) ^ 1u, &s_abort, p.err);
+                    if (!__all_sync(0xffffffffu, ok)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t dst0 = smem_u32(abuf + (size_t)as * kHalfBytes);
+                    const int64_t k0 = kc * kBK + 32 * h;
+                    if (!D.trans) {
+                        if (w == 16) load_rows<16>(D, row0, k0, 32 * pw, dst0);
+                        else if (w == 8) load_rows<8>(D, row0, k0, 32 * pw, dst0);
+                        else load_rows<4>(D, row0, k0, 32 * pw, dst0);
+                    } else {
+                        if (w == 16) load_cols<16>(D, row0, k0, 8 * pw, dst0);
+                        else if (w == 8) load_cols<8>(D, row0, k0, 8 * pw, dst0);
+                        else load_cols<4>(D, row0, k0, 8 * pw, dst0);
+                    }
+                    cp_async_arrive(&a_full[as]);
+                }
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == kBProdWarp) {
+        // ---------------- X^T producer: 16-byte cp.async, N rows x 128 bytes per chunk
+        int64_t g = 0;
+        bool ok = true;
+        for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+            const int b = find_block(p.pre, p.count, it);
+            const BatchDesc D = p.d[b];
+            const uint16_t* xt = p.xt + D.xt_off;
+            const int64_t kch = D.kpad / kBK;
+            for (int64_t kc = 0; kc < kch; ++kc, ++g) {
+                const int s = (int)(g % kStages);
+                ok = mbar_wait(&empty[s], (uint32_t)((g / kStages) & 1) ^ 1u, &s_abort, p.err);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t dst0 = smem_u32(bbuf + (size_t)s * b_stage);
+                for (int t = lane; t < p.N * 8; t += 32) {
+                    const int row = t >> 3, c = t & 7;
+                    cp_async16(dst0 + (uint32_t)row * 128u + ((uint32_t)(c ^ (row & 7)) << 4),
+                               xt + (int64_t)row * D.kpad + kc * kBK + 8 * c);
+                }
+                cp_async_arrive(&full_b[s]);
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(p.N);
+            int64_t g = 0, j = 0;
+            bool ok = true;
+            for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+                const int b = find_block(p.pre, p.count, it);
+                const int64_t kch = p.d[b].kpad / kBK;
+                const int a = (int)(j & 1);
+                if (!mbar_wait(&acce[a], (uint32_t)(((j >> 1) & 1) ^ 1), &s_abort, p.err)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(a * p.N);
+                for (int64_t kc = 0; kc < kch; ++kc, ++g) {
+                    const int s = (int)(g % kStages);
+                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                    if (!mbar_wait(&full_a[s], ph, &s_abort, p.err) || !mbar_wait(&full_b[s], ph, &s_abort, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    // X^T arrived through the generic proxy (cp.async): order it before the MMA's reads
+                    fence_proxy_async();
+                    tc_fence_after();
+                    const uint32_t bst = smem_u32(bbuf + (size_t)s * b_stage);
+                    const uint32_t ast = tmem_base + kAStageCol + 96u * (uint32_t)s;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint64_t bdesc = sw128_desc(bst + 32u * kk);
+#pragma unroll
+                        for (int term = 0; term < 3; ++term)
+                            mma_bf16_ts(d_tmem, ast + 32u * term + 8u * kk, bdesc, idesc, (kc | kk | term) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&accf[a]);
+                ++j;
+            }
+            mma_commit(&done_bar);
+            mbar_drain(&done_bar, 0);
+        }
+    } else {
+        // ---------------- epilogue warps 8..11: TMEM lanes 32*(warp%4) ..
+        const int q = warp & 3;
+        int64_t j = 0;
+        for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+            const int b = find_block(p.pre, p.count, it);
+            const int a = (int)(j & 1);
+            const bool ok = mbar_wait(&accf[a], (uint32_t)((j >> 1) & 1), &s_abort, p.err);
+            if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.ld is warp-wide
+            tc_fence_after();
+            const BatchDesc D = p.d[b];
+            const int64_t row = (it - p.pre[b]) * kBM + q * 32 + lane;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * p.N);
+            for (int c = 0; c < p.N; c += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c, v);
+                if (row < D.rows) {
+                    float* dst = p.ax + D.ax_off + row * p.ldax + p.col0 + c;
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        if (c + i < p.S) *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[a]);
+            ++j;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+// X_b^T[j][k] = bf16 normal X_b(k, col0 + j) for j < s, k < cols; zero elsewhere
+// in the nxt x kpad region (one thread per (block-relative k, group of 4 columns)).
+__global__ void gauss_xt_batched_kernel(const BatchDesc* __restrict__ d, int count, const int* __restrict__ active,
+                                        int col0, int s, int nxt, uint16_t* __restrict__ pool) {
+    const int b = blockIdx.y;
+    if (b >= count || !active[b]) return;
+    const BatchDesc D = d[b];
+    uint16_t* xt = pool + D.xt_off;
+    const int ng = nxt / 4;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < D.kpad * ng;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx % D.kpad;
+        const int g = (int)(idx / D.kpad);
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        if (k < D.cols && 4 * g < s) normals4((uint32_t)k, (uint32_t)((col0 >> 2) + g), kStreamGX, D.seed, z);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = 4 * g + e;
+            xt[(int64_t)j * D.kpad + k] = j < s ? (uint16_t)(__float_as_uint(z[e]) >> 16) : (uint16_t)0;
+        }
+    }
+}
+
+// act_pre[b] = number of 128-row tiles of the active blocks before b (one CTA).
+__global__ void __launch_bounds__(1024) compact_tiles_kernel(const BatchDesc* __restrict__ d, int count,
+                                                             const int* __restrict__ active,
+                                                             int64_t* __restrict__ act_pre) {
+    __shared__ int64_t s_part[1024];
+    const int t = threadIdx.x;
+    const int per = (count + 1023) / 1024;
+    const int b0 = t * per, b1 = min(count, b0 + per);
+    int64_t sum = 0;
+    for (int b = b0; b < b1; ++b)
+        if (active[b]) sum += (d[b].rows + kBM - 1) / kBM;
+    s_part[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {          // inclusive scan of the per-thread sums
+        const int64_t v = t >= o ? s_part[t - o] : 0;
+        __syncthreads();
+        s_part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = t > 0 ? s_part[t - 1] : 0;
+    for (int b = b0; b < b1; ++b) {
+        act_pre[b] = run;
+        if (active[b]) run += (d[b].rows + kBM - 1) / kBM;
+    }
+    if (t == 1023) act_pre[count] = s_part[1023];
+}
+
+int g_bsms = 0;
+
+}  // namespace
+
+cudaError_t launch_compact_tiles(const BatchDesc* d, int count, const int* active, int64_t* act_pre,
+                                 cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    compact_tiles_kernel<<<1, 1024, 0, st>>>(d, count, active, act_pre);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_xt_batched(const BatchDesc* d, int count, const int* active, int col0, int s, int nxt,
+                                    uint16_t* XTpool, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (s % 4 != 0 || col0 % 4 != 0 || nxt % 4 != 0 || count > 65535) return cudaErrorInvalidValue;
+    gauss_xt_batched_kernel<<<dim3(8, (unsigned)count), 256, 0, st>>>(d, count, active, col0, s, nxt, XTpool);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t* act_prefix, int64_t max_items,
+                                    const uint16_t* XTpool, int s, float* AXpool, int64_t ldax, int col0,
+                                    int* err_flag, cudaStream_t st) {
+    if (max_items <= 0 || s <= 0 || count <= 0) return cudaSuccess;
+    if (s > 256 || s % 8 != 0 || col0 % 4 != 0 || ldax % 4 != 0 || !err_flag) return cudaErrorInvalidValue;
+    TcBatchParams p;
+    p.d = d;
+    p.count = count;
+    p.pre = act_prefix;
+    p.xt = XTpool;
+    p.N = tc_mma_n(s);
+    p.S = s;
+    p.ax = AXpool;
+    p.ldax = ldax;
+    p.col0 = col0;
+    p.err = err_flag;
+    const size_t smem = (size_t)kHalfBytes * kAStages + (((size_t)p.N * 128 + 1023) & ~(size_t)1023) * kStages + 1024;
+    cudaError_t e = cudaFuncSetAttribute(right_tc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (!g_bsms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_bsms, cudaDevAttrMultiProcessorCount, dev);
+        if (!g_bsms) g_bsms = 148;
+    }
+    const int64_t grid = std::min<int64_t>(max_items, g_bsms);
+    right_tc_batched_kernel<<<(unsigned)grid, kThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace re

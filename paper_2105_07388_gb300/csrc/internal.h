@@ -33,6 +33,8 @@ struct BatchDesc {
     int64_t ax_off;     // offset (floats) of this block's AX region (rows x ldax) in the AX pool
     int64_t x_off;      // offset (floats) of this block's X region (cols x xs) in the X pool
     uint64_t seed;
+    int64_t xt_off;     // offset (BF16 elements) of this block's X^T region (nxt x kpad) in the X^T pool
+    int64_t kpad;       // cols rounded up to a multiple of 64
 };
 
 // ---- embeddings (embed.cu) ----------------------------------------------------
@@ -83,6 +85,22 @@ size_t left_tc_part_floats(int64_t M, int R, int S);
 cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0, int R,
                                     int col0, int S, float* part, size_t part_cap, int* err_flag, int* splits_out,
                                     cudaStream_t st);
+
+// Batched right sketch on the tensor cores (batched_tc.cu), BF16x3 as in
+// right_tc_kernel: for every active block b and each of its 128-row tiles,
+// AX_b[:, col0:col0+s] = A_b X_b with X_b^T BF16 in the X^T pool (nxt =
+// tc_mma_n(s) rows of kpad, rows >= s zero).  act_prefix (count + 1 entries,
+// from launch_compact_tiles) numbers the tiles of the active blocks; max_items
+// bounds their number.  A is loaded with asynchronous copies of 16, 8 or 4
+// bytes, so any row pitch works.
+cudaError_t launch_compact_tiles(const BatchDesc* d, int count, const int* active, int64_t* act_prefix,
+                                 cudaStream_t st);
+cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t* act_prefix, int64_t max_items,
+                                    const uint16_t* XTpool, int s, float* AXpool, int64_t ldax, int col0,
+                                    int* err_flag, cudaStream_t st);
+// X_b^T (BF16, nxt rows x kpad) of columns [col0, col0+s) for every active block.
+cudaError_t launch_gauss_xt_batched(const BatchDesc* d, int count, const int* active, int col0, int s, int nxt,
+                                    uint16_t* XTpool, cudaStream_t st);
 
 // Batched right sketch: for every active block b and each of its BM-row tiles
 // (tile_prefix[b] .. tile_prefix[b+1]-1 are b's work items), AX_b[:, col0:col0+s]

@@ -49,6 +49,18 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait that lets the thread sleep until the phase completes or about 20 us
+// pass (a waiting warp then takes no issue slots from the working ones)
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait; returns false (and raises the abort flag) on expiry or when
 // another role has already aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
@@ -56,7 +68,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = now_ns();
     while (true) {
-        if (mbar_test(bar, parity)) return true;
+        if (mbar_test_sleep(bar, parity)) return true;
         if (*abort_flag) return false;
         if (now_ns() - t0 > kWaitNs) {
             *abort_flag = 1;

@@ -12,13 +12,15 @@ pytestmark = pytest.mark.gpu
 SIGMA_TOL = 1e-4
 
 
-@pytest.fixture(scope="module")
-def h():
+@pytest.fixture(scope="module", params=[rk.RE_PREC_FP32, rk.RE_PREC_BF16X3], ids=["fp32", "bf16x3"])
+def h(request):
+    """FP32 CUDA-core sketch and BF16x3 tensor-core sketch (4-byte asynchronous
+    copies, any row pitch, transposed blocks included)."""
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from paper_2105_07388_gb300 import build
     build.build()
-    hd = rk.re_create(0, rk.make_opts(s_max=128))
+    hd = rk.re_create(0, rk.make_opts(s_max=128, precision=request.param))
     yield hd
     rk.re_destroy(hd)
 
