@@ -400,19 +400,26 @@ def bench_batched(rk, local, stream, args):
     blocks = [wl.kernel_block(m, n, seed=10_000 + i, device="cuda") for i, (m, n) in enumerate(shapes)]
     torch.cuda.synchronize()
     total_bytes = 4.0 * sum(m * n for m, n in shapes)
-    hb = rk.re_create(local, rk.make_opts(s_max=128))
-    rk.re_stats_enable(hb, False)
-    res, _ = rk.re_rank_estimate_batched(hb, blocks, 1e-6, rk.RE_GAUSSIAN, 500, stream=stream)   # autotune + capture
-    torch.cuda.synchronize()
     steps = max(1, min(args.steps, 3))
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        res, _ = rk.re_rank_estimate_batched(hb, blocks, 1e-6, rk.RE_GAUSSIAN, 500, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+
+    def run_batched(precision):
+        hb = rk.re_create(local, rk.make_opts(s_max=128, precision=precision))
+        rk.re_stats_enable(hb, False)
+        r, _ = rk.re_rank_estimate_batched(hb, blocks, 1e-6, rk.RE_GAUSSIAN, 500, stream=stream)   # capture
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            r, _ = rk.re_rank_estimate_batched(hb, blocks, 1e-6, rk.RE_GAUSSIAN, 500, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rk.re_destroy(hb)
+        return r, e0.elapsed_time(e1) / steps
+
+    # split precision on the tensor cores (the batched form), and the same on CUDA cores
+    res, ms = run_batched(rk.RE_PREC_BF16X3)
+    res32, ms32 = run_batched(rk.RE_PREC_FP32)
     passes = sum(r.passes for r in res)
     read_bytes = sum(4.0 * shapes[i][0] * shapes[i][1] * res[i].passes for i in range(count))
     # plain per-matrix form on a sample of blocks, same seeds and widths
@@ -428,11 +435,13 @@ def bench_batched(rk, local, stream, args):
     torch.cuda.synchronize()
     plain_ms_each = (time.perf_counter() - t0) * 1e3 / len(sample)
     rk.re_destroy(hp)
-    rk.re_destroy(hb)
     del blocks
     torch.cuda.empty_cache()
     return {"workload": f"{count} kernel blocks 1/|x-y|, m,n ~ U[256,4096], eps=1e-6, Gaussian, s<=128",
+            "form": "BF16x3 tensor-core sketch, one graph launch per batch",
             "blocks_bytes": total_bytes, "ms_per_batch": ms,
+            "fp32_ms_per_batch": ms32,
+            "fp32_same_rank_fraction": sum(int(a.rank == b.rank) for a, b in zip(res, res32)) / count,
             "rank_estimates_per_s": count * 1e3 / ms,
             "sketch_gbs": read_bytes / (ms * 1e-3) / 1e9,
             "mean_passes": passes / count,

@@ -24,6 +24,7 @@
 // column blocks per CTA, blocks rotating through the cluster each round).
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 
 #include <cooperative_groups.h>
@@ -785,52 +786,69 @@ cudaError_t launch_cluster_sigma(const double* core, int r2, int s, int64_t ld, 
 }
 
 // Step 8 (device): scaled sigma, threshold rank, gap index.
+// One warp: lanes take indices i = lane, lane + 32, ...; the threshold rank is the
+// smallest index with sigma^ <= tau and the gap the largest ratio, smallest index on
+// ties (the same values and decisions as a sequential scan).
 __global__ void readoff_kernel(const double* __restrict__ sigma, int r1, double scale, double eps,
                                double norm_a, const int* __restrict__ status_in,
                                DevReadoff* __restrict__ out, double* __restrict__ sigma_scaled) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     DevReadoff r;
     // status_in[0]: small-core step (RE_OK / RE_ERR_NONFINITE); status_in[1]: set
-    // by the tensor-core right sketch when one of its bounded waits expired
+    // by a tensor-core kernel when one of its bounded waits expired
     r.status = status_in ? status_in[0] : RE_OK;
     if (status_in && status_in[1]) r.status = RE_ERR_TIMEOUT;
     if (status_in && status_in[3]) {
         // the core step certified that no trusted sigma^ reaches the threshold
-        r.sweeps = 0;
-        r.rank = -1;
-        r.gap_index = 0;
-        r.gap_ratio = 0.0;
-        r.tau = 0.0;
-        *out = r;
+        if (lane == 0) {
+            r.sweeps = 0;
+            r.rank = -1;
+            r.gap_index = 0;
+            r.gap_ratio = 0.0;
+            r.tau = 0.0;
+            *out = r;
+        }
         return;
     }
     r.sweeps = status_in ? status_in[2] : 0;
-    for (int i = 0; i < r1; ++i) sigma_scaled[i] = sigma[i] * scale;
-    const double ref = norm_a > 0.0 ? norm_a : sigma_scaled[0];
+    const double ref = norm_a > 0.0 ? norm_a : sigma[0] * scale;
     r.tau = eps * ref;
-    r.rank = -1;
-    for (int i = 0; i < r1; ++i) {
-        if (sigma_scaled[i] <= r.tau) {
-            r.rank = i;
-            break;
-        }
-    }
+    int first = INT_MAX;
     int gi = r1 >= 1 ? 1 : 0;
     double gr = r1 >= 2 ? -1.0 : 1.0;
-    for (int i = 1; i < r1; ++i) {
-        const double a = sigma_scaled[i - 1], b = sigma_scaled[i];
-        double ratio;
-        if (b > 0.0) ratio = a / b;
-        else if (a > 0.0) ratio = INFINITY;
-        else ratio = 1.0;
-        if (ratio > gr) {
-            gr = ratio;
-            gi = i;
+    for (int i = lane; i < r1; i += 32) {
+        const double v = sigma[i] * scale;
+        sigma_scaled[i] = v;
+        if (v <= r.tau && i < first) first = i;
+        if (i >= 1) {
+            const double a = sigma[i - 1] * scale;
+            double ratio;
+            if (v > 0.0) ratio = a / v;
+            else if (a > 0.0) ratio = INFINITY;
+            else ratio = 1.0;
+            if (ratio > gr || (ratio == gr && i < gi)) {
+                gr = ratio;
+                gi = i;
+            }
         }
     }
-    r.gap_index = gi;
-    r.gap_ratio = gr;
-    *out = r;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+        const double g2 = __shfl_xor_sync(0xffffffffu, gr, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, gi, o);
+        if (g2 > gr || (g2 == gr && i2 < gi)) {
+            gr = g2;
+            gi = i2;
+        }
+    }
+    if (lane == 0) {
+        r.rank = first == INT_MAX ? -1 : first;
+        r.gap_index = gi;
+        r.gap_ratio = gr;
+        *out = r;
+    }
 }
 
 constexpr size_t kSmemLimit = 210 * 1024;
