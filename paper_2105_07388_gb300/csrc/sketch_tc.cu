@@ -9,10 +9,6 @@
 // accumulated in one TMEM accumulator.
 //
 // Persistent kernel, one CTA per SM, 128-row M tiles, K chunks of 64:
-//   warp 12     TMA producer of A: FP32 half chunks (128 rows x 32 k, 128B
-//               swizzle, zero fill past the edges) into an 8 deep ring, so up
-//               to 128 KB of A are in flight per SM.
-//   warp 13     TMA producer of X^T: BF16 chunk (N rows x 64 k, 128B swizzle).
 //   warps 0-7   converters: warp (q, h) reads, for row 32q + lane, the 32 FP32
 //               values of half h of a chunk (conflict-free 16-byte loads of the
 //               swizzled tile), splits them exactly into three BF16 terms and
@@ -20,10 +16,14 @@
 //               MMA takes them as its A operand.  The split terms never touch
 //               shared memory, which then carries only the TMA writes, the
 //               converter reads and the MMA's reads of X^T.
+//   warps 8-11  epilogue: tcgen05.ld (32 lanes x 16 columns) -> FP32 rows of AX.
+//   warp 12     TMA producer of A: FP32 half chunks (128 rows x 32 k, 128B
+//               swizzle, zero fill past the edges) into an 8 deep ring, so up
+//               to 128 KB of A are in flight per SM.
+//   warp 13     TMA producer of X^T: BF16 chunk (N rows x 64 k, 128B swizzle).
 //   warp 14     TMEM allocation; one elected thread issues 3 x 4 tcgen05.mma
 //               (M=128, N, K=16, kind::f16 BF16 -> FP32, A from TMEM) per chunk
 //               and tcgen05.commit to release stages / publish accumulators.
-//   warps 8-11  epilogue: tcgen05.ld (32 lanes x 16 columns) -> FP32 rows of AX.
 // TMEM (512 columns): accumulators in [0, 256) -- double buffered for N <= 128
 // so the epilogue of one tile overlaps the MMAs of the next -- and two A stages
 // of 96 columns from column 256.  Every mbarrier wait is bounded in time: on
@@ -46,12 +46,13 @@ using namespace tc;
 
 constexpr int kBM = 128;           // rows per M tile (UMMA M)
 constexpr int kBK = 64;            // K elements per chunk (one 128-byte swizzle row)
-constexpr int kConvWarps = 8;
+constexpr int kConvParts = 1;                                  // converter warps per (lane quarter, half chunk); 2 measured slower
+constexpr int kConvWarps = 8 * kConvParts;
 constexpr int kEpiWarps = 4;
-constexpr int kThreads = (kConvWarps + kEpiWarps + 3) * 32;   // 480
-constexpr int kAProdWarp = kConvWarps + kEpiWarps;             // 12
-constexpr int kBProdWarp = kAProdWarp + 1;                     // 13
-constexpr int kMmaWarp = kBProdWarp + 1;                       // 14
+constexpr int kThreads = (kConvWarps + kEpiWarps + 3) * 32;
+constexpr int kAProdWarp = kConvWarps + kEpiWarps;
+constexpr int kBProdWarp = kAProdWarp + 1;
+constexpr int kMmaWarp = kBProdWarp + 1;
 constexpr int kHalfWarps = kConvWarps / 2;                     // converter warps per half chunk
 constexpr uint32_t kHalfBytes = kBM * 32 * 4;                  // 16 KB FP32 half chunk
 constexpr int kMaxAStages = 8;                                 // FP32 half-chunk ring depth
@@ -138,9 +139,10 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     const int64_t nseg = total_chunks > 0 ? (c_end - 1) / K - t_first + 1 : 0;
 
     if (warp < kConvWarps) {
-        // ---------------- converters: warp (q, h) owns TMEM lanes 32q.. (rows 32q + lane)
-        // and half h of every chunk; one FP32 row segment of 32 k per thread.
-        const int q = warp & 3, h = warp >> 2;
+        // ---------------- converters: warp (q, h, part) owns TMEM lanes 32q.. (rows 32q + lane)
+        // and k = 32h + (32 / kConvParts) part .. of every chunk: one FP32 row piece per thread.
+        constexpr int KW = 32 / kConvParts;              // k per converter warp and chunk
+        const int q = warp & 3, hp = warp >> 2, h = hp / kConvParts, part = hp % kConvParts;
         const int r = 32 * q + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         for (int64_t g = 0; g < total_chunks; ++g) {
@@ -154,24 +156,27 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
             // row r of the 128B-swizzled half tile: 16-byte chunk c sits at slot c ^ (r & 7);
             // the 32 rows of a warp cover every bank four times per load (no conflicts)
             const unsigned char* src = abuf + (size_t)as * kHalfBytes + (size_t)r * 128;
-            float4 v[8];
+            float4 v[KW / 4];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const float4*>(src + ((c ^ (r & 7)) << 4));
+            for (int c = 0; c < KW / 4; ++c) {
+                const int cc = (KW / 4) * part + c;
+                v[c] = *reinterpret_cast<const float4*>(src + ((cc ^ (r & 7)) << 4));
+            }
             mbar_arrive(&a_empty[as]);
-            uint32_t hi[16], mid[16], lo[16];
+            uint32_t hi[KW / 2], mid[KW / 2], lo[KW / 2];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < KW / 4; ++c) {
                 split3(v[c].x, v[c].y, hi[2 * c], mid[2 * c], lo[2 * c]);
                 split3(v[c].z, v[c].w, hi[2 * c + 1], mid[2 * c + 1], lo[2 * c + 1]);
             }
             tc_fence_after();
             // A operand layout in TMEM (M = 128): lane = row, 32-bit column = two
             // consecutive k (lower k in the low half); term t of stage s starts at
-            // column kAStageCol + 96 s + 32 t, half h at +16 h
-            const uint32_t col = kAStageCol + 96u * (uint32_t)s + 16u * (uint32_t)h;
-            tmem_st16(lane_base + col, hi);
-            tmem_st16(lane_base + col + 32u, mid);
-            tmem_st16(lane_base + col + 64u, lo);
+            // column kAStageCol + 96 s + 32 t, and k of this warp at +16 h + (KW / 2) part
+            const uint32_t col = kAStageCol + 96u * (uint32_t)s + 16u * (uint32_t)h + (uint32_t)(KW / 2) * part;
+            tmem_st<KW / 2>(lane_base + col, hi);
+            tmem_st<KW / 2>(lane_base + col + 32u, mid);
+            tmem_st<KW / 2>(lane_base + col + 64u, lo);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             mbar_arrive(&full_a[s]);
