@@ -261,10 +261,12 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
     if (e == cudaSuccess)
         e = re::launch_perm(seed, re::kStreamPX, P.nbits, c0, cnt, static_cast<int*>(h->px.p), st);
     stage_end(h, st, g, kStageOther);
+    if (int r = ensure(h->status, 64)) return r;
     cudaEvent_t a = stage_begin(h, st);
     if (e == cudaSuccess)
         e = re::launch_right_srht(P.A, static_cast<const uint32_t*>(h->dx.p),
-                                  static_cast<const int*>(h->px.p), cnt, AX + c0, ld_ax, st);
+                                  static_cast<const int*>(h->px.p), cnt, AX + c0, ld_ax, st,
+                                  static_cast<int*>(h->status.p) + 1);
     if (e != cudaSuccess) return cuda_fail(e, "right sketch (SRHT)");
     stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 0),
               (double)P.A.rows * (double)P.n_pad * (double)P.nbits);

@@ -112,7 +112,7 @@ cudaError_t launch_right_simt_batched(const BatchDesc* d, int count, const int64
 // ---- right sketch, SRHT (sketch_srht.cu) --------------------------------------
 // C[:, 0:s] = A_oriented * D H S^T with sampled Hadamard columns cols[0..s).
 cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int* cols, int s,
-                              float* C, int64_t ldc, cudaStream_t st);
+                              float* C, int64_t ldc, cudaStream_t st, int* err = nullptr);
 
 // ---- right sketch, BF16x3 tensor cores (sketch_tc.cu) ------------------------------
 bool tc_supported(const MatView& A);

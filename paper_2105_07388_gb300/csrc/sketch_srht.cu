@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace re {
 
@@ -259,6 +260,120 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_vec_kernel(c
     }
 }
 
+// Double-buffered form of srht_vec_kernel for rows of a multiple of 4 floats:
+// one bulk copy (cp.async.bulk, completion on an mbarrier) brings row i+1 into
+// the second row buffer while row i is transformed; phase 1 then reads the row
+// from shared memory (conflict-free 16-byte loads), and the same buffer serves
+// the two transposes.  Waits are bounded in time; on expiry *err is set and the
+// CTA drains its copy and returns.
+template <int L>
+__global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __restrict__ A, int64_t lda,
+                                                                 int64_t M, int64_t N,
+                                                                 const uint32_t* __restrict__ dbits,
+                                                                 const int* __restrict__ cols, int s,
+                                                                 float* __restrict__ C, int64_t ldc, int* err) {
+    constexpr int T = 1 << (L - 5);
+    constexpr int NP = 1 << L;
+    extern __shared__ __align__(128) float4 smem4[];
+    float* rows = reinterpret_cast<float*>(smem4);          // 2 x NP floats
+    int* scol = reinterpret_cast<int*>(rows + 2 * NP);
+    __shared__ __align__(8) uint64_t full[2];
+    const int j = threadIdx.x;
+    const uint32_t row_bytes = (uint32_t)(N * 4);
+    const int64_t nwords = (N + 31) / 32;
+    if (j == 0) {
+        tc::mbar_init(&full[0], 1);
+        tc::mbar_init(&full[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int k = j; k < s; k += T) scol[k] = cols[k];
+    __syncthreads();
+    auto issue = [&](int64_t r, int b) {
+        tc::fence_proxy_async();                             // earlier generic accesses of the buffer first
+        tc::mbar_arrive_expect_tx(&full[b], row_bytes);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                tc::smem_u32(rows + (size_t)b * NP)),
+            "l"(A + r * lda), "r"(row_bytes), "r"(tc::smem_u32(&full[b]))
+            : "memory");
+    };
+    if (j == 0 && blockIdx.x < M) issue(blockIdx.x, 0);
+    int it = 0;
+    for (int64_t row = blockIdx.x; row < M; row += gridDim.x, ++it) {
+        const int b = it & 1;
+        float* buf = rows + (size_t)b * NP;
+        if (j == 0 && row + gridDim.x < M) issue(row + gridDim.x, b ^ 1);
+        // wait for this row's copy: the (it >> 1)-th completion of full[b]
+        bool ok = true;
+        {
+            const uint32_t par = (uint32_t)((it >> 1) & 1);
+            if (!tc::mbar_test(&full[b], par)) {
+                const unsigned long long t0 = tc::now_ns();
+                while (!tc::mbar_test_sleep(&full[b], par)) {
+                    if (tc::now_ns() - t0 > tc::kWaitNs) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            if (j == 0) {
+                // copies in flight: this row's (completion it >> 1 of full[b]) and, if
+                // issued, the next row's (completion (it + 1) >> 1 of full[b ^ 1])
+                if (err) atomicExch(err, 1);
+                tc::mbar_drain(&full[b], (uint32_t)((it >> 1) & 1));
+                if (row + gridDim.x < M) tc::mbar_drain(&full[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            return;
+        }
+        float x[32];
+        // phase 1: register e = 4 r + q  <->  logical bits (q: 0, 1; r: L-3 .. L-1)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int idx = r * 4 * T + 4 * j;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (idx < N) v = *reinterpret_cast<const float4*>(buf + idx);
+            const uint32_t w = (idx >> 5) < nwords ? __ldg(dbits + (idx >> 5)) >> (idx & 31) : 0u;
+            x[4 * r + 0] = __uint_as_float(__float_as_uint(v.x) ^ ((w & 1u) << 31));
+            x[4 * r + 1] = __uint_as_float(__float_as_uint(v.y) ^ (((w >> 1) & 1u) << 31));
+            x[4 * r + 2] = __uint_as_float(__float_as_uint(v.z) ^ (((w >> 2) & 1u) << 31));
+            x[4 * r + 3] = __uint_as_float(__float_as_uint(v.w) ^ (((w >> 3) & 1u) << 31));
+        }
+        fwht32<5>(x);
+        __syncthreads();                                      // every phase-1 read of buf is done
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            *reinterpret_cast<float4*>(buf + phys_sw(r * 4 * T + 4 * j)) =
+                make_float4(x[4 * r], x[4 * r + 1], x[4 * r + 2], x[4 * r + 3]);
+        __syncthreads();
+        {
+            const int base = (j >> 2) * 128 + (j & 3);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) x[c] = buf[phys_sw(base + 4 * c)];
+            fwht32<5>(x);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) buf[phys_sw(base + 4 * c)] = x[c];
+        }
+        __syncthreads();
+        {
+            const int base = (j >> 7) * 4096 + (j & 127);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) x[k] = buf[phys_sw(base + 128 * k)];
+            fwht32<L - 10>(x);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) buf[phys_sw(base + 128 * k)] = x[k];
+        }
+        __syncthreads();
+        for (int k = j; k < s; k += T) C[row * ldc + k] = buf[phys_sw(scol[k])];
+        __syncthreads();                                      // buf is free for the copy two rows on
+    }
+}
+
+template <int L>
+cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C, int64_t ldc,
+                        int* err, cudaStream_t st);
+
 template <int L>
 cudaError_t launch_vec(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
                        int64_t ldc, cudaStream_t st);
@@ -292,6 +407,23 @@ cudaError_t launch_vec(const MatView& A, const uint32_t* dbits, const int* cols,
     return cudaGetLastError();
 }
 
+template <int L>
+cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C, int64_t ldc,
+                        int* err, cudaStream_t st) {
+    constexpr int T = 1 << (L - 5);
+    const size_t smem = sizeof(float) * ((size_t)2 << L) + sizeof(int) * (size_t)s;
+    auto k = srht_bulk_kernel<L>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(A.rows, (int64_t)std::max(per_sm, 1) * sm_count()));
+    k<<<(unsigned)grid, T, smem, st>>>(static_cast<const float*>(A.ptr), A.ld, A.rows, A.cols, dbits, cols, s, C,
+                                       ldc, err);
+    return cudaGetLastError();
+}
+
 template <int LOGN, bool TRANS, typename TA>
 cudaError_t launch_reg(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
                        int64_t ldc, cudaStream_t st) {
@@ -316,9 +448,15 @@ cudaError_t launch_reg(const MatView& A, const uint32_t* dbits, const int* cols,
 
 template <bool TRANS, typename TA>
 cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
-                          int64_t ldc, cudaStream_t st) {
+                          int64_t ldc, int* err, cudaStream_t st) {
     const int need = pow2_bits(A.cols);
     if constexpr (!TRANS && sizeof(TA) == 4) {
+        if (err && need >= 12 && need <= 14 && (A.ld % 4) == 0 && (A.cols % 4) == 0 &&
+            (reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0) {
+            if (need == 12) return launch_bulk<12>(A, dbits, cols, s, C, ldc, err, st);
+            if (need == 13) return launch_bulk<13>(A, dbits, cols, s, C, ldc, err, st);
+            return launch_bulk<14>(A, dbits, cols, s, C, ldc, err, st);
+        }
         if (need >= 12 && need <= 14 && (A.ld % 4) == 0 && (reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0) {
             if (need == 12) return launch_vec<12>(A, dbits, cols, s, C, ldc, st);
             if (need == 13) return launch_vec<13>(A, dbits, cols, s, C, ldc, st);
@@ -343,13 +481,13 @@ cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* co
 }  // namespace
 
 cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int* cols, int s,
-                              float* C, int64_t ldc, cudaStream_t st) {
+                              float* C, int64_t ldc, cudaStream_t st, int* err) {
     if (s <= 0 || A.rows <= 0) return cudaSuccess;
     if (A.dtype == RE_F32)
-        return A.trans ? launch_srht_t<true, float>(A, dbits, cols, s, C, ldc, st)
-                       : launch_srht_t<false, float>(A, dbits, cols, s, C, ldc, st);
-    return A.trans ? launch_srht_t<true, double>(A, dbits, cols, s, C, ldc, st)
-                   : launch_srht_t<false, double>(A, dbits, cols, s, C, ldc, st);
+        return A.trans ? launch_srht_t<true, float>(A, dbits, cols, s, C, ldc, err, st)
+                       : launch_srht_t<false, float>(A, dbits, cols, s, C, ldc, err, st);
+    return A.trans ? launch_srht_t<true, double>(A, dbits, cols, s, C, ldc, err, st)
+                   : launch_srht_t<false, double>(A, dbits, cols, s, C, ldc, err, st);
 }
 
 }  // namespace re

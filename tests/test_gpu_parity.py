@@ -123,6 +123,23 @@ def test_right_sketch_parity(h, m, n, dtype, kind):
         assert np.all(AX[:, :col0].cpu().numpy() == 0)
 
 
+def test_srht_row_pitch_padded(h):
+    """n not a multiple of 4 inside a wider, aligned row pitch: the register FWHT
+    without bulk row copies (the bulk path needs whole 16-byte rows)."""
+    m, n, ld = 5000, 4094, 4096                         # m >= n: rows of A are sketched
+    gen = np.random.default_rng(17)
+    full = gen.standard_normal((m, ld)).astype(np.float32)
+    Ad = torch.from_numpy(full).cuda()[:, :n]
+    assert Ad.stride(0) == ld
+    A64 = full[:, :n].astype(np.float64)
+    AX = torch.zeros(m, 32, dtype=torch.float32, device="cuda")
+    rk.re_sketch_apply(h, Ad, 0, 32, rk.RE_SRHT, 4242, AX)
+    ref = alg.right_sketch(A64, 32, rk.RE_SRHT, 4242, 0)
+    X = alg.embeddings(rk.RE_SRHT, n, m, 32, 4242, col0=0, r2=0)[0]
+    got = AX.double().cpu().numpy()
+    assert np.all(np.abs(got - ref) <= _right_bound(A64, X))
+
+
 @pytest.mark.parametrize("kind", [rk.RE_GAUSSIAN, rk.RE_SRHT])
 def test_core_parity_with_appending(h, kind):
     m, n = 2000, 700
