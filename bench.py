@@ -129,6 +129,19 @@ def build_matrix(w, device):
     return A
 
 
+def host_cpu() -> str:
+    """Architecture and model name of the host cores (for the CPU baseline)."""
+    import platform
+    import subprocess
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        model = next((l.split(":", 1)[1].strip() for l in out.splitlines() if l.startswith("Model name")), "")
+    except Exception:
+        pass
+    return f"{platform.machine()} {model}".strip()
+
+
 def cpu_oracle_run(A_host: np.ndarray, w, kind: int, budget_s: float = 20.0):
     """Time the FP64 oracle on a bounded row sample; returns (GB/s, info)."""
     from oracle import algorithm1 as alg
@@ -165,7 +178,10 @@ def main():
            if args.workload in ("large", "medium") else
            f"single matrix {w['m']}x{w['n']}, sigma=10^-(i-1)/10, eps={w['eps']}",
            "m": w["m"], "n": w["n"], "dtype_A": "f32", "eps": w["eps"], "sketch": args.kind,
-           "precision": args.precision, "l2": "inputs larger than L2 (4 GiB A), no flush",
+           "precision": args.precision,
+           "l2": (f"inputs larger than L2 ({4 * w['m'] * w['n'] / 2**30:.2f} GiB A), no flush"
+                  if 4 * w["m"] * w["n"] > 129e6 else
+                  f"A ({4 * w['m'] * w['n'] / 2**20:.0f} MiB) fits in L2: not a headline workload"),
            "parallelism": f"replicas x{args.gpus}"}
 
     if args.impl == "reference":
@@ -192,7 +208,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": cfg,
                 "cpu_baseline": {"kind": "oracle", "value": value, "unit": "GB/s",
-                                 "cores": os.cpu_count(),
+                                 "cores": os.cpu_count(), "cpu": host_cpu(),
                                  "sample": f"first {info['rows']} rows x {info['cols']} of A, "
                                            f"full doubling ladder ({info['passes']} passes)"},
                 "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
@@ -378,7 +394,7 @@ def main():
         A_host = A.cpu().numpy()
         v, info = cpu_oracle_run(A_host, w, kind_code, budget_s=20.0)
         line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": os.cpu_count(),
-                                "kind": "oracle",
+                                "kind": "oracle", "cpu": host_cpu(),
                                 "sample": f"first {info['rows']} rows x {info['cols']} of A, "
                                           f"full doubling ladder, {info['runs']} runs in "
                                           f"{info['seconds']:.1f} s"}
