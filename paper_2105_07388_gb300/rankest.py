@@ -256,6 +256,12 @@ def re_sketch_apply(h: int, A, col0: int, s: int, sketch_kind: int, seed: int, A
                     stream=None) -> None:
     m, n = A.shape
     assert A.stride(1) == 1 and AX.stride(1) == 1
+    # the library writes rows max(m, n) of AX (A^T is sketched when m < n) and the
+    # leading 2 (col0 + s) x (col0 + s) block of core
+    if AX.shape[0] < max(m, n) or AX.shape[1] < col0 + s:
+        raise ValueError(f"AX must be at least {max(m, n)} x {col0 + s}, got {tuple(AX.shape)}")
+    if core is not None and (core.shape[0] < 2 * (col0 + s) or core.shape[1] < col0 + s):
+        raise ValueError(f"core must be at least {2 * (col0 + s)} x {col0 + s}, got {tuple(core.shape)}")
     ld_core = core.stride(0) if core is not None else 0
     _check(lib().re_sketch_apply(h, _ptr(A), _dtype_code(A), m, n, A.stride(0), col0, s,
                                  sketch_kind, seed, _ptr(AX), AX.stride(0), _ptr(core), ld_core,
@@ -299,6 +305,10 @@ def re_sketch_apply_noalloc(A, col0: int, s: int, seed: int, AX, core=None, stre
     """Gaussian sketch step without device allocation (static 16 MiB scratch, no handle)."""
     m, n = A.shape
     assert A.stride(1) == 1 and AX.stride(1) == 1
+    if AX.shape[0] < max(m, n) or AX.shape[1] < col0 + s:
+        raise ValueError(f"AX must be at least {max(m, n)} x {col0 + s}, got {tuple(AX.shape)}")
+    if core is not None and (core.shape[0] < 2 * (col0 + s) or core.shape[1] < col0 + s):
+        raise ValueError(f"core must be at least {2 * (col0 + s)} x {col0 + s}, got {tuple(core.shape)}")
     ld_core = core.stride(0) if core is not None else 0
     _check(lib().re_sketch_apply_noalloc(_ptr(A), _dtype_code(A), m, n, A.stride(0), col0, s, seed,
                                          _ptr(AX), AX.stride(0), _ptr(core), ld_core,
