@@ -83,7 +83,12 @@ typedef struct {
     int y_kind;      /* left embedding kind; -1 = same as the right one (default -1) */
     double norm_a;   /* > 0: use as ||A|| in the threshold; otherwise sigma^_1 (step 8) */
     int learned;     /* 1: let the sketch-size proposal network pick the next width (default 0) */
-    int reserved[7];
+    /* Test hook for the failure path (default 0; no counterpart in the paper): when
+     * 1, CTA 0 of the tensor-core right sketch withholds its first A tile, so its
+     * bounded waits expire (about 2 s); the call then returns RE_ERR_TIMEOUT and the
+     * CUDA context stays usable.  Never set outside tests. */
+    int test_drop_load;
+    int reserved[6];
 } re_opts;
 
 /* Outcome of one estimate.  sigma values go to a separate caller buffer. */

@@ -233,7 +233,8 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
             cudaEvent_t a = stage_begin(h, st);
             int nl = 0;
             e = re::launch_right_tc(P.A, static_cast<const uint16_t*>(h->xt.p), kpad, cnt,
-                                    AX + c0, ld_ax, static_cast<int*>(h->status.p) + 1, st, &nl);
+                                    AX + c0, ld_ax, static_cast<int*>(h->status.p) + 1, st, &nl,
+                                    h->opts.test_drop_load);
             if (e != cudaSuccess) return cuda_fail(e, "right sketch (tensor cores)");
             stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 2), 3.0 * 2.0 * P.A.rows * P.A.cols * cnt);
             h->stats.launches += 1 + nl;
@@ -478,6 +479,7 @@ int check_opts(const re_opts* o) {
         return fail(RE_ERR_ARG, "unknown precision");
     if (o->y_kind < -1 || o->y_kind > RE_SRHT) return fail(RE_ERR_ARG, "unknown y_kind");
     if (o->learned != 0 && o->learned != 1) return fail(RE_ERR_ARG, "learned must be 0 or 1");
+    if (o->test_drop_load != 0 && o->test_drop_load != 1) return fail(RE_ERR_ARG, "test_drop_load must be 0 or 1");
     return RE_OK;
 }
 

@@ -119,7 +119,8 @@ bool tc_supported(const MatView& A);
 // MMA N used for s output columns (>= 16, multiple of 16); X^T needs that many rows.
 int tc_mma_n(int s);
 cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, int s, float* C,
-                            int64_t ldc, int* err_flag, cudaStream_t st, int* launches = nullptr);
+                            int64_t ldc, int* err_flag, cudaStream_t st, int* launches = nullptr,
+                            int drop_first = 0);
 
 // ---- small core singular values (core_svd.cu) ----------------------------------
 size_t svd_workspace_bytes(int r2, int s);

@@ -204,6 +204,9 @@ __global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_cons
             for (int64_t hg = 0; hg < 2 * nchunks; ++hg) {
                 const int as = (int)(hg % kLAStages);
                 if (!mbar_wait(&a_empty[as], (uint32_t)((hg / kLAStages) & 1) ^ 1u, &s_abort, p.err)) break;
+                // the workers read this stage through the generic proxy; order those reads
+                // before the TMA (async proxy) overwrites it
+                fence_proxy_async();
                 mbar_arrive_expect_tx(&a_full[as], half_bytes);
                 tma_load_2d(abuf + (size_t)as * a_stage, &amap, mt * kLBM, (int)(i_begin + 32 * hg), &a_full[as]);
                 ++issued;

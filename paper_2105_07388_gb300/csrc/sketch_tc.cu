@@ -70,10 +70,10 @@ struct TcParams {
     int64_t ldc;
     int S;            // valid output columns
     int N;            // MMA N (>= 16, multiple of 16)
-    int astages;      // FP32 half-chunk ring depth
     int64_t tiles;
     int64_t kchunks;
     int* err;
+    int drop_first;   // test hook: CTA 0 withholds its first A half chunk
 };
 
 __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_constant__ CUtensorMap amap,
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int NA = p.astages;
+    constexpr int NA = kMaxAStages;                  // compile time: ring indices are shifts
     const int nacc = p.N <= 128 ? 2 : 1;            // accumulator buffers in TMEM
     const uint32_t b_bytes = (uint32_t)p.N * kBK * 2;
     const uint32_t b_stage = (b_bytes + 1023u) & ~1023u;
@@ -184,31 +184,41 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     } else if (warp == kAProdWarp) {
         // ---------------- TMA producer of A half chunks
         if (lane == 0) {
+            const bool drop0 = p.drop_first && blockIdx.x == 0;   // its converters' waits expire
             int64_t issued = 0;
+            int64_t tile = c_begin / K, kc = c_begin % K;   // stepped, no division in the loop
             for (int64_t hg = 0; hg < 2 * total_chunks; ++hg) {
                 const int as = (int)(hg % NA);
                 if (!mbar_wait(&a_empty[as], (uint32_t)((hg / NA) & 1) ^ 1u, &s_abort, p.err)) break;
-                const int64_t c = c_begin + (hg >> 1);
-                const int64_t tile = c / K;
-                const int64_t kc = c % K;
-                mbar_arrive_expect_tx(&a_full[as], kHalfBytes);
-                tma_load_2d(abuf + (size_t)as * kHalfBytes, &amap, (int)(kc * kBK + 32 * (hg & 1)),
-                            (int)(tile * kBM), &a_full[as]);
+                // the converters read this stage through the generic proxy; order those
+                // reads before the TMA (async proxy) overwrites it
+                fence_proxy_async();
+                if (!(drop0 && hg == 0)) {
+                    mbar_arrive_expect_tx(&a_full[as], kHalfBytes);
+                    tma_load_2d(abuf + (size_t)as * kHalfBytes, &amap, (int)(kc * kBK + 32 * (hg & 1)),
+                                (int)(tile * kBM), &a_full[as]);
+                }
                 ++issued;
+                if ((hg & 1) && ++kc == K) {
+                    kc = 0;
+                    ++tile;
+                }
             }
             for (int64_t hg = std::max<int64_t>(0, issued - NA); hg < issued; ++hg)
-                mbar_drain(&a_full[hg % NA], (uint32_t)((hg / NA) & 1));
+                if (!(drop0 && hg == 0)) mbar_drain(&a_full[hg % NA], (uint32_t)((hg / NA) & 1));
         }
     } else if (warp == kBProdWarp) {
         // ---------------- TMA producer of X^T chunks
         if (lane == 0) {
             int64_t issued = 0;
+            int64_t kc = c_begin % K;
             for (int64_t g = 0; g < total_chunks; ++g) {
                 const int s = (int)(g % kStages);
                 if (!mbar_wait(&empty[s], (uint32_t)((g / kStages) & 1) ^ 1u, &s_abort, p.err)) break;
                 mbar_arrive_expect_tx(&full_b[s], b_bytes);
-                tma_load_2d(bbuf + (size_t)s * b_stage, &xmap, (int)(((c_begin + g) % K) * kBK), 0, &full_b[s]);
+                tma_load_2d(bbuf + (size_t)s * b_stage, &xmap, (int)(kc * kBK), 0, &full_b[s]);
                 ++issued;
+                if (++kc == K) kc = 0;
             }
             for (int64_t g = std::max<int64_t>(0, issued - kStages); g < issued; ++g)
                 mbar_drain(&full_b[g % kStages], (uint32_t)((g / kStages) & 1));
@@ -327,7 +337,7 @@ bool tc_supported(const MatView& A) {
 int tc_mma_n(int s) { return s <= 16 ? 16 : (s + 15) / 16 * 16; }
 
 cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, int s, float* C,
-                            int64_t ldc, int* err_flag, cudaStream_t st, int* launches) {
+                            int64_t ldc, int* err_flag, cudaStream_t st, int* launches, int drop_first) {
     if (s <= 0 || A.rows <= 0) return cudaSuccess;
     if (s > 256 || s % 8 != 0) return cudaErrorInvalidValue;
     const int N = tc_mma_n(s);
@@ -360,12 +370,12 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
     p.ldc = ldc;
     p.S = s;
     p.N = N;
-    p.astages = kMaxAStages;           // 128 KB of A in flight per SM
     p.tiles = (A.rows + kBM - 1) / kBM;
     p.kchunks = (A.cols + kBK - 1) / kBK;
     p.err = err_flag;
+    p.drop_first = drop_first;
     const uint32_t b_bytes = (uint32_t)N * kBK * 2;
-    const size_t smem = (size_t)kHalfBytes * p.astages + ((b_bytes + 1023u) & ~1023u) * kStages + 1024;
+    const size_t smem = (size_t)kHalfBytes * kMaxAStages + ((b_bytes + 1023u) & ~1023u) * kStages + 1024;
     cudaError_t e = cudaFuncSetAttribute(right_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (!g_sms) {

@@ -42,7 +42,7 @@ RE_TRANSPOSED = 4
 class re_opts(ctypes.Structure):
     _fields_ = [("s0", ctypes.c_int), ("s_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("y_kind", ctypes.c_int), ("norm_a", ctypes.c_double), ("learned", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("test_drop_load", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class re_result(ctypes.Structure):

@@ -92,3 +92,29 @@ def test_tc_shared_tiles_deterministic(htc):
         outs.append(AX)
     assert torch.isfinite(outs[0]).all()
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_tc_bounded_wait_expires_and_context_survives():
+    """Failure path: with the test hook one CTA withholds its first A tile, so the
+    waits on it expire (bounded, about 2 s); every role drains and frees TMEM, the
+    estimate reports RE_ERR_TIMEOUT, and the next estimate on the same handle (same
+    CUDA context) is correct."""
+    import time
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    rank = 20
+    sig = wl.spectrum("step", 2048, rank=rank, tail_scale=1e-9)
+    A = wl.haar_matrix(4096, 2048, sig, seed=3).to(torch.float32).cuda()
+    h = rk.re_create(0, rk.make_opts(precision=rk.RE_PREC_BF16X3, test_drop_load=1))
+    try:
+        t0 = time.time()
+        with pytest.raises(rk.RankEstError) as e:
+            rk.re_rank_estimate(h, A, 1e-4, rk.RE_GAUSSIAN, 3)
+        assert e.value.code == rk.RE_ERR_TIMEOUT
+        assert time.time() - t0 < 60
+        rk.re_set_opts(h, rk.make_opts(precision=rk.RE_PREC_BF16X3))
+        res, _ = rk.re_rank_estimate(h, A, 1e-4, rk.RE_GAUSSIAN, 3)
+        assert res.status == 0 and res.rank == rank
+    finally:
+        rk.re_destroy(h)
+    torch.cuda.synchronize()
