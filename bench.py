@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # measured DRAM traffic / algorithmic bytes of right_tc_kernel (ncu, 16384x16384, N=32)
-TC_TRAFFIC_PER_ALGO_BYTE = 1.0012
+TC_TRAFFIC_PER_ALGO_BYTE = 1.0011
 
 WORKLOADS = {
     "large": dict(m=65536, n=16384, rank=200, eps=1e-4, seed=1, sketch_seed=12345),
