@@ -10,18 +10,23 @@
 // never formed (it would square the condition number and lose the small
 // singular values the read-off depends on).  Pairs are scheduled by the
 // round-robin (circle) ordering, so the rotations of a round are independent
-// and run on separate warps.
+// and run on separate lane groups.
 //
-// Arithmetic is FP32: on GB300 FP64 runs at about 1/57 of the FP32 rate, and the
+// Arithmetic is FP32: on GB300 FP64 runs at about 1/64 of the FP32 rate, and the
 // sketch itself is accumulated in FP32, so FP32 rotations (absolute error about
 // 1e-5 sigma_1 at s = 512) keep the whole path consistent.  Rotations whose
 // off-diagonal term is below (1e-7 sigma_1)^2 are skipped: they cannot move any
 // singular value by more than 1e-7 sigma_1, far below the FP32 noise floor.
+// Rotations run two lanes of data per instruction (packed FP32x2 multiply and
+// fused multiply-add, rounded per element exactly as the scalar forms).
 //
 // Small cores (r2 s + s^2 floats fit in shared memory) use one CTA; larger cores
-// use a cluster of 8 or 16 CTAs: the QR is column-cyclic with the Householder
-// vector broadcast over distributed shared memory, and Jacobi is blocked (two
-// column blocks per CTA, blocks rotating through the cluster each round).
+// use a cluster of 8 or 16 CTAs: the columns are dealt out in panels of 8, the
+// QR factors one panel at a time on the CTA that owns it and broadcasts its
+// reflectors over distributed shared memory, with one panel of lookahead (the
+// owner of the next panel updates and factors it while the other CTAs update
+// the rest); Jacobi is blocked (two column blocks per CTA, blocks rotating
+// through the cluster each round).
 #include <algorithm>
 #include <cfloat>
 #include <climits>
@@ -38,14 +43,19 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kSvdThreads = 512;      // cluster kernel
+constexpr int kSvdThreads = 512;      // cluster QR kernel
+constexpr int kJacThreads = 256;      // cluster Jacobi kernel
 constexpr int kCtaThreads = 1024;     // one-CTA kernel: 64 column pairs x 16 lanes
 constexpr int kMaxSweeps = 40;
+constexpr int kPanel = 8;             // cluster QR: columns per panel
 constexpr float kU = 5.9604644775390625e-08f;        // 2^-24
 constexpr float kAbsFloor = 1e-14f;                  // (1e-7)^2 of max column norm^2
 // A sweep whose largest rotated |cos| is below kStopFactor * u * sqrt(n) only
 // rotated pairs at the FP32 rounding level of the dot products: stop there.
 constexpr float kStopFactor = 32.f;
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+
+typedef unsigned long long u64;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -62,41 +72,77 @@ __device__ __forceinline__ float warp_max(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+__device__ __forceinline__ u64 warp_max(u64 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
 
-// Jacobi rotation of columns a, b (length 4*G*NV, 16-byte aligned) by a group
-// of G consecutive lanes; each lane holds NV float4 of each column in registers
-// (elements 4 (gl + G v) .. +3), so the columns are read once and written once.
+// |v| as its bit pattern: for finite doubles the unsigned order of these words is
+// the order of |v|, and a word >= kInfBits marks Inf or NaN (integer work only:
+// FP64 instructions issue at 1/64 rate on this part).
+__device__ __forceinline__ u64 abs_bits(double v) {
+    return (u64)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+// packed FP32x2 (low word = first element)
+__device__ __forceinline__ u64 pk2(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float sum2(u64 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a + b;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Jacobi rotation of two columns held in registers by a group of G consecutive
+// lanes (each lane holds NV float4 of each column: elements 4 (gl + G v) .. +3).
 // Every lane of the warp must call it (the reductions use full-warp shuffles);
 // inactive groups pass active = false.  A pair is rotated when
-// |a.b| > tol |a| |b| and |a.b| > floor_abs; then rotated is set and meas_max
-// takes max(|cos|).  The rotation parameters use the fast reciprocal square
-// root and division: their rounding only perturbs the angle, and c^2 + s^2
-// stays 1 to a few ulp.
+// |a.b| > tol |a| |b| and |a.b| > floor_abs; then rotated is set, meas_max takes
+// max(|cos|) and the function returns true.  The rotation parameters use the fast
+// reciprocal square root and division: their rounding only perturbs the angle,
+// and c^2 + s^2 stays 1 to a few ulp.  The dot products and the update run as
+// packed FP32x2 instructions; each element is rounded as by the scalar fmaf /
+// multiply.
 template <int G, int NV>
-__device__ __forceinline__ void jacobi_pair(bool active, float* a, float* b, float tol2, float floor_abs,
-                                            float& meas_max, int& rotated) {
-    const int gl = threadIdx.x & (G - 1);
-    float4 x[NV], y[NV];
-    float al = 0.f, be = 0.f, ga = 0.f, al2 = 0.f, be2 = 0.f, ga2 = 0.f;
+__device__ __forceinline__ bool rotate_pair(bool active, ulonglong2 (&x)[NV], ulonglong2 (&y)[NV], float tol2,
+                                            float floor_abs, float& meas_max, int& rotated) {
+    u64 al0 = 0ull, al1 = 0ull, be0 = 0ull, be1 = 0ull, ga0 = 0ull, ga1 = 0ull;
     if (active) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            x[v] = *reinterpret_cast<const float4*>(a + 4 * (gl + G * v));
-            y[v] = *reinterpret_cast<const float4*>(b + 4 * (gl + G * v));
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            al = fmaf(x[v].x, x[v].x, fmaf(x[v].y, x[v].y, al));
-            al2 = fmaf(x[v].z, x[v].z, fmaf(x[v].w, x[v].w, al2));
-            be = fmaf(y[v].x, y[v].x, fmaf(y[v].y, y[v].y, be));
-            be2 = fmaf(y[v].z, y[v].z, fmaf(y[v].w, y[v].w, be2));
-            ga = fmaf(x[v].x, y[v].x, fmaf(x[v].y, y[v].y, ga));
-            ga2 = fmaf(x[v].z, y[v].z, fmaf(x[v].w, y[v].w, ga2));
+            al0 = fma2(x[v].x, x[v].x, al0);
+            al1 = fma2(x[v].y, x[v].y, al1);
+            be0 = fma2(y[v].x, y[v].x, be0);
+            be1 = fma2(y[v].y, y[v].y, be1);
+            ga0 = fma2(x[v].x, y[v].x, ga0);
+            ga1 = fma2(x[v].y, y[v].y, ga1);
         }
     }
-    al += al2;
-    be += be2;
-    ga += ga2;
+    float al = sum2(add2(al0, al1));
+    float be = sum2(add2(be0, be1));
+    float ga = sum2(add2(ga0, ga1));
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
         al += __shfl_xor_sync(0xffffffffu, al, o);
@@ -107,7 +153,7 @@ __device__ __forceinline__ void jacobi_pair(bool active, float* a, float* b, flo
     const float ab = al * be;
     // ga^2 > tol^2 al be  <=>  |ga| > tol |a| |b|  (pairs below the absolute floor are
     // skipped first, so al be cannot have underflowed for a rotated pair)
-    if (!active || !(ag > floor_abs) || !(ga * ga > tol2 * ab)) return;
+    if (!active || !(ag > floor_abs) || !(ga * ga > tol2 * ab)) return false;
     rotated = 1;
     meas_max = fmaxf(meas_max, ag * rsqrtf(ab));
     const float zeta = __fdividef(be - al, ga + ga);
@@ -121,19 +167,54 @@ __device__ __forceinline__ void jacobi_pair(bool active, float* a, float* b, flo
     }
     const float c = rsqrtf(fmaf(tt, tt, 1.f));
     const float sn = c * tt;
+    const u64 c2 = pk2(c, c), s2 = pk2(sn, sn), n2 = pk2(-sn, -sn);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const float4 xa = x[v], ya = y[v];
-        x[v].x = fmaf(c, xa.x, -sn * ya.x);
-        x[v].y = fmaf(c, xa.y, -sn * ya.y);
-        x[v].z = fmaf(c, xa.z, -sn * ya.z);
-        x[v].w = fmaf(c, xa.w, -sn * ya.w);
-        y[v].x = fmaf(sn, xa.x, c * ya.x);
-        y[v].y = fmaf(sn, xa.y, c * ya.y);
-        y[v].z = fmaf(sn, xa.z, c * ya.z);
-        y[v].w = fmaf(sn, xa.w, c * ya.w);
-        *reinterpret_cast<float4*>(a + 4 * (gl + G * v)) = x[v];
-        *reinterpret_cast<float4*>(b + 4 * (gl + G * v)) = y[v];
+        const ulonglong2 xa = x[v], ya = y[v];
+        x[v].x = fma2(c2, xa.x, mul2(n2, ya.x));     // c a - s b
+        x[v].y = fma2(c2, xa.y, mul2(n2, ya.y));
+        y[v].x = fma2(s2, xa.x, mul2(c2, ya.x));     // s a + c b
+        y[v].y = fma2(s2, xa.y, mul2(c2, ya.y));
+    }
+    return true;
+}
+
+// rotate_pair on columns a, b in shared memory (length 4*G*NV, 16-byte aligned):
+// each is read once and, when rotated, written once
+template <int G, int NV>
+__device__ __forceinline__ void jacobi_pair(bool active, float* a, float* b, float tol2, float floor_abs,
+                                            float& meas_max, int& rotated) {
+    const int gl = threadIdx.x & (G - 1);
+    ulonglong2 x[NV], y[NV];
+    if (active) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            x[v] = *reinterpret_cast<const ulonglong2*>(a + 4 * (gl + G * v));
+            y[v] = *reinterpret_cast<const ulonglong2*>(b + 4 * (gl + G * v));
+        }
+    }
+    if (rotate_pair<G, NV>(active, x, y, tol2, floor_abs, meas_max, rotated)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            *reinterpret_cast<ulonglong2*>(a + 4 * (gl + G * v)) = x[v];
+            *reinterpret_cast<ulonglong2*>(b + 4 * (gl + G * v)) = y[v];
+        }
+    }
+}
+
+// rotate_pair of a register-held column x with column b in shared memory
+template <int G, int NV>
+__device__ __forceinline__ void jacobi_pair_x(bool active, ulonglong2 (&x)[NV], float* b, float tol2,
+                                              float floor_abs, float& meas_max, int& rotated) {
+    const int gl = threadIdx.x & (G - 1);
+    ulonglong2 y[NV];
+    if (active) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) y[v] = *reinterpret_cast<const ulonglong2*>(b + 4 * (gl + G * v));
+    }
+    if (rotate_pair<G, NV>(active, x, y, tol2, floor_abs, meas_max, rotated)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) *reinterpret_cast<ulonglong2*>(b + 4 * (gl + G * v)) = y[v];
     }
 }
 
@@ -168,46 +249,25 @@ __device__ __forceinline__ double col_norm(const float* a, int n) {
     return sqrt(warp_sum(acc));
 }
 
-// Descending rank sort of s_norm[0..n) into out (scaled by `scale`).
+// Descending rank sort of the non-negative s_norm[0..n) into out (scaled by
+// `scale`); compares the bit patterns as integers (same order for x >= 0).
 __device__ void sort_desc(const double* s_norm, int n, double scale, double* out) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const double v = s_norm[j];
+        const long long vb = __double_as_longlong(v);
         int rank = 0;
         for (int i = 0; i < n; ++i) {
-            const double w = s_norm[i];
-            rank += (w > v) || (w == v && i < j);
+            const long long w = __double_as_longlong(s_norm[i]);
+            rank += (w > vb) || (w == vb && i < j);
         }
         out[rank] = v * scale;
     }
 }
 
-// Householder reflector of x[0..L) (one warp): x[1..) becomes v (v[0] = 1
-// implicit), x[0] becomes beta; returns tau with H = I - tau v v^T.
-__device__ __forceinline__ float householder(float* x, int L) {
-    const int lane = threadIdx.x & 31;
-    float ss = 0.f;
-    for (int i = 1 + lane; i < L; i += 32) ss = fmaf(x[i], x[i], ss);
-    ss = warp_sum(ss);
-    const float x0 = x[0];
-    float tau = 0.f, beta = x0;
-    if (ss > 0.f) {
-        const float nrm = sqrtf(fmaf(x0, x0, ss));
-        beta = -copysignf(nrm, x0);
-        tau = (beta - x0) / beta;
-        const float scale = 1.f / (x0 - beta);
-        __syncwarp();
-        for (int i = 1 + lane; i < L; i += 32) x[i] *= scale;
-    }
-    __syncwarp();
-    if (lane == 0) x[0] = beta;
-    __syncwarp();
-    return tau;
-}
-
 // Register-resident versions for a column of length L <= 32*E (one warp; lane
 // l holds entries l, l+32, ..., masked past L).  householder_regs: reflector of
-// x = col[0..L) with the same arithmetic as householder(); v (v[0] = 1) goes to
-// col[1..), beta to col[0]; returns tau.
+// x = col[0..L) (H = I - tau v v^T, v[0] = 1): v[1..) goes to col[1..), beta to
+// col[0]; returns tau.
 template <int E>
 __device__ __forceinline__ float householder_regs(float* col, int L) {
     const int lane = threadIdx.x & 31;
@@ -269,10 +329,95 @@ __device__ __forceinline__ void apply_reflector(const float (&v)[E], float tau, 
     }
 }
 
+// Column held in registers across several reflectors (cluster QR): entries
+// i = lane + 32 e of a column segment of length L, zero past L.
+template <int E>
+__device__ __forceinline__ void load_col(const float* col, int L, float (&x)[E]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        x[e] = i < L ? col[i] : 0.f;
+    }
+}
+template <int E>
+__device__ __forceinline__ void store_col(float* col, int L, const float (&x)[E]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        if (i < L) col[i] = x[e];
+    }
+}
+
+// Reflector of the register column x below its diagonal entry d (d < 32): the
+// same arithmetic as householder_regs on x[d..L); entries past d become v
+// (v[d] = 1 implicit), x[d] becomes beta; returns tau.
+template <int E>
+__device__ __forceinline__ float householder_col(float (&x)[E], int d, int L) {
+    const int lane = threadIdx.x & 31;
+    float ss = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        if (i > d && i < L) ss = fmaf(x[e], x[e], ss);
+    }
+    ss = warp_sum(ss);
+    const float x0 = __shfl_sync(0xffffffffu, x[0], d);
+    float tau = 0.f;
+    if (ss > 0.f) {
+        const float nrm = sqrtf(fmaf(x0, x0, ss));
+        const float beta = -copysignf(nrm, x0);
+        tau = (beta - x0) / beta;
+        const float scale = 1.f / (x0 - beta);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = lane + 32 * e;
+            if (i > d && i < L) x[e] *= scale;
+        }
+        if (lane == d) x[0] = beta;
+    }
+    return tau;
+}
+
+// x <- (I - tau v v^T) x for the NC register columns x, with the reflector
+// whose diagonal is entry d: v[d] = 1, v[i] = vcol[i] for d < i < L, 0 before d.
+template <int E, int NC>
+__device__ __forceinline__ void reflect_cols(float (&x)[NC][E], const float* vcol, int d, int L, float tau) {
+    const int lane = threadIdx.x & 31;
+    float v[E];
+    float w[NC];
+#pragma unroll
+    for (int n = 0; n < NC; ++n) w[n] = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        v[e] = (i > d && i < L) ? vcol[i] : (i == d ? 1.f : 0.f);
+#pragma unroll
+        for (int n = 0; n < NC; ++n) w[n] = fmaf(v[e], x[n][e], w[n]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int n = 0; n < NC; ++n) w[n] += __shfl_xor_sync(0xffffffffu, w[n], o);
+    }
+#pragma unroll
+    for (int n = 0; n < NC; ++n) {
+        const float wt = w[n] * tau;
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[n][e] = fmaf(-wt, v[e], x[n][e]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // One CTA per core: core -> shared memory (column-major, scaled), QR in place,
 // R^T -> second region, Jacobi on R^T, norms.  blockIdx.x selects the core
 // (core_stride / sigma_stride apart) so one launch serves a batch.
+
+// column stride of the one-CTA kernel's core copy: odd, so the transposing
+// copies (lanes along a row of the core) touch 32 different banks
+__host__ __device__ __forceinline__ int cta_ldw(int r2) { return r2 | 1; }
+
 template <int NV, int E>
 __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     const double* __restrict__ core, int r2, int s, int64_t ld, int64_t core_stride,
@@ -283,13 +428,14 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     core += (int64_t)blockIdx.x * core_stride;
     sigma += (int64_t)blockIdx.x * sigma_stride;
     const int sp = 64 * NV;                             // padded column length of R^T (4 x 16 lanes x NV)
-    float* W = reinterpret_cast<float*>(smem);          // r2 x s, column-major
-    float* Rt = W + ((size_t)r2 * s + 31) / 32 * 32;    // sp x s, column c = row c of R (128-B aligned)
+    const int ldw = cta_ldw(r2);
+    float* W = reinterpret_cast<float*>(smem);          // r2 x s, column-major, column stride ldw
+    float* Rt = W + ((size_t)ldw * s + 31) / 32 * 32;   // sp x s, column c = row c of R (128-B aligned)
     __shared__ double s_norm[512];
     __shared__ float s_tau, s_red[32];
     __shared__ int s_bad, s_flag;
     __shared__ unsigned int s_meas;
-    __shared__ unsigned long long s_dmax;
+    __shared__ u64 s_dmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
     // power-of-two scale: largest |entry| -> [0.5, 1)
@@ -298,16 +444,21 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
         s_dmax = 0ull;
     }
     __syncthreads();
-    double mx = 0.0;
-    int bad = 0;
-    for (int64_t idx = tid; idx < (int64_t)r2 * s; idx += blockDim.x) {
-        const double v = core[(idx / s) * ld + idx % s];
-        bad |= !isfinite(v);
-        mx = fmax(mx, fabs(v));
+    {
+        u64 mx = 0ull;
+        int bad = 0;
+        for (int i = warp; i < r2; i += nwarps) {
+            const double* row = core + (int64_t)i * ld;
+            for (int j = lane; j < s; j += 32) {
+                const u64 ab = abs_bits(row[j]);
+                if (ab >= kInfBits) bad = 1;
+                else mx = ab > mx ? ab : mx;
+            }
+        }
+        if (bad) s_bad = 1;
+        mx = warp_max(mx);
+        if (lane == 0) atomicMax(&s_dmax, mx);
     }
-    if (bad) s_bad = 1;
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0 && isfinite(mx)) atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(mx));
     __syncthreads();
     if (s_bad) {
         for (int j = tid; j < s; j += blockDim.x) sigma[j] = nan("");
@@ -318,16 +469,16 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     const double dmax = __longlong_as_double((long long)s_dmax);
     if (dmax > 0.0) frexp(dmax, &e2);
     const double down = ldexp(1.0, -e2), up = ldexp(1.0, e2);
-    for (int64_t idx = tid; idx < (int64_t)r2 * s; idx += blockDim.x) {
-        const int i = (int)(idx / s), j = (int)(idx % s);
-        W[(size_t)j * r2 + i] = (float)(core[(int64_t)i * ld + j] * down);
+    for (int i = warp; i < r2; i += nwarps) {
+        const double* row = core + (int64_t)i * ld;
+        for (int j = lane; j < s; j += 32) W[(size_t)j * ldw + i] = (float)(row[j] * down);
     }
     __syncthreads();
 
     // Householder QR: column k's reflector, then the trailing columns (reflector
     // and each column held in registers, r2 <= 32 E)
     for (int k = 0; k < s; ++k) {
-        float* colk = W + (size_t)k * r2 + k;
+        float* colk = W + (size_t)k * ldw + k;
         const int L = r2 - k;
         if (warp == 0) {
             const float tau = householder_regs<E>(colk, L);
@@ -338,7 +489,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
         if (tau != 0.f && k + 1 + warp < s) {
             float v[E];
             load_reflector<E>(colk, L, v);
-            for (int j = k + 1 + warp; j < s; j += nwarps) apply_reflector<E>(v, tau, W + (size_t)j * r2 + k, L);
+            for (int j = k + 1 + warp; j < s; j += nwarps) apply_reflector<E>(v, tau, W + (size_t)j * ldw + k, L);
         }
         __syncthreads();
     }
@@ -347,47 +498,48 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     // and sigma_1(core) <= ||R||_F; when the lower bound exceeds cert_ratio times
     // the upper bound, the read-off cannot succeed at this width and the Jacobi
     // sweeps are skipped (status[3] = 1; sigma is not written).
-    if (cert_r1 > 0 && cert_r1 <= s) {
+    // (the scratch below needs (1 + min(32, r1)) rounded-up r1 columns of Rt)
+    if (cert_r1 > 0 && cert_r1 <= s &&
+        (size_t)((cert_r1 + 31) / 32 * 32) * (1 + min(nwarps, cert_r1)) <= (size_t)sp * s) {
         __shared__ float s_fro, s_inv;
         __shared__ int s_zero;
+        // Rt is free until the transpose below: 1/R_ii, then one right-hand side per warp
+        const int cpad = (cert_r1 + 31) / 32 * 32;
+        float* rinv = Rt;
+        float* bv = Rt + cpad + (size_t)warp * cpad;
         if (tid == 0) {
             s_fro = 0.f;
             s_inv = 0.f;
             s_zero = 0;
         }
         __syncthreads();
+        for (int i = tid; i < cert_r1; i += blockDim.x) {
+            const float d = W[(size_t)i * ldw + i];
+            rinv[i] = d != 0.f ? 1.f / d : 0.f;
+            if (d == 0.f) s_zero = 1;
+        }
         float fro = 0.f;
-        for (int64_t idx = tid; idx < (int64_t)s * s; idx += blockDim.x) {
-            const int j = (int)(idx / s), i = (int)(idx % s);
-            if (i <= j) {
-                const float v = W[(size_t)j * r2 + i];
+        for (int j = warp; j < s; j += nwarps)
+            for (int i = lane; i <= j; i += 32) {
+                const float v = W[(size_t)j * ldw + i];
                 fro = fmaf(v, v, fro);
             }
-        }
         fro = warp_sum(fro);
         if (lane == 0) atomicAdd(&s_fro, fro);
-        // columns of R11^{-1} by back substitution, one warp per column
-        float* x = Rt + (size_t)warp * sp;             // Rt is free until the transpose below
+        __syncthreads();
+        // columns of R11^{-1} by column-oriented back substitution (R11 x = e_j:
+        // x_i = b_i / R_ii, then b[0..i) -= x_i R[0..i, i]; column i of R is
+        // contiguous), one warp per column
         float inv = 0.f;
         for (int j = warp; j < cert_r1; j += nwarps) {
-            const float rjj = W[(size_t)j * r2 + j];
-            if (rjj == 0.f) {
-                if (lane == 0) s_zero = 1;
-                continue;
-            }
-            if (lane == 0) x[j] = 1.f / rjj;
+            for (int r = lane; r <= j; r += 32) bv[r] = r == j ? 1.f : 0.f;
             __syncwarp();
-            float acc = lane == 0 ? x[j] * x[j] : 0.f;
-            for (int i = j - 1; i >= 0; --i) {
-                float t = 0.f;
-                for (int k = i + 1 + lane; k <= j; k += 32) t = fmaf(W[(size_t)k * r2 + i], x[k], t);
-                t = warp_sum(t);
-                const float rii = W[(size_t)i * r2 + i];
-                const float xi = rii != 0.f ? -t / rii : INFINITY;
-                if (lane == 0) {
-                    x[i] = xi;
-                    acc = fmaf(xi, xi, acc);
-                }
+            float acc = 0.f;
+            for (int i = j; i >= 0; --i) {
+                const float xi = bv[i] * rinv[i];
+                acc = fmaf(xi, xi, acc);
+                const float* ci = W + (size_t)i * ldw;
+                for (int r = lane; r < i; r += 32) bv[r] = fmaf(-xi, ci[r], bv[r]);
                 __syncwarp();
             }
             inv += acc;
@@ -404,10 +556,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
         }
     }
     // R^T: column c of Rt = row c of R = W[j][c] for j >= c
-    for (int64_t idx = tid; idx < (int64_t)s * sp; idx += blockDim.x) {
-        const int c = (int)(idx / sp), j = (int)(idx % sp);
-        Rt[(size_t)c * sp + j] = (j >= c && j < s) ? W[(size_t)j * r2 + c] : 0.f;
-    }
+    for (int c = warp; c < s; c += nwarps)
+        for (int j = lane; j < sp; j += 32)
+            Rt[(size_t)c * sp + j] = (j >= c && j < s) ? W[(size_t)j * ldw + c] : 0.f;
     __syncthreads();
 
     // Jacobi on R^T (s x s)
@@ -438,6 +589,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
         float meas = 0.f;
         for (int t = 0; t < P - 1; ++t) {
             for (int base = 0; base < P / 2; base += ngrp) {
+                if (base + warp * (32 / G) >= P / 2) continue;     // no pair for this warp
                 const int q = base + grp;
                 int p = 0, qq = 0;
                 bool act = q < P / 2;
@@ -473,61 +625,100 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Cluster version.  Column j of the core lives in CTA j % CL (local column j / CL).
+// Cluster version: two kernels on the same stream.
+//
+// core_qr_cluster_kernel (CL CTAs of 512 threads): the columns are dealt out in
+// panels of kPanel: panel p (columns p kPanel ..) lives in CTA p % CL as its
+// local panel p / CL.  Column stride ldw keeps every column 16-byte aligned.
+// The owner of a panel publishes its reflectors once to global memory (each
+// panel has its own slot, so no CTA can hold a stale cached copy), and every
+// CTA reads them from there (L2, then its L1) after the cluster barrier.  R goes
+// to global memory column-major.
+//
+// core_jacobi_cluster_kernel (CL CTAs of 256 threads, 255 registers per
+// thread): blocked one-sided Jacobi on R^T with two column blocks per CTA; in
+// the cross rounds each CTA's slot-0 columns stay in registers.
 
-template <int CL, int NV, int E>
-__global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
-    const double* __restrict__ core, int r2, int s, int64_t ld, int b, double* __restrict__ sigma,
+__host__ __device__ __forceinline__ int cluster_ldw(int r2) { return (r2 + 31) / 32 * 32 + 4; }
+
+__device__ __forceinline__ void panel_bar() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kPanel * 32) : "memory");
+}
+
+// Global scratch of the cluster path (floats): R column-major (s x s), the
+// reflector slots (np kPanel columns of stride ldw), their taus, and the
+// power-of-two scale (one double).
+struct ClusterWs {
+    float* Rcm;
+    float* Vg;
+    float* taug;
+    double* up;
+};
+__host__ __device__ __forceinline__ size_t cluster_ws_floats(int r2, int s) {
+    const size_t np = (size_t)(s + kPanel - 1) / kPanel;
+    return ((size_t)s * s + 3) / 4 * 4 + np * kPanel * (size_t)cluster_ldw(r2) + (np * kPanel + 3) / 4 * 4 + 4;
+}
+__host__ __device__ __forceinline__ ClusterWs cluster_ws(void* ws, int r2, int s) {
+    ClusterWs w;
+    const size_t np = (size_t)(s + kPanel - 1) / kPanel;
+    w.Rcm = static_cast<float*>(ws);
+    w.Vg = w.Rcm + ((size_t)s * s + 3) / 4 * 4;
+    w.taug = w.Vg + np * kPanel * (size_t)cluster_ldw(r2);
+    w.up = reinterpret_cast<double*>(w.taug + (np * kPanel + 3) / 4 * 4);
+    return w;
+}
+
+template <int CL, int E>
+__global__ void __launch_bounds__(kSvdThreads, 1) core_qr_cluster_kernel(
+    const double* __restrict__ core, int r2, int s, int64_t ld, void* ws, double* __restrict__ sigma,
     int* __restrict__ status) {
-    constexpr int P2 = 2 * CL;
+    constexpr int NB = kPanel;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
-    const int nloc = (s + CL - 1) / CL;
-    const int sp = 128 * NV;                                   // padded column length of R^T
-    const size_t set_floats = 2 * (size_t)b * sp;              // two blocks of b columns
-    const size_t r1_floats = (max((size_t)nloc * r2, set_floats) + 31) / 32 * 32;
-    float* W = reinterpret_cast<float*>(smem);                // QR: nloc x r2 (column-major)
-    float* vbuf = W + r1_floats;                              // 2 x r2 Householder vectors
-    float* sets[2] = {vbuf + (2 * (size_t)r2 + 31) / 32 * 32, W};   // Jacobi ping-pong (set 1 reuses W)
-    __shared__ float s_tau[2];
-    __shared__ int s_block[2][2];                             // [set][slot] block ids
-    __shared__ int s_count, s_bad;
-    __shared__ unsigned int s_meas;
-    __shared__ float s_fmax;
-    __shared__ unsigned long long s_dmax;
-    __shared__ double s_norm[512];
-    __shared__ float s_red[32];
+    const int np = (s + NB - 1) / NB;                          // panels
+    const int nloc = (np + CL - 1) / CL * NB;                  // local columns
+    const int ldw = cluster_ldw(r2);
+    const ClusterWs g = cluster_ws(ws, r2, s);
+    float* W = reinterpret_cast<float*>(smem);                // nloc columns, stride ldw
+    __shared__ float s_ptau[NB];
+    __shared__ int s_bad;
+    __shared__ u64 s_dmax;
     const int k = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    // global column of local column jl
+    auto gcol = [&](int jl) { return ((jl / NB) * CL + k) * NB + (jl % NB); };
 
     // ---- own columns: finiteness and the power-of-two scale agreed across the cluster
     if (tid == 0) {
         s_bad = 0;
         s_dmax = 0ull;
-        s_count = 0;
-        s_meas = 0u;
     }
     __syncthreads();
     {
-        double mx = 0.0;
+        u64 mx = 0ull;
         int bad = 0;
-        for (int64_t idx = tid; idx < (int64_t)nloc * r2; idx += blockDim.x) {
-            const int jl = (int)(idx / r2), i = (int)(idx % r2);
-            const int j = jl * CL + k;
-            const double v = j < s ? core[(int64_t)i * ld + j] : 0.0;
-            bad |= !isfinite(v);
-            mx = fmax(mx, fabs(v));
+        for (int i = warp; i < r2; i += nwarps) {
+            const double* row = core + (int64_t)i * ld;
+            for (int jl = lane; jl < nloc; jl += 32) {
+                const int j = gcol(jl);
+                if (j < s) {
+                    const u64 ab = abs_bits(row[j]);
+                    if (ab >= kInfBits) bad = 1;
+                    else mx = ab > mx ? ab : mx;
+                }
+            }
         }
         if (bad) s_bad = 1;
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0 && isfinite(mx)) atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(mx));
+        mx = warp_max(mx);
+        if (lane == 0) atomicMax(&s_dmax, mx);
     }
     cluster.sync();
     int any_bad = 0;
-    double gmax = 0.0;
+    u64 gbits = 0ull;
     for (int r = 0; r < CL; ++r) {
         any_bad |= *cluster.map_shared_rank(&s_bad, r);
-        gmax = fmax(gmax, __longlong_as_double((long long)*cluster.map_shared_rank(&s_dmax, r)));
+        const u64 m = *cluster.map_shared_rank(&s_dmax, r);
+        gbits = m > gbits ? m : gbits;
     }
     if (any_bad) {
         if (k == 0) {
@@ -537,76 +728,191 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         cluster.sync();
         return;
     }
+    const double gmax = __longlong_as_double((long long)gbits);
     int e2 = 0;
     if (gmax > 0.0) frexp(gmax, &e2);
-    const double down = ldexp(1.0, -e2), up = ldexp(1.0, e2);
-    for (int64_t idx = tid; idx < (int64_t)nloc * r2; idx += blockDim.x) {
-        const int jl = (int)(idx / r2), i = (int)(idx % r2);
-        const int j = jl * CL + k;
-        W[idx] = j < s ? (float)(core[(int64_t)i * ld + j] * down) : 0.f;
+    const double down = ldexp(1.0, -e2);
+    if (k == 0 && tid == 0) {
+        *g.up = ldexp(1.0, e2);
+        *status = RE_OK;
+    }
+    for (int i = warp; i < ldw; i += nwarps) {
+        const double* row = core + (int64_t)i * ld;
+        for (int jl = lane; jl < nloc; jl += 32) {
+            const int j = gcol(jl);
+            W[(size_t)jl * ldw + i] = (i < r2 && j < s) ? (float)(row[j] * down) : 0.f;
+        }
     }
     cluster.sync();   // all CTAs have read every s_bad / s_dmax
 
-    // ---- column-cyclic Householder QR
-    for (int kk = 0; kk < s; ++kk) {
-        const int owner = kk % CL, jl = kk / CL, buf = kk & 1;
-        const int L = r2 - kk;
-        if (k == owner) {
-            float* colk = W + (size_t)jl * r2 + kk;
-            if (warp == 0) {
-                const float tau = householder_regs<E>(colk, L);
-                if (lane == 0) s_tau[buf] = tau;
+    // ---- panel Householder QR with one panel of lookahead.  Iteration p: the
+    // reflectors V_p of panel p are in global slot p (published before the
+    // barrier); the owner of panel p + 1 applies V_p to that panel, factors it and
+    // publishes its reflectors in slot p + 1, while every other warp applies V_p to
+    // the trailing columns of its CTA.
+    for (int p = -1; p < np; ++p) {
+        if (p >= 0) cluster.sync();
+        const int rb = p >= 0 ? p * NB : 0;                    // first row held in registers
+        const int Lr = r2 - rb;
+        const int nxt = p + 1;
+        const bool own_next = nxt < np && k == nxt % CL;
+        const float* Vp = g.Vg + (size_t)(p >= 0 ? p : 0) * NB * ldw + rb;
+        const float* tp = g.taug + (size_t)(p >= 0 ? p : 0) * NB;
+        if (own_next && warp < NB) {
+            const int c = warp;
+            const int lc = (nxt / CL) * NB + c;
+            float* col = W + (size_t)lc * ldw + rb;
+            float x[1][E];
+            load_col<E>(col, Lr, x[0]);
+            if (p >= 0) {
+                for (int c2 = 0; c2 < NB; ++c2) {
+                    const float tau = tp[c2];
+                    if (tau != 0.f) reflect_cols<E, 1>(x, Vp + (size_t)c2 * ldw, c2, Lr, tau);
+                }
             }
-            __syncthreads();
-            const float tau = s_tau[buf];
-            for (int r = 0; r < CL; ++r) {      // push v (leading 1) and tau to every CTA
-                float* dst = cluster.map_shared_rank(vbuf + (size_t)buf * r2, r);
-                for (int i = tid; i < L; i += blockDim.x) dst[i] = i == 0 ? 1.f : colk[i];
-                if (tid == 0) *cluster.map_shared_rank(&s_tau[buf], r) = tau;
+            const int d0 = nxt * NB - rb;                      // diagonal of the panel's first column
+            for (int c2 = 0; c2 < NB; ++c2) {
+                if (c == c2) {
+                    const float tau = householder_col<E>(x[0], d0 + c2, Lr);
+                    store_col<E>(col, Lr, x[0]);
+                    if (lane == 0) s_ptau[c2] = tau;
+                }
+                panel_bar();
+                if (c > c2) {
+                    const float tau = s_ptau[c2];
+                    if (tau != 0.f) reflect_cols<E, 1>(x, col + (c2 - c) * ldw, d0 + c2, Lr, tau);
+                }
+            }
+            // publish this column's rows [nxt NB, r2) and its tau in slot nxt
+            const float4* src = reinterpret_cast<const float4*>(W + (size_t)lc * ldw);
+            float4* dst = reinterpret_cast<float4*>(g.Vg + ((size_t)nxt * NB + c) * ldw);
+            for (int q = nxt * NB / 4 + lane; q < (r2 + 3) / 4; q += 32) dst[q] = src[q];
+            if (lane == 0) g.taug[(size_t)nxt * NB + c] = s_ptau[c];
+            __threadfence();
+        } else if (p >= 0) {
+            // trailing columns of this CTA: local panels whose global panel is > p
+            int lp0 = p >= k ? (p - k) / CL + 1 : 0;
+            if (own_next) ++lp0;                               // panel p + 1 is with warps < NB
+            const int w0 = own_next ? NB : 0;
+            constexpr int NC = E >= 32 ? 1 : 2;
+            for (int q = lp0 * NB + NC * (warp - w0); q < nloc; q += NC * (nwarps - w0)) {
+                float x[NC][E];
+                bool ok[NC];
+#pragma unroll
+                for (int n = 0; n < NC; ++n) {
+                    ok[n] = q + n < nloc && gcol(q + n) < s;   // padding columns stay zero
+                    if (ok[n]) load_col<E>(W + (size_t)(q + n) * ldw + rb, Lr, x[n]);
+                    else
+#pragma unroll
+                        for (int e = 0; e < E; ++e) x[n][e] = 0.f;
+                }
+                for (int c2 = 0; c2 < NB; ++c2) {
+                    const float tau = tp[c2];
+                    if (tau != 0.f) reflect_cols<E, NC>(x, Vp + (size_t)c2 * ldw, c2, Lr, tau);
+                }
+#pragma unroll
+                for (int n = 0; n < NC; ++n)
+                    if (ok[n]) store_col<E>(W + (size_t)(q + n) * ldw + rb, Lr, x[n]);
             }
         }
-        cluster.sync();
-        const float tau = s_tau[buf];
-        const float* v = vbuf + (size_t)buf * r2;
-        const int first = (kk + 1 - k + CL - 1) / CL;         // smallest jl with jl*CL + k > kk
-        if (tau != 0.f && first + warp < nloc) {
-            float vr[E];
-            load_reflector<E>(v, L, vr);
-            for (int j2 = first + warp; j2 < nloc; j2 += nwarps)
-                apply_reflector<E>(vr, tau, W + (size_t)j2 * r2 + kk, L);
+    }
+    __syncthreads();
+    // ---- R (upper triangle of the first s rows) to global, column-major
+    for (int jl = warp; jl < nloc; jl += nwarps) {
+        const int j = gcol(jl);
+        if (j >= s) continue;
+        for (int i = lane; i <= j; i += 32) g.Rcm[(size_t)j * s + i] = W[(size_t)jl * ldw + i];
+    }
+}
+
+// Cross pairs of one tournament round: in inner round u, column j of slot 0 (c0)
+// meets column (j+u) mod b of slot 1 (c1).  Column j (lane group j; b <= groups
+// per CTA) stays in registers for the b inner rounds, the slot-1 columns pass
+// through shared memory.
+template <int G, int NVG>
+__device__ __forceinline__ void cross_rounds(float* c0, float* c1, int b, int sp, float tol2, float floor_abs,
+                                             float& meas, int& rotated) {
+    const int tid = threadIdx.x, warp = tid >> 5, grp = tid / G, gl = tid & (G - 1);
+    const bool wact = warp * (32 / G) < b;                  // warp holds a slot-0 column
+    const int j = grp;
+    const bool act = j < b;
+    ulonglong2 x[NVG];
+    if (act) {
+#pragma unroll
+        for (int v = 0; v < NVG; ++v) x[v] = *reinterpret_cast<const ulonglong2*>(c0 + (size_t)j * sp + 4 * (gl + G * v));
+    }
+    for (int u = 0; u < b; ++u) {
+        if (wact) {
+            int jj = act ? j + u : 0;
+            if (jj >= b) jj -= b;
+            jacobi_pair_x<G, NVG>(act, x, c1 + (size_t)jj * sp, tol2, floor_abs, meas, rotated);
         }
         __syncthreads();
     }
-    cluster.sync();
+    if (act) {
+#pragma unroll
+        for (int v = 0; v < NVG; ++v) *reinterpret_cast<ulonglong2*>(c0 + (size_t)j * sp + 4 * (gl + G * v)) = x[v];
+    }
+}
 
-    // ---- gather the two R^T column blocks of this CTA (positions k and P2-1-k)
+// lanes per column pair of the cluster Jacobi: 8 (fewer shuffle levels) while
+// the register-held columns fit, 16 for the longest columns
+__host__ __device__ constexpr int jac_g(int nq) { return nq >= 4 ? 16 : 8; }
+
+template <int CL, int NQ>
+__global__ void __launch_bounds__(kJacThreads, 1) core_jacobi_cluster_kernel(
+    const void* ws, int r2, int s, int b, double* __restrict__ sigma, int* __restrict__ status) {
+    constexpr int P2 = 2 * CL;
+    constexpr int G = jac_g(NQ);                               // lanes per column pair
+    constexpr int NVG = 32 * NQ / G;                           // float4 per lane per column
+    constexpr int GPW = 32 / G;                                // pair groups per warp
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int sp = 128 * NQ;                                   // padded column length of R^T
+    const size_t set_floats = 2 * (size_t)b * sp;              // two blocks of b columns
+    float* const set0 = reinterpret_cast<float*>(smem);
+    auto sets = [&](int i) { return i ? set0 + set_floats : set0; };   // Jacobi ping-pong
+    __shared__ int s_block[2][2];                             // [set][slot] block ids
+    __shared__ int s_count;
+    __shared__ unsigned int s_meas;
+    __shared__ float s_fmax;
+    __shared__ double s_norm[512];
+    __shared__ float s_red[32];
+    const int k = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const ClusterWs g = cluster_ws(const_cast<void*>(ws), r2, s);
+    if (*status == RE_ERR_NONFINITE) return;                   // the QR kernel found Inf/NaN (uniform)
+
     if (tid == 0) {
+        s_count = 0;
+        s_meas = 0u;
         s_block[0][0] = k;
         s_block[0][1] = P2 - 1 - k;
     }
-    float* slot0 = sets[0];
-    for (int64_t idx = tid; idx < 2 * (int64_t)b * sp; idx += blockDim.x) {
-        const int sl = (int)(idx / ((int64_t)b * sp));
-        const int64_t off = idx % ((int64_t)b * sp);
-        const int jj = (int)(off / sp), col = (int)(off % sp);   // entry col of R^T column c
+    // ---- the two R^T column blocks of this CTA (positions k and P2-1-k): column
+    // c = row c of R, read from R column-major (16 consecutive rows per column)
+    for (int sl = 0; sl < 2; ++sl) {
         const int blk = sl == 0 ? k : P2 - 1 - k;
-        const int c = blk * b + jj;                              // = row c of R
-        float val = 0.f;
-        if (c < s && col >= c && col < s) {
-            const float* src = cluster.map_shared_rank(W, col % CL);
-            val = src[(size_t)(col / CL) * r2 + c];
+        float* dst = sets(0) + (size_t)sl * b * sp;
+        for (int idx = tid; idx < b * sp; idx += blockDim.x) {
+            const int jj = idx % b, col = idx / b;             // jj fastest: consecutive rows of R
+            const int c = blk * b + jj;
+            float val = 0.f;
+            if (c < s && col >= c && col < s) val = g.Rcm[(size_t)col * s + c];
+            dst[(size_t)jj * sp + col] = val;
         }
-        slot0[idx] = val;                                        // slot1 follows slot0
     }
+    __syncthreads();
     cluster.sync();
 
     // ---- blocked Jacobi on R^T (length-sp columns, zero padded)
     const float tol = 4.f * kU * sqrtf((float)s);
+    const int grp = tid / G, ngrp = blockDim.x / G;
     int cur = 0;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         float amax = 0.f;
         for (int q = warp; q < 2 * b; q += nwarps) {
-            const float* a = sets[cur] + (size_t)q * sp;
+            const float* a = sets(cur) + (size_t)q * sp;
             float acc = 0.f;
             for (int i = lane; i < sp; i += 32) acc = fmaf(a[i], a[i], acc);
             amax = fmaxf(amax, warp_sum(acc));
@@ -624,15 +930,14 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         int rotated = 0;
         float meas = 0.f;
         for (int t = 0; t < P2 - 1; ++t) {
-            float* c0 = sets[cur];
+            float* c0 = sets(cur);
             float* c1 = c0 + (size_t)b * sp;
-            constexpr int G = 32;                  // one warp per pair: few pairs per round
-            const int grp = tid / G, ngrp = blockDim.x / G;
             if (t == 0) {
                 // pairs inside each block (circle ordering on b columns)
                 const int P = b + (b & 1);
                 for (int u = 0; u < P - 1; ++u) {
                     for (int base = 0; base < P; base += ngrp) {
+                        if (base + warp * GPW >= P) continue;    // no pair for this warp
                         const int q = base + grp;
                         bool act = q < P;
                         float* pa = c0;
@@ -640,29 +945,18 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
                         if (act) {
                             const int sl = q / (P / 2), kq = q % (P / 2);
                             const int e1 = circle_player(kq, u, P), e2 = circle_player(P - 1 - kq, u, P);
-                            const int p = min(e1, e2), qq = max(e1, e2);
+                            const int pp = min(e1, e2), qq = max(e1, e2);
                             act = qq < b;
                             float* bs = sl == 0 ? c0 : c1;
-                            pa = bs + (size_t)p * sp;
+                            pa = bs + (size_t)pp * sp;
                             pb = bs + (size_t)qq * sp;
                         }
-                        jacobi_pair<G, NV>(act, pa, pb, tol * tol, floor_abs, meas, rotated);
+                        jacobi_pair<G, NVG>(act, pa, pb, tol * tol, floor_abs, meas, rotated);
                     }
                     __syncthreads();
                 }
             }
-            // cross pairs: in inner round u, column j of slot 0 meets column (j+u) mod b of slot 1
-            for (int u = 0; u < b; ++u) {
-                for (int base = 0; base < b; base += ngrp) {
-                    const int j = base + grp;
-                    const bool act = j < b;
-                    int jj = act ? j + u : 0;
-                    if (jj >= b) jj -= b;
-                    jacobi_pair<G, NV>(act, c0 + (size_t)(act ? j : 0) * sp, c1 + (size_t)jj * sp, tol * tol,
-                                       floor_abs, meas, rotated);
-                }
-                __syncthreads();
-            }
+            cross_rounds<G, NVG>(c0, c1, b, sp, tol * tol, floor_abs, meas, rotated);
             // tournament positions 1..P2-1 move up by one: pull the new blocks from
             // the current set of their source CTAs into this CTA's other set
             cluster.sync();
@@ -672,17 +966,26 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
             auto slot_of = [](int pos) { return pos < CL ? 0 : 1; };
             const int nxt = cur ^ 1;
             const int n4 = b * sp / 4;
-            for (int sl = 0; sl < 2; ++sl) {
-                const int src = sl == 0 ? src0 : src1;
-                const float4* from;
-                if (src >= 0) {
-                    const float* rs = cluster.map_shared_rank(sets[cur], cta_of(src));
-                    from = reinterpret_cast<const float4*>(rs + (size_t)slot_of(src) * b * sp);
-                } else {
-                    from = reinterpret_cast<const float4*>(sets[cur]);
+            const float4* from0 =
+                src0 >= 0 ? reinterpret_cast<const float4*>(cluster.map_shared_rank(sets(cur), cta_of(src0)) +
+                                                            (size_t)slot_of(src0) * b * sp)
+                          : reinterpret_cast<const float4*>(sets(cur));
+            const float4* from1 = reinterpret_cast<const float4*>(cluster.map_shared_rank(sets(cur), cta_of(src1)) +
+                                                                  (size_t)slot_of(src1) * b * sp);
+            float4* to = reinterpret_cast<float4*>(sets(nxt));
+            constexpr int U = 8;                                   // loads in flight per thread
+            for (int i0 = tid; i0 < 2 * n4; i0 += U * kJacThreads) {
+                float4 tmp[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * kJacThreads;
+                    if (i < 2 * n4) tmp[u] = i < n4 ? from0[i] : from1[i - n4];
                 }
-                float4* to = reinterpret_cast<float4*>(sets[nxt] + (size_t)sl * b * sp);
-                for (int i = tid; i < n4; i += blockDim.x) to[i] = from[i];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * kJacThreads;
+                    if (i < 2 * n4) to[i] = tmp[u];
+                }
             }
             if (tid == 0) {
                 s_block[nxt][0] = src0 >= 0
@@ -710,46 +1013,46 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_sigma_cluster_kernel(
         if (k == 0 && tid == 0) status[2] = sweep + 1;
         if (total == 0 || worst < kStopFactor * kU * sqrtf((float)s)) break;
     }
-    slot0 = sets[cur];
     // ---- norms gathered in CTA 0
     for (int q = warp; q < 2 * b; q += nwarps) {
         const int sl = q / b, j = q % b;
         const int c = s_block[cur][sl] * b + j;
-        const double nv = col_norm(slot0 + (size_t)q * sp, sp);
+        const double nv = col_norm(sets(cur) + (size_t)q * sp, sp);
         if (lane == 0 && c < s) *cluster.map_shared_rank(&s_norm[c], 0) = nv;
     }
     cluster.sync();
     if (k == 0) {
-        sort_desc(s_norm, s, up, sigma);
+        sort_desc(s_norm, s, *g.up, sigma);
         if (tid == 0) *status = RE_OK;
     }
 }
 
-size_t cluster_smem(int CL, int r2, int s, int* b_out) {
-    const int nloc = (s + CL - 1) / CL;
+size_t qr_cluster_smem(int CL, int r2, int s) {
+    const int np = (s + kPanel - 1) / kPanel;
+    const size_t nloc = (size_t)(np + CL - 1) / CL * kPanel;
+    return sizeof(float) * nloc * (size_t)cluster_ldw(r2);
+}
+size_t jac_cluster_smem(int CL, int s, int* b_out) {
     const int b = (s + 2 * CL - 1) / (2 * CL);
     const size_t sp = (size_t)(s + 127) / 128 * 128;
-    const size_t set_floats = 2 * (size_t)b * sp;
     *b_out = b;
-    return sizeof(float) * ((std::max((size_t)nloc * r2, set_floats) + 31) / 32 * 32 +
-                            (2 * (size_t)r2 + 31) / 32 * 32 + set_floats);
+    return sizeof(float) * 4 * (size_t)b * sp;
 }
 
-template <int CL, int NV, int E>
-cudaError_t launch_cluster_sigma_nv(const double* core, int r2, int s, int64_t ld, double* sigma,
-                                    int* status, cudaStream_t st) {
-    int b = 0;
-    const size_t smem = cluster_smem(CL, r2, s, &b);
-    auto kern = core_sigma_cluster_kernel<CL, NV, E>;
+template <int CL>
+cudaError_t set_cluster_attrs(const void* kern, size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && CL > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+template <int CL, class... Args>
+cudaError_t launch_cluster(void (*kern)(Args...), int threads, size_t smem, cudaStream_t st, Args... args) {
+    cudaError_t e = set_cluster_attrs<CL>(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
-    if (CL > 8) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL, 1, 1);
-    cfg.blockDim = dim3(kSvdThreads, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -759,28 +1062,38 @@ cudaError_t launch_cluster_sigma_nv(const double* core, int r2, int s, int64_t l
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, core, r2, s, ld, b, sigma, status);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <int CL, int NV>
-cudaError_t launch_cluster_sigma_e(const double* core, int r2, int s, int64_t ld, double* sigma, int* status,
-                                   cudaStream_t st) {
-    // column length r2 <= 32 E; this kernel only takes cores that do not fit one CTA (r2 > 128)
-    const int e = (r2 + 31) / 32;
-    if (e <= 8) return launch_cluster_sigma_nv<CL, NV, 8>(core, r2, s, ld, sigma, status, st);
-    if (e <= 16) return launch_cluster_sigma_nv<CL, NV, 16>(core, r2, s, ld, sigma, status, st);
-    if (e <= 32) return launch_cluster_sigma_nv<CL, NV, 32>(core, r2, s, ld, sigma, status, st);
+template <int CL>
+cudaError_t launch_qr_cluster(const double* core, int r2, int s, int64_t ld, void* ws, double* sigma, int* status,
+                              cudaStream_t st) {
+    const size_t smem = qr_cluster_smem(CL, r2, s);
+    const int e = (r2 + 31) / 32;                             // column length r2 <= 32 E
+    if (e <= 8)
+        return launch_cluster<CL>(core_qr_cluster_kernel<CL, 8>, kSvdThreads, smem, st, core, r2, s, ld, ws, sigma,
+                                  status);
+    if (e <= 16)
+        return launch_cluster<CL>(core_qr_cluster_kernel<CL, 16>, kSvdThreads, smem, st, core, r2, s, ld, ws, sigma,
+                                  status);
+    if (e <= 32)
+        return launch_cluster<CL>(core_qr_cluster_kernel<CL, 32>, kSvdThreads, smem, st, core, r2, s, ld, ws, sigma,
+                                  status);
     return cudaErrorInvalidValue;
 }
 
 template <int CL>
-cudaError_t launch_cluster_sigma(const double* core, int r2, int s, int64_t ld, double* sigma,
-                                 int* status, cudaStream_t st) {
-    switch ((s + 127) / 128) {
-        case 1: return launch_cluster_sigma_e<CL, 1>(core, r2, s, ld, sigma, status, st);
-        case 2: return launch_cluster_sigma_e<CL, 2>(core, r2, s, ld, sigma, status, st);
-        case 3: return launch_cluster_sigma_e<CL, 3>(core, r2, s, ld, sigma, status, st);
-        case 4: return launch_cluster_sigma_e<CL, 4>(core, r2, s, ld, sigma, status, st);
+cudaError_t launch_jacobi_cluster(void* ws, int r2, int s, double* sigma, int* status, cudaStream_t st) {
+    int b = 0;
+    const size_t smem = jac_cluster_smem(CL, s, &b);
+    const void* cws = ws;
+    const int nq = (s + 127) / 128;
+    if (nq < 1 || nq > 4 || b > kJacThreads / jac_g(nq)) return cudaErrorInvalidValue;   // one lane group per slot-0 column
+    switch (nq) {
+        case 1: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 1>, kJacThreads, smem, st, cws, r2, s, b, sigma, status);
+        case 2: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 2>, kJacThreads, smem, st, cws, r2, s, b, sigma, status);
+        case 3: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 3>, kJacThreads, smem, st, cws, r2, s, b, sigma, status);
+        case 4: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 4>, kJacThreads, smem, st, cws, r2, s, b, sigma, status);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -855,12 +1168,12 @@ constexpr size_t kSmemLimit = 210 * 1024;
 
 size_t cta_smem(int r2, int s) {
     const size_t sp = (size_t)(s + 63) / 64 * 64;
-    return sizeof(float) * (((size_t)r2 * s + 31) / 32 * 32 + sp * s);
+    return sizeof(float) * (((size_t)cta_ldw(r2) * s + 31) / 32 * 32 + sp * s);
 }
 
 }  // namespace
 
-size_t svd_workspace_bytes(int, int) { return 256; }
+size_t svd_workspace_bytes(int r2, int s) { return sizeof(float) * cluster_ws_floats(r2, s) + 256; }
 
 namespace {
 
@@ -908,16 +1221,24 @@ cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void*, double* sigma,
+cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws, double* sigma,
                               int* status, cudaStream_t st, int cert_r1, float cert_ratio) {
     if (s <= 0) return cudaSuccess;
     if (s > 512) return cudaErrorInvalidValue;
     if (cta_smem(r2, s) <= kSmemLimit)
         return launch_core_sigma_batched(core, r2, s, ld, 0, 1, sigma, 0, status, st, nullptr, cert_r1,
                                          cert_ratio);
+    // larger cores: QR on a cluster, then Jacobi on a cluster; ws holds
+    // svd_workspace_bytes(r2, s) (16-byte aligned)
+    if (!ws) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (qr_cluster_smem(8, r2, s) <= kSmemLimit) e = launch_qr_cluster<8>(core, r2, s, ld, ws, sigma, status, st);
+    else if (qr_cluster_smem(16, r2, s) <= kSmemLimit) e = launch_qr_cluster<16>(core, r2, s, ld, ws, sigma, status, st);
+    else return cudaErrorInvalidValue;
+    if (e != cudaSuccess) return e;
     int b = 0;
-    if (cluster_smem(8, r2, s, &b) <= kSmemLimit) return launch_cluster_sigma<8>(core, r2, s, ld, sigma, status, st);
-    if (cluster_smem(16, r2, s, &b) <= kSmemLimit) return launch_cluster_sigma<16>(core, r2, s, ld, sigma, status, st);
+    if (jac_cluster_smem(8, s, &b) <= kSmemLimit) return launch_jacobi_cluster<8>(ws, r2, s, sigma, status, st);
+    if (jac_cluster_smem(16, s, &b) <= kSmemLimit) return launch_jacobi_cluster<16>(ws, r2, s, sigma, status, st);
     return cudaErrorInvalidValue;
 }
 
