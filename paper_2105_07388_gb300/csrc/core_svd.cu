@@ -156,15 +156,12 @@ __device__ __forceinline__ bool rotate_pair(bool active, ulonglong2 (&x)[NV], ul
     if (!active || !(ag > floor_abs) || !(ga * ga > tol2 * ab)) return false;
     rotated = 1;
     meas_max = fmaxf(meas_max, ag * rsqrtf(ab));
-    const float zeta = __fdividef(be - al, ga + ga);
-    const float az = fabsf(zeta);
-    float tt;
-    if (az > 1e15f) {
-        tt = __fdividef(0.5f, zeta);
-    } else {
-        const float q = fmaf(zeta, zeta, 1.f);
-        tt = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
-    }
+    // t = tan(theta) = 2 ga / (d + sign(d) sqrt(d^2 + 4 ga^2)), d = be - al: the
+    // smaller root of t^2 + (d / ga) t - 1 = 0 (the usual zeta form multiplied
+    // through by 2 |ga|; d and the root share a sign, so nothing cancels)
+    const float d = be - al, g2 = ga + ga;
+    const float r2 = fmaf(d, d, g2 * g2);
+    const float tt = __fdividef(g2, d + copysignf(r2 * rsqrtf(r2), d));
     const float c = rsqrtf(fmaf(tt, tt, 1.f));
     const float sn = c * tt;
     const u64 c2 = pk2(c, c), s2 = pk2(sn, sn), n2 = pk2(-sn, -sn);
@@ -264,72 +261,7 @@ __device__ void sort_desc(const double* s_norm, int n, double scale, double* out
     }
 }
 
-// Register-resident versions for a column of length L <= 32*E (one warp; lane
-// l holds entries l, l+32, ..., masked past L).  householder_regs: reflector of
-// x = col[0..L) (H = I - tau v v^T, v[0] = 1): v[1..) goes to col[1..), beta to
-// col[0]; returns tau.
-template <int E>
-__device__ __forceinline__ float householder_regs(float* col, int L) {
-    const int lane = threadIdx.x & 31;
-    float x[E];
-    float ss = 0.f;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = lane + 32 * e;
-        x[e] = i < L ? col[i] : 0.f;
-        if (i >= 1) ss = fmaf(x[e], x[e], ss);
-    }
-    ss = warp_sum(ss);
-    const float x0 = __shfl_sync(0xffffffffu, x[0], 0);
-    float tau = 0.f, beta = x0;
-    if (ss > 0.f) {
-        const float nrm = sqrtf(fmaf(x0, x0, ss));
-        beta = -copysignf(nrm, x0);
-        tau = (beta - x0) / beta;
-        const float scale = 1.f / (x0 - beta);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int i = lane + 32 * e;
-            if (i >= 1 && i < L) col[i] = x[e] * scale;
-        }
-    }
-    if (lane == 0) col[0] = beta;
-    __syncwarp();
-    return tau;
-}
-
-// Load v (v[0] = 1, entries 1..L-1 from vsrc) into registers.
-template <int E>
-__device__ __forceinline__ void load_reflector(const float* vsrc, int L, float (&v)[E]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = lane + 32 * e;
-        v[e] = i < L ? (i == 0 ? 1.f : vsrc[i]) : 0.f;
-    }
-}
-
-// c <- (I - tau v v^T) c for one column of length L (one warp).
-template <int E>
-__device__ __forceinline__ void apply_reflector(const float (&v)[E], float tau, float* c, int L) {
-    const int lane = threadIdx.x & 31;
-    float x[E];
-    float w = 0.f;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = lane + 32 * e;
-        x[e] = i < L ? c[i] : 0.f;
-        w = fmaf(v[e], x[e], w);
-    }
-    w = warp_sum(w) * tau;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = lane + 32 * e;
-        if (i < L) c[i] = fmaf(-w, v[e], x[e]);
-    }
-}
-
-// Column held in registers across several reflectors (cluster QR): entries
+// Column held in registers across several reflectors (one warp): entries
 // i = lane + 32 e of a column segment of length L, zero past L.
 template <int E>
 __device__ __forceinline__ void load_col(const float* col, int L, float (&x)[E]) {
@@ -350,9 +282,10 @@ __device__ __forceinline__ void store_col(float* col, int L, const float (&x)[E]
     }
 }
 
-// Reflector of the register column x below its diagonal entry d (d < 32): the
-// same arithmetic as householder_regs on x[d..L); entries past d become v
-// (v[d] = 1 implicit), x[d] becomes beta; returns tau.
+// Householder reflector H = I - tau v v^T of the register column segment
+// x[d..L) (d < 32): beta = -sign(x_d) ||x[d..L)||, v = (x - beta e_d) / (x_d - beta)
+// so that v[d] = 1 (implicit); entries past d become v, x[d] becomes beta;
+// returns tau = (beta - x_d) / beta (0 when x[d+1..L) is zero).
 template <int E>
 __device__ __forceinline__ float householder_col(float (&x)[E], int d, int L) {
     const int lane = threadIdx.x & 31;
@@ -409,6 +342,12 @@ __device__ __forceinline__ void reflect_cols(float (&x)[NC][E], const float* vco
     }
 }
 
+// Named barrier of the kPanel warps that factor a panel (the other warps of
+// the CTA do not take part).
+__device__ __forceinline__ void panel_bar() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kPanel * 32) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // One CTA per core: core -> shared memory (column-major, scaled), QR in place,
 // R^T -> second region, Jacobi on R^T, norms.  blockIdx.x selects the core
@@ -432,7 +371,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     float* W = reinterpret_cast<float*>(smem);          // r2 x s, column-major, column stride ldw
     float* Rt = W + ((size_t)ldw * s + 31) / 32 * 32;   // sp x s, column c = row c of R (128-B aligned)
     __shared__ double s_norm[512];
-    __shared__ float s_tau, s_red[32];
+    __shared__ float s_ptau[2][kPanel], s_red[32];
     __shared__ int s_bad, s_flag;
     __shared__ unsigned int s_meas;
     __shared__ u64 s_dmax;
@@ -475,21 +414,74 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     }
     __syncthreads();
 
-    // Householder QR: column k's reflector, then the trailing columns (reflector
-    // and each column held in registers, r2 <= 32 E)
-    for (int k = 0; k < s; ++k) {
-        float* colk = W + (size_t)k * ldw + k;
-        const int L = r2 - k;
-        if (warp == 0) {
-            const float tau = householder_regs<E>(colk, L);
-            if (lane == 0) s_tau = tau;
-        }
-        __syncthreads();
-        const float tau = s_tau;
-        if (tau != 0.f && k + 1 + warp < s) {
-            float v[E];
-            load_reflector<E>(colk, L, v);
-            for (int j = k + 1 + warp; j < s; j += nwarps) apply_reflector<E>(v, tau, W + (size_t)j * ldw + k, L);
+    // Householder QR in panels of kPanel columns with one panel of lookahead.
+    // Iteration p: warps 0..kPanel-1 apply the reflectors of panel p to panel
+    // p + 1 and factor it (each reflector stays in W below its diagonal, the taus
+    // in s_ptau[(p + 1) & 1]); the other warps apply panel p's reflectors to the
+    // columns after panel p + 1.  Columns are held in registers (r2 <= 32 E).
+    {
+        constexpr int NB = kPanel;
+        const int np = (s + NB - 1) / NB;
+        for (int p = -1; p < np; ++p) {
+            if (p >= 0) __syncthreads();
+            const int rb = p >= 0 ? p * NB : 0;                // first row held in registers
+            const int Lr = r2 - rb;
+            const int nxt = p + 1;
+            const bool has_next = nxt < np;
+            const float* Vp = W + (size_t)(p >= 0 ? p : 0) * NB * ldw + rb;   // reflector c2 at Vp + c2 ldw
+            const float* tp = s_ptau[(p >= 0 ? p : 0) & 1];
+            if (has_next && warp < NB) {
+                const int c = warp;
+                const bool has = nxt * NB + c < s;
+                float* col = W + (size_t)(nxt * NB + c) * ldw + rb;
+                float x[1][E];
+                if (has) {
+                    load_col<E>(col, Lr, x[0]);
+                    if (p >= 0) {
+                        for (int c2 = 0; c2 < NB; ++c2) {
+                            const float tau = tp[c2];
+                            if (tau != 0.f) reflect_cols<E, 1>(x, Vp + (size_t)c2 * ldw, c2, Lr, tau);
+                        }
+                    }
+                }
+                const int d0 = nxt * NB - rb;                  // diagonal of the panel's first column
+                for (int c2 = 0; c2 < NB; ++c2) {
+                    if (c == c2) {
+                        float tau = 0.f;
+                        if (has) {
+                            tau = householder_col<E>(x[0], d0 + c2, Lr);
+                            store_col<E>(col, Lr, x[0]);
+                        }
+                        if (lane == 0) s_ptau[nxt & 1][c2] = tau;
+                    }
+                    panel_bar();
+                    if (c > c2 && has) {
+                        const float tau = s_ptau[nxt & 1][c2];
+                        if (tau != 0.f) reflect_cols<E, 1>(x, col + (c2 - c) * ldw, d0 + c2, Lr, tau);
+                    }
+                }
+            } else if (p >= 0) {
+                // columns after panel p + 1
+                const int w0 = has_next ? NB : 0;
+                constexpr int NC = E >= 16 ? 1 : 2;
+                for (int q = (nxt + 1) * NB + NC * (warp - w0); q < s; q += NC * (nwarps - w0)) {
+                    float x[NC][E];
+#pragma unroll
+                    for (int n = 0; n < NC; ++n) {
+                        if (q + n < s) load_col<E>(W + (size_t)(q + n) * ldw + rb, Lr, x[n]);
+                        else
+#pragma unroll
+                            for (int e = 0; e < E; ++e) x[n][e] = 0.f;
+                    }
+                    for (int c2 = 0; c2 < NB; ++c2) {
+                        const float tau = tp[c2];
+                        if (tau != 0.f) reflect_cols<E, NC>(x, Vp + (size_t)c2 * ldw, c2, Lr, tau);
+                    }
+#pragma unroll
+                    for (int n = 0; n < NC; ++n)
+                        if (q + n < s) store_col<E>(W + (size_t)(q + n) * ldw + rb, Lr, x[n]);
+                }
+            }
         }
         __syncthreads();
     }
@@ -640,10 +632,6 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
 // the cross rounds each CTA's slot-0 columns stay in registers.
 
 __host__ __device__ __forceinline__ int cluster_ldw(int r2) { return (r2 + 31) / 32 * 32 + 4; }
-
-__device__ __forceinline__ void panel_bar() {
-    asm volatile("bar.sync 1, %0;" ::"r"(kPanel * 32) : "memory");
-}
 
 // Global scratch of the cluster path (floats): R column-major (s x s), the
 // reflector slots (np kPanel columns of stride ldw), their taus, and the
@@ -828,10 +816,10 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_qr_cluster_kernel(
 // Cross pairs of one tournament round: in inner round u, column j of slot 0 (c0)
 // meets column (j+u) mod b of slot 1 (c1).  Column j (lane group j; b <= groups
 // per CTA) stays in registers for the b inner rounds, the slot-1 columns pass
-// through shared memory.
+// through shared memory; at the end column j is written to x_dst + j sp.
 template <int G, int NVG>
-__device__ __forceinline__ void cross_rounds(float* c0, float* c1, int b, int sp, float tol2, float floor_abs,
-                                             float& meas, int& rotated) {
+__device__ __forceinline__ void cross_rounds(const float* c0, float* c1, float* x_dst, int b, int sp, float tol2,
+                                             float floor_abs, float& meas, int& rotated) {
     const int tid = threadIdx.x, warp = tid >> 5, grp = tid / G, gl = tid & (G - 1);
     const bool wact = warp * (32 / G) < b;                  // warp holds a slot-0 column
     const int j = grp;
@@ -849,9 +837,9 @@ __device__ __forceinline__ void cross_rounds(float* c0, float* c1, int b, int sp
         }
         __syncthreads();
     }
-    if (act) {
+    if (act) {   // slot-0 column j to its next place (possibly another CTA's shared memory)
 #pragma unroll
-        for (int v = 0; v < NVG; ++v) *reinterpret_cast<ulonglong2*>(c0 + (size_t)j * sp + 4 * (gl + G * v)) = x[v];
+        for (int v = 0; v < NVG; ++v) *reinterpret_cast<ulonglong2*>(x_dst + (size_t)j * sp + 4 * (gl + G * v)) = x[v];
     }
 }
 
@@ -872,7 +860,6 @@ __global__ void __launch_bounds__(kJacThreads, 1) core_jacobi_cluster_kernel(
     const size_t set_floats = 2 * (size_t)b * sp;              // two blocks of b columns
     float* const set0 = reinterpret_cast<float*>(smem);
     auto sets = [&](int i) { return i ? set0 + set_floats : set0; };   // Jacobi ping-pong
-    __shared__ int s_block[2][2];                             // [set][slot] block ids
     __shared__ int s_count;
     __shared__ unsigned int s_meas;
     __shared__ float s_fmax;
@@ -886,8 +873,6 @@ __global__ void __launch_bounds__(kJacThreads, 1) core_jacobi_cluster_kernel(
     if (tid == 0) {
         s_count = 0;
         s_meas = 0u;
-        s_block[0][0] = k;
-        s_block[0][1] = P2 - 1 - k;
     }
     // ---- the two R^T column blocks of this CTA (positions k and P2-1-k): column
     // c = row c of R, read from R column-major (16 consecutive rows per column)
@@ -956,45 +941,25 @@ __global__ void __launch_bounds__(kJacThreads, 1) core_jacobi_cluster_kernel(
                     __syncthreads();
                 }
             }
-            cross_rounds<G, NVG>(c0, c1, b, sp, tol * tol, floor_abs, meas, rotated);
-            // tournament positions 1..P2-1 move up by one: pull the new blocks from
-            // the current set of their source CTAs into this CTA's other set
-            cluster.sync();
-            const int src0 = (k == 0) ? -1 : (k == 1 ? P2 - 1 : k - 1);
-            const int src1 = P2 - 2 - k;
-            auto cta_of = [](int pos) { return pos < CL ? pos : P2 - 1 - pos; };
-            auto slot_of = [](int pos) { return pos < CL ? 0 : 1; };
+            // tournament positions 1..P2-1 move up by one, position 0 stays (slot 0 of
+            // CTA k is position k, slot 1 is position P2-1-k): each CTA pushes its two
+            // blocks into the other set of the CTAs holding their next positions; that
+            // set was last used in the previous round, before the barrier below
             const int nxt = cur ^ 1;
-            const int n4 = b * sp / 4;
-            const float4* from0 =
-                src0 >= 0 ? reinterpret_cast<const float4*>(cluster.map_shared_rank(sets(cur), cta_of(src0)) +
-                                                            (size_t)slot_of(src0) * b * sp)
-                          : reinterpret_cast<const float4*>(sets(cur));
-            const float4* from1 = reinterpret_cast<const float4*>(cluster.map_shared_rank(sets(cur), cta_of(src1)) +
-                                                                  (size_t)slot_of(src1) * b * sp);
-            float4* to = reinterpret_cast<float4*>(sets(nxt));
-            constexpr int U = 8;                                   // loads in flight per thread
-            for (int i0 = tid; i0 < 2 * n4; i0 += U * kJacThreads) {
-                float4 tmp[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int i = i0 + u * kJacThreads;
-                    if (i < 2 * n4) tmp[u] = i < n4 ? from0[i] : from1[i - n4];
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int i = i0 + u * kJacThreads;
-                    if (i < 2 * n4) to[i] = tmp[u];
-                }
+            const int d0 = k == 0 ? 0 : (k < CL - 1 ? k + 1 : CL - 1);
+            const int sl0 = k == CL - 1 ? 1 : 0;
+            const int d1 = k == 0 ? 1 : k - 1;
+            const int sl1 = k == 0 ? 0 : 1;
+            float* x_dst = cluster.map_shared_rank(sets(nxt) + (size_t)sl0 * b * sp, d0);
+            cross_rounds<G, NVG>(c0, c1, x_dst, b, sp, tol * tol, floor_abs, meas, rotated);
+            {
+                const float4* from = reinterpret_cast<const float4*>(c1);
+                float4* to = reinterpret_cast<float4*>(cluster.map_shared_rank(sets(nxt) + (size_t)sl1 * b * sp, d1));
+                const int n4 = b * sp / 4;
+                for (int i = tid; i < n4; i += kJacThreads) to[i] = from[i];
             }
-            if (tid == 0) {
-                s_block[nxt][0] = src0 >= 0
-                                      ? cluster.map_shared_rank(&s_block[cur][0], cta_of(src0))[slot_of(src0)]
-                                      : s_block[cur][0];
-                s_block[nxt][1] = cluster.map_shared_rank(&s_block[cur][0], cta_of(src1))[slot_of(src1)];
-            }
+            cluster.sync();
             cur = nxt;
-            __syncthreads();
         }
         fold_sweep_flags(rotated, meas, &s_count, &s_meas);
         cluster.sync();
@@ -1016,7 +981,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) core_jacobi_cluster_kernel(
     // ---- norms gathered in CTA 0
     for (int q = warp; q < 2 * b; q += nwarps) {
         const int sl = q / b, j = q % b;
-        const int c = s_block[cur][sl] * b + j;
+        const int c = (sl == 0 ? k : P2 - 1 - k) * b + j;   // a whole sweep returns every block home
         const double nv = col_norm(sets(cur) + (size_t)q * sp, sp);
         if (lane == 0 && c < s) *cluster.map_shared_rank(&s_norm[c], 0) = nv;
     }
