@@ -156,12 +156,15 @@ __device__ __forceinline__ bool rotate_pair(bool active, ulonglong2 (&x)[NV], ul
     if (!active || !(ag > floor_abs) || !(ga * ga > tol2 * ab)) return false;
     rotated = 1;
     meas_max = fmaxf(meas_max, ag * rsqrtf(ab));
-    // t = tan(theta) = 2 ga / (d + sign(d) sqrt(d^2 + 4 ga^2)), d = be - al: the
-    // smaller root of t^2 + (d / ga) t - 1 = 0 (the usual zeta form multiplied
-    // through by 2 |ga|; d and the root share a sign, so nothing cancels)
-    const float d = be - al, g2 = ga + ga;
-    const float r2 = fmaf(d, d, g2 * g2);
-    const float tt = __fdividef(g2, d + copysignf(r2 * rsqrtf(r2), d));
+    const float zeta = __fdividef(be - al, ga + ga);
+    const float az = fabsf(zeta);
+    float tt;
+    if (az > 1e15f) {
+        tt = __fdividef(0.5f, zeta);
+    } else {
+        const float q = fmaf(zeta, zeta, 1.f);
+        tt = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
+    }
     const float c = rsqrtf(fmaf(tt, tt, 1.f));
     const float sn = c * tt;
     const u64 c2 = pk2(c, c), s2 = pk2(sn, sn), n2 = pk2(-sn, -sn);
@@ -285,24 +288,30 @@ __device__ __forceinline__ void store_col(float* col, int L, const float (&x)[E]
 // Householder reflector H = I - tau v v^T of the register column segment
 // x[d..L) (d < 32): beta = -sign(x_d) ||x[d..L)||, v = (x - beta e_d) / (x_d - beta)
 // so that v[d] = 1 (implicit); entries past d become v, x[d] becomes beta;
-// returns tau = (beta - x_d) / beta (0 when x[d+1..L) is zero).
+// returns tau = (beta - x_d) / beta (0 when x[d+1..L) is zero).  tau and the
+// scaling use the fast division: the relative error of a few ulp in tau leaves
+// H orthogonal to the FP32 rounding level of the rest of the path.
 template <int E>
 __device__ __forceinline__ float householder_col(float (&x)[E], int d, int L) {
     const int lane = threadIdx.x & 31;
-    float ss = 0.f;
+    float ss0 = 0.f, ss1 = 0.f;                          // two chains: half the dependent latency
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = lane + 32 * e;
-        if (i > d && i < L) ss = fmaf(x[e], x[e], ss);
+        if (i > d && i < L) {
+            if (e & 1) ss1 = fmaf(x[e], x[e], ss1);
+            else ss0 = fmaf(x[e], x[e], ss0);
+        }
     }
-    ss = warp_sum(ss);
+    const float ss = warp_sum(ss0 + ss1);
     const float x0 = __shfl_sync(0xffffffffu, x[0], d);
     float tau = 0.f;
     if (ss > 0.f) {
         const float nrm = sqrtf(fmaf(x0, x0, ss));
         const float beta = -copysignf(nrm, x0);
-        tau = (beta - x0) / beta;
-        const float scale = 1.f / (x0 - beta);
+        // fast divisions (about 2 ulp): H stays orthogonal to the FP32 level
+        tau = __fdividef(beta - x0, beta);
+        const float scale = __fdividef(1.f, x0 - beta);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i = lane + 32 * e;
@@ -319,16 +328,21 @@ template <int E, int NC>
 __device__ __forceinline__ void reflect_cols(float (&x)[NC][E], const float* vcol, int d, int L, float tau) {
     const int lane = threadIdx.x & 31;
     float v[E];
-    float w[NC];
+    float w[NC], w1[NC];                                  // two chains per column
 #pragma unroll
-    for (int n = 0; n < NC; ++n) w[n] = 0.f;
+    for (int n = 0; n < NC; ++n) w[n] = w1[n] = 0.f;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = lane + 32 * e;
         v[e] = (i > d && i < L) ? vcol[i] : (i == d ? 1.f : 0.f);
 #pragma unroll
-        for (int n = 0; n < NC; ++n) w[n] = fmaf(v[e], x[n][e], w[n]);
+        for (int n = 0; n < NC; ++n) {
+            if (e & 1) w1[n] = fmaf(v[e], x[n][e], w1[n]);
+            else w[n] = fmaf(v[e], x[n][e], w[n]);
+        }
     }
+#pragma unroll
+    for (int n = 0; n < NC; ++n) w[n] += w1[n];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -746,6 +760,15 @@ __global__ void __launch_bounds__(kSvdThreads, 1) core_qr_cluster_kernel(
         const bool own_next = nxt < np && k == nxt % CL;
         const float* Vp = g.Vg + (size_t)(p >= 0 ? p : 0) * NB * ldw + rb;
         const float* tp = g.taug + (size_t)(p >= 0 ? p : 0) * NB;
+        if (p >= 0) {
+            // request every line of V_p and its taus at once: the reflector loads
+            // below then hit L1 instead of paying one L2 round trip each
+            const int lpc = (Lr + 31) / 32 + 1;                // 128-byte steps per column
+            for (int i = tid; i < NB * lpc + 1; i += blockDim.x) {
+                const float* a = i < NB * lpc ? Vp + (size_t)(i / lpc) * ldw + 32 * (i % lpc) : tp;
+                asm volatile("prefetch.L1 [%0];" ::"l"(a));
+            }
+        }
         if (own_next && warp < NB) {
             const int c = warp;
             const int lc = (nxt / CL) * NB + c;
