@@ -78,10 +78,12 @@ def haar_orthonormal(m: int, k: int, seed: int, device="cpu") -> torch.Tensor:
     """m x k matrix with orthonormal columns, Haar distributed (QR of N(0,1))."""
     g = _gen(seed, device)
     G = torch.randn(m, k, generator=g, dtype=torch.float64, device=device)
-    Q, R = torch.linalg.qr(G)
+    # the factorisation runs on the host (the device linear-algebra library is an
+    # optional part of PyTorch installs; the input numbers stay the device draw)
+    Q, R = torch.linalg.qr(G.cpu())
     d = torch.sign(torch.diagonal(R))
     d[d == 0] = 1.0
-    return Q * d
+    return (Q * d).to(device)
 
 
 def haar_matrix(m: int, n: int, sigma: torch.Tensor, seed: int, device="cpu",
