@@ -425,22 +425,34 @@ __global__ void __launch_bounds__(256) left_kernel(uint64_t seed, const float* _
 // owns 32 consecutive outputs (one per lane, so every load is a 128-byte line),
 // warp w sums splits w, w+8, w+16, ..., and the 8 warp sums are added in warp
 // order (the result does not depend on scheduling).
+// Sum of the split-K partials of each core entry, in a fixed order (lanes over
+// entries, warps over splits, then warp 0 combines the 8 warp sums).  Each warp
+// accumulates in FP32 with an error-free TwoSum correction (s + c carries the
+// sum to about u^2 relative, as good as an FP64 accumulation for these term
+// counts) because FP64 adds issue at 1/64 of the FP32 rate on this part.
 __global__ void __launch_bounds__(256) left_reduce_kernel(const float* __restrict__ part, int splits, int R,
                                                           int S, int row0, int col0, double* __restrict__ core,
                                                           int64_t ld_core) {
-    __shared__ double s_sum[8][32];
+    __shared__ float s_hi[8][32], s_lo[8][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t total = (int64_t)R * S;
     const int64_t idx = (int64_t)blockIdx.x * 32 + lane;
-    double sum = 0.0;
+    float sum = 0.f, comp = 0.f;
     if (idx < total)
-        for (int p = w; p < splits; p += 8) sum += (double)part[(int64_t)p * total + idx];
-    s_sum[w][lane] = sum;
+        for (int p = w; p < splits; p += 8) {
+            const float x = part[(int64_t)p * total + idx];
+            const float t = sum + x;                       // TwoSum(sum, x)
+            const float bp = t - sum;
+            comp += (sum - (t - bp)) + (x - bp);
+            sum = t;
+        }
+    s_hi[w][lane] = sum;
+    s_lo[w][lane] = comp;
     __syncthreads();
     if (w == 0 && idx < total) {
-        double t = s_sum[0][lane];
+        double t = (double)s_hi[0][lane] + (double)s_lo[0][lane];
 #pragma unroll
-        for (int u = 1; u < 8; ++u) t += s_sum[u][lane];
+        for (int u = 1; u < 8; ++u) t += (double)s_hi[u][lane] + (double)s_lo[u][lane];
         const int r = (int)(idx / S), c = (int)(idx % S);
         core[(int64_t)(row0 + r) * ld_core + col0 + c] = t;
     }

@@ -160,6 +160,21 @@ __device__ __forceinline__ int phys_sw(int idx) {
     return (B << 7) | ((((idx >> 2) & 31) ^ (B & 7)) << 2) | (idx & 3);
 }
 
+// phys_sw in closed form for the two transposes of thread j: phase 2 touches
+// logical base + 4c (base = (j >> 2) 128 + (j & 3)), at o2[c & 7] + 4 (c & 24);
+// phase 3 touches logical (j >> 7) 4096 + (j & 127) + 128 k, at o3[k & 7] + 128 k.
+// With c and k unrolled, every access is a precomputed register plus an
+// immediate offset.
+__device__ __forceinline__ void sw_offsets(int j, int (&o2)[8], int (&o3)[8]) {
+    const int b = (j >> 2) & 7, p2 = (j >> 2) * 128 + (j & 3);
+    const int jj = (j & 127) >> 2, p3 = (j >> 7) * 4096 + (j & 3);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        o2[q] = p2 + 4 * (q ^ b);
+        o3[q] = p3 + 4 * (jj ^ q);
+    }
+}
+
 __device__ __forceinline__ void bfly2(float& a0, float& a1, float& b0, float& b1) {
     unsigned long long A, B, S, D;
     asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a0), "f"(a1));
@@ -206,6 +221,8 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_vec_kernel(c
     for (int k = threadIdx.x; k < s; k += T) scol[k] = cols[k];
     const int j = threadIdx.x;
     const int64_t nwords = (N + 31) / 32;
+    int o2[8], o3[8];
+    sw_offsets(j, o2, o3);
     __syncthreads();
 
     for (int64_t row = blockIdx.x; row < M; row += gridDim.x) {
@@ -237,22 +254,20 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_vec_kernel(c
         __syncthreads();
         // phase 2: register c <-> logical bits 2..6
         {
-            const int base = (j >> 2) * 128 + (j & 3);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) x[c] = buf[phys_sw(base + 4 * c)];
+            for (int c = 0; c < 32; ++c) x[c] = buf[o2[c & 7] + 4 * (c & 24)];
             fwht32<5>(x);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) buf[phys_sw(base + 4 * c)] = x[c];
+            for (int c = 0; c < 32; ++c) buf[o2[c & 7] + 4 * (c & 24)] = x[c];
         }
         __syncthreads();
         // phase 3: register k <-> logical bits 7..11, butterflies on bits 7 .. L-4
         {
-            const int base = (j >> 7) * 4096 + (j & 127);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) x[k] = buf[phys_sw(base + 128 * k)];
+            for (int k = 0; k < 32; ++k) x[k] = buf[o3[k & 7] + 128 * k];
             fwht32<L - 10>(x);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) buf[phys_sw(base + 128 * k)] = x[k];
+            for (int k = 0; k < 32; ++k) buf[o3[k & 7] + 128 * k] = x[k];
         }
         __syncthreads();
         for (int k = j; k < s; k += T) C[row * ldc + k] = buf[phys_sw(scol[k])];
@@ -281,6 +296,8 @@ __global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __
     const int j = threadIdx.x;
     const uint32_t row_bytes = (uint32_t)(N * 4);
     const int64_t nwords = (N + 31) / 32;
+    int o2[8], o3[8];
+    sw_offsets(j, o2, o3);
     if (j == 0) {
         tc::mbar_init(&full[0], 1);
         tc::mbar_init(&full[1], 1);
@@ -348,21 +365,19 @@ __global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __
                 make_float4(x[4 * r], x[4 * r + 1], x[4 * r + 2], x[4 * r + 3]);
         __syncthreads();
         {
-            const int base = (j >> 2) * 128 + (j & 3);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) x[c] = buf[phys_sw(base + 4 * c)];
+            for (int c = 0; c < 32; ++c) x[c] = buf[o2[c & 7] + 4 * (c & 24)];
             fwht32<5>(x);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) buf[phys_sw(base + 4 * c)] = x[c];
+            for (int c = 0; c < 32; ++c) buf[o2[c & 7] + 4 * (c & 24)] = x[c];
         }
         __syncthreads();
         {
-            const int base = (j >> 7) * 4096 + (j & 127);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) x[k] = buf[phys_sw(base + 128 * k)];
+            for (int k = 0; k < 32; ++k) x[k] = buf[o3[k & 7] + 128 * k];
             fwht32<L - 10>(x);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) buf[phys_sw(base + 128 * k)] = x[k];
+            for (int k = 0; k < 32; ++k) buf[o3[k & 7] + 128 * k] = x[k];
         }
         __syncthreads();
         for (int k = j; k < s; k += T) C[row * ldc + k] = buf[phys_sw(scol[k])];
