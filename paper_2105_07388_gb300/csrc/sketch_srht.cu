@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(1024) srht_smem_kernel(const TA* __restrict__ 
 // Shared memory holds the row with its 16-byte chunks XOR-swizzled inside each
 // 512-byte block by the block index, which makes the float4 stores of phase 1
 // and the scalar loads and stores of phases 2 and 3 conflict-free.  Butterflies
-// run two at a time with packed FP32x2 add/sub (round to nearest, as scalar).
+// on register bits 1..4 run two at a time with packed FP32x2 add/sub (round to
+// nearest, as scalar); bit 0 pairs neighbours and stays scalar.
 __device__ __forceinline__ int phys_sw(int idx) {
     const int B = idx >> 7;
     return (B << 7) | ((((idx >> 2) & 31) ^ (B & 7)) << 2) | (idx & 3);
@@ -189,8 +190,14 @@ __device__ __forceinline__ void bfly2(float& a0, float& a1, float& b0, float& b1
 template <int H>
 __device__ __forceinline__ void stage32(float (&x)[32]) {
     if constexpr (H == 1) {
+        // neighbours x[r], x[r+1] are not a packed pair of the next stages' layout:
+        // scalar butterflies here avoid moving registers in and out of pairs
 #pragma unroll
-        for (int r = 0; r < 32; r += 4) bfly2(x[r], x[r + 2], x[r + 1], x[r + 3]);
+        for (int r = 0; r < 32; r += 2) {
+            const float a = x[r], b = x[r + 1];
+            x[r] = a + b;
+            x[r + 1] = a - b;
+        }
     } else {
 #pragma unroll
         for (int r = 0; r < 32; r += 2)
@@ -319,7 +326,6 @@ __global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __
     for (int64_t row = blockIdx.x; row < M; row += gridDim.x, ++it) {
         const int b = it & 1;
         float* buf = rows + (size_t)b * NP;
-        if (j == 0 && row + gridDim.x < M) issue(row + gridDim.x, b ^ 1);
         // wait for this row's copy: the (it >> 1)-th completion of full[b]
         bool ok = true;
         {
@@ -336,11 +342,10 @@ __global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __
         }
         if (__syncthreads_or(!ok)) {
             if (j == 0) {
-                // copies in flight: this row's (completion it >> 1 of full[b]) and, if
-                // issued, the next row's (completion (it + 1) >> 1 of full[b ^ 1])
+                // the only copy in flight is this row's (completion it >> 1 of full[b]):
+                // the next row's is issued after this point
                 if (err) atomicExch(err, 1);
                 tc::mbar_drain(&full[b], (uint32_t)((it >> 1) & 1));
-                if (row + gridDim.x < M) tc::mbar_drain(&full[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
             }
             return;
         }
@@ -358,7 +363,11 @@ __global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __
             x[4 * r + 3] = __uint_as_float(__float_as_uint(v.w) ^ (((w >> 3) & 1u) << 31));
         }
         fwht32<5>(x);
-        __syncthreads();                                      // every phase-1 read of buf is done
+        // every phase-1 read of buf is done, and every access of the other buffer
+        // (the previous row, up to its gather) is behind this barrier: the next row
+        // may now be copied into it
+        __syncthreads();
+        if (j == 0 && row + gridDim.x < M) issue(row + gridDim.x, b ^ 1);
 #pragma unroll
         for (int r = 0; r < 8; ++r)
             *reinterpret_cast<float4*>(buf + phys_sw(r * 4 * T + 4 * j)) =
@@ -381,7 +390,6 @@ __global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __
         }
         __syncthreads();
         for (int k = j; k < s; k += T) C[row * ldc + k] = buf[phys_sw(scol[k])];
-        __syncthreads();                                      // buf is free for the copy two rows on
     }
 }
 
