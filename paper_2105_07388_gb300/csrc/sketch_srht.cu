@@ -282,57 +282,54 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_vec_kernel(c
     }
 }
 
-// Double-buffered form of srht_vec_kernel for rows of a multiple of 4 floats:
-// one bulk copy (cp.async.bulk, completion on an mbarrier) brings row i+1 into
-// the second row buffer while row i is transformed; phase 1 then reads the row
-// from shared memory (conflict-free 16-byte loads), and the same buffer serves
-// the two transposes.  Waits are bounded in time; on expiry *err is set and the
-// CTA drains its copy and returns.
+// Bulk-copy form of srht_vec_kernel for rows of a multiple of 4 floats: each
+// row arrives in shared memory by one bulk copy (cp.async.bulk, completion on an
+// mbarrier) issued as soon as the previous row's gather is done; phase 1 then
+// reads the row from shared memory (conflict-free 16-byte loads), and the same
+// buffer serves the two transposes.  With one row buffer per CTA, 2^(15-L) CTAs
+// share an SM, so one CTA's copy and barriers overlap the others' transforms.
+// Waits are bounded in time; on expiry *err is set and the CTA drains its copy
+// and returns.
 template <int L>
-__global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __restrict__ A, int64_t lda,
-                                                                 int64_t M, int64_t N,
-                                                                 const uint32_t* __restrict__ dbits,
-                                                                 const int* __restrict__ cols, int s,
-                                                                 float* __restrict__ C, int64_t ldc, int* err) {
+__global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_bulk_kernel(
+    const float* __restrict__ A, int64_t lda, int64_t M, int64_t N, const uint32_t* __restrict__ dbits,
+    const int* __restrict__ cols, int s, float* __restrict__ C, int64_t ldc, int* err) {
     constexpr int T = 1 << (L - 5);
     constexpr int NP = 1 << L;
     extern __shared__ __align__(128) float4 smem4[];
-    float* rows = reinterpret_cast<float*>(smem4);          // 2 x NP floats
-    int* scol = reinterpret_cast<int*>(rows + 2 * NP);
-    __shared__ __align__(8) uint64_t full[2];
+    float* buf = reinterpret_cast<float*>(smem4);           // NP floats, swizzled
+    int* scol = reinterpret_cast<int*>(buf + NP);
+    __shared__ __align__(8) uint64_t full;
     const int j = threadIdx.x;
     const uint32_t row_bytes = (uint32_t)(N * 4);
     const int64_t nwords = (N + 31) / 32;
     int o2[8], o3[8];
     sw_offsets(j, o2, o3);
     if (j == 0) {
-        tc::mbar_init(&full[0], 1);
-        tc::mbar_init(&full[1], 1);
+        tc::mbar_init(&full, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int k = j; k < s; k += T) scol[k] = cols[k];
     __syncthreads();
-    auto issue = [&](int64_t r, int b) {
-        tc::fence_proxy_async();                             // earlier generic accesses of the buffer first
-        tc::mbar_arrive_expect_tx(&full[b], row_bytes);
+    auto issue = [&](int64_t r) {
+        tc::fence_proxy_async();                             // earlier generic accesses of buf first
+        tc::mbar_arrive_expect_tx(&full, row_bytes);
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                tc::smem_u32(rows + (size_t)b * NP)),
-            "l"(A + r * lda), "r"(row_bytes), "r"(tc::smem_u32(&full[b]))
+                tc::smem_u32(buf)),
+            "l"(A + r * lda), "r"(row_bytes), "r"(tc::smem_u32(&full))
             : "memory");
     };
-    if (j == 0 && blockIdx.x < M) issue(blockIdx.x, 0);
+    if (j == 0 && blockIdx.x < M) issue(blockIdx.x);
     int it = 0;
     for (int64_t row = blockIdx.x; row < M; row += gridDim.x, ++it) {
-        const int b = it & 1;
-        float* buf = rows + (size_t)b * NP;
-        // wait for this row's copy: the (it >> 1)-th completion of full[b]
+        // wait for this row's copy: the it-th completion of full
         bool ok = true;
         {
-            const uint32_t par = (uint32_t)((it >> 1) & 1);
-            if (!tc::mbar_test(&full[b], par)) {
+            const uint32_t par = (uint32_t)(it & 1);
+            if (!tc::mbar_test(&full, par)) {
                 const unsigned long long t0 = tc::now_ns();
-                while (!tc::mbar_test_sleep(&full[b], par)) {
+                while (!tc::mbar_test_sleep(&full, par)) {
                     if (tc::now_ns() - t0 > tc::kWaitNs) {
                         ok = false;
                         break;
@@ -342,10 +339,8 @@ __global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __
         }
         if (__syncthreads_or(!ok)) {
             if (j == 0) {
-                // the only copy in flight is this row's (completion it >> 1 of full[b]):
-                // the next row's is issued after this point
                 if (err) atomicExch(err, 1);
-                tc::mbar_drain(&full[b], (uint32_t)((it >> 1) & 1));
+                tc::mbar_drain(&full, (uint32_t)(it & 1));   // the one copy in flight
             }
             return;
         }
@@ -363,11 +358,7 @@ __global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __
             x[4 * r + 3] = __uint_as_float(__float_as_uint(v.w) ^ (((w >> 3) & 1u) << 31));
         }
         fwht32<5>(x);
-        // every phase-1 read of buf is done, and every access of the other buffer
-        // (the previous row, up to its gather) is behind this barrier: the next row
-        // may now be copied into it
-        __syncthreads();
-        if (j == 0 && row + gridDim.x < M) issue(row + gridDim.x, b ^ 1);
+        __syncthreads();                                      // every phase-1 read of buf is done
 #pragma unroll
         for (int r = 0; r < 8; ++r)
             *reinterpret_cast<float4*>(buf + phys_sw(r * 4 * T + 4 * j)) =
@@ -390,6 +381,8 @@ __global__ void __launch_bounds__(1 << (L - 5)) srht_bulk_kernel(const float* __
         }
         __syncthreads();
         for (int k = j; k < s; k += T) C[row * ldc + k] = buf[phys_sw(scol[k])];
+        __syncthreads();                                      // every gather read of buf is done
+        if (j == 0 && row + gridDim.x < M) issue(row + gridDim.x);
     }
 }
 
@@ -434,7 +427,7 @@ template <int L>
 cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C, int64_t ldc,
                         int* err, cudaStream_t st) {
     constexpr int T = 1 << (L - 5);
-    const size_t smem = sizeof(float) * ((size_t)2 << L) + sizeof(int) * (size_t)s;
+    const size_t smem = sizeof(float) * ((size_t)1 << L) + sizeof(int) * (size_t)s;
     auto k = srht_bulk_kernel<L>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
