@@ -91,50 +91,62 @@ __global__ void gauss_x_batched_kernel(const BatchDesc* __restrict__ d, int coun
 
 // core_b[row0 + r][col0 + c] = sum_i Y_b[row0 + r][i] AX_b[i][col0 + c] over all
 // rows i of block b; one CTA per (block, 64 x 64 tile), FP32 accumulation.
-constexpr int kLT = 64;
-constexpr int kLK = 32;
-
-__global__ void __launch_bounds__(256) left_batched_kernel(
+// Left sketch of the batched estimate (Algorithm 1 steps 4-6 per block), one CTA
+// per (block, TR x TC core tile): core[row0 + r][col0 + c] = sum_i Y[row0 + r][i]
+// AX[i][col0 + c] over the block's rows i.  The tile is sized to the request
+// (TR = 16..64 rows, TC = 8..64 columns, 4 x 4 outputs per thread), and the 256
+// threads split each chunk of rows into KS = 256 / (TR TC / 16) interleaved
+// slices whose partial sums are added in a fixed order at the end.  A chunk
+// generates TR x KC normals of Y (KC = 2048 / TR rows, the same work for every
+// tile height) and reads KC x TC floats of AX.
+template <int TR, int TC>
+__global__ void __launch_bounds__(256, 3) left_batched_kernel(
     const BatchDesc* __restrict__ d, const int* __restrict__ active, const float* __restrict__ AXpool,
     int64_t ldax, double* __restrict__ corepool, int64_t core_stride, int ld_core, int row0, int R,
     int col0, int S, int tiles_c) {
-    __shared__ __align__(16) float Ys[kLK][kLT + 4];
-    __shared__ __align__(16) float Xs[kLK][kLT];
+    constexpr int KC = 2048 / TR;                  // rows of the block per chunk
+    constexpr int OTX = TC / 4, OT = (TR / 4) * OTX;   // output threads
+    constexpr int KS = 256 / OT;                   // row slices
+    __shared__ __align__(16) float Ys[KC][TR + 4];
+    __shared__ __align__(16) float Xs[KC][TC + 4];
+    __shared__ __align__(16) float red[KS > 1 ? KS : 1][KS > 1 ? OT : 1][16];
     const int b = blockIdx.x;
     if (!active[b]) return;
     const BatchDesc D = d[b];
     const int rt = blockIdx.y / tiles_c, ct = blockIdx.y % tiles_c;
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    const int qbase = row0 + rt * kLT;
+    const int tid = threadIdx.x;
+    const int o = tid % OT, ks = tid / OT;
+    const int ty = o / OTX, tx = o % OTX;
+    const int qbase = row0 + rt * TR;             // a multiple of 4
     const float* AX = AXpool + D.ax_off;
     float acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
-    for (int64_t i0 = 0; i0 < D.rows; i0 += kLK) {
+    for (int64_t i0 = 0; i0 < D.rows; i0 += KC) {
+        // Y tile: (TR / 4) x KC groups of four normals, two per thread
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int k = tid & 31;
-            const int g = (tid >> 5) + 8 * h;
+            const int c = tid + 256 * h;
+            const int k = c % KC, g = c / KC;
             const int64_t i = i0 + k;
             float z[4] = {0.f, 0.f, 0.f, 0.f};
-            if (i < D.rows && qbase + 4 * g - row0 < R)
+            if (i < D.rows && rt * TR + 4 * g < R)
                 normals4((uint32_t)i, (uint32_t)((qbase >> 2) + g), kStreamGY, D.seed, z);
             *reinterpret_cast<float4*>(&Ys[k][4 * g]) = make_float4(z[0], z[1], z[2], z[3]);
         }
-        {
-            const int k = tid >> 3, cb = (tid & 7) * 8;
-            const int64_t i = i0 + k;
+        // AX tile: KC x TC, consecutive threads along a row of AX
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int c = ct * kLT + cb + q;
-                Xs[k][cb + q] = (i < D.rows && c < S) ? __ldg(AX + i * ldax + col0 + c) : 0.f;
-            }
+        for (int idx = tid; idx < KC * TC; idx += 256) {
+            const int k = idx / TC, c = idx % TC;
+            const int64_t i = i0 + k;
+            const int cc = ct * TC + c;
+            Xs[k][c] = (i < D.rows && cc < S) ? __ldg(AX + i * ldax + col0 + cc) : 0.f;
         }
         __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < kLK; ++k) {
+#pragma unroll 4
+        for (int k = ks; k < KC; k += KS) {
             const float4 yv = *reinterpret_cast<const float4*>(&Ys[k][ty * 4]);
             const float4 xv = *reinterpret_cast<const float4*>(&Xs[k][tx * 4]);
             const float y[4] = {yv.x, yv.y, yv.z, yv.w};
@@ -147,16 +159,64 @@ __global__ void __launch_bounds__(256) left_batched_kernel(
         __syncthreads();
     }
     double* core = corepool + (int64_t)b * core_stride;
+    if constexpr (KS > 1) {
+        // slice partial sums, added in slice order; one output per thread
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int r = rt * kLT + ty * 4 + a;
-        if (r >= R) continue;
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int cc = ct * kLT + tx * 4 + c;
-            if (cc < S) core[(int64_t)(row0 + r) * ld_core + col0 + cc] = (double)acc[a][c];
+            for (int c = 0; c < 4; ++c) red[ks][o][4 * a + c] = acc[a][c];
+        __syncthreads();
+        for (int idx = tid; idx < OT * 16; idx += 256) {
+            const int oo = idx >> 4, a = (idx >> 2) & 3, c = idx & 3;
+            float t = red[0][oo][idx & 15];
+            for (int u = 1; u < KS; ++u) t += red[u][oo][idx & 15];
+            const int r = rt * TR + (oo / OTX) * 4 + a;
+            const int cc = ct * TC + (oo % OTX) * 4 + c;
+            if (r < R && cc < S) core[(int64_t)(row0 + r) * ld_core + col0 + cc] = (double)t;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int r = rt * TR + ty * 4 + a;
+            if (r >= R) continue;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int cc = ct * TC + tx * 4 + c;
+                if (cc < S) core[(int64_t)(row0 + r) * ld_core + col0 + cc] = (double)acc[a][c];
+            }
         }
     }
+}
+
+template <int TR, int TC>
+cudaError_t launch_left_batched_t(const BatchDesc* d, const int* active, int count, const float* AX, int64_t ldax,
+                                  double* core, int64_t core_stride, int ld_core, int row0, int R, int col0, int S,
+                                  cudaStream_t st) {
+    const int tr = (R + TR - 1) / TR, tc = (S + TC - 1) / TC;
+    left_batched_kernel<TR, TC><<<dim3(count, tr * tc), 256, 0, st>>>(d, active, AX, ldax, core, core_stride,
+                                                                      ld_core, row0, R, col0, S, tc);
+    return cudaGetLastError();
+}
+
+// TC <= TR (the ladder's requests have R >= 2 S; wider ones take more column tiles)
+template <int TR>
+cudaError_t launch_left_batched_r(const BatchDesc* d, const int* active, int count, const float* AX, int64_t ldax,
+                                  double* core, int64_t core_stride, int ld_core, int row0, int R, int col0, int S,
+                                  cudaStream_t st) {
+    if (S >= 64 && TR >= 64) return launch_left_batched_t<TR, (TR >= 64 ? 64 : TR)>(d, active, count, AX, ldax, core, core_stride, ld_core, row0, R, col0, S, st);
+    if (S >= 32 && TR >= 32) return launch_left_batched_t<TR, (TR >= 32 ? 32 : TR)>(d, active, count, AX, ldax, core, core_stride, ld_core, row0, R, col0, S, st);
+    if (S >= 16 && TR >= 16) return launch_left_batched_t<TR, 16>(d, active, count, AX, ldax, core, core_stride, ld_core, row0, R, col0, S, st);
+    return launch_left_batched_t<TR, 8>(d, active, count, AX, ldax, core, core_stride, ld_core, row0, R, col0, S, st);
+}
+
+// Core block rows [row0, row0 + R) x columns [col0, col0 + S) of every active block.
+cudaError_t launch_left_batched(const BatchDesc* d, const int* active, int count, const float* AX, int64_t ldax,
+                                double* core, int64_t core_stride, int ld_core, int row0, int R, int col0, int S,
+                                cudaStream_t st) {
+    if (R <= 0 || S <= 0 || count <= 0) return cudaSuccess;
+    if (R >= 64) return launch_left_batched_r<64>(d, active, count, AX, ldax, core, core_stride, ld_core, row0, R, col0, S, st);
+    if (R >= 32) return launch_left_batched_r<32>(d, active, count, AX, ldax, core, core_stride, ld_core, row0, R, col0, S, st);
+    return launch_left_batched_r<16>(d, active, count, AX, ldax, core, core_stride, ld_core, row0, R, col0, S, st);
 }
 
 // Read-off for every active block at width s (Algorithm 1 step 8); retires blocks.
@@ -414,21 +474,15 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
             nl += 2;
             if (e != cudaSuccess) break;
             if (s_prev > 0) {
-                const int R = 2 * sn, S = s_prev;
-                const int tr = (R + kLT - 1) / kLT, tc = (S + kLT - 1) / kLT;
-                left_batched_kernel<<<dim3(count, tr * tc), 256, 0, bs>>>(dd, active, st->ax.as<float>(), S_MAX,
-                                                                          st->core.as<double>(), core_stride, S_MAX,
-                                                                          2 * s_prev, R, 0, S, tc);
+                e = launch_left_batched(dd, active, count, st->ax.as<float>(), S_MAX, st->core.as<double>(),
+                                        core_stride, S_MAX, 2 * s_prev, 2 * sn, 0, s_prev, bs);
                 ++nl;
+                if (e != cudaSuccess) break;
             }
-            {
-                const int R = 2 * s, S = sn;
-                const int tr = (R + kLT - 1) / kLT, tc = (S + kLT - 1) / kLT;
-                left_batched_kernel<<<dim3(count, tr * tc), 256, 0, bs>>>(dd, active, st->ax.as<float>(), S_MAX,
-                                                                          st->core.as<double>(), core_stride, S_MAX, 0,
-                                                                          R, s_prev, S, tc);
-                ++nl;
-            }
+            e = launch_left_batched(dd, active, count, st->ax.as<float>(), S_MAX, st->core.as<double>(),
+                                    core_stride, S_MAX, 0, 2 * s, s_prev, sn, bs);
+            ++nl;
+            if (e != cudaSuccess) break;
             e = launch_core_sigma_batched(st->core.as<double>(), 2 * s, s, S_MAX, core_stride, count,
                                           st->sigma.as<double>(), S_MAX, status, bs, active);
             ++nl;
