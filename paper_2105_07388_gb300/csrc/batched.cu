@@ -6,8 +6,12 @@
 // sketch-width ladder s = s0, 2 s0, ..., one level at a time, and each level is
 // a fixed sequence of batched kernels over all blocks:
 //   generator     X_b columns [s_prev, s) for every active block (own seed each)
-//   right sketch  one CTA per (block, row tile) work item (FP32 CUDA cores)
-//   left sketch   one CTA per (block, 64 x 64 core tile), Y_b generated on the fly
+//   right sketch  one CTA per (block, row tile) work item (FP32 CUDA cores), or
+//                 the persistent tcgen05 kernel (BF16x3); on the tensor-core
+//                 path the first pass appends up to 4 s0 columns at once, so
+//                 the widths up to 4 s0 cost one read of each block
+//   left sketch   one CTA per (block, core tile sized to the request), Y_b
+//                 generated on the fly
 //   core sigma    one CTA per block (QR + one-sided Jacobi in shared memory)
 //   read-off      one thread per block; converged blocks, and blocks that reached
 //                 their largest width, retire by clearing their active flag
@@ -258,6 +262,14 @@ __global__ void readoff_batched_kernel(const BatchDesc* __restrict__ d, int coun
     if (r.status != RE_OK || r.rank >= 0 || 2 * s > d[b].smax || r1 >= d[b].cols) active[b] = 0;
 }
 
+// Width the first tensor-core pass of the batched ladder reaches: 4 s0, within
+// the X^T pool (snew rows) and the ladder (smax).
+int first_pass_width(int s0, int snew, int smax) {
+    int w = s0;
+    while (w < 4 * s0 && 2 * w <= snew && 2 * w <= smax) w *= 2;
+    return w;
+}
+
 int r1_of(int s) {
     int r = 1;
     while ((2 * 11 * (r + 1) + 10) / 20 <= s) ++r;
@@ -454,15 +466,28 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
         int* tcerr = use_tc ? st->tcerr.as<int>() : nullptr;
         init_active_kernel<<<(count + 255) / 256, 256, 0, bs>>>(st->valid.as<int>(), active, status, count, tcerr);
         ++nl;
+        // Tensor-core path: the first pass appends the right sketch up to W1 = 4 s0
+        // columns (within the X^T pool's SNEW rows) in one read of every block; the
+        // reads bound that pass, not the extra columns, and the next ladder widths
+        // up to W1 then need no pass over A.  Column j of AX does not depend on
+        // which pass computes it, so every width sees the same AX.
+        const int w1 = use_tc ? first_pass_width(s0, SNEW, S_MAX) : s0;
+        int covered = 0;                          // AX columns computed so far
         for (int s_prev = 0, s = s0; s <= S_MAX && e == cudaSuccess; s_prev = s, s *= 2) {
             const int sn = s - s_prev;
             if (use_tc) {
-                e = launch_gauss_xt_batched(dd, count, active, s_prev, sn, tc_mma_n(sn), st->xt.as<uint16_t>(), bs);
-                if (e == cudaSuccess) e = launch_compact_tiles(dd, count, active, st->actpre.as<int64_t>(), bs);
-                if (e == cudaSuccess)
-                    e = launch_right_tc_batched(dd, count, st->actpre.as<int64_t>(), pre128[count],
-                                                st->xt.as<uint16_t>(), sn, st->ax.as<float>(), S_MAX, s_prev, tcerr, bs);
-                ++nl;
+                if (s > covered) {
+                    const int upto = covered == 0 ? std::max(s, w1) : s;
+                    const int c0 = covered, cn = upto - covered;
+                    e = launch_gauss_xt_batched(dd, count, active, c0, cn, tc_mma_n(cn), st->xt.as<uint16_t>(), bs);
+                    if (e == cudaSuccess) e = launch_compact_tiles(dd, count, active, st->actpre.as<int64_t>(), bs);
+                    if (e == cudaSuccess)
+                        e = launch_right_tc_batched(dd, count, st->actpre.as<int64_t>(), pre128[count],
+                                                    st->xt.as<uint16_t>(), cn, st->ax.as<float>(), S_MAX, c0, tcerr,
+                                                    bs);
+                    covered = upto;
+                    nl += 3;
+                }
             } else {
                 const int bm = st->bm_for[31 - __builtin_clz((unsigned)sn)] == 64 ? 64 : 128;
                 gauss_x_batched_kernel<<<1024, 256, 0, bs>>>(dd, count, st->colpre.as<int64_t>(), active, s_prev, sn,
@@ -470,8 +495,8 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
                 e = launch_right_simt_batched(dd, count, bm == 128 ? st->pre128.as<int64_t>() : st->pre64.as<int64_t>(),
                                               bm == 128 ? pre128[count] : pre64[count], active, st->x.as<float>(), sn,
                                               st->ax.as<float>(), S_MAX, s_prev, bm, bs);
+                nl += 2;
             }
-            nl += 2;
             if (e != cudaSuccess) break;
             if (s_prev > 0) {
                 e = launch_left_batched(dd, active, count, st->ax.as<float>(), S_MAX, st->core.as<double>(),
@@ -541,8 +566,11 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
         R.tau = ro[i].tau;
         R.n_sigma = r1;
         R.final_s = s;
-        int passes = 0;
-        for (int t = s0; t <= s; t *= 2) ++passes;
+        // passes over A: one per right-sketch pass the block took part in (on the
+        // tensor-core path the first pass covers the widths up to w1)
+        const int w1 = use_tc ? first_pass_width(s0, SNEW, S_MAX) : s0;
+        int passes = 1;
+        for (int t = 2 * w1; t <= s; t *= 2) ++passes;
         R.passes = passes;
         R.flags = (conv ? RE_CONVERGED : RE_LOWER_BOUND_ONLY) | (hd[i].trans ? RE_TRANSPOSED : 0u);
         if (!sg.empty()) {
