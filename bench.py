@@ -166,6 +166,24 @@ def cpu_oracle_run(A_host: np.ndarray, w, kind: int, budget_s: float = 20.0):
                                      "seconds": el, "passes": res.passes}
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """Largest x over the ranks of the default process group (x itself when there
+    is no group or one rank): the job time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(a_bytes: float, passes: int, world: int, ms: float) -> float:
+    """Whole-job sketch throughput: every rank reads its replica of A `passes`
+    times per step, the step takes the slowest rank's `ms`."""
+    return a_bytes * passes * world / (ms * 1e-3) / 1e9
+
+
 def main():
     args = parse()
     w = WORKLOADS[args.workload]
@@ -255,13 +273,10 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     st = rk.re_stats_get(h)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, "cuda")
     passes = res.passes
     a_bytes = 4.0 * m * n
-    value = a_bytes * passes * world / (ms * 1e-3) / 1e9
+    value = job_gbs(a_bytes, passes, world, ms)
     hbm, bf16, src = peaks()
     clocks = clk.summary()
 
