@@ -21,12 +21,13 @@
 // fused multiply-add, rounded per element exactly as the scalar forms).
 //
 // Small cores (r2 s + s^2 floats fit in shared memory) use one CTA; larger cores
-// use a cluster of 8 or 16 CTAs: the columns are dealt out in panels of 8, the
-// QR factors one panel at a time on the CTA that owns it and broadcasts its
-// reflectors over distributed shared memory, with one panel of lookahead (the
-// owner of the next panel updates and factors it while the other CTAs update
-// the rest); Jacobi is blocked (two column blocks per CTA, blocks rotating
-// through the cluster each round).
+// use two cluster kernels of 8 or 16 CTAs: a QR kernel (the columns dealt out in
+// panels of 8; each panel factored on the CTA that owns it, which publishes its
+// reflectors once through global memory, with one panel of lookahead: the owner
+// of the next panel updates and factors it while the other CTAs update the
+// rest), then a Jacobi kernel (two column blocks per CTA, blocks moving through
+// the cluster each round).  Both QR forms factor panels of 8 columns with
+// lookahead.
 #include <algorithm>
 #include <cfloat>
 #include <climits>

@@ -125,7 +125,9 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
 // ---- small core singular values (core_svd.cu) ----------------------------------
 size_t svd_workspace_bytes(int r2, int s);
 // sigma (FP64, s entries, descending, unscaled) of core (FP64 row-major r2 x s, ld).
-// status (device int): 0 ok, RE_ERR_NONFINITE if core has NaN/Inf.
+// status (device int): 0 ok, RE_ERR_NONFINITE if core has NaN/Inf.  ws: device
+// scratch of svd_workspace_bytes(r2, s) bytes (16-byte aligned), used by the
+// cluster path (cores that do not fit one CTA).
 // With cert_r1 > 0 the one-CTA path first tries to certify that sigma_{cert_r1}
 // exceeds cert_ratio * sigma_1 (then status[3] = 1 and sigma is left unwritten).
 cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws,
