@@ -1205,8 +1205,12 @@ cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t
     if (!kern) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kern<<<count, kCtaThreads, sm, st>>>(core, r2, s, ld, core_stride, sigma, sigma_stride, status, active,
-                                         cert_r1, cert_ratio);
+    // many small cores: 512 threads (8 panel + 8 trailing warps, 32 pair groups) fit
+    // two CTAs in an SM's registers where 1024 fit one; every loop of the kernel
+    // takes its warp and group counts from the launch
+    const int threads = (count > 1 && s <= 64) ? 512 : kCtaThreads;
+    kern<<<count, threads, sm, st>>>(core, r2, s, ld, core_stride, sigma, sigma_stride, status, active,
+                                     cert_r1, cert_ratio);
     return cudaGetLastError();
 }
 
