@@ -599,8 +599,10 @@ int re_rank_estimate_host(re_handle h, const void* A_host, int dtype, int64_t m,
     const size_t es = dtype == RE_F32 ? 4 : 8;
     if (int r = ensure(h->acopy, es * (size_t)m * n)) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpy2DAsync(h->acopy.p, es * n, A_host, es * ld, es * n, m,
-                                      cudaMemcpyHostToDevice, st);
+    // contiguous rows: one linear copy (the 2-D form would be issued row by row)
+    cudaError_t e = ld == n ? cudaMemcpyAsync(h->acopy.p, A_host, es * (size_t)m * n, cudaMemcpyHostToDevice, st)
+                            : cudaMemcpy2DAsync(h->acopy.p, es * n, A_host, es * ld, es * n, m,
+                                                cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "host to device copy of A");
     return re_rank_estimate(h, h->acopy.p, dtype, m, n, n, eps, sketch_kind, seed, sigma_out,
                             sigma_cap, out, stream);
