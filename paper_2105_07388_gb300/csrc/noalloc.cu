@@ -5,7 +5,7 @@
 // handle's workspace, so the call needs no handle, no cudaMalloc/cudaFree and
 // no allocating library routine.
 //
-// Every GPU that loads this library holds the array (kScratchBytes) until the
+// Every GPU that loads this library holds the array (16 MiB) until the
 // process exits.  All calls on a device share it, so calls that overlap on
 // the GPU (different streams, or different host threads) race on it and must
 // be serialised by the caller.  Nothing in it needs to start at zero: each call
@@ -23,7 +23,6 @@ namespace re {
 namespace {
 
 constexpr size_t kScratchFloats = (size_t)4 << 20;          // 4 Mi floats = 16 MiB
-constexpr size_t kScratchBytes = kScratchFloats * sizeof(float);
 
 __device__ __align__(256) float g_scratch[kScratchFloats];
 

@@ -24,11 +24,11 @@ constexpr int kThreads = 256;
 
 template <int BN>
 struct SimtShape;
-template <> struct SimtShape<128> { static constexpr int TN = 8, TM = 8; };
-template <> struct SimtShape<64> { static constexpr int TN = 4, TM = 8; };
-template <> struct SimtShape<32> { static constexpr int TN = 2, TM = 8; };
-template <> struct SimtShape<16> { static constexpr int TN = 1, TM = 8; };
-template <> struct SimtShape<8> { static constexpr int TN = 1, TM = 4; };
+template <> struct SimtShape<128> { static constexpr int TN = 8; };
+template <> struct SimtShape<64> { static constexpr int TN = 4; };
+template <> struct SimtShape<32> { static constexpr int TN = 2; };
+template <> struct SimtShape<16> { static constexpr int TN = 1; };
+template <> struct SimtShape<8> { static constexpr int TN = 1; };
 
 template <typename TA>
 __device__ __forceinline__ float ld_as_f32(const TA* p) {
