@@ -10,7 +10,8 @@ the product package.
 Contents
 --------
 ``rng``        counter-based generator (Philox4x32-10, Box-Muller normals rounded
-               to BF16, random signs, keyed Feistel sampling) written from the
+               to BF16, random signs, keyed Feistel sampling, the HRTT's
+               CountSketch hashing built on them) written from the
                published definitions; the CUDA side has its own implementation of
                the same specification, so both draw identical X and Y.
 ``algorithm1`` Algorithm 1 (Sec. 5) step by step in FP64 with numpy: the sketch

@@ -5,7 +5,8 @@ Every step follows the algorithm box in order, with the embeddings written out
 densely so that each product is a plain matrix product a reader can check:
 
   step 1  r~1 = round(1.1 r1)                         -> ``oversampled``
-  step 2  draw X (n x r~1): Gaussian G or SRTT D H S^T -> ``rng.gaussian_x`` / ``rng.srtt_x``
+  step 2  draw X (n x r~1): Gaussian G, SRTT D H S^T or HRTT D H C^T
+                                                       -> ``rng.gaussian_x`` / ``rng.srtt_x`` / ``rng.hrtt_x``
   step 3  form A X                                     -> ``A @ X``
   step 4  r2 = 2 r~1
   step 5  draw Y (r2 x m): Gaussian or SRTT S H D      -> ``rng.gaussian_y`` / ``rng.srtt_y``
@@ -28,6 +29,13 @@ Readings of the paper taken here (the CUDA path takes the same ones):
   S H D / sqrt(r2) and likewise X = D H S^T / sqrt(s).  The unscaled sketches are
   formed and sigma is multiplied by 1/sqrt(s r2) afterwards.
 * Hadamard zero padding (Sec. 4): n and m are padded to the next power of two.
+* HRTT (Sec. 3.4, hashed randomized transform): X = D (H/sqrt(n_pad)) C^T with
+  a CountSketch C, so the singular values are scaled by 1/sqrt(n_pad r2).  Its
+  columns depend on the width, so each step of the doubling loop sketches anew.
+  The left embedding is Gaussian: the column space of A X is that of A's leading
+  left singular vectors, coherent whenever A is (a diagonal A gives coordinate
+  vectors), and a sampled Hadamard Y aliases on it as a sampled Hadamard X does
+  on the right.
 * m < n: the estimate is taken on A^T (Notation assumes m >= n; rank is
   invariant under transposition).
 * Read-off: tau = eps * sigma^_1 (or eps * normA when the caller gives ||A||);
@@ -49,6 +57,7 @@ from . import rng
 
 GAUSSIAN = 0
 SRHT = 1
+HRTT = 2
 
 
 def round_half_away(num: int, den: int) -> int:
@@ -77,7 +86,16 @@ def embeddings(kind: int, n: int, m: int, s: int, seed: int,
         return rng.gaussian_x(n, s, seed, col0), rng.gaussian_y(r2, m, seed, row0)
     if kind == SRHT:
         return rng.srtt_x(n, s, seed, col0), rng.srtt_y(r2, m, seed, row0)
+    if kind == HRTT:
+        if col0 != 0:
+            raise ValueError("HRTT columns depend on the width: col0 must be 0")
+        return rng.hrtt_x(n, s, seed), rng.gaussian_y(r2, m, seed, row0)
     raise ValueError(f"unknown sketch kind {kind}")
+
+
+def left_kind(kind: int) -> int:
+    """Kind of the left embedding Y drawn with right embedding `kind`."""
+    return GAUSSIAN if kind == HRTT else kind
 
 
 def orient(A: np.ndarray) -> tuple[np.ndarray, bool]:
@@ -98,15 +116,17 @@ def right_sketch(A: np.ndarray, s: int, kind: int, seed: int, col0: int = 0) -> 
 def left_sketch(AX: np.ndarray, r2: int, kind: int, seed: int, row0: int = 0) -> np.ndarray:
     """Steps 5-6: Y (A X) for rows row0..row0+r2-1 of the unscaled embedding."""
     m = AX.shape[0]
-    if kind == GAUSSIAN:
+    if left_kind(kind) == GAUSSIAN:
         Y = rng.gaussian_y(r2, m, seed, row0)
     else:
         Y = rng.srtt_y(r2, m, seed, row0)
     return Y @ AX
 
 
-def sketch_scale(s: int) -> float:
-    """1/sqrt(s * r2) with r2 = 2 s."""
+def sketch_scale(s: int, kind: int = GAUSSIAN, n: int = 0) -> float:
+    """1/sqrt(s * r2) with r2 = 2 s; for the HRTT 1/sqrt(n_pad * r2) (n columns)."""
+    if kind == HRTT:
+        return 1.0 / math.sqrt(float(1 << rng.next_pow2_bits(n)) * float(2 * s))
     return 1.0 / math.sqrt(float(s) * float(2 * s))
 
 
@@ -120,7 +140,7 @@ def sketched_sigma(A: np.ndarray, s: int, kind: int, seed: int) -> np.ndarray:
     """Step 7: all s singular values of Y A X, scaled (descending, FP64)."""
     C = core(A, s, kind, seed)
     sig = np.linalg.svd(C, compute_uv=False)
-    return sig * sketch_scale(s)
+    return sig * sketch_scale(s, kind, np.shape(A)[1])
 
 
 @dataclass
@@ -178,6 +198,8 @@ def ladder_limits(m: int, n: int, kind: int, s_max: int) -> int:
         n_pad = 1 << rng.next_pow2_bits(n)
         m_pad = 1 << rng.next_pow2_bits(m)
         cap = min(cap, n_pad, m_pad // 2)
+    if kind == HRTT:
+        cap = min(cap, 1 << rng.next_pow2_bits(n))      # no empty bucket
     return cap
 
 
@@ -186,8 +208,9 @@ def rank_estimate(A: np.ndarray, eps: float, kind: int = GAUSSIAN, seed: int = 0
     """Algorithm 1 with the doubling loop of step 8 (appending to X and Y).
 
     Each step recomputes the core from the plain definition Y[:2s] A X[:, :s];
-    because column j of X and row q of Y do not depend on s, this is the same
-    matrix the appended sketches give.
+    for the Gaussian and SRTT embeddings column j of X and row q of Y do not
+    depend on s, so this is the same matrix the appended sketches give (the
+    HRTT's X does depend on s and is drawn anew at every step).
     """
     A = np.asarray(A)
     if A.ndim != 2:

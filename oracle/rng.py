@@ -32,8 +32,13 @@ Specification (the CUDA side follows the same text):
   replacement"): the sampled index k is pi(k), pi a 4-round keyed Feistel
   bijection of [0, 2^b) whose round function is word 0 of
   Philox((half, round, stream, 0)).
+* HRTT hashing (Sec. 3.4: the sampling S replaced by a CountSketch hashing
+  matrix C, s x n_pad, one nonzero per column): coordinate c of the transform
+  goes to bucket h(c) = pi_X^{-1}(c) mod s with sign sigma_c (a sign of stream
+  SX, drawn like d_j), so bucket k holds {pi_X(k + t s) : k + t s < n_pad}.  D
+  and pi are the SRTT's (streams DX and PX).
 
-Stream identifiers: GX=1, GY=2, DX=3, PX=4, DY=5, PY=6.
+Stream identifiers: GX=1, GY=2, DX=3, PX=4, DY=5, PY=6, SX=7.
 """
 from __future__ import annotations
 
@@ -45,6 +50,7 @@ STREAM_DX = 3
 STREAM_PX = 4
 STREAM_DY = 5
 STREAM_PY = 6
+STREAM_SX = 7
 
 _M0 = np.uint64(0xD2511F53)
 _M1 = np.uint64(0xCD9E8D57)
@@ -291,3 +297,29 @@ def srtt_y(r2: int, m: int, seed: int, row0: int = 0) -> np.ndarray:
     d = signs(m, STREAM_DY, seed)
     rows = feistel_perm(np.arange(row0, row0 + r2), b, STREAM_PY, seed)
     return hadamard_entries(rows, np.arange(m)) * d[None, :]
+
+
+def hrtt_x(n: int, s: int, seed: int) -> np.ndarray:
+    """Unscaled hashed randomized Hadamard right embedding, n x s: X = D H C^T.
+
+    Sec. 3.4 (HRTT): Eq. (Theta) with the sampling matrix S replaced by a
+    hashing matrix; here C[h(c), c] = sigma_c with h(c) = pi^{-1}(c) mod s over
+    the zero-padded dimension n_pad = 2^ceil(log2 n).  Column k of X is
+    d * sum over the bucket {c = pi(k + t s)} of sigma_c H[:, c].  The columns
+    depend on s (the width is not appendable).  The orthonormal transform's
+    scale 1/sqrt(n_pad) is applied to the singular values afterwards.
+    """
+    if s < 1:
+        raise ValueError("s must be positive")
+    b = next_pow2_bits(n)
+    n_pad = 1 << b
+    if s > n_pad:
+        raise ValueError("HRTT width exceeds the padded dimension (empty buckets)")
+    d = signs(n, STREAM_DX, seed)
+    sigma = signs(n_pad, STREAM_SX, seed)
+    rows = np.arange(n)
+    X = np.empty((n, s), dtype=np.float64)
+    for k in range(s):
+        c = feistel_perm(np.arange(k, n_pad, s), b, STREAM_PX, seed)   # bucket k
+        X[:, k] = d * (hadamard_entries(rows, c) @ sigma[c])
+    return X

@@ -114,7 +114,7 @@ def test_left_sketch_preserves_all_singular_values():
         assert np.all(ratio > 0.2) and np.all(ratio < 1.9), (kind, ratio.min(), ratio.max())
 
 
-@pytest.mark.parametrize("kind", [alg.GAUSSIAN, alg.SRHT])
+@pytest.mark.parametrize("kind", [alg.GAUSSIAN, alg.SRHT, alg.HRTT])
 def test_exact_rank_on_clear_gap(kind):
     # Sec. 1.1: with a clear gap sigma_r >> eps ||A|| >> sigma_{r+1} the estimate is exact.
     m, n = 400, 300
@@ -207,3 +207,32 @@ def test_scaling_constant():
     Q = wl.haar_orthonormal(4000, 10, seed=3).numpy() @ wl.haar_orthonormal(10, 10, 4).numpy().T
     sig = alg.sketched_sigma(Q, 64, alg.GAUSSIAN, seed=3)[:10]
     assert np.all(sig > 0.6) and np.all(sig < 1.5)
+
+
+def test_hrtt_on_coherent_diagonal():
+    # Sec. 3.4: on a diagonal matrix (the most coherent input) subsampled
+    # Hadamard columns alias, while hashing keeps the embedding (the paper's
+    # reason for its HRTT default).  A = diag(1 x 100, 1e-8 ...), eps = 1e-4:
+    # the HRTT estimate is exact at every seed; the SRTT one stops short.
+    n = 1024
+    A = np.diag(np.where(np.arange(n) < 100, 1.0, 1e-8))
+    for seed in range(3):
+        res = alg.rank_estimate(A, 1e-4, kind=alg.HRTT, seed=seed)
+        assert res.converged and res.rank == 100 and res.final_s == 128 and res.gap_index == 100
+        assert [h[0] for h in res.history] == [8, 16, 32, 64, 128]
+        assert alg.rank_estimate(A, 1e-4, kind=alg.SRHT, seed=seed).rank < 100
+
+
+def test_hrtt_scale_and_limits():
+    # X = D (H/sqrt(n_pad)) C^T and Y = G/sqrt(2s): the sketched sigma of a matrix
+    # with orthonormal columns concentrate around 1, as for the Gaussian pair.
+    Q = wl.haar_orthonormal(3000, 10, seed=5).numpy() @ wl.haar_orthonormal(1000, 10, seed=6).numpy().T
+    sig = alg.sketched_sigma(Q, 64, alg.HRTT, seed=2)[:10]
+    assert np.all(sig > 0.6) and np.all(sig < 1.5)
+    assert alg.sketch_scale(64, alg.HRTT, 10) == 1.0 / np.sqrt(16 * 128)
+    assert alg.ladder_limits(5000, 100, alg.HRTT, 512) == 128     # s <= n_pad
+    with pytest.raises(ValueError):
+        alg.embeddings(alg.HRTT, 100, 200, 16, 0, col0=16)        # not appendable
+    # the left embedding of the HRTT is Gaussian
+    AX = np.random.default_rng(1).standard_normal((300, 8))
+    assert np.array_equal(alg.left_sketch(AX, 16, alg.HRTT, 3), alg.left_sketch(AX, 16, alg.GAUSSIAN, 3))

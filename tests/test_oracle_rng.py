@@ -138,3 +138,78 @@ def test_srtt_padding_drops_rows():
     b40, b64 = rng.next_pow2_bits(40), rng.next_pow2_bits(64)
     assert b40 == b64 == 6
     assert np.array_equal(Xp[:40], X)
+
+
+# ---------------------------------------------------------------------------
+# HRTT (Sec. 3.4): X = D H C^T with a CountSketch C
+def _countsketch(n_pad, s, seed):
+    """C (s x n_pad) built directly: hash h(c) = pi^{-1}(c) mod s from an
+    explicitly inverted permutation table, signs sigma_c of stream SX."""
+    b = rng.next_pow2_bits(n_pad)
+    perm = rng.feistel_perm(np.arange(n_pad), b, rng.STREAM_PX, seed)
+    inv = np.argsort(perm)                       # inv[c] = q with pi(q) = c
+    sigma = rng.signs(n_pad, rng.STREAM_SX, seed)
+    C = np.zeros((s, n_pad))
+    for c in range(n_pad):
+        C[inv[c] % s, c] = sigma[c]
+    return C
+
+
+@pytest.mark.parametrize("n,s", [(256, 16), (100, 24), (300, 512), (64, 64), (1, 1)])
+def test_hrtt_matches_explicit_countsketch(n, s):
+    n_pad = 1 << rng.next_pow2_bits(n)
+    C = _countsketch(n_pad, s, seed=21)
+    assert np.array_equal(np.abs(C).sum(axis=0), np.ones(n_pad))   # one nonzero per column
+    d = rng.signs(n, rng.STREAM_DX, seed=21)
+    want = d[:, None] * (scipy.linalg.hadamard(n_pad)[:n].astype(np.float64) @ C.T)
+    assert np.array_equal(rng.hrtt_x(n, s, seed=21), want)
+
+
+def test_hrtt_full_width_is_signed_srtt():
+    # s = n_pad: every bucket holds the single coordinate pi(k), so the HRTT is the
+    # fully sampled SRTT with column k multiplied by sigma_{pi(k)}.
+    n = 200
+    n_pad = 256
+    cols = rng.feistel_perm(np.arange(n_pad), 8, rng.STREAM_PX, seed=4)
+    sigma = rng.signs(n_pad, rng.STREAM_SX, seed=4)
+    assert np.array_equal(rng.hrtt_x(n, n_pad, seed=4), rng.srtt_x(n, n_pad, seed=4) * sigma[cols][None, :])
+
+
+@pytest.mark.parametrize("s", [2, 16, 128])
+def test_hrtt_buckets_fold(s):
+    # h_{s/2}(c) = h_s(c) mod s/2: bucket k at width s/2 is buckets k and k + s/2 at s
+    X = rng.hrtt_x(700, s, seed=9)
+    Xh = rng.hrtt_x(700, s // 2, seed=9)
+    assert np.array_equal(Xh, X[:, : s // 2] + X[:, s // 2:])
+
+
+@pytest.mark.parametrize("s", [24, 64])
+def test_hrtt_gram_closed_form(s):
+    # n = n_pad: X^T X = C H D D H C^T = n_pad C C^T = n_pad diag(|bucket k|),
+    # |bucket k| = number of q < n_pad with q = k mod s.
+    n = 256
+    X = rng.hrtt_x(n, s, seed=12)
+    sizes = np.array([len(range(k, n, s)) for k in range(s)], dtype=np.float64)
+    assert np.array_equal(X.T @ X, n * np.diag(sizes))
+
+
+def test_hrtt_is_unbiased():
+    # E[X X^T] = D H E[C^T C] H D = n_pad I (the signs sigma make E[C^T C] = I).
+    # Averaged over 400 seeds each entry of X X^T / n_pad has standard deviation
+    # about sqrt(2 / (s 400)) = 0.018 (s = 16): 0.1 is > 5 sigma.
+    n, s = 32, 16
+    acc = np.zeros((n, n))
+    for seed in range(400):
+        X = rng.hrtt_x(n, s, seed=seed)
+        acc += X @ X.T / n
+    acc /= 400
+    assert np.max(np.abs(acc - np.eye(n))) < 0.1
+    # without the signs sigma the diagonal of row 0 would be n_pad / s = 2
+    assert abs(acc[0, 0] - 1.0) < 0.1
+
+
+def test_hrtt_argument_errors():
+    with pytest.raises(ValueError):
+        rng.hrtt_x(100, 256, seed=0)                # s > n_pad = 128: empty buckets
+    with pytest.raises(ValueError):
+        rng.hrtt_x(100, 0, seed=0)
