@@ -266,14 +266,31 @@ def next_pow2_bits(n: int) -> int:
     return b
 
 
+_PARITY16 = None
+
+
+def _parity16() -> np.ndarray:
+    """parity(popcount(v)) for every 16-bit v, by shifting out the bits."""
+    global _PARITY16
+    if _PARITY16 is None:
+        a = np.arange(1 << 16, dtype=np.int64)
+        par = np.zeros_like(a)
+        while np.any(a):
+            par ^= a & 1
+            a = a >> 1
+        _PARITY16 = par.astype(np.uint8)
+    return _PARITY16
+
+
 def hadamard_entries(rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
-    """Sylvester Hadamard entries H[i, c] = (-1)^popcount(i & c), float64."""
+    """Sylvester Hadamard entries H[i, c] = (-1)^popcount(i & c), float64
+    (indices below 2^32; the parity of i & c from its two 16-bit halves)."""
     a = np.bitwise_and(np.asarray(rows, dtype=np.int64)[:, None],
                        np.asarray(cols, dtype=np.int64)[None, :])
-    par = np.zeros(a.shape, dtype=np.int64)
-    while np.any(a):
-        par ^= a & 1
-        a = a >> 1
+    if a.size and int(a.max()) >> 32:
+        raise ValueError("Hadamard index beyond 2^32")
+    t = _parity16()
+    par = t[a & 0xFFFF] ^ t[a >> 16]
     return 1.0 - 2.0 * par.astype(np.float64)
 
 
@@ -299,8 +316,9 @@ def srtt_y(r2: int, m: int, seed: int, row0: int = 0) -> np.ndarray:
     return hadamard_entries(rows, np.arange(m)) * d[None, :]
 
 
-def hrtt_x(n: int, s: int, seed: int) -> np.ndarray:
-    """Unscaled hashed randomized Hadamard right embedding, n x s: X = D H C^T.
+def hrtt_x(n: int, s: int, seed: int, rows=None) -> np.ndarray:
+    """Unscaled hashed randomized Hadamard right embedding, n x s: X = D H C^T
+    (only the given rows when `rows` is not None).
 
     Sec. 3.4 (HRTT): Eq. (Theta) with the sampling matrix S replaced by a
     hashing matrix; here C[h(c), c] = sigma_c with h(c) = pi^{-1}(c) mod s over
@@ -315,10 +333,10 @@ def hrtt_x(n: int, s: int, seed: int) -> np.ndarray:
     n_pad = 1 << b
     if s > n_pad:
         raise ValueError("HRTT width exceeds the padded dimension (empty buckets)")
-    d = signs(n, STREAM_DX, seed)
+    rows = np.arange(n) if rows is None else np.asarray(rows, dtype=np.int64)
+    d = signs(n, STREAM_DX, seed)[rows]
     sigma = signs(n_pad, STREAM_SX, seed)
-    rows = np.arange(n)
-    X = np.empty((n, s), dtype=np.float64)
+    X = np.empty((rows.size, s), dtype=np.float64)
     for k in range(s):
         c = feistel_perm(np.arange(k, n_pad, s), b, STREAM_PX, seed)   # bucket k
         X[:, k] = d * (hadamard_entries(rows, c) @ sigma[c])

@@ -208,8 +208,23 @@ def test_hrtt_is_unbiased():
     assert abs(acc[0, 0] - 1.0) < 0.1
 
 
+def test_hrtt_selected_rows():
+    idx = np.array([0, 5, 99, 37])
+    assert np.array_equal(rng.hrtt_x(100, 24, seed=3, rows=idx), rng.hrtt_x(100, 24, seed=3)[idx])
+
+
 def test_hrtt_argument_errors():
     with pytest.raises(ValueError):
         rng.hrtt_x(100, 256, seed=0)                # s > n_pad = 128: empty buckets
     with pytest.raises(ValueError):
         rng.hrtt_x(100, 0, seed=0)
+
+
+def test_hadamard_entries_wide_indices():
+    # indices above 16 bits use both halves of the parity table: compare with the
+    # Sylvester recursion H_{2N} = [[H, H], [H, -H]] at index 2^20 + i
+    i = np.arange(0, 1 << 21, 4099)
+    c = np.array([1 << 20, (1 << 20) | 5, 65537, 3])
+    got = rng.hadamard_entries(i, c)
+    want = np.array([[(-1.0) ** bin(int(a) & int(b)).count("1") for b in c] for a in i])
+    assert np.array_equal(got, want)
