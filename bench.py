@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
-    ap.add_argument("--kind", default="gaussian", choices=["gaussian", "srht"])
+    ap.add_argument("--kind", default="gaussian", choices=["gaussian", "srht", "hrtt"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -190,9 +190,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    kind_code = 0 if args.kind == "gaussian" else 1
+    kind_code = {"gaussian": 0, "srht": 1, "hrtt": 2}[args.kind]
+    xy = f"{args.kind} X, gaussian Y" if args.kind == "hrtt" else f"{args.kind} X and Y"
     cfg = {"workload": f"single matrix {w['m']}x{w['n']} FP32, sigma=1 (i<=200) then 1e-6/i, "
-                       f"eps={w['eps']}, {args.kind} X and Y, s=8..256 doubling"
+                       f"eps={w['eps']}, {xy}, s=8..256 doubling"
            if args.workload in ("large", "medium") else
            f"single matrix {w['m']}x{w['n']}, sigma=10^-(i-1)/10, eps={w['eps']}",
            "m": w["m"], "n": w["n"], "dtype_A": "f32", "eps": w["eps"], "sketch": args.kind,
@@ -359,31 +360,34 @@ def main():
     line["forms_identical_ranks"] = forms_ok
 
     if args.kind == "gaussian":
-        # the SRHT right sketch (register FWHT, one pass of A per append) on the same
-        # matrix; its rank is reported, not compared: on this coherent U, V the sampled
-        # Hadamard columns alias and the SRHT estimate may fall short of the true rank
-        hs = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_FP32))
-        rs, _ = rk.re_rank_estimate(hs, A, w["eps"], 1, w["sketch_seed"], stream=stream)
-        torch.cuda.synchronize()
-        rk.re_stats_enable(hs, True)
-        rk.re_stats_reset(hs)
-        es0 = torch.cuda.Event(enable_timing=True)
-        es1 = torch.cuda.Event(enable_timing=True)
-        es0.record(stream)
-        for _ in range(K):
-            rs, _ = rk.re_rank_estimate(hs, A, w["eps"], 1, w["sketch_seed"], stream=stream)
-        es1.record(stream)
-        torch.cuda.synchronize()
-        ss = rk.re_stats_get(hs)
-        rk.re_destroy(hs)
-        ms_s = es0.elapsed_time(es1) / K
-        gbs = ss.right_bytes / (ss.right_ms * 1e-3) / 1e9 if ss.right_ms else 0.0
-        line["srht"] = {"estimates_per_s": 1e3 / ms_s, "ms": ms_s, "rank": rs.rank, "final_s": rs.final_s,
-                        "passes": rs.passes, "flags": rs.flags,
-                        "right_sketch_gbs": gbs, "right_sketch_frac": gbs / hbm,
-                        "right_ms_per_step": ss.right_ms / K,
-                        "stage_ms_per_step": {"right": ss.right_ms / K, "left": ss.left_ms / K,
-                                              "svd": ss.svd_ms / K, "other": ss.other_ms / K}}
+        # the Hadamard right sketches (register FWHT, one pass of A per width) on the
+        # same matrix.  SRHT: sampled columns, appended; on this coherent U, V they
+        # alias and the estimate may fall short of the true rank (reported, not
+        # compared).  HRTT: hashed outputs, the whole width anew at every step,
+        # Gaussian Y; hashing keeps the embedding on coherent inputs.
+        for name, code in (("srht", rk.RE_SRHT), ("hrtt", rk.RE_HRTT)):
+            hs = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_FP32))
+            rs, _ = rk.re_rank_estimate(hs, A, w["eps"], code, w["sketch_seed"], stream=stream)
+            torch.cuda.synchronize()
+            rk.re_stats_enable(hs, True)
+            rk.re_stats_reset(hs)
+            es0 = torch.cuda.Event(enable_timing=True)
+            es1 = torch.cuda.Event(enable_timing=True)
+            es0.record(stream)
+            for _ in range(K):
+                rs, _ = rk.re_rank_estimate(hs, A, w["eps"], code, w["sketch_seed"], stream=stream)
+            es1.record(stream)
+            torch.cuda.synchronize()
+            ss = rk.re_stats_get(hs)
+            rk.re_destroy(hs)
+            ms_s = es0.elapsed_time(es1) / K
+            gbs = ss.right_bytes / (ss.right_ms * 1e-3) / 1e9 if ss.right_ms else 0.0
+            line[name] = {"estimates_per_s": 1e3 / ms_s, "ms": ms_s, "rank": rs.rank, "final_s": rs.final_s,
+                          "passes": rs.passes, "flags": rs.flags,
+                          "right_sketch_gbs": gbs, "right_sketch_frac": gbs / hbm,
+                          "right_ms_per_step": ss.right_ms / K,
+                          "stage_ms_per_step": {"right": ss.right_ms / K, "left": ss.left_ms / K,
+                                                "svd": ss.svd_ms / K, "other": ss.other_ms / K}}
 
     if not args.no_e2e:
         Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)

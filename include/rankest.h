@@ -63,6 +63,11 @@ extern "C" {
 /* embedding kinds (Sec. 3.4) */
 #define RE_GAUSSIAN 0 /* iid N(0,1) entries, scaled by 1/sqrt(width) */
 #define RE_SRHT 1     /* sqrt(N/r) S H D, H Sylvester Hadamard on the zero-padded dimension */
+/* Hashed randomized Hadamard transform (Sec. 3.4, HRTT): X = D (H/sqrt(N)) C^T,
+ * C a CountSketch (coordinate c in bucket pi^{-1}(c) mod s, random sign).  Right
+ * embedding only; its columns depend on the width, so it is not appendable and
+ * every doubling step sketches anew; the left embedding defaults to Gaussian. */
+#define RE_HRTT 2
 
 /* arithmetic of the Gaussian right sketch */
 #define RE_PREC_FP32 0   /* FP32 FMA on CUDA cores */
@@ -156,7 +161,10 @@ int re_stats_get(re_handle h, re_stats* out);
  * Algorithm 1 with doubling (Sec. 5): estimate rank_eps(A).
  *   A          device pointer, m x n row-major, leading dimension ld.
  *   eps        relative tolerance in (0, 1) (Definition 1).
- *   sketch_kind RE_GAUSSIAN or RE_SRHT (right embedding; left per opts.y_kind).
+ *   sketch_kind RE_GAUSSIAN, RE_SRHT or RE_HRTT (right embedding; left per
+ *              opts.y_kind, by default the same kind, Gaussian for RE_HRTT).
+ *              RE_SRHT / RE_HRTT take min(m, n) <= 32768 (else RE_ERR_UNSUPPORTED);
+ *              RE_HRTT with opts.learned is RE_ERR_UNSUPPORTED.
  *   seed       generator key for X and Y.
  *   sigma_out  host buffer of sigma_cap doubles, receives the first
  *              min(n_sigma, sigma_cap) scaled sketched singular values
@@ -181,7 +189,9 @@ int re_rank_estimate_host(re_handle h, const void* A_host, int dtype, int64_t m,
  *   AX   device FP32, rows x ld_ax row-major (rows = max(m, n)); columns
  *        k0 .. k0+s-1 receive the UNSCALED right sketch A*G[:, k0:k0+s] (Gaussian G
  *        entries, or D H S^T entries +-1 for RE_SRHT).  Columns < k0 must hold
- *        earlier columns from the same seed when core is non-NULL.
+ *        earlier columns from the same seed when core is non-NULL.  RE_HRTT
+ *        (col0 must be 0) writes the whole width-s sketch A D H C^T (unscaled:
+ *        the caller applies 1/sqrt(N), N = 2^ceil(log2 min(m, n))).
  *   core optional device FP64, (2 (k0+s)) x ld_core row-major: on entry its
  *        leading 2 k0 x k0 block holds the previous unscaled core; on return the
  *        leading 2(k0+s) x (k0+s) block holds Y[0:2(k0+s)] * A * X[:, 0:k0+s].
@@ -206,7 +216,8 @@ int re_core_sigma(re_handle h, const double* core, int r2, int s, int64_t ld,
  * The embeddings themselves, for tests and for callers that want X or Y
  * explicitly (the estimator never materialises them this way):
  *   re_embedding_x: out (device FP32, n x s row-major) = columns col0.. of the
- *                   unscaled X (n = number of columns of the oriented A).
+ *                   unscaled X (n = number of columns of the oriented A); for
+ *                   RE_HRTT col0 = 0 and the s columns of the width-s X.
  *   re_embedding_y: out (device FP32, r2 x m row-major) = rows row0.. of the
  *                   unscaled Y (m = number of rows of the oriented A).
  */

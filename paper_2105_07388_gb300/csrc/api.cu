@@ -50,7 +50,7 @@ struct re_handle_ {
     re_stats stats{};
     std::vector<PendingTiming> pending;
     std::vector<cudaEvent_t> event_pool;
-    DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status;
+    DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status, ht;
     re::BatchedState* batched = nullptr;
     // sketch-size proposal network: parameters, Adam moments, gradient, scratch
     DevBuf mlp_P, mlp_M, mlp_V, mlp_G, mlp_X, mlp_y, mlp_logits, mlp_keep, mlp_cls, mlp_feat, mlp_loss;
@@ -150,6 +150,14 @@ int r1_of_s(int s) {
     return r;
 }
 
+// Left embedding: opts.y_kind, else the right one's kind; the HRTT's is Gaussian
+// (the column space of A X is that of A's leading left singular vectors, as
+// coherent as A's, where a sampled Hadamard Y aliases).
+int left_kind(re_handle h, int kind) {
+    if (h->opts.y_kind >= 0) return h->opts.y_kind;
+    return kind == RE_HRTT ? RE_GAUSSIAN : kind;
+}
+
 struct Plan {
     re::MatView A;
     int kind;     // right embedding
@@ -166,7 +174,7 @@ int make_plan(const void* A, int dtype, int64_t m, int64_t n, int64_t ld, int ki
     if (m <= 0 || n <= 0) return fail(RE_ERR_ARG, "m and n must be positive");
     if (ld < n) return fail(RE_ERR_ARG, "ld < n");
     if (m > INT32_MAX || n > INT32_MAX) return fail(RE_ERR_ARG, "dimension too large");
-    if (kind != RE_GAUSSIAN && kind != RE_SRHT) return fail(RE_ERR_ARG, "unknown sketch kind");
+    if (kind != RE_GAUSSIAN && kind != RE_SRHT && kind != RE_HRTT) return fail(RE_ERR_ARG, "unknown sketch kind");
     if (ykind != RE_GAUSSIAN && ykind != RE_SRHT) return fail(RE_ERR_ARG, "unknown left sketch kind");
     p->A.ptr = A;
     p->A.dtype = dtype;
@@ -180,8 +188,10 @@ int make_plan(const void* A, int dtype, int64_t m, int64_t n, int64_t ld, int ki
     p->mbits = re::pow2_bits(p->A.rows);
     p->n_pad = int64_t(1) << p->nbits;
     p->m_pad = int64_t(1) << p->mbits;
+    if (kind != RE_GAUSSIAN && p->nbits > 15)
+        return fail(RE_ERR_UNSUPPORTED, "right Hadamard transforms of more than 2^15 points are not built");
     int64_t cap = s_max;
-    if (kind == RE_SRHT) cap = std::min<int64_t>(cap, p->n_pad);
+    if (kind == RE_SRHT || kind == RE_HRTT) cap = std::min<int64_t>(cap, p->n_pad);   // HRTT: no empty bucket
     if (ykind == RE_SRHT) cap = std::min<int64_t>(cap, p->m_pad / 2);
     p->cap = (int)cap;
     return RE_OK;
@@ -252,6 +262,25 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
         if (e != cudaSuccess) return cuda_fail(e, "right sketch (FP32)");
         stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 4), 2.0 * P.A.rows * P.A.cols * cnt);
         h->stats.launches += 2;
+        return RE_OK;
+    }
+    if (P.kind == RE_HRTT) {
+        // HRTT of width cnt (columns depend on the width: c0 is where AX receives them)
+        if (int r = ensure(h->dx, sizeof(uint32_t) * (size_t)(P.n_pad / 32 + 1))) return r;
+        if (int r = ensure(h->ht, sizeof(uint16_t) * (size_t)P.n_pad)) return r;
+        cudaEvent_t g = stage_begin(h, st);
+        e = re::launch_sign_bits(seed, re::kStreamDX, P.A.cols, static_cast<uint32_t*>(h->dx.p), st);
+        if (e == cudaSuccess) e = re::launch_hrtt_table(seed, P.nbits, static_cast<uint16_t*>(h->ht.p), st);
+        stage_end(h, st, g, kStageOther);
+        if (int r = ensure(h->status, 64)) return r;
+        cudaEvent_t a = stage_begin(h, st);
+        if (e == cudaSuccess)
+            e = re::launch_right_hrtt(P.A, static_cast<const uint32_t*>(h->dx.p), static_cast<const uint16_t*>(h->ht.p),
+                                      cnt, AX + c0, ld_ax, st, static_cast<int*>(h->status.p) + 1);
+        if (e != cudaSuccess) return cuda_fail(e, "right sketch (HRTT)");
+        stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 0),
+                  (double)P.A.rows * (double)P.n_pad * (double)(P.nbits + 1));
+        h->stats.launches += 3;
         return RE_OK;
     }
     // SRHT: signs of the padded n and sampled columns pi_X(c0 .. c0+cnt-1)
@@ -337,7 +366,9 @@ int check_width(re_handle h, const Plan& P, int s, int smax, double eps, re::Dev
     if (e != cudaSuccess) return cuda_fail(e, "core singular values");
     stage_end(h, st, a, kStageSvd);
     const int r1 = std::min(r1_of_s(s), s);
-    const double scale = 1.0 / std::sqrt((double)s * (double)(2 * s));
+    // X = G/sqrt(s) or D H S^T/sqrt(s); the HRTT's D (H/sqrt(n_pad)) C^T; Y scaled by 1/sqrt(2s)
+    const double xs = P.kind == RE_HRTT ? (double)P.n_pad : (double)s;
+    const double scale = 1.0 / std::sqrt(xs * (double)(2 * s));
     e = re::launch_readoff(static_cast<const double*>(h->sigma.p), r1, scale, eps, h->opts.norm_a, status,
                            static_cast<re::DevReadoff*>(h->ro.p), static_cast<double*>(h->sigma_scaled.p), st);
     if (e != cudaSuccess) return cuda_fail(e, "read-off");
@@ -377,12 +408,15 @@ int propose_width(re_handle h, const Plan& P, double eps, int* cls, cudaStream_t
 // target width s*, one more pass appends up to s*, and the read-off is checked
 // on the nested leading blocks at every ladder width up to s* in order -- so the
 // answer is the plain ladder's whenever s* is at least the plain final width;
-// otherwise doubling continues from s*.
+// otherwise doubling continues from s*.  The HRTT's columns depend on the
+// width, so with it every step sketches A and forms the core anew.
 int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* sigma_out, int sigma_cap,
                  re_result* out, cudaStream_t st) {
     const re_opts& o = h->opts;
     if (o.s0 > P.cap) return fail(RE_ERR_ARG, "initial sketch width exceeds the admissible width");
     if (o.learned && !h->mlp_ready) return fail(RE_ERR_ARG, "learned proposal requested but no network is loaded");
+    if (o.learned && P.kind == RE_HRTT)
+        return fail(RE_ERR_UNSUPPORTED, "the proposal network needs an appendable embedding (Gaussian or SRHT)");
     int smax = o.s0;
     while (smax * 2 <= P.cap) smax *= 2;
     const int64_t M = P.A.rows;
@@ -442,7 +476,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
         }
     }
     while (!done) {
-        if (int r = sketch_to(s_prev, s)) return r;
+        if (int r = sketch_to(P.kind == RE_HRTT ? 0 : s_prev, s)) return r;
         ++passes;
         if (int r = check_width(h, P, s, smax, eps, &ro, &r1, st, 2 * s <= smax)) return r;
         if (ro.rank >= 0 || 2 * s > smax || r1 >= P.A.cols) break;
@@ -534,7 +568,7 @@ int re_destroy(re_handle h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&h->x, &h->xt, &h->ax, &h->part, &h->core, &h->sigma, &h->sigma_scaled,
-                      &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status,
+                      &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status, &h->ht,
                       &h->mlp_P, &h->mlp_M, &h->mlp_V, &h->mlp_G, &h->mlp_X, &h->mlp_y,
                       &h->mlp_logits, &h->mlp_keep, &h->mlp_cls, &h->mlp_feat, &h->mlp_loss};
     for (DevBuf* b : bufs) release(*b);
@@ -582,7 +616,7 @@ int re_rank_estimate(re_handle h, const void* A, int dtype, int64_t m, int64_t n
     if (!(eps > 0.0 && eps < 1.0)) return fail(RE_ERR_ARG, "eps must lie in (0, 1)");
     if (sigma_cap > 0 && !sigma_out) return fail(RE_ERR_ARG, "sigma_out is NULL");
     cudaSetDevice(h->device);
-    const int ykind = h->opts.y_kind < 0 ? sketch_kind : h->opts.y_kind;
+    const int ykind = left_kind(h, sketch_kind);
     Plan P;
     if (int r = make_plan(A, dtype, m, n, ld, sketch_kind, ykind, h->opts.s_max, &P)) return r;
     return run_estimate(h, P, eps, seed, sigma_out, sigma_cap, out,
@@ -617,11 +651,13 @@ int re_sketch_apply(re_handle h, const void* A, int dtype, int64_t m, int64_t n,
     if (ld_ax < col0 + s) return fail(RE_ERR_ARG, "ld_ax < col0 + s");
     if (core && ld_core < col0 + s) return fail(RE_ERR_ARG, "ld_core < col0 + s");
     cudaSetDevice(h->device);
-    const int ykind = h->opts.y_kind < 0 ? sketch_kind : h->opts.y_kind;
+    const int ykind = left_kind(h, sketch_kind);
     Plan P;
     if (int r = make_plan(A, dtype, m, n, ld, sketch_kind, ykind, 1 << 30, &P)) return r;
-    if (sketch_kind == RE_SRHT && col0 + s > P.n_pad)
-        return fail(RE_ERR_ARG, "SRHT width exceeds the padded dimension");
+    if ((sketch_kind == RE_SRHT || sketch_kind == RE_HRTT) && col0 + s > P.n_pad)
+        return fail(RE_ERR_ARG, "SRHT/HRTT width exceeds the padded dimension");
+    if (sketch_kind == RE_HRTT && col0 != 0)
+        return fail(RE_ERR_ARG, "HRTT columns depend on the width: col0 must be 0");
     if (core && ykind == RE_SRHT && 2 * (int64_t)(col0 + s) > P.m_pad)
         return fail(RE_ERR_ARG, "SRHT left width exceeds the padded dimension");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -666,6 +702,18 @@ int re_embedding_x(re_handle h, int kind, uint64_t seed, int64_t n, int col0, in
         if (e == cudaSuccess)
             e = re::launch_srtt_x_dense(n, s, static_cast<const uint32_t*>(h->dx.p),
                                         static_cast<const int*>(h->px.p), out, s, st);
+    } else if (kind == RE_HRTT) {
+        const int bits = re::pow2_bits(n);
+        if (bits > 15) return fail(RE_ERR_UNSUPPORTED, "HRTT of more than 2^15 points");
+        if (col0 != 0) return fail(RE_ERR_ARG, "HRTT columns depend on the width: col0 must be 0");
+        if (s > (int64_t(1) << bits)) return fail(RE_ERR_ARG, "HRTT width exceeds the padded dimension");
+        if (int r = ensure(h->dx, sizeof(uint32_t) * (size_t)((int64_t(1) << bits) / 32 + 1))) return r;
+        if (int r = ensure(h->ht, sizeof(uint16_t) * (size_t)(int64_t(1) << bits))) return r;
+        e = re::launch_sign_bits(seed, re::kStreamDX, n, static_cast<uint32_t*>(h->dx.p), st);
+        if (e == cudaSuccess) e = re::launch_hrtt_table(seed, bits, static_cast<uint16_t*>(h->ht.p), st);
+        if (e == cudaSuccess)
+            e = re::launch_hrtt_x_dense(n, s, bits, static_cast<const uint32_t*>(h->dx.p),
+                                        static_cast<const uint16_t*>(h->ht.p), out, s, st);
     } else {
         return fail(RE_ERR_ARG, "unknown kind");
     }
@@ -707,7 +755,7 @@ int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int
     if (!(eps > 0.0 && eps < 1.0)) return fail(RE_ERR_ARG, "eps must lie in (0, 1)");
     if (count == 0) return RE_OK;
     cudaSetDevice(h->device);
-    const int ykind = h->opts.y_kind < 0 ? sketch_kind : h->opts.y_kind;
+    const int ykind = left_kind(h, sketch_kind);
     if (dtype == RE_F32 && sketch_kind == RE_GAUSSIAN && ykind == RE_GAUSSIAN && !h->opts.learned) {
         // one graph launch over all blocks (level-synchronous batched kernels)
         return re::batched_estimate(&h->batched, h->opts, blocks, count, eps, seed, sigma_out,

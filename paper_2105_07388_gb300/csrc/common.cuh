@@ -33,6 +33,7 @@ constexpr uint32_t kStreamDX = 3;
 constexpr uint32_t kStreamPX = 4;
 constexpr uint32_t kStreamDY = 5;
 constexpr uint32_t kStreamPY = 6;
+constexpr uint32_t kStreamSX = 7;   // CountSketch signs of the HRTT (one per transform coordinate)
 
 struct U4 {
     uint32_t x, y, z, w;

@@ -92,6 +92,36 @@ __global__ void srtt_x_dense_kernel(int64_t n, int s, const uint32_t* dbits, con
     X[k * ldx + j] = par ? -1.0f : 1.0f;
 }
 
+// HRTT hashing table (Sec. 3.4): entry q is c = pi_X(q) with bit 15 set when the
+// CountSketch sign sigma_c (stream SX, drawn as the SRTT signs) is -1.  Bucket k
+// of width s is {entry q : q = k mod s}, so one table serves every width.
+__global__ void hrtt_table_kernel(uint64_t seed, int bits, int np, uint16_t* tbl) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= np) return;
+    const uint32_t c = feistel((uint32_t)q, bits, kStreamPX, seed);
+    const U4 r = philox(c >> 7, 0u, kStreamSX, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const int sel = (int)((c & 127u) >> 5);
+    const uint32_t w = sel == 0 ? r.x : sel == 1 ? r.y : sel == 2 ? r.z : r.w;
+    tbl[q] = (uint16_t)(c | (((w >> (c & 31u)) & 1u) << 15));
+}
+
+// Dense HRTT X (n x s, entries are sums of +-1, exact in FP32):
+// X[k, j] = d_k sum over bucket j of sigma_c H[k, c].
+__global__ void hrtt_x_dense_kernel(int64_t n, int s, int np, const uint32_t* dbits, const uint16_t* tbl,
+                                    float* X, int64_t ldx) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * s) return;
+    const int64_t k = idx / s;
+    const int j = (int)(idx % s);
+    int acc = 0;
+    for (int q = j; q < np; q += s) {
+        const uint32_t e = tbl[q];
+        const uint32_t par = (__popcll((unsigned long long)(k & (int64_t)(e & 0x7fffu))) & 1) ^ (e >> 15);
+        acc += par ? -1 : 1;
+    }
+    X[k * ldx + j] = ((dbits[k >> 5] >> (k & 31)) & 1u) ? (float)-acc : (float)acc;
+}
+
 __global__ void srtt_y_dense_kernel(int64_t m, int r2, const uint32_t* dbits, const int* rows,
                                     float* Y, int64_t ldy) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,6 +183,20 @@ cudaError_t launch_srtt_x_dense(int64_t n, int s, const uint32_t* dbits, const i
                                 int64_t ldx, cudaStream_t st) {
     if (n <= 0 || s <= 0) return cudaSuccess;
     srtt_x_dense_kernel<<<blocks_for(n * s, 256), 256, 0, st>>>(n, s, dbits, cols, X, ldx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hrtt_table(uint64_t seed, int bits, uint16_t* tbl, cudaStream_t st) {
+    if (bits > 15) return cudaErrorInvalidValue;     // entries hold c in 15 bits
+    const int np = 1 << bits;
+    hrtt_table_kernel<<<blocks_for(np, 256), 256, 0, st>>>(seed, bits, np, tbl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hrtt_x_dense(int64_t n, int s, int bits, const uint32_t* dbits, const uint16_t* tbl,
+                                float* X, int64_t ldx, cudaStream_t st) {
+    if (n <= 0 || s <= 0) return cudaSuccess;
+    hrtt_x_dense_kernel<<<blocks_for(n * s, 256), 256, 0, st>>>(n, s, 1 << bits, dbits, tbl, X, ldx);
     return cudaGetLastError();
 }
 

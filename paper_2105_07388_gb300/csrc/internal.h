@@ -58,6 +58,11 @@ cudaError_t launch_srtt_x_dense(int64_t n, int s, const uint32_t* dbits, const i
                                 int64_t ldx, cudaStream_t st);
 cudaError_t launch_srtt_y_dense(int64_t m, int r2, const uint32_t* dbits, const int* rows, float* Y,
                                 int64_t ldy, cudaStream_t st);
+// HRTT hashing table of 2^bits entries (bits <= 15): entry q = pi_X(q) | (sigma < 0) << 15.
+cudaError_t launch_hrtt_table(uint64_t seed, int bits, uint16_t* tbl, cudaStream_t st);
+// Dense HRTT X (n x s, +-integer entries) for re_embedding_x.
+cudaError_t launch_hrtt_x_dense(int64_t n, int s, int bits, const uint32_t* dbits, const uint16_t* tbl,
+                                float* X, int64_t ldx, cudaStream_t st);
 
 // ---- right sketch, FP32 SIMT (sketch_simt.cu) -------------------------------------
 // C[:, 0:s] (row-major, ldc) = A_oriented * X[:, 0:s], X FP32 row-major n' x ldx.
@@ -112,6 +117,11 @@ cudaError_t launch_right_simt_batched(const BatchDesc* d, int count, const int64
 // ---- right sketch, SRHT (sketch_srht.cu) --------------------------------------
 // C[:, 0:s] = A_oriented * D H S^T with sampled Hadamard columns cols[0..s).
 cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int* cols, int s,
+                              float* C, int64_t ldc, cudaStream_t st, int* err = nullptr);
+// C[:, 0:s] = A_oriented D H C^T (HRTT, unscaled): output k sums the transform
+// coordinates of bucket k with their CountSketch signs, read from the table of
+// launch_hrtt_table (pow2_bits(cols) bits).  Requires s <= 2^bits.
+cudaError_t launch_right_hrtt(const MatView& A, const uint32_t* dbits, const uint16_t* tbl, int s,
                               float* C, int64_t ldc, cudaStream_t st, int* err = nullptr);
 
 // ---- right sketch, BF16x3 tensor cores (sketch_tc.cu) ------------------------------

@@ -18,6 +18,13 @@
 // transform longer than n_pad gives the same sampled values, so four kernel
 // sizes (2^8, 2^10, 2^12, 2^14) serve every n <= 16384.  Longer rows
 // (n <= 32768) use a shared-memory-only transform, one row per CTA.
+//
+// The same kernels give the hashed transform (HRTT, Sec. 3.4: the sampling S
+// replaced by a CountSketch C): instead of gathering s sampled coordinates,
+// output k adds every coordinate c of its bucket with the sign sigma_c.  The
+// buckets come from one table of n_pad 16-bit entries (entry q = pi(q) with
+// the sign in bit 15; bucket k = entries q = k mod s), so a row costs n_pad
+// extra shared-memory reads on top of the transform.
 #include <algorithm>
 
 #include "common.cuh"
@@ -49,11 +56,29 @@ __device__ __forceinline__ void fwht_regs(float (&x)[E]) {
     }
 }
 
+// HRTT outputs of one transformed row y (y[phys(c)] = coordinate c), any s:
+// output k adds the entries q = k, k + s, ... < np of the table in that order.
+// Thread j of T makes outputs j, j + T, ...
+template <typename Phys>
+__device__ __forceinline__ void hashed_outputs_any(const float* y, Phys phys, const uint16_t* __restrict__ htab,
+                                                   int np, int s, int j, int T, float* __restrict__ out) {
+    for (int k = j; k < s; k += T) {
+        float acc = 0.0f;
+        for (int q = k; q < np; q += s) {
+            const uint32_t e = __ldg(htab + q);
+            const float v = y[phys((int)(e & 0x7fffu))];
+            acc += (e & 0x8000u) ? -v : v;
+        }
+        out[k] = acc;
+    }
+}
+
 template <int LOGN, bool TRANS, typename TA>
 __global__ void __launch_bounds__(128) srht_reg_kernel(const TA* __restrict__ A, int64_t lda,
                                                        int64_t M, int64_t N,
                                                        const uint32_t* __restrict__ dbits,
-                                                       const int* __restrict__ cols, int s,
+                                                       const int* __restrict__ cols,
+                                                       const uint16_t* __restrict__ htab, int hnp, int s,
                                                        float* __restrict__ C, int64_t ldc) {
     constexpr int NP = 1 << LOGN;
     constexpr int LOGT = LOGN / 2;
@@ -70,7 +95,8 @@ __global__ void __launch_bounds__(128) srht_reg_kernel(const TA* __restrict__ A,
 
     const int64_t nwords = (N + 31) / 32;
     for (int w = threadIdx.x; w < NP / 32; w += blockDim.x) sd[w] = (w < nwords) ? dbits[w] : 0u;
-    for (int k = threadIdx.x; k < s; k += blockDim.x) scol[k] = cols[k];
+    if (!htab)
+        for (int k = threadIdx.x; k < s; k += blockDim.x) scol[k] = cols[k];
     __syncthreads();
 
     const int g = threadIdx.x / T;
@@ -104,7 +130,10 @@ __global__ void __launch_bounds__(128) srht_reg_kernel(const TA* __restrict__ A,
         for (int r = 0; r < E; ++r) gb[phys(j * E + r)] = x[r];
         __syncthreads();
         if (live) {
-            for (int k = j; k < s; k += T) C[row * ldc + k] = gb[phys(scol[k])];
+            if (htab)
+                hashed_outputs_any(gb, phys, htab, hnp, s, j, T, C + row * ldc);
+            else
+                for (int k = j; k < s; k += T) C[row * ldc + k] = gb[phys(scol[k])];
         }
         __syncthreads();
     }
@@ -115,7 +144,8 @@ template <bool TRANS, typename TA>
 __global__ void __launch_bounds__(1024) srht_smem_kernel(const TA* __restrict__ A, int64_t lda,
                                                          int64_t M, int64_t N, int logn,
                                                          const uint32_t* __restrict__ dbits,
-                                                         const int* __restrict__ cols, int s,
+                                                         const int* __restrict__ cols,
+                                                         const uint16_t* __restrict__ htab, int s,
                                                          float* __restrict__ C, int64_t ldc) {
     extern __shared__ float4 smem4[];
     float* buf = reinterpret_cast<float*>(smem4);
@@ -139,7 +169,11 @@ __global__ void __launch_bounds__(1024) srht_smem_kernel(const TA* __restrict__ 
             }
             __syncthreads();
         }
-        for (int k = threadIdx.x; k < s; k += blockDim.x) C[row * ldc + k] = buf[cols[k]];
+        if (htab)
+            hashed_outputs_any(buf, [](int c) { return c; }, htab, np, s, (int)threadIdx.x, (int)blockDim.x,
+                               C + row * ldc);
+        else
+            for (int k = threadIdx.x; k < s; k += blockDim.x) C[row * ldc + k] = buf[cols[k]];
         __syncthreads();
     }
 }
@@ -282,6 +316,47 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_vec_kernel(c
     }
 }
 
+// HRTT outputs of one row held in buf (phys_sw layout, NP = 32 T coordinates)
+// for s a power of two: thread j adds the 32 table entries q = u T + j in the
+// order of u.  For s >= T these land in its own buckets (u mod s/T) T + j, in
+// bucket order; for s < T all in bucket j mod s, whose T/s partial sums (T/32
+// after a shuffle reduction when s < 32) are then added through red.
+template <int T>
+__device__ __forceinline__ void hashed_outputs_pow2(const float* buf, const uint16_t* htab, int s, int j,
+                                                    float* red, float* __restrict__ out) {
+    auto term = [&](int u) {
+        const uint32_t e = htab[u * T + j];
+        const float v = buf[phys_sw((int)(e & 0x7fffu))];
+        return (e & 0x8000u) ? -v : v;
+    };
+    if (s >= T) {                                        // uniform across the CTA: no barrier below
+        const int V = s / T;
+        for (int v = 0; v < V; ++v) {
+            float acc = 0.0f;
+            for (int u = v; u < 32; u += V) acc += term(u);
+            out[v * T + j] = acc;
+        }
+        return;
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 32; ++u) acc += term(u);
+    if (s < 32) {
+        // lanes with equal lane mod s share a bucket: fold the higher lane bits
+        for (int off = 16; off >= s; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if ((j & 31) < s) red[(j >> 5) * s + (j & 31)] = acc;
+    } else {
+        red[j] = acc;
+    }
+    __syncthreads();
+    if (j < s) {
+        const int cnt = T / (s < 32 ? 32 : s);
+        float t = 0.0f;
+        for (int i = 0; i < cnt; ++i) t += red[i * s + j];
+        out[j] = t;
+    }
+}
+
 // Bulk-copy form of srht_vec_kernel for rows of a multiple of 4 floats: each
 // row arrives in shared memory by one bulk copy (cp.async.bulk, completion on an
 // mbarrier) issued as soon as the previous row's gather is done; phase 1 then
@@ -289,16 +364,20 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_vec_kernel(c
 // buffer serves the two transposes.  With one row buffer per CTA, 2^(15-L) CTAs
 // share an SM, so one CTA's copy and barriers overlap the others' transforms.
 // Waits are bounded in time; on expiry *err is set and the CTA drains its copy
-// and returns.
-template <int L>
+// and returns.  HASH selects the HRTT outputs (table htab of NP entries, s a
+// power of two) instead of the s sampled coordinates cols.
+template <int L, bool HASH>
 __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_bulk_kernel(
     const float* __restrict__ A, int64_t lda, int64_t M, int64_t N, const uint32_t* __restrict__ dbits,
-    const int* __restrict__ cols, int s, float* __restrict__ C, int64_t ldc, int* err) {
+    const int* __restrict__ cols, const uint16_t* __restrict__ htab_g, int s, float* __restrict__ C,
+    int64_t ldc, int* err) {
     constexpr int T = 1 << (L - 5);
     constexpr int NP = 1 << L;
     extern __shared__ __align__(128) float4 smem4[];
     float* buf = reinterpret_cast<float*>(smem4);           // NP floats, swizzled
-    int* scol = reinterpret_cast<int*>(buf + NP);
+    int* scol = reinterpret_cast<int*>(buf + NP);           // s sampled coordinates (SRHT)
+    uint16_t* htab = reinterpret_cast<uint16_t*>(buf + NP); // NP table entries (HRTT)
+    float* red = buf + NP + NP / 2;                         // T partial sums (HRTT)
     __shared__ __align__(8) uint64_t full;
     const int j = threadIdx.x;
     const uint32_t row_bytes = (uint32_t)(N * 4);
@@ -309,7 +388,11 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_bulk_kernel(
         tc::mbar_init(&full, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int k = j; k < s; k += T) scol[k] = cols[k];
+    if constexpr (HASH) {
+        for (int q = j; q < NP; q += T) htab[q] = htab_g[q];
+    } else {
+        for (int k = j; k < s; k += T) scol[k] = cols[k];
+    }
     __syncthreads();
     auto issue = [&](int64_t r) {
         tc::fence_proxy_async();                             // earlier generic accesses of buf first
@@ -380,15 +463,18 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_bulk_kernel(
             for (int k = 0; k < 32; ++k) buf[o3[k & 7] + 128 * k] = x[k];
         }
         __syncthreads();
-        for (int k = j; k < s; k += T) C[row * ldc + k] = buf[phys_sw(scol[k])];
+        if constexpr (HASH)
+            hashed_outputs_pow2<T>(buf, htab, s, j, red, C + row * ldc);
+        else
+            for (int k = j; k < s; k += T) C[row * ldc + k] = buf[phys_sw(scol[k])];
         __syncthreads();                                      // every gather read of buf is done
         if (j == 0 && row + gridDim.x < M) issue(row + gridDim.x);
     }
 }
 
-template <int L>
-cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C, int64_t ldc,
-                        int* err, cudaStream_t st);
+template <int L, bool HASH>
+cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, const uint16_t* htab, int s,
+                        float* C, int64_t ldc, int* err, cudaStream_t st);
 
 template <int L>
 cudaError_t launch_vec(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
@@ -423,26 +509,27 @@ cudaError_t launch_vec(const MatView& A, const uint32_t* dbits, const int* cols,
     return cudaGetLastError();
 }
 
-template <int L>
-cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C, int64_t ldc,
-                        int* err, cudaStream_t st) {
+template <int L, bool HASH>
+cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, const uint16_t* htab, int s,
+                        float* C, int64_t ldc, int* err, cudaStream_t st) {
     constexpr int T = 1 << (L - 5);
-    const size_t smem = sizeof(float) * ((size_t)1 << L) + sizeof(int) * (size_t)s;
-    auto k = srht_bulk_kernel<L>;
+    const size_t smem = sizeof(float) * ((size_t)1 << L) +
+                        (HASH ? sizeof(uint16_t) * ((size_t)1 << L) + sizeof(float) * T : sizeof(int) * (size_t)s);
+    auto k = srht_bulk_kernel<L, HASH>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(A.rows, (int64_t)std::max(per_sm, 1) * sm_count()));
-    k<<<(unsigned)grid, T, smem, st>>>(static_cast<const float*>(A.ptr), A.ld, A.rows, A.cols, dbits, cols, s, C,
-                                       ldc, err);
+    k<<<(unsigned)grid, T, smem, st>>>(static_cast<const float*>(A.ptr), A.ld, A.rows, A.cols, dbits, cols, htab,
+                                       s, C, ldc, err);
     return cudaGetLastError();
 }
 
 template <int LOGN, bool TRANS, typename TA>
-cudaError_t launch_reg(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
-                       int64_t ldc, cudaStream_t st) {
+cudaError_t launch_reg(const MatView& A, const uint32_t* dbits, const int* cols, const uint16_t* htab, int hnp,
+                       int s, float* C, int64_t ldc, cudaStream_t st) {
     constexpr int NP = 1 << LOGN;
     constexpr int T = 1 << (LOGN / 2);
     constexpr int G = 128 / T;
@@ -458,31 +545,40 @@ cudaError_t launch_reg(const MatView& A, const uint32_t* dbits, const int* cols,
     const int64_t groups = (A.rows + G - 1) / G;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)std::max(per_sm, 1) * sm_count()));
     k<<<(unsigned)grid, 128, smem, st>>>(static_cast<const TA*>(A.ptr), A.ld, A.rows, A.cols, dbits,
-                                         cols, s, C, ldc);
+                                         cols, htab, hnp, s, C, ldc);
     return cudaGetLastError();
 }
 
+// SRHT (cols, htab null) or HRTT (htab, cols null).
 template <bool TRANS, typename TA>
-cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* cols, int s, float* C,
-                          int64_t ldc, int* err, cudaStream_t st) {
+cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* cols, const uint16_t* htab, int s,
+                          float* C, int64_t ldc, int* err, cudaStream_t st) {
     const int need = pow2_bits(A.cols);
+    const int hnp = 1 << need;
     if constexpr (!TRANS && sizeof(TA) == 4) {
         if (err && need >= 12 && need <= 14 && (A.ld % 4) == 0 && (A.cols % 4) == 0 &&
             (reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0) {
-            if (need == 12) return launch_bulk<12>(A, dbits, cols, s, C, ldc, err, st);
-            if (need == 13) return launch_bulk<13>(A, dbits, cols, s, C, ldc, err, st);
-            return launch_bulk<14>(A, dbits, cols, s, C, ldc, err, st);
+            if (!htab) {
+                if (need == 12) return launch_bulk<12, false>(A, dbits, cols, nullptr, s, C, ldc, err, st);
+                if (need == 13) return launch_bulk<13, false>(A, dbits, cols, nullptr, s, C, ldc, err, st);
+                return launch_bulk<14, false>(A, dbits, cols, nullptr, s, C, ldc, err, st);
+            }
+            if ((s & (s - 1)) == 0) {
+                if (need == 12) return launch_bulk<12, true>(A, dbits, nullptr, htab, s, C, ldc, err, st);
+                if (need == 13) return launch_bulk<13, true>(A, dbits, nullptr, htab, s, C, ldc, err, st);
+                return launch_bulk<14, true>(A, dbits, nullptr, htab, s, C, ldc, err, st);
+            }
         }
-        if (need >= 12 && need <= 14 && (A.ld % 4) == 0 && (reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0) {
+        if (!htab && need >= 12 && need <= 14 && (A.ld % 4) == 0 && (reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0) {
             if (need == 12) return launch_vec<12>(A, dbits, cols, s, C, ldc, st);
             if (need == 13) return launch_vec<13>(A, dbits, cols, s, C, ldc, st);
             return launch_vec<14>(A, dbits, cols, s, C, ldc, st);
         }
     }
-    if (need <= 8) return launch_reg<8, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
-    if (need <= 10) return launch_reg<10, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
-    if (need <= 12) return launch_reg<12, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
-    if (need <= 14) return launch_reg<14, TRANS, TA>(A, dbits, cols, s, C, ldc, st);
+    if (need <= 8) return launch_reg<8, TRANS, TA>(A, dbits, cols, htab, hnp, s, C, ldc, st);
+    if (need <= 10) return launch_reg<10, TRANS, TA>(A, dbits, cols, htab, hnp, s, C, ldc, st);
+    if (need <= 12) return launch_reg<12, TRANS, TA>(A, dbits, cols, htab, hnp, s, C, ldc, st);
+    if (need <= 14) return launch_reg<14, TRANS, TA>(A, dbits, cols, htab, hnp, s, C, ldc, st);
     if (need > 15) return cudaErrorNotSupported;
     const size_t smem = sizeof(float) << need;
     auto k = srht_smem_kernel<TRANS, TA>;
@@ -490,7 +586,7 @@ cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* co
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(A.rows, (int64_t)sm_count() * 1);
     k<<<(unsigned)grid, 1024, smem, st>>>(static_cast<const TA*>(A.ptr), A.ld, A.rows, A.cols, need,
-                                          dbits, cols, s, C, ldc);
+                                          dbits, cols, htab, s, C, ldc);
     return cudaGetLastError();
 }
 
@@ -500,10 +596,21 @@ cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int
                               float* C, int64_t ldc, cudaStream_t st, int* err) {
     if (s <= 0 || A.rows <= 0) return cudaSuccess;
     if (A.dtype == RE_F32)
-        return A.trans ? launch_srht_t<true, float>(A, dbits, cols, s, C, ldc, err, st)
-                       : launch_srht_t<false, float>(A, dbits, cols, s, C, ldc, err, st);
-    return A.trans ? launch_srht_t<true, double>(A, dbits, cols, s, C, ldc, err, st)
-                   : launch_srht_t<false, double>(A, dbits, cols, s, C, ldc, err, st);
+        return A.trans ? launch_srht_t<true, float>(A, dbits, cols, nullptr, s, C, ldc, err, st)
+                       : launch_srht_t<false, float>(A, dbits, cols, nullptr, s, C, ldc, err, st);
+    return A.trans ? launch_srht_t<true, double>(A, dbits, cols, nullptr, s, C, ldc, err, st)
+                   : launch_srht_t<false, double>(A, dbits, cols, nullptr, s, C, ldc, err, st);
+}
+
+cudaError_t launch_right_hrtt(const MatView& A, const uint32_t* dbits, const uint16_t* tbl, int s,
+                              float* C, int64_t ldc, cudaStream_t st, int* err) {
+    if (s <= 0 || A.rows <= 0) return cudaSuccess;
+    if (!tbl || s > (int64_t(1) << pow2_bits(A.cols))) return cudaErrorInvalidValue;
+    if (A.dtype == RE_F32)
+        return A.trans ? launch_srht_t<true, float>(A, dbits, nullptr, tbl, s, C, ldc, err, st)
+                       : launch_srht_t<false, float>(A, dbits, nullptr, tbl, s, C, ldc, err, st);
+    return A.trans ? launch_srht_t<true, double>(A, dbits, nullptr, tbl, s, C, ldc, err, st)
+                   : launch_srht_t<false, double>(A, dbits, nullptr, tbl, s, C, ldc, err, st);
 }
 
 }  // namespace re

@@ -233,7 +233,7 @@ def test_small_fp64_decade_spectrum(h):
     assert s[res.rank] < 10 * 1e-4 and s[res.rank - 1] > 0.1 * 1e-4
 
 
-@pytest.mark.parametrize("kind", [rk.RE_GAUSSIAN, rk.RE_SRHT])
+@pytest.mark.parametrize("kind", [rk.RE_GAUSSIAN, rk.RE_SRHT, rk.RE_HRTT])
 @pytest.mark.parametrize("m,n,rank", [(1500, 600, 37), (600, 1500, 37), (4096, 4096, 120),
                                       (333, 257, 5), (2000, 1000, 0)])
 def test_clear_gap_exact_rank(h, kind, m, n, rank):
@@ -316,3 +316,120 @@ def test_batched_kernel_blocks(h):
         n = min(res[i].n_sigma, len(orc.sigma))
         assert np.max(np.abs(sig[i, :n] - orc.sigma[:n])) <= SIGMA_TOL * orc.sigma[0]
         assert ranks_agree(res[i].rank, orc, SIGMA_TOL * orc.sigma[0])
+
+
+# ---------------------------------------------------------------------------
+# HRTT (Sec. 3.4): hashed randomized Hadamard right sketch
+@pytest.mark.parametrize("n,s", [(1000, 64), (37, 24), (4099, 40), (256, 256)])
+def test_hrtt_x_exact(h, n, s):
+    out = torch.empty(n, s, dtype=torch.float32, device="cuda")
+    rk.re_embedding_x(h, rk.RE_HRTT, 77, n, 0, s, out)
+    assert np.array_equal(out.cpu().numpy(), rng.hrtt_x(n, s, 77))
+
+
+def _hrtt_bounds(Ao, s):
+    """Per-entry bounds for the FP32 HRTT sketch of the rows a of Ao.
+
+    Rigorous: each transformed value is a sum of +-a_i over L = log2 n_pad
+    levels and a bucket adds b <= ceil(n_pad / s) of them, so in any order of
+    additions |err| <= (L + b) b u ||a||_1 (doubled).  Discriminating: an
+    output is typically sqrt(b) ||a||_2 in size and one wrong or missing term
+    moves it by about ||a||_2, while rounding moves it by about
+    u sqrt(L + b) sqrt(b) ||a||_2; 1e-3 sqrt(b) ||a||_2 separates the two."""
+    L = rng.next_pow2_bits(Ao.shape[1])
+    b = -(-(1 << L) // s)
+    l1 = np.abs(Ao).sum(axis=1)[:, None]
+    l2 = np.sqrt((Ao * Ao).sum(axis=1))[:, None]
+    return 2.0 * (L + b) * b * U32 * l1 + 1e-30, 1e-3 * np.sqrt(b) * l2 + 1e-30
+
+
+@pytest.mark.parametrize("m,n,dtype,widths", [
+    (1000, 777, torch.float32, (16, 24, 64)),       # 2^10 register transform, sums per output
+    (300, 1100, torch.float32, (16,)),              # m < n: A^T is sketched
+    (513, 129, torch.float64, (8, 24)),             # FP64 input (read as FP32)
+    (3001, 2500, torch.float32, (16, 64, 256)),     # 2^12 bulk rows: s < 32, 32 <= s < T, s > T
+    (5003, 4100, torch.float32, (24, 128)),         # 2^13: width not a power of two, then bulk
+    (9100, 9000, torch.float32, (16, 512)),         # 2^14 bulk rows, s = T
+    (2000, 4097, torch.float32, (16,)),             # row pitch not a multiple of 4
+])
+def test_hrtt_right_sketch_parity(h, m, n, dtype, widths):
+    gen = np.random.default_rng(m * 11 + n)
+    A = gen.standard_normal((m, n))
+    Ad = dev(A, dtype)
+    Ao, _ = alg.orient(Ad.double().cpu().numpy())
+    Ao = Ao.astype(np.float32).astype(np.float64)        # the values the kernels add
+    rows = Ao.shape[0]
+    for s in widths:
+        AX = torch.zeros(rows, s, dtype=torch.float32, device="cuda")
+        rk.re_sketch_apply(h, Ad, 0, s, rk.RE_HRTT, 4242, AX)
+        ref = alg.right_sketch(Ao, s, rk.RE_HRTT, 4242)
+        err = np.abs(AX.double().cpu().numpy() - ref)
+        rigorous, tight = _hrtt_bounds(Ao, s)
+        assert np.all(err <= rigorous) and np.all(err <= tight), (s, float(np.max(err / tight)))
+
+
+def test_hrtt_shared_memory_transform(h):
+    """2^15-point rows (16400 columns, one row per CTA): A is zero outside 48
+    columns (the last one among them), so the oracle needs only those rows of X."""
+    m = n = 16400
+    gen = np.random.default_rng(5)
+    nz = np.sort(np.append(gen.choice(n - 1, 47, replace=False), n - 1))
+    vals = gen.standard_normal((m, nz.size)).astype(np.float32)
+    Ad = torch.zeros(m, n, dtype=torch.float32, device="cuda")
+    Ad[:, torch.from_numpy(nz).cuda()] = torch.from_numpy(vals).cuda()
+    Asub = vals.astype(np.float64)
+    for s in (16, 40):
+        AX = torch.zeros(m, s, dtype=torch.float32, device="cuda")
+        rk.re_sketch_apply(h, Ad, 0, s, rk.RE_HRTT, 99, AX)
+        ref = Asub @ rng.hrtt_x(n, s, 99, rows=nz)
+        err = np.abs(AX.double().cpu().numpy() - ref)
+        b = -(-(1 << 15) // s)
+        l1 = np.abs(Asub).sum(axis=1)[:, None]
+        l2 = np.sqrt((Asub * Asub).sum(axis=1))[:, None]
+        assert np.all(err <= 2.0 * (15 + b) * b * U32 * l1) and np.all(err <= 1e-3 * np.sqrt(b) * l2)
+    del Ad
+    torch.cuda.empty_cache()
+
+
+def test_hrtt_core_parity(h):
+    # the whole width-s sketch and its 2s x s core (Gaussian Y) in one call
+    m, n, s = 2000, 700, 32
+    A = np.random.default_rng(8).standard_normal((m, n)).astype(np.float32)
+    AX = torch.zeros(m, s, dtype=torch.float32, device="cuda")
+    core = torch.zeros(2 * s, s, dtype=torch.float64, device="cuda")
+    rk.re_sketch_apply(h, dev(A), 0, s, rk.RE_HRTT, 31, AX, core)
+    A64 = A.astype(np.float64)
+    ref = alg.core(A64, s, rk.RE_HRTT, 31)
+    Y = alg.embeddings(rk.RE_HRTT, n, m, s, 31)[1]
+    b = -(-1024 // s)
+    # |AX entries| error as above, then FP32 accumulation of the left sketch
+    ax_abs = (np.abs(A64).sum(axis=1) * b)[:, None] * np.ones((1, s))
+    bound = 4.0 * (m / 32 + 10 + b + 64) * U32 * (np.abs(Y) @ ax_abs)
+    assert np.all(np.abs(core.cpu().numpy() - ref) <= bound)
+
+
+def test_hrtt_coherent_diagonal(h):
+    """Sec. 3.4: on a diagonal matrix the hashed transform keeps the exact rank
+    (and the oracle's sigma), while the sampled one falls short."""
+    n = 2048
+    A = np.diag(np.where(np.arange(n) < 150, 1.0, 1e-8))
+    res, orc = check_estimate(h, A, 1e-4, rk.RE_HRTT, 5)
+    assert res.rank == 150 and res.final_s == 256 and res.passes == 6 and res.gap_index == 150
+    res_s, _ = rk.re_rank_estimate(h, dev(A), 1e-4, rk.RE_SRHT, 5)
+    assert res_s.rank < 150
+
+
+def test_hrtt_errors(h):
+    A = torch.randn(300, 100, device="cuda")
+    AX = torch.zeros(300, 64, device="cuda")
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_sketch_apply(h, A, 8, 8, rk.RE_HRTT, 1, AX)          # not appendable
+    assert e.value.code == rk.RE_ERR_ARG
+    AX = torch.zeros(300, 256, device="cuda")
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_sketch_apply(h, A, 0, 256, rk.RE_HRTT, 1, AX)        # s > n_pad = 128
+    assert e.value.code == rk.RE_ERR_ARG
+    # full column rank 100: at s = 128 (r1 = 116) the core has rank 100 and the
+    # read-off finds sigma_101 at the rounding level
+    res, _ = rk.re_rank_estimate(h, A, 1e-3, rk.RE_HRTT, 1)
+    assert res.rank == 100 and res.flags & rk.RE_CONVERGED and res.final_s == 128
