@@ -317,8 +317,9 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_vec_kernel(c
 }
 
 // HRTT outputs of one row held in buf (phys_sw layout, NP = 32 T coordinates)
-// for s a power of two: thread j adds the 32 table entries q = u T + j in the
-// order of u.  For s >= T these land in its own buckets (u mod s/T) T + j, in
+// for s a power of two; htab holds the swizzled offset phys_sw(c) of each
+// table entry with the sign in bit 15.  Thread j adds the 32 entries
+// q = u T + j in the order of u.  For s >= T these land in its own buckets (u mod s/T) T + j, in
 // bucket order; for s < T all in bucket j mod s, whose T/s partial sums (T/32
 // after a shuffle reduction when s < 32) are then added through red.
 template <int T>
@@ -326,8 +327,8 @@ __device__ __forceinline__ void hashed_outputs_pow2(const float* buf, const uint
                                                     float* red, float* __restrict__ out) {
     auto term = [&](int u) {
         const uint32_t e = htab[u * T + j];
-        const float v = buf[phys_sw((int)(e & 0x7fffu))];
-        return (e & 0x8000u) ? -v : v;
+        const float v = buf[e & 0x7fffu];
+        return __uint_as_float(__float_as_uint(v) ^ ((e << 16) & 0x80000000u));
     };
     if (s >= T) {                                        // uniform across the CTA: no barrier below
         const int V = s / T;
@@ -389,7 +390,10 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_bulk_kernel(
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if constexpr (HASH) {
-        for (int q = j; q < NP; q += T) htab[q] = htab_g[q];
+        for (int q = j; q < NP; q += T) {
+            const uint32_t e = htab_g[q];
+            htab[q] = (uint16_t)(phys_sw((int)(e & 0x7fffu)) | (e & 0x8000u));
+        }
     } else {
         for (int k = j; k < s; k += T) scol[k] = cols[k];
     }
