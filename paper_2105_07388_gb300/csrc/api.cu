@@ -275,7 +275,7 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
         if (int r = ensure(h->status, 64)) return r;
         cudaEvent_t a = stage_begin(h, st);
         if (e == cudaSuccess)
-            e = re::launch_right_hrtt(P.A, static_cast<const uint32_t*>(h->dx.p), static_cast<const uint16_t*>(h->ht.p),
+            e = re::launch_right_hrtt(P.A, static_cast<const uint32_t*>(h->dx.p), static_cast<uint16_t*>(h->ht.p),
                                       cnt, AX + c0, ld_ax, st, static_cast<int*>(h->status.p) + 1);
         if (e != cudaSuccess) return cuda_fail(e, "right sketch (HRTT)");
         stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 0),

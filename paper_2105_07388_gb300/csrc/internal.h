@@ -120,8 +120,10 @@ cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int
                               float* C, int64_t ldc, cudaStream_t st, int* err = nullptr);
 // C[:, 0:s] = A_oriented D H C^T (HRTT, unscaled): output k sums the transform
 // coordinates of bucket k with their CountSketch signs, read from the table of
-// launch_hrtt_table (pow2_bits(cols) bits).  Requires s <= 2^bits.
-cudaError_t launch_right_hrtt(const MatView& A, const uint32_t* dbits, const uint16_t* tbl, int s,
+// launch_hrtt_table (pow2_bits(cols) bits).  Requires s <= 2^bits.  The table
+// is reordered in place for the bulk kernel (entries stay in their buckets;
+// only the order of each bucket's sum changes).
+cudaError_t launch_right_hrtt(const MatView& A, const uint32_t* dbits, uint16_t* tbl, int s,
                               float* C, int64_t ldc, cudaStream_t st, int* err = nullptr);
 
 // ---- right sketch, BF16x3 tensor cores (sketch_tc.cu) ------------------------------

@@ -358,6 +358,60 @@ __device__ __forceinline__ void hashed_outputs_pow2(const float* buf, const uint
     }
 }
 
+// Orders the table for hashed_outputs_pow2 (in place).  Thread j of the bulk
+// kernel reads the entries at q = u T + j in the order of u; any order of a
+// thread's entries that keeps u mod V (V = max(1, s/T)) keeps every entry in
+// its bucket.  Step by step, the lanes of a warp take, lowest lane first, an
+// unused entry whose shared-memory bank (of its swizzled offset) no lower lane
+// took at this step; a lane left without such an entry takes its first unused
+// one.  Deterministic; one warp per 32 threads of the bulk kernel's CTA.
+template <int L>
+__global__ void __launch_bounds__(32) hrtt_order_kernel(uint16_t* __restrict__ tbl, int s) {
+    constexpr int T = 1 << (L - 5);
+    const int lane = threadIdx.x;
+    const int j = blockIdx.x * 32 + lane;
+    const int V = s >= T ? s / T : 1;                 // 1 .. 32, a power of two
+    uint32_t e[32], bank[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+        e[u] = tbl[u * T + j];
+        bank[u] = (uint32_t)phys_sw((int)(e[u] & 0x7fffu)) & 31u;
+    }
+    uint32_t cls0 = 0;                                // entries u = 0 mod V
+    for (int u = 0; u < 32; u += V) cls0 |= 1u << u;
+    uint32_t rem = 0xffffffffu;
+    for (int uo = 0; uo < 32; ++uo) {
+        const uint32_t cls = cls0 << (uo % V);
+        uint32_t taken = 0;
+        int pick = -1;
+        for (int round = 0; round < 32; ++round) {
+            int cand = -1;
+            if (pick < 0) {
+                const uint32_t avail = rem & cls;
+#pragma unroll
+                for (int i = 31; i >= 0; --i)
+                    if (((avail >> i) & 1u) && !((taken >> bank[i]) & 1u)) cand = i;
+            }
+            if (!__any_sync(0xffffffffu, cand >= 0)) break;
+            uint32_t b = 32u + (uint32_t)lane;            // distinct for lanes without a candidate
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (i == cand) b = bank[i];
+            const uint32_t grp = __match_any_sync(0xffffffffu, b);
+            const bool win = cand >= 0 && (__ffs(grp) - 1) == lane;
+            if (win) pick = cand;
+            taken |= __reduce_or_sync(0xffffffffu, win ? (1u << b) : 0u);
+        }
+        if (pick < 0) pick = __ffs(rem & cls) - 1;        // every bank left is taken: accept a conflict
+        uint32_t v = 0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i == pick) v = e[i];
+        tbl[uo * T + j] = (uint16_t)v;
+        rem &= ~(1u << pick);
+    }
+}
+
 // Bulk-copy form of srht_vec_kernel for rows of a multiple of 4 floats: each
 // row arrives in shared memory by one bulk copy (cp.async.bulk, completion on an
 // mbarrier) issued as soon as the previous row's gather is done; phase 1 then
@@ -477,7 +531,7 @@ __global__ void __launch_bounds__(1 << (L - 5), 1 << (15 - L)) srht_bulk_kernel(
 }
 
 template <int L, bool HASH>
-cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, const uint16_t* htab, int s,
+cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, uint16_t* htab, int s,
                         float* C, int64_t ldc, int* err, cudaStream_t st);
 
 template <int L>
@@ -514,9 +568,14 @@ cudaError_t launch_vec(const MatView& A, const uint32_t* dbits, const int* cols,
 }
 
 template <int L, bool HASH>
-cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, const uint16_t* htab, int s,
+cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols, uint16_t* htab, int s,
                         float* C, int64_t ldc, int* err, cudaStream_t st) {
     constexpr int T = 1 << (L - 5);
+    if constexpr (HASH) {
+        hrtt_order_kernel<L><<<T / 32, 32, 0, st>>>(htab, s);
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
     const size_t smem = sizeof(float) * ((size_t)1 << L) +
                         (HASH ? sizeof(uint16_t) * ((size_t)1 << L) + sizeof(float) * T : sizeof(int) * (size_t)s);
     auto k = srht_bulk_kernel<L, HASH>;
@@ -555,7 +614,7 @@ cudaError_t launch_reg(const MatView& A, const uint32_t* dbits, const int* cols,
 
 // SRHT (cols, htab null) or HRTT (htab, cols null).
 template <bool TRANS, typename TA>
-cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* cols, const uint16_t* htab, int s,
+cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* cols, uint16_t* htab, int s,
                           float* C, int64_t ldc, int* err, cudaStream_t st) {
     const int need = pow2_bits(A.cols);
     const int hnp = 1 << need;
@@ -606,7 +665,7 @@ cudaError_t launch_right_srht(const MatView& A, const uint32_t* dbits, const int
                    : launch_srht_t<false, double>(A, dbits, cols, nullptr, s, C, ldc, err, st);
 }
 
-cudaError_t launch_right_hrtt(const MatView& A, const uint32_t* dbits, const uint16_t* tbl, int s,
+cudaError_t launch_right_hrtt(const MatView& A, const uint32_t* dbits, uint16_t* tbl, int s,
                               float* C, int64_t ldc, cudaStream_t st, int* err) {
     if (s <= 0 || A.rows <= 0) return cudaSuccess;
     if (!tbl || s > (int64_t(1) << pow2_bits(A.cols))) return cudaErrorInvalidValue;
