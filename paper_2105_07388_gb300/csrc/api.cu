@@ -50,7 +50,7 @@ struct re_handle_ {
     re_stats stats{};
     std::vector<PendingTiming> pending;
     std::vector<cudaEvent_t> event_pool;
-    DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status, ht;
+    DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status, ht, fz;
     re::BatchedState* batched = nullptr;
     // sketch-size proposal network: parameters, Adam moments, gradient, scratch
     DevBuf mlp_P, mlp_M, mlp_V, mlp_G, mlp_X, mlp_y, mlp_logits, mlp_keep, mlp_cls, mlp_feat, mlp_loss;
@@ -306,39 +306,51 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
 
 // Left-sketch blocks after AX columns [c0, c1) were added: rows [2 c0, 2 c1) x cols
 // [0, c0) and rows [0, 2 c1) x cols [c0, c1) of core (FP64 row-major, ld_core).
+// With the SRTT Y the columns are transformed once into the handle's Z (H D AX,
+// m_pad x ld_ax) and the blocks sampled from it: within one estimate only the new
+// columns are transformed (transform_from = c0); a standalone sketch step
+// transforms from column 0 (the caller supplies the earlier AX columns).
 int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const float* AX,
-                int64_t ld_ax, double* core, int64_t ld_core, cudaStream_t st) {
+                int64_t ld_ax, double* core, int64_t ld_core, cudaStream_t st, int transform_from) {
     const int64_t M = P.A.rows;
+    if (int r = ensure(h->status, 64)) return r;
     if (P.ykind == RE_SRHT) {
         if (int r = ensure(h->dy, sizeof(uint32_t) * (size_t)(P.m_pad / 32 + 1))) return r;
         if (int r = ensure(h->py, sizeof(int) * (size_t)(2 * c1))) return r;
+        if (int r = ensure(h->fz, sizeof(float) * (size_t)P.m_pad * (size_t)ld_ax)) return r;
         cudaEvent_t g = stage_begin(h, st);
         cudaError_t e = re::launch_sign_bits(seed, re::kStreamDY, M, static_cast<uint32_t*>(h->dy.p), st);
         if (e == cudaSuccess)
             e = re::launch_perm(seed, re::kStreamPY, P.mbits, 0, 2 * c1, static_cast<int*>(h->py.p), st);
         if (e != cudaSuccess) return cuda_fail(e, "left embedding");
         stage_end(h, st, g, kStageOther);
-        h->stats.launches += 2;
+        float* Z = static_cast<float*>(h->fz.p);
+        const int* perm = static_cast<const int*>(h->py.p);
+        cudaEvent_t a = stage_begin(h, st);
+        e = re::launch_left_srtt_transform(AX, ld_ax, M, P.mbits, static_cast<const uint32_t*>(h->dy.p),
+                                           transform_from, c1, Z, ld_ax, st);
+        if (e == cudaSuccess && c0 > 0)
+            e = re::launch_left_srtt_sample(Z, ld_ax, perm, 2 * c0, 2 * (c1 - c0), 0, c0, core, ld_core, st);
+        if (e == cudaSuccess) e = re::launch_left_srtt_sample(Z, ld_ax, perm, 0, 2 * c1, c0, c1 - c0, core, ld_core, st);
+        if (e != cudaSuccess) return cuda_fail(e, "left sketch (SRTT)");
+        stage_end(h, st, a, kStageLeft);
+        h->stats.launches += 2 + (P.mbits + 9) / 10 + (c0 > 0 ? 2 : 1);
+        return RE_OK;
     }
     const size_t need = std::max({re::left_part_floats(M, 2 * (c1 - c0), c0),
                                   re::left_part_floats(M, 2 * c1, c1 - c0),
                                   re::left_tc_part_floats(M, 2 * (c1 - c0), c0),
                                   re::left_tc_part_floats(M, 2 * c1, c1 - c0)});
     if (int r = ensure(h->part, sizeof(float) * need)) return r;
-    if (int r = ensure(h->status, 64)) return r;
     int* tmo = static_cast<int*>(h->status.p) + 1;     // bounded-wait expiry flag of the tensor-core kernels
     cudaError_t e = cudaSuccess;
     cudaEvent_t a = stage_begin(h, st);
     if (c0 > 0)
-        e = re::launch_left(P.ykind, seed, AX, ld_ax, M, 2 * c0, 2 * (c1 - c0), 0, c0,
-                            static_cast<const uint32_t*>(h->dy.p), static_cast<const int*>(h->py.p),
-                            static_cast<float*>(h->part.p), h->part.cap / sizeof(float), core,
-                            ld_core, st, tmo);
+        e = re::launch_left(seed, AX, ld_ax, M, 2 * c0, 2 * (c1 - c0), 0, c0, static_cast<float*>(h->part.p),
+                            h->part.cap / sizeof(float), core, ld_core, st, tmo);
     if (e == cudaSuccess)
-        e = re::launch_left(P.ykind, seed, AX, ld_ax, M, 0, 2 * c1, c0, c1 - c0,
-                            static_cast<const uint32_t*>(h->dy.p), static_cast<const int*>(h->py.p),
-                            static_cast<float*>(h->part.p), h->part.cap / sizeof(float), core,
-                            ld_core, st, tmo);
+        e = re::launch_left(seed, AX, ld_ax, M, 0, 2 * c1, c0, c1 - c0, static_cast<float*>(h->part.p),
+                            h->part.cap / sizeof(float), core, ld_core, st, tmo);
     if (e != cudaSuccess) return cuda_fail(e, "left sketch");
     stage_end(h, st, a, kStageLeft);
     h->stats.launches += c0 > 0 ? 4 : 2;
@@ -435,7 +447,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
     }
     auto sketch_to = [&](int c0, int c1) -> int {
         if (int r = right_columns(h, P, seed, c0, c1 - c0, AX, smax, st)) return r;
-        if (int r = left_blocks(h, P, seed, c0, c1, AX, smax, core, smax, st)) return r;
+        if (int r = left_blocks(h, P, seed, c0, c1, AX, smax, core, smax, st, c0)) return r;
         h->stats.passes += 1;
         return RE_OK;
     };
@@ -460,7 +472,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
             h->stats.passes += 1;
             passes = 2;
             for (int w = 32; w <= target && !done; w *= 2) {
-                if (int r = left_blocks(h, P, seed, w / 2, w, AX, smax, core, smax, st)) return r;
+                if (int r = left_blocks(h, P, seed, w / 2, w, AX, smax, core, smax, st, w / 2)) return r;
                 if (int r = check_width(h, P, w, smax, eps, &ro, &r1, st, 2 * w <= smax)) return r;
                 s = w;
                 done = ro.rank >= 0 || r1 >= P.A.cols;
@@ -568,7 +580,7 @@ int re_destroy(re_handle h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&h->x, &h->xt, &h->ax, &h->part, &h->core, &h->sigma, &h->sigma_scaled,
-                      &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status, &h->ht,
+                      &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status, &h->ht, &h->fz,
                       &h->mlp_P, &h->mlp_M, &h->mlp_V, &h->mlp_G, &h->mlp_X, &h->mlp_y,
                       &h->mlp_logits, &h->mlp_keep, &h->mlp_cls, &h->mlp_feat, &h->mlp_loss};
     for (DevBuf* b : bufs) release(*b);
@@ -663,7 +675,7 @@ int re_sketch_apply(re_handle h, const void* A, int dtype, int64_t m, int64_t n,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (int r = right_columns(h, P, seed, col0, s, AX, ld_ax, st)) return r;
     if (core) {
-        if (int r = left_blocks(h, P, seed, col0, col0 + s, AX, ld_ax, core, ld_core, st)) return r;
+        if (int r = left_blocks(h, P, seed, col0, col0 + s, AX, ld_ax, core, ld_core, st, 0)) return r;
     }
     return RE_OK;
 }
@@ -1002,7 +1014,7 @@ int re_mlp_features(re_handle h, const void* A, int dtype, int64_t m, int64_t n,
     if (e0 != cudaSuccess) return cuda_fail(e0, "clear status");
     float* AX = static_cast<float*>(h->ax.p);
     if (int r = right_columns(h, P, seed, 0, 16, AX, 16, st)) return r;
-    if (int r = left_blocks(h, P, seed, 0, 16, AX, 16, static_cast<double*>(h->core.p), 16, st)) return r;
+    if (int r = left_blocks(h, P, seed, 0, 16, AX, 16, static_cast<double*>(h->core.p), 16, st, 0)) return r;
     re::DevReadoff ro;
     int r1 = 0;
     if (int r = check_width(h, P, 16, 16, eps, &ro, &r1, st)) return r;

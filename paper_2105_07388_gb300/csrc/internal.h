@@ -71,17 +71,23 @@ cudaError_t launch_right_simt(const MatView& A, const float* X, int64_t ldx, int
 
 // ---- left sketch (sketch_simt.cu) ---------------------------------------------
 // core[row0+r][col0+c] (FP64, ld_core) = sum_i Y[row0+r][i] * AX[i][col0+c] for
-// r < R, c < S, i < M.  Y Gaussian (kind RE_GAUSSIAN) or SRTT from dbits/perm
-// (perm holds pi_Y(q) for q in [0, row0+R)).  `part` is FP32 scratch of
-// part_cap floats.
+// r < R, c < S, i < M, Y Gaussian.  `part` is FP32 scratch of part_cap floats.
 // With a non-null err_flag (a device word that a bounded wait sets on expiry),
-// Gaussian blocks of aligned AX run on the tensor cores (left_tc.cu); otherwise,
-// and when `part` is too small for that kernel's split count, on CUDA cores.
-cudaError_t launch_left(int kind, uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0,
-                        int R, int col0, int S, const uint32_t* dbits, const int* perm,
-                        float* part, size_t part_cap, double* core, int64_t ld_core,
-                        cudaStream_t st, int* err_flag = nullptr);
+// blocks of aligned AX run on the tensor cores (left_tc.cu); otherwise, and when
+// `part` is too small for that kernel's split count, on CUDA cores.
+cudaError_t launch_left(uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0, int S,
+                        float* part, size_t part_cap, double* core, int64_t ld_core, cudaStream_t st,
+                        int* err_flag = nullptr);
 size_t left_part_floats(int64_t M, int R, int S);
+
+// ---- left sketch with the SRTT Y by fast transforms (left_fwht.cu) ------------
+// Z[i][c] = (H D AX)[i][c] for c in [c0, c1) and i < 2^mbits (Z row-major, ldz >= c1,
+// 2^mbits rows; AX rows >= M are zero; dbits the DY signs).
+cudaError_t launch_left_srtt_transform(const float* AX, int64_t ldax, int64_t M, int mbits, const uint32_t* dbits,
+                                       int c0, int c1, float* Z, int64_t ldz, cudaStream_t st);
+// core[row0+r][col0+c] = Z[perm[row0+r]][col0+c] for r < R, c < S (perm = pi_Y).
+cudaError_t launch_left_srtt_sample(const float* Z, int64_t ldz, const int* perm, int row0, int R, int col0, int S,
+                                    double* core, int64_t ld_core, cudaStream_t st);
 
 // ---- left sketch on the tensor cores (left_tc.cu) -----------------------------
 bool left_tc_supported(const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0, int S);

@@ -91,11 +91,9 @@ extern "C" int re_sketch_apply_noalloc(const void* A, int dtype, int64_t m, int6
     e = launch_gauss_x(seed, V.cols, col0, s, X, s, st);
     if (e == cudaSuccess) e = launch_right_simt(V, X, s, s, AX + col0, ld_ax, st);
     if (e == cudaSuccess && core && col0 > 0)
-        e = launch_left(RE_GAUSSIAN, seed, AX, ld_ax, V.rows, 2 * col0, 2 * s, 0, col0, nullptr, nullptr,
-                        part, part_floats, core, ld_core, st);
+        e = launch_left(seed, AX, ld_ax, V.rows, 2 * col0, 2 * s, 0, col0, part, part_floats, core, ld_core, st);
     if (e == cudaSuccess && core)
-        e = launch_left(RE_GAUSSIAN, seed, AX, ld_ax, V.rows, 0, 2 * c1, col0, s, nullptr, nullptr, part,
-                        part_floats, core, ld_core, st);
+        e = launch_left(seed, AX, ld_ax, V.rows, 0, 2 * c1, col0, s, part, part_floats, core, ld_core, st);
     if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, cudaGetErrorString(e));
     return RE_OK;
 }

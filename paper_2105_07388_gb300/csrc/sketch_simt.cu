@@ -310,16 +310,15 @@ cudaError_t dispatch_right(const MatView& A, const float* X, int64_t ldx, int s,
 }
 
 // ---------------------------------------------------------------------------
-// Left sketch: part[split][r][c] = sum over the split's rows i of Y[row0+r][i] AX[i][col0+c].
+// Left sketch (Gaussian Y): part[split][r][c] = sum over the split's rows i of
+// Y[row0+r][i] AX[i][col0+c].
 constexpr int kLR = 64;     // rows of Y per tile
 constexpr int kLK = 32;     // i per k step
 
-template <int LC, int KIND>
+template <int LC>
 __global__ void __launch_bounds__(256) left_kernel(uint64_t seed, const float* __restrict__ AX,
                                                    int64_t ldax, int64_t M, int row0, int R,
                                                    int col0, int S, int64_t chunk,
-                                                   const uint32_t* __restrict__ dbits,
-                                                   const int* __restrict__ perm,
                                                    float* __restrict__ part) {
     constexpr int TC = LC / 16;           // columns per thread
     __shared__ __align__(16) float Ys[kLK][kLR];
@@ -337,45 +336,17 @@ __global__ void __launch_bounds__(256) left_kernel(uint64_t seed, const float* _
 #pragma unroll
         for (int b = 0; b < TC; ++b) acc[a][b] = 0.0f;
 
-    int my_perm[4];
-    if (KIND == RE_SRHT) {
-        // each thread generates 8 entries per k step: rows 4*(tid&15)+e? use a fixed map below
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int q = qbase + (tid & 15) * 4 + e;
-            my_perm[e] = (q - row0 < R) ? perm[q] : 0;
-        }
-    }
-
     for (int64_t i0 = i_begin; i0 < i_end; i0 += kLK) {
         // ---- Y tile: Ys[k][r] = Y[qbase + r][i0 + k]
-        if (KIND == RE_GAUSSIAN) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = tid & 31;
-                const int g = (tid >> 5) + 8 * h;        // 16 groups of 4 rows
-                const int64_t i = i0 + k;
-                float z[4] = {0.f, 0.f, 0.f, 0.f};
-                if (i < i_end && qbase + 4 * g - row0 < R)
-                    normals4((uint32_t)i, (uint32_t)((qbase >> 2) + g), kStreamGY, seed, z);
-                *reinterpret_cast<float4*>(&Ys[k][4 * g]) = make_float4(z[0], z[1], z[2], z[3]);
-            }
-        } else {
-            // thread: rows 4*(tid&15) .. +3, k = (tid >> 4) and (tid >> 4) + 16
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = (tid >> 4) + 16 * h;
-                const int64_t i = i0 + k;
-                float y[4];
-                const uint32_t di = (i < i_end) ? ((dbits[i >> 5] >> (i & 31)) & 1u) : 0u;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int q = qbase + (tid & 15) * 4 + e;
-                    const uint32_t par = (__popcll((unsigned long long)(i & (int64_t)my_perm[e])) & 1) ^ di;
-                    y[e] = (i < i_end && q - row0 < R) ? (par ? -1.0f : 1.0f) : 0.0f;
-                }
-                *reinterpret_cast<float4*>(&Ys[k][(tid & 15) * 4]) = make_float4(y[0], y[1], y[2], y[3]);
-            }
+        for (int h = 0; h < 2; ++h) {
+            const int k = tid & 31;
+            const int g = (tid >> 5) + 8 * h;            // 16 groups of 4 rows
+            const int64_t i = i0 + k;
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+            if (i < i_end && qbase + 4 * g - row0 < R)
+                normals4((uint32_t)i, (uint32_t)((qbase >> 2) + g), kStreamGY, seed, z);
+            *reinterpret_cast<float4*>(&Ys[k][4 * g]) = make_float4(z[0], z[1], z[2], z[3]);
         }
         // ---- AX tile: Xs[k][c] = AX[i0 + k][col0 + ct*LC + c]
         {
@@ -498,12 +469,11 @@ size_t left_part_floats(int64_t M, int R, int S) {
     return (size_t)splits * R * S;
 }
 
-cudaError_t launch_left(int kind, uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0,
-                        int R, int col0, int S, const uint32_t* dbits, const int* perm,
-                        float* part, size_t part_cap, double* core, int64_t ld_core,
-                        cudaStream_t st, int* err_flag) {
+cudaError_t launch_left(uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0, int S,
+                        float* part, size_t part_cap, double* core, int64_t ld_core, cudaStream_t st,
+                        int* err_flag) {
     if (R <= 0 || S <= 0) return cudaSuccess;
-    if (kind == RE_GAUSSIAN && err_flag && left_tc_supported(AX, ldax, M, row0, R, col0, S) &&
+    if (err_flag && left_tc_supported(AX, ldax, M, row0, R, col0, S) &&
         left_tc_part_floats(M, R, S) <= part_cap) {
         int tsplits = 0;
         cudaError_t e = launch_left_tc_partials(seed, AX, ldax, M, row0, R, col0, S, part, part_cap, err_flag,
@@ -520,17 +490,10 @@ cudaError_t launch_left(int kind, uint64_t seed, const float* AX, int64_t ldax, 
     const bool wide = S >= 128;
     dim3 grid((unsigned)((S + (wide ? 127 : 63)) / (wide ? 128 : 64)), (unsigned)((R + kLR - 1) / kLR),
               (unsigned)splits);
-    if (kind == RE_GAUSSIAN) {
-        if (wide)
-            left_kernel<128, RE_GAUSSIAN><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, dbits, perm, part);
-        else
-            left_kernel<64, RE_GAUSSIAN><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, dbits, perm, part);
-    } else {
-        if (wide)
-            left_kernel<128, RE_SRHT><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, dbits, perm, part);
-        else
-            left_kernel<64, RE_SRHT><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, dbits, perm, part);
-    }
+    if (wide)
+        left_kernel<128><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, part);
+    else
+        left_kernel<64><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)R * S;

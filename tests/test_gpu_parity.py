@@ -157,6 +157,33 @@ def test_core_parity_with_appending(h, kind):
     assert np.all(np.abs(got - ref) <= bound)
 
 
+@pytest.mark.parametrize("m,n,steps", [
+    (1_100_000, 12, ((0, 8),)),             # 2^21 padded rows: three transform passes (10 + 10 + 1 bits)
+    (3001, 700, ((0, 16), (16, 16), (32, 32))),   # 2^12 rows (10 + 2 bits), appended columns and rows
+])
+def test_srtt_left_transform_parity(h, m, n, steps):
+    """The SRTT left sketch by fast transforms of the columns of D A X, sampled
+    at pi_Y(q): the whole core against the oracle's dense S H D (A X) after
+    each appending step."""
+    A = np.random.default_rng(m).standard_normal((m, n)).astype(np.float32)
+    Ad = dev(A)
+    c1 = steps[-1][0] + steps[-1][1]
+    AX = torch.zeros(m, c1, dtype=torch.float32, device="cuda")
+    core = torch.zeros(2 * c1, c1, dtype=torch.float64, device="cuda")
+    A64 = A.astype(np.float64)
+    for col0, s in steps:
+        rk.re_sketch_apply(h, Ad, col0, s, rk.RE_SRHT, 77, AX, core)
+        w = col0 + s
+        AXg = AX[:, :w].double().cpu().numpy()               # the GPU's right sketch, as the left one saw it
+        Y = rng.srtt_y(2 * w, m, 77)
+        ref = Y @ AXg
+        # FP32 transform: log2(m_pad) levels of additions of +-AX entries
+        L = rng.next_pow2_bits(m)
+        bound = 2.0 * (L + 2) * U32 * (np.abs(Y) @ np.abs(AXg)) + 1e-30
+        got = core[:2 * w, :w].cpu().numpy()
+        assert np.all(np.abs(got - ref) <= bound), (col0, s, float(np.max(np.abs(got - ref) / bound)))
+
+
 @pytest.mark.parametrize("m,n,c0,c1", [
     (3001, 900, 0, 8),          # 16 x 8 core block
     (4099, 1200, 64, 136),      # appended: 144 x 64 and 272 x 72 blocks (two N tiles)
