@@ -117,6 +117,15 @@ typedef struct {
     int64_t m, n, ld;
 } re_block;
 
+/* One matrix-free kernel block: K[i][j] = 1 / |x_i - y_j| for 3-D points x (m x 3)
+ * and y (n x 3), device FP32, row-major (the structured blocks of Sec. 1 and
+ * Sec. 3.4's remark that structure in A can make A X cheaper than a dense read). */
+typedef struct {
+    const float* x;
+    const float* y;
+    int64_t m, n;
+} re_kblock;
+
 /* Per-handle counters for measurement: kernel launches made by the library and,
  * when timing is enabled, CUDA-event time of each stage on the caller's stream.
  * right_bytes / right_flops are the algorithmic bytes (A read once, X read,
@@ -241,6 +250,21 @@ int re_embedding_y(re_handle h, int kind, uint64_t seed, int64_t m, int row0, in
 int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int dtype,
                              double eps, int sketch_kind, uint64_t seed,
                              double* sigma_out, int sigma_cap, re_result* out, void* stream);
+
+/*
+ * As re_rank_estimate_batched with Gaussian embeddings, for matrix-free kernel
+ * blocks (HOST array of re_kblock): the tensor-core right sketch computes each
+ * entry 1 / |x_i - y_j| in FP32 (differences, fused multiply-adds, the hardware
+ * reciprocal square root, relative error below 2^-22) as it feeds the MMA, so
+ * no block is ever stored.  Blocks with m < n are sketched as
+ * K^T (the kernel is symmetric: the point sets swap roles), RE_TRANSPOSED set.
+ * Needs opts.precision = RE_PREC_BF16X3 and neither opts.learned nor a non-Gaussian
+ * opts.y_kind (else RE_ERR_UNSUPPORTED).  Coincident points give an infinite
+ * entry and RE_ERR_NONFINITE in that block's status.  Synchronises `stream`.
+ */
+int re_rank_estimate_kernel_blocks(re_handle h, const re_kblock* blocks, int count, double eps,
+                                   uint64_t seed, double* sigma_out, int sigma_cap, re_result* out,
+                                   void* stream);
 
 /*
  * Sketch-size proposal network (answers the question left open in the paper's

@@ -759,6 +759,21 @@ int re_embedding_y(re_handle h, int kind, uint64_t seed, int64_t m, int row0, in
     return RE_OK;
 }
 
+int re_rank_estimate_kernel_blocks(re_handle h, const re_kblock* blocks, int count, double eps, uint64_t seed,
+                                   double* sigma_out, int sigma_cap, re_result* out, void* stream) {
+    if (!h || (count > 0 && (!blocks || !out))) return fail(RE_ERR_ARG, "NULL argument");
+    if (count < 0) return fail(RE_ERR_ARG, "count < 0");
+    if (!(eps > 0.0 && eps < 1.0)) return fail(RE_ERR_ARG, "eps must lie in (0, 1)");
+    if (h->opts.precision != RE_PREC_BF16X3)
+        return fail(RE_ERR_UNSUPPORTED, "matrix-free kernel blocks need the tensor-core sketch (RE_PREC_BF16X3)");
+    if (h->opts.learned || (h->opts.y_kind >= 0 && h->opts.y_kind != RE_GAUSSIAN))
+        return fail(RE_ERR_UNSUPPORTED, "matrix-free kernel blocks take the plain ladder with Gaussian embeddings");
+    if (count == 0) return RE_OK;
+    cudaSetDevice(h->device);
+    return re::batched_estimate(&h->batched, h->opts, nullptr, blocks, count, eps, seed, sigma_out,
+                                sigma_out ? sigma_cap : 0, out, static_cast<cudaStream_t>(stream), &h->stats.launches);
+}
+
 int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int dtype, double eps,
                              int sketch_kind, uint64_t seed, double* sigma_out, int sigma_cap,
                              re_result* out, void* stream) {
@@ -770,7 +785,7 @@ int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int
     const int ykind = left_kind(h, sketch_kind);
     if (dtype == RE_F32 && sketch_kind == RE_GAUSSIAN && ykind == RE_GAUSSIAN && !h->opts.learned) {
         // one graph launch over all blocks (level-synchronous batched kernels)
-        return re::batched_estimate(&h->batched, h->opts, blocks, count, eps, seed, sigma_out,
+        return re::batched_estimate(&h->batched, h->opts, blocks, nullptr, count, eps, seed, sigma_out,
                                     sigma_out ? sigma_cap : 0, out, static_cast<cudaStream_t>(stream),
                                     &h->stats.launches);
     }

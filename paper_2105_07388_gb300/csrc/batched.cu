@@ -302,9 +302,9 @@ void batched_destroy(BatchedState* st) {
     delete st;
 }
 
-int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* blocks, int count, double eps,
-                     uint64_t seed, double* sigma_out, int sigma_cap, re_result* out, cudaStream_t ustream,
-                     int64_t* launches) {
+int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* blocks, const re_kblock* kblocks,
+                     int count, double eps, uint64_t seed, double* sigma_out, int sigma_cap, re_result* out,
+                     cudaStream_t ustream, int64_t* launches) {
     if (!*pst) {
         BatchedState* st = new BatchedState();
         if (cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -321,20 +321,39 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
     const int scap = std::min(o.s_max, 128);
     // ---- host descriptors
     std::vector<BatchDesc> hd(count);
-    std::vector<int> valid(count, 0);
+    std::vector<int> valid(count, 0), transposed(count, 0);
     std::vector<int64_t> pre128(count + 1, 0), pre64(count + 1, 0), colpre(count + 1, 0);
     int S_MAX = 0;
     for (int i = 0; i < count; ++i) {
-        const re_block& B = blocks[i];
         BatchDesc& D = hd[i];
         std::memset(&D, 0, sizeof(D));
-        const bool ok = B.ptr && B.m > 0 && B.n > 0 && B.ld >= B.n && B.m <= INT32_MAX && B.n <= INT32_MAX;
+        int64_t m = 0, n = 0;
+        bool ok;
+        if (kblocks) {
+            // matrix-free: orient by swapping the point sets (the kernel is symmetric)
+            const re_kblock& B = kblocks[i];
+            m = B.m;
+            n = B.n;
+            ok = B.x && B.y && m > 0 && n > 0 && m <= INT32_MAX && n <= INT32_MAX;
+            if (ok) {
+                D.px = m >= n ? B.x : B.y;
+                D.py = m >= n ? B.y : B.x;
+            }
+        } else {
+            const re_block& B = blocks[i];
+            m = B.m;
+            n = B.n;
+            ok = B.ptr && m > 0 && n > 0 && B.ld >= n && m <= INT32_MAX && n <= INT32_MAX;
+            if (ok) {
+                D.A = static_cast<const float*>(B.ptr);
+                D.ld = B.ld;
+                D.trans = m < n;
+            }
+        }
         if (ok) {
-            D.A = static_cast<const float*>(B.ptr);
-            D.ld = B.ld;
-            D.trans = B.m < B.n;
-            D.rows = std::max(B.m, B.n);
-            D.cols = std::min(B.m, B.n);
+            transposed[i] = m < n;
+            D.rows = std::max(m, n);
+            D.cols = std::min(m, n);
             int sm = s0;
             while (sm * 2 <= scap) sm *= 2;
             D.smax = sm;
@@ -572,7 +591,7 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
         int passes = 1;
         for (int t = 2 * w1; t <= s; t *= 2) ++passes;
         R.passes = passes;
-        R.flags = (conv ? RE_CONVERGED : RE_LOWER_BOUND_ONLY) | (hd[i].trans ? RE_TRANSPOSED : 0u);
+        R.flags = (conv ? RE_CONVERGED : RE_LOWER_BOUND_ONLY) | (transposed[i] ? RE_TRANSPOSED : 0u);
         if (!sg.empty()) {
             const int nc = std::min(r1, sigma_cap);
             for (int j = 0; j < nc; ++j) sigma_out[(size_t)i * sigma_cap + j] = sg[(size_t)i * S_MAX + j];

@@ -13,9 +13,18 @@
 //             along rows into a k-major tile for blocks stored transposed; zero
 //             fill past the block's edges; completion tracked by the stage's
 //             mbarrier (cp.async.mbarrier.arrive.noinc).
+//             For a matrix-free kernel block (no A, 3-D points) they instead
+//             stage the tile's 128 row points and the half chunk's 32 column
+//             points (negated, as three coordinate arrays; padding far away so
+//             that entries past the block come out as 1/sqrt(inf) = 0) and
+//             arrive on the stage's mbarrier directly.
 //   warp 16   X^T producer: 16-byte copies of the BF16 X^T chunk (N rows x 64 k).
 //   warps 0-7 converters (either tile layout), warp 17 MMA issuer, warps 8-11
-//             epilogue: as in the single-matrix kernel.
+//             epilogue: as in the single-matrix kernel.  For a matrix-free block a
+//             converter thread computes its row's 32 entries 1 / |x_r - y_k| in
+//             FP32 from the staged points (differences, squares and fused
+//             multiply-adds two entries at a time in packed FP32x2, the hardware
+//             reciprocal square root), so the block is never in HBM.
 // Every mbarrier wait is bounded in time (on expiry: error flag, drain, free
 // TMEM, return).
 #include <algorithm>
@@ -45,6 +54,47 @@ constexpr int kAStages = 8;
 constexpr int kStages = 2;
 constexpr uint32_t kAStageCol = 256;
 constexpr uint32_t kTmemCols = 512;
+// matrix-free stage layout: 128 row points (float4) then the negated column
+// coordinates x[32], y[32], z[32]; padding points sit at +-kFar
+constexpr uint32_t kColPts = 128 * 16;
+constexpr float kFar = 1e30f;
+
+__device__ __forceinline__ unsigned long long pk(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long add_x2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul_x2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fma_x2(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// entries 1/|x_r - y_k| for two columns: (nx, ny, nz) hold the negated column
+// coordinates of both, (x0, x1, x2) the row point in both halves
+__device__ __forceinline__ void kernel_pair(unsigned long long x0, unsigned long long x1, unsigned long long x2,
+                                            unsigned long long nx, unsigned long long ny, unsigned long long nz,
+                                            float& e0, float& e1) {
+    const unsigned long long dx = add_x2(x0, nx), dy = add_x2(x1, ny), dz = add_x2(x2, nz);
+    const unsigned long long d2 = fma_x2(dz, dz, fma_x2(dy, dy, mul_x2(dx, dx)));
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(d2));
+    // the hardware reciprocal square root (relative error below 2^-22): d2 is a
+    // positive normal number for distinct points, +inf for padding (entry 0) and
+    // 0 only for coincident points (entry +inf, reported as non-finite)
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(e0) : "f"(a));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(b));
+}
 
 __device__ __forceinline__ int find_block(const int64_t* prefix, int count, int64_t item) {
     int lo = 0, hi = count - 1;
@@ -82,8 +132,15 @@ __device__ __forceinline__ int copy_width(const float* A, int64_t ld) {
 // layout (row r at r*128, 16-byte chunk c at c ^ (r & 7)); this warp copies rows
 // rbase .. rbase+31; lanes cover (row, W-byte segment) pairs.  Rows past the block
 // are zero-filled in a second loop, so the main loop has no row test.
+// The block's pointer and sizes arrive by value: the copies' "memory" clobbers
+// would otherwise make every loop iteration reload them from the descriptor.
+struct BlockRef {
+    const float* A;
+    int64_t ld, rows, cols;
+};
+
 template <int W>
-__device__ __forceinline__ void load_rows(const BatchDesc& D, int64_t row0, int64_t k0, int rbase, uint32_t dst0) {
+__device__ __forceinline__ void load_rows(const BlockRef D, int64_t row0, int64_t k0, int rbase, uint32_t dst0) {
     constexpr int SEG = 128 / W;                  // segments per 128-byte row
     constexpr int RPI = 32 / SEG;                 // rows per warp instruction
     const int lane = threadIdx.x & 31;
@@ -113,7 +170,7 @@ __device__ __forceinline__ void load_rows(const BatchDesc& D, int64_t row0, int6
 // into a k-major tile: k row kk at kk*512, 128 oriented rows contiguous; this warp
 // copies k rows kbase .. kbase+7, lanes over W-byte segments of each.
 template <int W>
-__device__ __forceinline__ void load_cols(const BatchDesc& D, int64_t row0, int64_t k0, int kbase, uint32_t dst0) {
+__device__ __forceinline__ void load_cols(const BlockRef D, int64_t row0, int64_t k0, int kbase, uint32_t dst0) {
     constexpr int SEG = 512 / W;                  // segments per 512-byte k row
     constexpr int PER = W / 4;                    // floats per segment
     const int lane = threadIdx.x & 31;
@@ -207,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
             const int b = find_block(p.pre, p.count, it);
             const int64_t kch = p.d[b].kpad / kBK;
             const bool trans = p.d[b].trans != 0;
+            const bool mfree = p.d[b].A == nullptr;
             for (int64_t kc = 0; kc < kch; ++kc, ++g) {
                 const int s = (int)(g % kStages);
                 ok = mbar_wait(&empty[s], (uint32_t)((g / kStages) & 1) ^ 1u, &s_abort, p.err);
@@ -218,31 +276,59 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
                     break;
                 }
                 const unsigned char* tile = abuf + (size_t)as * kHalfBytes;
-                float4 v[8];
-                if (!trans) {
-                    const unsigned char* src = tile + (size_t)r * 128;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const float4*>(src + ((c ^ (r & 7)) << 4));
-                } else {
-                    // k-major tile: column r (consecutive lanes read consecutive words)
-                    const float* src = reinterpret_cast<const float*>(tile) + r;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        v[c] = make_float4(src[(4 * c) * 128], src[(4 * c + 1) * 128], src[(4 * c + 2) * 128],
-                                           src[(4 * c + 3) * 128]);
-                }
-                mbar_arrive(&a_empty[as]);
-                uint32_t hi[16], mid[16], lo[16];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    split3(v[c].x, v[c].y, hi[2 * c], mid[2 * c], lo[2 * c]);
-                    split3(v[c].z, v[c].w, hi[2 * c + 1], mid[2 * c + 1], lo[2 * c + 1]);
-                }
-                tc_fence_after();
                 const uint32_t col = kAStageCol + 96u * (uint32_t)s + 16u * (uint32_t)h;
-                tmem_st16(lane_base + col, hi);
-                tmem_st16(lane_base + col + 32u, mid);
-                tmem_st16(lane_base + col + 64u, lo);
+                if (mfree) {
+                    // entries computed and stored to TMEM eight words (16 entries) at a time
+                    const float4 xr = reinterpret_cast<const float4*>(tile)[r];
+                    const unsigned long long x0 = pk(xr.x, xr.x), x1 = pk(xr.y, xr.y), x2 = pk(xr.z, xr.z);
+                    const float* cx = reinterpret_cast<const float*>(tile + kColPts);
+                    tc_fence_after();
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        uint32_t h8[8], m8[8], l8[8];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int cc = 4 * half + c;
+                            const float4 gx = *reinterpret_cast<const float4*>(cx + 4 * cc);
+                            const float4 gy = *reinterpret_cast<const float4*>(cx + 32 + 4 * cc);
+                            const float4 gz = *reinterpret_cast<const float4*>(cx + 64 + 4 * cc);
+                            float e0, e1, e2, e3;
+                            kernel_pair(x0, x1, x2, pk(gx.x, gx.y), pk(gy.x, gy.y), pk(gz.x, gz.y), e0, e1);
+                            kernel_pair(x0, x1, x2, pk(gx.z, gx.w), pk(gy.z, gy.w), pk(gz.z, gz.w), e2, e3);
+                            split3(e0, e1, h8[2 * c], m8[2 * c], l8[2 * c]);
+                            split3(e2, e3, h8[2 * c + 1], m8[2 * c + 1], l8[2 * c + 1]);
+                        }
+                        tmem_st8(lane_base + col + 8u * half, h8);
+                        tmem_st8(lane_base + col + 32u + 8u * half, m8);
+                        tmem_st8(lane_base + col + 64u + 8u * half, l8);
+                    }
+                    mbar_arrive(&a_empty[as]);
+                } else {
+                    float4 v[8];
+                    if (!trans) {
+                        const unsigned char* src = tile + (size_t)r * 128;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const float4*>(src + ((c ^ (r & 7)) << 4));
+                    } else {
+                        // k-major tile: column r (consecutive lanes read consecutive words)
+                        const float* src = reinterpret_cast<const float*>(tile) + r;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            v[c] = make_float4(src[(4 * c) * 128], src[(4 * c + 1) * 128], src[(4 * c + 2) * 128],
+                                               src[(4 * c + 3) * 128]);
+                    }
+                    mbar_arrive(&a_empty[as]);
+                    uint32_t hi[16], mid[16], lo[16];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        split3(v[c].x, v[c].y, hi[2 * c], mid[2 * c], lo[2 * c]);
+                        split3(v[c].z, v[c].w, hi[2 * c + 1], mid[2 * c + 1], lo[2 * c + 1]);
+                    }
+                    tc_fence_after();
+                    tmem_st16(lane_base + col, hi);
+                    tmem_st16(lane_base + col + 32u, mid);
+                    tmem_st16(lane_base + col + 64u, lo);
+                }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(&full_a[s]);
@@ -255,10 +341,13 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
         bool ok = true;
         for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
             const int b = find_block(p.pre, p.count, it);
-            const BatchDesc D = p.d[b];
+            const BatchDesc& D = p.d[b];
+            const BlockRef B{D.A, D.ld, D.rows, D.cols};   // in registers for the whole tile
+            const bool tr = D.trans != 0;
             const int64_t row0 = (it - p.pre[b]) * kBM;
             const int64_t kch = D.kpad / kBK;
-            const int w = copy_width(D.A, D.ld);
+            const bool mfree = B.A == nullptr;
+            const int w = mfree ? 4 : copy_width(B.A, B.ld);
             for (int64_t kc = 0; kc < kch && ok; ++kc) {
                 for (int h = 0; h < 2; ++h, ++hg) {
                     const int as = (int)(hg % kAStages);
@@ -269,14 +358,41 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
                     }
                     const uint32_t dst0 = smem_u32(abuf + (size_t)as * kHalfBytes);
                     const int64_t k0 = kc * kBK + 32 * h;
-                    if (!D.trans) {
-                        if (w == 16) load_rows<16>(D, row0, k0, 32 * pw, dst0);
-                        else if (w == 8) load_rows<8>(D, row0, k0, 32 * pw, dst0);
-                        else load_rows<4>(D, row0, k0, 32 * pw, dst0);
+                    if (mfree) {
+                        unsigned char* stg = abuf + (size_t)as * kHalfBytes;
+                        const int t = 32 * pw + lane;          // row point t of the tile
+                        const int64_t row = row0 + t;
+                        float4 rp = make_float4(kFar, kFar, kFar, 0.f);
+                        if (row < B.rows) {
+                            const float* xp = D.px + 3 * row;
+                            rp = make_float4(xp[0], xp[1], xp[2], 0.f);
+                        }
+                        reinterpret_cast<float4*>(stg)[t] = rp;
+                        if (pw == 0) {                          // column point k0 + lane, negated
+                            const int64_t k = k0 + lane;
+                            float nx = kFar, ny = kFar, nz = kFar;
+                            if (k < B.cols) {
+                                const float* yp = D.py + 3 * k;
+                                nx = -yp[0];
+                                ny = -yp[1];
+                                nz = -yp[2];
+                            }
+                            float* cs = reinterpret_cast<float*>(stg + kColPts);
+                            cs[lane] = nx;
+                            cs[32 + lane] = ny;
+                            cs[64 + lane] = nz;
+                        }
+                        mbar_arrive(&a_full[as]);             // release: the staged points before the arrival
+                        continue;
+                    }
+                    if (!tr) {
+                        if (w == 16) load_rows<16>(B, row0, k0, 32 * pw, dst0);
+                        else if (w == 8) load_rows<8>(B, row0, k0, 32 * pw, dst0);
+                        else load_rows<4>(B, row0, k0, 32 * pw, dst0);
                     } else {
-                        if (w == 16) load_cols<16>(D, row0, k0, 8 * pw, dst0);
-                        else if (w == 8) load_cols<8>(D, row0, k0, 8 * pw, dst0);
-                        else load_cols<4>(D, row0, k0, 8 * pw, dst0);
+                        if (w == 16) load_cols<16>(B, row0, k0, 8 * pw, dst0);
+                        else if (w == 8) load_cols<8>(B, row0, k0, 8 * pw, dst0);
+                        else load_cols<4>(B, row0, k0, 8 * pw, dst0);
                     }
                     cp_async_arrive(&a_full[as]);
                 }
@@ -289,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
         bool ok = true;
         for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
             const int b = find_block(p.pre, p.count, it);
-            const BatchDesc D = p.d[b];
+            const BatchDesc& D = p.d[b];
             const uint16_t* xt = p.xt + D.xt_off;
             const int64_t kch = D.kpad / kBK;
             for (int64_t kc = 0; kc < kch; ++kc, ++g) {
@@ -359,7 +475,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
             const bool ok = mbar_wait(&accf[a], (uint32_t)((j >> 1) & 1), &s_abort, p.err);
             if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.ld is warp-wide
             tc_fence_after();
-            const BatchDesc D = p.d[b];
+            const BatchDesc& D = p.d[b];
             const int64_t row = (it - p.pre[b]) * kBM + q * 32 + lane;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * p.N);
             for (int c = 0; c < p.N; c += 16) {

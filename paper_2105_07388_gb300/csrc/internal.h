@@ -35,6 +35,10 @@ struct BatchDesc {
     uint64_t seed;
     int64_t xt_off;     // offset (BF16 elements) of this block's X^T region (nxt x kpad) in the X^T pool
     int64_t kpad;       // cols rounded up to a multiple of 64
+    // matrix-free kernel block (A == nullptr): entry (r, c) of the oriented block
+    // is 1 / |px[r] - py[c]| for 3-D points (FP32, 3 per point), trans == 0
+    const float* px;
+    const float* py;
 };
 
 // ---- embeddings (embed.cu) ----------------------------------------------------
@@ -191,9 +195,11 @@ void mlp_init_host(float* P, uint64_t seed);
 struct BatchedState;
 // Level-synchronous batched Algorithm 1 (FP32 input, Gaussian X and Y); state is
 // created on first use and owned by the handle.  launches is incremented by the
-// number of kernels in one replay of the captured graph.
-int batched_estimate(BatchedState** st, const re_opts& o, const re_block* blocks, int count,
-                     double eps, uint64_t seed, double* sigma_out, int sigma_cap, re_result* out,
+// number of kernels in one replay of the captured graph.  Exactly one of blocks
+// (stored matrices) and kblocks (matrix-free kernel blocks, tensor-core
+// precision only) is non-null.
+int batched_estimate(BatchedState** st, const re_opts& o, const re_block* blocks, const re_kblock* kblocks,
+                     int count, double eps, uint64_t seed, double* sigma_out, int sigma_cap, re_result* out,
                      cudaStream_t stream, int64_t* launches);
 void batched_destroy(BatchedState* st);
 

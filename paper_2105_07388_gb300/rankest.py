@@ -61,6 +61,10 @@ class re_block(ctypes.Structure):
                 ("ld", ctypes.c_int64)]
 
 
+class re_kblock(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64)]
+
+
 class re_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("right_launches", ctypes.c_int64),
                 ("right_ms", ctypes.c_double), ("right_bytes", ctypes.c_double),
@@ -107,6 +111,8 @@ _SIGS = {
     "re_embedding_y": (_I, [_VP, _I, _U64, _I64, _I, _I, _VP, _VP]),
     "re_rank_estimate_batched": (_I, [_VP, ctypes.POINTER(re_block), _I, _I, _D, _I, _U64, _VP,
                                       _I, ctypes.POINTER(re_result), _VP]),
+    "re_rank_estimate_kernel_blocks": (_I, [_VP, ctypes.POINTER(re_kblock), _I, _D, _U64, _VP, _I,
+                                            ctypes.POINTER(re_result), _VP]),
     "re_sketch_apply_noalloc": (_I, [_VP, _I, _I64, _I64, _I64, _I, _I, _U64, _VP, _I64, _VP, _I64,
                                      _VP]),
     "re_mlp_init": (_I, [_VP, _U64]),
@@ -299,6 +305,26 @@ def re_rank_estimate_batched(h: int, blocks, eps: float, sketch_kind: int = RE_G
     _check(lib().re_rank_estimate_batched(h, arr, count, dtype, eps, sketch_kind, seed,
                                           sig.ctypes.data if sig is not None else None,
                                           sigma_cap, res, _stream(stream)))
+    return [res[i] for i in range(count)], sig
+
+
+def re_rank_estimate_kernel_blocks(h: int, points, eps: float, seed: int = 0, sigma_cap: int = 0,
+                                   stream=None):
+    """points: list of (x, y) device FP32 tensors of shapes (m, 3) and (n, 3), each
+    the matrix-free block K = 1/|x_i - y_j|.  Returns (results, sigma or None)."""
+    count = len(points)
+    arr = (re_kblock * max(count, 1))()
+    for i, (x, y) in enumerate(points):
+        for t in (x, y):
+            if not (t.is_floating_point() and t.element_size() == 4 and t.is_contiguous() and t.shape[1] == 3):
+                raise ValueError("points must be contiguous FP32 tensors of shape (k, 3)")
+        arr[i].x, arr[i].y = x.data_ptr(), y.data_ptr()
+        arr[i].m, arr[i].n = x.shape[0], y.shape[0]
+    res = (re_result * max(count, 1))()
+    sig = np.zeros((count, sigma_cap), dtype=np.float64) if sigma_cap > 0 else None
+    _check(lib().re_rank_estimate_kernel_blocks(h, arr, count, eps, seed,
+                                                sig.ctypes.data if sig is not None else None,
+                                                sigma_cap, res, _stream(stream)))
     return [res[i] for i in range(count)], sig
 
 

@@ -135,13 +135,20 @@ def householder_matrix(m: int, n: int, sigma: torch.Tensor, seed: int, device="c
     return C.to(dtype).contiguous()
 
 
-def kernel_block(m: int, n: int, seed: int, device="cpu", dtype=torch.float32) -> torch.Tensor:
-    """K_ij = 1/|x_i - y_j|, x ~ U[0,1]^3, y ~ U[0,1]^3 + (1 + d) e_1, d ~ U[1, 4]."""
+def kernel_points(m: int, n: int, seed: int, device="cpu"):
+    """Point sets of a kernel block (FP64): x ~ U[0,1]^3 (m points) and
+    y ~ U[0,1]^3 + (1 + d) e_1 (n points), d ~ U[1, 4]."""
     g = _gen(seed, device)
     d = 1.0 + 3.0 * torch.rand((), generator=g, dtype=torch.float64, device=device)
     x = torch.rand(m, 3, generator=g, dtype=torch.float64, device=device)
     y = torch.rand(n, 3, generator=g, dtype=torch.float64, device=device)
     y[:, 0] += 1.0 + d
+    return x, y
+
+
+def kernel_block(m: int, n: int, seed: int, device="cpu", dtype=torch.float32) -> torch.Tensor:
+    """K_ij = 1/|x_i - y_j| for the points of kernel_points."""
+    x, y = kernel_points(m, n, seed, device)
     K = 1.0 / torch.cdist(x, y)
     return K.to(dtype).contiguous()
 

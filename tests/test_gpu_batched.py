@@ -112,3 +112,73 @@ def test_batched_invalid_block_reported(h):
     assert rc == 0
     assert out[0].status == 0 and out[0].rank == 7
     assert out[1].status == rk.RE_ERR_ARG
+
+
+def _points(shapes, seed0):
+    out = []
+    for i, (m, n) in enumerate(shapes):
+        x, y = wl.kernel_points(m, n, seed=seed0 + i)
+        out.append((x.float().contiguous().cuda(), y.float().contiguous().cuda()))
+    return out
+
+
+def _dense(x, y):
+    """The block of the FP32 points in FP64 (what the oracle sketches)."""
+    xd, yd = x.double().cpu().numpy(), y.double().cpu().numpy()
+    return 1.0 / np.sqrt(((xd[:, None, :] - yd[None, :, :]) ** 2).sum(axis=2))
+
+
+def test_matrix_free_kernel_blocks():
+    """Matrix-free kernel blocks (entries 1/|x_i - y_j| computed in FP32 as the
+    tensor-core sketch consumes them) against the FP64 oracle on the same points,
+    against the stored-matrix batched path, and on graph replay."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2105_07388_gb300 import build
+    build.build()
+    hm = rk.re_create(0, rk.make_opts(s_max=128, precision=rk.RE_PREC_BF16X3))
+    shapes = wl.kernel_block_sizes(14, seed=21, lo=256, hi=1500) + [(100, 1900), (1900, 70), (333, 333)]
+    pts = _points(shapes, 600)
+    res, sig = rk.re_rank_estimate_kernel_blocks(hm, pts, 1e-6, 77, sigma_cap=128)
+    res2, sig2 = rk.re_rank_estimate_kernel_blocks(hm, pts, 1e-6, 77, sigma_cap=128)     # graph replay
+    assert [r.rank for r in res] == [r.rank for r in res2] and np.array_equal(sig, sig2)
+    dense = [_dense(x, y) for x, y in pts]
+    for i, (m, n) in enumerate(shapes):
+        orc = alg.rank_estimate(dense[i], 1e-6, kind=alg.GAUSSIAN, seed=77 + i, s_max=128)
+        assert res[i].status == 0
+        assert bool(res[i].flags & rk.RE_TRANSPOSED) == (m < n)
+        assert res[i].final_s == orc.final_s or _agree(res[i].rank, orc, 1e-6)
+        if res[i].final_s == orc.final_s:
+            k = min(res[i].n_sigma, len(orc.sigma))
+            assert np.max(np.abs(sig[i, :k] - orc.sigma[:k])) <= SIGMA_TOL * orc.sigma[0]
+        assert _agree(res[i].rank, orc, 1e-6)
+    # the stored blocks (FP64 distances of the same points, rounded to FP32)
+    blocks = [torch.from_numpy(D).float().cuda() for D in dense]
+    rs, ss = rk.re_rank_estimate_batched(hm, blocks, 1e-6, rk.RE_GAUSSIAN, 77, sigma_cap=128)
+    same = sum(int(a.rank == b.rank) for a, b in zip(res, rs))
+    assert same >= len(shapes) - 2, same
+    for i in range(len(shapes)):
+        if res[i].final_s == rs[i].final_s:
+            k = min(res[i].n_sigma, rs[i].n_sigma)
+            assert np.max(np.abs(sig[i, :k] - ss[i, :k])) <= SIGMA_TOL * ss[i, 0]
+    rk.re_destroy(hm)
+
+
+def test_matrix_free_errors():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2105_07388_gb300 import build
+    build.build()
+    pts = _points([(300, 200), (256, 260)], 900)
+    # coincident points: an infinite entry, reported in that block's status only
+    x, y = pts[1]
+    y[5] = x[3]
+    h32 = rk.re_create(0, rk.make_opts(s_max=128, precision=rk.RE_PREC_FP32))
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_rank_estimate_kernel_blocks(h32, pts, 1e-6, 1)
+    assert e.value.code == rk.RE_ERR_UNSUPPORTED
+    rk.re_destroy(h32)
+    hm = rk.re_create(0, rk.make_opts(s_max=128, precision=rk.RE_PREC_BF16X3))
+    res, _ = rk.re_rank_estimate_kernel_blocks(hm, pts, 1e-6, 1)
+    assert res[0].status == 0 and res[1].status == rk.RE_ERR_NONFINITE
+    rk.re_destroy(hm)
