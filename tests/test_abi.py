@@ -51,3 +51,44 @@ def test_create_without_gpu_fails_cleanly(built):
     with pytest.raises(rankest.RankEstError) as ei:
         rankest.re_create(0)
     assert ei.value.code in (rankest.RE_ERR_CUDA, rankest.RE_ERR_ARG)
+
+
+def _header_layout(tmp_path):
+    """Sizes and field offsets of the header's structs and the values of its
+    RE_* constants, as a C compiler sees them (gcc on this host)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {name: [f for f, _ in getattr(rankest, name)._fields_]
+               for name in ("re_opts", "re_result", "re_block", "re_kblock", "re_stats")}
+    consts = [n for n in dir(rankest) if re.fullmatch(r"RE_[A-Z0-9_]+", n)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rankest.h"', "int main(void) {"]
+    for s, fields in structs.items():
+        lines.append(f'printf("{s} size %zu\\n", sizeof({s}));')
+        for f in fields:
+            lines.append(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    for c in consts:
+        lines.append(f'printf("{c} %lld\\n", (long long)({c}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for ln in out.splitlines():
+        k, v = ln.rsplit(" ", 1)
+        got[k] = int(v)
+    return structs, consts, got
+
+
+def test_binding_layout_matches_header(tmp_path):
+    structs, consts, c = _header_layout(tmp_path)
+    for s, fields in structs.items():
+        cls = getattr(rankest, s)
+        assert ctypes.sizeof(cls) == c[f"{s} size"], s
+        for f in fields:
+            assert getattr(cls, f).offset == c[f"{s}.{f}"], (s, f)
+    for name in consts:
+        assert getattr(rankest, name) == c[name], name
