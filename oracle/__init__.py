@@ -17,6 +17,10 @@ Contents
 ``algorithm1`` Algorithm 1 (Sec. 5) step by step in FP64 with numpy: the sketch
                matrices written out densely, A·X and Θ·(A·X) by matrix products,
                singular values by LAPACK, read-off by Definition 1.
+``algorithm3`` Algorithm 3 (Sec. 5.1): rank estimation combined with the
+               randomized rangefinder -- the Frobenius criterion on the
+               sketched singular values picks r, then a Householder thin QR of
+               the first r + p columns of A X and B = Q^T A.
 ``mlp``        the sketch-size proposal network's forward/backward in FP64
                (plain numpy), used to check the GPU gradients.
 
