@@ -251,6 +251,38 @@ int re_rank_estimate_batched(re_handle h, const re_block* blocks, int count, int
                              double eps, int sketch_kind, uint64_t seed,
                              double* sigma_out, int sigma_cap, re_result* out, void* stream);
 
+/* Result of re_rank_estimate_qb. */
+typedef struct {
+    int r;            /* target rank chosen by the Frobenius criterion (Algorithm 3 step 5) */
+    int k;            /* columns of Q: r + p, or the last width when the criterion was not met */
+    int final_s;      /* sketch width at which r was chosen */
+    int passes;       /* reads of A by the sketch (B = Q^T A is one more) */
+    uint32_t flags;   /* RE_CONVERGED: criterion met; RE_LOWER_BOUND_ONLY: the ladder ended
+                         first; RE_TRANSPOSED: m < n, Q and B factor A^T */
+    int status;       /* RE_OK, or RE_ERR_NONFINITE */
+    double bound;     /* (1 + r/(p-1))^{1/2} (sum_{j>r} sigma^_j^2)^{1/2}: the estimated error */
+    double norm_a;    /* ||A|| used by the criterion (sigma^_1 unless opts.norm_a) */
+} re_qb_result;
+
+/*
+ * Algorithm 3 (Sec. 5.1): rank estimation combined with the randomized
+ * rangefinder, for FP32 A (device, m x n row-major, ld).  The doubling ladder of
+ * Algorithm 1 (Gaussian X; left embedding per opts.y_kind) runs until the
+ * smallest r with (1 + r/(p-1))^{1/2} (sum_{j>r} sigma^_j^2)^{1/2} <= eps ||A||
+ * (sigma^_j = sigma^_{r1} for r1 < j <= min(m, n), step 4) also has r + p <= s;
+ * then Q (device FP32, max(m,n) x k, ldq >= k) gets orthonormal columns spanning
+ * the first k = r + p columns of A X, and B = Q^T A (device FP32, k x min(m,n),
+ * ldb >= min(m,n)), so A ~ Q B (A^T ~ Q B when m < n).  The thin QR uses the
+ * core Y (A X_k) to precondition (Sec. 4's randomized approximate
+ * orthogonalization) and two Cholesky-QR passes; products are cuBLAS GEMMs.
+ * p >= 2 (Halko et al. suggest 5 or 10).  If k exceeds k_cap, returns
+ * RE_ERR_ARG with out->k set (call again with larger Q and B).  Synchronises
+ * `stream`.
+ */
+int re_rank_estimate_qb(re_handle h, const float* A, int64_t m, int64_t n, int64_t ld, double eps, int p,
+                        uint64_t seed, float* Q, int64_t ldq, float* B, int64_t ldb, int k_cap,
+                        re_qb_result* out, void* stream);
+
 /*
  * As re_rank_estimate_batched with Gaussian embeddings, for matrix-free kernel
  * blocks (HOST array of re_kblock): the tensor-core right sketch computes each

@@ -19,7 +19,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librankest.so")
 
 SOURCES = ["api.cu", "embed.cu", "sketch_simt.cu", "sketch_srht.cu", "sketch_tc.cu",
-           "core_svd.cu", "noalloc.cu", "batched.cu", "mlp.cu", "left_tc.cu", "batched_tc.cu", "left_fwht.cu"]
+           "core_svd.cu", "noalloc.cu", "batched.cu", "mlp.cu", "left_tc.cu", "batched_tc.cu", "left_fwht.cu",
+           "rangefinder.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -62,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -51,6 +53,8 @@ struct re_handle_ {
     std::vector<PendingTiming> pending;
     std::vector<cudaEvent_t> event_pool;
     DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status, ht, fz;
+    DevBuf qbws, qbsel;                 // Algorithm 3: factorization workspace, selection record
+    void* cublas = nullptr;             // cublasHandle_t, created on first use (Algorithm 3's GEMMs)
     re::BatchedState* batched = nullptr;
     // sketch-size proposal network: parameters, Adam moments, gradient, scratch
     DevBuf mlp_P, mlp_M, mlp_V, mlp_G, mlp_X, mlp_y, mlp_logits, mlp_keep, mlp_cls, mlp_feat, mlp_loss;
@@ -517,6 +521,80 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
     return RE_OK;
 }
 
+// Algorithm 3 (Sec. 5.1): the doubling ladder of Algorithm 1 with the Frobenius
+// criterion of step 5 as its stopping rule, then the thin QR of the first
+// k = r + p columns of A X and B = Q^T A (rangefinder.cu).
+int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* Q, int64_t ldq, float* B,
+           int64_t ldb, int k_cap, re_qb_result* out, cudaStream_t st) {
+    const re_opts& o = h->opts;
+    if (o.s0 > P.cap) return fail(RE_ERR_ARG, "initial sketch width exceeds the admissible width");
+    int smax = o.s0;
+    while (smax * 2 <= P.cap) smax *= 2;
+    const int64_t M = P.A.rows;
+    if (int r = ensure(h->ax, sizeof(float) * (size_t)M * smax)) return r;
+    if (int r = ensure(h->core, sizeof(double) * (size_t)2 * smax * smax)) return r;
+    if (int r = ensure(h->sigma, sizeof(double) * (size_t)smax)) return r;
+    if (int r = ensure(h->sigma_scaled, sizeof(double) * (size_t)smax)) return r;
+    if (int r = ensure(h->svdws, re::svd_workspace_bytes(2 * smax, smax))) return r;
+    if (int r = ensure(h->ro, sizeof(re::DevReadoff))) return r;
+    if (int r = ensure(h->status, 64)) return r;
+    if (int r = ensure(h->qbsel, sizeof(re::QbSelect) + 16)) return r;
+    float* AX = static_cast<float*>(h->ax.p);
+    double* core = static_cast<double*>(h->core.p);
+    re::QbSelect* sel_dev = static_cast<re::QbSelect*>(h->qbsel.p);
+    int* floored = reinterpret_cast<int*>(static_cast<char*>(h->qbsel.p) + sizeof(re::QbSelect));
+    cudaError_t e = cudaMemsetAsync(h->status.p, 0, 4 * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(floored, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
+    std::memset(out, 0, sizeof(*out));
+    int s_prev = 0, s = o.s0, passes = 0, r1 = 0;
+    re::DevReadoff ro{};
+    re::QbSelect sel{};
+    for (;;) {
+        if (int r = right_columns(h, P, seed, s_prev, s - s_prev, AX, smax, st)) return r;
+        if (int r = left_blocks(h, P, seed, s_prev, s, AX, smax, core, smax, st, s_prev)) return r;
+        h->stats.passes += 1;
+        ++passes;
+        if (int r = check_width(h, P, s, smax, eps, &ro, &r1, st, false)) {
+            out->status = r;
+            return r;
+        }
+        e = re::launch_select_rank(static_cast<const double*>(h->sigma_scaled.p), r1, P.A.cols, eps, o.norm_a, p,
+                                   s, sel_dev, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&sel, sel_dev, sizeof(sel), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "rank selection");
+        h->stats.launches += 1;
+        if (sel.met || 2 * s > smax || r1 >= P.A.cols) break;
+        s_prev = s;
+        s *= 2;
+    }
+    const bool met = sel.met != 0;
+    const int r = met ? sel.r : std::max(s - p, 0);
+    const int k = (int)std::min<int64_t>(met ? r + p : s, P.A.cols);
+    out->r = r;
+    out->k = k;
+    out->final_s = s;
+    out->passes = passes;
+    out->flags = (met ? RE_CONVERGED : RE_LOWER_BOUND_ONLY) | (P.A.trans ? RE_TRANSPOSED : 0u);
+    out->bound = met ? sel.bound : -1.0;
+    out->norm_a = sel.norm_a;
+    if (k > k_cap) return fail(RE_ERR_ARG, "k_cap is smaller than the chosen k = r + p (out->k holds it)");
+    if (ldq < k) return fail(RE_ERR_ARG, "ldq < k");
+    if (int rr = ensure(h->qbws, re::qb_workspace_bytes(M, k))) return rr;
+    if (!h->cublas) {
+        cublasHandle_t hb = nullptr;
+        if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) return fail(RE_ERR_CUDA, "cuBLAS handle creation failed");
+        h->cublas = hb;
+    }
+    e = re::launch_qb_factor(h->cublas, P.A, AX, smax, core, smax, 2 * s, k, Q, ldq, B, ldb, h->qbws.p, floored,
+                             st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "thin QR and B = Q^T A");
+    h->stats.launches += 7;
+    return RE_OK;
+}
+
 int check_opts(const re_opts* o) {
     if (o->s0 < 8 || o->s0 % 8 != 0) return fail(RE_ERR_ARG, "s0 must be a positive multiple of 8");
     if (o->s_max < o->s0) return fail(RE_ERR_ARG, "s_max < s0");
@@ -581,10 +659,12 @@ int re_destroy(re_handle h) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&h->x, &h->xt, &h->ax, &h->part, &h->core, &h->sigma, &h->sigma_scaled,
                       &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status, &h->ht, &h->fz,
+                      &h->qbws, &h->qbsel,
                       &h->mlp_P, &h->mlp_M, &h->mlp_V, &h->mlp_G, &h->mlp_X, &h->mlp_y,
                       &h->mlp_logits, &h->mlp_keep, &h->mlp_cls, &h->mlp_feat, &h->mlp_loss};
     for (DevBuf* b : bufs) release(*b);
     re::batched_destroy(h->batched);
+    if (h->cublas) cublasDestroy(static_cast<cublasHandle_t>(h->cublas));
     resolve_timings(h);
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     if (h->h_ro) cudaFreeHost(h->h_ro);
@@ -652,6 +732,20 @@ int re_rank_estimate_host(re_handle h, const void* A_host, int dtype, int64_t m,
     if (e != cudaSuccess) return cuda_fail(e, "host to device copy of A");
     return re_rank_estimate(h, h->acopy.p, dtype, m, n, n, eps, sketch_kind, seed, sigma_out,
                             sigma_cap, out, stream);
+}
+
+int re_rank_estimate_qb(re_handle h, const float* A, int64_t m, int64_t n, int64_t ld, double eps, int p,
+                        uint64_t seed, float* Q, int64_t ldq, float* B, int64_t ldb, int k_cap, re_qb_result* out,
+                        void* stream) {
+    if (!h || !A || !Q || !B || !out) return fail(RE_ERR_ARG, "NULL argument");
+    if (!(eps > 0.0 && eps < 1.0)) return fail(RE_ERR_ARG, "eps must lie in (0, 1)");
+    if (p < 2) return fail(RE_ERR_ARG, "p must be at least 2");
+    if (k_cap < 1) return fail(RE_ERR_ARG, "k_cap must be positive");
+    cudaSetDevice(h->device);
+    Plan P;
+    if (int r = make_plan(A, RE_F32, m, n, ld, RE_GAUSSIAN, left_kind(h, RE_GAUSSIAN), h->opts.s_max, &P)) return r;
+    if (ldb < P.A.cols) return fail(RE_ERR_ARG, "ldb < min(m, n)");
+    return run_qb(h, P, eps, p, seed, Q, ldq, B, ldb, k_cap, out, static_cast<cudaStream_t>(stream));
 }
 
 int re_sketch_apply(re_handle h, const void* A, int dtype, int64_t m, int64_t n, int64_t ld,

@@ -191,6 +191,27 @@ cudaError_t mlp_argmax(const float* logits, int count, int* cls, cudaStream_t st
 cudaError_t mlp_features(const double* sigma16, double eps, int64_t rows, int64_t cols, float* f, cudaStream_t st);
 void mlp_init_host(float* P, uint64_t seed);
 
+// ---- Algorithm 3 after the sketch (rangefinder.cu) ----------------------------
+struct QbSelect {
+    int r;           // selected target rank, -1 when no r in [0, r1] meets the criterion
+    int met;         // r >= 0 and r + p <= s
+    double bound;    // (1 + r/(p-1))^{1/2} (sum_{j>r} sigma^_j^2)^{1/2} at r
+    double norm_a;   // ||A|| used (sigma^_1 unless given)
+};
+// Step 5 on the r1 trusted scaled sigma (device) of the width-s sketch; n = the
+// smaller dimension (the conservative tail runs to it).
+cudaError_t launch_select_rank(const double* sigma_scaled, int r1, int64_t n, double eps, double norm_a, int p,
+                               int s, QbSelect* out, cudaStream_t st);
+size_t qb_workspace_bytes(int64_t rows, int k);
+// Steps 7-8 for the first k columns of AX (rows x ldax FP32) with the FP64 core
+// (r2 rows, ld_core) as the preconditioning sketch: Q (rows x k, ldq) with
+// orthonormal columns, B = Q^T A_oriented (k x cols, ldb).  cublas is a
+// cublasHandle_t; ws holds qb_workspace_bytes(rows, k); *floored (device) is set
+// when a Cholesky pivot had to be raised (an exactly singular Gram matrix).
+cudaError_t launch_qb_factor(void* cublas, const MatView& A, const float* AX, int64_t ldax, const double* core,
+                             int64_t ld_core, int r2, int k, float* Q, int64_t ldq, float* B, int64_t ldb, void* ws,
+                             int* floored, cudaStream_t st);
+
 // ---- batched estimate (batched.cu) --------------------------------------------
 struct BatchedState;
 // Level-synchronous batched Algorithm 1 (FP32 input, Gaussian X and Y); state is

@@ -65,6 +65,12 @@ class re_kblock(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64)]
 
 
+class re_qb_result(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int), ("k", ctypes.c_int), ("final_s", ctypes.c_int), ("passes", ctypes.c_int),
+                ("flags", ctypes.c_uint32), ("status", ctypes.c_int), ("bound", ctypes.c_double),
+                ("norm_a", ctypes.c_double)]
+
+
 class re_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("right_launches", ctypes.c_int64),
                 ("right_ms", ctypes.c_double), ("right_bytes", ctypes.c_double),
@@ -113,6 +119,8 @@ _SIGS = {
                                       _I, ctypes.POINTER(re_result), _VP]),
     "re_rank_estimate_kernel_blocks": (_I, [_VP, ctypes.POINTER(re_kblock), _I, _D, _U64, _VP, _I,
                                             ctypes.POINTER(re_result), _VP]),
+    "re_rank_estimate_qb": (_I, [_VP, _VP, _I64, _I64, _I64, _D, _I, _U64, _VP, _I64, _VP, _I64, _I,
+                                 ctypes.POINTER(re_qb_result), _VP]),
     "re_sketch_apply_noalloc": (_I, [_VP, _I, _I64, _I64, _I64, _I, _I, _U64, _VP, _I64, _VP, _I64,
                                      _VP]),
     "re_mlp_init": (_I, [_VP, _U64]),
@@ -306,6 +314,28 @@ def re_rank_estimate_batched(h: int, blocks, eps: float, sketch_kind: int = RE_G
                                           sig.ctypes.data if sig is not None else None,
                                           sigma_cap, res, _stream(stream)))
     return [res[i] for i in range(count)], sig
+
+
+def re_rank_estimate_qb(h: int, A, eps: float, p: int = 10, seed: int = 0, Q=None, B=None, k_cap: int = 0,
+                        stream=None):
+    """Algorithm 3: returns (result, Q[:, :k], B[:k]) for FP32 device A.  Unless
+    given, Q and B are allocated with k_cap = min(min(m, n), 512) columns / rows,
+    enough for any width of the ladder; given buffers too small for the chosen k
+    raise RankEstError with code RE_ERR_ARG."""
+    import torch
+    m, n = A.shape
+    assert A.stride(1) == 1 and A.is_floating_point() and A.element_size() == 4
+    rows, cols = max(m, n), min(m, n)
+    if k_cap <= 0:
+        k_cap = min(cols, 512)
+    if Q is None:
+        Q = torch.empty(rows, k_cap, dtype=torch.float32, device=A.device)
+    if B is None:
+        B = torch.empty(k_cap, cols, dtype=torch.float32, device=A.device)
+    res = re_qb_result()
+    _check(lib().re_rank_estimate_qb(h, _ptr(A), m, n, A.stride(0), eps, p, seed, _ptr(Q), Q.stride(0), _ptr(B),
+                                     B.stride(0), k_cap, ctypes.byref(res), _stream(stream)))
+    return res, Q[:, :res.k], B[:res.k]
 
 
 def re_rank_estimate_kernel_blocks(h: int, points, eps: float, seed: int = 0, sigma_cap: int = 0,

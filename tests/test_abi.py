@@ -61,7 +61,7 @@ def _header_layout(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("no C compiler")
     structs = {name: [f for f, _ in getattr(rankest, name)._fields_]
-               for name in ("re_opts", "re_result", "re_block", "re_kblock", "re_stats")}
+               for name in ("re_opts", "re_result", "re_block", "re_kblock", "re_stats", "re_qb_result")}
     consts = [n for n in dir(rankest) if re.fullmatch(r"RE_[A-Z0-9_]+", n)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rankest.h"', "int main(void) {"]
     for s, fields in structs.items():

@@ -1,0 +1,103 @@
+"""Algorithm 3 (rank estimation combined with the randomized rangefinder,
+Sec. 5.1) through the C ABI against the FP64 oracle.
+
+The oracle's thin QR is Householder; the library's is sketch-preconditioned
+Cholesky-QR, so Q is compared through what is unique: the selected r, k and
+width, orthonormality, B = Q^T A within the FP32 product bound, the
+approximation error against the oracle's, and the span of the leading r
+columns (the nested spans of A X_k's columns, fixed by the shared X)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import algorithm3 as a3
+from paper_2105_07388_gb300 import rankest as rk
+from paper_2105_07388_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2105_07388_gb300 import build
+    build.build()
+    hd = rk.re_create(0)
+    yield hd
+    rk.re_destroy(hd)
+
+
+def _sin_angle(Q1, Q2):
+    """Sine of the largest principal angle between span(Q1) and span(Q2)."""
+    c = np.linalg.svd(Q1.T @ Q2, compute_uv=False)
+    return math.sqrt(max(0.0, 1.0 - float(c.min()) ** 2))
+
+
+CASES = [
+    ("step", 1500, 600, dict(rank=37, tail_scale=1e-9), 1e-5, 10),   # a clear gap
+    ("fp", 1200, 500, {}, 1e-3, 10),                                # algebraic decay, no gap
+    ("fe", 700, 700, {}, 1e-4, 5),                                   # exponential decay
+    ("step", 400, 1100, dict(rank=20, tail_scale=1e-9), 1e-5, 5),   # m < n: A^T is factored
+]
+
+
+@pytest.mark.parametrize("fam,m,n,kw,eps,p", CASES)
+def test_qb_parity(h, fam, m, n, kw, eps, p):
+    sig = wl.spectrum(fam, min(m, n), **kw)
+    A = wl.haar_matrix(m, n, sig, seed=m + n).numpy().astype(np.float32)
+    A64 = A.astype(np.float64)
+    res, Q, B = rk.re_rank_estimate_qb(h, torch.from_numpy(A).cuda(), eps, p=p, seed=21)
+    orc = a3.qb(A64, eps, p=p, seed=21)
+    assert res.status == 0
+    assert bool(res.flags & rk.RE_TRANSPOSED) == (m < n) == orc.transposed
+    assert bool(res.flags & rk.RE_CONVERGED) == orc.met
+    assert res.final_s == orc.final_s
+    if fam == "step":
+        assert res.r == orc.r == kw["rank"]
+    else:
+        # sketched sigma agree to 1e-4 sigma_1: at the threshold the choice may move by one
+        assert abs(res.r - orc.r) <= 1
+    assert res.k == res.r + p
+    Qg, Bg = Q.double().cpu().numpy(), B.double().cpu().numpy()
+    k = res.k
+    assert np.max(np.abs(Qg.T @ Qg - np.eye(k))) < 1e-5
+    Ao = A64.T if m < n else A64
+    bound = 2.0 * (Ao.shape[0] / 32 + 32) * U32 * (np.abs(Qg).T @ np.abs(Ao)) + 1e-30
+    assert np.all(np.abs(Bg - Qg.T @ Ao) <= bound)
+    nrm = np.linalg.norm(Ao)
+    err_g = np.linalg.norm(Ao - Qg @ Bg)
+    err_o = np.linalg.norm(Ao - orc.Q @ orc.B)
+    assert err_g <= 1.5 * err_o + 1e-5 * nrm, (err_g / nrm, err_o / nrm)
+    r = min(res.r, orc.r)
+    if r > 0:
+        assert _sin_angle(Qg[:, :r], orc.Q[:, :r]) < 1e-2
+    assert res.bound > 0 and res.bound <= eps * res.norm_a * (1 + 1e-12)
+
+
+def test_qb_exact_low_rank_and_zero(h):
+    sig = wl.spectrum("step", 300, rank=12, tail_scale=0.0)
+    A = wl.haar_matrix(700, 300, sig, seed=9).to(torch.float32).cuda()
+    res, Q, B = rk.re_rank_estimate_qb(h, A, 1e-5, p=5, seed=3)
+    assert res.r == 12 and res.k == 17 and res.flags & rk.RE_CONVERGED
+    err = torch.linalg.norm(A.double() - Q.double() @ B.double()) / torch.linalg.norm(A.double())
+    assert float(err) < 1e-5
+    Z = torch.zeros(500, 200, device="cuda")
+    res, Q, B = rk.re_rank_estimate_qb(h, Z, 1e-3, p=4, seed=1)
+    assert res.r == 0 and res.k == 4
+    assert torch.all(torch.isfinite(Q)) and torch.all(B == 0)
+
+
+def test_qb_errors(h):
+    A = torch.randn(300, 200, device="cuda")
+    Q = torch.empty(300, 4, device="cuda")
+    B = torch.empty(4, 200, device="cuda")
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_rank_estimate_qb(h, A, 1e-3, p=5, seed=1, Q=Q, B=B, k_cap=4)      # full rank: k > 4
+    assert e.value.code == rk.RE_ERR_ARG
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_rank_estimate_qb(h, A, 1e-3, p=1)
+    assert e.value.code == rk.RE_ERR_ARG
