@@ -109,3 +109,18 @@ def test_qb_transposed_and_errors():
         a3.qb(A, 1e-5, p=1)
     with pytest.raises(ValueError):
         a3.qb(A, 0.0)
+
+
+def test_qb_ladder_end_and_norm_override():
+    # a full-rank matrix with a flat spectrum cannot meet eps = 1e-6 within s <= 32:
+    # the ladder ends, k = s = 32 columns are returned and the criterion is not met
+    A = np.random.default_rng(2).standard_normal((300, 200))
+    res = a3.qb(A, 1e-6, p=5, seed=1, s_max=32)
+    assert not res.met and res.final_s == 32 and res.k == 32 and res.r == 27
+    assert np.max(np.abs(res.Q.T @ res.Q - np.eye(32))) < 1e-12
+    # a larger ||A|| given by the caller loosens the criterion: a smaller or equal r
+    sig = wl.spectrum("fp", 300)
+    B = wl.haar_matrix(500, 300, sig, seed=2).numpy()
+    r_default = a3.qb(B, 1e-3, p=5, seed=4).r
+    r_loose = a3.qb(B, 1e-3, p=5, seed=4, norm_a=10.0 * float(sig[0])).r
+    assert r_loose < r_default
