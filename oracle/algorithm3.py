@@ -19,11 +19,12 @@ The steps in the algorithm box's order:
 Readings taken here (the CUDA path takes the same ones):
 
 * ||A|| is sigma^_1 unless the caller gives it (the algorithm's fallback).
-* r ranges over 0 .. r1 (r = 0 when even the whole estimated tail is below
-  eps ||A||); the tail beyond r1 counts n - r1 copies of sigma^_{r1}, n the
-  smaller dimension.  r + p must not exceed the width s; otherwise s doubles.
-* When the ladder cannot grow, the largest factorization it has (k = s) is
-  returned with ``met = False``.
+* r ranges over 0 .. min(r1, n) (r = 0 when even the whole estimated tail is
+  below eps ||A||); the tail beyond r1 counts n - r1 copies of sigma^_{r1}, n
+  the smaller dimension, and sketched values beyond the n-th count as zero.
+  r + p must not exceed the width s; otherwise s doubles.
+* When the ladder cannot grow, the largest factorization it has (k = s, at
+  most n) is returned with ``met = False`` and r = k - p.
 * m < n: the factorization is of A^T (Q spans the column space of A^T).
 """
 from __future__ import annotations
@@ -38,9 +39,10 @@ from . import rng
 
 
 def tail_sums(sig_trusted: np.ndarray, n: int) -> np.ndarray:
-    """Step 4: T[r] = sum_{j>r} sigma^_j^2 for r = 0 .. r1, with sigma^_j =
-    sigma^_{r1} for r1 < j <= n."""
-    sig = np.asarray(sig_trusted, dtype=np.float64)
+    """Step 4: T[r] = sum_{j>r} sigma^_j^2 for r = 0 .. min(r1, n), with sigma^_j =
+    sigma^_{r1} for r1 < j <= n; values beyond the n-th are zero (A has only n
+    singular values), so a sketch wider than n trusts at most n of them."""
+    sig = np.asarray(sig_trusted, dtype=np.float64)[:max(n, 0)]
     r1 = sig.size
     rest = max(n - r1, 0) * (sig[-1] ** 2 if r1 else 0.0)
     T = np.empty(r1 + 1)
@@ -97,11 +99,10 @@ def qb(A: np.ndarray, eps: float, p: int = 10, seed: int = 0, s0: int = 8, s_max
             break
         s *= 2
     if met:
-        k = r + p
+        k = min(r + p, n)
     else:
-        k = s
-        r = max(s - p, 0)
-    k = min(k, n)
+        k = min(s, n)
+        r = max(k - p, 0)
     AXk = A64 @ rng.gaussian_x(n, k, seed)                 # step 6: the first k columns of AX
     Q, R = np.linalg.qr(AXk)                               # step 7
     d = np.sign(np.diag(R))

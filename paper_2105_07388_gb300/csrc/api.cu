@@ -570,8 +570,8 @@ int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* 
         s *= 2;
     }
     const bool met = sel.met != 0;
-    const int r = met ? sel.r : std::max(s - p, 0);
-    const int k = (int)std::min<int64_t>(met ? r + p : s, P.A.cols);
+    const int k = (int)std::min<int64_t>(met ? sel.r + p : s, P.A.cols);
+    const int r = met ? sel.r : std::max(k - p, 0);
     out->r = r;
     out->k = k;
     out->final_s = s;

@@ -2,9 +2,10 @@
 // rangefinder) after the sketch: the rank selection of step 5 and the thin QR of
 // step 7 and product of step 8 for the first k = r + p columns of A X.
 //
-// Step 5 (`select_rank_kernel`): the smallest r in [0, r1] with
+// Step 5 (`select_rank_kernel`): the smallest r in [0, min(r1, n)] with
 //   (1 + r/(p-1))^{1/2} (sum_{j>r} sigma^_j^2)^{1/2} <= eps ||A||,
-// sigma^_j = sigma^_{r1} for r1 < j <= n (step 4), in FP64 on one thread.
+// sigma^_j = sigma^_{r1} for r1 < j <= n (step 4), values beyond the n-th zero,
+// in FP64 on one thread.
 //
 // Step 7 by sketch-to-precondition (the randomized approximate orthogonalization
 // of Sec. 4): the core Y (A X_k) is a sketch of A X_k, so with R_s its triangular
@@ -34,13 +35,15 @@ __global__ void select_rank_kernel(const double* __restrict__ sig, int r1, int64
                                    int p, int s, QbSelect* __restrict__ out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double ref = norm_a > 0.0 ? norm_a : (r1 > 0 ? sig[0] : 0.0);
-    const double last = r1 > 0 ? sig[r1 - 1] : 0.0;
-    // T(r) = sum_{j>r} sigma^_j^2, accumulated from the tail: T(r1) = (n - r1) sigma^_{r1}^2
-    double T = (n > r1 ? (double)(n - r1) : 0.0) * last * last;
+    // A has only n singular values: a sketch wider than n trusts at most n of them
+    const int re = (int)(n < (int64_t)r1 ? n : (int64_t)r1);
+    const double last = re > 0 ? sig[re - 1] : 0.0;
+    // T(r) = sum_{j>r} sigma^_j^2, accumulated from the tail: T(re) = (n - re) sigma^_{re}^2
+    double T = (double)(n - re) * last * last;
     int best = -1;
     double best_bound = 0.0;
-    for (int r = r1; r >= 0; --r) {
-        if (r < r1) T += sig[r] * sig[r];
+    for (int r = re; r >= 0; --r) {
+        if (r < re) T += sig[r] * sig[r];
         const double bound = sqrt(1.0 + (double)r / (p - 1.0)) * sqrt(T);
         if (bound <= eps * ref) {
             best = r;                     // walking down: the last hit is the smallest r

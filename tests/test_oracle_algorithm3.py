@@ -124,3 +124,15 @@ def test_qb_ladder_end_and_norm_override():
     r_default = a3.qb(B, 1e-3, p=5, seed=4).r
     r_loose = a3.qb(B, 1e-3, p=5, seed=4, norm_a=10.0 * float(sig[0])).r
     assert r_loose < r_default
+
+
+def test_qb_sketch_wider_than_the_matrix():
+    # n = 20 columns, sketch widths up to 32: A has only 20 singular values, so the
+    # values beyond the 20th count as zero and r never exceeds n; the exact rank 20
+    # meets any tolerance and k = min(r + p, n) = 20
+    A = np.random.default_rng(3).standard_normal((200, 20))
+    for eps in (1e-9, 1e-15):
+        res = a3.qb(A, eps, p=5, seed=2)
+        assert res.met and res.r == 20 and res.k == 20 and res.final_s == 32
+    assert a3.select_rank(np.array([1.0, 0.5, 1e-15, 1e-15]), 2, 1e-16, 5) == 2
+    assert np.linalg.norm(A - res.Q @ res.B) <= 1e-12 * np.linalg.norm(A)
