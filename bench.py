@@ -305,8 +305,8 @@ def main():
                 "peak_source": f"{src} hbm_gbs",
                 "tensor_tflops_achieved": right_tflops if args.precision == "bf16x3" else None}
     # DRAM bytes per launch from an ncu capture of this kernel (dram__bytes_read.sum +
-    # dram__bytes_write.sum on a 16384x16384 launch, profiles/right_tc_kernel_16384x16384.md),
-    # expressed per algorithmic byte and scaled to this launch; only for the kernel it was taken on
+    # dram__bytes_write.sum on a 16384x16384 launch), expressed per algorithmic byte and
+    # scaled to this launch; only for the kernel it was taken on
     roof["traffic"] = (TC_TRAFFIC_PER_ALGO_BYTE * st.right_bytes / max(st.right_launches, 1)
                        if args.precision == "bf16x3" and args.kind == "gaussian" else None)
     roof["algorithmic_bytes_per_launch"] = st.right_bytes / max(st.right_launches, 1)

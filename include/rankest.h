@@ -348,6 +348,9 @@ int re_mlp_features(re_handle h, const void* A, int dtype, int64_t m, int64_t n,
  *   lives in one 16 MiB static device array that every GPU loading the library
  *   holds until exit; calls needing more (about min(m,n)*s + 2(col0+s)*s*splits
  *   floats > 4 Mi) return RE_ERR_ARG.
+ *   The kernels run on the device that holds A (the current device is restored
+ *   on return); AX and core must be device memory of that same device, else
+ *   RE_ERR_ARG.
  *   The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress); make that first call before any stream capture.
  *   All calls share the array: calls that overlap on the GPU race on it and must

@@ -22,7 +22,8 @@ Readings taken here (the CUDA path takes the same ones):
 * r ranges over 0 .. min(r1, n) (r = 0 when even the whole estimated tail is
   below eps ||A||); the tail beyond r1 counts n - r1 copies of sigma^_{r1}, n
   the smaller dimension, and sketched values beyond the n-th count as zero.
-  r + p must not exceed the width s; otherwise s doubles.
+  k = min(r + p, n) must not exceed the width s; otherwise s doubles (when r + p
+  exceeds n, the n columns of a sketch at least n wide already factor A).
 * When the ladder cannot grow, the largest factorization it has (k = s, at
   most n) is returned with ``met = False`` and r = k - p.
 * m < n: the factorization is of A^T (Q spans the column space of A^T).
@@ -94,7 +95,9 @@ def qb(A: np.ndarray, eps: float, p: int = 10, seed: int = 0, s0: int = 8, s_max
         r1 = alg.r1_of_s(s)
         sig = alg.sketched_sigma(A64, s, alg.GAUSSIAN, seed)[:r1]
         r = select_rank(sig, n, eps, p, norm_a)
-        met = r is not None and r + p <= s
+        # k = min(r + p, n) columns factor A exactly once the sketch covers all n
+        # singular values: the criterion is met when those k columns are sketched
+        met = r is not None and min(r + p, n) <= s
         if met or 2 * s > cap or r1 >= n:
             break
         s *= 2

@@ -51,7 +51,10 @@ __global__ void select_rank_kernel(const double* __restrict__ sig, int r1, int64
         }
     }
     out->r = best;
-    out->met = (best >= 0 && best + p <= s) ? 1 : 0;
+    // k = min(r + p, n) columns factor A exactly once the sketch covers all n
+    // singular values, so the criterion is met when those k columns are sketched
+    const int64_t k = (int64_t)best + p < n ? (int64_t)best + p : n;
+    out->met = (best >= 0 && k <= s) ? 1 : 0;
     out->bound = best_bound;
     out->norm_a = ref;
 }

@@ -359,9 +359,21 @@ def re_rank_estimate_kernel_blocks(h: int, points, eps: float, seed: int = 0, si
 
 
 def re_sketch_apply_noalloc(A, col0: int, s: int, seed: int, AX, core=None, stream=None) -> None:
-    """Gaussian sketch step without device allocation (static 16 MiB scratch, no handle)."""
+    """Gaussian sketch step without device allocation (static 16 MiB scratch, no handle).
+    A (FP32 or FP64), AX (FP32) and core (FP64, optional) must be CUDA tensors of one device."""
+    import torch
     m, n = A.shape
-    assert A.stride(1) == 1 and AX.stride(1) == 1
+    if AX.dtype != torch.float32:
+        raise ValueError("AX must be float32")
+    if core is not None and core.dtype != torch.float64:
+        raise ValueError("core must be float64")
+    for name, t in (("A", A), ("AX", AX), ("core", core)):
+        if t is not None and t.device.type != "cuda":
+            raise ValueError(f"{name} must be a CUDA tensor")
+    if AX.device != A.device or (core is not None and core.device != A.device):
+        raise ValueError("A, AX and core must be on the same device")
+    if A.stride(1) != 1 or AX.stride(1) != 1 or (core is not None and core.stride(1) != 1):
+        raise ValueError("A, AX and core must be row-major (unit column stride)")
     if AX.shape[0] < max(m, n) or AX.shape[1] < col0 + s:
         raise ValueError(f"AX must be at least {max(m, n)} x {col0 + s}, got {tuple(AX.shape)}")
     if core is not None and (core.shape[0] < 2 * (col0 + s) or core.shape[1] < col0 + s):

@@ -92,3 +92,16 @@ def test_binding_layout_matches_header(tmp_path):
             assert getattr(cls, f).offset == c[f"{s}.{f}"], (s, f)
     for name in consts:
         assert getattr(rankest, name) == c[name], name
+
+
+def test_noalloc_binding_rejects_wrong_dtypes_and_devices():
+    """The allocation-free binding checks dtypes and devices before any C call
+    (CPU tensors are never passed to the library)."""
+    import torch
+    A = torch.zeros(64, 32)
+    with pytest.raises(ValueError, match="float32"):
+        rankest.re_sketch_apply_noalloc(A, 0, 8, 1, torch.zeros(64, 8, dtype=torch.float64))
+    with pytest.raises(ValueError, match="float64"):
+        rankest.re_sketch_apply_noalloc(A, 0, 8, 1, torch.zeros(64, 8), torch.zeros(16, 8))
+    with pytest.raises(ValueError, match="CUDA"):
+        rankest.re_sketch_apply_noalloc(A, 0, 8, 1, torch.zeros(64, 8), torch.zeros(16, 8, dtype=torch.float64))

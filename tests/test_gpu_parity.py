@@ -16,6 +16,8 @@ from oracle import rng
 from paper_2105_07388_gb300 import rankest as rk
 from paper_2105_07388_gb300 import workloads as wl
 
+from rankcheck import decision_consistent, desiderata_hold
+
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
@@ -35,15 +37,6 @@ def h():
 
 def dev(a, dtype=torch.float32):
     return torch.as_tensor(np.ascontiguousarray(a)).to(dtype).cuda()
-
-
-def ranks_agree(gpu_rank, orc, tol):
-    """Ranks equal, or the oracle has a trusted sigma within tol of its threshold
-    (then both answers are legitimate: the decision is within FP32 noise)."""
-    if gpu_rank == orc.rank:
-        return True
-    tau = orc.sigma[0] * orc._eps
-    return bool(np.any(np.abs(orc.sigma - tau) <= tol))
 
 
 def oracle_estimate(A, eps, kind, seed, **kw):
@@ -238,11 +231,11 @@ def check_estimate(h, A_host, eps, kind, seed, dtype=torch.float32, exact=True, 
     assert res.final_s == orc.final_s or not exact
     n = min(len(sig), len(orc.sigma))
     assert np.max(np.abs(sig[:n] - orc.sigma[:n])) <= SIGMA_TOL * orc.sigma[0]
-    tol = SIGMA_TOL * orc.sigma[0]
     if exact:
         assert res.rank == orc.rank
     else:
-        assert ranks_agree(res.rank, orc, tol)
+        assert decision_consistent(res.rank, res.final_s, sig, A_used, eps, kind, seed,
+                                   converged=bool(res.flags & rk.RE_CONVERGED), **kw), (res.rank, orc.rank)
     assert bool(res.flags & rk.RE_CONVERGED) == orc.converged
     assert bool(res.flags & rk.RE_TRANSPOSED) == orc.transposed
     return res, orc
@@ -338,11 +331,16 @@ def test_batched_kernel_blocks(h):
     blocks = [wl.kernel_block(m, n, seed=100 + i).cuda() for i, (m, n) in enumerate(shapes)]
     res, sig = rk.re_rank_estimate_batched(h, blocks, 1e-6, rk.RE_GAUSSIAN, 500, sigma_cap=512)
     for i, B in enumerate(blocks):
-        orc = oracle_estimate(B.double().cpu().numpy(), 1e-6, alg.GAUSSIAN, 500 + i)
+        Ah = B.double().cpu().numpy()
+        orc = oracle_estimate(Ah, 1e-6, alg.GAUSSIAN, 500 + i)
         assert res[i].status == 0
-        n = min(res[i].n_sigma, len(orc.sigma))
-        assert np.max(np.abs(sig[i, :n] - orc.sigma[:n])) <= SIGMA_TOL * orc.sigma[0]
-        assert ranks_agree(res[i].rank, orc, SIGMA_TOL * orc.sigma[0])
+        if res[i].final_s == orc.final_s:
+            n = min(res[i].n_sigma, len(orc.sigma))
+            assert np.max(np.abs(sig[i, :n] - orc.sigma[:n])) <= SIGMA_TOL * orc.sigma[0]
+        k = res[i].n_sigma
+        assert decision_consistent(res[i].rank, res[i].final_s, sig[i, :k], Ah, 1e-6, alg.GAUSSIAN, 500 + i,
+                                   converged=bool(res[i].flags & rk.RE_CONVERGED)), (i, res[i].rank, orc.rank)
+        assert desiderata_hold(res[i].rank, Ah, 1e-6)
 
 
 # ---------------------------------------------------------------------------

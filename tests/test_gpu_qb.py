@@ -101,3 +101,24 @@ def test_qb_errors(h):
     with pytest.raises(rk.RankEstError) as e:
         rk.re_rank_estimate_qb(h, A, 1e-3, p=1)
     assert e.value.code == rk.RE_ERR_ARG
+
+
+@pytest.mark.parametrize("m,n,p,eps,s_max,final_s", [
+    (200, 20, 5, 1e-9, 512, 32),       # r1(32) = 29 > n: the values beyond the 20th count as zero
+    (200, 20, 5, 1e-15, 512, 32),
+    (600, 450, 100, 1e-12, 512, 512),  # r + p = 550 > s, but k = min(r + p, n) = 450 <= s
+])
+def test_qb_sketch_wider_than_the_matrix(h, m, n, p, eps, s_max, final_s):
+    """The step-5 selection once the sketch trusts more values than A has (n <
+    r1): r = n meets any tolerance, k = min(r + p, n), as in the oracle."""
+    A = np.random.default_rng(m + n).standard_normal((m, n)).astype(np.float32)
+    A64 = A.astype(np.float64)
+    res, Q, B = rk.re_rank_estimate_qb(h, torch.from_numpy(A).cuda(), eps, p=p, seed=2)
+    orc = a3.qb(A64, eps, p=p, seed=2, s_max=s_max)
+    assert orc.met and orc.r == n and orc.k == n and orc.final_s == final_s
+    assert res.status == 0 and res.flags & rk.RE_CONVERGED
+    assert (res.r, res.k, res.final_s) == (orc.r, orc.k, orc.final_s)
+    Qg, Bg = Q.double().cpu().numpy(), B.double().cpu().numpy()
+    nrm = np.linalg.norm(A64)
+    assert np.linalg.norm(A64 - Qg @ Bg) <= 1e-5 * nrm
+    assert np.linalg.norm(A64 - orc.Q @ orc.B) <= 1e-12 * nrm

@@ -136,3 +136,13 @@ def test_qb_sketch_wider_than_the_matrix():
         assert res.met and res.r == 20 and res.k == 20 and res.final_s == 32
     assert a3.select_rank(np.array([1.0, 0.5, 1e-15, 1e-15]), 2, 1e-16, 5) == 2
     assert np.linalg.norm(A - res.Q @ res.B) <= 1e-12 * np.linalg.norm(A)
+
+
+def test_qb_met_when_the_sketch_covers_every_singular_value():
+    # n = 450 < r1(512) = 465: the sketch holds all 450 singular values, r = 450 meets
+    # any tolerance, and k = min(r + p, n) = 450 columns (not r + p = 550) factor A
+    # exactly, so the criterion counts as met at s = 512 although r + p > s
+    A = np.random.default_rng(5).standard_normal((600, 450))
+    res = a3.qb(A, 1e-12, p=100, seed=4, s_max=512)
+    assert res.met and res.r == 450 and res.k == 450 and res.final_s == 512
+    assert np.linalg.norm(A - res.Q @ res.B) <= 1e-12 * np.linalg.norm(A)
