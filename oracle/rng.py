@@ -19,8 +19,11 @@ Specification (the CUDA side follows the same text):
   logarithm (the atanh series ln f = 2 atanh((f-1)/(f+1)) after reducing f to
   [sqrt(1/2), sqrt(2))) and project-written sine/cosine (Taylor polynomials on a
   quarter period).  Two 32-bit words give two normals; the result is rounded to
-  BF16 (round to nearest even) and |z| < 2^-14 is flushed to +0, so every entry
-  is exact in BF16, FP16, FP32 and FP64.
+  BF16 (round to nearest even) and then to the nearest multiple of 2^-13 (ties to
+  even, zero as +0).  Values of magnitude >= 2^-6 are BF16 multiples of 2^-13
+  already, so the second rounding moves only smaller values, by at most 2^-14.
+  Every entry is then an integer multiple of 2^-13 below 6 in magnitude (a
+  16-bit fixed-point number), exact in BF16, FP16, FP32 and FP64.
 * Gaussian X (n x s, unscaled G): entry (k, j) is normal t = j mod 4 of
   Philox((k, j div 4, STREAM_GX, 0)).  Gaussian Y (r2 x m, unscaled G): entry
   (q, i) is normal t = q mod 4 of Philox((i, q div 4, STREAM_GY, 0)).  Column j of
@@ -156,19 +159,27 @@ def sincos_quarter_f32(theta: np.ndarray):
     return s, c_
 
 
-def round_bf16_flush(z: np.ndarray) -> np.ndarray:
-    """Round binary32 to the nearest BF16 (ties to even); |z| < 2^-14 -> +0."""
+def round_bf16(z: np.ndarray) -> np.ndarray:
+    """Round binary32 to the nearest BF16 (ties to even), as binary32."""
     z = np.asarray(z, dtype=np.float32)
     bits = z.view(np.uint32).astype(np.uint64)
     lsb = (bits >> np.uint64(16)) & np.uint64(1)
     bits = ((bits + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)).astype(np.uint32)
-    r = bits.view(np.float32).copy()
-    r[np.abs(r) < _f(2.0 ** -14)] = _f(0.0)
+    return bits.view(np.float32).copy()
+
+
+def round_normal(z: np.ndarray) -> np.ndarray:
+    """Round binary32 to BF16 (ties to even), then to the nearest multiple of
+    2^-13 (ties to even; zero as +0)."""
+    r = round_bf16(z)
+    t = (np.round(r.astype(np.float64) * 8192.0) / 8192.0).astype(np.float32)   # numpy rounds ties to even
+    r = np.where(np.abs(r) < _f(2.0 ** -6), t, r).astype(np.float32)
+    r[r == 0] = _f(0.0)
     return r
 
 
 def box_muller_bf16(a: np.ndarray, b: np.ndarray):
-    """Two BF16-exact standard normals from two uint32 words (Box-Muller)."""
+    """Two standard normals (BF16-exact multiples of 2^-13) from two uint32 words (Box-Muller)."""
     a = np.asarray(a, dtype=np.uint32)
     b = np.asarray(b, dtype=np.uint32)
     u1 = ((a >> np.uint32(8)).astype(np.float32) + _ONE) * _TWO_M24     # (0, 1]
@@ -186,7 +197,7 @@ def box_muller_bf16(a: np.ndarray, b: np.ndarray):
     sin_phi = np.select([q == 0, q == 1, q == 2], [s, c, -s], -c).astype(np.float32)
     z0 = (r * cos_phi).astype(np.float32)
     z1 = (r * sin_phi).astype(np.float32)
-    return round_bf16_flush(z0), round_bf16_flush(z1)
+    return round_normal(z0), round_normal(z1)
 
 
 def normals4(c0, c1, stream: int, seed: int):

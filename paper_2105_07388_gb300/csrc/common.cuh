@@ -14,7 +14,12 @@
 //    u2 = (b>>8) 2^-24, r = sqrt(-2 ln u1), angle 2 pi u2 split into a quadrant
 //    and theta in [0, pi/2); ln by the atanh series after reducing the mantissa
 //    to [sqrt(1/2), sqrt(2)), sin/cos by Taylor polynomials (own code, not a
-//    libm); result rounded to BF16 (nearest even), |z| < 2^-14 -> +0.
+//    libm); result rounded to BF16 (nearest even) and then to the nearest
+//    multiple of 2^-13 (ties to even; zero is +0).  Values of magnitude >= 2^-6
+//    are BF16 multiples of 2^-13 already, so the second rounding moves only values
+//    below 2^-6, by at most 2^-14; every normal is then an integer multiple of
+//    2^-13 below 6 in magnitude (16-bit fixed point, exact in BF16 and FP16), which
+//    splits exactly into two 8-bit pieces on the grids 2^-5 and 2^-13.
 //  * X(k, j) = normal (j mod 4) of Philox(k, j/4, 1, 0); Y(q, i) = normal (q mod 4)
 //    of Philox(i, q/4, 2, 0); SRTT sign d_j = bit (j mod 128) of
 //    Philox(j/128, 0, stream, 0) (stream 3 right, 5 left); sampled index
@@ -115,11 +120,14 @@ __device__ __forceinline__ void sincos_quarter(float th, float& s, float& c) {
     c = fadd(fmul(pc, t2), 1.0f);
 }
 
-__device__ __forceinline__ float round_bf16_flush(float z) {
+__device__ __forceinline__ float round_normal(float z) {
     uint32_t b = __float_as_uint(z);
     b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
     const float r = __uint_as_float(b);
-    return fabsf(r) < 0x1p-14f ? 0.0f : r;
+    if (fabsf(r) >= 0x1p-6f) return r;
+    // |r| < 2^-6: 1536 + r lies in [1024, 2048), whose spacing is 2^-13, so the sum
+    // rounds r to the 2^-13 grid (ties to even) and the difference is exact (+0 for 0)
+    return __fsub_rn(__fadd_rn(r, 1536.0f), 1536.0f);
 }
 
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
@@ -142,8 +150,8 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
     } else {
         cp = s; sp = -c;
     }
-    z0 = round_bf16_flush(fmul(r, cp));
-    z1 = round_bf16_flush(fmul(r, sp));
+    z0 = round_normal(fmul(r, cp));
+    z1 = round_normal(fmul(r, sp));
 }
 
 // The four normals of Philox((c0, c1, stream, 0)).

@@ -70,3 +70,10 @@ def test_features_formula():
     assert np.isclose(f[0], 4.0) and np.isclose(f[14], 3.0) and np.isclose(f[16], 4.0)
     assert np.isclose(f[17], (f[13] - f[7]) / 6.0)
     assert np.allclose(np.diff(f[:14]), -6 / 15)
+
+
+def test_mlp_bf16_rounding_ties_to_even():
+    """The network's BF16 weights round to nearest, ties to even (hand-chosen ties)."""
+    src = np.array([0x3F808000, 0x3F818000, 0x3F808001, 0xBF818000], dtype=np.uint32).view(np.float32)
+    want = np.array([0x3F800000, 0x3F820000, 0x3F810000, 0xBF820000], dtype=np.uint32).view(np.float32)
+    assert np.array_equal(mlp.bf16(src), want.astype(np.float64))

@@ -45,10 +45,44 @@ def test_sincos_against_library():
 
 def test_normals_are_exact_bf16_and_fp16():
     z = rng.gaussian_x(512, 64, seed=5).ravel().astype(np.float32)
-    assert np.array_equal(rng.round_bf16_flush(z), z)
+    assert np.array_equal(rng.round_normal(z), z)
     assert np.array_equal(z.astype(np.float16).astype(np.float32), z)
+    # 16-bit fixed point: integer multiples of 2^-13 below 6 in magnitude
+    k = z.astype(np.float64) * 8192.0
+    assert np.array_equal(k, np.round(k)) and np.max(np.abs(z)) < 6.0
     nz = z[z != 0]
-    assert np.min(np.abs(nz)) >= 2.0 ** -14
+    assert np.min(np.abs(nz)) >= 2.0 ** -13
+
+
+def _bits(x):
+    return np.asarray(x, dtype=np.float32).view(np.uint32)
+
+
+def test_bf16_rounding_ties_to_even():
+    """Hand-chosen ties and near-ties: truncation, round-half-up or
+    round-half-away would each get one of these wrong."""
+    cases = [(0x3F808000, 0x3F800000),    # 1 + 2^-8: tie, even neighbour 1.0 below
+             (0x3F818000, 0x3F820000),    # 1 + 3 2^-8: tie, even neighbour above
+             (0x3F807FFF, 0x3F800000),    # just below the tie
+             (0x3F808001, 0x3F810000),    # just above the tie
+             (0xBF808000, 0xBF800000),    # -(1 + 2^-8): tie, magnitude down
+             (0xBF818000, 0xBF820000),    # -(1 + 3 2^-8): tie, magnitude up
+             (0x477F8000, 0x47800000)]    # 65280 + 128: tie, carries into the exponent
+    src = np.array([c[0] for c in cases], dtype=np.uint32).view(np.float32)
+    want = np.array([c[1] for c in cases], dtype=np.uint32)
+    assert np.array_equal(_bits(rng.round_bf16(src)), want)
+
+
+def test_grid_rounding_ties_to_even():
+    """Below 2^-6 the normal goes to the 2^-13 grid, ties to the even multiple;
+    zero comes out as +0; from 2^-6 on nothing moves."""
+    u = 2.0 ** -13
+    src = np.array([0.5 * u, 1.5 * u, 2.5 * u, 0.75 * u, -0.5 * u, -1.5 * u, -0.25 * u,
+                    2.0 ** -6, -(2.0 ** -6) * 1.5, 3.0], dtype=np.float32)
+    want = np.array([0.0, 2 * u, 2 * u, u, 0.0, -2 * u, 0.0, 2.0 ** -6, -(2.0 ** -6) * 1.5, 3.0],
+                    dtype=np.float32)
+    got = rng.round_normal(src)
+    assert np.array_equal(_bits(got), _bits(want))      # bitwise: the zeros are +0
 
 
 def test_normal_distribution():
