@@ -72,6 +72,18 @@ extern "C" {
 /* arithmetic of the Gaussian right sketch */
 #define RE_PREC_FP32 0   /* FP32 FMA on CUDA cores */
 #define RE_PREC_BF16X3 1 /* A split into three BF16 terms, tensor cores (tcgen05), FP32 accumulation */
+/* Exact products and exact sums on the tensor cores: A (and A X for the left
+ * sketch) cut into five 8-bit digits per entry relative to a power-of-two bound of
+ * its row, the normals of X and Y into two (they are 16-bit fixed point), the
+ * digit products summed exactly in FP32 accumulators over segments and in int64
+ * across them; A X and Y A X are then exact up to one rounding at 2^-40 of their
+ * rows' scale, and the core's singular values come from a preconditioned FP32
+ * Jacobi (W = core V1 formed in FP64 from the FP32 right singular vectors V1, its
+ * graded columns taken with a purely relative rotation test).  Resolves sketched
+ * values down to about 1e-11 sigma_1 (Algorithm 1 at eps = 1e-8 on the
+ * ten-decade spectra of Sec. 6).  Gaussian X and Y, FP32 A with m >= n, 16-byte
+ * aligned rows and min(m, n) <= 2^20; other inputs give RE_ERR_UNSUPPORTED. */
+#define RE_PREC_EXACT 2
 
 /* result flags */
 #define RE_CONVERGED 1u        /* some trusted sigma^_{i+1} <= eps ||A|| was found */
@@ -210,6 +222,20 @@ int re_rank_estimate_host(re_handle h, const void* A_host, int dtype, int64_t m,
 int re_sketch_apply(re_handle h, const void* A, int dtype, int64_t m, int64_t n, int64_t ld,
                     int col0, int s, int sketch_kind, uint64_t seed,
                     float* AX, int64_t ld_ax, double* core, int64_t ld_core, void* stream);
+
+/*
+ * re_sketch_apply for the exact-product precision mode (RE_PREC_EXACT, whatever
+ * the handle's opts): Gaussian X and Y, FP32 A (m >= n, 16-byte aligned rows).
+ *   AX   device FP64, rows x ld_ax row-major: columns col0 .. col0+s-1 receive the
+ *        unscaled A*G[:, col0:col0+s], exact up to one rounding at 2^-40 of each
+ *        row's power-of-two bound (then rounded to FP64).  When core is given,
+ *        columns < col0 must hold the earlier columns (from this call's seed).
+ *   core optional device FP64 as in re_sketch_apply (leading 2(col0+s) x (col0+s)
+ *        block: Y[0:2(col0+s)] * A * X[:, 0:col0+s], exact to the same rounding).
+ * col0 and s are multiples of 8, col0 + s <= 512.  Synchronises `stream`.
+ */
+int re_sketch_apply_exact(re_handle h, const float* A, int64_t m, int64_t n, int64_t ld, int col0, int s,
+                          uint64_t seed, double* AX, int64_t ld_ax, double* core, int64_t ld_core, void* stream);
 
 /*
  * Step 7 alone: the singular values of a device FP64 r2 x s matrix (row-major,

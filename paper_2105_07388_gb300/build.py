@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librankest.so")
 
-SOURCES = ["api.cu", "embed.cu", "sketch_simt.cu", "sketch_srht.cu", "sketch_tc.cu",
+SOURCES = ["api.cu", "embed.cu", "sketch_simt.cu", "sketch_srht.cu", "sketch_tc.cu", "sketch_ex.cu",
            "core_svd.cu", "noalloc.cu", "batched.cu", "mlp.cu", "left_tc.cu", "batched_tc.cu", "left_fwht.cu",
            "rangefinder.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -54,6 +54,12 @@ struct re_handle_ {
     std::vector<cudaEvent_t> event_pool;
     DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status, ht, fz;
     DevBuf qbws, qbsel;                 // Algorithm 3: factorization workspace, selection record
+    // precision mode (exact-product sketches): row exponents of A, digit slices of X
+    // and Y, int64 accumulators of the right and left sketches, A X as FP32 pair planes
+    // (transposed) with column exponents, and the precise singular-value scratch
+    DevBuf ex_rexp, ex_xd, ex_tr, ex_hi, ex_lo, ex_cexp, ex_yd, ex_tc, ex_svd;
+    int64_t ex_ldp = 0, ex_ldy = 0;     // plane and Y-digit leading dimensions
+    int ex_cap = 0;                     // width capacity of the exact buffers
     void* cublas = nullptr;             // cublasHandle_t, created on first use (Algorithm 3's GEMMs)
     re::BatchedState* batched = nullptr;
     // sketch-size proposal network: parameters, Adam moments, gradient, scratch
@@ -215,10 +221,136 @@ struct Step {
     re::DevReadoff ro{};
 };
 
+// ---- precision mode: exact-product sketches (sketch_ex.cu) ----------------------
+bool exact_mode(re_handle h, const Plan& P) { return h->opts.precision == RE_PREC_EXACT && P.kind == RE_GAUSSIAN; }
+
+// Buffers of the exact path for widths up to cap, and the row exponents of A
+// (one read of A; Inf/NaN and entries of 2^126 or more are reported here).
+int exact_prepare(re_handle h, const Plan& P, int cap, cudaStream_t st) {
+    const re::MatView& A = P.A;
+    if (A.dtype != RE_F32 || A.trans || (A.ld % 4) != 0 || (reinterpret_cast<uintptr_t>(A.ptr) & 15) != 0)
+        return fail(RE_ERR_UNSUPPORTED,
+                    "the exact-product precision mode takes FP32 A with m >= n and 16-byte aligned rows");
+    if (A.cols > (int64_t(1) << 20)) return fail(RE_ERR_UNSUPPORTED, "the exact-product precision mode takes min(m, n) <= 2^20");
+    if (P.ykind != RE_GAUSSIAN) return fail(RE_ERR_UNSUPPORTED, "the exact-product precision mode takes a Gaussian Y");
+    const int64_t M = A.rows, Kc = A.cols;
+    const int64_t kpad = (Kc + 63) / 64 * 64;
+    cap = std::max(cap, 16);
+    const int cap16 = (cap + 15) / 16 * 16;
+    h->ex_ldp = (M + 3) / 4 * 4;
+    h->ex_ldy = (M + 63) / 64 * 64;
+    h->ex_cap = cap;
+    if (int r = ensure(h->ex_rexp, sizeof(int) * (size_t)M)) return r;
+    if (int r = ensure(h->ex_xd, sizeof(uint16_t) * 2 * (size_t)cap16 * kpad)) return r;
+    if (int r = ensure(h->ex_tr, sizeof(long long) * (size_t)M * cap)) return r;
+    if (int r = ensure(h->ex_hi, sizeof(float) * (size_t)cap * h->ex_ldp)) return r;
+    if (int r = ensure(h->ex_lo, sizeof(float) * (size_t)cap * h->ex_ldp)) return r;
+    if (int r = ensure(h->ex_cexp, sizeof(int) * (size_t)cap)) return r;
+    if (int r = ensure(h->ex_yd, sizeof(uint16_t) * 2 * (size_t)(2 * cap) * h->ex_ldy)) return r;
+    if (int r = ensure(h->ex_tc, sizeof(long long) * (size_t)cap * (2 * cap))) return r;
+    if (int r = ensure(h->ex_svd, re::svd_precise_bytes(2 * cap, cap))) return r;
+    if (int r = ensure(h->status, 64)) return r;
+    int* flag = static_cast<int*>(h->status.p) + 4;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    cudaEvent_t g = stage_begin(h, st);
+    if (e == cudaSuccess)
+        e = re::launch_row_exponent(static_cast<const float*>(A.ptr), A.ld, M, Kc, static_cast<int*>(h->ex_rexp.p),
+                                    flag, st);
+    stage_end(h, st, g, kStageOther);
+    int hf = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "row exponents");
+    h->stats.launches += 1;
+    if (hf & 1) return fail(RE_ERR_NONFINITE, "non-finite values in A");
+    if (hf & 2) return fail(RE_ERR_UNSUPPORTED, "entries of magnitude 2^126 or more are outside the precision mode");
+    return RE_OK;
+}
+
+// Exact right sketch of columns [c0, c0+cnt): int64 sums, then the FP32 pair planes
+// of A X (and, when V is given, its FP64 values) with the column exponents.
+int right_columns_exact(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, double* V, int64_t ldv,
+                        cudaStream_t st) {
+    const int64_t M = P.A.rows, Kc = P.A.cols, kpad = (Kc + 63) / 64 * 64;
+    if (c0 + cnt > h->ex_cap) return fail(RE_ERR_ARG, "exact sketch width exceeds the prepared capacity");
+    const int q16 = (cnt + 15) / 16 * 16;
+    uint16_t* xd = static_cast<uint16_t*>(h->ex_xd.p);
+    long long* T = static_cast<long long*>(h->ex_tr.p);
+    int* status = static_cast<int*>(h->status.p);
+    cudaEvent_t g = stage_begin(h, st);
+    cudaError_t e = re::launch_normal_digits(seed, re::kStreamGX, Kc, kpad, c0, cnt, xd, kpad, q16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(T, 0, sizeof(long long) * (size_t)M * cnt, st);
+    stage_end(h, st, g, kStageOther);
+    if (e != cudaSuccess) return cuda_fail(e, "X digits");
+    cudaEvent_t a = stage_begin(h, st);
+    int nl = 0;
+    e = re::launch_ex_sketch(static_cast<const float*>(P.A.ptr), nullptr, P.A.ld, M, Kc,
+                             static_cast<const int*>(h->ex_rexp.p), xd, kpad, q16, 0, cnt,
+                             reinterpret_cast<unsigned long long*>(T), cnt, status + 1, st, &nl);
+    if (e != cudaSuccess) return cuda_fail(e, "right sketch (exact products)");
+    stage_end(h, st, a, kStageRight, 4.0 * (double)M * Kc + 4.0 * (double)q16 * Kc + 8.0 * (double)M * cnt,
+              9.0 * 2.0 * (double)M * Kc * cnt);
+    g = stage_begin(h, st);
+    int* cexp = static_cast<int*>(h->ex_cexp.p);
+    e = cudaMemsetAsync(cexp + c0, 0x80, sizeof(int) * (size_t)cnt, st);
+    if (e == cudaSuccess)
+        e = re::launch_ex_finalize(T, cnt, static_cast<const int*>(h->ex_rexp.p), M, cnt,
+                                   static_cast<float*>(h->ex_hi.p) + (size_t)c0 * h->ex_ldp,
+                                   static_cast<float*>(h->ex_lo.p) + (size_t)c0 * h->ex_ldp, h->ex_ldp, V, ldv,
+                                   cexp + c0, st);
+    stage_end(h, st, g, kStageOther);
+    if (e != cudaSuccess) return cuda_fail(e, "A X from the exact sums");
+    h->stats.launches += 3 + nl;
+    return RE_OK;
+}
+
+// Exact left-sketch blocks after A X columns [c0, c1): Y rows [2 c0, 2 c1) x columns
+// [0, c0) and Y rows [0, 2 c1) x columns [c0, c1), FP64 into core.  Y digit rows
+// from y_from on are generated (earlier ones are kept from the previous step).
+int left_blocks_exact(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, double* core, int64_t ld_core,
+                      cudaStream_t st, int y_from) {
+    const int64_t M = P.A.rows, ldy = h->ex_ldy, ldp = h->ex_ldp;
+    const int slice_rows = 2 * h->ex_cap, ldtc = 2 * h->ex_cap;
+    uint16_t* yd = static_cast<uint16_t*>(h->ex_yd.p);
+    long long* Tc = static_cast<long long*>(h->ex_tc.p);
+    const float* hi = static_cast<const float*>(h->ex_hi.p);
+    const float* lo = static_cast<const float*>(h->ex_lo.p);
+    const int* cexp = static_cast<const int*>(h->ex_cexp.p);
+    int* status = static_cast<int*>(h->status.p);
+    cudaEvent_t a = stage_begin(h, st);
+    cudaError_t e = re::launch_normal_digits(seed, re::kStreamGY, M, ldy, y_from, 2 * c1 - y_from,
+                                             yd + (size_t)y_from * ldy, ldy, slice_rows, st);
+    int nl = 1;
+    if (e == cudaSuccess && c0 > 0) {
+        e = cudaMemset2DAsync(Tc + 2 * c0, sizeof(long long) * ldtc, 0, sizeof(long long) * 2 * (c1 - c0), c0, st);
+        if (e == cudaSuccess)
+            e = re::launch_ex_sketch(hi, lo, ldp, c0, M, cexp, yd, ldy, slice_rows, 2 * c0, 2 * (c1 - c0),
+                                     reinterpret_cast<unsigned long long*>(Tc + 2 * c0), ldtc, status + 1, st, &nl);
+        if (e == cudaSuccess)
+            e = re::launch_ex_core_finalize(Tc + 2 * c0, ldtc, cexp, c0, 2 * (c1 - c0), 0, 2 * c0, core, ld_core, st);
+        ++nl;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemset2DAsync(Tc + (size_t)c0 * ldtc, sizeof(long long) * ldtc, 0, sizeof(long long) * 2 * c1, c1 - c0,
+                              st);
+    if (e == cudaSuccess)
+        e = re::launch_ex_sketch(hi + (size_t)c0 * ldp, lo + (size_t)c0 * ldp, ldp, c1 - c0, M, cexp + c0, yd, ldy,
+                                 slice_rows, 0, 2 * c1, reinterpret_cast<unsigned long long*>(Tc + (size_t)c0 * ldtc),
+                                 ldtc, status + 1, st, &nl);
+    if (e == cudaSuccess)
+        e = re::launch_ex_core_finalize(Tc + (size_t)c0 * ldtc, ldtc, cexp, c1 - c0, 2 * c1, c0, 0, core, ld_core, st);
+    ++nl;
+    if (e != cudaSuccess) return cuda_fail(e, "left sketch (exact products)");
+    stage_end(h, st, a, kStageLeft);
+    h->stats.launches += nl;
+    return RE_OK;
+}
+
 // Right sketch columns [c0, c0+cnt) of the oriented A into AX (row-major, ld_ax).
 int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, float* AX,
                   int64_t ld_ax, cudaStream_t st) {
     cudaError_t e;
+    if (exact_mode(h, P)) return right_columns_exact(h, P, seed, c0, cnt, nullptr, 0, st);
     if (P.kind == RE_GAUSSIAN) {
         // the tensor-core kernel writes AX rows with 16-byte stores
         const bool tc = h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && (ld_ax % 4) == 0 &&
@@ -316,6 +448,7 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
 // transforms from column 0 (the caller supplies the earlier AX columns).
 int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const float* AX,
                 int64_t ld_ax, double* core, int64_t ld_core, cudaStream_t st, int transform_from) {
+    if (exact_mode(h, P)) return left_blocks_exact(h, P, seed, c0, c1, core, ld_core, st, 2 * c0);
     const int64_t M = P.A.rows;
     if (int r = ensure(h->status, 64)) return r;
     if (P.ykind == RE_SRHT) {
@@ -374,25 +507,42 @@ int check_width(re_handle h, const Plan& P, int s, int smax, double eps, re::Dev
     // not used there (the certificate compares with sigma_1 of the core)
     const bool skip_ok = may_skip && h->opts.norm_a <= 0.0 && r1c < P.A.cols;
     const float ratio = (float)(4.0 * std::max(eps, 1e-5));
-    cudaError_t e = cudaMemsetAsync(status + 3, 0, sizeof(int), st);
-    if (e != cudaSuccess) return cuda_fail(e, "clear status");
-    cudaEvent_t a = stage_begin(h, st);
-    e = re::launch_core_sigma(core, 2 * s, s, smax, h->svdws.p, static_cast<double*>(h->sigma.p), status, st,
-                              skip_ok ? r1c : 0, ratio);
-    if (e != cudaSuccess) return cuda_fail(e, "core singular values");
-    stage_end(h, st, a, kStageSvd);
     const int r1 = std::min(r1_of_s(s), s);
     // X = G/sqrt(s) or D H S^T/sqrt(s); the HRTT's D (H/sqrt(n_pad)) C^T; Y scaled by 1/sqrt(2s)
     const double xs = P.kind == RE_HRTT ? (double)P.n_pad : (double)s;
     const double scale = 1.0 / std::sqrt(xs * (double)(2 * s));
-    e = re::launch_readoff(static_cast<const double*>(h->sigma.p), r1, scale, eps, h->opts.norm_a, status,
-                           static_cast<re::DevReadoff*>(h->ro.p), static_cast<double*>(h->sigma_scaled.p), st);
-    if (e != cudaSuccess) return cuda_fail(e, "read-off");
-    e = cudaMemcpyAsync(h->h_ro, h->ro.p, sizeof(re::DevReadoff), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "read-off copy");
-    h->stats.launches += 2;
-    resolve_timings(h);
+    // the precision mode takes the preconditioned FP32 singular values (stage 1 is
+    // the plain FP32 step, which may first certify that this width cannot succeed)
+    const bool precise = exact_mode(h, P);
+    bool certify = skip_ok;
+    for (int pass = 0; pass < 2; ++pass) {
+        cudaError_t e = cudaMemsetAsync(status + 3, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "clear status");
+        cudaEvent_t a = stage_begin(h, st);
+        if (precise && !(certify && re::core_sigma_fits_cta(2 * s, s)))
+            e = re::launch_core_sigma_precise(core, 2 * s, s, smax, h->svdws.p, h->ex_svd.p,
+                                              static_cast<double*>(h->sigma.p), status, st);
+        else
+            e = re::launch_core_sigma(core, 2 * s, s, smax, h->svdws.p, static_cast<double*>(h->sigma.p), status, st,
+                                      skip_ok ? r1c : 0, ratio);
+        if (e != cudaSuccess) return cuda_fail(e, "core singular values");
+        stage_end(h, st, a, kStageSvd);
+        e = re::launch_readoff(static_cast<const double*>(h->sigma.p), r1, scale, eps, h->opts.norm_a, status,
+                               static_cast<re::DevReadoff*>(h->ro.p), static_cast<double*>(h->sigma_scaled.p), st);
+        if (e != cudaSuccess) return cuda_fail(e, "read-off");
+        e = cudaMemcpyAsync(h->h_ro, h->ro.p, sizeof(re::DevReadoff), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "read-off copy");
+        h->stats.launches += 2;
+        resolve_timings(h);
+        // a certified width (no Jacobi, tau = 0) needs nothing more; otherwise the
+        // precision mode replaces the FP32 values by the preconditioned ones
+        const bool certified = h->h_ro->rank < 0 && h->h_ro->sweeps == 0 && h->h_ro->tau == 0.0;
+        if (!precise || !certify || certified || h->h_ro->status != RE_OK ||
+            !re::core_sigma_fits_cta(2 * s, s))
+            break;
+        certify = false;
+    }
     *ro = *h->h_ro;
     *r1_out = r1;
     if (ro->status == RE_ERR_TIMEOUT) return fail(ro->status, "a bounded device wait expired");
@@ -448,6 +598,9 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
     {
         cudaError_t e0 = cudaMemsetAsync(h->status.p, 0, 4 * sizeof(int), st);
         if (e0 != cudaSuccess) return cuda_fail(e0, "clear status");
+    }
+    if (exact_mode(h, P)) {
+        if (int r = exact_prepare(h, P, smax, st)) return r;
     }
     auto sketch_to = [&](int c0, int c1) -> int {
         if (int r = right_columns(h, P, seed, c0, c1 - c0, AX, smax, st)) return r;
@@ -527,6 +680,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
 int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* Q, int64_t ldq, float* B,
            int64_t ldb, int k_cap, re_qb_result* out, cudaStream_t st) {
     const re_opts& o = h->opts;
+    if (exact_mode(h, P)) return fail(RE_ERR_UNSUPPORTED, "Algorithm 3 runs with the FP32 or BF16x3 sketch");
     if (o.s0 > P.cap) return fail(RE_ERR_ARG, "initial sketch width exceeds the admissible width");
     int smax = o.s0;
     while (smax * 2 <= P.cap) smax *= 2;
@@ -599,7 +753,7 @@ int check_opts(const re_opts* o) {
     if (o->s0 < 8 || o->s0 % 8 != 0) return fail(RE_ERR_ARG, "s0 must be a positive multiple of 8");
     if (o->s_max < o->s0) return fail(RE_ERR_ARG, "s_max < s0");
     if (o->s_max > 512) return fail(RE_ERR_ARG, "s_max above 512");
-    if (o->precision != RE_PREC_FP32 && o->precision != RE_PREC_BF16X3)
+    if (o->precision != RE_PREC_FP32 && o->precision != RE_PREC_BF16X3 && o->precision != RE_PREC_EXACT)
         return fail(RE_ERR_ARG, "unknown precision");
     if (o->y_kind < -1 || o->y_kind > RE_SRHT) return fail(RE_ERR_ARG, "unknown y_kind");
     if (o->learned != 0 && o->learned != 1) return fail(RE_ERR_ARG, "learned must be 0 or 1");
@@ -660,6 +814,8 @@ int re_destroy(re_handle h) {
     DevBuf* bufs[] = {&h->x, &h->xt, &h->ax, &h->part, &h->core, &h->sigma, &h->sigma_scaled,
                       &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status, &h->ht, &h->fz,
                       &h->qbws, &h->qbsel,
+                      &h->ex_rexp, &h->ex_xd, &h->ex_tr, &h->ex_hi, &h->ex_lo, &h->ex_cexp, &h->ex_yd, &h->ex_tc,
+                      &h->ex_svd,
                       &h->mlp_P, &h->mlp_M, &h->mlp_V, &h->mlp_G, &h->mlp_X, &h->mlp_y,
                       &h->mlp_logits, &h->mlp_keep, &h->mlp_cls, &h->mlp_feat, &h->mlp_loss};
     for (DevBuf* b : bufs) release(*b);
@@ -767,10 +923,51 @@ int re_sketch_apply(re_handle h, const void* A, int dtype, int64_t m, int64_t n,
     if (core && ykind == RE_SRHT && 2 * (int64_t)(col0 + s) > P.m_pad)
         return fail(RE_ERR_ARG, "SRHT left width exceeds the padded dimension");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (exact_mode(h, P))
+        return fail(RE_ERR_UNSUPPORTED, "the exact-product precision mode writes FP64 A X: use re_sketch_apply_exact");
     if (int r = right_columns(h, P, seed, col0, s, AX, ld_ax, st)) return r;
     if (core) {
         if (int r = left_blocks(h, P, seed, col0, col0 + s, AX, ld_ax, core, ld_core, st, 0)) return r;
     }
+    return RE_OK;
+}
+
+int re_sketch_apply_exact(re_handle h, const float* A, int64_t m, int64_t n, int64_t ld, int col0, int s,
+                          uint64_t seed, double* AX, int64_t ld_ax, double* core, int64_t ld_core, void* stream) {
+    if (!h || !AX) return fail(RE_ERR_ARG, "NULL argument");
+    if (col0 < 0 || col0 % 8 != 0 || s <= 0 || s % 8 != 0)
+        return fail(RE_ERR_ARG, "col0 and s must be multiples of 8, s > 0");
+    if (col0 + s > 512) return fail(RE_ERR_ARG, "col0 + s above 512");
+    if (ld_ax < col0 + s) return fail(RE_ERR_ARG, "ld_ax < col0 + s");
+    if (core && ld_core < col0 + s) return fail(RE_ERR_ARG, "ld_core < col0 + s");
+    cudaSetDevice(h->device);
+    Plan P;
+    if (int r = make_plan(A, RE_F32, m, n, ld, RE_GAUSSIAN, RE_GAUSSIAN, 1 << 30, &P)) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int c1 = col0 + s;
+    if (int r = exact_prepare(h, P, c1, st)) return r;
+    if (int r = ensure(h->status, 64)) return r;
+    cudaError_t e = cudaMemsetAsync(h->status.p, 0, 4 * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
+    if (int r = right_columns_exact(h, P, seed, col0, s, AX + col0, ld_ax, st)) return r;
+    if (core) {
+        // the caller's earlier columns of A X become the pair planes of the left sketch
+        if (col0 > 0) {
+            int* cexp = static_cast<int*>(h->ex_cexp.p);
+            e = cudaMemsetAsync(cexp, 0x80, sizeof(int) * (size_t)col0, st);
+            if (e == cudaSuccess)
+                e = re::launch_f64_to_pairs(AX, ld_ax, P.A.rows, col0, static_cast<float*>(h->ex_hi.p),
+                                            static_cast<float*>(h->ex_lo.p), h->ex_ldp, cexp, st);
+            if (e != cudaSuccess) return cuda_fail(e, "earlier columns of A X");
+            h->stats.launches += 2;
+        }
+        if (int r = left_blocks_exact(h, P, seed, col0, c1, core, ld_core, st, 0)) return r;
+    }
+    int tmo = 0;
+    e = cudaMemcpyAsync(&tmo, static_cast<int*>(h->status.p) + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "exact sketch step");
+    if (tmo) return fail(RE_ERR_TIMEOUT, "a bounded device wait expired");
     return RE_OK;
 }
 

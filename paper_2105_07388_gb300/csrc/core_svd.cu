@@ -376,7 +376,8 @@ template <int NV, int E>
 __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     const double* __restrict__ core, int r2, int s, int64_t ld, int64_t core_stride,
     double* __restrict__ sigma, int64_t sigma_stride, int* __restrict__ status,
-    const int* __restrict__ active, int cert_r1, float cert_ratio) {
+    const int* __restrict__ active, int cert_r1, float cert_ratio, float* __restrict__ vout,
+    double* __restrict__ vnorm, int rel_only) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (active && !active[blockIdx.x]) return;
     core += (int64_t)blockIdx.x * core_stride;
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
             if (lane == 0) s_red[0] = v;
         }
         __syncthreads();
-        const float floor_abs = kAbsFloor * s_red[0];
+        const float floor_abs = rel_only ? 0.f : kAbsFloor * s_red[0];
         constexpr int G = 16;
         const int grp = tid / G, ngrp = blockDim.x / G;
         int rotated = 0;
@@ -625,6 +626,12 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     for (int j = warp; j < s; j += nwarps) {
         const double nv = col_norm(Rt + (size_t)j * sp, sp);
         if (lane == 0) s_norm[j] = nv;
+        if (vout) {
+            // right singular vectors of the core: the columns of R^T J, normalised
+            const float inv = nv > 0.0 ? (float)(1.0 / nv) : 0.f;
+            for (int i = lane; i < s; i += 32) vout[(size_t)j * s + i] = Rt[(size_t)j * sp + i] * inv;
+            if (lane == 0) vnorm[j] = nv * up;
+        }
     }
     __syncthreads();
     sort_desc(s_norm, s, up, sigma);
@@ -873,7 +880,8 @@ __host__ __device__ constexpr int jac_g(int nq) { return nq >= 4 ? 16 : 8; }
 
 template <int CL, int NQ>
 __global__ void __launch_bounds__(kJacThreads, 1) core_jacobi_cluster_kernel(
-    const void* ws, int r2, int s, int b, double* __restrict__ sigma, int* __restrict__ status) {
+    const void* ws, int r2, int s, int b, double* __restrict__ sigma, int* __restrict__ status,
+    float* __restrict__ vout, double* __restrict__ vnorm, int rel_only) {
     constexpr int P2 = 2 * CL;
     constexpr int G = jac_g(NQ);                               // lanes per column pair
     constexpr int NVG = 32 * NQ / G;                           // float4 per lane per column
@@ -935,7 +943,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) core_jacobi_cluster_kernel(
         cluster.sync();
         float gm = 0.f;
         for (int r = 0; r < CL; ++r) gm = fmaxf(gm, *cluster.map_shared_rank(&s_fmax, r));
-        const float floor_abs = kAbsFloor * gm;
+        const float floor_abs = rel_only ? 0.f : kAbsFloor * gm;
         int rotated = 0;
         float meas = 0.f;
         for (int t = 0; t < P2 - 1; ++t) {
@@ -1008,6 +1016,13 @@ __global__ void __launch_bounds__(kJacThreads, 1) core_jacobi_cluster_kernel(
         const int c = (sl == 0 ? k : P2 - 1 - k) * b + j;   // a whole sweep returns every block home
         const double nv = col_norm(sets(cur) + (size_t)q * sp, sp);
         if (lane == 0 && c < s) *cluster.map_shared_rank(&s_norm[c], 0) = nv;
+        if (vout && c < s) {
+            // right singular vectors of the core: the columns of R^T J, normalised
+            const float inv = nv > 0.0 ? (float)(1.0 / nv) : 0.f;
+            const float* col = sets(cur) + (size_t)q * sp;
+            for (int i = lane; i < s; i += 32) vout[(size_t)c * s + i] = col[i] * inv;
+            if (lane == 0) vnorm[c] = nv * *g.up;
+        }
     }
     cluster.sync();
     if (k == 0) {
@@ -1072,17 +1087,18 @@ cudaError_t launch_qr_cluster(const double* core, int r2, int s, int64_t ld, voi
 }
 
 template <int CL>
-cudaError_t launch_jacobi_cluster(void* ws, int r2, int s, double* sigma, int* status, cudaStream_t st) {
+cudaError_t launch_jacobi_cluster(void* ws, int r2, int s, double* sigma, int* status, cudaStream_t st, float* vout,
+                                  double* vnorm, int rel_only) {
     int b = 0;
     const size_t smem = jac_cluster_smem(CL, s, &b);
     const void* cws = ws;
     const int nq = (s + 127) / 128;
     if (nq < 1 || nq > 4 || b > kJacThreads / jac_g(nq)) return cudaErrorInvalidValue;   // one lane group per slot-0 column
     switch (nq) {
-        case 1: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 1>, kJacThreads, smem, st, cws, r2, s, b, sigma, status);
-        case 2: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 2>, kJacThreads, smem, st, cws, r2, s, b, sigma, status);
-        case 3: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 3>, kJacThreads, smem, st, cws, r2, s, b, sigma, status);
-        case 4: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 4>, kJacThreads, smem, st, cws, r2, s, b, sigma, status);
+        case 1: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 1>, kJacThreads, smem, st, cws, r2, s, b, sigma, status, vout, vnorm, rel_only);
+        case 2: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 2>, kJacThreads, smem, st, cws, r2, s, b, sigma, status, vout, vnorm, rel_only);
+        case 3: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 3>, kJacThreads, smem, st, cws, r2, s, b, sigma, status, vout, vnorm, rel_only);
+        case 4: return launch_cluster<CL>(core_jacobi_cluster_kernel<CL, 4>, kJacThreads, smem, st, cws, r2, s, b, sigma, status, vout, vnorm, rel_only);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1167,7 +1183,7 @@ size_t svd_workspace_bytes(int r2, int s) { return sizeof(float) * cluster_ws_fl
 namespace {
 
 using CtaKernel = void (*)(const double*, int, int, int64_t, int64_t, double*, int64_t, int*, const int*, int,
-                           float);
+                           float, float*, double*, int);
 
 template <int NV>
 CtaKernel cta_kernel_e(int e) {
@@ -1210,17 +1226,30 @@ cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t
     // takes its warp and group counts from the launch
     const int threads = (count > 1 && s <= 64) ? 512 : kCtaThreads;
     kern<<<count, threads, sm, st>>>(core, r2, s, ld, core_stride, sigma, sigma_stride, status, active,
-                                     cert_r1, cert_ratio);
+                                     cert_r1, cert_ratio, nullptr, nullptr, 0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws, double* sigma,
-                              int* status, cudaStream_t st, int cert_r1, float cert_ratio) {
+namespace {
+
+// The single-core path with the optional outputs of the precision mode: the
+// normalised Jacobi columns (vout, s x s column-major, unsorted) with their
+// norms, and rel_only (no absolute rotation floor).
+cudaError_t core_sigma_one(const double* core, int r2, int s, int64_t ld, void* ws, double* sigma, int* status,
+                           cudaStream_t st, int cert_r1, float cert_ratio, float* vout, double* vnorm,
+                           int rel_only) {
     if (s <= 0) return cudaSuccess;
     if (s > 512) return cudaErrorInvalidValue;
-    if (cta_smem(r2, s) <= kSmemLimit)
-        return launch_core_sigma_batched(core, r2, s, ld, 0, 1, sigma, 0, status, st, nullptr, cert_r1,
-                                         cert_ratio);
+    if (cta_smem(r2, s) <= kSmemLimit) {
+        const size_t sm = cta_smem(r2, s);
+        auto kern = cta_kernel_for((s + 63) / 64, (r2 + 31) / 32);
+        if (!kern) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        kern<<<1, kCtaThreads, sm, st>>>(core, r2, s, ld, 0, sigma, 0, status, nullptr, cert_r1, cert_ratio, vout,
+                                         vnorm, rel_only);
+        return cudaGetLastError();
+    }
     // larger cores: QR on a cluster, then Jacobi on a cluster; ws holds
     // svd_workspace_bytes(r2, s) (16-byte aligned)
     if (!ws) return cudaErrorInvalidValue;
@@ -1230,9 +1259,105 @@ cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, voi
     else return cudaErrorInvalidValue;
     if (e != cudaSuccess) return e;
     int b = 0;
-    if (jac_cluster_smem(8, s, &b) <= kSmemLimit) return launch_jacobi_cluster<8>(ws, r2, s, sigma, status, st);
-    if (jac_cluster_smem(16, s, &b) <= kSmemLimit) return launch_jacobi_cluster<16>(ws, r2, s, sigma, status, st);
+    if (jac_cluster_smem(8, s, &b) <= kSmemLimit)
+        return launch_jacobi_cluster<8>(ws, r2, s, sigma, status, st, vout, vnorm, rel_only);
+    if (jac_cluster_smem(16, s, &b) <= kSmemLimit)
+        return launch_jacobi_cluster<16>(ws, r2, s, sigma, status, st, vout, vnorm, rel_only);
     return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws, double* sigma,
+                              int* status, cudaStream_t st, int cert_r1, float cert_ratio) {
+    return core_sigma_one(core, r2, s, ld, ws, sigma, status, st, cert_r1, cert_ratio, nullptr, nullptr, 0);
+}
+
+namespace {
+
+// perm[rank] = j, ranks by descending vnorm (ties: smaller j first); one CTA.
+__global__ void norm_order_kernel(const double* __restrict__ vnorm, int s, int* __restrict__ perm) {
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+        const long long vb = __double_as_longlong(vnorm[j]);
+        int rank = 0;
+        for (int i = 0; i < s; ++i) {
+            const long long w = __double_as_longlong(vnorm[i]);
+            rank += (w > vb) || (w == vb && i < j);
+        }
+        perm[rank] = j;
+    }
+}
+
+// W = C V(:, perm) in FP64 (C r2 x s row-major with ld; V s x s column-major FP32,
+// exact in FP64): 32 x 32 output tiles, K tiles of 32, four outputs per thread.
+__global__ void __launch_bounds__(256) precond_gemm_kernel(const double* __restrict__ C, int64_t ld, int r2, int s,
+                                                           const float* __restrict__ V, const int* __restrict__ perm,
+                                                           double* __restrict__ W, int64_t ldw) {
+    __shared__ double cs[32][33], vs[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // ty 0..7
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const int jcol = j0 + tx < s ? perm[j0 + tx] : 0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k0 = 0; k0 < s; k0 += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int i = i0 + r, k = k0 + tx;
+            cs[r][tx] = (i < r2 && k < s) ? C[(int64_t)i * ld + k] : 0.0;
+            // vs[k][j]: column perm[j0 + r] of V, row k0 + tx
+            const int jj = j0 + r;
+            vs[tx][r] = (jj < s && k < s) ? (double)V[(size_t)perm[jj] * s + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const double v = vs[k][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fma(cs[ty + 8 * q][k], v, acc[q]);
+        }
+        __syncthreads();
+    }
+    (void)jcol;
+    if (j0 + tx < s)
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + ty + 8 * q;
+            if (i < r2) W[(int64_t)i * ldw + j0 + tx] = acc[q];
+        }
+}
+
+}  // namespace
+
+size_t svd_precise_bytes(int r2, int s) {
+    const size_t v = ((size_t)s * s * sizeof(float) + 255) / 256 * 256;
+    const size_t n = ((size_t)s * sizeof(double) + 255) / 256 * 256;
+    const size_t pm = ((size_t)s * sizeof(int) + 255) / 256 * 256;
+    const size_t w = ((size_t)r2 * s * sizeof(double) + 255) / 256 * 256;
+    return v + n + pm + w;
+}
+
+cudaError_t launch_core_sigma_precise(const double* core, int r2, int s, int64_t ld, void* ws, void* pws,
+                                      double* sigma, int* status, cudaStream_t st) {
+    if (s <= 0) return cudaSuccess;
+    if (s > 512 || !pws) return cudaErrorInvalidValue;
+    char* b = static_cast<char*>(pws);
+    float* V = reinterpret_cast<float*>(b);
+    b += ((size_t)s * s * sizeof(float) + 255) / 256 * 256;
+    double* vnorm = reinterpret_cast<double*>(b);
+    b += ((size_t)s * sizeof(double) + 255) / 256 * 256;
+    int* perm = reinterpret_cast<int*>(b);
+    b += ((size_t)s * sizeof(int) + 255) / 256 * 256;
+    double* W = reinterpret_cast<double*>(b);
+    // stage 1: FP32 QR + Jacobi of the core, keeping its right singular vectors V1
+    cudaError_t e = core_sigma_one(core, r2, s, ld, ws, sigma, status, st, 0, 0.f, V, vnorm, 0);
+    if (e != cudaSuccess) return e;
+    norm_order_kernel<<<1, 512, 0, st>>>(vnorm, s, perm);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // stage 2: W = core V1 in FP64; its columns are graded (nearly sigma_k u_k)
+    dim3 grid((unsigned)((s + 31) / 32), (unsigned)((r2 + 31) / 32));
+    precond_gemm_kernel<<<grid, 256, 0, st>>>(core, ld, r2, s, V, perm, W, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // stage 3: FP32 QR + Jacobi of W with the relative rotation test only
+    return core_sigma_one(W, r2, s, s, ws, sigma, status, st, 0, 0.f, nullptr, nullptr, 1);
 }
 
 cudaError_t launch_readoff(const double* sigma, int r1, double scale, double eps, double norm_a,

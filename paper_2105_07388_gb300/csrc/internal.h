@@ -144,6 +144,36 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
                             int64_t ldc, int* err_flag, cudaStream_t st, int* launches = nullptr,
                             int drop_first = 0);
 
+// ---- exact-product sketches of the precision mode (sketch_ex.cu) --------------
+// e[r] = smallest e with |A[r][k]| < 2^e (0 for a zero row); *status |= 1 for
+// Inf/NaN, |= 2 for an entry of 2^126 or more.
+cudaError_t launch_row_exponent(const float* A, int64_t ld, int64_t M, int64_t K, int* e, int* status,
+                                cudaStream_t st);
+// Two BF16 digit slices of Gaussian normals, K-major: slice t row r at D + (t slice_rows + r) ld,
+// entries k < kpad (zero for k >= kvalid); row r is short index row0 + r of the
+// embedding of `stream` (kStreamGX: X^T rows = X columns; kStreamGY: Y rows).
+cudaError_t launch_normal_digits(uint64_t seed, uint32_t stream, int64_t kvalid, int64_t kpad, int row0, int rows,
+                                 uint16_t* D, int64_t ld, int64_t slice_rows, cudaStream_t st);
+// T[r][q] += exact sum_k P[r][k] Q[q][k] in units of 2^(e_r - 40) (int64, atomics; T
+// must start at zero).  P FP32 row-major (ldp % 4 == 0, 16-byte aligned), or the pair
+// P + P_lo; Q rows q_row0 .. q_row0 + N - 1 of the digit-slice array (ldq % 64 == 0,
+// >= K rounded up to 64).  K <= 2^20.
+cudaError_t launch_ex_sketch(const float* P, const float* P_lo, int64_t ldp, int64_t M, int64_t K, const int* rexp,
+                             const uint16_t* Qd, int64_t ldq, int q_slice_rows, int q_row0, int N,
+                             unsigned long long* T, int64_t ldt, int* err_flag, cudaStream_t st, int* launches);
+// T (M x N, units 2^(rexp[r] - 40)) -> FP32 pair planes of the transpose (row c of the
+// planes = column c, ld ldp; may be NULL), FP64 values V (row-major, ldv; may be NULL)
+// and atomicMax of each column's exponent into cexp (set to INT_MIN-like before).
+cudaError_t launch_ex_finalize(const long long* T, int64_t ldt, const int* rexp, int64_t M, int N, float* Phi,
+                               float* Plo, int64_t ldp, double* V, int64_t ldv, int* cexp, cudaStream_t st);
+// core[q_off + q][c_off + c] = T[c][q] 2^(cexp[c_off + c] - 40) for c < C, q < Q.
+cudaError_t launch_ex_core_finalize(const long long* T, int64_t ldt, const int* cexp, int C, int Q, int c_off,
+                                    int q_off, double* core, int64_t ld_core, cudaStream_t st);
+// FP64 values (row-major M x N, ldv) -> FP32 pair planes of the transpose and column
+// exponents (as launch_ex_finalize).
+cudaError_t launch_f64_to_pairs(const double* V, int64_t ldv, int64_t M, int N, float* Phi, float* Plo, int64_t ldp,
+                                int* cexp, cudaStream_t st);
+
 // ---- small core singular values (core_svd.cu) ----------------------------------
 size_t svd_workspace_bytes(int r2, int s);
 // sigma (FP64, s entries, descending, unscaled) of core (FP64 row-major r2 x s, ld).
@@ -155,6 +185,17 @@ size_t svd_workspace_bytes(int r2, int s);
 cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws,
                               double* sigma, int* status, cudaStream_t st, int cert_r1 = 0,
                               float cert_ratio = 0.f);
+// Precision-mode singular values (sigma descending, unscaled, status as above):
+// the FP32 QR + Jacobi of the core gives right singular vectors V1; W = core V1
+// (columns ordered by decreasing norm) is formed in FP64 and its singular values
+// are taken by the same FP32 QR + Jacobi with a purely relative rotation test.
+// W's columns are graded (about sigma_k u_k), and Householder QR and one-sided
+// Jacobi are column-wise backward stable, so values far below u sigma_1 keep
+// their relative accuracy; sigma(W) = sigma(core) up to the relative
+// non-orthogonality of V1.  pws: svd_precise_bytes(r2, s) of device scratch.
+size_t svd_precise_bytes(int r2, int s);
+cudaError_t launch_core_sigma_precise(const double* core, int r2, int s, int64_t ld, void* ws, void* pws,
+                                      double* sigma, int* status, cudaStream_t st);
 // `count` cores core + i*core_stride (each r2 x s, ld) -> sigma + i*sigma_stride,
 // status[i]; one CTA each (requires core_sigma_fits_cta).
 bool core_sigma_fits_cta(int r2, int s);

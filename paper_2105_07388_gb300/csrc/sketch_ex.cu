@@ -1,0 +1,761 @@
+// Exact-product sketches of the precision mode (RE_PREC_EXACT): the right sketch
+// A*X (Algorithm 1 step 3) and the left sketch Y*(A X) (step 6) on the tcgen05
+// tensor cores with every product exact and every sum exact, the only rounding
+// being one at 2^-40 of the row's power-of-two scale.  This resolves sketched
+// singular values far below the FP32 accumulation floor (about 3e-7 sigma_1),
+// e.g. the eps = 1e-8 read-off on the ten-decade spectra of Sec. 6.
+//
+// One kernel computes D = P * Q^T over a contraction of length K, where
+//   * P (M rows) is FP32 -- or an FP32 pair hi + lo for the left sketch, whose P
+//     is A X -- and each row r has a power-of-two bound |p_rk| < 2^e_r;
+//   * Q (N rows) is given as two BF16 digit slices: the embeddings' normals are
+//     multiples of 2^-13 below 6 in magnitude (the generator's grid rounding),
+//     so g = xi0 + xi1 with xi0 on the 2^-5 grid (|xi0| <= 6) and xi1 = g - xi0
+//     on the 2^-13 grid (|xi1| <= 2^-6), both exact in BF16.
+// The converter warps cut p' = p 2^-e_r (|p'| < 1) into five digits on the grids
+// 2^-8, 2^-16, 2^-24, 2^-32, 2^-40 (delta_0 = n 2^-8 with |n| <= 256, the others
+// |n| <= 129), each exact in BF16, by adding and subtracting 1.5 2^k (exact
+// rounding to a grid); the part of p' below 2^-41 is dropped.  The products
+// delta_s xi_t are then exact, and grouped by level s + t into four TMEM
+// accumulators:
+//   L0 = sum delta_0 xi_0                    multiples of 2^-13
+//   L1 = sum delta_0 xi_1 + delta_1 xi_0     multiples of 2^-21
+//   L2 = sum delta_1 xi_1 + delta_2 xi_0     multiples of 2^-29
+//   R3 = the levels 3 and 4 (delta_2 xi_1, delta_3 xi_0, delta_3 xi_1, delta_4 xi_0)
+// (the level-5 product delta_4 xi_1 is below 2^-46 and dropped).  Each product
+// of L0, L1 and L2 is at most 2^16 of its level's unit, so a partial sum stays an
+// exactly representable FP32 integer multiple of the unit while it is below
+// 2^24 units: the sums are exact, whatever order the tensor core adds them in.
+// Over a segment of 8192 terms the partial sums are random walks (the digits of
+// the embedding are independent of P) with a standard deviation of at most 2^19.5
+// units, so 2^24 is more than 20 standard deviations away.  R3 is rounded by
+// FP32 as it accumulates: at most about 2^-24 sqrt(2048) of a level that is
+// itself about 2^-21 of L0, i.e. near 2^-39 of the result.
+// After each segment the epilogue warps convert the four accumulators to
+// integers in units of 2^-40 (exact for L0..L2, R3 rounded to 2^-40) and add them
+// into an int64 tile in shared memory; at the end of a tile they add that tile
+// into the int64 output with atomic adds -- integer additions, so tiles split
+// between CTAs (stream-K) sum exactly and the result does not depend on the
+// order.  D_rq = T_rq 2^(e_r - 40); |T| < K 2^42.6 fits int64 for K <= 2^20.
+//
+// Warp roles (persistent, one CTA per SM, 128-row P tiles x NT (<= 64) Q rows,
+// K chunks of 64, stream-K over (tile, chunk)):
+//   warps 0-7   converters: warp (q, h) converts, for row 32q + lane, half h
+//               (32 K) of every chunk into five digit slices in TMEM (the MMA's
+//               A operand), three TMEM stages of 5 x 16 columns.
+//   warps 8-11  epilogue: drains the accumulators into the int64 tile.
+//   warp 12     TMA producer of P (FP32 half chunks 128 x 32, 128B swizzle,
+//               zero fill past the edges; the lo plane too in pair mode).
+//   warp 13     TMA producer of the two Q digit slices (NT rows x 64 K each).
+//   warp 14     TMEM allocation; one thread issues 9 tcgen05.mma (M = 128,
+//               N = NT, K = 16, BF16 -> FP32) per K step.
+// TMEM: accumulators at columns [0, 256) (64 per accumulator), A stages from 256.
+// Every mbarrier wait is bounded in time (2 s): on expiry the kernel raises the
+// error flag, every role drains what it has in flight and TMEM is freed.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace re {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;
+constexpr int kNTMax = 64;                 // Q rows per tile (MMA N)
+constexpr int kConvWarps = 8;
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = (kConvWarps + kEpiWarps + 3) * 32;
+constexpr int kPProdWarp = kConvWarps + kEpiWarps;
+constexpr int kQProdWarp = kPProdWarp + 1;
+constexpr int kMmaWarp = kQProdWarp + 1;
+constexpr uint32_t kHalfBytes = kBM * 32 * 4;     // 16 KB FP32 half chunk
+constexpr int kRingMax = 4;                        // FP32 half-chunk ring: 4 slots (2 for pairs)
+constexpr int kAStages = 3;                        // TMEM digit stages (one half chunk each)
+constexpr int kQStages = 3;                        // Q chunk stages
+constexpr uint32_t kAccCols = 64;                  // TMEM columns per accumulator
+constexpr uint32_t kAStageCol = 4 * kAccCols;      // 256
+constexpr uint32_t kAStageCols = 5 * 16;           // five slices x 32 K (16 columns of BF16 pairs)
+constexpr uint32_t kTmemCols = 512;
+constexpr int kSegChunks = 128;                    // 8192 K per exact segment
+constexpr int kTPitch = kBM + 1;                   // int64 tile: column-major, odd pitch
+static_assert(kAStageCol + kAStages * kAStageCols <= kTmemCols, "TMEM budget");
+
+struct ExParams {
+    const int* rexp;          // e_r of every P row (|p_rk| < 2^e_r), -127 <= e_r <= 126
+    int64_t M, K;
+    int N;                    // valid Q rows of this launch (output columns)
+    int NT;                   // MMA N (multiple of 16, <= 64)
+    int ntn;                  // Q tiles
+    int64_t tiles, kchunks;   // tiles = P tiles x Q tiles
+    int q_row0;               // first Q row of this launch inside the slice array
+    int q_slice_rows;         // rows per digit slice in the Q array
+    unsigned long long* T;    // int64 output (M x ldt), added to atomically
+    int64_t ldt;
+    int* err;
+};
+
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+
+// Round to the grid of spacing ulp(c) (c = 1.5 2^k), ties to even: exact when
+// |x| < 2^(k-1).
+__device__ __forceinline__ float grid(float x, float c) { return sub_rn(add_rn(x, c), c); }
+
+// The five digits of p' (|p'| < 1, FP32 exact): delta_0..delta_4.
+__device__ __forceinline__ void digits5(float a, float (&d)[5]) {
+    d[0] = grid(a, 49152.f);              // 1.5 2^15: grid 2^-8
+    float r = sub_rn(a, d[0]);
+    d[1] = grid(r, 192.f);                // 1.5 2^7: grid 2^-16
+    r = sub_rn(r, d[1]);
+    d[2] = grid(r, 0.75f);                // 1.5 2^-1: grid 2^-24
+    r = sub_rn(r, d[2]);
+    d[3] = grid(r, 0x1.8p-9f);            // grid 2^-32
+    r = sub_rn(r, d[3]);
+    d[4] = grid(r, 0x1.8p-17f);           // grid 2^-40
+}
+
+// Digits of hi' + lo' (an FP32 pair, |lo'| <= ulp(hi')/2): delta_0 and delta_1 from
+// hi' exactly, then lo' joins the residual (one rounding far below 2^-40).
+__device__ __forceinline__ void digits5_pair(float a, float b, float (&d)[5]) {
+    d[0] = grid(a, 49152.f);
+    float r = sub_rn(a, d[0]);
+    d[1] = grid(r, 192.f);
+    r = add_rn(sub_rn(r, d[1]), b);
+    d[2] = grid(r, 0.75f);
+    r = sub_rn(r, d[2]);
+    d[3] = grid(r, 0x1.8p-9f);
+    r = sub_rn(r, d[3]);
+    d[4] = grid(r, 0x1.8p-17f);
+}
+
+// two exact-BF16 FP32 values -> one word, the lower K element in the low half
+__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
+    return __byte_perm(__float_as_uint(lo_k), __float_as_uint(hi_k), 0x7632);
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }   // -126 <= e <= 127
+
+template <bool kPair>
+__global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_constant__ CUtensorMap pmap,
+                                                                const __grid_constant__ CUtensorMap pmap_lo,
+                                                                const __grid_constant__ CUtensorMap qmap,
+                                                                const ExParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr int kRing = kPair ? 2 : kRingMax;
+    __shared__ __align__(8) uint64_t r_full[kRingMax], r_empty[kRingMax];
+    __shared__ __align__(8) uint64_t a_full[kAStages], a_empty[kAStages];
+    __shared__ __align__(8) uint64_t q_full[kQStages], q_empty[kQStages];
+    __shared__ __align__(8) uint64_t accf, acce, done_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int NP = kPair ? 2 : 1;                          // FP32 planes
+    const uint32_t q_slice_bytes = (uint32_t)p.NT * kBK * 2;   // one digit slice of a chunk
+    const uint32_t q_stage = (2 * q_slice_bytes + 1023u) & ~1023u;
+    unsigned char* ring = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* qbuf = ring + (size_t)kRing * NP * kHalfBytes;
+    long long* tacc = reinterpret_cast<long long*>(qbuf + (size_t)kQStages * q_stage);
+
+    if (tid == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            mbar_init(&r_full[i], 1);
+            mbar_init(&r_empty[i], 4 * 32);
+        }
+        for (int i = 0; i < kAStages; ++i) {
+            mbar_init(&a_full[i], 4 * 32);
+            mbar_init(&a_empty[i], 1);
+        }
+        for (int i = 0; i < kQStages; ++i) {
+            mbar_init(&q_full[i], 1);
+            mbar_init(&q_empty[i], 1);
+        }
+        mbar_init(&accf, 1);
+        mbar_init(&acce, kEpiWarps * 32);
+        mbar_init(&done_bar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    for (int i = tid; i < p.NT * kTPitch; i += blockDim.x) tacc[i] = 0;
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = s_tmem;
+
+    // stream-K: this CTA owns chunks [c_begin, c_end) of the tile-major (tile, chunk) order
+    const int64_t K = p.kchunks;
+    const int64_t c_total = p.tiles * K;
+    const int64_t c_begin = (int64_t)blockIdx.x * c_total / gridDim.x;
+    const int64_t c_end = ((int64_t)blockIdx.x + 1) * c_total / gridDim.x;
+    const int64_t total_chunks = c_end - c_begin;
+    const int64_t t_first = c_begin / K;
+    const int64_t ntile_span = total_chunks > 0 ? (c_end - 1) / K - t_first + 1 : 0;
+
+    if (warp < kConvWarps) {
+        // ---------------- converters: rows 32q + lane, half h of every chunk
+        const int q = warp & 3, h = warp >> 2;
+        const int r = 32 * q + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        int64_t mt = t_first / p.ntn, kc = c_begin % K;      // stepped below, no division in the loop
+        int nt = (int)(t_first % p.ntn);
+        int64_t cur_mt = -1;
+        float scale = 1.f;
+        for (int64_t g = 0; g < total_chunks; ++g) {
+            const int64_t hg = 2 * g + h;
+            const int sa = (int)(hg % kAStages);
+            const int rs = (int)(hg % kRing);
+            bool ok = mbar_wait(&a_empty[sa], (uint32_t)((hg / kAStages) & 1) ^ 1u, &s_abort, p.err);
+            if (ok) ok = mbar_wait(&r_full[rs], (uint32_t)((hg / kRing) & 1), &s_abort, p.err);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            if (mt != cur_mt) {
+                cur_mt = mt;
+                const int64_t row = mt * kBM + r;
+                scale = row < p.M ? pow2f(-p.rexp[row]) : 0.f;
+            }
+            // row r of the 128B-swizzled half tile: 16-byte chunk c sits at slot c ^ (r & 7)
+            const unsigned char* src = ring + (size_t)rs * NP * kHalfBytes + (size_t)r * 128;
+            tc_fence_after();
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {            // 16 K per part
+                uint32_t w[5][8];
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int cc = 4 * part + c4;
+                    const float4 v = *reinterpret_cast<const float4*>(src + ((cc ^ (r & 7)) << 4));
+                    float4 vl = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if constexpr (kPair) vl = *reinterpret_cast<const float4*>(src + kHalfBytes + ((cc ^ (r & 7)) << 4));
+                    float dx[5], dy[5], dz[5], dw[5];
+                    if constexpr (kPair) {
+                        digits5_pair(v.x * scale, vl.x * scale, dx);
+                        digits5_pair(v.y * scale, vl.y * scale, dy);
+                        digits5_pair(v.z * scale, vl.z * scale, dz);
+                        digits5_pair(v.w * scale, vl.w * scale, dw);
+                    } else {
+                        digits5(v.x * scale, dx);
+                        digits5(v.y * scale, dy);
+                        digits5(v.z * scale, dz);
+                        digits5(v.w * scale, dw);
+                    }
+#pragma unroll
+                    for (int s = 0; s < 5; ++s) {
+                        w[s][2 * c4] = pack_bf16(dx[s], dy[s]);
+                        w[s][2 * c4 + 1] = pack_bf16(dz[s], dw[s]);
+                    }
+                }
+                if (part == 1) mbar_arrive(&r_empty[rs]);      // both parts read: the slot may refill
+                // A operand in TMEM: lane = row, column = two consecutive k; slice s of
+                // stage sa at kAStageCol + 80 sa + 16 s, this part at + 8 part
+                const uint32_t col = kAStageCol + kAStageCols * (uint32_t)sa + 8u * (uint32_t)part;
+#pragma unroll
+                for (int s = 0; s < 5; ++s) tmem_st8(lane_base + col + 16u * (uint32_t)s, w[s]);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(&a_full[sa]);
+            if (++kc == K) {
+                kc = 0;
+                if (++nt == p.ntn) {
+                    nt = 0;
+                    ++mt;
+                }
+            }
+        }
+    } else if (warp == kPProdWarp) {
+        // ---------------- TMA producer of P half chunks (both planes in pair mode)
+        if (lane == 0) {
+            int64_t issued = 0;
+            int64_t mt = t_first / p.ntn, kc = c_begin % K;
+            int nt = (int)(t_first % p.ntn);
+            for (int64_t hg = 0; hg < 2 * total_chunks; ++hg) {
+                const int rs = (int)(hg % kRing);
+                if (!mbar_wait(&r_empty[rs], (uint32_t)((hg / kRing) & 1) ^ 1u, &s_abort, p.err)) break;
+                // the converters read this slot through the generic proxy; order those
+                // reads before the TMA (async proxy) overwrites it
+                fence_proxy_async();
+                unsigned char* dst = ring + (size_t)rs * NP * kHalfBytes;
+                mbar_arrive_expect_tx(&r_full[rs], NP * kHalfBytes);
+                tma_load_2d(dst, &pmap, (int)(kc * kBK + 32 * (hg & 1)), (int)(mt * kBM), &r_full[rs]);
+                if constexpr (kPair)
+                    tma_load_2d(dst + kHalfBytes, &pmap_lo, (int)(kc * kBK + 32 * (hg & 1)), (int)(mt * kBM),
+                                &r_full[rs]);
+                ++issued;
+                if ((hg & 1) && ++kc == K) {
+                    kc = 0;
+                    if (++nt == p.ntn) {
+                        nt = 0;
+                        ++mt;
+                    }
+                }
+            }
+            for (int64_t hg = std::max<int64_t>(0, issued - kRing); hg < issued; ++hg)
+                mbar_drain(&r_full[hg % kRing], (uint32_t)((hg / kRing) & 1));
+        }
+    } else if (warp == kQProdWarp) {
+        // ---------------- TMA producer of the Q digit slices
+        if (lane == 0) {
+            int64_t issued = 0;
+            int64_t kc = c_begin % K;
+            int nt = (int)(t_first % p.ntn);
+            for (int64_t g = 0; g < total_chunks; ++g) {
+                const int sq = (int)(g % kQStages);
+                if (!mbar_wait(&q_empty[sq], (uint32_t)((g / kQStages) & 1) ^ 1u, &s_abort, p.err)) break;
+                unsigned char* dst = qbuf + (size_t)sq * q_stage;
+                const int y0 = p.q_row0 + nt * p.NT;
+                mbar_arrive_expect_tx(&q_full[sq], 2 * q_slice_bytes);
+                tma_load_2d(dst, &qmap, (int)(kc * kBK), y0, &q_full[sq]);
+                tma_load_2d(dst + q_slice_bytes, &qmap, (int)(kc * kBK), p.q_slice_rows + y0, &q_full[sq]);
+                ++issued;
+                if (++kc == K) {
+                    kc = 0;
+                    if (++nt == p.ntn) nt = 0;
+                }
+            }
+            for (int64_t g = std::max<int64_t>(0, issued - kQStages); g < issued; ++g)
+                mbar_drain(&q_full[g % kQStages], (uint32_t)((g / kQStages) & 1));
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(p.NT);
+            int64_t g = 0;            // chunk counter within this CTA's range
+            int64_t nseg = 0;         // drains so far
+            bool ok = true;
+            for (int64_t j = 0; j < ntile_span && ok; ++j) {
+                const int64_t t0 = (t_first + j) * K;
+                const int64_t k0 = std::max(c_begin, t0) - t0, k1 = std::min(c_end, t0 + K) - t0;
+                for (int64_t sk = k0; sk < k1 && ok; sk += kSegChunks) {
+                    const int64_t sk1 = std::min(k1, sk + kSegChunks);
+                    // the accumulators are free once the previous drain has read them
+                    if (!mbar_wait(&acce, (uint32_t)((nseg & 1) ^ 1), &s_abort, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    bool first = true;
+                    for (int64_t kc = sk; kc < sk1; ++kc, ++g) {
+                        const int sq = (int)(g % kQStages);
+                        if (!mbar_wait(&q_full[sq], (uint32_t)((g / kQStages) & 1), &s_abort, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t qst = smem_u32(qbuf + (size_t)sq * q_stage);
+                        for (int h = 0; h < 2 && ok; ++h) {
+                            const int64_t hg = 2 * g + h;
+                            const int sa = (int)(hg % kAStages);
+                            if (!mbar_wait(&a_full[sa], (uint32_t)((hg / kAStages) & 1), &s_abort, p.err)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t ast = tmem_base + kAStageCol + kAStageCols * (uint32_t)sa;
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {
+                                const uint32_t koff = 32u * (uint32_t)(2 * h + kk);
+                                const uint64_t b0 = sw128_desc(qst + koff);
+                                const uint64_t b1 = sw128_desc(qst + q_slice_bytes + koff);
+                                const uint32_t a0 = ast + 8u * kk, a1 = a0 + 16u, a2 = a0 + 32u, a3 = a0 + 48u,
+                                               a4 = a0 + 64u;
+                                const uint32_t d0 = tmem_base, d1 = tmem_base + kAccCols,
+                                               d2 = tmem_base + 2 * kAccCols, d3 = tmem_base + 3 * kAccCols;
+                                const uint32_t acc = first ? 0u : 1u;
+                                mma_bf16_ts(d0, a0, b0, idesc, acc);
+                                mma_bf16_ts(d1, a0, b1, idesc, acc);
+                                mma_bf16_ts(d1, a1, b0, idesc, 1u);
+                                mma_bf16_ts(d2, a1, b1, idesc, acc);
+                                mma_bf16_ts(d2, a2, b0, idesc, 1u);
+                                mma_bf16_ts(d3, a2, b1, idesc, acc);
+                                mma_bf16_ts(d3, a3, b0, idesc, 1u);
+                                mma_bf16_ts(d3, a3, b1, idesc, 1u);
+                                mma_bf16_ts(d3, a4, b0, idesc, 1u);
+                                first = false;
+                            }
+                            mma_commit(&a_empty[sa]);
+                        }
+                        if (ok) mma_commit(&q_empty[sq]);
+                    }
+                    if (ok) {
+                        mma_commit(&accf);
+                        ++nseg;
+                    }
+                }
+            }
+            mma_commit(&done_bar);
+            mbar_drain(&done_bar, 0);
+        }
+    } else {
+        // ---------------- epilogue: drain each segment into the int64 tile, add tiles out
+        const int q = warp - kConvWarps;          // lane quarter (warps 8..11 -> 0..3)
+        const int r = 32 * q + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        int64_t nseg = 0;
+        bool ok = true;
+        for (int64_t j = 0; j < ntile_span && ok; ++j) {
+            const int64_t tile = t_first + j;
+            const int64_t t0 = tile * K;
+            const int64_t k0 = std::max(c_begin, t0) - t0, k1 = std::min(c_end, t0 + K) - t0;
+            for (int64_t sk = k0; sk < k1; sk += kSegChunks) {
+                ok = mbar_wait(&accf, (uint32_t)(nseg & 1), &s_abort, p.err);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int c = 0; c < p.NT; c += 16) {
+                    float v0[16], v1[16], v2[16], v3[16];
+                    tmem_ld16(lane_base + (uint32_t)c, v0);
+                    tmem_ld16(lane_base + kAccCols + (uint32_t)c, v1);
+                    tmem_ld16(lane_base + 2 * kAccCols + (uint32_t)c, v2);
+                    tmem_ld16(lane_base + 3 * kAccCols + (uint32_t)c, v3);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        // units of 2^-40: L0 (2^-13), L1 (2^-21), L2 (2^-29) exact, R3 rounded
+                        const long long t = (__float2ll_rn(v0[i] * 8192.f) << 27) +
+                                            (__float2ll_rn(v1[i] * 2097152.f) << 19) +
+                                            (__float2ll_rn(v2[i] * 536870912.f) << 11) +
+                                            __float2ll_rn(v3[i] * 1099511627776.f);
+                        tacc[(size_t)(c + i) * kTPitch + r] += t;
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&acce);
+                ++nseg;
+            }
+            if (!ok) break;
+            // tile done (for this CTA): add it into the output and clear it
+            const int64_t mt = tile / p.ntn;
+            const int nt = (int)(tile % p.ntn);
+            const int64_t row = mt * kBM + r;
+            const int n0 = nt * p.NT;
+            const int nvalid = std::min(p.NT, p.N - n0);
+            for (int c = 0; c < p.NT; ++c) {
+                long long& cell = tacc[(size_t)c * kTPitch + r];
+                if (c < nvalid && row < p.M && cell != 0)
+                    atomicAdd(p.T + row * p.ldt + n0 + c, (unsigned long long)cell);
+                cell = 0;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+// ---- helpers around the kernel ------------------------------------------------
+
+// e[r] = the smallest e with |A[r][k]| < 2^e for all k < K (0 for a zero row),
+// from the largest |entry| as a bit pattern; status[0] |= 1 when a row holds Inf
+// or NaN, |= 2 when an entry is 2^126 or more (outside the converter's scaling).
+// One warp per row.
+__global__ void row_exponent_kernel(const float* __restrict__ A, int64_t ld, int64_t M, int64_t K,
+                                    int* __restrict__ e, int* __restrict__ status) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    const float* a = A + row * ld;
+    uint32_t mx = 0;
+    if ((ld & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+        const int64_t K4 = K >> 2;
+        const float4* a4 = reinterpret_cast<const float4*>(a);
+        for (int64_t k = lane; k < K4; k += 32) {
+            const float4 v = __ldcs(a4 + k);
+            mx = max(mx, max(max(__float_as_uint(v.x) & 0x7FFFFFFFu, __float_as_uint(v.y) & 0x7FFFFFFFu),
+                             max(__float_as_uint(v.z) & 0x7FFFFFFFu, __float_as_uint(v.w) & 0x7FFFFFFFu)));
+        }
+        for (int64_t k = 4 * K4 + lane; k < K; k += 32) mx = max(mx, __float_as_uint(a[k]) & 0x7FFFFFFFu);
+    } else {
+        for (int64_t k = lane; k < K; k += 32) mx = max(mx, __float_as_uint(a[k]) & 0x7FFFFFFFu);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        int ex = 0;
+        if (mx >= 0x7F800000u) atomicOr(status, 1);
+        else if (mx != 0u) ex = (int)(mx >> 23) - 126;     // |a| in [2^(E-127), 2^(E-126))
+        if (ex > 126) {
+            atomicOr(status, 2);
+            ex = 126;
+        }
+        e[row] = ex < -126 ? -126 : ex;
+    }
+}
+
+// The two digit slices of Gaussian normals, K-major: D[t][row][k] for rows
+// [0, rows) of the slice array (slice stride slice_rows x ld), k < kpad (zero
+// for k >= kvalid).  Entry (row, k) is the normal of the embedding with
+// (long index, short index) = (k, row0 + row): X(k, j) for X^T (stream GX) or
+// Y(q, i) with i = k for Y (stream GY).  xi0 = g on the 2^-5 grid, xi1 = g - xi0.
+__global__ void normal_digits_kernel(uint64_t seed, uint32_t stream, int64_t kvalid, int64_t kpad, int row0,
+                                     int rows, uint16_t* __restrict__ D, int64_t ld, int64_t slice_rows) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g0 = row0 >> 2;
+    const int ng = (row0 + rows + 3) / 4 - g0;
+    if (idx >= kpad * ng) return;
+    const int64_t k = idx % kpad;
+    const int g = g0 + (int)(idx / kpad);
+    float z[4] = {0.f, 0.f, 0.f, 0.f};
+    if (k < kvalid) normals4((uint32_t)k, (uint32_t)g, stream, seed, z);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int row = 4 * g + t - row0;
+        if (row < 0 || row >= rows) continue;
+        const float x0 = __fsub_rn(__fadd_rn(z[t], 0x1.8p18f), 0x1.8p18f);   // grid 2^-5
+        const float x1 = __fsub_rn(z[t], x0);
+        D[(int64_t)row * ld + k] = (uint16_t)(__float_as_uint(x0) >> 16);
+        D[(slice_rows + row) * ld + k] = (uint16_t)(__float_as_uint(x1) >> 16);
+    }
+}
+
+// T (int64, units of 2^-40 of 2^e_r, row-major M x ldt) -> FP32 pair planes of
+// the transposed result (column c of the result = row c of the planes, ld ldp)
+// and optionally FP64 values (row-major, ldv); cexp[c] = max over rows of the
+// exponent e with |value| < 2^e (atomicMax; the planes feed the left sketch).
+// 32 x 32 tiles through shared memory so both sides are coalesced.
+__global__ void ex_finalize_kernel(const long long* __restrict__ T, int64_t ldt, const int* __restrict__ rexp,
+                                   int64_t M, int N, float* __restrict__ Phi, float* __restrict__ Plo, int64_t ldp,
+                                   double* __restrict__ V, int64_t ldv, int* __restrict__ cexp) {
+    __shared__ float shi[32][33], slo[32][33];
+    __shared__ int sexp[32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // 32 x 8 threads
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    if (threadIdx.x < 32) sexp[threadIdx.x] = -1000;
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int64_t r = r0 + i;
+        const int c = c0 + tx;
+        float hi = 0.f, lo = 0.f;
+        if (r < M && c < N) {
+            const double v = ldexp((double)T[r * ldt + c], rexp[r] - 40);
+            hi = (float)v;
+            lo = (float)(v - (double)hi);
+            if (V) V[r * ldv + c] = v;
+            const uint32_t b = __float_as_uint(hi) & 0x7FFFFFFFu;
+            if (b != 0u) atomicMax(&sexp[tx], (int)(b >> 23) - 126);
+        }
+        shi[i][tx] = hi;
+        slo[i][tx] = lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && c0 + (int)threadIdx.x < N && sexp[threadIdx.x] > -1000)
+        atomicMax(&cexp[c0 + threadIdx.x], sexp[threadIdx.x]);
+    if (!Phi) return;
+    for (int i = ty; i < 32; i += 8) {
+        const int c = c0 + i;
+        const int64_t r = r0 + tx;
+        if (c < N && r < M) {
+            Phi[(int64_t)c * ldp + r] = shi[tx][i];
+            Plo[(int64_t)c * ldp + r] = slo[tx][i];
+        }
+    }
+}
+
+// The left sketch's T (rows = A X columns c, columns = Y rows q) -> core[q][c]
+// (FP64 row-major), value T 2^(cexp[c] - 40).
+__global__ void ex_core_finalize_kernel(const long long* __restrict__ T, int64_t ldt, const int* __restrict__ cexp,
+                                        int C, int Q, int c_off, int q_off, double* __restrict__ core,
+                                        int64_t ld_core) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)C * Q) return;
+    const int q = (int)(idx / C), c = (int)(idx % C);
+    core[(int64_t)(q_off + q) * ld_core + c_off + c] =
+        ldexp((double)T[(int64_t)c * ldt + q], cexp[c_off + c] - 40);
+}
+
+// FP64 row-major values -> pair planes of the transpose and column exponents
+// (the caller's earlier columns of A X when a sketch step appends).
+__global__ void f64_pairs_kernel(const double* __restrict__ V, int64_t ldv, int64_t M, int N, float* __restrict__ Phi,
+                                 float* __restrict__ Plo, int64_t ldp, int* __restrict__ cexp) {
+    __shared__ float shi[32][33], slo[32][33];
+    __shared__ int sexp[32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    if (threadIdx.x < 32) sexp[threadIdx.x] = -1000;
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int64_t r = r0 + i;
+        const int c = c0 + tx;
+        float hi = 0.f, lo = 0.f;
+        if (r < M && c < N) {
+            const double v = V[r * ldv + c];
+            hi = (float)v;
+            lo = (float)(v - (double)hi);
+            const uint32_t b = __float_as_uint(hi) & 0x7FFFFFFFu;
+            if (b != 0u) atomicMax(&sexp[tx], (int)(b >> 23) - 126);
+        }
+        shi[i][tx] = hi;
+        slo[i][tx] = lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && c0 + (int)threadIdx.x < N && sexp[threadIdx.x] > -1000)
+        atomicMax(&cexp[c0 + threadIdx.x], sexp[threadIdx.x]);
+    for (int i = ty; i < 32; i += 8) {
+        const int c = c0 + i;
+        const int64_t r = r0 + tx;
+        if (c < N && r < M) {
+            Phi[(int64_t)c * ldp + r] = shi[tx][i];
+            Plo[(int64_t)c * ldp + r] = slo[tx][i];
+        }
+    }
+}
+
+// column exponents left at the sentinel (an all-zero column) become 0
+__global__ void fix_exp_kernel(int* __restrict__ e, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && e[i] < -126) e[i] = 0;
+}
+
+int g_ex_sms = 0;
+
+}  // namespace
+
+// ---- host side -----------------------------------------------------------------
+
+cudaError_t launch_row_exponent(const float* A, int64_t ld, int64_t M, int64_t K, int* e, int* status,
+                                cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    const int warps = 8;
+    row_exponent_kernel<<<(unsigned)((M + warps - 1) / warps), warps * 32, 0, st>>>(A, ld, M, K, e, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normal_digits(uint64_t seed, uint32_t stream, int64_t kvalid, int64_t kpad, int row0, int rows,
+                                 uint16_t* D, int64_t ld, int64_t slice_rows, cudaStream_t st) {
+    if (rows <= 0 || kpad <= 0) return cudaSuccess;
+    const int ng = (row0 + rows + 3) / 4 - (row0 >> 2);
+    const int64_t total = kpad * ng;
+    normal_digits_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(seed, stream, kvalid, kpad, row0, rows, D,
+                                                                        ld, slice_rows);
+    return cudaGetLastError();
+}
+
+int ex_tile_n(int n) { return n >= kNTMax ? kNTMax : std::max(16, (n + 15) / 16 * 16); }
+
+cudaError_t launch_ex_sketch(const float* P, const float* P_lo, int64_t ldp, int64_t M, int64_t K, const int* rexp,
+                             const uint16_t* Qd, int64_t ldq, int q_slice_rows, int q_row0, int N,
+                             unsigned long long* T, int64_t ldt, int* err_flag, cudaStream_t st, int* launches) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (K > ((int64_t)1 << 20)) return cudaErrorInvalidValue;
+    EncodeTiled enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint32_t estr[2] = {1, 1};
+    CUtensorMap pmap, pmap_lo, qmap;
+    const cuuint64_t pdim[2] = {(cuuint64_t)K, (cuuint64_t)M};
+    const cuuint64_t pstride[1] = {(cuuint64_t)ldp * 4};
+    const cuuint32_t pbox[2] = {32u, (cuuint32_t)kBM};
+    CUresult r = enc(&pmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P), pdim, pstride, pbox, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    pmap_lo = pmap;
+    if (P_lo) {
+        r = enc(&pmap_lo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P_lo), pdim, pstride, pbox, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    const int NT = ex_tile_n(N);
+    const cuuint64_t qdim[2] = {(cuuint64_t)ldq, (cuuint64_t)(2 * (int64_t)q_slice_rows)};
+    const cuuint64_t qstride[1] = {(cuuint64_t)ldq * 2};
+    const cuuint32_t qbox[2] = {(cuuint32_t)kBK, (cuuint32_t)NT};
+    r = enc(&qmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(Qd), qdim, qstride, qbox, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    ExParams p;
+    p.rexp = rexp;
+    p.M = M;
+    p.K = K;
+    p.N = N;
+    p.NT = NT;
+    p.ntn = (N + NT - 1) / NT;
+    p.kchunks = (K + kBK - 1) / kBK;
+    p.tiles = (M + kBM - 1) / kBM * p.ntn;
+    p.q_row0 = q_row0;
+    p.q_slice_rows = q_slice_rows;
+    p.T = T;
+    p.ldt = ldt;
+    p.err = err_flag;
+    const int np = P_lo ? 2 : 1;
+    const int ring = P_lo ? 2 : kRingMax;
+    const uint32_t q_stage = ((uint32_t)2 * NT * kBK * 2 + 1023u) & ~1023u;
+    const size_t smem = (size_t)ring * np * kHalfBytes + (size_t)kQStages * q_stage +
+                        sizeof(long long) * (size_t)NT * kTPitch + 1024;
+    if (!g_ex_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_ex_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int64_t grid = std::min<int64_t>(p.tiles * p.kchunks, g_ex_sms);
+    cudaError_t e;
+    if (P_lo) {
+        e = cudaFuncSetAttribute(ex_sketch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ex_sketch_kernel<true><<<(unsigned)grid, kThreads, smem, st>>>(pmap, pmap_lo, qmap, p);
+    } else {
+        e = cudaFuncSetAttribute(ex_sketch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ex_sketch_kernel<false><<<(unsigned)grid, kThreads, smem, st>>>(pmap, pmap_lo, qmap, p);
+    }
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ex_finalize(const long long* T, int64_t ldt, const int* rexp, int64_t M, int N, float* Phi,
+                               float* Plo, int64_t ldp, double* V, int64_t ldv, int* cexp, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((M + 31) / 32), (unsigned)((N + 31) / 32));
+    ex_finalize_kernel<<<grid, 256, 0, st>>>(T, ldt, rexp, M, N, Phi, Plo, ldp, V, ldv, cexp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && cexp) {
+        fix_exp_kernel<<<(N + 255) / 256, 256, 0, st>>>(cexp, N);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t launch_ex_core_finalize(const long long* T, int64_t ldt, const int* cexp, int C, int Q, int c_off,
+                                    int q_off, double* core, int64_t ld_core, cudaStream_t st) {
+    if (C <= 0 || Q <= 0) return cudaSuccess;
+    const int64_t total = (int64_t)C * Q;
+    ex_core_finalize_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(T, ldt, cexp, C, Q, c_off, q_off, core,
+                                                                            ld_core);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_pairs(const double* V, int64_t ldv, int64_t M, int N, float* Phi, float* Plo, int64_t ldp,
+                                int* cexp, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((M + 31) / 32), (unsigned)((N + 31) / 32));
+    f64_pairs_kernel<<<grid, 256, 0, st>>>(V, ldv, M, N, Phi, Plo, ldp, cexp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        fix_exp_kernel<<<(N + 255) / 256, 256, 0, st>>>(cexp, N);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace re

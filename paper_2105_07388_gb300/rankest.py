@@ -30,6 +30,7 @@ RE_SRHT = 1
 RE_HRTT = 2
 RE_PREC_FP32 = 0
 RE_PREC_BF16X3 = 1
+RE_PREC_EXACT = 2
 
 RE_MLP_IN = 18
 RE_MLP_OUT = 12
@@ -112,6 +113,7 @@ _SIGS = {
                                    ctypes.POINTER(re_result), _VP]),
     "re_sketch_apply": (_I, [_VP, _VP, _I, _I64, _I64, _I64, _I, _I, _I, _U64, _VP, _I64, _VP,
                              _I64, _VP]),
+    "re_sketch_apply_exact": (_I, [_VP, _VP, _I64, _I64, _I64, _I, _I, _U64, _VP, _I64, _VP, _I64, _VP]),
     "re_core_sigma": (_I, [_VP, _VP, _I, _I, _I64, _VP, _VP]),
     "re_embedding_x": (_I, [_VP, _I, _U64, _I64, _I, _I, _VP, _VP]),
     "re_embedding_y": (_I, [_VP, _I, _U64, _I64, _I, _I, _VP, _VP]),
@@ -281,6 +283,25 @@ def re_sketch_apply(h: int, A, col0: int, s: int, sketch_kind: int, seed: int, A
     _check(lib().re_sketch_apply(h, _ptr(A), _dtype_code(A), m, n, A.stride(0), col0, s,
                                  sketch_kind, seed, _ptr(AX), AX.stride(0), _ptr(core), ld_core,
                                  _stream(stream)))
+
+
+def re_sketch_apply_exact(h: int, A, col0: int, s: int, seed: int, AX, core=None, stream=None) -> None:
+    """Exact-product sketch step (precision mode): A FP32 CUDA tensor (m >= n), AX
+    FP64 (rows x >= col0 + s) receives columns col0..col0+s-1, core FP64 optional."""
+    import torch
+    m, n = A.shape
+    if A.dtype != torch.float32:
+        raise ValueError("A must be float32")
+    if AX.dtype != torch.float64 or (core is not None and core.dtype != torch.float64):
+        raise ValueError("AX and core must be float64")
+    if A.stride(1) != 1 or AX.stride(1) != 1 or (core is not None and core.stride(1) != 1):
+        raise ValueError("A, AX and core must be row-major (unit column stride)")
+    if AX.shape[0] < max(m, n) or AX.shape[1] < col0 + s:
+        raise ValueError(f"AX must be at least {max(m, n)} x {col0 + s}")
+    if core is not None and (core.shape[0] < 2 * (col0 + s) or core.shape[1] < col0 + s):
+        raise ValueError(f"core must be at least {2 * (col0 + s)} x {col0 + s}")
+    _check(lib().re_sketch_apply_exact(h, _ptr(A), m, n, A.stride(0), col0, s, seed, _ptr(AX), AX.stride(0),
+                                       _ptr(core), core.stride(0) if core is not None else 0, _stream(stream)))
 
 
 def re_core_sigma(h: int, core, sigma, stream=None, r2=None, s=None) -> None:
