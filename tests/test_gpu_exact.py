@@ -38,6 +38,16 @@ def h():
     rk.re_destroy(hd)
 
 
+def padded(A):
+    """A FP32 CUDA view whose row pitch is a multiple of 4 floats (16 bytes, what the
+    tensor-memory copies take), whatever n is."""
+    m, n = A.shape
+    ld = (n + 3) // 4 * 4
+    full = torch.zeros(m, ld, dtype=torch.float32, device="cuda")
+    full[:, :n] = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)).cuda()
+    return full[:, :n]
+
+
 def row_scale(A64):
     """2^e_i: the smallest power of two above every |a_ik| of row i."""
     mx = np.abs(A64).max(axis=1)
@@ -58,7 +68,7 @@ def right_bound(A64, X):
 def test_exact_right_sketch_parity(h, m, n, steps):
     A = np.random.default_rng(m + n).standard_normal((m, n)).astype(np.float32)
     A64 = A.astype(np.float64)
-    Ad = torch.from_numpy(A).cuda()
+    Ad = padded(A)
     c1 = steps[-1][0] + steps[-1][1]
     AX = torch.zeros(m, c1, dtype=torch.float64, device="cuda")
     for col0, s in steps:
@@ -96,7 +106,7 @@ def test_exact_accumulation_at_largest_digits(h):
 def test_exact_core_parity(h, m, n, steps):
     A = np.random.default_rng(7 * m + n).standard_normal((m, n)).astype(np.float32)
     A64 = A.astype(np.float64)
-    Ad = torch.from_numpy(A).cuda()
+    Ad = padded(A)
     c1 = steps[-1][0] + steps[-1][1]
     AX = torch.zeros(m, c1, dtype=torch.float64, device="cuda")
     core = torch.zeros(2 * c1, c1, dtype=torch.float64, device="cuda")
@@ -132,6 +142,10 @@ def test_exact_errors(h):
     with pytest.raises(rk.RankEstError) as e:
         rk.re_sketch_apply(h, A, 0, 16, rk.RE_GAUSSIAN, 1, torch.zeros(300, 16, device="cuda"))
     assert e.value.code == rk.RE_ERR_UNSUPPORTED              # FP32 A X output
+    C = torch.randn(300, 201, device="cuda")
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_sketch_apply_exact(h, C, 0, 16, 1, AX)
+    assert e.value.code == rk.RE_ERR_UNSUPPORTED              # row pitch not a multiple of 16 bytes
     res, _ = rk.re_rank_estimate(h, torch.zeros(256, 128, device="cuda"), 1e-8)
     assert res.rank == 0
 
