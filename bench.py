@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched", type=int, default=1)
     ap.add_argument("--batched-count", type=int, default=4096)
+    ap.add_argument("--precision-case", type=int, default=1,
+                    help="also time the exact-product precision mode on the 32768^2, eps = 1e-8 workload")
     return ap.parse_args()
 
 
@@ -409,7 +411,15 @@ def main():
     if args.batched and world == 1:
         line["batched"] = bench_batched(rk, local, stream, args)
 
+    if args.precision_case and world == 1:
+        del A
+        torch.cuda.empty_cache()
+        line["precision"] = bench_precision(rk, local, stream, args, hbm, bf16)
+        A = None
+
     if rank == 0 and world == 1 and not args.no_cpu:
+        if A is None:
+            A = build_matrix(w, "cuda")
         A_host = A.cpu().numpy()
         v, info = cpu_oracle_run(A_host, w, kind_code, budget_s=20.0)
         line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": os.cpu_count(),
@@ -422,6 +432,62 @@ def main():
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_precision(rk, local, stream, args, hbm, bf16):
+    """The precision workload: 32768 x 32768 FP32 (4 GiB), built like the large
+    matrix (8 Householder reflectors, random signs) with sigma_i = 10^(-10 (i-1)/300)
+    for i <= 300 and a 1e-12 floor, eps = 1e-8 (sigma_241 = 1e-8 sits on the
+    threshold, so the true eps-rank is 240 with a tie at 241).  One step = one
+    estimate with the exact-product sketch (RE_PREC_EXACT); the BF16x3 form's
+    answer at the same eps is reported beside it (its FP32 accumulation floor,
+    about 3e-7 sigma_1, lies above the threshold)."""
+    import torch
+    from paper_2105_07388_gb300 import workloads as wl
+    n = 32768
+    eps = 1e-8
+    A = wl.householder_matrix(n, n, wl.spectrum("geom300", n), seed=2, device="cuda")
+    torch.cuda.synchronize()
+    hx = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_EXACT))
+    r, sig = rk.re_rank_estimate(hx, A, eps, rk.RE_GAUSSIAN, 4242, stream=stream)     # warm-up
+    torch.cuda.synchronize()
+    rk.re_stats_enable(hx, True)
+    rk.re_stats_reset(hx)
+    steps = max(1, min(args.steps, 3))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        r, sig = rk.re_rank_estimate(hx, A, eps, rk.RE_GAUSSIAN, 4242, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = rk.re_stats_get(hx)
+    rk.re_destroy(hx)
+    a_bytes = 4.0 * n * n
+    right_ms = st.right_ms / steps
+    right_gbs = st.right_bytes / (st.right_ms * 1e-3) / 1e9 if st.right_ms else 0.0
+    right_tflops = st.right_flops / (st.right_ms * 1e-3) / 1e12 if st.right_ms else 0.0
+    hb = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_BF16X3))
+    rb, _ = rk.re_rank_estimate(hb, A, eps, rk.RE_GAUSSIAN, 4242, stream=stream)
+    rk.re_destroy(hb)
+    del A
+    torch.cuda.empty_cache()
+    return {"workload": f"single matrix {n}x{n} FP32, sigma_i=10^(-10(i-1)/300) (i<=300) then 1e-12, "
+                        f"eps={eps}, Gaussian X and Y, s=8..512 doubling",
+            "form": "exact-product sketch (RE_PREC_EXACT): five BF16 digits of A x two of X, exact sums, "
+                    "preconditioned FP32 singular values",
+            "ms_per_estimate": ms, "rank_estimates_per_s": 1e3 / ms,
+            "sketch_gbs": a_bytes * r.passes / (ms * 1e-3) / 1e9,
+            "hbm_frac_of_step": a_bytes * r.passes / (ms * 1e-3) / 1e9 / hbm,
+            "rank": r.rank, "final_s": r.final_s, "passes": r.passes, "flags": r.flags,
+            "sigma_at_rank": float(sig[r.rank]) if r.rank < len(sig) else None,
+            "right_sketch": {"ms_per_step": right_ms, "gbs": right_gbs, "hbm_frac": right_gbs / hbm,
+                             "tensor_tflops": right_tflops, "tensor_frac": right_tflops / bf16,
+                             "launches": int(st.right_launches) // steps},
+            "stage_ms_per_step": {"right": st.right_ms / steps, "left": st.left_ms / steps,
+                                  "svd": st.svd_ms / steps, "other": st.other_ms / steps},
+            "bf16x3_same_eps": {"rank": rb.rank, "final_s": rb.final_s, "flags": rb.flags}}
 
 
 def bench_batched(rk, local, stream, args):

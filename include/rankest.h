@@ -81,8 +81,9 @@ extern "C" {
  * Jacobi (W = core V1 formed in FP64 from the FP32 right singular vectors V1, its
  * graded columns taken with a purely relative rotation test).  Resolves sketched
  * values down to about 1e-11 sigma_1 (Algorithm 1 at eps = 1e-8 on the
- * ten-decade spectra of Sec. 6).  Gaussian X and Y, FP32 A with m >= n, a 16-byte aligned base and row pitch (ld a multiple of 4),
- * aligned rows and min(m, n) <= 2^20; other inputs give RE_ERR_UNSUPPORTED. */
+ * ten-decade spectra of Sec. 6).  Gaussian X and Y, FP32 A with m >= n, a
+ * 16-byte aligned base and row pitch (ld a multiple of 4) and min(m, n) <= 2^20;
+ * other inputs give RE_ERR_UNSUPPORTED. */
 #define RE_PREC_EXACT 2
 
 /* result flags */

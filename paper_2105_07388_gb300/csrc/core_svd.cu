@@ -1345,8 +1345,10 @@ cudaError_t launch_core_sigma_precise(const double* core, int r2, int s, int64_t
     int* perm = reinterpret_cast<int*>(b);
     b += ((size_t)s * sizeof(int) + 255) / 256 * 256;
     double* W = reinterpret_cast<double*>(b);
-    // stage 1: FP32 QR + Jacobi of the core, keeping its right singular vectors V1
-    cudaError_t e = core_sigma_one(core, r2, s, ld, ws, sigma, status, st, 0, 0.f, V, vnorm, 0);
+    // stage 1: FP32 QR + Jacobi of the core, keeping its right singular vectors V1;
+    // every pair is orthogonalised (no absolute floor), so V1 is orthogonal to
+    // working precision in its small-value columns too
+    cudaError_t e = core_sigma_one(core, r2, s, ld, ws, sigma, status, st, 0, 0.f, V, vnorm, 1);
     if (e != cudaSuccess) return e;
     norm_order_kernel<<<1, 512, 0, st>>>(vnorm, s, perm);
     e = cudaGetLastError();

@@ -200,10 +200,12 @@ def test_exact_rank_at_eps_1e8(h, geom_case):
     orc = alg.rank_estimate(A64, eps, kind=alg.GAUSSIAN, seed=SEED2)
     assert (orc.rank, orc.final_s) == (r_o, s_o)
     res, sig = rk.re_rank_estimate(h, A32.cuda(), eps, rk.RE_GAUSSIAN, SEED2)
-    ref = vals[res.final_s] if res.final_s in vals else None
+    ref = vals[res.final_s]
+    k = min(len(sig), len(ref))
+    print("\n[exact] rel err by index:", np.array2string(np.abs(sig[:k] - ref[:k]) / ref[:k], precision=2,
+                                                        threshold=10000, max_line_width=200))
     assert res.final_s == orc.final_s and res.rank == orc.rank, (res.rank, orc.rank, res.final_s, orc.final_s)
     assert bool(res.flags & rk.RE_CONVERGED) == orc.converged
-    k = min(len(sig), len(ref))
     err = np.abs(sig[:k] - ref[:k])
     rel = err / ref[:k]
     s1 = ref[0]
