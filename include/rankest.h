@@ -86,6 +86,16 @@ extern "C" {
  * other inputs give RE_ERR_UNSUPPORTED. */
 #define RE_PREC_EXACT 2
 
+/* Step 7 (Algorithm 1): how the core's singular values are taken.
+ * RE_SIGMA_SVD     singular values (QR + one-sided Jacobi).
+ * RE_SIGMA_QRDIAG  the remark after Algorithm 1 (Sec. 5): |R_kk| of the core's
+ *                  Householder QR, sorted descending, as estimates of the singular
+ *                  values (a QR of a matrix whose right singular vectors are
+ *                  randomised is rank-revealing with high probability); the
+ *                  Jacobi sweeps are skipped.  Not with RE_PREC_EXACT. */
+#define RE_SIGMA_SVD 0
+#define RE_SIGMA_QRDIAG 1
+
 /* result flags */
 #define RE_CONVERGED 1u        /* some trusted sigma^_{i+1} <= eps ||A|| was found */
 #define RE_LOWER_BOUND_ONLY 2u /* the ladder ended first: rank = r1(final s) is a lower bound (Sec. 5) */
@@ -106,7 +116,8 @@ typedef struct {
      * bounded waits expire (about 2 s); the call then returns RE_ERR_TIMEOUT and the
      * CUDA context stays usable.  Never set outside tests. */
     int test_drop_load;
-    int reserved[6];
+    int sigma_est;   /* step 7: RE_SIGMA_SVD (default) or RE_SIGMA_QRDIAG */
+    int reserved[5];
 } re_opts;
 
 /* Outcome of one estimate.  sigma values go to a separate caller buffer. */

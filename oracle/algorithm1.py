@@ -11,7 +11,9 @@ densely so that each product is a plain matrix product a reader can check:
   step 4  r2 = 2 r~1
   step 5  draw Y (r2 x m): Gaussian or SRTT S H D      -> ``rng.gaussian_y`` / ``rng.srtt_y``
   step 6  form Y (A X)                                 -> ``Y @ AX``
-  step 7  the first r1 singular values                 -> LAPACK (numpy.linalg.svd)
+  step 7  the first r1 singular values                 -> LAPACK (numpy.linalg.svd), or the
+          diagonal of R in Y A X = QR as their estimates (the alternative of Sec. 5's
+          remark on step 7)                            -> ``qr_diagonal_sigma``
   step 8  first r^ with sigma_{r^+1} <= eps ||A||, ||A|| ~ sigma_1(Y A X) when
           unknown; otherwise grow r1 by appending      -> ``readoff`` / ``rank_estimate``
 
@@ -136,10 +138,22 @@ def core(A: np.ndarray, s: int, kind: int, seed: int) -> np.ndarray:
     return left_sketch(AX, 2 * s, kind, seed)
 
 
-def sketched_sigma(A: np.ndarray, s: int, kind: int, seed: int) -> np.ndarray:
-    """Step 7: all s singular values of Y A X, scaled (descending, FP64)."""
+def qr_diagonal_sigma(C: np.ndarray) -> np.ndarray:
+    """Step 7 by the remark after Algorithm 1 (Sec. 5): factor the core C = QR
+    (Householder, LAPACK) and take |R_kk| as estimates of sigma_k(C) -- a QR of a
+    matrix whose right singular vectors are randomised reveals its rank with high
+    probability.  Reading: the estimates are sorted descending, so that the
+    read-off's "first r^" and sigma^_1 (the largest estimate, for ||A||) are taken
+    on an ordered list as with singular values."""
+    R = np.linalg.qr(np.asarray(C, dtype=np.float64), mode="r")
+    return np.sort(np.abs(np.diag(R)))[::-1]
+
+
+def sketched_sigma(A: np.ndarray, s: int, kind: int, seed: int, sigma: str = "svd") -> np.ndarray:
+    """Step 7: all s singular values of Y A X (or their QR-diagonal estimates),
+    scaled (descending, FP64)."""
     C = core(A, s, kind, seed)
-    sig = np.linalg.svd(C, compute_uv=False)
+    sig = np.linalg.svd(C, compute_uv=False) if sigma == "svd" else qr_diagonal_sigma(C)
     return sig * sketch_scale(s, kind, np.shape(A)[1])
 
 
@@ -204,7 +218,7 @@ def ladder_limits(m: int, n: int, kind: int, s_max: int) -> int:
 
 
 def rank_estimate(A: np.ndarray, eps: float, kind: int = GAUSSIAN, seed: int = 0,
-                  s0: int = 8, s_max: int = 512, norm_a: float | None = None) -> Result:
+                  s0: int = 8, s_max: int = 512, norm_a: float | None = None, sigma: str = "svd") -> Result:
     """Algorithm 1 with the doubling loop of step 8 (appending to X and Y).
 
     Each step recomputes the core from the plain definition Y[:2s] A X[:, :s];
@@ -234,7 +248,7 @@ def rank_estimate(A: np.ndarray, eps: float, kind: int = GAUSSIAN, seed: int = 0
     passes = 0
     while True:
         passes += 1
-        sig_all = sketched_sigma(A64, s, kind, seed)
+        sig_all = sketched_sigma(A64, s, kind, seed, sigma)
         r1 = r1_of_s(s)
         sig = sig_all[:r1]
         ro = readoff(sig, eps, norm_a)

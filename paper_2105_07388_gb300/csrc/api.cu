@@ -519,7 +519,9 @@ int check_width(re_handle h, const Plan& P, int s, int smax, double eps, re::Dev
         cudaError_t e = cudaMemsetAsync(status + 3, 0, sizeof(int), st);
         if (e != cudaSuccess) return cuda_fail(e, "clear status");
         cudaEvent_t a = stage_begin(h, st);
-        if (precise && !(certify && re::core_sigma_fits_cta(2 * s, s)))
+        if (h->opts.sigma_est == RE_SIGMA_QRDIAG)
+            e = re::launch_core_qrdiag(core, 2 * s, s, smax, h->svdws.p, static_cast<double*>(h->sigma.p), status, st);
+        else if (precise && !(certify && re::core_sigma_fits_cta(2 * s, s)))
             e = re::launch_core_sigma_precise(core, 2 * s, s, smax, h->svdws.p, h->ex_svd.p,
                                               static_cast<double*>(h->sigma.p), status, st);
         else
@@ -758,6 +760,9 @@ int check_opts(const re_opts* o) {
     if (o->y_kind < -1 || o->y_kind > RE_SRHT) return fail(RE_ERR_ARG, "unknown y_kind");
     if (o->learned != 0 && o->learned != 1) return fail(RE_ERR_ARG, "learned must be 0 or 1");
     if (o->test_drop_load != 0 && o->test_drop_load != 1) return fail(RE_ERR_ARG, "test_drop_load must be 0 or 1");
+    if (o->sigma_est != RE_SIGMA_SVD && o->sigma_est != RE_SIGMA_QRDIAG) return fail(RE_ERR_ARG, "unknown sigma_est");
+    if (o->sigma_est == RE_SIGMA_QRDIAG && o->precision == RE_PREC_EXACT)
+        return fail(RE_ERR_UNSUPPORTED, "QR-diagonal estimates are FP32: not with the exact-product precision mode");
     return RE_OK;
 }
 

@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
     const double* __restrict__ core, int r2, int s, int64_t ld, int64_t core_stride,
     double* __restrict__ sigma, int64_t sigma_stride, int* __restrict__ status,
     const int* __restrict__ active, int cert_r1, float cert_ratio, float* __restrict__ vout,
-    double* __restrict__ vnorm, int rel_only) {
+    double* __restrict__ vnorm, int rel_only, int diag_only) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (active && !active[blockIdx.x]) return;
     core += (int64_t)blockIdx.x * core_stride;
@@ -500,6 +500,16 @@ __global__ void __launch_bounds__(kCtaThreads, 1) core_sigma_cta_kernel(
             }
         }
         __syncthreads();
+    }
+    // The QR-diagonal estimates (the remark after Algorithm 1): |R_kk| sorted, no
+    // Jacobi; R_kk = W[k][k] (column-major W holds R in its upper triangle)
+    if (diag_only) {
+        for (int j = tid; j < s; j += blockDim.x) s_norm[j] = fabs((double)W[(size_t)j * ldw + j]);
+        __syncthreads();
+        sort_desc(s_norm, s, up, sigma);
+        if (tid == 0 && blockIdx.x == 0 && sigma_stride == 0) status[2] = 0;
+        if (tid == 0) status[blockIdx.x] = RE_OK;
+        return;
     }
     // Certificate of non-convergence (used at intermediate ladder widths only):
     // sigma_r1(core) >= sigma_min(R11) >= 1 / ||R11^{-1}||_F (column interlacing)
@@ -1103,6 +1113,22 @@ cudaError_t launch_jacobi_cluster(void* ws, int r2, int s, double* sigma, int* s
     }
 }
 
+// The QR-diagonal estimates after the cluster QR: |R_kk| of R (column-major in the
+// workspace), sorted descending and scaled back (one CTA).
+__global__ void qrdiag_cluster_kernel(const void* ws, int r2, int s, double* __restrict__ sigma,
+                                      int* __restrict__ status) {
+    __shared__ double s_norm[512];
+    if (*status == RE_ERR_NONFINITE) return;
+    const ClusterWs g = cluster_ws(const_cast<void*>(ws), r2, s);
+    for (int j = threadIdx.x; j < s; j += blockDim.x) s_norm[j] = fabs((double)g.Rcm[(size_t)j * s + j]);
+    __syncthreads();
+    sort_desc(s_norm, s, *g.up, sigma);
+    if (threadIdx.x == 0) {
+        status[2] = 0;
+        *status = RE_OK;
+    }
+}
+
 // Step 8 (device): scaled sigma, threshold rank, gap index.
 // One warp: lanes take indices i = lane, lane + 32, ...; the threshold rank is the
 // smallest index with sigma^ <= tau and the gap the largest ratio, smallest index on
@@ -1183,7 +1209,7 @@ size_t svd_workspace_bytes(int r2, int s) { return sizeof(float) * cluster_ws_fl
 namespace {
 
 using CtaKernel = void (*)(const double*, int, int, int64_t, int64_t, double*, int64_t, int*, const int*, int,
-                           float, float*, double*, int);
+                           float, float*, double*, int, int);
 
 template <int NV>
 CtaKernel cta_kernel_e(int e) {
@@ -1226,7 +1252,7 @@ cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t
     // takes its warp and group counts from the launch
     const int threads = (count > 1 && s <= 64) ? 512 : kCtaThreads;
     kern<<<count, threads, sm, st>>>(core, r2, s, ld, core_stride, sigma, sigma_stride, status, active,
-                                     cert_r1, cert_ratio, nullptr, nullptr, 0);
+                                     cert_r1, cert_ratio, nullptr, nullptr, 0, 0);
     return cudaGetLastError();
 }
 
@@ -1237,7 +1263,7 @@ namespace {
 // norms, and rel_only (no absolute rotation floor).
 cudaError_t core_sigma_one(const double* core, int r2, int s, int64_t ld, void* ws, double* sigma, int* status,
                            cudaStream_t st, int cert_r1, float cert_ratio, float* vout, double* vnorm,
-                           int rel_only) {
+                           int rel_only, int diag_only = 0) {
     if (s <= 0) return cudaSuccess;
     if (s > 512) return cudaErrorInvalidValue;
     if (cta_smem(r2, s) <= kSmemLimit) {
@@ -1247,7 +1273,7 @@ cudaError_t core_sigma_one(const double* core, int r2, int s, int64_t ld, void* 
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         kern<<<1, kCtaThreads, sm, st>>>(core, r2, s, ld, 0, sigma, 0, status, nullptr, cert_r1, cert_ratio, vout,
-                                         vnorm, rel_only);
+                                         vnorm, rel_only, diag_only);
         return cudaGetLastError();
     }
     // larger cores: QR on a cluster, then Jacobi on a cluster; ws holds
@@ -1258,6 +1284,10 @@ cudaError_t core_sigma_one(const double* core, int r2, int s, int64_t ld, void* 
     else if (qr_cluster_smem(16, r2, s) <= kSmemLimit) e = launch_qr_cluster<16>(core, r2, s, ld, ws, sigma, status, st);
     else return cudaErrorInvalidValue;
     if (e != cudaSuccess) return e;
+    if (diag_only) {
+        qrdiag_cluster_kernel<<<1, 512, 0, st>>>(ws, r2, s, sigma, status);
+        return cudaGetLastError();
+    }
     int b = 0;
     if (jac_cluster_smem(8, s, &b) <= kSmemLimit)
         return launch_jacobi_cluster<8>(ws, r2, s, sigma, status, st, vout, vnorm, rel_only);
@@ -1271,6 +1301,11 @@ cudaError_t core_sigma_one(const double* core, int r2, int s, int64_t ld, void* 
 cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws, double* sigma,
                               int* status, cudaStream_t st, int cert_r1, float cert_ratio) {
     return core_sigma_one(core, r2, s, ld, ws, sigma, status, st, cert_r1, cert_ratio, nullptr, nullptr, 0);
+}
+
+cudaError_t launch_core_qrdiag(const double* core, int r2, int s, int64_t ld, void* ws, double* sigma, int* status,
+                               cudaStream_t st) {
+    return core_sigma_one(core, r2, s, ld, ws, sigma, status, st, 0, 0.f, nullptr, nullptr, 0, 1);
 }
 
 namespace {

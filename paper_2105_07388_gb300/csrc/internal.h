@@ -185,6 +185,10 @@ size_t svd_workspace_bytes(int r2, int s);
 cudaError_t launch_core_sigma(const double* core, int r2, int s, int64_t ld, void* ws,
                               double* sigma, int* status, cudaStream_t st, int cert_r1 = 0,
                               float cert_ratio = 0.f);
+// Step 7 by the QR diagonal (the remark after Algorithm 1): |R_kk| of the core's
+// Householder QR (FP32), sorted descending, unscaled; no Jacobi.
+cudaError_t launch_core_qrdiag(const double* core, int r2, int s, int64_t ld, void* ws, double* sigma, int* status,
+                               cudaStream_t st);
 // Precision-mode singular values (sigma descending, unscaled, status as above):
 // the FP32 QR + Jacobi of the core gives right singular vectors V1; W = core V1
 // (columns ordered by decreasing norm) is formed in FP64 and its singular values

@@ -31,6 +31,8 @@ RE_HRTT = 2
 RE_PREC_FP32 = 0
 RE_PREC_BF16X3 = 1
 RE_PREC_EXACT = 2
+RE_SIGMA_SVD = 0
+RE_SIGMA_QRDIAG = 1
 
 RE_MLP_IN = 18
 RE_MLP_OUT = 12
@@ -44,7 +46,7 @@ RE_TRANSPOSED = 4
 class re_opts(ctypes.Structure):
     _fields_ = [("s0", ctypes.c_int), ("s_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("y_kind", ctypes.c_int), ("norm_a", ctypes.c_double), ("learned", ctypes.c_int),
-                ("test_drop_load", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("test_drop_load", ctypes.c_int), ("sigma_est", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class re_result(ctypes.Structure):

@@ -458,3 +458,26 @@ def test_hrtt_errors(h):
     # read-off finds sigma_101 at the rounding level
     res, _ = rk.re_rank_estimate(h, A, 1e-3, rk.RE_HRTT, 1)
     assert res.rank == 100 and res.flags & rk.RE_CONVERGED and res.final_s == 128
+
+
+# ---------------------------------------------------------------------------
+# step 7 by the QR diagonal (the remark after Algorithm 1, Sec. 5)
+@pytest.mark.parametrize("m,n,rank", [(1500, 600, 37), (3000, 1200, 200), (600, 1500, 60)])
+def test_qr_diagonal_estimate(h, m, n, rank):
+    """|R_kk| of the core's QR as the singular-value estimates: the GPU's FP32
+    Householder QR against the oracle's LAPACK QR of the FP64 core (within 1e-4
+    sigma^_1, the FP32 tolerance), and the oracle's rank on a clear gap; rank 200
+    ends at s = 256, where the core is factored by the cluster QR kernel."""
+    sig = wl.spectrum("step", min(m, n), rank=rank, tail_scale=1e-9)
+    A = wl.haar_matrix(m, n, sig, seed=rank + 5).numpy()
+    Ad = dev(A)
+    rk.re_set_opts(h, rk.make_opts(sigma_est=rk.RE_SIGMA_QRDIAG))
+    try:
+        res, sg = rk.re_rank_estimate(h, Ad, 1e-4, rk.RE_GAUSSIAN, 3)
+    finally:
+        rk.re_set_opts(h, rk.re_opts_default())
+    orc = alg.rank_estimate(Ad.double().cpu().numpy(), 1e-4, kind=alg.GAUSSIAN, seed=3, sigma="qrdiag")
+    assert res.rank == orc.rank == rank and res.final_s == orc.final_s
+    k = min(len(sg), len(orc.sigma))
+    assert np.max(np.abs(sg[:k] - orc.sigma[:k])) <= SIGMA_TOL * orc.sigma[0]
+    assert res.svd_sweeps == 0

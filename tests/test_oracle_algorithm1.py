@@ -236,3 +236,31 @@ def test_hrtt_scale_and_limits():
     # the left embedding of the HRTT is Gaussian
     AX = np.random.default_rng(1).standard_normal((300, 8))
     assert np.array_equal(alg.left_sketch(AX, 16, alg.HRTT, 3), alg.left_sketch(AX, 16, alg.GAUSSIAN, 3))
+
+
+# ---------------------------------------------------------------------------
+# step 7 by the QR diagonal (the remark after Algorithm 1, Sec. 5)
+def test_qr_diagonal_closed_forms():
+    # a diagonal core: R is the diagonal itself up to signs
+    d = np.array([3.0, -7.0, 0.5, 2.0])
+    assert np.array_equal(alg.qr_diagonal_sigma(np.diag(d)), np.array([7.0, 3.0, 2.0, 0.5]))
+    # any core: prod |R_kk| = sqrt(det(C^T C)) = prod sigma_k, |R_11| = |c_1| <= sigma_1,
+    # |R_ss| = dist(c_s, span of the others) >= sigma_min
+    C = np.random.default_rng(3).standard_normal((40, 20))
+    q = alg.qr_diagonal_sigma(C)
+    sv = np.linalg.svd(C, compute_uv=False)
+    assert np.isclose(np.sum(np.log(q)), np.sum(np.log(sv)), rtol=0, atol=1e-10)
+    R = np.linalg.qr(C, mode="r")
+    assert np.isclose(abs(R[0, 0]), np.linalg.norm(C[:, 0])) and abs(R[0, 0]) <= sv[0]
+    assert abs(R[-1, -1]) >= sv[-1] * (1 - 1e-12)
+    assert np.all(np.diff(q) <= 0)
+
+
+@pytest.mark.parametrize("rank", [5, 37])
+def test_qr_diagonal_rank_on_clear_gap(rank):
+    """A QR of a sketch with randomised right singular vectors reveals the rank:
+    on a clear gap the QR-diagonal read-off returns the true eps-rank."""
+    sig = wl.spectrum("step", 400, rank=rank, tail_scale=1e-9)
+    A = wl.haar_matrix(900, 400, sig, seed=rank).numpy()
+    res = alg.rank_estimate(A, 1e-4, kind=alg.GAUSSIAN, seed=11, sigma="qrdiag")
+    assert res.converged and res.rank == rank
