@@ -109,36 +109,61 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 // |x| < 2^(k-1).
 __device__ __forceinline__ float grid(float x, float c) { return sub_rn(add_rn(x, c), c); }
 
-// The five digits of p' (|p'| < 1, FP32 exact): delta_0..delta_4.
-__device__ __forceinline__ void digits5(float a, float (&d)[5]) {
-    d[0] = grid(a, 49152.f);              // 1.5 2^15: grid 2^-8
-    float r = sub_rn(a, d[0]);
-    d[1] = grid(r, 192.f);                // 1.5 2^7: grid 2^-16
-    r = sub_rn(r, d[1]);
-    d[2] = grid(r, 0.75f);                // 1.5 2^-1: grid 2^-24
-    r = sub_rn(r, d[2]);
-    d[3] = grid(r, 0x1.8p-9f);            // grid 2^-32
-    r = sub_rn(r, d[3]);
-    d[4] = grid(r, 0x1.8p-17f);           // grid 2^-40
+// ---- digit extraction on packed FP32x2 values (each lane rounded exactly as the
+// scalar add / subtract / multiply, no contraction)
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 grid2(f2 x, f2 c) { return sub2(add2(x, c), c); }
+
+// The five digits delta_0..delta_4 of two values p' (|p'| < 1): d[s] holds digit s
+// of both.  In pair mode p' = a + b (an FP32 pair, |b| <= ulp(a)/2): delta_0 and
+// delta_1 come from a exactly, then b joins the residual (one rounding far below
+// 2^-40).
+template <bool kPair>
+__device__ __forceinline__ void digits5x2(f2 a, f2 b, f2 (&d)[5]) {
+    const f2 c8 = pk(49152.f, 49152.f), c16 = pk(192.f, 192.f), c24 = pk(0.75f, 0.75f),
+             c32 = pk(0x1.8p-9f, 0x1.8p-9f), c40 = pk(0x1.8p-17f, 0x1.8p-17f);
+    d[0] = grid2(a, c8);
+    f2 r = sub2(a, d[0]);
+    d[1] = grid2(r, c16);
+    r = sub2(r, d[1]);
+    if constexpr (kPair) r = add2(r, b);
+    d[2] = grid2(r, c24);
+    r = sub2(r, d[2]);
+    d[3] = grid2(r, c32);
+    r = sub2(r, d[3]);
+    d[4] = grid2(r, c40);
 }
 
-// Digits of hi' + lo' (an FP32 pair, |lo'| <= ulp(hi')/2): delta_0 and delta_1 from
-// hi' exactly, then lo' joins the residual (one rounding far below 2^-40).
-__device__ __forceinline__ void digits5_pair(float a, float b, float (&d)[5]) {
-    d[0] = grid(a, 49152.f);
-    float r = sub_rn(a, d[0]);
-    d[1] = grid(r, 192.f);
-    r = add_rn(sub_rn(r, d[1]), b);
-    d[2] = grid(r, 0.75f);
-    r = sub_rn(r, d[2]);
-    d[3] = grid(r, 0x1.8p-9f);
-    r = sub_rn(r, d[3]);
-    d[4] = grid(r, 0x1.8p-17f);
-}
-
-// two exact-BF16 FP32 values -> one word, the lower K element in the low half
-__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
-    return __byte_perm(__float_as_uint(lo_k), __float_as_uint(hi_k), 0x7632);
+// two packed pairs (k, k+1) and (k+2, k+3) of one digit -> two BF16x2 words
+__device__ __forceinline__ void pack4(f2 p01, f2 p23, uint32_t& w0, uint32_t& w1) {
+    float x0, x1, x2, x3;
+    upk(p01, x0, x1);
+    upk(p23, x2, x3);
+    w0 = __byte_perm(__float_as_uint(x0), __float_as_uint(x1), 0x7632);
+    w1 = __byte_perm(__float_as_uint(x2), __float_as_uint(x3), 0x7632);
 }
 
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }   // -126 <= e <= 127
@@ -241,23 +266,12 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
                     const float4 v = *reinterpret_cast<const float4*>(src + ((cc ^ (r & 7)) << 4));
                     float4 vl = make_float4(0.f, 0.f, 0.f, 0.f);
                     if constexpr (kPair) vl = *reinterpret_cast<const float4*>(src + kHalfBytes + ((cc ^ (r & 7)) << 4));
-                    float dx[5], dy[5], dz[5], dw[5];
-                    if constexpr (kPair) {
-                        digits5_pair(v.x * scale, vl.x * scale, dx);
-                        digits5_pair(v.y * scale, vl.y * scale, dy);
-                        digits5_pair(v.z * scale, vl.z * scale, dz);
-                        digits5_pair(v.w * scale, vl.w * scale, dw);
-                    } else {
-                        digits5(v.x * scale, dx);
-                        digits5(v.y * scale, dy);
-                        digits5(v.z * scale, dz);
-                        digits5(v.w * scale, dw);
-                    }
+                    const f2 sc = pk(scale, scale);
+                    f2 d01[5], d23[5];
+                    digits5x2<kPair>(mul2(pk(v.x, v.y), sc), mul2(pk(vl.x, vl.y), sc), d01);
+                    digits5x2<kPair>(mul2(pk(v.z, v.w), sc), mul2(pk(vl.z, vl.w), sc), d23);
 #pragma unroll
-                    for (int s = 0; s < 5; ++s) {
-                        w[s][2 * c4] = pack_bf16(dx[s], dy[s]);
-                        w[s][2 * c4 + 1] = pack_bf16(dz[s], dw[s]);
-                    }
+                    for (int s = 0; s < 5; ++s) pack4(d01[s], d23[s], w[s][2 * c4], w[s][2 * c4 + 1]);
                 }
                 if (part == 1) mbar_arrive(&r_empty[rs]);      // both parts read: the slot may refill
                 // A operand in TMEM: lane = row, column = two consecutive k; slice s of
