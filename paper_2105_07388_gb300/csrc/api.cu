@@ -972,6 +972,7 @@ int re_sketch_apply_exact(re_handle h, const float* A, int64_t m, int64_t n, int
     e = cudaMemcpyAsync(&tmo, static_cast<int*>(h->status.p) + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "exact sketch step");
+    resolve_timings(h);
     if (tmo) return fail(RE_ERR_TIMEOUT, "a bounded device wait expired");
     return RE_OK;
 }
