@@ -26,24 +26,23 @@
 // of L0, L1 and L2 is at most 2^16 of its level's unit, so a partial sum stays an
 // exactly representable FP32 integer multiple of the unit while it is below
 // 2^24 units: the sums are exact, whatever order the tensor core adds them in.
-// Over a segment of 8192 terms the partial sums are random walks (the digits of
-// the embedding are independent of P) with a standard deviation of at most 2^19.5
-// units, so 2^24 is more than 20 standard deviations away.  R3 is rounded by
+// Over a segment of 32768 terms the partial sums are random walks (the digits of
+// the embedding are independent of P) with a standard deviation of at most 2^20.5
+// units, so 2^24 is more than 11 standard deviations away.  R3 is rounded by
 // FP32 as it accumulates: at most about 2^-24 sqrt(2048) of a level that is
 // itself about 2^-21 of L0, i.e. near 2^-39 of the result.
 // After each segment the epilogue warps convert the four accumulators to
 // integers in units of 2^-40 (exact for L0..L2, R3 rounded to 2^-40) and add them
-// into an int64 tile in shared memory; at the end of a tile they add that tile
-// into the int64 output with atomic adds -- integer additions, so tiles split
-// between CTAs (stream-K) sum exactly and the result does not depend on the
-// order.  D_rq = T_rq 2^(e_r - 40); |T| < K 2^42.6 fits int64 for K <= 2^20.
+// into the int64 output with atomic adds -- integer additions, so segments and
+// tiles split between CTAs (stream-K) sum exactly and the result does not depend
+// on the order.  D_rq = T_rq 2^(e_r - 40); |T| < K 2^42.6 fits int64 for K <= 2^20.
 //
 // Warp roles (persistent, one CTA per SM, 128-row P tiles x NT (<= 64) Q rows,
 // K chunks of 64, stream-K over (tile, chunk)):
 //   warps 0-7   converters: warp (q, h) converts, for row 32q + lane, half h
 //               (32 K) of every chunk into five digit slices in TMEM (the MMA's
 //               A operand), three TMEM stages of 5 x 16 columns.
-//   warps 8-11  epilogue: drains the accumulators into the int64 tile.
+//   warps 8-11  epilogue: drains the accumulators into the int64 output.
 //   warp 12     TMA producer of P (FP32 half chunks 128 x 32, 128B swizzle,
 //               zero fill past the edges; the lo plane too in pair mode).
 //   warp 13     TMA producer of the two Q digit slices (NT rows x 64 K each).
@@ -77,15 +76,14 @@ constexpr int kPProdWarp = kConvWarps + kEpiWarps;
 constexpr int kQProdWarp = kPProdWarp + 1;
 constexpr int kMmaWarp = kQProdWarp + 1;
 constexpr uint32_t kHalfBytes = kBM * 32 * 4;     // 16 KB FP32 half chunk
-constexpr int kRingMax = 4;                        // FP32 half-chunk ring: 4 slots (2 for pairs)
+constexpr int kRingMax = 8;                        // FP32 half-chunk ring: 8 slots (4 for pairs)
 constexpr int kAStages = 3;                        // TMEM digit stages (one half chunk each)
 constexpr int kQStages = 3;                        // Q chunk stages
 constexpr uint32_t kAccCols = 64;                  // TMEM columns per accumulator
 constexpr uint32_t kAStageCol = 4 * kAccCols;      // 256
 constexpr uint32_t kAStageCols = 5 * 16;           // five slices x 32 K (16 columns of BF16 pairs)
 constexpr uint32_t kTmemCols = 512;
-constexpr int kSegChunks = 128;                    // 8192 K per exact segment
-constexpr int kTPitch = kBM + 1;                   // int64 tile: column-major, odd pitch
+constexpr int kSegChunks = 512;                    // 32768 K per exact segment
 static_assert(kAStageCol + kAStages * kAStageCols <= kTmemCols, "TMEM budget");
 
 struct ExParams {
@@ -174,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
                                                                 const __grid_constant__ CUtensorMap qmap,
                                                                 const ExParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    constexpr int kRing = kPair ? 2 : kRingMax;
+    constexpr int kRing = kPair ? kRingMax / 2 : kRingMax;
     __shared__ __align__(8) uint64_t r_full[kRingMax], r_empty[kRingMax];
     __shared__ __align__(8) uint64_t a_full[kAStages], a_empty[kAStages];
     __shared__ __align__(8) uint64_t q_full[kQStages], q_empty[kQStages];
@@ -189,7 +187,6 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
     unsigned char* ring = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* qbuf = ring + (size_t)kRing * NP * kHalfBytes;
-    long long* tacc = reinterpret_cast<long long*>(qbuf + (size_t)kQStages * q_stage);
 
     if (tid == 0) {
         for (int i = 0; i < kRing; ++i) {
@@ -211,7 +208,6 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
-    for (int i = tid; i < p.NT * kTPitch; i += blockDim.x) tacc[i] = 0;
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_tmem)),
@@ -414,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
             mbar_drain(&done_bar, 0);
         }
     } else {
-        // ---------------- epilogue: drain each segment into the int64 tile, add tiles out
+        // ---------------- epilogue: each segment's sums, as int64, added into the output
         const int q = warp - kConvWarps;          // lane quarter (warps 8..11 -> 0..3)
         const int r = 32 * q + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
@@ -424,6 +420,10 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
             const int64_t tile = t_first + j;
             const int64_t t0 = tile * K;
             const int64_t k0 = std::max(c_begin, t0) - t0, k1 = std::min(c_end, t0 + K) - t0;
+            const int64_t row = (tile / p.ntn) * kBM + r;
+            const int n0 = (int)(tile % p.ntn) * p.NT;
+            const int nvalid = std::min(p.NT, p.N - n0);
+            unsigned long long* out = p.T + row * p.ldt + n0;
             for (int64_t sk = k0; sk < k1; sk += kSegChunks) {
                 ok = mbar_wait(&accf, (uint32_t)(nseg & 1), &s_abort, p.err);
                 if (!__all_sync(0xffffffffu, ok)) {
@@ -437,32 +437,21 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
                     tmem_ld16(lane_base + kAccCols + (uint32_t)c, v1);
                     tmem_ld16(lane_base + 2 * kAccCols + (uint32_t)c, v2);
                     tmem_ld16(lane_base + 3 * kAccCols + (uint32_t)c, v3);
+                    if (row < p.M) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        // units of 2^-40: L0 (2^-13), L1 (2^-21), L2 (2^-29) exact, R3 rounded
-                        const long long t = (__float2ll_rn(v0[i] * 8192.f) << 27) +
-                                            (__float2ll_rn(v1[i] * 2097152.f) << 19) +
-                                            (__float2ll_rn(v2[i] * 536870912.f) << 11) +
-                                            __float2ll_rn(v3[i] * 1099511627776.f);
-                        tacc[(size_t)(c + i) * kTPitch + r] += t;
+                        for (int i = 0; i < 16; ++i) {
+                            // units of 2^-40: L0 (2^-13), L1 (2^-21), L2 (2^-29) exact, R3 rounded
+                            const long long t = (__float2ll_rn(v0[i] * 8192.f) << 27) +
+                                                (__float2ll_rn(v1[i] * 2097152.f) << 19) +
+                                                (__float2ll_rn(v2[i] * 536870912.f) << 11) +
+                                                __float2ll_rn(v3[i] * 1099511627776.f);
+                            if (c + i < nvalid && t != 0) atomicAdd(out + c + i, (unsigned long long)t);
+                        }
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(&acce);
                 ++nseg;
-            }
-            if (!ok) break;
-            // tile done (for this CTA): add it into the output and clear it
-            const int64_t mt = tile / p.ntn;
-            const int nt = (int)(tile % p.ntn);
-            const int64_t row = mt * kBM + r;
-            const int n0 = nt * p.NT;
-            const int nvalid = std::min(p.NT, p.N - n0);
-            for (int c = 0; c < p.NT; ++c) {
-                long long& cell = tacc[(size_t)c * kTPitch + r];
-                if (c < nvalid && row < p.M && cell != 0)
-                    atomicAdd(p.T + row * p.ldt + n0 + c, (unsigned long long)cell);
-                cell = 0;
             }
         }
     }
@@ -713,10 +702,9 @@ cudaError_t launch_ex_sketch(const float* P, const float* P_lo, int64_t ldp, int
     p.ldt = ldt;
     p.err = err_flag;
     const int np = P_lo ? 2 : 1;
-    const int ring = P_lo ? 2 : kRingMax;
+    const int ring = P_lo ? kRingMax / 2 : kRingMax;
     const uint32_t q_stage = ((uint32_t)2 * NT * kBK * 2 + 1023u) & ~1023u;
-    const size_t smem = (size_t)ring * np * kHalfBytes + (size_t)kQStages * q_stage +
-                        sizeof(long long) * (size_t)NT * kTPitch + 1024;
+    const size_t smem = (size_t)ring * np * kHalfBytes + (size_t)kQStages * q_stage + 1024;
     if (!g_ex_sms) {
         int dev = 0;
         cudaGetDevice(&dev);

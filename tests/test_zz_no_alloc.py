@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import algorithm1 as alg
 from paper_2105_07388_gb300 import rankest as rk
 
 pytestmark = pytest.mark.gpu
@@ -51,6 +52,14 @@ def test_noalloc_matches_sketch_apply_two_calls(h, m, n):
         k_ref = core_ref[:2 * c1, :c1].cpu().numpy()
         k_new = core_new[:2 * c1, :c1].cpu().numpy()
         assert np.max(np.abs(k_new - k_ref)) <= 1e-5 * np.abs(k_ref).max()
+        # and against the FP64 oracle's core entry by entry, with the FP32 bound of
+        # the other core tests (A X and Y (A X) both accumulated in FP32)
+        A64 = A.double().cpu().numpy()
+        Ao = A64.T if m < n else A64
+        X, Y = alg.embeddings(alg.GAUSSIAN, Ao.shape[1], Ao.shape[0], c1, 77)
+        ref = Y @ (Ao @ X)
+        bound = 4.0 * (Ao.shape[0] / 32 + Ao.shape[1] / 32 + 64) * U32 * (np.abs(Y) @ np.abs(Ao) @ np.abs(X))
+        assert np.all(np.abs(k_new - ref) <= bound), float(np.max(np.abs(k_new - ref) / bound))
 
 
 def test_noalloc_rejects_oversize():
