@@ -39,14 +39,14 @@
 //
 // Warp roles (persistent, one CTA per SM, 128-row P tiles x NT (<= 64) Q rows,
 // K chunks of 64, stream-K over (tile, chunk)):
-//   warps 0-7   converters: warp (q, h) converts, for row 32q + lane, half h
-//               (32 K) of every chunk into five digit slices in TMEM (the MMA's
-//               A operand), three TMEM stages of 5 x 16 columns.
-//   warps 8-11  epilogue: drains the accumulators into the int64 output.
-//   warp 12     TMA producer of P (FP32 half chunks 128 x 32, 128B swizzle,
+//   warps 0-15  converters: warp (q, h, part) converts, for row 32q + lane, 16 K
+//               (part) of half h (32 K) of every chunk into five digit slices in
+//               TMEM (the MMA's A operand), three TMEM stages of 5 x 16 columns.
+//   warps 16-19 epilogue: drains the accumulators into the int64 output.
+//   warp 20     TMA producer of P (FP32 half chunks 128 x 32, 128B swizzle,
 //               zero fill past the edges; the lo plane too in pair mode).
-//   warp 13     TMA producer of the two Q digit slices (NT rows x 64 K each).
-//   warp 14     TMEM allocation; one thread issues 9 tcgen05.mma (M = 128,
+//   warp 21     TMA producer of the two Q digit slices (NT rows x 64 K each).
+//   warp 22     TMEM allocation; one thread issues 9 tcgen05.mma (M = 128,
 //               N = NT, K = 16, BF16 -> FP32) per K step.
 // TMEM: accumulators at columns [0, 256) (64 per accumulator), A stages from 256.
 // Every mbarrier wait is bounded in time (2 s): on expiry the kernel raises the
@@ -69,7 +69,8 @@ using namespace tc;
 constexpr int kBM = 128;
 constexpr int kBK = 64;
 constexpr int kNTMax = 64;                 // Q rows per tile (MMA N)
-constexpr int kConvWarps = 8;
+constexpr int kConvParts = 2;                      // converter warps per (lane quarter, half chunk)
+constexpr int kConvWarps = 8 * kConvParts;
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = (kConvWarps + kEpiWarps + 3) * 32;
 constexpr int kPProdWarp = kConvWarps + kEpiWarps;
@@ -164,6 +165,16 @@ __device__ __forceinline__ void pack4(f2 p01, f2 p23, uint32_t& w0, uint32_t& w1
     w1 = __byte_perm(__float_as_uint(x2), __float_as_uint(x3), 0x7632);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }   // -126 <= e <= 127
 
 template <bool kPair>
@@ -191,10 +202,10 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
     if (tid == 0) {
         for (int i = 0; i < kRing; ++i) {
             mbar_init(&r_full[i], 1);
-            mbar_init(&r_empty[i], 4 * 32);
+            mbar_init(&r_empty[i], 4 * kConvParts * 32);
         }
         for (int i = 0; i < kAStages; ++i) {
-            mbar_init(&a_full[i], 4 * 32);
+            mbar_init(&a_full[i], 4 * kConvParts * 32);
             mbar_init(&a_empty[i], 1);
         }
         for (int i = 0; i < kQStages; ++i) {
@@ -230,8 +241,9 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
     const int64_t ntile_span = total_chunks > 0 ? (c_end - 1) / K - t_first + 1 : 0;
 
     if (warp < kConvWarps) {
-        // ---------------- converters: rows 32q + lane, half h of every chunk
-        const int q = warp & 3, h = warp >> 2;
+        // ---------------- converters: rows 32q + lane, 32 / kConvParts K of half h of every chunk
+        constexpr int KP = 2 / kConvParts;                     // 16-K parts per converter warp
+        const int q = warp & 3, h = (warp >> 2) & 1, part0 = (warp >> 3) * KP;
         const int r = 32 * q + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         int64_t mt = t_first / p.ntn, kc = c_begin % K;      // stepped below, no division in the loop
@@ -254,7 +266,8 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
             const unsigned char* src = ring + (size_t)rs * NP * kHalfBytes + (size_t)r * 128;
             tc_fence_after();
 #pragma unroll
-            for (int part = 0; part < 2; ++part) {            // 16 K per part
+            for (int pi = 0; pi < KP; ++pi) {                  // 16 K per part
+                const int part = part0 + pi;
                 uint32_t w[5][8];
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
@@ -269,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
 #pragma unroll
                     for (int s = 0; s < 5; ++s) pack4(d01[s], d23[s], w[s][2 * c4], w[s][2 * c4 + 1]);
                 }
-                if (part == 1) mbar_arrive(&r_empty[rs]);      // both parts read: the slot may refill
+                if (pi == KP - 1) mbar_arrive(&r_empty[rs]);   // all parts read: the slot may refill
                 // A operand in TMEM: lane = row, column = two consecutive k; slice s of
                 // stage sa at kAStageCol + 80 sa + 16 s, this part at + 8 part
                 const uint32_t col = kAStageCol + kAStageCols * (uint32_t)sa + 8u * (uint32_t)part;
@@ -411,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
         }
     } else {
         // ---------------- epilogue: each segment's sums, as int64, added into the output
-        const int q = warp - kConvWarps;          // lane quarter (warps 8..11 -> 0..3)
+        const int q = warp - kConvWarps;          // lane quarter of this epilogue warp
         const int r = 32 * q + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
         int64_t nseg = 0;
@@ -431,15 +444,15 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
                     break;
                 }
                 tc_fence_after();
-                for (int c = 0; c < p.NT; c += 16) {
-                    float v0[16], v1[16], v2[16], v3[16];
-                    tmem_ld16(lane_base + (uint32_t)c, v0);
-                    tmem_ld16(lane_base + kAccCols + (uint32_t)c, v1);
-                    tmem_ld16(lane_base + 2 * kAccCols + (uint32_t)c, v2);
-                    tmem_ld16(lane_base + 3 * kAccCols + (uint32_t)c, v3);
+                for (int c = 0; c < p.NT; c += 8) {
+                    float v0[8], v1[8], v2[8], v3[8];
+                    tmem_ld8(lane_base + (uint32_t)c, v0);
+                    tmem_ld8(lane_base + kAccCols + (uint32_t)c, v1);
+                    tmem_ld8(lane_base + 2 * kAccCols + (uint32_t)c, v2);
+                    tmem_ld8(lane_base + 3 * kAccCols + (uint32_t)c, v3);
                     if (row < p.M) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
+                        for (int i = 0; i < 8; ++i) {
                             // units of 2^-40: L0 (2^-13), L1 (2^-21), L2 (2^-29) exact, R3 rounded
                             const long long t = (__float2ll_rn(v0[i] * 8192.f) << 27) +
                                                 (__float2ll_rn(v1[i] * 2097152.f) << 19) +
