@@ -16,39 +16,43 @@
 // 2^-8, 2^-16, 2^-24, 2^-32, 2^-40 (delta_0 = n 2^-8 with |n| <= 256, the others
 // |n| <= 129), each exact in BF16, by adding and subtracting 1.5 2^k (exact
 // rounding to a grid); the part of p' below 2^-41 is dropped.  The products
-// delta_s xi_t are then exact, and grouped by level s + t into four TMEM
+// delta_s xi_t are then exact, and summed by level s + t into five TMEM
 // accumulators:
 //   L0 = sum delta_0 xi_0                    multiples of 2^-13
 //   L1 = sum delta_0 xi_1 + delta_1 xi_0     multiples of 2^-21
 //   L2 = sum delta_1 xi_1 + delta_2 xi_0     multiples of 2^-29
-//   R3 = the levels 3 and 4 (delta_2 xi_1, delta_3 xi_0, delta_3 xi_1, delta_4 xi_0)
-// (the level-5 product delta_4 xi_1 is below 2^-46 and dropped).  Each product
-// of L0, L1 and L2 is at most 2^16 of its level's unit, so a partial sum stays an
-// exactly representable FP32 integer multiple of the unit while it is below
-// 2^24 units: the sums are exact, whatever order the tensor core adds them in.
-// Over a segment of 32768 terms the partial sums are random walks (the digits of
-// the embedding are independent of P) with a standard deviation of at most 2^20.5
-// units, so 2^24 is more than 11 standard deviations away.  R3 is rounded by
-// FP32 as it accumulates: at most about 2^-24 sqrt(2048) of a level that is
-// itself about 2^-21 of L0, i.e. near 2^-39 of the result.
-// After each segment the epilogue warps convert the four accumulators to
-// integers in units of 2^-40 (exact for L0..L2, R3 rounded to 2^-40) and add them
-// into the int64 output with atomic adds -- integer additions, so segments and
-// tiles split between CTAs (stream-K) sum exactly and the result does not depend
-// on the order.  D_rq = T_rq 2^(e_r - 40); |T| < K 2^42.6 fits int64 for K <= 2^20.
+//   L3 = sum delta_2 xi_1 + delta_3 xi_0     multiples of 2^-37
+//   L4 = sum delta_3 xi_1 + delta_4 xi_0     (rounded; below 2^-29 of L0)
+// (the level-5 product delta_4 xi_1 is below 2^-46 and dropped).  One MMA per A
+// digit slice s multiplies it with both Q slices at once (N = 2 NT, the two
+// slices being adjacent rows of the Q stage), writing (s, 0) into L_s and (s, 1)
+// into the next accumulator L_{s+1}: five MMAs per K step.  Each product of L0 ..
+// L3 is at most 2^16 of its level's unit, so a partial sum stays an exactly
+// representable FP32 integer multiple of the unit while it is below 2^24 units:
+// the sums are exact, whatever order the tensor core adds them in.  Over a
+// segment of 32768 terms the partial sums are random walks (the digits of the
+// embedding are independent of P) with a standard deviation of at most 2^20.5
+// units, so 2^24 is more than 11 standard deviations away.  L4 is rounded by FP32
+// as it accumulates, far below 2^-40 of the result.
+// After each segment the epilogue warps convert the accumulators to integers in
+// units of 2^-40 (exact for L0..L3, L4 rounded), add them into the int64 output
+// with atomic adds -- integer additions, so segments and tiles split between
+// CTAs (stream-K) sum exactly and the result does not depend on the order -- and
+// clear the accumulators for the next segment.  D_rq = T_rq 2^(e_r - 40);
+// |T| < K 2^42.6 fits int64 for K <= 2^20.
 //
 // Warp roles (persistent, one CTA per SM, 128-row P tiles x NT (<= 64) Q rows,
 // K chunks of 64, stream-K over (tile, chunk)):
 //   warps 0-15  converters: warp (q, h, part) converts, for row 32q + lane, 16 K
 //               (part) of half h (32 K) of every chunk into five digit slices in
-//               TMEM (the MMA's A operand), three TMEM stages of 5 x 16 columns.
+//               TMEM (the MMA's A operand), two TMEM stages of 5 x 16 columns.
 //   warps 16-19 epilogue: drains the accumulators into the int64 output.
 //   warp 20     TMA producer of P (FP32 half chunks 128 x 32, 128B swizzle,
 //               zero fill past the edges; the lo plane too in pair mode).
 //   warp 21     TMA producer of the two Q digit slices (NT rows x 64 K each).
-//   warp 22     TMEM allocation; one thread issues 9 tcgen05.mma (M = 128,
-//               N = NT, K = 16, BF16 -> FP32) per K step.
-// TMEM: accumulators at columns [0, 256) (64 per accumulator), A stages from 256.
+//   warp 22     TMEM allocation; one thread issues 5 tcgen05.mma (M = 128,
+//               N = 2 NT or NT, K = 16, BF16 -> FP32) per K step.
+// TMEM: accumulators L0..L4 at columns [0, 5 NT) (NT apart), A stages from 320.
 // Every mbarrier wait is bounded in time (2 s): on expiry the kernel raises the
 // error flag, every role drains what it has in flight and TMEM is freed.
 #include <cuda.h>
@@ -78,14 +82,15 @@ constexpr int kQProdWarp = kPProdWarp + 1;
 constexpr int kMmaWarp = kQProdWarp + 1;
 constexpr uint32_t kHalfBytes = kBM * 32 * 4;     // 16 KB FP32 half chunk
 constexpr int kRingMax = 8;                        // FP32 half-chunk ring: 8 slots (4 for pairs)
-constexpr int kAStages = 3;                        // TMEM digit stages (one half chunk each)
+constexpr int kAStages = 2;                        // TMEM digit stages (one half chunk each)
 constexpr int kQStages = 3;                        // Q chunk stages
-constexpr uint32_t kAccCols = 64;                  // TMEM columns per accumulator
-constexpr uint32_t kAStageCol = 4 * kAccCols;      // 256
+constexpr int kLevels = 5;                         // accumulators L0..L4, NT columns each
+constexpr uint32_t kAStageCol = kLevels * kNTMax;  // 320
 constexpr uint32_t kAStageCols = 5 * 16;           // five slices x 32 K (16 columns of BF16 pairs)
 constexpr uint32_t kTmemCols = 512;
 constexpr int kSegChunks = 512;                    // 32768 K per exact segment
 static_assert(kAStageCol + kAStages * kAStageCols <= kTmemCols, "TMEM budget");
+static_assert(kNTMax * 2 <= 256, "MMA N");
 
 struct ExParams {
     const int* rexp;          // e_r of every P row (|p_rk| < 2^e_r), -127 <= e_r <= 126
@@ -356,7 +361,13 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(p.NT);
+            // one MMA per A digit slice s against both Q slices at once (N = 2 NT: the
+            // two slices are contiguous rows of the Q stage) writes the products
+            // (s, 0) and (s, 1) into the adjacent accumulators L_s and L_{s+1}: level
+            // s + t lands in L_{s+t}.  The last slice takes Q slice 0 only.  The
+            // epilogue zeroes the accumulators before each segment, so every MMA adds.
+            const uint32_t idesc2 = idesc_bf16(2 * p.NT), idesc1 = idesc_bf16(p.NT);
+            const uint32_t lstride = (uint32_t)p.NT;
             int64_t g = 0;            // chunk counter within this CTA's range
             int64_t nseg = 0;         // drains so far
             bool ok = true;
@@ -365,13 +376,12 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
                 const int64_t k0 = std::max(c_begin, t0) - t0, k1 = std::min(c_end, t0 + K) - t0;
                 for (int64_t sk = k0; sk < k1 && ok; sk += kSegChunks) {
                     const int64_t sk1 = std::min(k1, sk + kSegChunks);
-                    // the accumulators are free once the previous drain has read them
-                    if (!mbar_wait(&acce, (uint32_t)((nseg & 1) ^ 1), &s_abort, p.err)) {
+                    // the accumulators are zero once the epilogue has drained (and cleared) them
+                    if (!mbar_wait(&acce, (uint32_t)(nseg & 1), &s_abort, p.err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    bool first = true;
                     for (int64_t kc = sk; kc < sk1; ++kc, ++g) {
                         const int sq = (int)(g % kQStages);
                         if (!mbar_wait(&q_full[sq], (uint32_t)((g / kQStages) & 1), &s_abort, p.err)) {
@@ -390,24 +400,12 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
                             const uint32_t ast = tmem_base + kAStageCol + kAStageCols * (uint32_t)sa;
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {
-                                const uint32_t koff = 32u * (uint32_t)(2 * h + kk);
-                                const uint64_t b0 = sw128_desc(qst + koff);
-                                const uint64_t b1 = sw128_desc(qst + q_slice_bytes + koff);
-                                const uint32_t a0 = ast + 8u * kk, a1 = a0 + 16u, a2 = a0 + 32u, a3 = a0 + 48u,
-                                               a4 = a0 + 64u;
-                                const uint32_t d0 = tmem_base, d1 = tmem_base + kAccCols,
-                                               d2 = tmem_base + 2 * kAccCols, d3 = tmem_base + 3 * kAccCols;
-                                const uint32_t acc = first ? 0u : 1u;
-                                mma_bf16_ts(d0, a0, b0, idesc, acc);
-                                mma_bf16_ts(d1, a0, b1, idesc, acc);
-                                mma_bf16_ts(d1, a1, b0, idesc, 1u);
-                                mma_bf16_ts(d2, a1, b1, idesc, acc);
-                                mma_bf16_ts(d2, a2, b0, idesc, 1u);
-                                mma_bf16_ts(d3, a2, b1, idesc, acc);
-                                mma_bf16_ts(d3, a3, b0, idesc, 1u);
-                                mma_bf16_ts(d3, a3, b1, idesc, 1u);
-                                mma_bf16_ts(d3, a4, b0, idesc, 1u);
-                                first = false;
+                                const uint64_t b = sw128_desc(qst + 32u * (uint32_t)(2 * h + kk));
+                                const uint32_t a0 = ast + 8u * kk;
+#pragma unroll
+                                for (int sl = 0; sl < 4; ++sl)
+                                    mma_bf16_ts(tmem_base + lstride * sl, a0 + 16u * sl, b, idesc2, 1u);
+                                mma_bf16_ts(tmem_base + lstride * 4, a0 + 64u, b, idesc1, 1u);
                             }
                             mma_commit(&a_empty[sa]);
                         }
@@ -427,8 +425,19 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
         const int q = warp - kConvWarps;          // lane quarter of this epilogue warp
         const int r = 32 * q + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+        const uint32_t ncols = (uint32_t)(kLevels * p.NT);
+        // clear the accumulators (this warp's lanes), then let the MMAs start
+        auto clear = [&]() {
+            const uint32_t z[16] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            for (uint32_t c = 0; c < ncols; c += 16) tmem_st16(lane_base + c, z);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(&acce);
+        };
+        clear();
         int64_t nseg = 0;
         bool ok = true;
+        const uint32_t ls = (uint32_t)p.NT;
         for (int64_t j = 0; j < ntile_span && ok; ++j) {
             const int64_t tile = t_first + j;
             const int64_t t0 = tile * K;
@@ -445,25 +454,28 @@ __global__ void __launch_bounds__(kThreads, 1) ex_sketch_kernel(const __grid_con
                 }
                 tc_fence_after();
                 for (int c = 0; c < p.NT; c += 8) {
-                    float v0[8], v1[8], v2[8], v3[8];
+                    float v0[8], v1[8], v2[8], v3[8], v4[8];
                     tmem_ld8(lane_base + (uint32_t)c, v0);
-                    tmem_ld8(lane_base + kAccCols + (uint32_t)c, v1);
-                    tmem_ld8(lane_base + 2 * kAccCols + (uint32_t)c, v2);
-                    tmem_ld8(lane_base + 3 * kAccCols + (uint32_t)c, v3);
+                    tmem_ld8(lane_base + ls + (uint32_t)c, v1);
+                    tmem_ld8(lane_base + 2 * ls + (uint32_t)c, v2);
+                    tmem_ld8(lane_base + 3 * ls + (uint32_t)c, v3);
+                    tmem_ld8(lane_base + 4 * ls + (uint32_t)c, v4);
                     if (row < p.M) {
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            // units of 2^-40: L0 (2^-13), L1 (2^-21), L2 (2^-29) exact, R3 rounded
+                            // units of 2^-40: L0 (2^-13), L1 (2^-21), L2 (2^-29), L3 (2^-37)
+                            // exact, L4 rounded
                             const long long t = (__float2ll_rn(v0[i] * 8192.f) << 27) +
                                                 (__float2ll_rn(v1[i] * 2097152.f) << 19) +
                                                 (__float2ll_rn(v2[i] * 536870912.f) << 11) +
-                                                __float2ll_rn(v3[i] * 1099511627776.f);
+                                                (__float2ll_rn(v3[i] * 137438953472.f) << 3) +
+                                                __float2ll_rn(v4[i] * 1099511627776.f);
                             if (c + i < nvalid && t != 0) atomicAdd(out + c + i, (unsigned long long)t);
                         }
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(&acce);
+                clear();
                 ++nseg;
             }
         }
