@@ -260,6 +260,17 @@ int re_core_sigma(re_handle h, const double* core, int r2, int s, int64_t ld,
                   double* sigma, void* stream);
 
 /*
+ * Step 7 alone with the precision mode's preconditioned singular values (same
+ * arguments as re_core_sigma): FP32 QR + Jacobi of the core gives its right
+ * singular vectors V1, W = core * V1 is formed in FP64, and the singular values
+ * of W are taken by FP32 QR + Jacobi with a purely relative rotation test.  W's
+ * columns are graded, so each value keeps its relative accuracy far below
+ * u * sigma_1 (about 1e-12 * sigma_1 absolute).  Synchronises `stream`.
+ */
+int re_core_sigma_exact(re_handle h, const double* core, int r2, int s, int64_t ld,
+                        double* sigma, void* stream);
+
+/*
  * The embeddings themselves, for tests and for callers that want X or Y
  * explicitly (the estimator never materialises them this way):
  *   re_embedding_x: out (device FP32, n x s row-major) = columns col0.. of the

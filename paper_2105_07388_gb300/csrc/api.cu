@@ -646,6 +646,32 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
             }
         }
     }
+    // The exact-product sketch costs about the same per pass for up to 64 new columns
+    // (one Q tile: its MMA count does not depend on the tile's width), so its first
+    // pass appends up to 64 columns at once and the read-off runs on the nested
+    // leading blocks of the core at s0, 2 s0, ... within it: the plain ladder's
+    // answer, with fewer passes over A.
+    if (!done && !o.learned && exact_mode(h, P) && s_prev == 0) {
+        int w1 = s;
+        while (w1 * 2 <= std::min(64, smax)) w1 *= 2;
+        if (w1 > s) {
+            if (int r = sketch_to(0, w1)) return r;
+            passes = 1;
+            for (int w = s; w <= w1 && !done; w *= 2) {
+                if (int r = check_width(h, P, w, smax, eps, &ro, &r1, st, 2 * w <= smax)) return r;
+                s = w;
+                done = ro.rank >= 0 || r1 >= P.A.cols;
+            }
+            if (!done) {
+                if (2 * s > smax) {
+                    done = true;
+                } else {
+                    s_prev = s;
+                    s *= 2;
+                }
+            }
+        }
+    }
     while (!done) {
         if (int r = sketch_to(P.kind == RE_HRTT ? 0 : s_prev, s)) return r;
         ++passes;
@@ -989,6 +1015,26 @@ int re_core_sigma(re_handle h, const double* core, int r2, int s, int64_t ld, do
                                           static_cast<int*>(h->status.p),
                                           static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "core singular values");
+    return RE_OK;
+}
+
+int re_core_sigma_exact(re_handle h, const double* core, int r2, int s, int64_t ld, double* sigma, void* stream) {
+    if (!h || !core || !sigma) return fail(RE_ERR_ARG, "NULL argument");
+    if (s < 1 || s > 512 || r2 < s || r2 > 1024 || ld < s)
+        return fail(RE_ERR_ARG, "need 1 <= s <= 512, s <= r2 <= 1024, ld >= s");
+    cudaSetDevice(h->device);
+    if (int r = ensure(h->svdws, re::svd_workspace_bytes(r2, s))) return r;
+    if (int r = ensure(h->ex_svd, re::svd_precise_bytes(r2, s))) return r;
+    if (int r = ensure(h->status, 64)) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = re::launch_core_sigma_precise(core, r2, s, ld, h->svdws.p, h->ex_svd.p, sigma,
+                                                  static_cast<int*>(h->status.p), st);
+    if (e != cudaSuccess) return cuda_fail(e, "core singular values (precise)");
+    int stv = 0;
+    e = cudaMemcpyAsync(&stv, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "core singular values (precise)");
+    if (stv != RE_OK) return fail(stv, "non-finite values in the core");
     return RE_OK;
 }
 

@@ -117,6 +117,7 @@ _SIGS = {
                              _I64, _VP]),
     "re_sketch_apply_exact": (_I, [_VP, _VP, _I64, _I64, _I64, _I, _I, _U64, _VP, _I64, _VP, _I64, _VP]),
     "re_core_sigma": (_I, [_VP, _VP, _I, _I, _I64, _VP, _VP]),
+    "re_core_sigma_exact": (_I, [_VP, _VP, _I, _I, _I64, _VP, _VP]),
     "re_embedding_x": (_I, [_VP, _I, _U64, _I64, _I, _I, _VP, _VP]),
     "re_embedding_y": (_I, [_VP, _I, _U64, _I64, _I, _I, _VP, _VP]),
     "re_rank_estimate_batched": (_I, [_VP, ctypes.POINTER(re_block), _I, _I, _D, _I, _U64, _VP,
@@ -310,6 +311,12 @@ def re_core_sigma(h: int, core, sigma, stream=None, r2=None, s=None) -> None:
     r2 = core.shape[0] if r2 is None else r2
     s = core.shape[1] if s is None else s
     _check(lib().re_core_sigma(h, _ptr(core), r2, s, core.stride(0), _ptr(sigma), _stream(stream)))
+
+
+def re_core_sigma_exact(h: int, core, sigma, stream=None, r2=None, s=None) -> None:
+    r2 = core.shape[0] if r2 is None else r2
+    s = core.shape[1] if s is None else s
+    _check(lib().re_core_sigma_exact(h, _ptr(core), r2, s, core.stride(0), _ptr(sigma), _stream(stream)))
 
 
 def re_embedding_x(h: int, kind: int, seed: int, n: int, col0: int, s: int, out, stream=None):

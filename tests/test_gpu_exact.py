@@ -213,6 +213,8 @@ def test_exact_rank_at_eps_1e8(h, geom_case, center):
                                                         threshold=10000, max_line_width=200))
     assert res.final_s == orc.final_s and res.rank == orc.rank, (res.rank, orc.rank, res.final_s, orc.final_s)
     assert bool(res.flags & rk.RE_CONVERGED) == orc.converged
+    # the first pass of the exact-product sketch covers the widths up to 64
+    assert res.passes == 1 + max(0, int(round(np.log2(res.final_s / 64))))
     err = np.abs(sig[:k] - ref[:k])
     rel = err / ref[:k]
     s1 = ref[0]
@@ -228,3 +230,24 @@ def test_exact_rank_at_eps_1e8(h, geom_case, center):
     assert np.all(err <= bound), float(np.max(err / bound))
     # the decision itself is resolved: the error at tau is far below the margin
     assert rel[min(res.rank, k - 1)] < 0.1 * margin
+
+
+@pytest.mark.parametrize("r2,s,seed", [(128, 64, 1), (512, 256, 2), (1024, 512, 3), (600, 300, 4)])
+def test_precise_core_sigma_against_lapack(h, r2, s, seed):
+    """The preconditioned singular values (step 7 of the precision mode) against
+    LAPACK on cores with values spread over twelve decades: relative accuracy
+    1e-4 down to the smallest, where the FP32 form (re_core_sigma) has an absolute
+    error near 1e-5 sigma_1."""
+    gen = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(gen.standard_normal((r2, s)))
+    V, _ = np.linalg.qr(gen.standard_normal((s, s)))
+    sv = np.logspace(0, -12, s)
+    C = (U * sv) @ V.T
+    ref = np.linalg.svd(C, compute_uv=False)
+    sig = torch.zeros(s, dtype=torch.float64, device="cuda")
+    rk.re_core_sigma_exact(h, torch.from_numpy(C).cuda(), sig)
+    got = sig.cpu().numpy()
+    assert np.all(np.diff(got) <= 0)
+    err = np.abs(got - ref)
+    print(f"\n[precise sigma {r2}x{s}] max rel err {np.max(err / ref):.2e}, max |err|/sigma_1 {err.max() / ref[0]:.2e}")
+    assert np.all(err <= 1e-4 * ref + 1e-13 * ref[0]), float(np.max(err / (1e-4 * ref + 1e-13 * ref[0])))
