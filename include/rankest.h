@@ -117,7 +117,8 @@ typedef struct {
      * CUDA context stays usable.  Never set outside tests. */
     int test_drop_load;
     int sigma_est;   /* step 7: RE_SIGMA_SVD (default) or RE_SIGMA_QRDIAG */
-    int reserved[5];
+    int batch_first_width; /* batched tensor-core ladder: width of its first pass; 0 (default) = autotuned */
+    int reserved[4];
 } re_opts;
 
 /* Outcome of one estimate.  sigma values go to a separate caller buffer. */

@@ -787,6 +787,8 @@ int check_opts(const re_opts* o) {
     if (o->learned != 0 && o->learned != 1) return fail(RE_ERR_ARG, "learned must be 0 or 1");
     if (o->test_drop_load != 0 && o->test_drop_load != 1) return fail(RE_ERR_ARG, "test_drop_load must be 0 or 1");
     if (o->sigma_est != RE_SIGMA_SVD && o->sigma_est != RE_SIGMA_QRDIAG) return fail(RE_ERR_ARG, "unknown sigma_est");
+    if (o->batch_first_width < 0 || o->batch_first_width % 8 != 0)
+        return fail(RE_ERR_ARG, "batch_first_width must be 0 or a positive multiple of 8");
     if (o->sigma_est == RE_SIGMA_QRDIAG && o->precision == RE_PREC_EXACT)
         return fail(RE_ERR_UNSUPPORTED, "QR-diagonal estimates are FP32: not with the exact-product precision mode");
     return RE_OK;

@@ -8,8 +8,8 @@
 //   generator     X_b columns [s_prev, s) for every active block (own seed each)
 //   right sketch  one CTA per (block, row tile) work item (FP32 CUDA cores), or
 //                 the persistent tcgen05 kernel (BF16x3); on the tensor-core
-//                 path the first pass appends up to 4 s0 columns at once, so
-//                 the widths up to 4 s0 cost one read of each block
+//                 path the first pass appends up to w1 columns at once, so the
+//                 widths up to w1 cost one read of each block
 //   left sketch   one CTA per (block, core tile sized to the request), Y_b
 //                 generated on the fly
 //   core sigma    one CTA per block (QR + one-sided Jacobi in shared memory)
@@ -18,9 +18,13 @@
 // Inactive blocks cost each kernel only a flag test.  The whole ladder is
 // captured once into a CUDA graph and replayed for identical batches, so an
 // estimate of thousands of uneven blocks is one graph launch with no host
-// round trips.  The right sketch's tile height (64 or 128 rows) is chosen per
-// sketch width by timing both on the batch at hand (autotuner, cached per
-// handle and width).
+// round trips.  Autotuners, run on the batch at hand and cached with its graph:
+// on CUDA cores the right sketch's tile height (64 or 128 rows) per sketch width;
+// on the tensor cores the first pass's width w1 (s0, 2 s0, ... up to the X^T
+// pool), i.e. the N tile of the first pass -- a wider first pass costs little more
+// than a narrow one (it is bound by reading the blocks) and spares later passes
+// for the blocks that need them, but its tensor work grows; the ladders of every
+// candidate give the same bits, so the fastest is kept.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -262,14 +266,6 @@ __global__ void readoff_batched_kernel(const BatchDesc* __restrict__ d, int coun
     if (r.status != RE_OK || r.rank >= 0 || 2 * s > d[b].smax || r1 >= d[b].cols) active[b] = 0;
 }
 
-// Width the first tensor-core pass of the batched ladder reaches: 4 s0, within
-// the X^T pool (snew rows) and the ladder (smax).
-int first_pass_width(int s0, int snew, int smax) {
-    int w = s0;
-    while (w < 4 * s0 && 2 * w <= snew && 2 * w <= smax) w *= 2;
-    return w;
-}
-
 int r1_of(int s) {
     int r = 1;
     while ((2 * 11 * (r + 1) + 10) / 20 <= s) ++r;
@@ -285,6 +281,7 @@ struct BatchedState {
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned char> key;
     int bm_for[16] = {0};
+    int w1 = 0;                       // tensor-core path: width of the ladder's first pass
     int64_t launches_per_run = 0;
 };
 
@@ -477,77 +474,123 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
             e = cudaStreamSynchronize(bs);
             if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: autotune failed");
         }
-        // ---- capture the whole ladder
-        cudaGraph_t graph = nullptr;
-        e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: begin capture failed");
-        int64_t nl = 0;
-        int* tcerr = use_tc ? st->tcerr.as<int>() : nullptr;
-        init_active_kernel<<<(count + 255) / 256, 256, 0, bs>>>(st->valid.as<int>(), active, status, count, tcerr);
-        ++nl;
-        // Tensor-core path: the first pass appends the right sketch up to W1 = 4 s0
-        // columns (within the X^T pool's SNEW rows) in one read of every block; the
-        // reads bound that pass, not the extra columns, and the next ladder widths
-        // up to W1 then need no pass over A.  Column j of AX does not depend on
-        // which pass computes it, so every width sees the same AX.
-        const int w1 = use_tc ? first_pass_width(s0, SNEW, S_MAX) : s0;
-        int covered = 0;                          // AX columns computed so far
-        for (int s_prev = 0, s = s0; s <= S_MAX && e == cudaSuccess; s_prev = s, s *= 2) {
-            const int sn = s - s_prev;
-            if (use_tc) {
-                if (s > covered) {
-                    const int upto = covered == 0 ? std::max(s, w1) : s;
-                    const int c0 = covered, cn = upto - covered;
-                    e = launch_gauss_xt_batched(dd, count, active, c0, cn, tc_mma_n(cn), st->xt.as<uint16_t>(), bs);
-                    if (e == cudaSuccess) e = launch_compact_tiles(dd, count, active, st->actpre.as<int64_t>(), bs);
-                    if (e == cudaSuccess)
-                        e = launch_right_tc_batched(dd, count, st->actpre.as<int64_t>(), pre128[count],
-                                                    st->xt.as<uint16_t>(), cn, st->ax.as<float>(), S_MAX, c0, tcerr,
-                                                    bs);
-                    covered = upto;
-                    nl += 3;
+        // ---- capture the whole ladder.  Tensor-core path: the first pass appends the
+        // right sketch up to w1 columns (within the X^T pool's SNEW rows) in one read
+        // of every block; the later ladder widths up to w1 then need no pass over A.
+        // Column j of AX does not depend on which pass computes it, so every width
+        // sees the same AX whatever w1 is: the results are the same bits, only the
+        // number of passes (and the time) changes.
+        auto capture = [&](int w1, cudaGraphExec_t* exec, int64_t* nl_out) -> cudaError_t {
+            cudaGraph_t graph = nullptr;
+            cudaError_t ec = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
+            if (ec != cudaSuccess) return ec;
+            int64_t nl = 0;
+            int* tcerr = use_tc ? st->tcerr.as<int>() : nullptr;
+            init_active_kernel<<<(count + 255) / 256, 256, 0, bs>>>(st->valid.as<int>(), active, status, count, tcerr);
+            ++nl;
+            int covered = 0;                          // AX columns computed so far
+            cudaError_t el = cudaSuccess;
+            for (int s_prev = 0, s = s0; s <= S_MAX && el == cudaSuccess; s_prev = s, s *= 2) {
+                const int sn = s - s_prev;
+                if (use_tc) {
+                    if (s > covered) {
+                        const int upto = covered == 0 ? std::max(s, w1) : s;
+                        const int c0 = covered, cn = upto - covered;
+                        el = launch_gauss_xt_batched(dd, count, active, c0, cn, tc_mma_n(cn), st->xt.as<uint16_t>(), bs);
+                        if (el == cudaSuccess) el = launch_compact_tiles(dd, count, active, st->actpre.as<int64_t>(), bs);
+                        if (el == cudaSuccess)
+                            el = launch_right_tc_batched(dd, count, st->actpre.as<int64_t>(), pre128[count],
+                                                         st->xt.as<uint16_t>(), cn, st->ax.as<float>(), S_MAX, c0, tcerr,
+                                                         bs);
+                        covered = upto;
+                        nl += 3;
+                    }
+                } else {
+                    const int bm = st->bm_for[31 - __builtin_clz((unsigned)sn)] == 64 ? 64 : 128;
+                    gauss_x_batched_kernel<<<1024, 256, 0, bs>>>(dd, count, st->colpre.as<int64_t>(), active, s_prev, sn,
+                                                                st->x.as<float>());
+                    el = launch_right_simt_batched(dd, count, bm == 128 ? st->pre128.as<int64_t>() : st->pre64.as<int64_t>(),
+                                                   bm == 128 ? pre128[count] : pre64[count], active, st->x.as<float>(), sn,
+                                                   st->ax.as<float>(), S_MAX, s_prev, bm, bs);
+                    nl += 2;
                 }
-            } else {
-                const int bm = st->bm_for[31 - __builtin_clz((unsigned)sn)] == 64 ? 64 : 128;
-                gauss_x_batched_kernel<<<1024, 256, 0, bs>>>(dd, count, st->colpre.as<int64_t>(), active, s_prev, sn,
-                                                            st->x.as<float>());
-                e = launch_right_simt_batched(dd, count, bm == 128 ? st->pre128.as<int64_t>() : st->pre64.as<int64_t>(),
-                                              bm == 128 ? pre128[count] : pre64[count], active, st->x.as<float>(), sn,
-                                              st->ax.as<float>(), S_MAX, s_prev, bm, bs);
-                nl += 2;
-            }
-            if (e != cudaSuccess) break;
-            if (s_prev > 0) {
-                e = launch_left_batched(dd, active, count, st->ax.as<float>(), S_MAX, st->core.as<double>(),
-                                        core_stride, S_MAX, 2 * s_prev, 2 * sn, 0, s_prev, bs);
+                if (el != cudaSuccess) break;
+                if (s_prev > 0) {
+                    el = launch_left_batched(dd, active, count, st->ax.as<float>(), S_MAX, st->core.as<double>(),
+                                             core_stride, S_MAX, 2 * s_prev, 2 * sn, 0, s_prev, bs);
+                    ++nl;
+                    if (el != cudaSuccess) break;
+                }
+                el = launch_left_batched(dd, active, count, st->ax.as<float>(), S_MAX, st->core.as<double>(),
+                                         core_stride, S_MAX, 0, 2 * s, s_prev, sn, bs);
                 ++nl;
-                if (e != cudaSuccess) break;
+                if (el != cudaSuccess) break;
+                el = launch_core_sigma_batched(st->core.as<double>(), 2 * s, s, S_MAX, core_stride, count,
+                                               st->sigma.as<double>(), S_MAX, status, bs, active);
+                ++nl;
+                if (el != cudaSuccess) break;
+                readoff_batched_kernel<<<(count + 127) / 128, 128, 0, bs>>>(
+                    dd, count, active, st->sigma.as<double>(), S_MAX, s, std::min(r1_of(s), s),
+                    1.0 / std::sqrt((double)s * (double)(2 * s)), eps, o.norm_a, status, st->out.as<DevReadoff>(),
+                    st->sscaled.as<double>(), st->finals.as<int>(), tcerr);
+                ++nl;
             }
-            e = launch_left_batched(dd, active, count, st->ax.as<float>(), S_MAX, st->core.as<double>(),
-                                    core_stride, S_MAX, 0, 2 * s, s_prev, sn, bs);
-            ++nl;
-            if (e != cudaSuccess) break;
-            e = launch_core_sigma_batched(st->core.as<double>(), 2 * s, s, S_MAX, core_stride, count,
-                                          st->sigma.as<double>(), S_MAX, status, bs, active);
-            ++nl;
-            if (e != cudaSuccess) break;
-            readoff_batched_kernel<<<(count + 127) / 128, 128, 0, bs>>>(
-                dd, count, active, st->sigma.as<double>(), S_MAX, s, std::min(r1_of(s), s),
-                1.0 / std::sqrt((double)s * (double)(2 * s)), eps, o.norm_a, status, st->out.as<DevReadoff>(),
-                st->sscaled.as<double>(), st->finals.as<int>(), tcerr);
-            ++nl;
+            ec = cudaStreamEndCapture(bs, &graph);
+            if (el == cudaSuccess) el = ec;
+            if (el == cudaSuccess) el = cudaGraphInstantiate(exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            *nl_out = nl;
+            return el;
+        };
+        // ---- autotune the first-pass width of the tensor-core ladder on this batch:
+        // each candidate ladder is captured and timed once after a warm-up run (the
+        // candidates give identical results, so the fastest is kept)
+        std::vector<int> cands;
+        if (use_tc) {
+            if (o.batch_first_width > 0) {
+                cands.push_back(std::min(std::max(o.batch_first_width, s0), std::min(SNEW, S_MAX)));
+            } else {
+                for (int w = s0; w <= SNEW && w <= S_MAX; w *= 2) cands.push_back(w);
+            }
+        } else {
+            cands.push_back(s0);
         }
-        cudaError_t ec = cudaStreamEndCapture(bs, &graph);
-        if (e == cudaSuccess) e = ec;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&st->exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            st->exec = nullptr;
-            return set_last_error(RE_ERR_CUDA, "batched: graph capture failed");
+        float best = 1e30f;
+        for (size_t ci = 0; ci < cands.size(); ++ci) {
+            cudaGraphExec_t ex = nullptr;
+            int64_t nl = 0;
+            e = capture(cands[ci], &ex, &nl);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                if (ex) cudaGraphExecDestroy(ex);
+                if (st->exec) cudaGraphExecDestroy(st->exec);
+                st->exec = nullptr;
+                return set_last_error(RE_ERR_CUDA, "batched: graph capture failed");
+            }
+            float ms = 0.f;
+            if (cands.size() > 1) {
+                e = cudaGraphLaunch(ex, bs);
+                if (e == cudaSuccess) e = cudaEventRecord(st->t0, bs);
+                if (e == cudaSuccess) e = cudaGraphLaunch(ex, bs);
+                if (e == cudaSuccess) e = cudaEventRecord(st->t1, bs);
+                if (e == cudaSuccess) e = cudaEventSynchronize(st->t1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, st->t0, st->t1);
+                if (e != cudaSuccess) {
+                    cudaGraphExecDestroy(ex);
+                    return set_last_error(RE_ERR_CUDA, "batched: first-pass autotune failed");
+                }
+            }
+            if (ms < best) {
+                best = ms;
+                if (st->exec) cudaGraphExecDestroy(st->exec);
+                st->exec = ex;
+                st->w1 = cands[ci];
+                st->launches_per_run = nl;
+            } else {
+                cudaGraphExecDestroy(ex);
+            }
         }
         st->key = key;
-        st->launches_per_run = nl;
     }
     // ---- one graph launch, ordered after the caller's stream
     e = cudaEventRecord(st->ev_in, ustream);
@@ -587,7 +630,7 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
         R.final_s = s;
         // passes over A: one per right-sketch pass the block took part in (on the
         // tensor-core path the first pass covers the widths up to w1)
-        const int w1 = use_tc ? first_pass_width(s0, SNEW, S_MAX) : s0;
+        const int w1 = use_tc ? st->w1 : s0;
         int passes = 1;
         for (int t = 2 * w1; t <= s; t *= 2) ++passes;
         R.passes = passes;

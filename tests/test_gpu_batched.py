@@ -35,7 +35,10 @@ def h(request):
         pytest.skip("no GPU")
     from paper_2105_07388_gb300 import build
     build.build()
-    hd = rk.re_create(0, rk.make_opts(s_max=128, precision=request.param))
+    # the tensor-core ladder's first pass pinned to 32 columns (autotuned by default,
+    # tested separately below), so that the pass counts are known
+    hd = rk.re_create(0, rk.make_opts(s_max=128, precision=request.param,
+                                      batch_first_width=32 if request.param == rk.RE_PREC_BF16X3 else 0))
     PREC[hd] = request.param
     yield hd
     rk.re_destroy(hd)
@@ -186,3 +189,27 @@ def test_matrix_free_errors():
     res, _ = rk.re_rank_estimate_kernel_blocks(hm, pts, 1e-6, 1)
     assert res[0].status == 0 and res[1].status == rk.RE_ERR_NONFINITE
     rk.re_destroy(hm)
+
+
+def test_batched_first_pass_autotune_same_bits():
+    """The tensor-core ladder's first-pass width (the autotuned N tile of the first
+    pass) changes only the number of passes: ranks, widths and sketched values are
+    the same bits for every candidate, and the autotuned handle returns them too."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    shapes = wl.kernel_block_sizes(20, seed=41, lo=256, hi=1500) + [(300, 900), (1024, 1024)]
+    blocks = [wl.kernel_block(m, n, seed=700 + i).cuda() for i, (m, n) in enumerate(shapes)]
+    ref = None
+    for w1 in (8, 16, 32, 64, 0):
+        hd = rk.re_create(0, rk.make_opts(s_max=128, precision=rk.RE_PREC_BF16X3, batch_first_width=w1))
+        try:
+            res, sig = rk.re_rank_estimate_batched(hd, blocks, 1e-6, rk.RE_GAUSSIAN, 31, sigma_cap=128)
+        finally:
+            rk.re_destroy(hd)
+        got = ([r.rank for r in res], [r.final_s for r in res], sig)
+        if ref is None:
+            ref = got
+        assert got[0] == ref[0] and got[1] == ref[1] and np.array_equal(got[2], ref[2]), w1
+        if w1:
+            for r in res:
+                assert r.passes == 1 + sum(1 for t in (16, 32, 64, 128) if 2 * w1 <= t <= r.final_s)
