@@ -50,11 +50,6 @@ constexpr int kBProdWarp = kAProdWarp + kAProdWarps;           // 16
 constexpr int kMmaWarp = kBProdWarp + 1;                       // 17
 constexpr int kThreads = (kMmaWarp + 1) * 32;                  // 576
 constexpr uint32_t kHalfBytes = kBM * 32 * 4;                  // 16 KB FP32 half chunk
-// ring slot: a half chunk, or its 16-byte-aligned superset for blocks whose rows do
-// not start on 16 bytes (128 rows of 144 bytes, or 32 k rows of 528 bytes)
-constexpr uint32_t kSupRow = 144, kSupKRow = 528;
-constexpr uint32_t kSlotBytes = kBM * kSupRow;                 // 18 KB
-static_assert(32 * kSupKRow <= kSlotBytes, "k-major superset tile");
 constexpr int kAStages = 8;
 constexpr int kStages = 2;
 constexpr uint32_t kAStageCol = 256;
@@ -194,62 +189,6 @@ __device__ __forceinline__ void load_cols(const BlockRef D, int64_t row0, int64_
     }
 }
 
-// 16-byte-aligned granule start at or below p, and a valid 16-byte-aligned address
-// to name in a copy that reads nothing
-__device__ __forceinline__ uintptr_t granule(const void* p) { return reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15; }
-
-// One half chunk of a row-major block whose rows do not all start on 16 bytes: the
-// 32 floats of each row are fetched as their 16-byte-aligned superset -- 9 chunks
-// of 16 bytes from the granule holding the first float -- into a plain 144-byte row
-// (no swizzle); the converter takes the 32 floats at the row's offset inside it.
-// A chunk that holds at least one float of the row's segment is read whole (it
-// lies in the same 16-byte granule as that float, so in mapped memory); chunks
-// past the row's last float or past the segment, and rows past the block, are
-// zero-filled.  Lanes over (row, chunk) pairs of rows rbase .. rbase+31.
-__device__ __forceinline__ void load_rows_sup(const BlockRef D, int64_t row0, int64_t k0, int rbase, uint32_t dst0) {
-    const int lane = threadIdx.x & 31;
-    const uintptr_t none = granule(D.A);
-#pragma unroll 3
-    for (int t = lane; t < 32 * 9; t += 32) {
-        const int i = t / 9, c = t - 9 * i;
-        const int rr = rbase + i;
-        const int64_t row = row0 + rr;
-        uintptr_t src = none;
-        uint32_t nb = 0;
-        if (row < D.rows && k0 < D.cols) {
-            const float* seg = D.A + row * D.ld + k0;
-            const uintptr_t cs = granule(seg) + 16u * (uint32_t)c;
-            const uintptr_t end = reinterpret_cast<uintptr_t>(seg + std::min<int64_t>(32, D.cols - k0));
-            if (cs < end) {
-                src = cs;
-                nb = 16;
-            }
-        }
-        cp_async_w<16>(dst0 + (uint32_t)rr * kSupRow + 16u * (uint32_t)c, reinterpret_cast<const void*>(src), nb);
-    }
-}
-
-// The same for a block stored transposed (k-major tile): k row kk holds the 128
-// floats A[k][row0 ..] fetched as 33 granules (528 bytes); warp covers k rows
-// kbase .. kbase+7.
-__device__ __forceinline__ void load_cols_sup(const BlockRef D, int64_t row0, int64_t k0, int kbase, uint32_t dst0) {
-    const int lane = threadIdx.x & 31;
-    const uintptr_t none = granule(D.A);
-    for (int kk = kbase; kk < kbase + 8; ++kk) {
-        const int64_t k = k0 + kk;
-        const bool kin = k < D.cols && row0 < D.rows;
-        const float* seg = D.A + (kin ? k : 0) * D.ld + row0;
-        const uintptr_t base = granule(seg);
-        const uintptr_t end = reinterpret_cast<uintptr_t>(seg + std::min<int64_t>(128, D.rows - row0));
-        for (int c = lane; c < 33; c += 32) {
-            const uintptr_t cs = base + 16u * (uint32_t)c;
-            const bool rd = kin && cs < end;
-            cp_async_w<16>(dst0 + (uint32_t)kk * kSupKRow + 16u * (uint32_t)c, reinterpret_cast<const void*>(rd ? cs : none),
-                           rd ? 16u : 0u);
-        }
-    }
-}
-
 // the mbarrier receives one arrival when all prior cp.async of this thread land
 __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -281,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
     const uint32_t b_stage = ((uint32_t)p.N * 128u + 1023u) & ~1023u;
     unsigned char* abuf = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    unsigned char* bbuf = abuf + (size_t)kAStages * kSlotBytes;
+    unsigned char* bbuf = abuf + (size_t)kAStages * kHalfBytes;
 
     if (tid == 0) {
         for (int i = 0; i < kAStages; ++i) {
@@ -336,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
                     ok = false;
                     break;
                 }
-                const unsigned char* tile = abuf + (size_t)as * kSlotBytes;
+                const unsigned char* tile = abuf + (size_t)as * kHalfBytes;
                 const uint32_t col = kAStageCol + 96u * (uint32_t)s + 16u * (uint32_t)h;
                 if (mfree) {
                     // entries computed and stored to TMEM eight words (16 entries) at a time
@@ -366,66 +305,17 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
                     mbar_arrive(&a_empty[as]);
                 } else {
                     float4 v[8];
-                    const BatchDesc& D = p.d[b];
-                    const bool sup = copy_width(D.A, D.ld) < 16;
-                    const int64_t k0 = kc * kBK + 32 * h;
-                    const int64_t row0 = (it - p.pre[b]) * kBM;
-                    if (!trans && !sup) {
+                    if (!trans) {
                         const unsigned char* src = tile + (size_t)r * 128;
 #pragma unroll
                         for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const float4*>(src + ((c ^ (r & 7)) << 4));
-                    } else if (!trans) {
-                        // 16-byte-aligned superset of the row: the 32 floats start `sh` floats in;
-                        // floats past the block's columns are zero
-                        const float4* src = reinterpret_cast<const float4*>(tile + (size_t)r * kSupRow);
-                        float4 t[9];
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) t[c] = src[c];
-                        const int sh = (int)((reinterpret_cast<uintptr_t>(D.A + (row0 + r) * D.ld + k0) >> 2) & 3);
-                        switch (sh) {
-                            case 0:
-#pragma unroll
-                                for (int c = 0; c < 8; ++c) v[c] = t[c];
-                                break;
-                            case 1:
-#pragma unroll
-                                for (int c = 0; c < 8; ++c) v[c] = make_float4(t[c].y, t[c].z, t[c].w, t[c + 1].x);
-                                break;
-                            case 2:
-#pragma unroll
-                                for (int c = 0; c < 8; ++c) v[c] = make_float4(t[c].z, t[c].w, t[c + 1].x, t[c + 1].y);
-                                break;
-                            default:
-#pragma unroll
-                                for (int c = 0; c < 8; ++c) v[c] = make_float4(t[c].w, t[c + 1].x, t[c + 1].y, t[c + 1].z);
-                                break;
-                        }
-                        const int64_t kv = D.cols - k0;
-                        if (kv < 32) {           // the block's last K chunk: floats past its columns are zero
-                            float* vf = reinterpret_cast<float*>(v);
-#pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (j >= kv) vf[j] = 0.f;
-                        }
-                    } else if (!sup) {
+                    } else {
                         // k-major tile: column r (consecutive lanes read consecutive words)
                         const float* src = reinterpret_cast<const float*>(tile) + r;
 #pragma unroll
                         for (int c = 0; c < 8; ++c)
                             v[c] = make_float4(src[(4 * c) * 128], src[(4 * c + 1) * 128], src[(4 * c + 2) * 128],
                                                src[(4 * c + 3) * 128]);
-                    } else {
-                        // k-major superset: k row kk starts its 128 floats at its own offset;
-                        // oriented rows past the block are zero (the granules hold other data)
-                        const float* src = reinterpret_cast<const float*>(tile);
-                        const bool rin = row0 + r < D.rows;
-                        float* vf = reinterpret_cast<float*>(v);
-#pragma unroll
-                        for (int kk = 0; kk < 32; ++kk) {
-                            const int sh = (int)((reinterpret_cast<uintptr_t>(D.A + (k0 + kk) * D.ld + row0) >> 2) & 3);
-                            const float x = src[kk * (kSupKRow / 4) + sh + r];
-                            vf[kk] = rin ? x : 0.f;
-                        }
                     }
                     mbar_arrive(&a_empty[as]);
                     uint32_t hi[16], mid[16], lo[16];
@@ -466,10 +356,10 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
                         ok = false;
                         break;
                     }
-                    const uint32_t dst0 = smem_u32(abuf + (size_t)as * kSlotBytes);
+                    const uint32_t dst0 = smem_u32(abuf + (size_t)as * kHalfBytes);
                     const int64_t k0 = kc * kBK + 32 * h;
                     if (mfree) {
-                        unsigned char* stg = abuf + (size_t)as * kSlotBytes;
+                        unsigned char* stg = abuf + (size_t)as * kHalfBytes;
                         const int t = 32 * pw + lane;          // row point t of the tile
                         const int64_t row = row0 + t;
                         float4 rp = make_float4(kFar, kFar, kFar, 0.f);
@@ -497,10 +387,12 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
                     }
                     if (!tr) {
                         if (w == 16) load_rows<16>(B, row0, k0, 32 * pw, dst0);
-                        else load_rows_sup(B, row0, k0, 32 * pw, dst0);
+                        else if (w == 8) load_rows<8>(B, row0, k0, 32 * pw, dst0);
+                        else load_rows<4>(B, row0, k0, 32 * pw, dst0);
                     } else {
                         if (w == 16) load_cols<16>(B, row0, k0, 8 * pw, dst0);
-                        else load_cols_sup(B, row0, k0, 8 * pw, dst0);
+                        else if (w == 8) load_cols<8>(B, row0, k0, 8 * pw, dst0);
+                        else load_cols<4>(B, row0, k0, 8 * pw, dst0);
                     }
                     cp_async_arrive(&a_full[as]);
                 }
@@ -696,7 +588,7 @@ cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t
     p.ldax = ldax;
     p.col0 = col0;
     p.err = err_flag;
-    const size_t smem = (size_t)kSlotBytes * kAStages + (((size_t)p.N * 128 + 1023) & ~(size_t)1023) * kStages + 1024;
+    const size_t smem = (size_t)kHalfBytes * kAStages + (((size_t)p.N * 128 + 1023) & ~(size_t)1023) * kStages + 1024;
     cudaError_t e = cudaFuncSetAttribute(right_tc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
