@@ -38,6 +38,9 @@ WORKLOADS = {
     "large": dict(m=65536, n=16384, rank=200, eps=1e-4, seed=1, sketch_seed=12345),
     "medium": dict(m=16384, n=16384, rank=200, eps=1e-4, seed=1, sketch_seed=12345),
     "small": dict(m=2048, n=1024, rank=40, eps=1e-4, seed=0, sketch_seed=12345),
+    # the precision workload (ten-decade spectrum, eps = 1e-8) with the exact-product sketch
+    "precision": dict(m=32768, n=32768, spectrum="geom300", eps=1e-8, seed=2, sketch_seed=4242),
+    "precision-small": dict(m=16384, n=16384, spectrum="geom300", eps=1e-8, seed=2, sketch_seed=4242),
 }
 
 
@@ -49,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--kind", default="gaussian", choices=["gaussian", "srht", "hrtt"])
-    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3", "exact"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched", type=int, default=1)
@@ -121,7 +124,10 @@ class ClockSampler:
 def build_matrix(w, device):
     import torch
     from paper_2105_07388_gb300 import workloads as wl
-    if w["m"] >= 16384:
+    if w.get("spectrum") == "geom300":
+        sig = wl.spectrum("geom300", w["n"])
+        A = wl.householder_matrix(w["m"], w["n"], sig, seed=w["seed"], device=device)
+    elif w["m"] >= 16384:
         sig = wl.spectrum("step", w["n"], rank=w["rank"], tail_scale=1e-6)
         A = wl.householder_matrix(w["m"], w["n"], sig, seed=w["seed"], device=device)
     else:
@@ -189,6 +195,11 @@ def job_gbs(a_bytes: float, passes: int, world: int, ms: float) -> float:
 def main():
     args = parse()
     w = WORKLOADS[args.workload]
+    prec_wl = args.workload.startswith("precision")
+    if prec_wl:
+        # the precision workloads run the exact-product mode and nothing else
+        args.precision, args.kind = "exact", "gaussian"
+        args.batched, args.precision_case, args.no_e2e = 0, 0, True
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -197,6 +208,9 @@ def main():
     cfg = {"workload": f"single matrix {w['m']}x{w['n']} FP32, sigma=1 (i<=200) then 1e-6/i, "
                        f"eps={w['eps']}, {xy}, s=8..256 doubling"
            if args.workload in ("large", "medium") else
+           f"single matrix {w['m']}x{w['n']} FP32, sigma_i=10^(-10(i-1)/300) (i<=300) then 1e-12, "
+           f"eps={w['eps']}, Gaussian X and Y, exact-product sketch, s=8..512 (first pass to 64)"
+           if prec_wl else
            f"single matrix {w['m']}x{w['n']}, sigma=10^-(i-1)/10, eps={w['eps']}",
            "m": w["m"], "n": w["n"], "dtype_A": "f32", "eps": w["eps"], "sketch": args.kind,
            "precision": args.precision,
@@ -247,7 +261,7 @@ def main():
     _b.build()
     A = build_matrix(w, "cuda")
     m, n = A.shape
-    prec = rk.RE_PREC_FP32 if args.precision == "fp32" else rk.RE_PREC_BF16X3
+    prec = {"fp32": rk.RE_PREC_FP32, "bf16x3": rk.RE_PREC_BF16X3, "exact": rk.RE_PREC_EXACT}[args.precision]
     h = rk.re_create(local, rk.make_opts(precision=prec))
     stream = torch.cuda.current_stream()
 
@@ -296,7 +310,22 @@ def main():
     else:
         fp32_peak, alu_frac = None, 0.0
     hbm_frac = right_gbs / hbm
-    if alu_frac > hbm_frac:
+    if args.precision == "exact":
+        # the exact-product sketch: five MMAs per K step of the digit products; its
+        # wide passes are tensor-bound, its narrow ones bound by converting A
+        tensor_frac = right_tflops / bf16
+        roof = {"kernel": "right sketch (exact-product tcgen05)",
+                "bound": "tensor" if tensor_frac > hbm_frac else "hbm",
+                "achieved": right_tflops if tensor_frac > hbm_frac else right_gbs,
+                "peak": bf16 if tensor_frac > hbm_frac else hbm,
+                "unit": "TFLOP/s" if tensor_frac > hbm_frac else "GB/s",
+                "frac": max(tensor_frac, hbm_frac),
+                "peak_source": f"{src} bf16_tflops (the digit products are BF16)" if tensor_frac > hbm_frac
+                else f"{src} hbm_gbs",
+                "flops_counted": "9 exact BF16 digit products x 2 m n N per pass",
+                "hbm_achieved_gbs": right_gbs, "hbm_frac": hbm_frac,
+                "tensor_tflops_achieved": right_tflops, "tensor_frac": tensor_frac}
+    elif alu_frac > hbm_frac:
         roof = {"kernel": "right sketch (FP32 SIMT)", "bound": "alu", "achieved": right_tflops,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu_frac,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock under load",
@@ -319,11 +348,20 @@ def main():
     line = {"metric": "sketch GB/s (A read once, % of HBM peak); rank estimates/s vs plain at same ranks",
             "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": cfg, "hbm_frac_of_step": value / world / hbm,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 digit products, exact int64 sums" if args.precision == "exact" else "f32",
+            "data": "synthetic", "config": cfg, "hbm_frac_of_step": value / world / hbm,
             "result": {"rank": res.rank, "final_s": res.final_s, "passes": passes,
                        "flags": res.flags},
             "gpu_launches": int(st.launches), "roofline": roof, "clocks": clocks}
+
+    if prec_wl:
+        rk.re_destroy(h)
+        if rank == 0:
+            print(json.dumps(line))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
 
     # rank estimates per second of the single-matrix forms, at identical ranks
     forms = {}
