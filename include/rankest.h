@@ -100,6 +100,8 @@ extern "C" {
 #define RE_CONVERGED 1u        /* some trusted sigma^_{i+1} <= eps ||A|| was found */
 #define RE_LOWER_BOUND_ONLY 2u /* the ladder ended first: rank = r1(final s) is a lower bound (Sec. 5) */
 #define RE_TRANSPOSED 4u       /* m < n: the estimate was taken on A^T */
+#define RE_QB_DEFLATED 8u      /* Algorithm 3: a column of A X_k was numerically dependent on the
+                                  earlier ones; the matching column of Q is zero */
 
 typedef struct re_handle_* re_handle;
 
@@ -165,7 +167,10 @@ typedef struct {
     double svd_ms;           /* small-core singular values */
     double other_ms;         /* generator and read-off kernels */
     int64_t passes;          /* sketch passes over A */
-    int64_t reserved[4];
+    double qb_precondition_ms;   /* Algorithm 3: core Gram, R_s, W = A X_k R_s^{-1} */
+    double qb_orthonormalise_ms; /* Algorithm 3: two Cholesky-QR passes on W */
+    double qb_product_ms;        /* Algorithm 3: B = Q^T A */
+    int64_t reserved[1];
 } re_stats;
 
 /* Library version as major*10000 + minor*100 + patch. */
@@ -308,7 +313,8 @@ typedef struct {
     int final_s;      /* sketch width at which r was chosen */
     int passes;       /* reads of A by the sketch (B = Q^T A is one more) */
     uint32_t flags;   /* RE_CONVERGED: criterion met; RE_LOWER_BOUND_ONLY: the ladder ended
-                         first; RE_TRANSPOSED: m < n, Q and B factor A^T */
+                         first; RE_TRANSPOSED: m < n, Q and B factor A^T;
+                         RE_QB_DEFLATED: some columns of Q are zero (see below) */
     int status;       /* RE_OK, or RE_ERR_NONFINITE */
     double bound;     /* (1 + r/(p-1))^{1/2} (sum_{j>r} sigma^_j^2)^{1/2}: the estimated error */
     double norm_a;    /* ||A|| used by the criterion (sigma^_1 unless opts.norm_a) */
@@ -324,7 +330,14 @@ typedef struct {
  * the first k = r + p columns of A X, and B = Q^T A (device FP32, k x min(m,n),
  * ldb >= min(m,n)), so A ~ Q B (A^T ~ Q B when m < n).  The thin QR uses the
  * core Y (A X_k) to precondition (Sec. 4's randomized approximate
- * orthogonalization) and two Cholesky-QR passes; products are cuBLAS GEMMs.
+ * orthogonalization) and two Cholesky-QR passes, all in the library's own
+ * kernels (FP64 Gram of the core and FP64 blocked Cholesky factorizations and
+ * triangular inverses; FP32 products on CUDA cores).  A column of A X_k that
+ * adds nothing resolvable to the span of the earlier ones (a Cholesky pivot below
+ * 1e-24 of its squared norm for the core, 1e-12 in the FP32 passes: for example
+ * columns at the FP32 noise floor when the ladder ends at s_max) is deflated:
+ * its column of Q is zero and RE_QB_DEFLATED is set; the other columns stay
+ * orthonormal and A ~ Q B holds as before.
  * p >= 2 (Halko et al. suggest 5 or 10).  If k exceeds k_cap, returns
  * RE_ERR_ARG with out->k set (call again with larger Q and B).  Synchronises
  * `stream`.

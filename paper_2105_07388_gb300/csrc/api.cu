@@ -11,7 +11,6 @@
 #include <string>
 #include <vector>
 
-#include <cublas_v2.h>
 
 #include "common.cuh"
 #include "internal.h"
@@ -37,7 +36,8 @@ struct DevBuf {
 
 }  // namespace
 
-enum Stage { kStageRight = 0, kStageLeft = 1, kStageSvd = 2, kStageOther = 3 };
+enum Stage { kStageRight = 0, kStageLeft = 1, kStageSvd = 2, kStageOther = 3, kStageQbPre = 4, kStageQbOrth = 5,
+             kStageQbProduct = 6 };
 
 struct PendingTiming {
     int stage;
@@ -60,7 +60,6 @@ struct re_handle_ {
     DevBuf ex_rexp, ex_xd, ex_tr, ex_hi, ex_lo, ex_cexp, ex_yd, ex_tc, ex_svd;
     int64_t ex_ldp = 0, ex_ldy = 0;     // plane and Y-digit leading dimensions
     int ex_cap = 0;                     // width capacity of the exact buffers
-    void* cublas = nullptr;             // cublasHandle_t, created on first use (Algorithm 3's GEMMs)
     re::BatchedState* batched = nullptr;
     // sketch-size proposal network: parameters, Adam moments, gradient, scratch
     DevBuf mlp_P, mlp_M, mlp_V, mlp_G, mlp_X, mlp_y, mlp_logits, mlp_keep, mlp_cls, mlp_feat, mlp_loss;
@@ -122,6 +121,9 @@ void resolve_timings(re_handle h) {
                 break;
             case kStageLeft: h->stats.left_ms += ms; break;
             case kStageSvd: h->stats.svd_ms += ms; break;
+            case kStageQbPre: h->stats.qb_precondition_ms += ms; break;
+            case kStageQbOrth: h->stats.qb_orthonormalise_ms += ms; break;
+            case kStageQbProduct: h->stats.qb_product_ms += ms; break;
             default: h->stats.other_ms += ms; break;
         }
         h->event_pool.push_back(p.a);
@@ -763,17 +765,28 @@ int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* 
     out->norm_a = sel.norm_a;
     if (k > k_cap) return fail(RE_ERR_ARG, "k_cap is smaller than the chosen k = r + p (out->k holds it)");
     if (ldq < k) return fail(RE_ERR_ARG, "ldq < k");
-    if (int rr = ensure(h->qbws, re::qb_workspace_bytes(M, k))) return rr;
-    if (!h->cublas) {
-        cublasHandle_t hb = nullptr;
-        if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) return fail(RE_ERR_CUDA, "cuBLAS handle creation failed");
-        h->cublas = hb;
+    if (int rr = ensure(h->qbws, re::qb_workspace_bytes(M, P.A.cols, k))) return rr;
+    int nl = 0;
+    cudaEvent_t a = stage_begin(h, st);
+    e = re::launch_qb_precondition(AX, smax, M, P.A.cols, core, smax, 2 * s, k, h->qbws.p, floored, st, &nl);
+    stage_end(h, st, a, kStageQbPre);
+    if (e == cudaSuccess) {
+        a = stage_begin(h, st);
+        e = re::launch_qb_orthonormalise(M, P.A.cols, k, Q, ldq, h->qbws.p, floored, st, &nl);
+        stage_end(h, st, a, kStageQbOrth);
     }
-    e = re::launch_qb_factor(h->cublas, P.A, AX, smax, core, smax, 2 * s, k, Q, ldq, B, ldb, h->qbws.p, floored,
-                             st);
+    if (e == cudaSuccess) {
+        a = stage_begin(h, st);
+        e = re::launch_qb_product(P.A, Q, ldq, k, B, ldb, h->qbws.p, st, &nl);
+        stage_end(h, st, a, kStageQbProduct);
+    }
+    h->stats.launches += nl;
+    int hf = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, floored, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "thin QR and B = Q^T A");
-    h->stats.launches += 6;     // three Cholesky factorizations and three inverses (the GEMMs are cuBLAS's)
+    if (hf) out->flags |= RE_QB_DEFLATED;
+    resolve_timings(h);
     return RE_OK;
 }
 
@@ -853,7 +866,6 @@ int re_destroy(re_handle h) {
                       &h->mlp_logits, &h->mlp_keep, &h->mlp_cls, &h->mlp_feat, &h->mlp_loss};
     for (DevBuf* b : bufs) release(*b);
     re::batched_destroy(h->batched);
-    if (h->cublas) cublasDestroy(static_cast<cublasHandle_t>(h->cublas));
     resolve_timings(h);
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     if (h->h_ro) cudaFreeHost(h->h_ro);

@@ -247,15 +247,23 @@ struct QbSelect {
 // smaller dimension (the conservative tail runs to it).
 cudaError_t launch_select_rank(const double* sigma_scaled, int r1, int64_t n, double eps, double norm_a, int p,
                                int s, QbSelect* out, cudaStream_t st);
-size_t qb_workspace_bytes(int64_t rows, int k);
+size_t qb_workspace_bytes(int64_t rows, int64_t cols, int k);
 // Steps 7-8 for the first k columns of AX (rows x ldax FP32) with the FP64 core
-// (r2 rows, ld_core) as the preconditioning sketch: Q (rows x k, ldq) with
-// orthonormal columns, B = Q^T A_oriented (k x cols, ldb).  cublas is a
-// cublasHandle_t; ws holds qb_workspace_bytes(rows, k); *floored (device) is set
-// when a Cholesky pivot had to be raised (an exactly singular Gram matrix).
-cudaError_t launch_qb_factor(void* cublas, const MatView& A, const float* AX, int64_t ldax, const double* core,
-                             int64_t ld_core, int r2, int k, float* Q, int64_t ldq, float* B, int64_t ldb, void* ws,
-                             int* floored, cudaStream_t st);
+// (r2 rows, ld_core) as the preconditioning sketch, in three stream-ordered
+// stages on the workspace ws (qb_workspace_bytes(rows, cols, k)):
+//   precondition:   W = A X_k R_s^{-1}, R_s from the core's Gram (FP64);
+//   orthonormalise: two Cholesky-QR passes on W, Q (rows x k, ldq) with
+//                   orthonormal columns;
+//   product:        B = Q^T A_oriented (k x cols, ldb).
+// *floored (device) is set when a Cholesky pivot had to be raised (an exactly
+// singular Gram matrix).  launches (may be null) counts the kernels launched.
+cudaError_t launch_qb_precondition(const float* AX, int64_t ldax, int64_t rows, int64_t cols, const double* core,
+                                   int64_t ld_core, int r2, int k, void* ws, int* floored, cudaStream_t st,
+                                   int* launches);
+cudaError_t launch_qb_orthonormalise(int64_t rows, int64_t cols, int k, float* Q, int64_t ldq, void* ws,
+                                     int* floored, cudaStream_t st, int* launches);
+cudaError_t launch_qb_product(const MatView& A, const float* Q, int64_t ldq, int k, float* B, int64_t ldb, void* ws,
+                              cudaStream_t st, int* launches);
 
 // ---- batched estimate (batched.cu) --------------------------------------------
 struct BatchedState;

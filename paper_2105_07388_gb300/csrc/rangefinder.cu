@@ -15,12 +15,18 @@
 // columns of Q span the same nested subspaces as those of A X_k.  R_s comes from
 // the FP64 Cholesky factor of the core's Gram matrix (k x k; the core is FP64, so
 // its Gram keeps the squared condition number, 1e14, inside FP64).  Small
-// factorizations (Cholesky, triangular inverse; k <= 512) run in one CTA in
-// FP64; every product is a plain cuBLAS GEMM (FP64 for the core's Gram, FP32
-// otherwise, pedantic math mode: no reduced-precision tensor paths).
+// factorizations (Cholesky, triangular inverse; k <= 1024) run in one CTA, in
+// FP64 for R_s and in FP32 for the two passes on the well-conditioned W.
+//
+// Products (all kernels of this file, no library GEMM):
+//   the core's Gram    FP64, 32 x 32 output tiles (`gram64_kernel`);
+//   W = (A X_k) L^{-T} FP32 CUDA-core tiles of 128 x 128 (`sgemm_kernel`);
+//   V^T V              the same tiles, split over the rows of V, the partial
+//                      Gram matrices summed in FP64 in a fixed order;
+//   B = Q^T A          the same tiles (A read once per 128 columns of Q), split
+//                      over the rows of A when the output has few tiles.
 #include <cmath>
-
-#include <cublas_v2.h>
+#include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
@@ -29,7 +35,6 @@ namespace re {
 
 namespace {
 
-constexpr int kSmallThreads = 1024;
 
 __global__ void select_rank_kernel(const double* __restrict__ sig, int r1, int64_t n, double eps, double norm_a,
                                    int p, int s, QbSelect* __restrict__ out) {
@@ -59,75 +64,488 @@ __global__ void select_rank_kernel(const double* __restrict__ sig, int r1, int64
     out->norm_a = ref;
 }
 
-// The lower triangle of the k x k row-major G (FP64, or FP32 widened) is copied
-// to L and factored in place, G = L L^T.  A pivot not above 1e-30 of the largest
-// diagonal entry (an exactly singular Gram matrix) is raised to it, 1 when the
-// whole matrix is zero, and *floored is set.
-template <typename TG>
-__global__ void __launch_bounds__(kSmallThreads) chol_lower_kernel(const TG* __restrict__ G, int ldg, double* L,
-                                                                  int k, int* floored) {
-    __shared__ double s_inv, s_floor;
-    const int tid = threadIdx.x;
-    for (int64_t e = tid; e < (int64_t)k * k; e += blockDim.x) {
-        const int i = (int)(e / k), l = (int)(e % k);
-        L[e] = l <= i ? (double)G[(int64_t)i * ldg + l] : 0.0;
+// ---- blocked FP64 Cholesky factorization and triangular inverse (k <= 1024)
+// Both work on kp x kp row-major matrices, kp = the power of two >= k (at least
+// kTB = 32), the k x k matrix padded with the identity (so the padding factors
+// and inverts to the identity and never mixes with the leading block).
+//
+// Cholesky G = L L^T, right-looking by 32-column block steps J: every CTA of
+// `blk_potrf_trsm_kernel` factors the diagonal block (J, J) (redundantly, in
+// shared memory) and CTA c > 0 then solves the block (J + c, J) against it;
+// `blk_syrk_kernel` subtracts L(I, J) L(K, J)^T from every trailing tile
+// J < K <= I.  Deflation: a pivot d_j (the squared norm of what column j adds
+// to the span of the earlier columns) not above rel * G_jj, or not above 1e-30
+// of G's largest diagonal entry, marks column j as numerically dependent: its
+// pivot becomes 1, the entries below it 0 (so nothing of it reaches the later
+// columns), defl[j] = 1 and *floored is set; the inverse's row j is then
+// written as zeros, and the orthonormalised column j comes out as zero.
+//
+// Inverse X = L^{-1} by recursive doubling: the 32 x 32 diagonal blocks are
+// inverted by forward substitution, then for block size s = 32, 64, ...: with
+// [[A, 0], [B, C]] a diagonal block of size 2s, its lower-left block of the
+// inverse is -C^{-1} (B A^{-1}) -- two batched FP64 products per level.
+constexpr int kTB = 32;
+
+__global__ void blk_init_kernel(const double* __restrict__ G, int ldg, int k, int kp, double* __restrict__ Lp) {
+    const int64_t total = (int64_t)kp * kp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / kp), j = (int)(e % kp);
+        double v = 0.0;
+        if (i < k && j < k) v = j <= i ? G[(int64_t)i * ldg + j] : 0.0;
+        else if (i == j) v = 1.0;
+        Lp[e] = v;
     }
+}
+
+__global__ void blk_floor_kernel(const double* __restrict__ G, int ldg, int k, double* __restrict__ fl) {
+    __shared__ double red[32];
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) mx = fmax(mx, G[(int64_t)i * ldg + i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
-    if (tid == 0) {
-        double mx = 0.0;
-        for (int i = 0; i < k; ++i) mx = fmax(mx, L[(int64_t)i * k + i]);
-        s_floor = mx > 0.0 ? mx * 1e-30 : 1.0;      // an all-zero Gram matrix (A X_k = 0) factors as L = I
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+        fl[0] = mx > 0.0 ? mx * 1e-30 : 1.0;   // an all-zero Gram matrix (A X_k = 0): every column deflates
     }
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {
-        if (tid == 0) {
-            double d = L[(int64_t)j * k + j];
-            if (!(d > s_floor)) {
-                d = s_floor;
-                if (floored) *floored = 1;
-            }
-            const double sd = sqrt(d);
-            L[(int64_t)j * k + j] = sd;
-            s_inv = 1.0 / sd;
+}
+
+// 32 x 32 lower Cholesky factorization of D (shared, row pitch kTB + 1) by the
+// 1024 threads of the block, thread (r, c) = (tid / 32, tid % 32).  thr[j] is
+// column j's deflation threshold; dfl[j] (shared) receives its mark.
+__device__ void potrf32(double (*D)[kTB + 1], const double* thr, int* dfl) {
+    const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
+    for (int j = 0; j < kTB; ++j) {
+        if (r == j && c == j) {
+            const double d = D[j][j];
+            const bool dep = !(d > thr[j]);
+            dfl[j] = dep ? 1 : 0;
+            D[j][j] = dep ? 1.0 : sqrt(d);
         }
         __syncthreads();
-        for (int i = j + 1 + tid; i < k; i += blockDim.x) L[(int64_t)i * k + j] *= s_inv;
+        if (c == j && r > j) D[r][j] = dfl[j] ? 0.0 : D[r][j] / D[j][j];
         __syncthreads();
-        for (int i = j + 1 + tid; i < k; i += blockDim.x) {
-            const double lij = L[(int64_t)i * k + j];
-            for (int l = j + 1; l <= i; ++l) L[(int64_t)i * k + l] -= lij * L[(int64_t)l * k + j];
-        }
+        if (r > j && c > j && c <= r) D[r][c] -= D[r][j] * D[c][j];
         __syncthreads();
     }
 }
 
-// X = L^{-1} (lower triangular, FP64 forward substitution, one thread per column),
-// written as FP32 with zeros above the diagonal.
-__global__ void __launch_bounds__(kSmallThreads) tri_inv_lower_kernel(const double* __restrict__ L, int k,
-                                                                     double* __restrict__ work,
-                                                                     float* __restrict__ X) {
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        double* x = work + (int64_t)j * k;           // column j of L^{-1}, rows j .. k-1
-        x[j] = 1.0 / L[(int64_t)j * k + j];
-        for (int i = j + 1; i < k; ++i) {
+// X (shared) = D^{-1} for the lower-triangular D: thread c of warp 0 owns column c.
+__device__ void trinv32(const double (*D)[kTB + 1], double (*X)[kTB + 1]) {
+    const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
+    X[r][c] = 0.0;
+    __syncthreads();
+    if (threadIdx.x < kTB) {
+        X[c][c] = 1.0 / D[c][c];
+        for (int i = c + 1; i < kTB; ++i) {
             double acc = 0.0;
-            for (int l = j; l < i; ++l) acc = fma(L[(int64_t)i * k + l], x[l], acc);
-            x[i] = -acc / L[(int64_t)i * k + i];
+            for (int l = c; l < i; ++l) acc = fma(D[i][l], X[l][c], acc);
+            X[i][c] = -acc / D[i][i];
         }
-        for (int i = 0; i < k; ++i) X[(int64_t)i * k + j] = i < j ? 0.f : (float)x[i];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) blk_potrf_trsm_kernel(double* __restrict__ Lp, int kp, int J,
+                                                              const double* __restrict__ G, int ldg, int k,
+                                                              double rel, const double* __restrict__ fl,
+                                                              int* __restrict__ defl, int* floored) {
+    __shared__ double D[kTB][kTB + 1], Dinv[kTB][kTB + 1], P[kTB][kTB + 1];
+    __shared__ double thr[kTB];
+    __shared__ int dfl[kTB];
+    const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
+    const int64_t j0 = (int64_t)J * kTB, i0 = j0 + (int64_t)blockIdx.x * kTB;
+    D[r][c] = c <= r ? Lp[(j0 + r) * kp + j0 + c] : 0.0;
+    if (r == 0) {
+        const int64_t jj = j0 + c;
+        // padding columns (identity) never deflate
+        thr[c] = jj < k ? fmax(rel * G[jj * ldg + jj], fl[0]) : 0.0;
+    }
+    __syncthreads();
+    potrf32(D, thr, dfl);
+    if (blockIdx.x == 0) {
+        Lp[(j0 + r) * kp + j0 + c] = c <= r ? D[r][c] : 0.0;
+        if (r == 0) {
+            defl[j0 + c] = dfl[c];
+            if (dfl[c] && j0 + c < k && floored) *floored = 1;
+        }
+        return;
+    }
+    trinv32(D, Dinv);
+    // L(I, J) = P D^{-T}: L[r][c] = sum_{l <= c} P[r][l] Dinv[c][l]; 0 in deflated columns
+    P[r][c] = Lp[(i0 + r) * kp + j0 + c];
+    __syncthreads();
+    double acc = 0.0;
+    for (int l = 0; l <= c; ++l) acc = fma(P[r][l], Dinv[c][l], acc);
+    Lp[(i0 + r) * kp + j0 + c] = dfl[c] ? 0.0 : acc;
+}
+
+// Trailing update after step J: tile t of the lower triangle J < K <= I < nb
+// (row-major order of the (I, K) pairs); 256 threads, 4 outputs each.
+__global__ void __launch_bounds__(256) blk_syrk_kernel(double* __restrict__ Lp, int kp, int J) {
+    __shared__ double Ta[kTB][kTB + 1], Tb[kTB][kTB + 1];
+    int t = (int)blockIdx.x, I = J + 1;
+    while (t >= I - J) {                  // row I holds I - J tiles K = J+1 .. I
+        t -= I - J;
+        ++I;
+    }
+    const int K = J + 1 + t;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t j0 = (int64_t)J * kTB, ib = (int64_t)I * kTB, kb = (int64_t)K * kTB;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        Ta[ty + 8 * q][tx] = Lp[(ib + ty + 8 * q) * kp + j0 + tx];
+        Tb[ty + 8 * q][tx] = Lp[(kb + ty + 8 * q) * kp + j0 + tx];
+    }
+    __syncthreads();
+    // Lp[I][K] (r, c) -= sum_l Ta[r][l] Tb[c][l]
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int rr = ty + 8 * q;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int l = 0; l < kTB; ++l) acc = fma(Ta[rr][l], Tb[tx][l], acc);
+        Lp[(ib + rr) * kp + kb + tx] -= acc;
     }
 }
 
-// Row-major C (mr x nc) = op_a(A) op_b(B) through column-major cuBLAS (the row-major
-// matrices are the transposes cuBLAS sees; C^T = op_b(B)^T op_a(A)^T).
-cublasStatus_t sgemm_rm(cublasHandle_t hb, bool ta, bool tb, int mr, int nc, int kk, const float* A, int64_t lda,
-                        const float* B, int64_t ldb, float* C, int64_t ldc) {
-    const float one = 1.f, zero = 0.f;
-    return cublasSgemm(hb, tb ? CUBLAS_OP_T : CUBLAS_OP_N, ta ? CUBLAS_OP_T : CUBLAS_OP_N, nc, mr, kk, &one, B,
-                       (int)ldb, A, (int)lda, &zero, C, (int)ldc);
+__global__ void __launch_bounds__(1024) blk_inv_diag_kernel(const double* __restrict__ Lp, int kp,
+                                                            double* __restrict__ Xp) {
+    __shared__ double D[kTB][kTB + 1], X[kTB][kTB + 1];
+    const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
+    const int64_t j0 = (int64_t)blockIdx.x * kTB;
+    D[r][c] = Lp[(j0 + r) * kp + j0 + c];
+    __syncthreads();
+    trinv32(D, X);
+    // the whole block row of X: the diagonal block, zeros elsewhere (filled level by level)
+    for (int64_t col = c; col < kp; col += kTB) {
+        const bool diag = col >= j0 && col < j0 + kTB;
+        Xp[(j0 + r) * kp + col] = diag ? X[r][col - j0] : 0.0;
+    }
 }
 
-cudaError_t cublas_err(cublasStatus_t s) { return s == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown; }
+// Batched FP64 product C_p = alpha A_p B_p of s x s blocks (s a multiple of 32),
+// pair p = blockIdx.z at A + p a_step etc.; one 32 x 32 tile of C_p per block.
+struct PairGemm {
+    const double* A;
+    int64_t lda, a_step;
+    const double* B;
+    int64_t ldb, b_step;
+    double* C;
+    int64_t ldc, c_step;
+    int s;
+    double alpha;
+};
+
+__global__ void __launch_bounds__(256) blk_pair_gemm_kernel(const PairGemm g) {
+    __shared__ double Ta[kTB][kTB + 1], Tb[kTB][kTB + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const double* A = g.A + (int64_t)blockIdx.z * g.a_step + (int64_t)blockIdx.y * kTB * g.lda;
+    const double* B = g.B + (int64_t)blockIdx.z * g.b_step + (int64_t)blockIdx.x * kTB;
+    double* C = g.C + (int64_t)blockIdx.z * g.c_step + (int64_t)blockIdx.y * kTB * g.ldc + (int64_t)blockIdx.x * kTB;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l0 = 0; l0 < g.s; l0 += kTB) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            Ta[ty + 8 * q][tx] = A[(int64_t)(ty + 8 * q) * g.lda + l0 + tx];
+            Tb[ty + 8 * q][tx] = B[(int64_t)(l0 + ty + 8 * q) * g.ldb + tx];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int l = 0; l < kTB; ++l) {
+            const double b = Tb[l][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fma(Ta[ty + 8 * q][l], b, acc[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) C[(int64_t)(ty + 8 * q) * g.ldc + tx] = g.alpha * acc[q];
+}
+
+// Xinv (k x k FP32) = the leading block of Xp, zeros above the diagonal and in
+// the rows of deflated columns.
+__global__ void blk_out_kernel(const double* __restrict__ Xp, int kp, int k, const int* __restrict__ defl,
+                               float* __restrict__ X) {
+    const int64_t total = (int64_t)k * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / k), j = (int)(e % k);
+        X[e] = (j <= i && !defl[i]) ? (float)Xp[(int64_t)i * kp + j] : 0.f;
+    }
+}
+
+// the padded order: a power of two (the doubling levels then pair every block)
+int kpad(int k) {
+    int kp = kTB;
+    while (kp < k) kp *= 2;
+    return kp;
+}
+
+// L L^T = G (k x k FP64, ldg) and Xinv = L^{-1} (FP32); Lp, Xp hold kp^2 doubles,
+// T kp^2 / 4, fl one double, defl kp ints; rel is the relative deflation threshold.
+// Adds the number of kernels launched to *launches.
+cudaError_t chol_inverse(const double* G, int ldg, int k, double rel, double* Lp, double* Xp, double* T, double* fl,
+                         int* defl, float* Xinv, int* floored, cudaStream_t st, int* launches) {
+    const int kp = kpad(k), nb = kp / kTB;
+    int nl = 0;
+    const int eb = (int)std::min<int64_t>(((int64_t)kp * kp + 255) / 256, 1024);
+    blk_init_kernel<<<eb, 256, 0, st>>>(G, ldg, k, kp, Lp);
+    blk_floor_kernel<<<1, 1024, 0, st>>>(G, ldg, k, fl);
+    nl += 2;
+    for (int J = 0; J < nb; ++J) {
+        blk_potrf_trsm_kernel<<<nb - J, 1024, 0, st>>>(Lp, kp, J, G, ldg, k, rel, fl, defl, floored);
+        ++nl;
+        const int rem = nb - J - 1;
+        if (rem > 0) {
+            blk_syrk_kernel<<<rem * (rem + 1) / 2, 256, 0, st>>>(Lp, kp, J);
+            ++nl;
+        }
+    }
+    blk_inv_diag_kernel<<<nb, 1024, 0, st>>>(Lp, kp, Xp);
+    ++nl;
+    for (int s = kTB; s < kp; s *= 2) {
+        const int pairs = kp / (2 * s);      // diagonal blocks of size 2s at o = p 2s
+        // T_p = B A^{-1}: B = L[o+s.., o..], A^{-1} = X[o.., o..]
+        PairGemm g1{Lp + (int64_t)s * kp, kp, (int64_t)2 * s * (kp + 1), Xp, kp, (int64_t)2 * s * (kp + 1),
+                    T, s, (int64_t)s * s, s, 1.0};
+        blk_pair_gemm_kernel<<<dim3(s / kTB, s / kTB, pairs), 256, 0, st>>>(g1);
+        // X[o+s.., o..] = -C^{-1} T_p, C^{-1} = X[o+s.., o+s..]
+        PairGemm g2{Xp + (int64_t)s * (kp + 1), kp, (int64_t)2 * s * (kp + 1), T, s, (int64_t)s * s,
+                    Xp + (int64_t)s * kp, kp, (int64_t)2 * s * (kp + 1), s, -1.0};
+        blk_pair_gemm_kernel<<<dim3(s / kTB, s / kTB, pairs), 256, 0, st>>>(g2);
+        nl += 2;
+    }
+    blk_out_kernel<<<eb, 256, 0, st>>>(Xp, kp, k, defl, Xinv);
+    ++nl;
+    if (launches) *launches += nl;
+    return cudaGetLastError();
+}
+
+// G (k x k, FP64) = C^T C for the first k columns of the r2 rows of the core C
+// (FP64, row pitch ld): one 32 x 32 tile of G per block, 32-row slabs of C staged
+// in shared memory.
+__global__ void __launch_bounds__(256) gram64_kernel(const double* __restrict__ C, int64_t ld, int r2, int k,
+                                                     double* __restrict__ G) {
+    __shared__ double Ta[32][33], Tb[32][33];
+    const int c1b = blockIdx.y * 32, c2b = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i0 = 0; i0 < r2; i0 += 32) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + ty + 8 * q;
+            Ta[ty + 8 * q][tx] = (i < r2 && c1b + tx < k) ? C[(int64_t)i * ld + c1b + tx] : 0.0;
+            Tb[ty + 8 * q][tx] = (i < r2 && c2b + tx < k) ? C[(int64_t)i * ld + c2b + tx] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int ii = 0; ii < 32; ++ii) {
+            const double b = Tb[ii][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fma(Ta[ii][ty + 8 * q], b, acc[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c1 = c1b + ty + 8 * q, c2 = c2b + tx;
+        if (c1 < k && c2 < k) G[(int64_t)c1 * k + c2] = acc[q];
+    }
+}
+
+// ---- FP32 CUDA-core GEMM: C(r, c) = sum_kk A(r, kk) B(kk, c) over the split's kk range.
+// A(r, kk) = A[r sar + kk sak], B(kk, c) = B[kk sbk + c sbc], C(r, c) = C[z zstride + r ldc + c]
+// for split z = blockIdx.z.  KA (KB): A (B) is contiguous along kk, else along r (c); each
+// thread loads 8 elements of each 128 x 16 operand tile along the contiguous index, so a
+// warp reads whole 64- or 128-byte runs.  Tiles are double-buffered in shared memory; each
+// thread accumulates an 8 x 8 block (rows ty*4.., 64+ty*4..; columns tx*4.., 64+tx*4..).
+constexpr int kGBM = 128, kGBN = 128, kGBK = 16, kGThreads = 256, kGPad = 4;
+
+struct GemmArgs {
+    const float* A;
+    int64_t sar, sak;
+    const float* B;
+    int64_t sbk, sbc;
+    float* C;
+    int64_t ldc;
+    int64_t M, N, K;
+    int64_t kper;      // contraction length per split (a multiple of kGBK)
+    int64_t zstride;   // floats between the partial outputs of consecutive splits
+};
+
+template <bool KA, bool KB>
+__global__ void __launch_bounds__(kGThreads, 2) sgemm_kernel(const GemmArgs g) {
+    __shared__ __align__(16) float As[2][kGBK][kGBM + kGPad];
+    __shared__ __align__(16) float Bs[2][kGBK][kGBN + kGPad];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int64_t r0 = (int64_t)blockIdx.y * kGBM, c0 = (int64_t)blockIdx.x * kGBN;
+    const int64_t kb = (int64_t)blockIdx.z * g.kper;
+    const int64_t ke = g.K < kb + g.kper ? g.K : kb + g.kper;
+    // this thread's load coordinates within a tile
+    const int arl = KA ? (t >> 4) : (t & 127), akl = KA ? (t & 15) : (t >> 7);
+    const int bcl = KB ? (t >> 4) : (t & 127), bkl = KB ? (t & 15) : (t >> 7);
+    float ra[8], rb[8];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int rl = KA ? arl + 16 * i : arl, kl = KA ? akl : akl + 2 * i;
+            const int64_t r = r0 + rl, kk = k0 + kl;
+            ra[i] = (r < g.M && kk < ke) ? g.A[r * g.sar + kk * g.sak] : 0.f;
+            const int cl = KB ? bcl + 16 * i : bcl, kl2 = KB ? bkl : bkl + 2 * i;
+            const int64_t c = c0 + cl, k2 = k0 + kl2;
+            rb[i] = (c < g.N && k2 < ke) ? g.B[k2 * g.sbk + c * g.sbc] : 0.f;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            As[buf][KA ? akl : akl + 2 * i][KA ? arl + 16 * i : arl] = ra[i];
+            Bs[buf][KB ? bkl : bkl + 2 * i][KB ? bcl + 16 * i : bcl] = rb[i];
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    const int64_t ntiles = ke > kb ? (ke - kb + kGBK - 1) / kGBK : 0;
+    if (ntiles > 0) {
+        load(kb);
+        store(0);
+        __syncthreads();
+    }
+    for (int64_t tt = 0; tt < ntiles; ++tt) {
+        const int cur = (int)(tt & 1);
+        if (tt + 1 < ntiles) load(kb + (tt + 1) * kGBK);
+#pragma unroll
+        for (int kk = 0; kk < kGBK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (tt + 1 < ntiles) store(cur ^ 1);
+        __syncthreads();
+    }
+    float* C = g.C + (int64_t)blockIdx.z * g.zstride;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = r0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        if (r >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t c = c0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+            if (c < g.N) C[r * g.ldc + c] = acc[i][j];
+        }
+    }
+}
+
+// out(r, c) = sum over the splits z = 0, 1, ... of P[z zstride + r N + c], summed in
+// FP64 in that order.
+template <typename TO>
+__global__ void reduce_parts_kernel(const float* __restrict__ P, int splits, int64_t zstride, int64_t M, int64_t N,
+                                    TO* __restrict__ out, int64_t ldo) {
+    const int64_t total = M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / N, c = e % N;
+        double acc = 0.0;
+        for (int z = 0; z < splits; ++z) acc += (double)P[(int64_t)z * zstride + e];
+        out[r * ldo + c] = (TO)acc;
+    }
+}
+
+int g_qb_sms = 0;
+
+int sm_count() {
+    if (!g_qb_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_qb_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_qb_sms <= 0) g_qb_sms = 1;
+    }
+    return g_qb_sms;
+}
+
+// Splits of the contraction for an M x N output: enough blocks for two per SM,
+// at least 512 contraction entries per split, at most `cap`.
+int choose_splits(int64_t M, int64_t N, int64_t K, int cap) {
+    const int64_t tiles = ((M + kGBM - 1) / kGBM) * ((N + kGBN - 1) / kGBN);
+    const int64_t want = (2 * (int64_t)sm_count() + tiles - 1) / tiles;
+    const int64_t by_len = std::max<int64_t>(1, K / 512);
+    return (int)std::max<int64_t>(1, std::min<int64_t>({want, by_len, (int64_t)cap}));
+}
+
+template <bool KA, bool KB>
+cudaError_t gemm(const float* A, int64_t sar, int64_t sak, const float* B, int64_t sbk, int64_t sbc, float* C,
+                 int64_t ldc, int64_t M, int64_t N, int64_t K, int splits, int64_t zstride, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    GemmArgs g{A, sar, sak, B, sbk, sbc, C, ldc, M, N, K, 0, zstride};
+    const int64_t per = (K + splits - 1) / splits;
+    g.kper = std::max<int64_t>(kGBK, (per + kGBK - 1) / kGBK * kGBK);
+    const dim3 grid((unsigned)((N + kGBN - 1) / kGBN), (unsigned)((M + kGBM - 1) / kGBM), (unsigned)splits);
+    sgemm_kernel<KA, KB><<<grid, kGThreads, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+template <typename TO>
+cudaError_t reduce_parts(const float* P, int splits, int64_t M, int64_t N, TO* out, int64_t ldo, cudaStream_t st) {
+    const int64_t total = M * N;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8 * (int64_t)sm_count());
+    reduce_parts_kernel<TO><<<blocks, 256, 0, st>>>(P, splits, M * N, M, N, out, ldo);
+    return cudaGetLastError();
+}
+
+// Workspace carve-up (see qb_workspace_bytes)
+struct QbWs {
+    double *G64, *Lp, *Xp, *T, *fl;
+    int* defl;
+    float *Xinv, *W, *Q1, *part;
+};
+
+constexpr int kPartCap = 128;       // largest split count of any product
+// Relative deflation thresholds (pivot over the column's own squared norm): the
+// core is FP64 but holds what FP32 A X resolves, about 1e-7 of a column's norm
+// at the noise floor, so 1e-24 deflates only columns dependent far below that;
+// W is FP32 and its Gram matrix sums FP32 products, so a column adding less than
+// 1e-6 of its norm (pivot 1e-12) is dependent at FP32 resolution.
+constexpr double kDeflPre = 1e-24;
+constexpr double kDeflPass = 1e-12;
+
+size_t part_floats_needed(int64_t rows, int64_t cols, int k) {
+    // the Gram splits (k x k each) and the product's splits (k x cols each)
+    const int64_t sg = choose_splits(k, k, rows, kPartCap);
+    const int64_t sb = choose_splits(k, cols, rows, kPartCap);
+    const int64_t a = sg * (int64_t)k * k;
+    const int64_t b = sb > 1 ? sb * (int64_t)k * cols : 0;
+    return (size_t)std::max(a, b);
+}
+
+size_t ws_doubles(int k) {
+    const size_t kp = (size_t)kpad(k);
+    return (size_t)k * k + 2 * kp * kp + kp * kp / 4 + 2 + kp / 2;   // G64, Lp, Xp, T, fl (+ pad), defl
+}
+
+QbWs carve(void* ws, int64_t rows, int k) {
+    const size_t kp = (size_t)kpad(k);
+    QbWs w;
+    w.G64 = static_cast<double*>(ws);
+    w.Lp = w.G64 + (size_t)k * k;
+    w.Xp = w.Lp + kp * kp;
+    w.T = w.Xp + kp * kp;
+    w.fl = w.T + kp * kp / 4;
+    w.defl = reinterpret_cast<int*>(w.fl + 2);
+    w.Xinv = reinterpret_cast<float*>(w.G64 + ws_doubles(k));
+    w.W = w.Xinv + (size_t)k * k;
+    w.Q1 = w.W + (size_t)rows * k;
+    w.part = w.Q1 + (size_t)rows * k;
+    return w;
+}
 
 }  // namespace
 
@@ -137,59 +555,74 @@ cudaError_t launch_select_rank(const double* sigma_scaled, int r1, int64_t n, do
     return cudaGetLastError();
 }
 
-size_t qb_workspace_bytes(int64_t rows, int k) {
-    // W and Q1 (rows x k FP32), two FP32 k x k (Gram, inverse), two FP64 k x k (L, work)
-    return sizeof(float) * ((size_t)2 * rows * k + (size_t)2 * k * k) + sizeof(double) * (size_t)2 * k * k + 256;
+size_t qb_workspace_bytes(int64_t rows, int64_t cols, int k) {
+    // the FP64 factorization buffers, the FP32 inverse (k x k), W and Q1 (rows x k
+    // FP32), the split partials
+    return sizeof(double) * ws_doubles(k) + sizeof(float) * ((size_t)k * k + (size_t)2 * rows * k) +
+           sizeof(float) * part_floats_needed(rows, cols, k) + 256;
 }
 
-cudaError_t launch_qb_factor(void* cublas, const MatView& A, const float* AX, int64_t ldax, const double* core,
-                             int64_t ld_core, int r2, int k, float* Q, int64_t ldq, float* B, int64_t ldb, void* ws,
-                             int* floored, cudaStream_t st) {
-    if (A.dtype != RE_F32 || k <= 0 || k > 1024) return cudaErrorInvalidValue;
-    cublasHandle_t hb = static_cast<cublasHandle_t>(cublas);
-    if (cublasSetStream(hb, st) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    if (cublasSetMathMode(hb, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    const int64_t M = A.rows;
-    float* W = static_cast<float*>(ws);
-    float* Q1 = W + (size_t)M * k;
-    float* G32 = Q1 + (size_t)M * k;
-    float* Xinv = G32 + (size_t)k * k;
-    double* L = reinterpret_cast<double*>(Xinv + (size_t)k * k);   // 2 M k + 2 k^2 floats: 8-byte aligned
-    double* work = L + (size_t)k * k;
-    double* G64 = work;                               // the core's Gram, consumed before work is needed
-    // R_s: Cholesky of the core's Gram C_k^T C_k (C_k = the first k columns of the r2 x s core)
-    {
-        const double one = 1.0, zero = 0.0;
-        cublasStatus_t cs = cublasDgemm(hb, CUBLAS_OP_N, CUBLAS_OP_T, k, k, r2, &one, core, (int)ld_core, core,
-                                        (int)ld_core, &zero, G64, k);
-        if (cs != CUBLAS_STATUS_SUCCESS) return cublas_err(cs);
-    }
-    chol_lower_kernel<double><<<1, kSmallThreads, 0, st>>>(G64, k, L, k, floored);
-    tri_inv_lower_kernel<<<1, kSmallThreads, 0, st>>>(L, k, work, Xinv);
-    cudaError_t e = cudaGetLastError();
+cudaError_t launch_qb_precondition(const float* AX, int64_t ldax, int64_t rows, int64_t cols, const double* core,
+                                   int64_t ld_core, int r2, int k, void* ws, int* floored, cudaStream_t st,
+                                   int* launches) {
+    (void)cols;
+    if (k <= 0 || k > 1024) return cudaErrorInvalidValue;
+    QbWs w = carve(ws, rows, k);
+    // R_s^T R_s = C_k^T C_k (C_k = the first k columns of the r2 x s core), L = R_s^T
+    const dim3 g64((unsigned)((k + 31) / 32), (unsigned)((k + 31) / 32));
+    gram64_kernel<<<g64, 256, 0, st>>>(core, ld_core, r2, k, w.G64);
+    if (launches) *launches += 1;
+    cudaError_t e = chol_inverse(w.G64, k, k, kDeflPre, w.Lp, w.Xp, w.T, w.fl, w.defl, w.Xinv, floored, st, launches);
     if (e != cudaSuccess) return e;
-    // W = (A X_k) R_s^{-1} = (A X_k) (L^{-1})^T
-    cublasStatus_t cs = sgemm_rm(hb, false, true, (int)M, k, k, AX, ldax, Xinv, k, W, k);
-    if (cs != CUBLAS_STATUS_SUCCESS) return cublas_err(cs);
+    // W = (A X_k) R_s^{-1} = (A X_k) (L^{-1})^T: W(r, c) = sum_l AX[r][l] Xinv[c][l]
+    e = gemm<true, true>(AX, ldax, 1, w.Xinv, 1, k, w.W, k, rows, k, k, 1, 0, st);
+    if (launches) *launches += 1;
+    return e;
+}
+
+cudaError_t launch_qb_orthonormalise(int64_t rows, int64_t cols, int k, float* Q, int64_t ldq, void* ws,
+                                     int* floored, cudaStream_t st, int* launches) {
+    (void)cols;
+    QbWs w = carve(ws, rows, k);
     // two Cholesky-QR passes: G = V^T V, V <- V (L^{-1})^T
-    const float* V = W;
-    for (int pass = 0; pass < 2; ++pass) {
-        float* out = pass == 0 ? Q1 : Q;
+    const float* V = w.W;
+    const int splits = choose_splits(k, k, rows, kPartCap);
+    cudaError_t e = cudaSuccess;
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+        float* out = pass == 0 ? w.Q1 : Q;
         const int64_t ldo = pass == 0 ? k : ldq;
-        cs = sgemm_rm(hb, true, false, k, k, (int)M, V, k, V, k, G32, k);
-        if (cs != CUBLAS_STATUS_SUCCESS) return cublas_err(cs);
-        chol_lower_kernel<float><<<1, kSmallThreads, 0, st>>>(G32, k, L, k, floored);
-        tri_inv_lower_kernel<<<1, kSmallThreads, 0, st>>>(L, k, work, Xinv);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        cs = sgemm_rm(hb, false, true, (int)M, k, k, V, k, Xinv, k, out, ldo);
-        if (cs != CUBLAS_STATUS_SUCCESS) return cublas_err(cs);
-        V = Q1;
+        // partial Gram matrices over row ranges, summed in FP64
+        e = gemm<false, false>(V, 1, k, V, k, 1, w.part, k, k, k, rows, splits, (int64_t)k * k, st);
+        if (e == cudaSuccess) e = reduce_parts<double>(w.part, splits, k, k, w.G64, k, st);
+        if (launches) *launches += 2;
+        if (e == cudaSuccess)
+            e = chol_inverse(w.G64, k, k, kDeflPass, w.Lp, w.Xp, w.T, w.fl, w.defl, w.Xinv, floored, st, launches);
+        if (e == cudaSuccess) e = gemm<true, true>(V, k, 1, w.Xinv, 1, k, out, ldo, rows, k, k, 1, 0, st);
+        if (launches) *launches += 1;
+        V = w.Q1;
     }
-    // B = Q^T A_oriented (k x cols): A_oriented is A (row-major) or A^T when transposed
-    cs = sgemm_rm(hb, true, A.trans, k, (int)A.cols, (int)M, Q, ldq, static_cast<const float*>(A.ptr), A.ld, B,
-                  ldb);
-    return cublas_err(cs);
+    return e;
+}
+
+cudaError_t launch_qb_product(const MatView& A, const float* Q, int64_t ldq, int k, float* B, int64_t ldb, void* ws,
+                              cudaStream_t st, int* launches) {
+    if (A.dtype != RE_F32) return cudaErrorInvalidValue;
+    QbWs w = carve(ws, A.rows, k);
+    const float* Ap = static_cast<const float*>(A.ptr);
+    const int64_t M = A.rows, N = A.cols;
+    const int splits = choose_splits(k, N, M, kPartCap);
+    float* out = splits > 1 ? w.part : B;
+    const int64_t ldo = splits > 1 ? N : ldb;
+    const int64_t zs = (int64_t)k * N;
+    // B(c, j) = sum_i Q[i][c] A_o(i, j); A_o(i, j) = A[i][j], or A[j][i] when the view is transposed
+    cudaError_t e = A.trans ? gemm<false, true>(Q, 1, ldq, Ap, 1, A.ld, out, ldo, k, N, M, splits, zs, st)
+                            : gemm<false, false>(Q, 1, ldq, Ap, A.ld, 1, out, ldo, k, N, M, splits, zs, st);
+    if (launches) *launches += 1;
+    if (e == cudaSuccess && splits > 1) {
+        e = reduce_parts<float>(w.part, splits, k, N, B, ldb, st);
+        if (launches) *launches += 1;
+    }
+    return e;
 }
 
 }  // namespace re

@@ -41,6 +41,7 @@ RE_MLP_PARAMS = 20492
 RE_CONVERGED = 1
 RE_LOWER_BOUND_ONLY = 2
 RE_TRANSPOSED = 4
+RE_QB_DEFLATED = 8
 
 
 class re_opts(ctypes.Structure):
@@ -80,7 +81,9 @@ class re_stats(ctypes.Structure):
                 ("right_ms", ctypes.c_double), ("right_bytes", ctypes.c_double),
                 ("right_flops", ctypes.c_double), ("left_ms", ctypes.c_double),
                 ("svd_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
-                ("passes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
+                ("passes", ctypes.c_int64), ("qb_precondition_ms", ctypes.c_double),
+                ("qb_orthonormalise_ms", ctypes.c_double), ("qb_product_ms", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 1)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -122,3 +122,41 @@ def test_qb_sketch_wider_than_the_matrix(h, m, n, p, eps, s_max, final_s):
     nrm = np.linalg.norm(A64)
     assert np.linalg.norm(A64 - Qg @ Bg) <= 1e-5 * nrm
     assert np.linalg.norm(A64 - orc.Q @ orc.B) <= 1e-12 * nrm
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_qb_noise_floor_columns(precision):
+    """The ladder ends at s_max with hundreds of columns of A X at the FP32 noise
+    floor (eps below what the FP32 sketch resolves, while the FP64 oracle meets
+    the criterion at s = 256): every column of Q stays finite,
+    the columns that are not deflated are orthonormal, deflated ones are zero
+    and flagged, and Q B approximates A as well as the oracle's factorization."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    m, n = 8192, 2048
+    sig = wl.spectrum("step", n, rank=200, tail_scale=1e-6)
+    A = wl.householder_matrix(m, n, sig, seed=4, device="cuda").to(torch.float32)
+    hd = rk.re_create(0, rk.make_opts(precision=precision))
+    try:
+        res, Q, B = rk.re_rank_estimate_qb(hd, A, 1e-6, p=10, seed=5)
+    finally:
+        rk.re_destroy(hd)
+    assert res.status == 0 and res.flags & rk.RE_LOWER_BOUND_ONLY
+    assert res.final_s == 512 and res.k == 512 and res.r == 502
+    assert torch.all(torch.isfinite(Q)) and torch.all(torch.isfinite(B))
+    Qg = Q.double()
+    norms = torch.linalg.norm(Qg, dim=0)
+    live = norms > 0.5
+    assert torch.all(live | (norms == 0))
+    assert bool(res.flags & rk.RE_QB_DEFLATED) == bool((~live).any())
+    Ql = Qg[:, live]
+    assert float((Ql.T @ Ql - torch.eye(Ql.shape[1], device=Ql.device, dtype=Ql.dtype)).abs().max()) < 1e-5
+    A64 = A.double()
+    nrm = float(torch.linalg.norm(A64))
+    err_g = float(torch.linalg.norm(A64 - Qg @ B.double()))
+    # the FP64 oracle resolves the tail and meets the criterion earlier (k = 210 at
+    # s = 256); the GPU's wider factorization must approximate A at least as well
+    orc = a3.qb(A64.cpu().numpy(), 1e-6, p=10, seed=5)
+    assert orc.met and orc.k <= res.k
+    err_o = float(np.linalg.norm(A64.cpu().numpy() - orc.Q @ orc.B))
+    assert err_g <= 1.5 * err_o + 1e-5 * nrm, (err_g / nrm, err_o / nrm)
