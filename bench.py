@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--kind", default="gaussian", choices=["gaussian", "srht", "hrtt"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3", "exact"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--qb", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched", type=int, default=1)
     ap.add_argument("--batched-count", type=int, default=4096)
@@ -394,6 +395,14 @@ def main():
         rl, msl = time_form(hl, learned=True)
         rk.re_destroy(hl)
         forms["learned_bf16x3"] = {"estimates_per_s": 1e3 / msl, "ms": msl, "rank": rl.rank, "passes": rl.passes}
+    if args.kind == "gaussian":
+        # the plain ladder's read-offs with a 128-column first pass (an HBM-bound pass
+        # costs the same for 8 or 128 columns): same rank and width, fewer passes
+        hw = rk.re_create(local, rk.make_opts(precision=prec, first_width=128))
+        rw, msw = time_form(hw)
+        rk.re_destroy(hw)
+        forms[f"{args.precision}_first_width_128"] = {"estimates_per_s": 1e3 / msw, "ms": msw, "rank": rw.rank,
+                                                      "passes": rw.passes}
     forms_ok = len({f["rank"] for f in forms.values()}) == 1
     line["rank_estimates_per_s"] = {k: v["estimates_per_s"] for k, v in forms.items()}
     line["forms"] = forms
@@ -429,6 +438,9 @@ def main():
                           "stage_ms_per_step": {"right": ss.right_ms / K, "left": ss.left_ms / K,
                                                 "svd": ss.svd_ms / K, "other": ss.other_ms / K}}
 
+    if args.kind == "gaussian" and args.qb and world == 1:
+        line["qb"] = bench_qb(rk, local, stream, A, w, K, hbm)
+
     if not args.no_e2e:
         Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
         Ah.copy_(A)
@@ -443,7 +455,25 @@ def main():
         e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
         line["e2e"] = {"value": a_bytes * r2.passes / (e_ms * 1e-3) / 1e9, "unit": "GB/s",
                        "ms_per_step": e_ms, "h2d_bytes_per_step": int(a_bytes),
-                       "d2h_bytes_per_step": int(r2.passes * 40 + 8 * r2.n_sigma)}
+                       "d2h_bytes_per_step": int(r2.passes * 40 + 8 * r2.n_sigma),
+                       "form": "plain ladder; A copied in 8 row chunks, the first pass sketching each as it lands",
+                       "rank": r2.rank, "passes": r2.passes}
+        if kind_code == 0 and args.precision in ("bf16x3", "fp32"):
+            # the same call with a 256-column first pass: the whole ladder's right sketch
+            # runs under the copy, then only the nested read-offs remain
+            hw = rk.re_create(local, rk.make_opts(precision=prec, first_width=256))
+            rk.re_rank_estimate_host(hw, Ah_np, w["eps"], kind_code, w["sketch_seed"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e_steps):
+                r3, _ = rk.re_rank_estimate_host(hw, Ah_np, w["eps"], kind_code, w["sketch_seed"])
+            torch.cuda.synchronize()
+            w_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+            rk.re_destroy(hw)
+            line["e2e"]["first_width_256"] = {"ms_per_step": w_ms, "estimates_per_s": 1e3 / w_ms,
+                                              "rank": r3.rank, "passes": r3.passes,
+                                              "same_rank": r3.rank == r2.rank}
+            line["e2e"]["estimates_per_s"] = 1e3 / e_ms
         del Ah
 
     if args.batched and world == 1:
@@ -470,6 +500,49 @@ def main():
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_qb(rk, local, stream, A, w, K, hbm):
+    """Algorithm 3 (rank estimation + randomized rangefinder) on the same matrix:
+    the BF16x3 ladder with the Frobenius criterion, then the preconditioned
+    Cholesky-QR and B = Q^T A on the library's kernels, with the stage split."""
+    import torch
+    m, n = A.shape
+    p = 10
+    hq = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_BF16X3))
+    Q = torch.empty(m, 512, dtype=torch.float32, device=A.device)
+    B = torch.empty(512, n, dtype=torch.float32, device=A.device)
+    res, _, _ = rk.re_rank_estimate_qb(hq, A, w["eps"], p=p, seed=w["sketch_seed"], Q=Q, B=B, k_cap=512,
+                                       stream=stream)
+    torch.cuda.synchronize()
+    rk.re_stats_enable(hq, True)
+    rk.re_stats_reset(hq)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        res, _, _ = rk.re_rank_estimate_qb(hq, A, w["eps"], p=p, seed=w["sketch_seed"], Q=Q, B=B, k_cap=512,
+                                           stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = rk.re_stats_get(hq)
+    rk.re_destroy(hq)
+    ms_q = e0.elapsed_time(e1) / K
+    k = res.k
+    prod_ms = st.qb_product_ms / K
+    prod_bytes = 4.0 * m * n + 4.0 * m * k + 4.0 * k * n
+    prod_flops = 2.0 * m * n * k
+    del Q, B
+    return {"workload": f"Algorithm 3 on the same matrix, eps={w['eps']}, p={p}, BF16x3 ladder",
+            "ms": ms_q, "r": res.r, "k": k, "final_s": res.final_s, "passes": res.passes, "flags": res.flags,
+            "criterion_met": bool(res.flags & rk.RE_CONVERGED),
+            "stage_ms_per_call": {"right": st.right_ms / K, "left": st.left_ms / K, "svd": st.svd_ms / K,
+                                  "other": st.other_ms / K, "precondition": st.qb_precondition_ms / K,
+                                  "orthonormalise": st.qb_orthonormalise_ms / K, "product": prod_ms},
+            "product": {"kernel": "B = Q^T A, FP32 CUDA-core tiles", "ms": prod_ms,
+                        "gbs": prod_bytes / (prod_ms * 1e-3) / 1e9 if prod_ms else None,
+                        "hbm_frac": prod_bytes / (prod_ms * 1e-3) / 1e9 / hbm if prod_ms else None,
+                        "tflops": prod_flops / (prod_ms * 1e-3) / 1e12 if prod_ms else None}}
 
 
 def bench_precision(rk, local, stream, args, hbm, bf16):

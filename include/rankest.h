@@ -120,7 +120,16 @@ typedef struct {
     int test_drop_load;
     int sigma_est;   /* step 7: RE_SIGMA_SVD (default) or RE_SIGMA_QRDIAG */
     int batch_first_width; /* batched tensor-core ladder: width of its first pass; 0 (default) = autotuned */
-    int reserved[4];
+    /* Single-matrix ladder (Gaussian X, FP32 or BF16x3): the first pass appends the
+     * columns up to this width (a ladder width s0 2^j) in one read of A and the
+     * read-off runs on the nested leading blocks of the core at s0, 2 s0, ... within
+     * it: the plain ladder's rank, width and sigma with fewer passes (an HBM-bound
+     * pass costs the same for 8 or 128 columns).  0 (default) = s0, the plain
+     * ladder.  In re_rank_estimate_host the first pass runs under the
+     * host-to-device copy, so a wide one (up to 256 columns) costs nothing there.
+     * Not with learned = 1. */
+    int first_width;
+    int reserved[3];
 } re_opts;
 
 /* Outcome of one estimate.  sigma values go to a separate caller buffer. */
@@ -217,7 +226,12 @@ int re_rank_estimate(re_handle h, const void* A, int dtype, int64_t m, int64_t n
 
 /* As re_rank_estimate, but A is a HOST pointer: the call copies A to the
  * handle's device workspace (host->device inside the call) and reads back only
- * the result and sigma. */
+ * the result and sigma.  For FP32 A with m >= n, a Gaussian sketch and the
+ * BF16x3 or FP32 precision (learned = 0), the copy runs in row chunks on a
+ * stream of the handle while the first pass of the right sketch (s0 columns, or
+ * opts.first_width) sketches each chunk on `stream` as it lands; the ladder then
+ * continues on the device copy.  The result equals re_rank_estimate's up to the
+ * rounding of A X (the tensor-core kernel's work split follows the row count). */
 int re_rank_estimate_host(re_handle h, const void* A_host, int dtype, int64_t m, int64_t n,
                           int64_t ld, double eps, int sketch_kind, uint64_t seed,
                           double* sigma_out, int sigma_cap, re_result* out, void* stream);

@@ -65,6 +65,8 @@ struct re_handle_ {
     DevBuf mlp_P, mlp_M, mlp_V, mlp_G, mlp_X, mlp_y, mlp_logits, mlp_keep, mlp_cls, mlp_feat, mlp_loss;
     int mlp_step = 0;
     bool mlp_ready = false;
+    cudaStream_t copy_stream = nullptr;         // host entry point: chunked copies of A
+    std::vector<cudaEvent_t> chunk_events;      // one per copied row chunk (plus the start event)
     re::DevReadoff* h_ro = nullptr;   // pinned
     double* h_sigma = nullptr;        // pinned, 1024 doubles
     int sm_count = 0;
@@ -580,8 +582,10 @@ int propose_width(re_handle h, const Plan& P, double eps, int* cls, cudaStream_t
 // answer is the plain ladder's whenever s* is at least the plain final width;
 // otherwise doubling continues from s*.  The HRTT's columns depend on the
 // width, so with it every step sketches A and forms the core anew.
+// pre > 0: the caller has already written columns [0, pre) of the handle's AX
+// (first pass of the host entry point); the first pass then only adds the core.
 int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* sigma_out, int sigma_cap,
-                 re_result* out, cudaStream_t st) {
+                 re_result* out, cudaStream_t st, int pre = 0) {
     const re_opts& o = h->opts;
     if (o.s0 > P.cap) return fail(RE_ERR_ARG, "initial sketch width exceeds the admissible width");
     if (o.learned && !h->mlp_ready) return fail(RE_ERR_ARG, "learned proposal requested but no network is loaded");
@@ -652,12 +656,22 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
     // (one Q tile: its MMA count does not depend on the tile's width), so its first
     // pass appends up to 64 columns at once and the read-off runs on the nested
     // leading blocks of the core at s0, 2 s0, ... within it: the plain ladder's
-    // answer, with fewer passes over A.
-    if (!done && !o.learned && exact_mode(h, P) && s_prev == 0) {
+    // answer, with fewer passes over A.  The FP32 and BF16x3 Gaussian ladders do
+    // the same up to opts.first_width (HBM-bound passes cost the same for 8 or 128
+    // columns), and up to `pre` when the caller sketched that far.
+    int wfirst = 0;
+    if (exact_mode(h, P)) wfirst = 64;
+    else if (P.kind == RE_GAUSSIAN) wfirst = std::max(pre, o.first_width);
+    if (!done && !o.learned && wfirst > 0 && s_prev == 0) {
         int w1 = s;
-        while (w1 * 2 <= std::min(64, smax)) w1 *= 2;
-        if (w1 > s) {
-            if (int r = sketch_to(0, w1)) return r;
+        while (w1 * 2 <= std::min(wfirst, smax)) w1 *= 2;
+        if (w1 > s || pre > 0) {
+            if (pre >= w1) {
+                if (int r = left_blocks(h, P, seed, 0, w1, AX, smax, core, smax, st, 0)) return r;
+                h->stats.passes += 1;
+            } else if (int r = sketch_to(0, w1)) {
+                return r;
+            }
             passes = 1;
             for (int w = s; w <= w1 && !done; w *= 2) {
                 if (int r = check_width(h, P, w, smax, eps, &ro, &r1, st, 2 * w <= smax)) return r;
@@ -802,6 +816,9 @@ int check_opts(const re_opts* o) {
     if (o->sigma_est != RE_SIGMA_SVD && o->sigma_est != RE_SIGMA_QRDIAG) return fail(RE_ERR_ARG, "unknown sigma_est");
     if (o->batch_first_width < 0 || o->batch_first_width % 8 != 0)
         return fail(RE_ERR_ARG, "batch_first_width must be 0 or a positive multiple of 8");
+    if (o->first_width < 0 || o->first_width % 8 != 0)
+        return fail(RE_ERR_ARG, "first_width must be 0 or a positive multiple of 8");
+    if (o->first_width > 0 && o->learned) return fail(RE_ERR_ARG, "first_width and learned exclude each other");
     if (o->sigma_est == RE_SIGMA_QRDIAG && o->precision == RE_PREC_EXACT)
         return fail(RE_ERR_UNSUPPORTED, "QR-diagonal estimates are FP32: not with the exact-product precision mode");
     return RE_OK;
@@ -868,6 +885,8 @@ int re_destroy(re_handle h) {
     re::batched_destroy(h->batched);
     resolve_timings(h);
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->chunk_events) cudaEventDestroy(e);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->h_ro) cudaFreeHost(h->h_ro);
     if (h->h_sigma) cudaFreeHost(h->h_sigma);
     delete h;
@@ -922,17 +941,70 @@ int re_rank_estimate_host(re_handle h, const void* A_host, int dtype, int64_t m,
     if (!h || !out || !A_host) return fail(RE_ERR_ARG, "NULL argument");
     if (m <= 0 || n <= 0 || ld < n) return fail(RE_ERR_ARG, "bad shape");
     if (dtype != RE_F32 && dtype != RE_F64) return fail(RE_ERR_ARG, "bad dtype");
+    if (!(eps > 0.0 && eps < 1.0)) return fail(RE_ERR_ARG, "eps must lie in (0, 1)");
+    if (sigma_cap > 0 && !sigma_out) return fail(RE_ERR_ARG, "sigma_out is NULL");
     cudaSetDevice(h->device);
     const size_t es = dtype == RE_F32 ? 4 : 8;
     if (int r = ensure(h->acopy, es * (size_t)m * n)) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // contiguous rows: one linear copy (the 2-D form would be issued row by row)
-    cudaError_t e = ld == n ? cudaMemcpyAsync(h->acopy.p, A_host, es * (size_t)m * n, cudaMemcpyHostToDevice, st)
-                            : cudaMemcpy2DAsync(h->acopy.p, es * n, A_host, es * ld, es * n, m,
-                                                cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "host to device copy of A");
-    return re_rank_estimate(h, h->acopy.p, dtype, m, n, n, eps, sketch_kind, seed, sigma_out,
-                            sigma_cap, out, stream);
+    const re_opts& o = h->opts;
+    const bool pipe = dtype == RE_F32 && m >= n && sketch_kind == RE_GAUSSIAN && !o.learned &&
+                      (o.precision == RE_PREC_BF16X3 || o.precision == RE_PREC_FP32);
+    if (!pipe) {
+        // contiguous rows: one linear copy (the 2-D form would be issued row by row)
+        cudaError_t e = ld == n ? cudaMemcpyAsync(h->acopy.p, A_host, es * (size_t)m * n, cudaMemcpyHostToDevice, st)
+                                : cudaMemcpy2DAsync(h->acopy.p, es * n, A_host, es * ld, es * n, m,
+                                                    cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "host to device copy of A");
+        return re_rank_estimate(h, h->acopy.p, dtype, m, n, n, eps, sketch_kind, seed, sigma_out,
+                                sigma_cap, out, stream);
+    }
+    Plan P;
+    if (int r = make_plan(h->acopy.p, dtype, m, n, n, sketch_kind, left_kind(h, sketch_kind), o.s_max, &P)) return r;
+    if (o.s0 > P.cap) return fail(RE_ERR_ARG, "initial sketch width exceeds the admissible width");
+    int smax = o.s0;
+    while (smax * 2 <= P.cap) smax *= 2;
+    int w1 = o.s0;
+    while (w1 * 2 <= std::min(o.first_width, smax)) w1 *= 2;
+    if (int r = ensure(h->ax, sizeof(float) * (size_t)m * smax)) return r;
+    float* AX = static_cast<float*>(h->ax.p);
+    // chunks of whole 128-row tiles; the copy stream starts after the caller's
+    // earlier work on `stream` (which may still read the device copy of A)
+    constexpr int kChunks = 8;
+    const int64_t rows_per = std::max<int64_t>(128, ((m + kChunks - 1) / kChunks + 127) / 128 * 128);
+    const int nch = (int)((m + rows_per - 1) / rows_per);
+    cudaError_t e = cudaSuccess;
+    if (!h->copy_stream) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    while (e == cudaSuccess && (int)h->chunk_events.size() < nch + 1) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) h->chunk_events.push_back(ev);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy stream and events");
+    e = cudaEventRecord(h->chunk_events[nch], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->chunk_events[nch], 0);
+    char* dst = static_cast<char*>(h->acopy.p);
+    const char* src = static_cast<const char*>(A_host);
+    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+        const int64_t r0 = (int64_t)c * rows_per, rc = std::min(rows_per, m - r0);
+        e = ld == n ? cudaMemcpyAsync(dst + es * (size_t)r0 * n, src + es * (size_t)r0 * ld, es * (size_t)rc * n,
+                                      cudaMemcpyHostToDevice, h->copy_stream)
+                    : cudaMemcpy2DAsync(dst + es * (size_t)r0 * n, es * n, src + es * (size_t)r0 * ld, es * ld,
+                                        es * n, rc, cudaMemcpyHostToDevice, h->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->chunk_events[c], h->copy_stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "chunked host to device copy of A");
+    // first pass chunk by chunk as the rows land (the rows of AX are independent)
+    for (int c = 0; c < nch; ++c) {
+        const int64_t r0 = (int64_t)c * rows_per, rc = std::min(rows_per, m - r0);
+        e = cudaStreamWaitEvent(st, h->chunk_events[c], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "wait for a copied chunk");
+        Plan Pc = P;
+        Pc.A.ptr = dst + es * (size_t)r0 * n;
+        Pc.A.rows = rc;
+        if (int r = right_columns(h, Pc, seed, 0, w1, AX + (size_t)r0 * smax, smax, st)) return r;
+    }
+    return run_estimate(h, P, eps, seed, sigma_out, sigma_cap, out, st, w1);
 }
 
 int re_rank_estimate_qb(re_handle h, const float* A, int64_t m, int64_t n, int64_t ld, double eps, int p,

@@ -48,7 +48,8 @@ class re_opts(ctypes.Structure):
     _fields_ = [("s0", ctypes.c_int), ("s_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("y_kind", ctypes.c_int), ("norm_a", ctypes.c_double), ("learned", ctypes.c_int),
                 ("test_drop_load", ctypes.c_int), ("sigma_est", ctypes.c_int),
-                ("batch_first_width", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("batch_first_width", ctypes.c_int), ("first_width", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class re_result(ctypes.Structure):

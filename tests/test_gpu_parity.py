@@ -304,6 +304,48 @@ def test_host_entry_point_matches_device(h):
     assert r1.rank == r2.rank == 30 and np.array_equal(s1, s2)
 
 
+@pytest.mark.parametrize("precision", [rk.RE_PREC_BF16X3, rk.RE_PREC_FP32])
+def test_first_width_and_pipelined_host_path(precision):
+    """A wide first pass (opts.first_width) and the host entry point's chunked
+    copy with the first pass under it return the plain ladder's rank and width,
+    sigma within the small-core SVD's accuracy, in fewer passes over A."""
+    sig = wl.spectrum("step", 2048, rank=150, tail_scale=1e-9)
+    A = wl.haar_matrix(8192, 2048, sig, seed=6).to(torch.float32)
+    Ad = A.cuda()
+    hp = rk.re_create(0, rk.make_opts(precision=precision))
+    hw = rk.re_create(0, rk.make_opts(precision=precision, first_width=128))
+    try:
+        r0, s0 = rk.re_rank_estimate(hp, Ad, 1e-4, rk.RE_GAUSSIAN, 3, sigma_cap=512)
+        r1, s1 = rk.re_rank_estimate(hw, Ad, 1e-4, rk.RE_GAUSSIAN, 3, sigma_cap=512)
+        hh = rk.re_create(0, rk.make_opts(precision=precision, first_width=256))
+        r2, s2 = rk.re_rank_estimate_host(hh, A.numpy(), 1e-4, rk.RE_GAUSSIAN, 3, sigma_cap=512)
+        r3, s3 = rk.re_rank_estimate_host(hh, A.numpy(), 1e-4, rk.RE_GAUSSIAN, 3, sigma_cap=512)
+        rk.re_destroy(hh)
+        r4, s4 = rk.re_rank_estimate_host(hp, A.numpy(), 1e-4, rk.RE_GAUSSIAN, 3, sigma_cap=512)
+    finally:
+        rk.re_destroy(hp)
+        rk.re_destroy(hw)
+    assert r0.rank == 150 and r0.final_s == 256 and r0.passes == 6
+    for r, sg in ((r1, s1), (r2, s2), (r3, s3), (r4, s4)):
+        assert (r.rank, r.final_s, r.flags, r.n_sigma) == (r0.rank, r0.final_s, r0.flags, r0.n_sigma)
+        # A X differs by FP32 rounding; the FP32 small-core SVD holds sigma to about
+        # 1e-5 sigma_1 (its stop rule), the bound used for it against LAPACK
+        assert np.max(np.abs(sg[:r0.n_sigma] - s0[:r0.n_sigma])) <= 3e-5 * s0[0]
+    assert r1.passes == 2          # 128 columns, then 128 more
+    assert r2.passes == 1 and r3.passes == 1   # 256 columns sketched under the copy
+    assert r4.passes == r0.passes              # plain ladder, its first pass under the copy
+    assert np.array_equal(s2, s3)  # the chunked path is deterministic
+
+
+def test_first_width_option_errors():
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_create(0, rk.make_opts(first_width=12))
+    assert e.value.code == rk.RE_ERR_ARG
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_create(0, rk.make_opts(first_width=64, learned=1))
+    assert e.value.code == rk.RE_ERR_ARG
+
+
 def test_errors(h):
     A = torch.ones(64, 32, device="cuda")
     with pytest.raises(rk.RankEstError) as e:
