@@ -529,17 +529,22 @@ def bench_qb(rk, local, stream, A, w, K, hbm):
     rk.re_destroy(hq)
     ms_q = e0.elapsed_time(e1) / K
     k = res.k
+    # ||A - Q B||_F / ||A||_F on every 64th row (outside the timed region)
+    rows = torch.arange(0, m, 64, device=A.device)
+    As = A[rows].double()
+    rel_err = float(torch.linalg.norm(As - Q[rows, :k].double() @ B[:k].double()) / torch.linalg.norm(As))
     prod_ms = st.qb_product_ms / K
     prod_bytes = 4.0 * m * n + 4.0 * m * k + 4.0 * k * n
     prod_flops = 2.0 * m * n * k
     del Q, B
     return {"workload": f"Algorithm 3 on the same matrix, eps={w['eps']}, p={p}, BF16x3 ladder",
             "ms": ms_q, "r": res.r, "k": k, "final_s": res.final_s, "passes": res.passes, "flags": res.flags,
-            "criterion_met": bool(res.flags & rk.RE_CONVERGED),
+            "criterion_met": bool(res.flags & rk.RE_CONVERGED), "rel_err_row_sample": rel_err,
             "stage_ms_per_call": {"right": st.right_ms / K, "left": st.left_ms / K, "svd": st.svd_ms / K,
                                   "other": st.other_ms / K, "precondition": st.qb_precondition_ms / K,
                                   "orthonormalise": st.qb_orthonormalise_ms / K, "product": prod_ms},
-            "product": {"kernel": "B = Q^T A, FP32 CUDA-core tiles", "ms": prod_ms,
+            "product": {"kernel": "B = Q^T A, tcgen05, both factors split into three BF16 terms (6 products)",
+                        "ms": prod_ms, "bf16_tflops": 6 * prod_flops / (prod_ms * 1e-3) / 1e12 if prod_ms else None,
                         "gbs": prod_bytes / (prod_ms * 1e-3) / 1e9 if prod_ms else None,
                         "hbm_frac": prod_bytes / (prod_ms * 1e-3) / 1e9 / hbm if prod_ms else None,
                         "tflops": prod_flops / (prod_ms * 1e-3) / 1e12 if prod_ms else None}}

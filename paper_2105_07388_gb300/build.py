@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "librankest.so")
 
 SOURCES = ["api.cu", "embed.cu", "sketch_simt.cu", "sketch_srht.cu", "sketch_tc.cu", "sketch_ex.cu",
            "core_svd.cu", "noalloc.cu", "batched.cu", "mlp.cu", "left_tc.cu", "batched_tc.cu", "left_fwht.cu",
-           "rangefinder.cu"]
+           "rangefinder.cu", "qb_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

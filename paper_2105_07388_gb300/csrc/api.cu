@@ -779,7 +779,10 @@ int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* 
     out->norm_a = sel.norm_a;
     if (k > k_cap) return fail(RE_ERR_ARG, "k_cap is smaller than the chosen k = r + p (out->k holds it)");
     if (ldq < k) return fail(RE_ERR_ARG, "ldq < k");
-    if (int rr = ensure(h->qbws, re::qb_workspace_bytes(M, P.A.cols, k))) return rr;
+    // B = Q^T A on the tensor cores (BF16x3 split of both factors) unless the
+    // handle asks for the plain FP32 form
+    const bool tensor = o.precision == RE_PREC_BF16X3;
+    if (int rr = ensure(h->qbws, re::qb_workspace_bytes(M, P.A.cols, k, tensor))) return rr;
     int nl = 0;
     cudaEvent_t a = stage_begin(h, st);
     e = re::launch_qb_precondition(AX, smax, M, P.A.cols, core, smax, 2 * s, k, h->qbws.p, floored, st, &nl);
@@ -791,14 +794,18 @@ int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* 
     }
     if (e == cudaSuccess) {
         a = stage_begin(h, st);
-        e = re::launch_qb_product(P.A, Q, ldq, k, B, ldb, h->qbws.p, st, &nl);
+        e = re::launch_qb_product(P.A, Q, ldq, k, B, ldb, h->qbws.p, tensor, static_cast<int*>(h->status.p) + 1, st,
+                                  &nl);
         stage_end(h, st, a, kStageQbProduct);
     }
     h->stats.launches += nl;
-    int hf = 0;
+    int hf = 0, tmo = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, floored, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&tmo, static_cast<int*>(h->status.p) + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "thin QR and B = Q^T A");
+    if (tmo) return fail(RE_ERR_TIMEOUT, "a bounded device wait expired");
     if (hf) out->flags |= RE_QB_DEFLATED;
     resolve_timings(h);
     return RE_OK;

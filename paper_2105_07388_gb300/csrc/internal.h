@@ -247,7 +247,7 @@ struct QbSelect {
 // smaller dimension (the conservative tail runs to it).
 cudaError_t launch_select_rank(const double* sigma_scaled, int r1, int64_t n, double eps, double norm_a, int p,
                                int s, QbSelect* out, cudaStream_t st);
-size_t qb_workspace_bytes(int64_t rows, int64_t cols, int k);
+size_t qb_workspace_bytes(int64_t rows, int64_t cols, int k, bool tensor);
 // Steps 7-8 for the first k columns of AX (rows x ldax FP32) with the FP64 core
 // (r2 rows, ld_core) as the preconditioning sketch, in three stream-ordered
 // stages on the workspace ws (qb_workspace_bytes(rows, cols, k)):
@@ -262,8 +262,26 @@ cudaError_t launch_qb_precondition(const float* AX, int64_t ldax, int64_t rows, 
                                    int* launches);
 cudaError_t launch_qb_orthonormalise(int64_t rows, int64_t cols, int k, float* Q, int64_t ldq, void* ws,
                                      int* floored, cudaStream_t st, int* launches);
+// tensor: B = Q^T A on the tensor cores (qb_tc.cu) when the view allows it (else
+// CUDA cores); err_flag receives a bounded wait's expiry.
 cudaError_t launch_qb_product(const MatView& A, const float* Q, int64_t ldq, int k, float* B, int64_t ldb, void* ws,
-                              cudaStream_t st, int* launches);
+                              bool tensor, int* err_flag, cudaStream_t st, int* launches);
+// out (M x N, pitch ldo) = the sum over `splits` FP32 partials (pitch N, M N apart),
+// added in FP64 in split order.
+cudaError_t reduce_parts_f32(const float* part, int splits, int64_t M, int64_t N, float* out, int64_t ldo,
+                             cudaStream_t st);
+
+// ---- B = Q^T A on tcgen05 (qb_tc.cu) -------------------------------------------
+bool qb_tc_supported(const MatView& A);
+int64_t qb_tc_qt_ld(int64_t M);          // row pitch of the Q^T terms
+int qb_tc_qt_rows(int k);                // rows per term (k rounded up to 128)
+int qb_tc_splits(int64_t tiles, int64_t kchunks, int cap);
+// Qt (3 x qb_tc_qt_rows(k) rows of pitch qb_tc_qt_ld(M), BF16 bits) = the three
+// BF16 terms of Q^T (Q: M x k FP32, pitch ldq)
+cudaError_t launch_qt_split(const float* Q, int64_t ldq, int64_t M, int k, uint16_t* Qt, cudaStream_t st);
+// rows [c0, c0 + kq) of Q^T A (kq <= 128) into out (pitch ldo); split partials in part
+cudaError_t launch_qb_product_tc(const MatView& A, const uint16_t* Qt, int k, int c0, int kq, float* out,
+                                 int64_t ldo, float* part, int splits, int* err_flag, cudaStream_t st);
 
 // ---- batched estimate (batched.cu) --------------------------------------------
 struct BatchedState;

@@ -506,9 +506,13 @@ struct QbWs {
     double *G64, *Lp, *Xp, *T, *fl;
     int* defl;
     float *Xinv, *W, *Q1, *part;
+    uint16_t* qt;                   // the Q^T terms of the tensor-core product
 };
 
-constexpr int kPartCap = 128;       // largest split count of any product
+constexpr int kPartCap = 128;       // largest split count of any CUDA-core product
+constexpr size_t kTcPartFloats = (size_t)16 << 20;   // tensor-core product partials: 64 MB
+
+int tc_part_cap(int64_t cols) { return (int)std::max<int64_t>(1, (int64_t)kTcPartFloats / (128 * cols)); }
 // Relative deflation thresholds (pivot over the column's own squared norm): the
 // core is FP64 but holds what FP32 A X resolves, about 1e-7 of a column's norm
 // at the noise floor, so 1e-24 deflates only columns dependent far below that;
@@ -517,13 +521,15 @@ constexpr int kPartCap = 128;       // largest split count of any product
 constexpr double kDeflPre = 1e-24;
 constexpr double kDeflPass = 1e-12;
 
-size_t part_floats_needed(int64_t rows, int64_t cols, int k) {
-    // the Gram splits (k x k each) and the product's splits (k x cols each)
+size_t part_floats_needed(int64_t rows, int64_t cols, int k, bool tensor) {
+    // the Gram splits (k x k each) and the product's splits (k x cols each, or
+    // 128 x cols each on the tensor cores)
     const int64_t sg = choose_splits(k, k, rows, kPartCap);
     const int64_t sb = choose_splits(k, cols, rows, kPartCap);
     const int64_t a = sg * (int64_t)k * k;
     const int64_t b = sb > 1 ? sb * (int64_t)k * cols : 0;
-    return (size_t)std::max(a, b);
+    const int64_t c = tensor ? (int64_t)tc_part_cap(cols) * 128 * cols : 0;
+    return (size_t)std::max({a, b, c});
 }
 
 size_t ws_doubles(int k) {
@@ -531,7 +537,7 @@ size_t ws_doubles(int k) {
     return (size_t)k * k + 2 * kp * kp + kp * kp / 4 + 2 + kp / 2;   // G64, Lp, Xp, T, fl (+ pad), defl
 }
 
-QbWs carve(void* ws, int64_t rows, int k) {
+QbWs carve(void* ws, int64_t rows, int64_t cols, int k, bool tensor) {
     const size_t kp = (size_t)kpad(k);
     QbWs w;
     w.G64 = static_cast<double*>(ws);
@@ -544,6 +550,9 @@ QbWs carve(void* ws, int64_t rows, int k) {
     w.W = w.Xinv + (size_t)k * k;
     w.Q1 = w.W + (size_t)rows * k;
     w.part = w.Q1 + (size_t)rows * k;
+    // 16-byte aligned: the tensor maps of the product start here
+    const uintptr_t q = reinterpret_cast<uintptr_t>(w.part + part_floats_needed(rows, cols, k, tensor));
+    w.qt = reinterpret_cast<uint16_t*>((q + 15) & ~(uintptr_t)15);
     return w;
 }
 
@@ -555,19 +564,24 @@ cudaError_t launch_select_rank(const double* sigma_scaled, int r1, int64_t n, do
     return cudaGetLastError();
 }
 
-size_t qb_workspace_bytes(int64_t rows, int64_t cols, int k) {
+size_t qb_workspace_bytes(int64_t rows, int64_t cols, int k, bool tensor) {
     // the FP64 factorization buffers, the FP32 inverse (k x k), W and Q1 (rows x k
-    // FP32), the split partials
+    // FP32), the split partials, the Q^T terms (tensor cores)
+    const size_t qt = tensor ? sizeof(uint16_t) * 3 * (size_t)qb_tc_qt_rows(k) * (size_t)qb_tc_qt_ld(rows) : 0;
     return sizeof(double) * ws_doubles(k) + sizeof(float) * ((size_t)k * k + (size_t)2 * rows * k) +
-           sizeof(float) * part_floats_needed(rows, cols, k) + 256;
+           sizeof(float) * part_floats_needed(rows, cols, k, tensor) + qt + 256;
+}
+
+cudaError_t reduce_parts_f32(const float* part, int splits, int64_t M, int64_t N, float* out, int64_t ldo,
+                             cudaStream_t st) {
+    return reduce_parts<float>(part, splits, M, N, out, ldo, st);
 }
 
 cudaError_t launch_qb_precondition(const float* AX, int64_t ldax, int64_t rows, int64_t cols, const double* core,
                                    int64_t ld_core, int r2, int k, void* ws, int* floored, cudaStream_t st,
                                    int* launches) {
-    (void)cols;
     if (k <= 0 || k > 1024) return cudaErrorInvalidValue;
-    QbWs w = carve(ws, rows, k);
+    QbWs w = carve(ws, rows, cols, k, false);
     // R_s^T R_s = C_k^T C_k (C_k = the first k columns of the r2 x s core), L = R_s^T
     const dim3 g64((unsigned)((k + 31) / 32), (unsigned)((k + 31) / 32));
     gram64_kernel<<<g64, 256, 0, st>>>(core, ld_core, r2, k, w.G64);
@@ -582,8 +596,7 @@ cudaError_t launch_qb_precondition(const float* AX, int64_t ldax, int64_t rows, 
 
 cudaError_t launch_qb_orthonormalise(int64_t rows, int64_t cols, int k, float* Q, int64_t ldq, void* ws,
                                      int* floored, cudaStream_t st, int* launches) {
-    (void)cols;
-    QbWs w = carve(ws, rows, k);
+    QbWs w = carve(ws, rows, cols, k, false);
     // two Cholesky-QR passes: G = V^T V, V <- V (L^{-1})^T
     const float* V = w.W;
     const int splits = choose_splits(k, k, rows, kPartCap);
@@ -605,11 +618,27 @@ cudaError_t launch_qb_orthonormalise(int64_t rows, int64_t cols, int k, float* Q
 }
 
 cudaError_t launch_qb_product(const MatView& A, const float* Q, int64_t ldq, int k, float* B, int64_t ldb, void* ws,
-                              cudaStream_t st, int* launches) {
+                              bool tensor, int* err_flag, cudaStream_t st, int* launches) {
     if (A.dtype != RE_F32) return cudaErrorInvalidValue;
-    QbWs w = carve(ws, A.rows, k);
     const float* Ap = static_cast<const float*>(A.ptr);
     const int64_t M = A.rows, N = A.cols;
+    if (tensor && qb_tc_supported(A)) {
+        // B = Q^T A on the tensor cores: the three BF16 terms of Q^T once, then one
+        // launch per 128 columns of Q (each reads A once)
+        QbWs w = carve(ws, M, N, k, true);
+        cudaError_t e = launch_qt_split(Q, ldq, M, k, w.qt, st);
+        int nl = 1;
+        const int64_t tiles = (N + 127) / 128, kchunks = (M + 63) / 64;
+        const int splits = qb_tc_splits(tiles, kchunks, tc_part_cap(N));
+        for (int c0 = 0; c0 < k && e == cudaSuccess; c0 += 128) {
+            const int kq = std::min(128, k - c0);
+            e = launch_qb_product_tc(A, w.qt, k, c0, kq, B + (size_t)c0 * ldb, ldb, w.part, splits, err_flag, st);
+            nl += splits > 1 ? 2 : 1;
+        }
+        if (launches) *launches += nl;
+        return e;
+    }
+    QbWs w = carve(ws, M, N, k, false);
     const int splits = choose_splits(k, N, M, kPartCap);
     float* out = splits > 1 ? w.part : B;
     const int64_t ldo = splits > 1 ? N : ldb;

@@ -45,12 +45,24 @@ CASES = [
 ]
 
 
+@pytest.fixture(scope="module")
+def h_tc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    hd = rk.re_create(0, rk.make_opts(precision=rk.RE_PREC_BF16X3))
+    yield hd
+    rk.re_destroy(hd)
+
+
+@pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("fam,m,n,kw,eps,p", CASES)
-def test_qb_parity(h, fam, m, n, kw, eps, p):
+def test_qb_parity(h, h_tc, tensor, fam, m, n, kw, eps, p):
+    """FP32 handle: CUDA-core products; BF16x3 handle: B = Q^T A on the tensor
+    cores (both factors split into three BF16 terms, six products)."""
     sig = wl.spectrum(fam, min(m, n), **kw)
     A = wl.haar_matrix(m, n, sig, seed=m + n).numpy().astype(np.float32)
     A64 = A.astype(np.float64)
-    res, Q, B = rk.re_rank_estimate_qb(h, torch.from_numpy(A).cuda(), eps, p=p, seed=21)
+    res, Q, B = rk.re_rank_estimate_qb(h_tc if tensor else h, torch.from_numpy(A).cuda(), eps, p=p, seed=21)
     orc = a3.qb(A64, eps, p=p, seed=21)
     assert res.status == 0
     assert bool(res.flags & rk.RE_TRANSPOSED) == (m < n) == orc.transposed
