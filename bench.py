@@ -439,7 +439,10 @@ def main():
                                                 "svd": ss.svd_ms / K, "other": ss.other_ms / K}}
 
     if args.kind == "gaussian" and args.qb and world == 1:
-        line["qb"] = bench_qb(rk, local, stream, A, w, K, hbm)
+        line["qb"] = bench_qb(rk, local, stream, A, w, K, hbm, rk.RE_PREC_BF16X3)
+        # the exact-product ladder resolves the tail that step 5 sums: the criterion is
+        # met at the gap instead of running to s_max
+        line["qb"]["exact_product_ladder"] = bench_qb(rk, local, stream, A, w, K, hbm, rk.RE_PREC_EXACT)
 
     if not args.no_e2e:
         Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
@@ -502,14 +505,15 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def bench_qb(rk, local, stream, A, w, K, hbm):
+def bench_qb(rk, local, stream, A, w, K, hbm, precision):
     """Algorithm 3 (rank estimation + randomized rangefinder) on the same matrix:
-    the BF16x3 ladder with the Frobenius criterion, then the preconditioned
-    Cholesky-QR and B = Q^T A on the library's kernels, with the stage split."""
+    the ladder (BF16x3 or exact-product sketch) with the Frobenius criterion, then
+    the preconditioned Cholesky-QR and B = Q^T A on the library's kernels, with
+    the stage split."""
     import torch
     m, n = A.shape
     p = 10
-    hq = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_BF16X3))
+    hq = rk.re_create(local, rk.make_opts(precision=precision))
     Q = torch.empty(m, 512, dtype=torch.float32, device=A.device)
     B = torch.empty(512, n, dtype=torch.float32, device=A.device)
     res, _, _ = rk.re_rank_estimate_qb(hq, A, w["eps"], p=p, seed=w["sketch_seed"], Q=Q, B=B, k_cap=512,
@@ -537,7 +541,9 @@ def bench_qb(rk, local, stream, A, w, K, hbm):
     prod_bytes = 4.0 * m * n + 4.0 * m * k + 4.0 * k * n
     prod_flops = 2.0 * m * n * k
     del Q, B
-    return {"workload": f"Algorithm 3 on the same matrix, eps={w['eps']}, p={p}, BF16x3 ladder",
+    ladder = "exact-product" if precision == rk.RE_PREC_EXACT else "BF16x3"
+    return {"workload": f"Algorithm 3 on the same matrix, eps={w['eps']}, p={p}, {ladder} ladder",
+            "deflated": bool(res.flags & rk.RE_QB_DEFLATED),
             "ms": ms_q, "r": res.r, "k": k, "final_s": res.final_s, "passes": res.passes, "flags": res.flags,
             "criterion_met": bool(res.flags & rk.RE_CONVERGED), "rel_err_row_sample": rel_err,
             "stage_ms_per_call": {"right": st.right_ms / K, "left": st.left_ms / K, "svd": st.svd_ms / K,

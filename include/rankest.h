@@ -346,7 +346,12 @@ typedef struct {
  * core Y (A X_k) to precondition (Sec. 4's randomized approximate
  * orthogonalization) and two Cholesky-QR passes, all in the library's own
  * kernels (FP64 Gram of the core and FP64 blocked Cholesky factorizations and
- * triangular inverses; FP32 products on CUDA cores).  A column of A X_k that
+ * triangular inverses; FP32 products on CUDA cores).  opts.precision selects
+ * the ladder's sketch and B's product: RE_PREC_FP32 (FP32 SIMT sketch, B on
+ * CUDA cores), RE_PREC_BF16X3 (tensor-core sketch; B = Q^T A on the tensor
+ * cores with both factors split into three BF16 terms), RE_PREC_EXACT (the
+ * exact-product sketch, which resolves the tail values step 5 sums, m >= n
+ * only; B as for BF16X3).  A column of A X_k that
  * adds nothing resolvable to the span of the earlier ones (a Cholesky pivot below
  * 1e-24 of its squared norm for the core, 1e-12 in the FP32 passes: for example
  * columns at the FP32 noise floor when the ladder ends at s_max) is deflated:

@@ -724,7 +724,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
 int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* Q, int64_t ldq, float* B,
            int64_t ldb, int k_cap, re_qb_result* out, cudaStream_t st) {
     const re_opts& o = h->opts;
-    if (exact_mode(h, P)) return fail(RE_ERR_UNSUPPORTED, "Algorithm 3 runs with the FP32 or BF16x3 sketch");
+    const bool exact = exact_mode(h, P);
     if (o.s0 > P.cap) return fail(RE_ERR_ARG, "initial sketch width exceeds the admissible width");
     int smax = o.s0;
     while (smax * 2 <= P.cap) smax *= 2;
@@ -744,6 +744,11 @@ int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* 
     cudaError_t e = cudaMemsetAsync(h->status.p, 0, 4 * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(floored, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, "clear status");
+    // the exact-product sketch resolves the tail values that step 5 sums (its A X
+    // stays in FP32 pair planes; the factorization takes their leading FP32 part)
+    if (exact) {
+        if (int r = exact_prepare(h, P, smax, st)) return r;
+    }
     std::memset(out, 0, sizeof(*out));
     int s_prev = 0, s = o.s0, passes = 0, r1 = 0;
     re::DevReadoff ro{};
@@ -781,11 +786,14 @@ int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* 
     if (ldq < k) return fail(RE_ERR_ARG, "ldq < k");
     // B = Q^T A on the tensor cores (BF16x3 split of both factors) unless the
     // handle asks for the plain FP32 form
-    const bool tensor = o.precision == RE_PREC_BF16X3;
+    const bool tensor = o.precision == RE_PREC_BF16X3 || exact;
     if (int rr = ensure(h->qbws, re::qb_workspace_bytes(M, P.A.cols, k, tensor))) return rr;
     int nl = 0;
     cudaEvent_t a = stage_begin(h, st);
-    e = re::launch_qb_precondition(AX, smax, M, P.A.cols, core, smax, 2 * s, k, h->qbws.p, floored, st, &nl);
+    e = exact ? re::launch_qb_precondition(static_cast<const float*>(h->ex_hi.p), 1, h->ex_ldp, M, P.A.cols, core,
+                                           smax, 2 * s, k, h->qbws.p, floored, st, &nl)
+              : re::launch_qb_precondition(AX, smax, 1, M, P.A.cols, core, smax, 2 * s, k, h->qbws.p, floored, st,
+                                           &nl);
     stage_end(h, st, a, kStageQbPre);
     if (e == cudaSuccess) {
         a = stage_begin(h, st);

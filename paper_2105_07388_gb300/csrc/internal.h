@@ -257,9 +257,10 @@ size_t qb_workspace_bytes(int64_t rows, int64_t cols, int k, bool tensor);
 //   product:        B = Q^T A_oriented (k x cols, ldb).
 // *floored (device) is set when a Cholesky pivot had to be raised (an exactly
 // singular Gram matrix).  launches (may be null) counts the kernels launched.
-cudaError_t launch_qb_precondition(const float* AX, int64_t ldax, int64_t rows, int64_t cols, const double* core,
-                                   int64_t ld_core, int r2, int k, void* ws, int* floored, cudaStream_t st,
-                                   int* launches);
+// AX(r, l) at AX[r sar + l sak] (sak == 1: row-major; sar == 1: transposed planes)
+cudaError_t launch_qb_precondition(const float* AX, int64_t sar, int64_t sak, int64_t rows, int64_t cols,
+                                   const double* core, int64_t ld_core, int r2, int k, void* ws, int* floored,
+                                   cudaStream_t st, int* launches);
 cudaError_t launch_qb_orthonormalise(int64_t rows, int64_t cols, int k, float* Q, int64_t ldq, void* ws,
                                      int* floored, cudaStream_t st, int* launches);
 // tensor: B = Q^T A on the tensor cores (qb_tc.cu) when the view allows it (else

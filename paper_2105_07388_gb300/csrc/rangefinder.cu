@@ -577,9 +577,9 @@ cudaError_t reduce_parts_f32(const float* part, int splits, int64_t M, int64_t N
     return reduce_parts<float>(part, splits, M, N, out, ldo, st);
 }
 
-cudaError_t launch_qb_precondition(const float* AX, int64_t ldax, int64_t rows, int64_t cols, const double* core,
-                                   int64_t ld_core, int r2, int k, void* ws, int* floored, cudaStream_t st,
-                                   int* launches) {
+cudaError_t launch_qb_precondition(const float* AX, int64_t sar, int64_t sak, int64_t rows, int64_t cols,
+                                   const double* core, int64_t ld_core, int r2, int k, void* ws, int* floored,
+                                   cudaStream_t st, int* launches) {
     if (k <= 0 || k > 1024) return cudaErrorInvalidValue;
     QbWs w = carve(ws, rows, cols, k, false);
     // R_s^T R_s = C_k^T C_k (C_k = the first k columns of the r2 x s core), L = R_s^T
@@ -588,8 +588,11 @@ cudaError_t launch_qb_precondition(const float* AX, int64_t ldax, int64_t rows, 
     if (launches) *launches += 1;
     cudaError_t e = chol_inverse(w.G64, k, k, kDeflPre, w.Lp, w.Xp, w.T, w.fl, w.defl, w.Xinv, floored, st, launches);
     if (e != cudaSuccess) return e;
-    // W = (A X_k) R_s^{-1} = (A X_k) (L^{-1})^T: W(r, c) = sum_l AX[r][l] Xinv[c][l]
-    e = gemm<true, true>(AX, ldax, 1, w.Xinv, 1, k, w.W, k, rows, k, k, 1, 0, st);
+    // W = (A X_k) R_s^{-1} = (A X_k) (L^{-1})^T: W(r, c) = sum_l AX(r, l) Xinv[c][l],
+    // AX(r, l) at AX[r sar + l sak] (row-major, or the transposed planes of the
+    // exact-product mode)
+    e = sak == 1 ? gemm<true, true>(AX, sar, 1, w.Xinv, 1, k, w.W, k, rows, k, k, 1, 0, st)
+                 : gemm<false, true>(AX, sar, sak, w.Xinv, 1, k, w.W, k, rows, k, k, 1, 0, st);
     if (launches) *launches += 1;
     return e;
 }

@@ -172,3 +172,39 @@ def test_qb_noise_floor_columns(precision):
     assert orc.met and orc.k <= res.k
     err_o = float(np.linalg.norm(A64.cpu().numpy() - orc.Q @ orc.B))
     assert err_g <= 1.5 * err_o + 1e-5 * nrm, (err_g / nrm, err_o / nrm)
+
+
+def test_qb_exact_product_ladder_meets_the_criterion():
+    """With the exact-product sketch (RE_PREC_EXACT) the tail values that step 5
+    sums are resolved: on the matrix where the FP32 ladder runs to s_max, the
+    criterion is met at the oracle's r, k and width, and Q B approximates A as
+    well as the oracle's factorization."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    m, n = 8192, 2048
+    sig = wl.spectrum("step", n, rank=200, tail_scale=1e-6)
+    A = wl.householder_matrix(m, n, sig, seed=4, device="cuda").to(torch.float32)
+    hd = rk.re_create(0, rk.make_opts(precision=rk.RE_PREC_EXACT))
+    try:
+        res, Q, B = rk.re_rank_estimate_qb(hd, A, 1e-6, p=10, seed=5)
+    finally:
+        rk.re_destroy(hd)
+    A64 = A.double()
+    orc = a3.qb(A64.cpu().numpy(), 1e-6, p=10, seed=5)
+    assert orc.met and res.flags & rk.RE_CONVERGED
+    assert (res.r, res.k, res.final_s) == (orc.r, orc.k, orc.final_s) == (200, 210, 256)
+    # the p extra columns sit at the 5e-9 tail: below what the FP64 Gram matrix of
+    # the core (squared: 2.5e-17 < 2^-53) and the FP32 A X resolve, so they may
+    # deflate; the r leading columns never do
+    Qg = Q.double()
+    norms = torch.linalg.norm(Qg, dim=0)
+    live = norms > 0.5
+    assert torch.all(live | (norms == 0)) and bool(live[:200].all())
+    assert bool(res.flags & rk.RE_QB_DEFLATED) == bool((~live).any())
+    Ql = Qg[:, live]
+    assert float((Ql.T @ Ql - torch.eye(Ql.shape[1], device=Ql.device, dtype=Ql.dtype)).abs().max()) < 1e-5
+    nrm = float(torch.linalg.norm(A64))
+    err_g = float(torch.linalg.norm(A64 - Qg @ B.double()))
+    err_o = float(np.linalg.norm(A64.cpu().numpy() - orc.Q @ orc.B))
+    assert err_g <= 1.5 * err_o + 1e-5 * nrm, (err_g / nrm, err_o / nrm)
+    assert res.bound <= 1e-6 * res.norm_a * (1 + 1e-12)
