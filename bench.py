@@ -175,6 +175,31 @@ def cpu_oracle_run(A_host: np.ndarray, w, kind: int, budget_s: float = 20.0):
                                      "seconds": el, "passes": res.passes}
 
 
+def cpu_oracle_single_thread(A_host: np.ndarray, w, kind: int, budget_s: float = 8.0):
+    """The oracle as cpu_oracle_run, in a child process whose BLAS and OpenMP pools
+    have one thread; returns (GB/s, info) or (None, reason)."""
+    import subprocess
+    import sys
+    import tempfile
+    rows = min(A_host.shape[0], 1024)
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "a.npy")
+        np.save(path, A_host[:rows])
+        env = dict(os.environ)
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[v] = "1"
+        code = ("import json, sys, numpy as np; sys.path.insert(0, %r); import bench; "
+                "a = np.load(%r); v, info = bench.cpu_oracle_run(a, %r, %d, budget_s=%r); "
+                "print(json.dumps([v, info]))" % (ROOT, path, dict(w), kind, budget_s))
+        try:
+            r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                               timeout=20 * budget_s)
+            v, info = json.loads(r.stdout.strip().splitlines()[-1])
+            return v, info
+        except Exception as e:  # noqa: BLE001 - the single-thread figure is optional context
+            return None, {"error": str(e)[:200]}
+
+
 def max_over_ranks(x: float, device="cpu") -> float:
     """Largest x over the ranks of the default process group (x itself when there
     is no group or one rank): the job time is the slowest rank's."""
@@ -448,6 +473,19 @@ def main():
         Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
         Ah.copy_(A)
         Ah_np = Ah.numpy()
+        # the host-to-device link on its own: one linear copy of the pinned A
+        Ad = torch.empty_like(A)
+        Ad.copy_(Ah, non_blocking=True)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(3):
+            Ad.copy_(Ah, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = 3 * a_bytes / (c0.elapsed_time(c1) * 1e-3) / 1e9
+        del Ad
         rk.re_rank_estimate_host(h, Ah_np, w["eps"], kind_code, w["sketch_seed"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -460,6 +498,8 @@ def main():
                        "ms_per_step": e_ms, "h2d_bytes_per_step": int(a_bytes),
                        "d2h_bytes_per_step": int(r2.passes * 40 + 8 * r2.n_sigma),
                        "form": "plain ladder; A copied in 8 row chunks, the first pass sketching each as it lands",
+                       "h2d_link_gbs": h2d_gbs,
+                       "copy_floor_ms": a_bytes / (h2d_gbs * 1e9) * 1e3,
                        "rank": r2.rank, "passes": r2.passes}
         if kind_code == 0 and args.precision in ("bf16x3", "fp32"):
             # the same call with a 256-column first pass: the whole ladder's right sketch
@@ -498,6 +538,14 @@ def main():
                                 "sample": f"first {info['rows']} rows x {info['cols']} of A, "
                                           f"full doubling ladder, {info['runs']} runs in "
                                           f"{info['seconds']:.1f} s"}
+        v1, info1 = cpu_oracle_single_thread(A_host, w, kind_code)
+        if v1 is not None:
+            line["cpu_baseline"]["single_thread"] = {
+                "value": v1, "unit": "GB/s", "cores": 1,
+                "sample": f"first {info1['rows']} rows x {info1['cols']} of A, full doubling ladder, "
+                          f"{info1['runs']} runs in {info1['seconds']:.1f} s, BLAS and OpenMP pools of one thread"}
+        else:
+            line["cpu_baseline"]["single_thread"] = info1
     rk.re_destroy(h)
     if rank == 0:
         print(json.dumps(line))
