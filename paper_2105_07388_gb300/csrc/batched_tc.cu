@@ -589,8 +589,7 @@ cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t
     p.col0 = col0;
     p.err = err_flag;
     const size_t smem = (size_t)kHalfBytes * kAStages + (((size_t)p.N * 128 + 1023) & ~(size_t)1023) * kStages + 1024;
-    cudaError_t e = cudaFuncSetAttribute(right_tc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(right_tc_batched_kernel));
     if (e != cudaSuccess) return e;
     if (!g_bsms) {
         int dev = 0;

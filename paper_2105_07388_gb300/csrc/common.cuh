@@ -32,6 +32,22 @@
 
 namespace re {
 
+// Lets `kern` take as much dynamic shared memory as the device allows beside its
+// static shared memory.  The limit is one fixed value per kernel, so host threads
+// that launch the same kernel with different sizes cannot lower it under one
+// another's launches; a launch still reserves only the size it requests.
+inline cudaError_t allow_dynamic_smem(const void* kern) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    int optin = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 constexpr uint32_t kStreamGX = 1;
 constexpr uint32_t kStreamGY = 2;
 constexpr uint32_t kStreamDX = 3;

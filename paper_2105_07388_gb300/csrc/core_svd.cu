@@ -1055,7 +1055,7 @@ size_t jac_cluster_smem(int CL, int s, int* b_out) {
 
 template <int CL>
 cudaError_t set_cluster_attrs(const void* kern, size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e == cudaSuccess && CL > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
@@ -1245,7 +1245,7 @@ cudaError_t launch_core_sigma_batched(const double* core, int r2, int s, int64_t
     if (sm > kSmemLimit || count <= 0) return cudaErrorInvalidValue;
     auto kern = cta_kernel_for((s + 63) / 64, (r2 + 31) / 32);
     if (!kern) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;
     // many small cores: 512 threads (8 panel + 8 trailing warps, 32 pair groups) fit
     // two CTAs in an SM's registers where 1024 fit one; every loop of the kernel
@@ -1270,7 +1270,7 @@ cudaError_t core_sigma_one(const double* core, int r2, int s, int64_t ld, void* 
         const size_t sm = cta_smem(r2, s);
         auto kern = cta_kernel_for((s + 63) / 64, (r2 + 31) / 32);
         if (!kern) return cudaErrorInvalidValue;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(kern));
         if (e != cudaSuccess) return e;
         kern<<<1, kCtaThreads, sm, st>>>(core, r2, s, ld, 0, sigma, 0, status, nullptr, cert_r1, cert_ratio, vout,
                                          vnorm, rel_only, diag_only);

@@ -86,10 +86,9 @@ cudaError_t launch_left_srtt_transform(const float* AX, int64_t ldax, int64_t M,
     const int nc = c1 - c0;
     const unsigned gy = (unsigned)((nc + kCW - 1) / kCW);
     const int smem_max = (int)(sizeof(float) * ((size_t)kCW << kMaxBits));   // 64 KB: above the default 48 KB
-    cudaError_t ea = cudaFuncSetAttribute(fwht_rows_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          smem_max);
+    cudaError_t ea = allow_dynamic_smem(reinterpret_cast<const void*>(fwht_rows_pass_kernel<true>));
     if (ea == cudaSuccess)
-        ea = cudaFuncSetAttribute(fwht_rows_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+        ea = allow_dynamic_smem(reinterpret_cast<const void*>(fwht_rows_pass_kernel<false>));
     if (ea != cudaSuccess) return ea;
     int lo = 0;
     bool first = true;

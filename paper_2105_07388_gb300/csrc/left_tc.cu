@@ -332,7 +332,7 @@ cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax
     const size_t a_stage = (kLBM * 32 * 4 + 1023) & ~1023;
     const size_t y_stage = ((size_t)pl.N * 128 + 1023) & ~(size_t)1023;
     const size_t smem = a_stage * kLAStages + y_stage * kLStages + 1024;
-    cudaError_t e = cudaFuncSetAttribute(left_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(left_tc_kernel));
     if (e != cudaSuccess) return e;
     const int64_t grid = (int64_t)pl.splits * pl.n_tiles * pl.m_tiles;
     if (grid > 0x7fffffff) return cudaErrorInvalidConfiguration;

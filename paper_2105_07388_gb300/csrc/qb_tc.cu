@@ -372,7 +372,7 @@ cudaError_t launch_qb_product_tc(const MatView& A, const uint16_t* Qt, int k, in
     p.zstride = (int64_t)kq * N;
     p.err = err_flag;
     const size_t smem = (size_t)kHalfBytes * kAStages + (size_t)3 * kTermBytes * kStages + 1024;
-    cudaError_t e = cudaFuncSetAttribute(qb_product_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(qb_product_tc_kernel));
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((N + kBM - 1) / kBM), (unsigned)used);
     qb_product_tc_kernel<<<grid, kThreads, smem, st>>>(amap, qmap, p);

@@ -738,11 +738,11 @@ cudaError_t launch_ex_sketch(const float* P, const float* P_lo, int64_t ldp, int
     const int64_t grid = std::min<int64_t>(p.tiles * p.kchunks, g_ex_sms);
     cudaError_t e;
     if (P_lo) {
-        e = cudaFuncSetAttribute(ex_sketch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dynamic_smem(reinterpret_cast<const void*>(ex_sketch_kernel<true>));
         if (e != cudaSuccess) return e;
         ex_sketch_kernel<true><<<(unsigned)grid, kThreads, smem, st>>>(pmap, pmap_lo, qmap, p);
     } else {
-        e = cudaFuncSetAttribute(ex_sketch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dynamic_smem(reinterpret_cast<const void*>(ex_sketch_kernel<false>));
         if (e != cudaSuccess) return e;
         ex_sketch_kernel<false><<<(unsigned)grid, kThreads, smem, st>>>(pmap, pmap_lo, qmap, p);
     }

@@ -264,7 +264,7 @@ cudaError_t launch_batched_t(const BatchDesc* d, int count, const int64_t* tile_
                              int col0, cudaStream_t st) {
     const size_t smem = sizeof(float) * (2 * kBK * (BM + 4) + 2 * kBK * BN);
     auto kern = right_simt_batched_kernel<BN, BM>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)items, kThreads, smem, st>>>(d, count, tile_prefix, active, Xpool, s, AXpool, ldax, col0);
     return cudaGetLastError();
@@ -289,7 +289,7 @@ cudaError_t launch_right_simt_t(const MatView& A, const float* X, int64_t ldx, i
                                 int64_t ldc, cudaStream_t st) {
     const size_t smem = sizeof(float) * (2 * kBK * (kBM + 4) + 2 * kBK * BN);
     auto kern = right_simt_kernel<BN, TRANS, TA>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(kern));
     if (e != cudaSuccess) return e;
     const int vec = ((reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0 && (A.ld & 3) == 0) ? 1 : 0;
     dim3 grid((unsigned)((s + BN - 1) / BN), (unsigned)((A.rows + kBM - 1) / kBM));

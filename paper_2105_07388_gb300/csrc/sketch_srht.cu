@@ -556,7 +556,7 @@ cudaError_t launch_vec(const MatView& A, const uint32_t* dbits, const int* cols,
     constexpr int T = 1 << (L - 5);
     const size_t smem = sizeof(float) * ((size_t)1 << L) + sizeof(int) * (size_t)s;
     auto k = srht_vec_kernel<L>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(k));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, smem);
@@ -579,7 +579,7 @@ cudaError_t launch_bulk(const MatView& A, const uint32_t* dbits, const int* cols
     const size_t smem = sizeof(float) * ((size_t)1 << L) +
                         (HASH ? sizeof(uint16_t) * ((size_t)1 << L) + sizeof(float) * T : sizeof(int) * (size_t)s);
     auto k = srht_bulk_kernel<L, HASH>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(k));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, smem);
@@ -600,7 +600,7 @@ cudaError_t launch_reg(const MatView& A, const uint32_t* dbits, const int* cols,
     const size_t smem = sizeof(float) * (size_t)G * PITCH + sizeof(uint32_t) * (NP / 32) +
                         sizeof(int) * (size_t)s;
     auto k = srht_reg_kernel<LOGN, TRANS, TA>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(k));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
@@ -645,7 +645,7 @@ cudaError_t launch_srht_t(const MatView& A, const uint32_t* dbits, const int* co
     if (need > 15) return cudaErrorNotSupported;
     const size_t smem = sizeof(float) << need;
     auto k = srht_smem_kernel<TRANS, TA>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(k));
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(A.rows, (int64_t)sm_count() * 1);
     k<<<(unsigned)grid, 1024, smem, st>>>(static_cast<const TA*>(A.ptr), A.ld, A.rows, A.cols, need,

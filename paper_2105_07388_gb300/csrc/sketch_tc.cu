@@ -376,7 +376,7 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
     p.drop_first = drop_first;
     const uint32_t b_bytes = (uint32_t)N * kBK * 2;
     const size_t smem = (size_t)kHalfBytes * kMaxAStages + ((b_bytes + 1023u) & ~1023u) * kStages + 1024;
-    cudaError_t e = cudaFuncSetAttribute(right_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(right_tc_kernel));
     if (e != cudaSuccess) return e;
     if (!g_sms) {
         int dev = 0;

@@ -337,6 +337,40 @@ def test_first_width_and_pipelined_host_path(precision):
     assert np.array_equal(s2, s3)  # the chunked path is deterministic
 
 
+def test_handles_on_concurrent_host_threads():
+    """Handles are independent: host threads, each with its own handle and
+    stream, estimating matrices of different shapes at the same time (so the
+    kernels' dynamic shared memory differs between concurrent launches) get
+    exactly the results of one thread running them in turn."""
+    import concurrent.futures as cf
+    shapes = [(4096, 1024, 60), (2048, 512, 30), (3000, 700, 45), (1024, 1024, 80)]
+    mats = []
+    for i, (m, n, r) in enumerate(shapes):
+        sig = wl.spectrum("step", n, rank=r, tail_scale=1e-9)
+        mats.append(wl.haar_matrix(m, n, sig, seed=20 + i).to(torch.float32).cuda())
+    opts = rk.make_opts(precision=rk.RE_PREC_BF16X3)
+
+    def run(j, reps):
+        hd = rk.re_create(0, opts)
+        st = torch.cuda.Stream()
+        out = []
+        try:
+            for _ in range(reps):
+                res, sg = rk.re_rank_estimate(hd, mats[j], 1e-5, rk.RE_GAUSSIAN, 7 + j, sigma_cap=256, stream=st)
+                out.append((res.rank, res.final_s, res.flags, sg.copy()))
+        finally:
+            rk.re_destroy(hd)
+        return out
+
+    ref = [run(j, 1)[0] for j in range(len(mats))]
+    with cf.ThreadPoolExecutor(max_workers=len(mats)) as ex:
+        got = list(ex.map(lambda j: run(j, 6), range(len(mats))))
+    for j, (m, n, r) in enumerate(shapes):
+        assert ref[j][0] == r
+        for res in got[j]:
+            assert res[:3] == ref[j][:3] and np.array_equal(res[3], ref[j][3])
+
+
 def test_first_width_option_errors():
     with pytest.raises(rk.RankEstError) as e:
         rk.re_create(0, rk.make_opts(first_width=12))
