@@ -9,7 +9,8 @@ densely so that each product is a plain matrix product a reader can check:
                                                        -> ``rng.gaussian_x`` / ``rng.srtt_x`` / ``rng.hrtt_x``
   step 3  form A X                                     -> ``A @ X``
   step 4  r2 = 2 r~1
-  step 5  draw Y (r2 x m): Gaussian or SRTT S H D      -> ``rng.gaussian_y`` / ``rng.srtt_y``
+  step 5  draw Y (r2 x m): Gaussian, SRTT S H D or S C D (C the DCT-II)
+                                                       -> ``rng.gaussian_y`` / ``rng.srtt_y`` / ``rng.srct_y``
   step 6  form Y (A X)                                 -> ``Y @ AX``
   step 7  the first r1 singular values                 -> LAPACK (numpy.linalg.svd), or the
           diagonal of R in Y A X = QR as their estimates (the alternative of Sec. 5's
@@ -60,6 +61,7 @@ from . import rng
 GAUSSIAN = 0
 SRHT = 1
 HRTT = 2
+SRCT = 3        # left embedding only: subsampled randomized DCT (Sec. 4, eta = 2)
 
 
 def round_half_away(num: int, den: int) -> int:
@@ -115,13 +117,19 @@ def right_sketch(A: np.ndarray, s: int, kind: int, seed: int, col0: int = 0) -> 
     return A64 @ X
 
 
-def left_sketch(AX: np.ndarray, r2: int, kind: int, seed: int, row0: int = 0) -> np.ndarray:
-    """Steps 5-6: Y (A X) for rows row0..row0+r2-1 of the unscaled embedding."""
+def left_sketch(AX: np.ndarray, r2: int, kind: int, seed: int, row0: int = 0, ykind: int | None = None) -> np.ndarray:
+    """Steps 5-6: Y (A X) for rows row0..row0+r2-1 of the unscaled embedding (Y of
+    kind `ykind`, by default the one drawn with right embedding `kind`)."""
     m = AX.shape[0]
-    if left_kind(kind) == GAUSSIAN:
+    yk = left_kind(kind) if ykind is None else ykind
+    if yk == GAUSSIAN:
         Y = rng.gaussian_y(r2, m, seed, row0)
-    else:
+    elif yk == SRHT:
         Y = rng.srtt_y(r2, m, seed, row0)
+    elif yk == SRCT:
+        Y = rng.srct_y(r2, m, seed, row0)
+    else:
+        raise ValueError(f"unknown left embedding {yk}")
     return Y @ AX
 
 
@@ -132,10 +140,10 @@ def sketch_scale(s: int, kind: int = GAUSSIAN, n: int = 0) -> float:
     return 1.0 / math.sqrt(float(s) * float(2 * s))
 
 
-def core(A: np.ndarray, s: int, kind: int, seed: int) -> np.ndarray:
+def core(A: np.ndarray, s: int, kind: int, seed: int, ykind: int | None = None) -> np.ndarray:
     """Unscaled 2s x s core Y A X of an already oriented (m >= n) matrix."""
     AX = right_sketch(A, s, kind, seed)
-    return left_sketch(AX, 2 * s, kind, seed)
+    return left_sketch(AX, 2 * s, kind, seed, ykind=ykind)
 
 
 def qr_diagonal_sigma(C: np.ndarray) -> np.ndarray:
@@ -149,10 +157,11 @@ def qr_diagonal_sigma(C: np.ndarray) -> np.ndarray:
     return np.sort(np.abs(np.diag(R)))[::-1]
 
 
-def sketched_sigma(A: np.ndarray, s: int, kind: int, seed: int, sigma: str = "svd") -> np.ndarray:
+def sketched_sigma(A: np.ndarray, s: int, kind: int, seed: int, sigma: str = "svd",
+                   ykind: int | None = None) -> np.ndarray:
     """Step 7: all s singular values of Y A X (or their QR-diagonal estimates),
     scaled (descending, FP64)."""
-    C = core(A, s, kind, seed)
+    C = core(A, s, kind, seed, ykind)
     sig = np.linalg.svd(C, compute_uv=False) if sigma == "svd" else qr_diagonal_sigma(C)
     return sig * sketch_scale(s, kind, np.shape(A)[1])
 
@@ -205,20 +214,22 @@ class Result:
     history: list = field(default_factory=list)   # (s, r1, rank or None) per step
 
 
-def ladder_limits(m: int, n: int, kind: int, s_max: int) -> int:
+def ladder_limits(m: int, n: int, kind: int, s_max: int, ykind: int | None = None) -> int:
     """Largest admissible sketch width for an oriented m x n matrix (m >= n)."""
     cap = s_max
+    yk = left_kind(kind) if ykind is None else ykind
     if kind == SRHT:
-        n_pad = 1 << rng.next_pow2_bits(n)
-        m_pad = 1 << rng.next_pow2_bits(m)
-        cap = min(cap, n_pad, m_pad // 2)
+        cap = min(cap, 1 << rng.next_pow2_bits(n))
+    if yk in (SRHT, SRCT):
+        cap = min(cap, (1 << rng.next_pow2_bits(m)) // 2)   # 2s sampled rows of the padded transform
     if kind == HRTT:
         cap = min(cap, 1 << rng.next_pow2_bits(n))      # no empty bucket
     return cap
 
 
 def rank_estimate(A: np.ndarray, eps: float, kind: int = GAUSSIAN, seed: int = 0,
-                  s0: int = 8, s_max: int = 512, norm_a: float | None = None, sigma: str = "svd") -> Result:
+                  s0: int = 8, s_max: int = 512, norm_a: float | None = None, sigma: str = "svd",
+                  ykind: int | None = None) -> Result:
     """Algorithm 1 with the doubling loop of step 8 (appending to X and Y).
 
     Each step recomputes the core from the plain definition Y[:2s] A X[:, :s];
@@ -239,7 +250,7 @@ def rank_estimate(A: np.ndarray, eps: float, kind: int = GAUSSIAN, seed: int = 0
     m, n = Ao.shape
     if m == 0 or n == 0:
         raise ValueError("empty matrix")
-    cap = ladder_limits(m, n, kind, s_max)
+    cap = ladder_limits(m, n, kind, s_max, ykind)
     if s0 > cap:
         raise ValueError("initial sketch width exceeds the admissible width")
     A64 = np.asarray(Ao, dtype=np.float64)
@@ -248,7 +259,7 @@ def rank_estimate(A: np.ndarray, eps: float, kind: int = GAUSSIAN, seed: int = 0
     passes = 0
     while True:
         passes += 1
-        sig_all = sketched_sigma(A64, s, kind, seed, sigma)
+        sig_all = sketched_sigma(A64, s, kind, seed, sigma, ykind)
         r1 = r1_of_s(s)
         sig = sig_all[:r1]
         ro = readoff(sig, eps, norm_a)

@@ -45,6 +45,8 @@ Stream identifiers: GX=1, GY=2, DX=3, PX=4, DY=5, PY=6, SX=7.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 STREAM_GX = 1
@@ -325,6 +327,30 @@ def srtt_y(r2: int, m: int, seed: int, row0: int = 0) -> np.ndarray:
     d = signs(m, STREAM_DY, seed)
     rows = feistel_perm(np.arange(row0, row0 + r2), b, STREAM_PY, seed)
     return hadamard_entries(rows, np.arange(m)) * d[None, :]
+
+
+def dct_entries(rows: np.ndarray, cols: np.ndarray, N: int) -> np.ndarray:
+    """sqrt(N) times the orthonormal DCT-II matrix of order N, rows k x columns i:
+    sqrt(2) w_k cos(pi (2 i + 1) k / (2 N)), w_0 = 1/sqrt(2), w_k = 1 otherwise.
+    The phase (2 i + 1) k is reduced modulo 4 N in integers before the cosine."""
+    k = np.asarray(rows, dtype=np.int64)[:, None]
+    i = np.asarray(cols, dtype=np.int64)[None, :]
+    ph = ((2 * i + 1) * k) % (4 * N)
+    v = math.sqrt(2.0) * np.cos(np.pi * ph.astype(np.float64) / (2.0 * N))
+    return np.where(k == 0, 1.0, v)
+
+
+def srct_y(r2: int, m: int, seed: int, row0: int = 0) -> np.ndarray:
+    """Unscaled subsampled randomized DCT left embedding, r2 x m (Eq. (Theta) with F
+    the orthonormal DCT-II, coherence eta = 2: the transform the paper's
+    experiments use for Y, Sec. 4 and Sec. 6).  As for the Hadamard form the order
+    is the zero-padded m_pad = 2^ceil(log2 m), row q samples frequency pi_Y(q)
+    (stream PY) and D holds the signs of stream DY; the entries are
+    sqrt(m_pad) F D, so Theta = Y / sqrt(r2)."""
+    b = next_pow2_bits(m)
+    d = signs(m, STREAM_DY, seed)
+    rows = feistel_perm(np.arange(row0, row0 + r2), b, STREAM_PY, seed)
+    return dct_entries(rows, np.arange(m), 1 << b) * d[None, :]
 
 
 def hrtt_x(n: int, s: int, seed: int, rows=None) -> np.ndarray:
