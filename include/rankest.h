@@ -68,6 +68,12 @@ extern "C" {
  * embedding only; its columns depend on the width, so it is not appendable and
  * every doubling step sketches anew; the left embedding defaults to Gaussian. */
 #define RE_HRTT 2
+/* Subsampled randomized DCT (Eq. (Theta) with F the orthonormal DCT-II, eta = 2;
+ * Sec. 4, the transform the paper's experiments use for Y): left embedding only
+ * (opts.y_kind), sqrt(m_pad/r2) S F D on the zero-padded m_pad = 2^ceil(log2 m),
+ * sampled frequencies pi_Y(q), signs D.  Its rows are generated on the fly from a
+ * cosine table (m_pad + 1 FP32 values) inside the CUDA-core left sketch. */
+#define RE_SRCT 3
 
 /* arithmetic of the Gaussian right sketch */
 #define RE_PREC_FP32 0   /* FP32 FMA on CUDA cores */
@@ -110,7 +116,8 @@ typedef struct {
     int s0;          /* initial X width, multiple of 8 (default 8) */
     int s_max;       /* largest X width, <= 512 (default 512) */
     int precision;   /* RE_PREC_* for the Gaussian right sketch (default RE_PREC_FP32) */
-    int y_kind;      /* left embedding kind; -1 = same as the right one (default -1) */
+    int y_kind;      /* left embedding kind: -1 = same as the right one (Gaussian for RE_HRTT;
+                        default), RE_GAUSSIAN, RE_SRHT or RE_SRCT */
     double norm_a;   /* > 0: use as ||A|| in the threshold; otherwise sigma^_1 (step 8) */
     int learned;     /* 1: let the sketch-size proposal network pick the next width (default 0) */
     /* Test hook for the failure path (default 0; no counterpart in the paper): when

@@ -54,6 +54,7 @@ struct re_handle_ {
     std::vector<cudaEvent_t> event_pool;
     DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status, ht, fz;
     DevBuf qbws, qbsel;                 // Algorithm 3: factorization workspace, selection record
+    DevBuf ctab;                        // cosine table of the SRCT left embedding
     // precision mode (exact-product sketches): row exponents of A, digit slices of X
     // and Y, int64 accumulators of the right and left sketches, A X as FP32 pair planes
     // (transposed) with column exponents, and the precise singular-value scratch
@@ -189,7 +190,7 @@ int make_plan(const void* A, int dtype, int64_t m, int64_t n, int64_t ld, int ki
     if (ld < n) return fail(RE_ERR_ARG, "ld < n");
     if (m > INT32_MAX || n > INT32_MAX) return fail(RE_ERR_ARG, "dimension too large");
     if (kind != RE_GAUSSIAN && kind != RE_SRHT && kind != RE_HRTT) return fail(RE_ERR_ARG, "unknown sketch kind");
-    if (ykind != RE_GAUSSIAN && ykind != RE_SRHT) return fail(RE_ERR_ARG, "unknown left sketch kind");
+    if (ykind != RE_GAUSSIAN && ykind != RE_SRHT && ykind != RE_SRCT) return fail(RE_ERR_ARG, "unknown left sketch kind");
     p->A.ptr = A;
     p->A.dtype = dtype;
     p->A.trans = m < n;
@@ -206,7 +207,7 @@ int make_plan(const void* A, int dtype, int64_t m, int64_t n, int64_t ld, int ki
         return fail(RE_ERR_UNSUPPORTED, "right Hadamard transforms of more than 2^15 points are not built");
     int64_t cap = s_max;
     if (kind == RE_SRHT || kind == RE_HRTT) cap = std::min<int64_t>(cap, p->n_pad);   // HRTT: no empty bucket
-    if (ykind == RE_SRHT) cap = std::min<int64_t>(cap, p->m_pad / 2);
+    if (ykind == RE_SRHT || ykind == RE_SRCT) cap = std::min<int64_t>(cap, p->m_pad / 2);
     p->cap = (int)cap;
     return RE_OK;
 }
@@ -476,6 +477,34 @@ int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const
         if (e != cudaSuccess) return cuda_fail(e, "left sketch (SRTT)");
         stage_end(h, st, a, kStageLeft);
         h->stats.launches += 2 + (P.mbits + 9) / 10 + (c0 > 0 ? 2 : 1);
+        return RE_OK;
+    }
+    if (P.ykind == RE_SRCT) {
+        // DCT rows generated inside the CUDA-core left kernel from the sampled
+        // frequencies, the signs and a cosine table of the padded order
+        if (int r = ensure(h->dy, sizeof(uint32_t) * (size_t)(P.m_pad / 32 + 1))) return r;
+        if (int r = ensure(h->py, sizeof(int) * (size_t)(2 * c1))) return r;
+        if (int r = ensure(h->ctab, sizeof(float) * (size_t)(P.m_pad + 1))) return r;
+        const size_t needc = std::max(re::left_part_floats(M, 2 * (c1 - c0), c0), re::left_part_floats(M, 2 * c1, c1 - c0));
+        if (int r = ensure(h->part, sizeof(float) * needc)) return r;
+        cudaEvent_t g = stage_begin(h, st);
+        cudaError_t e = re::launch_sign_bits(seed, re::kStreamDY, M, static_cast<uint32_t*>(h->dy.p), st);
+        if (e == cudaSuccess)
+            e = re::launch_perm(seed, re::kStreamPY, P.mbits, 0, 2 * c1, static_cast<int*>(h->py.p), st);
+        if (e == cudaSuccess) e = re::launch_cos_table(P.mbits, static_cast<float*>(h->ctab.p), st);
+        if (e != cudaSuccess) return cuda_fail(e, "left embedding");
+        stage_end(h, st, g, kStageOther);
+        re::DctRows Yd{static_cast<const int*>(h->py.p), static_cast<const uint32_t*>(h->dy.p),
+                       static_cast<const float*>(h->ctab.p), P.mbits};
+        cudaEvent_t a = stage_begin(h, st);
+        float* part = static_cast<float*>(h->part.p);
+        const size_t cap = h->part.cap / sizeof(float);
+        if (c0 > 0) e = re::launch_left_dct(Yd, AX, ld_ax, M, 2 * c0, 2 * (c1 - c0), 0, c0, part, cap, core, ld_core, st);
+        if (e == cudaSuccess)
+            e = re::launch_left_dct(Yd, AX, ld_ax, M, 0, 2 * c1, c0, c1 - c0, part, cap, core, ld_core, st);
+        if (e != cudaSuccess) return cuda_fail(e, "left sketch (SRCT)");
+        stage_end(h, st, a, kStageLeft);
+        h->stats.launches += 3 + (c0 > 0 ? 4 : 2);
         return RE_OK;
     }
     const size_t need = std::max({re::left_part_floats(M, 2 * (c1 - c0), c0),
@@ -825,7 +854,7 @@ int check_opts(const re_opts* o) {
     if (o->s_max > 512) return fail(RE_ERR_ARG, "s_max above 512");
     if (o->precision != RE_PREC_FP32 && o->precision != RE_PREC_BF16X3 && o->precision != RE_PREC_EXACT)
         return fail(RE_ERR_ARG, "unknown precision");
-    if (o->y_kind < -1 || o->y_kind > RE_SRHT) return fail(RE_ERR_ARG, "unknown y_kind");
+    if (o->y_kind < -1 || o->y_kind == RE_HRTT || o->y_kind > RE_SRCT) return fail(RE_ERR_ARG, "unknown y_kind");
     if (o->learned != 0 && o->learned != 1) return fail(RE_ERR_ARG, "learned must be 0 or 1");
     if (o->test_drop_load != 0 && o->test_drop_load != 1) return fail(RE_ERR_ARG, "test_drop_load must be 0 or 1");
     if (o->sigma_est != RE_SIGMA_SVD && o->sigma_est != RE_SIGMA_QRDIAG) return fail(RE_ERR_ARG, "unknown sigma_est");
@@ -891,7 +920,7 @@ int re_destroy(re_handle h) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&h->x, &h->xt, &h->ax, &h->part, &h->core, &h->sigma, &h->sigma_scaled,
                       &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status, &h->ht, &h->fz,
-                      &h->qbws, &h->qbsel,
+                      &h->qbws, &h->qbsel, &h->ctab,
                       &h->ex_rexp, &h->ex_xd, &h->ex_tr, &h->ex_hi, &h->ex_lo, &h->ex_cexp, &h->ex_yd, &h->ex_tc,
                       &h->ex_svd,
                       &h->mlp_P, &h->mlp_M, &h->mlp_V, &h->mlp_G, &h->mlp_X, &h->mlp_y,

@@ -4,6 +4,8 @@
 // step into a small buffer (n x s, L2-resident) that the right-sketch kernels
 // stream; the left embedding Y is generated inside the left-sketch kernel and
 // is only written out here for re_embedding_y.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -204,6 +206,22 @@ cudaError_t launch_srtt_y_dense(int64_t m, int r2, const uint32_t* dbits, const 
                                 int64_t ldy, cudaStream_t st) {
     if (m <= 0 || r2 <= 0) return cudaSuccess;
     srtt_y_dense_kernel<<<blocks_for(m * r2, 256), 256, 0, st>>>(m, r2, dbits, rows, Y, ldy);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void cos_table_kernel(int nbits, float* __restrict__ ctab) {
+    const int64_t N = int64_t(1) << nbits;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= N; j += (int64_t)gridDim.x * blockDim.x)
+        ctab[j] = (float)cospi((double)j / (double)(2 * N));   // j / 2N is exact in FP64
+}
+}  // namespace
+
+cudaError_t launch_cos_table(int nbits, float* ctab, cudaStream_t st) {
+    if (nbits < 0 || nbits > 31) return cudaErrorInvalidValue;
+    const int64_t N = int64_t(1) << nbits;
+    const int blocks = (int)std::min<int64_t>((N + 256) / 256, 4096);
+    cos_table_kernel<<<blocks, 256, 0, st>>>(nbits, ctab);
     return cudaGetLastError();
 }
 

@@ -83,6 +83,21 @@ cudaError_t launch_left(uint64_t seed, const float* AX, int64_t ldax, int64_t M,
                         float* part, size_t part_cap, double* core, int64_t ld_core, cudaStream_t st,
                         int* err_flag = nullptr);
 size_t left_part_floats(int64_t M, int R, int S);
+// Rows of the unscaled SRCT left embedding: Y[q][i] = sqrt(2) w_k cos(pi (2i+1) k / (2N)) d_i
+// with k = krow[q], N = 2^nbits (w_0 = 1/sqrt(2), else 1), d_i from the sign bits (bit
+// set = -1) and cos(pi j / (2N)) = ctab[j] for j in [0, N].
+struct DctRows {
+    const int* krow;
+    const uint32_t* dbits;
+    const float* ctab;
+    int nbits;
+};
+// ctab[j] = cos(pi j / 2^(nbits+1)) for j in [0, 2^nbits] (FP32 from FP64 cospi).
+cudaError_t launch_cos_table(int nbits, float* ctab, cudaStream_t st);
+// core[row0+r][col0+c] (FP64) = sum_i Y[row0+r][i] AX[i][col0+c], Y the SRCT rows
+// above, on CUDA cores (FP32 split-K partials in `part`, summed as for launch_left).
+cudaError_t launch_left_dct(const DctRows& Y, const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0,
+                            int S, float* part, size_t part_cap, double* core, int64_t ld_core, cudaStream_t st);
 
 // ---- left sketch with the SRTT Y by fast transforms (left_fwht.cu) ------------
 // Z[i][c] = (H D AX)[i][c] for c in [c0, c1) and i < 2^mbits (Z row-major, ldz >= c1,

@@ -310,16 +310,30 @@ cudaError_t dispatch_right(const MatView& A, const float* X, int64_t ldx, int s,
 }
 
 // ---------------------------------------------------------------------------
-// Left sketch (Gaussian Y): part[split][r][c] = sum over the split's rows i of
-// Y[row0+r][i] AX[i][col0+c].
+// Left sketch: part[split][r][c] = sum over the split's rows i of
+// Y[row0+r][i] AX[i][col0+c], Y Gaussian (normals of stream GY) or, with DCT,
+// the SRCT rows of Yd generated from the cosine table.
 constexpr int kLR = 64;     // rows of Y per tile
 constexpr int kLK = 32;     // i per k step
 
-template <int LC>
+// Entry (q, i) of the unscaled SRCT left embedding (see DctRows): the phase
+// (2i+1) k is reduced modulo 4N in integers, then folded onto [0, N] by the
+// symmetries cos(2 pi - x) = cos x and cos(pi - x) = -cos x.
+__device__ __forceinline__ float dct_entry(const DctRows& Y, int q, int64_t i, float d) {
+    const int k = __ldg(Y.krow + q);
+    if (k == 0) return d;
+    const unsigned long long N = 1ull << Y.nbits;
+    unsigned long long ph = ((2ull * (unsigned long long)i + 1ull) * (unsigned long long)k) & (4ull * N - 1ull);
+    if (ph > 2ull * N) ph = 4ull * N - ph;
+    const float c = ph <= N ? __ldg(Y.ctab + ph) : -__ldg(Y.ctab + (2ull * N - ph));
+    return 1.41421356237309515f * c * d;
+}
+
+template <int LC, bool DCT>
 __global__ void __launch_bounds__(256) left_kernel(uint64_t seed, const float* __restrict__ AX,
                                                    int64_t ldax, int64_t M, int row0, int R,
                                                    int col0, int S, int64_t chunk,
-                                                   float* __restrict__ part) {
+                                                   float* __restrict__ part, const DctRows Yd) {
     constexpr int TC = LC / 16;           // columns per thread
     __shared__ __align__(16) float Ys[kLK][kLR];
     __shared__ __align__(16) float Xs[kLK][LC];
@@ -344,8 +358,19 @@ __global__ void __launch_bounds__(256) left_kernel(uint64_t seed, const float* _
             const int g = (tid >> 5) + 8 * h;            // 16 groups of 4 rows
             const int64_t i = i0 + k;
             float z[4] = {0.f, 0.f, 0.f, 0.f};
-            if (i < i_end && qbase + 4 * g - row0 < R)
-                normals4((uint32_t)i, (uint32_t)((qbase >> 2) + g), kStreamGY, seed, z);
+            if constexpr (DCT) {
+                if (i < i_end) {
+                    const float d = ((__ldg(Yd.dbits + (i >> 5)) >> (i & 31)) & 1u) ? -1.f : 1.f;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int q = qbase + 4 * g + a;
+                        if (q - row0 < R) z[a] = dct_entry(Yd, q, i, d);
+                    }
+                }
+            } else {
+                if (i < i_end && qbase + 4 * g - row0 < R)
+                    normals4((uint32_t)i, (uint32_t)((qbase >> 2) + g), kStreamGY, seed, z);
+            }
             *reinterpret_cast<float4*>(&Ys[k][4 * g]) = make_float4(z[0], z[1], z[2], z[3]);
         }
         // ---- AX tile: Xs[k][c] = AX[i0 + k][col0 + ct*LC + c]
@@ -490,15 +515,36 @@ cudaError_t launch_left(uint64_t seed, const float* AX, int64_t ldax, int64_t M,
     const bool wide = S >= 128;
     dim3 grid((unsigned)((S + (wide ? 127 : 63)) / (wide ? 128 : 64)), (unsigned)((R + kLR - 1) / kLR),
               (unsigned)splits);
+    const DctRows none{nullptr, nullptr, nullptr, 0};
     if (wide)
-        left_kernel<128><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, part);
+        left_kernel<128, false><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, part, none);
     else
-        left_kernel<64><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, part);
+        left_kernel<64, false><<<grid, 256, 0, st>>>(seed, AX, ldax, M, row0, R, col0, S, chunk, part, none);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)R * S;
     left_reduce_kernel<<<(unsigned)((total + 31) / 32), 256, 0, st>>>(part, splits, R, S, row0, col0,
                                                                              core, ld_core);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_left_dct(const DctRows& Y, const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0,
+                            int S, float* part, size_t part_cap, double* core, int64_t ld_core, cudaStream_t st) {
+    if (R <= 0 || S <= 0) return cudaSuccess;
+    int64_t chunk;
+    const int splits = left_splits(M, R, S, &chunk);
+    if ((size_t)splits * R * S > part_cap) return cudaErrorInvalidValue;
+    const bool wide = S >= 128;
+    dim3 grid((unsigned)((S + (wide ? 127 : 63)) / (wide ? 128 : 64)), (unsigned)((R + kLR - 1) / kLR),
+              (unsigned)splits);
+    if (wide)
+        left_kernel<128, true><<<grid, 256, 0, st>>>(0, AX, ldax, M, row0, R, col0, S, chunk, part, Y);
+    else
+        left_kernel<64, true><<<grid, 256, 0, st>>>(0, AX, ldax, M, row0, R, col0, S, chunk, part, Y);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)R * S;
+    left_reduce_kernel<<<(unsigned)((total + 31) / 32), 256, 0, st>>>(part, splits, R, S, row0, col0, core, ld_core);
     return cudaGetLastError();
 }
 

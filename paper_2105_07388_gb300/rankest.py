@@ -28,6 +28,7 @@ RE_F64 = 1
 RE_GAUSSIAN = 0
 RE_SRHT = 1
 RE_HRTT = 2
+RE_SRCT = 3
 RE_PREC_FP32 = 0
 RE_PREC_BF16X3 = 1
 RE_PREC_EXACT = 2

@@ -200,6 +200,58 @@ def test_core_blocks_parity(h, m, n, c0, c1):
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
 
 
+@pytest.mark.parametrize("m,n,steps", [
+    (3001, 700, ((0, 16), (16, 16), (32, 32))),   # m_pad 4096: appended columns and rows
+    (70000, 40, ((0, 8), (8, 24))),               # m_pad 2^17: phases reduced modulo 2^19
+])
+def test_srct_left_parity(m, n, steps):
+    """The SRCT left embedding (DCT-II rows generated from the cosine table):
+    the whole core against the oracle's dense S F D (A X) on the GPU's own A X
+    after each appending step."""
+    A = np.random.default_rng(m + n).standard_normal((m, n)).astype(np.float32)
+    Ad = dev(A)
+    c1 = steps[-1][0] + steps[-1][1]
+    AX = torch.zeros(m, c1, dtype=torch.float32, device="cuda")
+    core = torch.zeros(2 * c1, c1, dtype=torch.float64, device="cuda")
+    hd = rk.re_create(0, rk.make_opts(y_kind=rk.RE_SRCT))
+    try:
+        for col0, s in steps:
+            rk.re_sketch_apply(hd, Ad, col0, s, rk.RE_GAUSSIAN, 41, AX, core)
+            w = col0 + s
+            AXg = AX[:, :w].double().cpu().numpy()
+            Y = rng.srct_y(2 * w, m, 41)
+            ref = Y @ AXg
+            # FP32 entries of Y (table values rounded once) and FP32 split-K sums,
+            # bounded as the Gaussian core blocks are
+            bound = 4.0 * (m / 32 + 64) * U32 * (np.abs(Y) @ np.abs(AXg)) + 1e-30
+            got = core[:2 * w, :w].cpu().numpy()
+            assert np.all(np.abs(got - ref) <= bound), (col0, s, float(np.max(np.abs(got - ref) / bound)))
+    finally:
+        rk.re_destroy(hd)
+
+
+@pytest.mark.parametrize("precision", [rk.RE_PREC_FP32, rk.RE_PREC_BF16X3])
+def test_srct_left_rank_estimate(precision):
+    """Gaussian X with the SRCT Y (the paper's experimental pairing for the rank
+    estimate, Sec. 6.1): the oracle's rank, width and sketched values on a gap."""
+    sig = wl.spectrum("step", 700, rank=45, tail_scale=1e-9)
+    A = wl.haar_matrix(2500, 700, sig, seed=13).numpy().astype(np.float32)
+    hd = rk.re_create(0, rk.make_opts(precision=precision, y_kind=rk.RE_SRCT))
+    try:
+        res, sg = rk.re_rank_estimate(hd, dev(A), 1e-5, rk.RE_GAUSSIAN, 19, sigma_cap=512)
+    finally:
+        rk.re_destroy(hd)
+    orc = alg.rank_estimate(A.astype(np.float64), 1e-5, kind=alg.GAUSSIAN, seed=19, ykind=alg.SRCT)
+    assert orc.converged and (res.rank, res.final_s) == (orc.rank, orc.final_s) == (45, 64)
+    assert np.max(np.abs(sg[:res.n_sigma] - orc.sigma)) <= 1e-4 * orc.sigma[0]
+
+
+def test_srct_y_kind_errors():
+    with pytest.raises(rk.RankEstError) as e:
+        rk.re_create(0, rk.make_opts(y_kind=rk.RE_HRTT))
+    assert e.value.code == rk.RE_ERR_ARG
+
+
 def test_core_sigma_against_lapack(h):
     for (r2, s, seed) in ((16, 8, 0), (128, 64, 1), (256, 128, 2), (512, 256, 3), (37, 29, 4),
                           (1024, 512, 5), (600, 300, 6), (1000, 70, 7)):
