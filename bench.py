@@ -439,11 +439,15 @@ def main():
         # alias and the estimate may fall short of the true rank (reported, not
         # compared).  HRTT: hashed outputs, the whole width anew at every step,
         # Gaussian Y; hashing keeps the embedding on coherent inputs.
-        for name, code in (("srht", rk.RE_SRHT), ("hrtt", rk.RE_HRTT), ("srct_y", rk.RE_GAUSSIAN)):
-            # srct_y: the BF16x3 Gaussian right sketch with the DCT left embedding, the
-            # paper's pairing for the rank estimate
-            hs = rk.re_create(local, rk.make_opts(precision=rk.RE_PREC_FP32) if code != rk.RE_GAUSSIAN else
-                              rk.make_opts(precision=rk.RE_PREC_BF16X3, y_kind=rk.RE_SRCT))
+        # srht / hrtt: the register transforms (FP32 precision); srht_tc: the SRHT's +-1
+        # columns through the BF16x3 tensor-core contraction; srct_y: the BF16x3 Gaussian
+        # right sketch with the DCT left embedding, the paper's pairing for the estimate
+        variants = (("srht", rk.RE_SRHT, rk.make_opts(precision=rk.RE_PREC_FP32)),
+                    ("srht_tc", rk.RE_SRHT, rk.make_opts(precision=rk.RE_PREC_BF16X3)),
+                    ("hrtt", rk.RE_HRTT, rk.make_opts(precision=rk.RE_PREC_FP32)),
+                    ("srct_y", rk.RE_GAUSSIAN, rk.make_opts(precision=rk.RE_PREC_BF16X3, y_kind=rk.RE_SRCT)))
+        for name, code, opts_v in variants:
+            hs = rk.re_create(local, opts_v)
             rs, _ = rk.re_rank_estimate(hs, A, w["eps"], code, w["sketch_seed"], stream=stream)
             torch.cuda.synchronize()
             rk.re_stats_enable(hs, True)

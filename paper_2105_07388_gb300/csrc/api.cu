@@ -427,6 +427,42 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
     // SRHT: signs of the padded n and sampled columns pi_X(c0 .. c0+cnt-1)
     if (int r = ensure(h->dx, sizeof(uint32_t) * (size_t)(P.n_pad / 32 + 1))) return r;
     if (int r = ensure(h->px, sizeof(int) * (size_t)cnt)) return r;
+    const bool tc = h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && (ld_ax % 4) == 0 &&
+                    (reinterpret_cast<uintptr_t>(AX + c0) & 15) == 0;
+    if (tc && cnt > 256) {
+        for (int c = 0; c < cnt; c += 256)
+            if (int r = right_columns(h, P, seed, c0 + c, std::min(256, cnt - c), AX, ld_ax, st)) return r;
+        return RE_OK;
+    }
+    if (tc) {
+        // X = D H S^T has +-1 entries, exact in BF16: the sampled columns go through the
+        // tensor-core contraction of the Gaussian sketch (A in three BF16 terms, exact
+        // products, FP32 accumulation) instead of the register transform
+        const int64_t kpad = (P.A.cols + 63) / 64 * 64;
+        const int nrows = re::tc_mma_n(cnt);
+        if (int r = ensure(h->xt, sizeof(uint16_t) * (size_t)kpad * nrows)) return r;
+        if (int r = ensure(h->status, 64)) return r;
+        cudaEvent_t g = stage_begin(h, st);
+        e = re::launch_sign_bits(seed, re::kStreamDX, P.A.cols, static_cast<uint32_t*>(h->dx.p), st);
+        if (e == cudaSuccess) e = re::launch_perm(seed, re::kStreamPX, P.nbits, c0, cnt, static_cast<int*>(h->px.p), st);
+        if (e == cudaSuccess && nrows > cnt)
+            e = cudaMemsetAsync(static_cast<uint16_t*>(h->xt.p) + (size_t)kpad * cnt, 0,
+                                sizeof(uint16_t) * (size_t)kpad * (nrows - cnt), st);
+        if (e == cudaSuccess)
+            e = re::launch_srht_xt_bf16(P.A.cols, kpad, static_cast<const int*>(h->px.p),
+                                        static_cast<const uint32_t*>(h->dx.p), cnt, static_cast<uint16_t*>(h->xt.p),
+                                        kpad, st);
+        if (e != cudaSuccess) return cuda_fail(e, "generate X (SRHT)");
+        stage_end(h, st, g, kStageOther);
+        cudaEvent_t a = stage_begin(h, st);
+        int nl = 0;
+        e = re::launch_right_tc(P.A, static_cast<const uint16_t*>(h->xt.p), kpad, cnt, AX + c0, ld_ax,
+                                static_cast<int*>(h->status.p) + 1, st, &nl, h->opts.test_drop_load);
+        if (e != cudaSuccess) return cuda_fail(e, "right sketch (SRHT, tensor cores)");
+        stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 2), 3.0 * 2.0 * P.A.rows * P.A.cols * cnt);
+        h->stats.launches += 3 + nl;
+        return RE_OK;
+    }
     cudaEvent_t g = stage_begin(h, st);
     e = re::launch_sign_bits(seed, re::kStreamDX, P.A.cols, static_cast<uint32_t*>(h->dx.p), st);
     if (e == cudaSuccess)

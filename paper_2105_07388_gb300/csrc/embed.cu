@@ -46,6 +46,24 @@ __global__ void gauss_xt_bf16_kernel(uint64_t seed, int64_t n, int64_t n_alloc, 
     }
 }
 
+// Xt[j][k] (BF16 bits) = d_k H[k][cols[j]] for k < n, 0 for n <= k < n_alloc: the
+// SRTT right embedding's sampled columns, +-1 and exact in BF16.
+__global__ void srht_xt_bf16_kernel(int64_t n, int64_t n_alloc, const int* __restrict__ cols,
+                                    const uint32_t* __restrict__ dbits, int s, uint16_t* __restrict__ Xt,
+                                    int64_t ldt) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_alloc * s) return;
+    const int64_t k = idx % n_alloc;
+    const int j = (int)(idx / n_alloc);
+    uint16_t v = 0;
+    if (k < n) {
+        const uint32_t neg = ((dbits[k >> 5] >> (k & 31)) ^ (uint32_t)__popcll((unsigned long long)k &
+                                                                              (unsigned long long)cols[j])) & 1u;
+        v = neg ? (uint16_t)0xBF80u : (uint16_t)0x3F80u;      // -1 / +1
+    }
+    Xt[(int64_t)j * ldt + k] = v;
+}
+
 __global__ void gauss_y_kernel(uint64_t seed, int64_t m, int g0, int ng, int row0, int r2, float* Y,
                                int64_t ldy) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -155,6 +173,13 @@ cudaError_t launch_gauss_xt_bf16(uint64_t seed, int64_t n, int64_t n_alloc, int 
     const int g0 = col0 / 4, g1 = (col0 + s + 3) / 4, ng = g1 - g0;
     gauss_xt_bf16_kernel<<<blocks_for(n_alloc * ng, 256), 256, 0, st>>>(seed, n, n_alloc, g0, ng,
                                                                          col0, s, Xt, ldt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_srht_xt_bf16(int64_t n, int64_t n_alloc, const int* cols, const uint32_t* dbits, int s,
+                                uint16_t* Xt, int64_t ldt, cudaStream_t st) {
+    if (n_alloc <= 0 || s <= 0) return cudaSuccess;
+    srht_xt_bf16_kernel<<<blocks_for(n_alloc * s, 256), 256, 0, st>>>(n, n_alloc, cols, dbits, s, Xt, ldt);
     return cudaGetLastError();
 }
 

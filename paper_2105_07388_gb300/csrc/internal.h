@@ -48,6 +48,10 @@ cudaError_t launch_gauss_x(uint64_t seed, int64_t n, int col0, int s, float* X, 
 // X columns [col0, col0+s) as BF16 bits, column-major (s rows of n): Xt[j*ldt + k].
 cudaError_t launch_gauss_xt_bf16(uint64_t seed, int64_t n, int64_t n_alloc, int col0, int s,
                                  uint16_t* Xt, int64_t ldt, cudaStream_t st);
+// SRTT right embedding columns as BF16 bits: Xt[j][k] = d_k H[k][cols[j]] (+-1) for
+// k < n, zero up to n_alloc; j < s; d from the sign bits (bit set = -1).
+cudaError_t launch_srht_xt_bf16(int64_t n, int64_t n_alloc, const int* cols, const uint32_t* dbits, int s,
+                                uint16_t* Xt, int64_t ldt, cudaStream_t st);
 // Y rows [row0, row0+r2) as FP32, row-major r2 x ldy.
 cudaError_t launch_gauss_y(uint64_t seed, int64_t m, int row0, int r2, float* Y, int64_t ldy,
                            cudaStream_t st);

@@ -118,3 +118,45 @@ def test_tc_bounded_wait_expires_and_context_survives():
     finally:
         rk.re_destroy(h)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("m,n,col0,s", [
+    (300, 100, 0, 8),        # ragged M and K, n_pad 128
+    (1000, 777, 16, 48),     # appended columns
+    (2049, 1030, 0, 128),
+    (513, 300, 8, 256),      # N = 256
+    (20400, 1000, 8, 128),   # shared tiles
+])
+def test_tc_srht_right_sketch_parity(htc, m, n, col0, s):
+    """With BF16x3 precision the SRHT's sampled columns (X = D H S^T, +-1 entries,
+    exact in BF16) go through the tensor-core contraction: the oracle's dense
+    S H D product within the FP32 accumulation bound."""
+    A = np.random.default_rng(m + n + s + 1).standard_normal((m, n)).astype(np.float32)
+    Ad = torch.from_numpy(A).cuda()
+    AX = torch.zeros(m, col0 + s, dtype=torch.float32, device="cuda")
+    rk.re_sketch_apply(htc, Ad, col0, s, rk.RE_SRHT, 99, AX)
+    A64 = A.astype(np.float64)
+    ref = alg.right_sketch(A64, s, alg.SRHT, 99, col0)
+    X = alg.embeddings(alg.SRHT, n, m, s, 99, col0=col0, r2=0)[0]
+    bound = 2.0 * (n / 16 + 32) * U32 * (np.abs(A64) @ np.abs(X)) + 1e-35
+    err = np.abs(AX[:, col0:].double().cpu().numpy() - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
+def test_tc_srht_rank_matches_transform_path(htc):
+    """The tensor-core SRHT and the register-transform SRHT compute the same sketch
+    up to FP32 rounding: same rank, width and passes on a clear gap, sigma within
+    the small-core SVD's accuracy; both equal to the oracle's rank."""
+    sig = wl.spectrum("step", 1500, rank=70, tail_scale=1e-9)
+    A = wl.haar_matrix(4000, 1500, sig, seed=31).to(torch.float32)
+    Ad = A.cuda()
+    r_tc, s_tc = rk.re_rank_estimate(htc, Ad, 1e-5, rk.RE_SRHT, 8)
+    h32 = rk.re_create(0)
+    try:
+        r_fw, s_fw = rk.re_rank_estimate(h32, Ad, 1e-5, rk.RE_SRHT, 8)
+    finally:
+        rk.re_destroy(h32)
+    orc = alg.rank_estimate(A.double().numpy(), 1e-5, kind=alg.SRHT, seed=8)
+    assert (r_tc.rank, r_tc.final_s, r_tc.passes) == (r_fw.rank, r_fw.final_s, r_fw.passes) == \
+        (orc.rank, orc.final_s, orc.passes)
+    assert np.max(np.abs(s_tc[:r_tc.n_sigma] - s_fw[:r_fw.n_sigma])) <= 3e-5 * s_fw[0]
