@@ -440,11 +440,14 @@ def main():
         # compared).  HRTT: hashed outputs, the whole width anew at every step,
         # Gaussian Y; hashing keeps the embedding on coherent inputs.
         # srht / hrtt: the register transforms (FP32 precision); srht_tc: the SRHT's +-1
-        # columns through the BF16x3 tensor-core contraction; srct_y: the BF16x3 Gaussian
+        # columns through the BF16x3 tensor-core contraction; hrtt_tc: the same for the
+        # HRTT widths whose buckets hold at most 256 coordinates (the register transform
+        # for the narrower ones); srct_y: the BF16x3 Gaussian
         # right sketch with the DCT left embedding, the paper's pairing for the estimate
         variants = (("srht", rk.RE_SRHT, rk.make_opts(precision=rk.RE_PREC_FP32)),
                     ("srht_tc", rk.RE_SRHT, rk.make_opts(precision=rk.RE_PREC_BF16X3)),
                     ("hrtt", rk.RE_HRTT, rk.make_opts(precision=rk.RE_PREC_FP32)),
+                    ("hrtt_tc", rk.RE_HRTT, rk.make_opts(precision=rk.RE_PREC_BF16X3)),
                     ("srct_y", rk.RE_GAUSSIAN, rk.make_opts(precision=rk.RE_PREC_BF16X3, y_kind=rk.RE_SRCT)))
         for name, code, opts_v in variants:
             hs = rk.re_create(local, opts_v)

@@ -220,6 +220,53 @@ cudaError_t launch_hrtt_table(uint64_t seed, int bits, uint16_t* tbl, cudaStream
     return cudaGetLastError();
 }
 
+// Rows j0 .. j0 + gridDim.x - 1 of the HRTT's X^T as BF16 bits: row j (over k < n,
+// zero up to kpad) = d_k (H v_j)[k], v_j the signed indicator of bucket j (entries
+// q = j + t s of the table).  One CTA per bucket: v_j scattered into shared memory
+// (2^bits floats) and transformed in place by the unnormalised Walsh-Hadamard
+// butterflies; the results are integers of magnitude at most the bucket size,
+// exact in BF16 when that is at most 256.
+__global__ void __launch_bounds__(1024) hrtt_xt_bf16_kernel(int64_t n, int64_t kpad, int s, int j0, int bits,
+                                                            const uint32_t* __restrict__ dbits,
+                                                            const uint16_t* __restrict__ tbl,
+                                                            uint16_t* __restrict__ Xt, int64_t ldt) {
+    extern __shared__ float y[];
+    const int N = 1 << bits, j = j0 + (int)blockIdx.x;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) y[i] = 0.f;
+    __syncthreads();
+    for (int q = j + (int)threadIdx.x * s; q < N; q += (int)blockDim.x * s) {
+        const uint32_t e = tbl[q];
+        y[e & 0x7fffu] = (e >> 15) ? -1.f : 1.f;       // distinct coordinates: the table is a bijection
+    }
+    __syncthreads();
+    for (int h = 1; h < N; h <<= 1) {
+        for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+            const int i = (t / h) * 2 * h + (t % h);
+            const float a = y[i], b = y[i + h];
+            y[i] = a + b;
+            y[i + h] = a - b;
+        }
+        __syncthreads();
+    }
+    uint16_t* row = Xt + (int64_t)blockIdx.x * ldt;
+    for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x) {
+        float v = 0.f;
+        if (k < n) v = ((dbits[k >> 5] >> (k & 31)) & 1u) ? -y[k] : y[k];
+        row[k] = (uint16_t)(__float_as_uint(v) >> 16);
+    }
+}
+
+cudaError_t launch_hrtt_xt_bf16(int64_t n, int64_t kpad, int s, int j0, int cnt, int bits, const uint32_t* dbits,
+                                const uint16_t* tbl, uint16_t* Xt, int64_t ldt, cudaStream_t st) {
+    if (cnt <= 0) return cudaSuccess;
+    if (bits < 0 || bits > 15 || s <= 0 || j0 < 0 || j0 + cnt > s) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float) << bits;
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(hrtt_xt_bf16_kernel));
+    if (e != cudaSuccess) return e;
+    hrtt_xt_bf16_kernel<<<cnt, 1024, smem, st>>>(n, kpad, s, j0, bits, dbits, tbl, Xt, ldt);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hrtt_x_dense(int64_t n, int s, int bits, const uint32_t* dbits, const uint16_t* tbl,
                                 float* X, int64_t ldx, cudaStream_t st) {
     if (n <= 0 || s <= 0) return cudaSuccess;

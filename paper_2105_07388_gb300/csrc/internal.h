@@ -68,6 +68,11 @@ cudaError_t launch_srtt_y_dense(int64_t m, int r2, const uint32_t* dbits, const 
                                 int64_t ldy, cudaStream_t st);
 // HRTT hashing table of 2^bits entries (bits <= 15): entry q = pi_X(q) | (sigma < 0) << 15.
 cudaError_t launch_hrtt_table(uint64_t seed, int bits, uint16_t* tbl, cudaStream_t st);
+// Rows j0 .. j0+cnt-1 of the width-s HRTT's X^T as BF16 bits (kpad per row, zero past
+// n): Xt[j - j0][k] = d_k sum over bucket j of sigma_c H[k, c]; exact when every
+// bucket holds at most 256 coordinates (2^bits <= 256 s).
+cudaError_t launch_hrtt_xt_bf16(int64_t n, int64_t kpad, int s, int j0, int cnt, int bits, const uint32_t* dbits,
+                                const uint16_t* tbl, uint16_t* Xt, int64_t ldt, cudaStream_t st);
 // Dense HRTT X (n x s, +-integer entries) for re_embedding_x.
 cudaError_t launch_hrtt_x_dense(int64_t n, int s, int bits, const uint32_t* dbits, const uint16_t* tbl,
                                 float* X, int64_t ldx, cudaStream_t st);

@@ -160,3 +160,29 @@ def test_tc_srht_rank_matches_transform_path(htc):
     assert (r_tc.rank, r_tc.final_s, r_tc.passes) == (r_fw.rank, r_fw.final_s, r_fw.passes) == \
         (orc.rank, orc.final_s, orc.passes)
     assert np.max(np.abs(s_tc[:r_tc.n_sigma] - s_fw[:r_fw.n_sigma])) <= 3e-5 * s_fw[0]
+
+
+@pytest.mark.parametrize("m,n,s", [
+    (300, 1000, 8),          # m < n: transposed, the register transform (not the tensor-core path)
+    (2000, 1000, 8),         # n_pad 1024 <= 256 s: tensor cores
+    (3001, 3000, 16),        # 4096, buckets of 256
+    (9100, 9000, 64),        # 16384, buckets of 256
+    (5000, 5000, 512),       # 8192: two launches of 256 columns
+    (4000, 9000, 32),        # 16384 > 256 s: the register transform
+])
+def test_tc_hrtt_right_sketch_parity(htc, m, n, s):
+    """With BF16x3 precision, HRTT widths whose buckets hold at most 256 coordinates
+    take the dense X = D H C^T (integers of magnitude <= 256, exact in BF16) through
+    the tensor-core contraction: the oracle's X within the FP32 accumulation bound."""
+    A = np.random.default_rng(m + n + s + 2).standard_normal((m, n)).astype(np.float32)
+    Ad = torch.from_numpy(A).cuda()
+    A64 = A.astype(np.float64)
+    Ao, _ = alg.orient(A64)
+    rows, cols = Ao.shape
+    AX = torch.zeros(rows, s, dtype=torch.float32, device="cuda")
+    rk.re_sketch_apply(htc, Ad, 0, s, rk.RE_HRTT, 61, AX)
+    ref = alg.right_sketch(Ao, s, alg.HRTT, 61)
+    X = alg.embeddings(alg.HRTT, cols, rows, s, 61, r2=0)[0]
+    bound = 2.0 * (cols / 16 + 32) * U32 * (np.abs(Ao) @ np.abs(X)) + 1e-35
+    err = np.abs(AX.double().cpu().numpy() - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
