@@ -278,6 +278,7 @@ struct BatchedState {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
     DBuf ax, x, xt, tcerr, actpre, core, sigma, sscaled, status, out, active, valid, descs, pre128, pre64, colpre, finals;
+    DBuf tmaps;                       // tensor-core path: four row-class tensor maps per block
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned char> key;
     int bm_for[16] = {0};
@@ -289,7 +290,7 @@ void batched_destroy(BatchedState* st) {
     if (!st) return;
     if (st->exec) cudaGraphExecDestroy(st->exec);
     DBuf* bufs[] = {&st->ax, &st->x, &st->xt, &st->tcerr, &st->actpre, &st->core, &st->sigma, &st->sscaled, &st->status, &st->out,
-                    &st->active, &st->valid, &st->descs, &st->pre128, &st->pre64, &st->colpre, &st->finals};
+                    &st->active, &st->valid, &st->descs, &st->pre128, &st->pre64, &st->colpre, &st->finals, &st->tmaps};
     for (DBuf* b : bufs) b->release();
     if (st->ev_in) cudaEventDestroy(st->ev_in);
     if (st->ev_out) cudaEventDestroy(st->ev_out);
@@ -365,6 +366,24 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
     // otherwise FP32 CUDA cores with an autotuned tile height
     const bool use_tc = o.precision == RE_PREC_BF16X3;
     const int NXT = tc_mma_n(SNEW);
+    // row-major stored blocks on the tensor-core path: four row-class tensor maps each
+    const size_t mapb = row_class_map_bytes();
+    std::vector<unsigned char> hmaps;
+    if (use_tc && !kblocks) {
+        hmaps.assign((size_t)count * 4 * mapb, 0);
+        for (int i = 0; i < count; ++i) {
+            BatchDesc& D = hd[i];
+            // row-major: 36 floats (32 values and up to 3 before) x 32 rows per class and
+            // half chunk; stored transposed: 132 floats (128 oriented rows and up to 3
+            // before) x 8 stored rows
+            if (valid[i] && D.A && !D.trans)
+                D.tmaps = encode_row_class_maps(D.A, D.ld, D.rows, D.cols, 36, 32,
+                                                hmaps.data() + (size_t)i * 4 * mapb) ? 1 : 0;
+            else if (valid[i] && D.A && D.trans)
+                D.tmaps = encode_row_class_maps(D.A, D.ld, D.cols, D.rows, 132, 8,
+                                                hmaps.data() + (size_t)i * 4 * mapb) ? 2 : 0;
+        }
+    }
     int64_t ax_total = 0, x_total = 0, xt_total = 0;
     for (int i = 0; i < count; ++i) {
         BatchDesc& D = hd[i];
@@ -404,6 +423,7 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
     ens(st->pre64, sizeof(int64_t) * (size_t)(count + 1));
     ens(st->colpre, sizeof(int64_t) * (size_t)(count + 1));
     ens(st->finals, sizeof(int) * (size_t)count);
+    if (!hmaps.empty()) ens(st->tmaps, hmaps.size());
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_last_error(RE_ERR_NOMEM, "batched: device workspace allocation failed");
@@ -420,7 +440,7 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
     put(hd.data(), sizeof(BatchDesc) * hd.size());
     put(valid.data(), sizeof(int) * valid.size());
     const void* pools[] = {st->ax.p, st->x.p, st->xt.p, st->tcerr.p, st->actpre.p, st->core.p, st->sigma.p, st->sscaled.p,
-                           st->status.p, st->out.p, st->active.p, st->finals.p};
+                           st->status.p, st->out.p, st->active.p, st->finals.p, st->tmaps.p};
     put(pools, sizeof(pools));
 
     cudaStream_t bs = st->stream;
@@ -437,6 +457,7 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
         if (e == cudaSuccess) e = cudaMemcpy(st->pre128.p, pre128.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(st->pre64.p, pre64.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(st->colpre.p, colpre.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !hmaps.empty()) e = cudaMemcpy(st->tmaps.p, hmaps.data(), hmaps.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return set_last_error(RE_ERR_CUDA, "batched: descriptor upload failed");
         // ---- autotune the right-sketch tile height for each width of the ladder
         // (CUDA-core path; the candidates differ only in tiling, not in arithmetic)
@@ -501,7 +522,7 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
                         if (el == cudaSuccess)
                             el = launch_right_tc_batched(dd, count, st->actpre.as<int64_t>(), pre128[count],
                                                          st->xt.as<uint16_t>(), cn, st->ax.as<float>(), S_MAX, c0, tcerr,
-                                                         bs);
+                                                         st->tmaps.p, bs);
                         covered = upto;
                         nl += 3;
                     }

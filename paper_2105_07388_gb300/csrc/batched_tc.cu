@@ -5,29 +5,40 @@
 // one persistent CTA per SM walks its items and K chunks in one pipeline.
 //
 // Blocks come with any row pitch (a kernel block of n columns has ld = n), which
-// TMA cannot address, so the tiles are fetched with asynchronous 4-byte copies
-// (cp.async) straight into the 128B-swizzled layout the converters read:
-//   warps 12-15  A producers: per half chunk (128 rows x 32 k), copies of 16,
-//             8 or 4 bytes (the widest the block's row starts allow), coalesced
-//             along k into the 128B-swizzled row layout for row-major blocks, or
-//             along rows into a k-major tile for blocks stored transposed; zero
-//             fill past the block's edges; completion tracked by the stage's
-//             mbarrier (cp.async.mbarrier.arrive.noinc).
+// one tensor map cannot address (its row pitch must be a multiple of 16 bytes).
+// Every fourth row can: rows c, c+4, c+8, ... sit 16 ld bytes apart, and all of
+// them start at the same offset (0..3 floats) past a 16-byte boundary.  So a
+// row-major block gets four tensor maps, one per row class c, each starting at the
+// 16-byte boundary at or below row c, and a tile's 128 rows are held in class
+// order (tile row 32c + t = block row 4t + c of the tile's 128), which the
+// epilogue undoes:
+//   warps 12-15  A producers: per half chunk (128 rows x 32 k), row-major
+//             blocks: one thread issues the four classes' boxes of 36 floats x 32
+//             rows (the 32 values of each row with up to 3 before them) by TMA,
+//             zero fill past the block's columns and rows.  Blocks stored
+//             transposed: asynchronous copies of 16, 8 or 4 bytes along rows into
+//             a k-major tile (cp.async, mbarrier arrive.noinc), zero fill past the
+//             edges.
 //             For a matrix-free kernel block (no A, 3-D points) they instead
 //             stage the tile's 128 row points and the half chunk's 32 column
 //             points (negated, as three coordinate arrays; padding far away so
 //             that entries past the block come out as 1/sqrt(inf) = 0) and
 //             arrive on the stage's mbarrier directly.
 //   warp 16   X^T producer: 16-byte copies of the BF16 X^T chunk (N rows x 64 k).
-//   warps 0-7 converters (either tile layout), warp 17 MMA issuer, warps 8-11
-//             epilogue: as in the single-matrix kernel.  For a matrix-free block a
+//   warps 0-7 converters, warp 17 MMA issuer, warps 8-11 epilogue: as in the
+//             single-matrix kernel.  Converter warp (q, h) of a row-major block
+//             reads row class q, whose offset is one value for the whole warp, so
+//             it takes the row's 32 values at a fixed position of its 36.  For a matrix-free block a
 //             converter thread computes its row's 32 entries 1 / |x_r - y_k| in
 //             FP32 from the staged points (differences, squares and fused
 //             multiply-adds two entries at a time in packed FP32x2, the hardware
 //             reciprocal square root), so the block is never in HBM.
 // Every mbarrier wait is bounded in time (on expiry: error flag, drain, free
 // TMEM, return).
+#include <cuda.h>
+
 #include <algorithm>
+#include <cstring>
 #include <cstdint>
 
 #include "common.cuh"
@@ -49,7 +60,11 @@ constexpr int kAProdWarp = kConvWarps + kEpiWarps;             // 12..15
 constexpr int kBProdWarp = kAProdWarp + kAProdWarps;           // 16
 constexpr int kMmaWarp = kBProdWarp + 1;                       // 17
 constexpr int kThreads = (kMmaWarp + 1) * 32;                  // 576
-constexpr uint32_t kHalfBytes = kBM * 32 * 4;                  // 16 KB FP32 half chunk
+constexpr uint32_t kClassPitch = 144;                          // row-class box: 36 floats per row
+constexpr uint32_t kClassBytes = 32 * kClassPitch;             // 32 rows of one class
+constexpr uint32_t kHalfBytes = 4 * kClassBytes;               // 18 KB half-chunk stage (other layouts use 16 KB)
+constexpr uint32_t kTClassPitch = 528;                         // transposed block: 132 floats per stored row
+constexpr uint32_t kTClassBytes = 8 * kTClassPitch;            // 8 stored rows of one class
 constexpr int kAStages = 8;
 constexpr int kStages = 2;
 constexpr uint32_t kAStageCol = 256;
@@ -195,6 +210,7 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
 }
 
 struct TcBatchParams {
+    const CUtensorMap* tmaps; // four row-class maps per block (row-major blocks with d[b].tmaps)
     const BatchDesc* d;
     int count;
     const int64_t* pre;       // prefix of the active blocks' 128-row tiles (count + 1 entries)
@@ -265,6 +281,19 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
             const int64_t kch = p.d[b].kpad / kBK;
             const bool trans = p.d[b].trans != 0;
             const bool mfree = p.d[b].A == nullptr;
+            const bool cls = p.d[b].tmaps == 1, tcls = p.d[b].tmaps == 2;
+            // row class q's offset past its 16-byte boundary (one value for the warp)
+            const int off = cls ? (int)((reinterpret_cast<uintptr_t>(p.d[b].A + (int64_t)q * p.d[b].ld) & 15u) >> 2) : 0;
+            // stored transposed: each class's first value of this thread's oriented row r
+            // (class c, stored row 4t + c at c * kTClassBytes + t * kTClassPitch)
+            uint32_t tbase[4] = {0u, 0u, 0u, 0u};
+            if (tcls) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint32_t o = (uint32_t)((reinterpret_cast<uintptr_t>(p.d[b].A + (int64_t)c * p.d[b].ld) & 15u) >> 2);
+                    tbase[c] = (uint32_t)c * kTClassBytes + 4u * (o + (uint32_t)r);
+                }
+            }
             for (int64_t kc = 0; kc < kch; ++kc, ++g) {
                 const int s = (int)(g % kStages);
                 ok = mbar_wait(&empty[s], (uint32_t)((g / kStages) & 1) ^ 1u, &s_abort, p.err);
@@ -305,7 +334,39 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
                     mbar_arrive(&a_empty[as]);
                 } else {
                     float4 v[8];
-                    if (!trans) {
+                    if (cls) {
+                        // class q, row lane: 36 floats at pitch 144 (granules 9 lane + c: eight
+                        // consecutive lanes hit distinct bank groups); the row's values start at off
+                        const float4* src = reinterpret_cast<const float4*>(tile + (size_t)q * kClassBytes +
+                                                                            (size_t)lane * kClassPitch);
+                        float4 w4[9];
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) w4[c] = src[c];
+                        if (off == 0) {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) v[c] = w4[c];
+                        } else if (off == 1) {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) v[c] = make_float4(w4[c].y, w4[c].z, w4[c].w, w4[c + 1].x);
+                        } else if (off == 2) {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) v[c] = make_float4(w4[c].z, w4[c].w, w4[c + 1].x, w4[c + 1].y);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) v[c] = make_float4(w4[c].w, w4[c + 1].x, w4[c + 1].y, w4[c + 1].z);
+                        }
+                    } else if (tcls) {
+                        // k-major rows by class: value (kk, r) at tbase[kk % 4] + (kk / 4) * pitch;
+                        // consecutive lanes read consecutive words
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const unsigned char* t = tile + (size_t)c * kTClassPitch;
+                            v[c] = make_float4(*reinterpret_cast<const float*>(t + tbase[0]),
+                                               *reinterpret_cast<const float*>(t + tbase[1]),
+                                               *reinterpret_cast<const float*>(t + tbase[2]),
+                                               *reinterpret_cast<const float*>(t + tbase[3]));
+                        }
+                    } else if (!trans) {
                         const unsigned char* src = tile + (size_t)r * 128;
 #pragma unroll
                         for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const float4*>(src + ((c ^ (r & 7)) << 4));
@@ -358,6 +419,31 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
                     }
                     const uint32_t dst0 = smem_u32(abuf + (size_t)as * kHalfBytes);
                     const int64_t k0 = kc * kBK + 32 * h;
+                    if (D.tmaps) {
+                        // the four row classes' boxes by TMA (one thread; the others arrive).
+                        // Row-major: class c's 32 rows of the tile (x = k0, y = row0 / 4).
+                        // Stored transposed: class c's 8 stored rows of the half chunk
+                        // (x = row0, the tile's first oriented row; y = k0 / 4)
+                        if (pw == 0 && lane == 0) {
+                            // the converters read this stage through the generic proxy; order
+                            // those reads before the TMA (async proxy) overwrites it
+                            fence_proxy_async();
+                            const bool rm = D.tmaps == 1;
+                            const int64_t srows = rm ? B.rows : B.cols;     // stored rows
+                            const uint32_t cb = rm ? kClassBytes : kTClassBytes;
+                            int ncls = 0;
+                            for (int c = 0; c < 4; ++c) ncls += srows > c ? 1 : 0;
+                            mbar_arrive_expect_tx(&a_full[as], (uint32_t)ncls * cb);
+                            for (int c = 0; c < 4; ++c)
+                                if (srows > c)
+                                    tma_load_2d(abuf + (size_t)as * kHalfBytes + (size_t)c * cb,
+                                                p.tmaps + 4 * (int64_t)b + c, rm ? (int)k0 : (int)row0,
+                                                rm ? (int)(row0 / 4) : (int)(k0 / 4), &a_full[as]);
+                        } else {
+                            mbar_arrive(&a_full[as]);
+                        }
+                        continue;
+                    }
                     if (mfree) {
                         unsigned char* stg = abuf + (size_t)as * kHalfBytes;
                         const int t = 32 * pw + lane;          // row point t of the tile
@@ -399,6 +485,12 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
             }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
+        if (!ok) {
+            // aborted: let TMA loads already issued into this CTA's shared memory land
+            const unsigned long long t0 = now_ns();
+            while (now_ns() - t0 < 100000ull) {
+            }
+        }
     } else if (warp == kBProdWarp) {
         // ---------------- X^T producer: 16-byte cp.async, N rows x 128 bytes per chunk
         int64_t g = 0;
@@ -476,7 +568,9 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
             if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.ld is warp-wide
             tc_fence_after();
             const BatchDesc& D = p.d[b];
-            const int64_t row = (it - p.pre[b]) * kBM + q * 32 + lane;
+            // tile rows in class order for blocks fetched by row class (tile row 32q + lane
+            // is block row 4 lane + q of the tile)
+            const int64_t row = (it - p.pre[b]) * kBM + (D.tmaps == 1 ? 4 * lane + q : q * 32 + lane);
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * p.N);
             for (int c = 0; c < p.N; c += 16) {
                 float v[16];
@@ -572,12 +666,38 @@ cudaError_t launch_gauss_xt_batched(const BatchDesc* d, int count, const int* ac
     return cudaGetLastError();
 }
 
+size_t row_class_map_bytes() { return sizeof(CUtensorMap); }
+
+bool encode_row_class_maps(const float* A, int64_t ld, int64_t rows, int64_t cols, int box_x, int box_y,
+                           void* out) {
+    EncodeTiled enc = encode_fn();
+    if (!enc || !A || rows <= 0 || cols <= 0 || ld < cols) return false;
+    CUtensorMap* maps = static_cast<CUtensorMap*>(out);
+    for (int c = 0; c < 4; ++c) {
+        std::memset(&maps[c], 0, sizeof(CUtensorMap));
+        if (rows <= c) continue;                      // an empty class is never loaded
+        const uintptr_t first = reinterpret_cast<uintptr_t>(A + (int64_t)c * ld);
+        const uintptr_t base = first & ~(uintptr_t)15;
+        const uint64_t off = (first - base) / 4;      // floats before row c's first value
+        const cuuint64_t dim[2] = {(cuuint64_t)(off + cols), (cuuint64_t)((rows - c + 3) / 4)};
+        const cuuint64_t stride[1] = {(cuuint64_t)ld * 16};
+        const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = enc(&maps[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, reinterpret_cast<void*>(base), dim, stride,
+                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
+}
+
 cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t* act_prefix, int64_t max_items,
                                     const uint16_t* XTpool, int s, float* AXpool, int64_t ldax, int col0,
-                                    int* err_flag, cudaStream_t st) {
+                                    int* err_flag, const void* tmaps, cudaStream_t st) {
     if (max_items <= 0 || s <= 0 || count <= 0) return cudaSuccess;
     if (s > 256 || s % 8 != 0 || col0 % 4 != 0 || ldax % 4 != 0 || !err_flag) return cudaErrorInvalidValue;
     TcBatchParams p;
+    p.tmaps = static_cast<const CUtensorMap*>(tmaps);
     p.d = d;
     p.count = count;
     p.pre = act_prefix;

@@ -39,6 +39,10 @@ struct BatchDesc {
     // is 1 / |px[r] - py[c]| for 3-D points (FP32, 3 per point), trans == 0
     const float* px;
     const float* py;
+    // tensor-core path: 1 (row-major block) or 2 (block stored transposed) when its
+    // stored rows are fetched through four row-class tensor maps (stored rows c, c+4,
+    // c+8, ... for c = 0..3); 0: asynchronous copies
+    int tmaps;
 };
 
 // ---- embeddings (embed.cu) ----------------------------------------------------
@@ -134,9 +138,20 @@ cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax
 // bytes, so any row pitch works.
 cudaError_t launch_compact_tiles(const BatchDesc* d, int count, const int* active, int64_t* act_prefix,
                                  cudaStream_t st);
+// tmaps: device array of 4 tensor maps per block (block b's at 4b .. 4b+3, used when
+// d[b].tmaps is set; see encode_row_class_maps).
 cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t* act_prefix, int64_t max_items,
                                     const uint16_t* XTpool, int s, float* AXpool, int64_t ldax, int col0,
-                                    int* err_flag, cudaStream_t st);
+                                    int* err_flag, const void* tmaps, cudaStream_t st);
+// Bytes of one tensor map (CUtensorMap) of the row-class fetch.
+size_t row_class_map_bytes();
+// Encodes into out (4 maps) the row classes of an FP32 matrix stored row-major with
+// srows x scols values, pitch ld: class c holds stored rows c, c+4, ... (pitch 16 ld
+// bytes, always a multiple of 16) from the 16-byte boundary at or below its first
+// row; boxes of box_x floats x box_y rows, zero fill past the stored columns and
+// rows.  Returns false when a map cannot be encoded.
+bool encode_row_class_maps(const float* A, int64_t ld, int64_t srows, int64_t scols, int box_x, int box_y,
+                           void* out);
 // X_b^T (BF16, nxt rows x kpad) of columns [col0, col0+s) for every active block.
 cudaError_t launch_gauss_xt_batched(const BatchDesc* d, int count, const int* active, int col0, int s, int nxt,
                                     uint16_t* XTpool, cudaStream_t st);
