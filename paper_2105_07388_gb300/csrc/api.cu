@@ -577,19 +577,22 @@ int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const
         h->stats.launches += 3 + (c0 > 0 ? 4 : 2);
         return RE_OK;
     }
-    const size_t need = std::max({re::left_part_floats(M, 2 * (c1 - c0), c0),
-                                  re::left_part_floats(M, 2 * c1, c1 - c0),
-                                  re::left_tc_part_floats(M, 2 * (c1 - c0), c0),
-                                  re::left_tc_part_floats(M, 2 * c1, c1 - c0)});
+    // the new core entries as two rectangles that each need their own Y rows once:
+    // rows [2 c0, 2 c1) x columns [0, c1) and rows [0, 2 c0) x columns [c0, c1) (the
+    // Gaussian Y is generated inside the kernels, and generating it is what they spend
+    // their time on)
+    const size_t need = std::max({re::left_part_floats(M, 2 * (c1 - c0), c1),
+                                  re::left_part_floats(M, 2 * c0, c1 - c0),
+                                  re::left_tc_part_floats(M, 2 * (c1 - c0), c1),
+                                  re::left_tc_part_floats(M, 2 * c0, c1 - c0)});
     if (int r = ensure(h->part, sizeof(float) * need)) return r;
     int* tmo = static_cast<int*>(h->status.p) + 1;     // bounded-wait expiry flag of the tensor-core kernels
     cudaError_t e = cudaSuccess;
     cudaEvent_t a = stage_begin(h, st);
-    if (c0 > 0)
-        e = re::launch_left(seed, AX, ld_ax, M, 2 * c0, 2 * (c1 - c0), 0, c0, static_cast<float*>(h->part.p),
-                            h->part.cap / sizeof(float), core, ld_core, st, tmo);
-    if (e == cudaSuccess)
-        e = re::launch_left(seed, AX, ld_ax, M, 0, 2 * c1, c0, c1 - c0, static_cast<float*>(h->part.p),
+    e = re::launch_left(seed, AX, ld_ax, M, 2 * c0, 2 * (c1 - c0), 0, c1, static_cast<float*>(h->part.p),
+                        h->part.cap / sizeof(float), core, ld_core, st, tmo);
+    if (e == cudaSuccess && c0 > 0)
+        e = re::launch_left(seed, AX, ld_ax, M, 0, 2 * c0, c0, c1 - c0, static_cast<float*>(h->part.p),
                             h->part.cap / sizeof(float), core, ld_core, st, tmo);
     if (e != cudaSuccess) return cuda_fail(e, "left sketch");
     stage_end(h, st, a, kStageLeft);
