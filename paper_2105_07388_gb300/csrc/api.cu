@@ -415,33 +415,37 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
         stage_end(h, st, g, kStageOther);
         if (int r = ensure(h->status, 64)) return r;
         const bool tc = h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && (ld_ax % 4) == 0 &&
-                        (reinterpret_cast<uintptr_t>(AX + c0) & 15) == 0 && P.n_pad <= 256 * (int64_t)cnt;
+                        (reinterpret_cast<uintptr_t>(AX + c0) & 15) == 0;
         if (e == cudaSuccess && tc) {
-            // buckets of at most 256 coordinates: the dense X = D H C^T has integer
-            // entries of magnitude at most 256, exact in BF16, so the width goes through
-            // the tensor-core contraction (256 columns per launch) instead of the
-            // register transform
+            // the dense X = D H C^T has integer entries of magnitude at most the bucket
+            // size: exact in BF16 when buckets hold at most 256 coordinates (one plane,
+            // 256 columns per launch), otherwise as a BF16 and its remainder (two planes,
+            // six products, 128 columns per launch); the width goes through the
+            // tensor-core contraction instead of the register transform
+            const int planes = P.n_pad <= 256 * (int64_t)cnt ? 1 : 2;
+            const int wmax = planes == 1 ? 256 : 128;
             const int64_t kpad = (P.A.cols + 63) / 64 * 64;
-            for (int j0 = 0; j0 < cnt && e == cudaSuccess; j0 += 256) {
-                const int w = std::min(256, cnt - j0);
+            for (int j0 = 0; j0 < cnt && e == cudaSuccess; j0 += wmax) {
+                const int w = std::min(wmax, cnt - j0);
                 const int nrows = re::tc_mma_n(w);
-                if (int r = ensure(h->xt, sizeof(uint16_t) * (size_t)kpad * nrows)) return r;
+                if (int r = ensure(h->xt, sizeof(uint16_t) * (size_t)kpad * nrows * planes)) return r;
                 cudaEvent_t g2 = stage_begin(h, st);
-                if (nrows > w)
-                    e = cudaMemsetAsync(static_cast<uint16_t*>(h->xt.p) + (size_t)kpad * w, 0,
+                for (int pl = 0; pl < planes && e == cudaSuccess && nrows > w; ++pl)
+                    e = cudaMemsetAsync(static_cast<uint16_t*>(h->xt.p) + (size_t)kpad * ((size_t)pl * nrows + w), 0,
                                         sizeof(uint16_t) * (size_t)kpad * (nrows - w), st);
                 if (e == cudaSuccess)
                     e = re::launch_hrtt_xt_bf16(P.A.cols, kpad, cnt, j0, w, P.nbits,
                                                 static_cast<const uint32_t*>(h->dx.p),
                                                 static_cast<const uint16_t*>(h->ht.p),
-                                                static_cast<uint16_t*>(h->xt.p), kpad, st);
+                                                static_cast<uint16_t*>(h->xt.p), kpad, st, planes, nrows);
                 stage_end(h, st, g2, kStageOther);
                 if (e != cudaSuccess) break;
                 cudaEvent_t a2 = stage_begin(h, st);
                 int nl = 0;
                 e = re::launch_right_tc(P.A, static_cast<const uint16_t*>(h->xt.p), kpad, w, AX + c0 + j0, ld_ax,
-                                        static_cast<int*>(h->status.p) + 1, st, &nl, h->opts.test_drop_load);
-                stage_end(h, st, a2, kStageRight, right_bytes(P, w, 2), 3.0 * 2.0 * P.A.rows * P.A.cols * w);
+                                        static_cast<int*>(h->status.p) + 1, st, &nl, h->opts.test_drop_load, planes);
+                stage_end(h, st, a2, kStageRight, right_bytes(P, w, 2 * planes),
+                          3.0 * planes * 2.0 * P.A.rows * P.A.cols * w);
                 h->stats.launches += 1 + nl;
             }
             if (e != cudaSuccess) return cuda_fail(e, "right sketch (HRTT, tensor cores)");

@@ -6,6 +6,8 @@
 // is only written out here for re_embedding_y.
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -229,7 +231,8 @@ cudaError_t launch_hrtt_table(uint64_t seed, int bits, uint16_t* tbl, cudaStream
 __global__ void __launch_bounds__(1024) hrtt_xt_bf16_kernel(int64_t n, int64_t kpad, int s, int j0, int bits,
                                                             const uint32_t* __restrict__ dbits,
                                                             const uint16_t* __restrict__ tbl,
-                                                            uint16_t* __restrict__ Xt, int64_t ldt) {
+                                                            uint16_t* __restrict__ Xt, int64_t ldt, int planes,
+                                                            int64_t plane_rows) {
     extern __shared__ float y[];
     const int N = 1 << bits, j = j0 + (int)blockIdx.x;
     for (int i = threadIdx.x; i < N; i += blockDim.x) y[i] = 0.f;
@@ -249,21 +252,34 @@ __global__ void __launch_bounds__(1024) hrtt_xt_bf16_kernel(int64_t n, int64_t k
         __syncthreads();
     }
     uint16_t* row = Xt + (int64_t)blockIdx.x * ldt;
+    uint16_t* row_lo = row + plane_rows * ldt;
     for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x) {
         float v = 0.f;
         if (k < n) v = ((dbits[k >> 5] >> (k & 31)) & 1u) ? -y[k] : y[k];
-        row[k] = (uint16_t)(__float_as_uint(v) >> 16);
+        if (planes == 1) {
+            row[k] = (uint16_t)(__float_as_uint(v) >> 16);
+        } else {
+            // an integer below 2^16 in magnitude: its nearest BF16 and the (exact,
+            // at most 8-bit) remainder
+            const uint32_t hb = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+            const float lo = v - __uint_as_float(hb << 16);
+            row[k] = (uint16_t)hb;
+            row_lo[k] = (uint16_t)(__float_as_uint(lo) >> 16);
+        }
     }
 }
 
 cudaError_t launch_hrtt_xt_bf16(int64_t n, int64_t kpad, int s, int j0, int cnt, int bits, const uint32_t* dbits,
-                                const uint16_t* tbl, uint16_t* Xt, int64_t ldt, cudaStream_t st) {
+                                const uint16_t* tbl, uint16_t* Xt, int64_t ldt, cudaStream_t st, int planes,
+                                int64_t plane_rows) {
     if (cnt <= 0) return cudaSuccess;
-    if (bits < 0 || bits > 15 || s <= 0 || j0 < 0 || j0 + cnt > s) return cudaErrorInvalidValue;
+    if (bits < 0 || bits > 15 || s <= 0 || j0 < 0 || j0 + cnt > s || (planes != 1 && planes != 2) ||
+        (planes == 2 && plane_rows < cnt))
+        return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) << bits;
     cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(hrtt_xt_bf16_kernel));
     if (e != cudaSuccess) return e;
-    hrtt_xt_bf16_kernel<<<cnt, 1024, smem, st>>>(n, kpad, s, j0, bits, dbits, tbl, Xt, ldt);
+    hrtt_xt_bf16_kernel<<<cnt, 1024, smem, st>>>(n, kpad, s, j0, bits, dbits, tbl, Xt, ldt, planes, plane_rows);
     return cudaGetLastError();
 }
 

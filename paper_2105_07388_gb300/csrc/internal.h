@@ -73,10 +73,13 @@ cudaError_t launch_srtt_y_dense(int64_t m, int r2, const uint32_t* dbits, const 
 // HRTT hashing table of 2^bits entries (bits <= 15): entry q = pi_X(q) | (sigma < 0) << 15.
 cudaError_t launch_hrtt_table(uint64_t seed, int bits, uint16_t* tbl, cudaStream_t st);
 // Rows j0 .. j0+cnt-1 of the width-s HRTT's X^T as BF16 bits (kpad per row, zero past
-// n): Xt[j - j0][k] = d_k sum over bucket j of sigma_c H[k, c]; exact when every
-// bucket holds at most 256 coordinates (2^bits <= 256 s).
+// n): Xt[j - j0][k] = d_k sum over bucket j of sigma_c H[k, c].  planes = 1: exact when
+// every bucket holds at most 256 coordinates (2^bits <= 256 s); planes = 2: the
+// entries' nearest BF16 in rows 0.., their remainders in rows plane_rows.. (exact
+// for any bucket size up to 2^15).
 cudaError_t launch_hrtt_xt_bf16(int64_t n, int64_t kpad, int s, int j0, int cnt, int bits, const uint32_t* dbits,
-                                const uint16_t* tbl, uint16_t* Xt, int64_t ldt, cudaStream_t st);
+                                const uint16_t* tbl, uint16_t* Xt, int64_t ldt, cudaStream_t st, int planes = 1,
+                                int64_t plane_rows = 0);
 // Dense HRTT X (n x s, +-integer entries) for re_embedding_x.
 cudaError_t launch_hrtt_x_dense(int64_t n, int s, int bits, const uint32_t* dbits, const uint16_t* tbl,
                                 float* X, int64_t ldx, cudaStream_t st);
@@ -179,9 +182,12 @@ cudaError_t launch_right_hrtt(const MatView& A, const uint32_t* dbits, uint16_t*
 bool tc_supported(const MatView& A);
 // MMA N used for s output columns (>= 16, multiple of 16); X^T needs that many rows.
 int tc_mma_n(int s);
+// X^T holds xterms BF16 planes of tc_mma_n(s) rows each (plane t at row t * tc_mma_n(s)):
+// 1 for BF16-exact X, 2 for X = hi + lo exactly, 3 for FP32 X (six products, error
+// below 2^-24 of |A||X|); xterms > 1 takes at most 128 columns.
 cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, int s, float* C,
                             int64_t ldc, int* err_flag, cudaStream_t st, int* launches = nullptr,
-                            int drop_first = 0);
+                            int drop_first = 0, int xterms = 1);
 
 // ---- exact-product sketches of the precision mode (sketch_ex.cu) --------------
 // e[r] = smallest e with |A[r][k]| < 2^e (0 for a zero row); *status |= 1 for

@@ -74,7 +74,15 @@ struct TcParams {
     int64_t kchunks;
     int* err;
     int drop_first;   // test hook: CTA 0 withholds its first A half chunk
+    int xterms;       // BF16 planes of X (1: exact X; 2: X = hi + lo exactly; 3: FP32 X)
+    int xrows;        // rows of one plane in the X^T map (plane t starts at row t * xrows)
 };
+
+// (A term, X term) products accumulated per K step with more than one plane of X
+// (one plane: every A term times X): with two exact planes all six; with three planes the six whose terms
+// carry at most 16 bits below the leading one (the rest are below 2^-24 relative).
+__device__ constexpr int kPairs2A[6] = {0, 1, 2, 0, 1, 2}, kPairs2X[6] = {0, 0, 0, 1, 1, 1};
+__device__ constexpr int kPairs3A[6] = {0, 0, 1, 0, 1, 2}, kPairs3X[6] = {0, 1, 0, 2, 1, 0};
 
 __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_constant__ CUtensorMap amap,
                                                                const __grid_constant__ CUtensorMap xmap,
@@ -89,8 +97,9 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int NA = kMaxAStages;                  // compile time: ring indices are shifts
     const int nacc = p.N <= 128 ? 2 : 1;            // accumulator buffers in TMEM
-    const uint32_t b_bytes = (uint32_t)p.N * kBK * 2;
-    const uint32_t b_stage = (b_bytes + 1023u) & ~1023u;
+    const uint32_t b_bytes = (uint32_t)p.N * kBK * 2;                 // one plane of one stage
+    const uint32_t b_plane = (b_bytes + 1023u) & ~1023u;
+    const uint32_t b_stage = b_plane * (uint32_t)p.xterms;
     unsigned char* abuf = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* bbuf = abuf + (size_t)NA * kHalfBytes;
@@ -215,8 +224,10 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
             for (int64_t g = 0; g < total_chunks; ++g) {
                 const int s = (int)(g % kStages);
                 if (!mbar_wait(&empty[s], (uint32_t)((g / kStages) & 1) ^ 1u, &s_abort, p.err)) break;
-                mbar_arrive_expect_tx(&full_b[s], b_bytes);
-                tma_load_2d(bbuf + (size_t)s * b_stage, &xmap, (int)(kc * kBK), 0, &full_b[s]);
+                mbar_arrive_expect_tx(&full_b[s], b_bytes * (uint32_t)p.xterms);
+                for (int t = 0; t < p.xterms; ++t)
+                    tma_load_2d(bbuf + (size_t)s * b_stage + (size_t)t * b_plane, &xmap, (int)(kc * kBK), t * p.xrows,
+                                &full_b[s]);
                 ++issued;
                 if (++kc == K) kc = 0;
             }
@@ -247,13 +258,28 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_kernel(const __grid_cons
                     tc_fence_after();
                     const uint32_t bst = smem_u32(bbuf + (size_t)s * b_stage);
                     const uint32_t ast = tmem_base + kAStageCol + 96u * (uint32_t)s;
+                    if (p.xterms == 1) {
 #pragma unroll
-                    for (int kk = 0; kk < kBK / 16; ++kk) {
-                        const uint64_t bdesc = sw128_desc(bst + 32u * kk);
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+                            const uint64_t bdesc = sw128_desc(bst + 32u * kk);
 #pragma unroll
-                        for (int term = 0; term < 3; ++term)
-                            mma_bf16_ts(d_tmem, ast + 32u * term + 8u * kk, bdesc, idesc,
-                                        (kc != k0 || kk || term) ? 1u : 0u);
+                            for (int term = 0; term < 3; ++term)
+                                mma_bf16_ts(d_tmem, ast + 32u * term + 8u * kk, bdesc, idesc,
+                                            (kc != k0 || kk || term) ? 1u : 0u);
+                        }
+                    } else {
+                        const bool two = p.xterms == 2;
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+#pragma unroll
+                            for (int pr = 0; pr < 6; ++pr) {
+                                const int ta = two ? kPairs2A[pr] : kPairs3A[pr];
+                                const int tx = two ? kPairs2X[pr] : kPairs3X[pr];
+                                const uint64_t bdesc = sw128_desc(bst + (uint32_t)tx * b_plane + 32u * kk);
+                                mma_bf16_ts(d_tmem, ast + 32u * ta + 8u * kk, bdesc, idesc,
+                                            (kc != k0 || kk || pr) ? 1u : 0u);
+                            }
+                        }
                     }
                     mma_commit(&empty[s]);
                 }
@@ -337,14 +363,15 @@ bool tc_supported(const MatView& A) {
 int tc_mma_n(int s) { return s <= 16 ? 16 : (s + 15) / 16 * 16; }
 
 cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, int s, float* C,
-                            int64_t ldc, int* err_flag, cudaStream_t st, int* launches, int drop_first) {
+                            int64_t ldc, int* err_flag, cudaStream_t st, int* launches, int drop_first, int xterms) {
     if (s <= 0 || A.rows <= 0) return cudaSuccess;
-    if (s > 256 || s % 8 != 0) return cudaErrorInvalidValue;
+    if (s > 256 || s % 8 != 0 || xterms < 1 || xterms > 3) return cudaErrorInvalidValue;
     const int N = tc_mma_n(s);
+    if (xterms > 1 && N > 128) return cudaErrorInvalidValue;      // shared memory: three planes of 128 rows
     EncodeTiled enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t gdim[2] = {(cuuint64_t)ldt, (cuuint64_t)N};
+    const cuuint64_t gdim[2] = {(cuuint64_t)ldt, (cuuint64_t)N * xterms};
     const cuuint64_t gstride[1] = {(cuuint64_t)ldt * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)N};
     const cuuint32_t estr[2] = {1, 1};
@@ -374,8 +401,11 @@ cudaError_t launch_right_tc(const MatView& A, const uint16_t* Xt, int64_t ldt, i
     p.kchunks = (A.cols + kBK - 1) / kBK;
     p.err = err_flag;
     p.drop_first = drop_first;
+    p.xterms = xterms;
+    p.xrows = N;
     const uint32_t b_bytes = (uint32_t)N * kBK * 2;
-    const size_t smem = (size_t)kHalfBytes * kMaxAStages + ((b_bytes + 1023u) & ~1023u) * kStages + 1024;
+    const size_t smem =
+        (size_t)kHalfBytes * kMaxAStages + ((b_bytes + 1023u) & ~1023u) * (size_t)xterms * kStages + 1024;
     cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(right_tc_kernel));
     if (e != cudaSuccess) return e;
     if (!g_sms) {

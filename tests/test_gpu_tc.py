@@ -164,16 +164,19 @@ def test_tc_srht_rank_matches_transform_path(htc):
 
 @pytest.mark.parametrize("m,n,s", [
     (300, 1000, 8),          # m < n: transposed, the register transform (not the tensor-core path)
-    (2000, 1000, 8),         # n_pad 1024 <= 256 s: tensor cores
+    (2000, 1000, 8),         # n_pad 1024 <= 256 s: one BF16 plane of X
     (3001, 3000, 16),        # 4096, buckets of 256
     (9100, 9000, 64),        # 16384, buckets of 256
     (5000, 5000, 512),       # 8192: two launches of 256 columns
-    (4000, 9000, 32),        # 16384 > 256 s: the register transform
+    (9000, 4000, 8),         # 4096 > 256 s: buckets of 512, two planes (BF16 and remainder)
+    (9100, 9000, 32),        # 16384: buckets of 512, two planes
+    (5000, 20000, 16),       # transposed, 2^15: the register transform
 ])
 def test_tc_hrtt_right_sketch_parity(htc, m, n, s):
-    """With BF16x3 precision, HRTT widths whose buckets hold at most 256 coordinates
-    take the dense X = D H C^T (integers of magnitude <= 256, exact in BF16) through
-    the tensor-core contraction: the oracle's X within the FP32 accumulation bound."""
+    """With BF16x3 precision the HRTT's dense X = D H C^T (integer entries of
+    magnitude at most the bucket size) goes through the tensor-core contraction:
+    one exact BF16 plane for buckets of at most 256 coordinates, a BF16 and its
+    exact remainder otherwise.  The oracle's X within the FP32 accumulation bound."""
     A = np.random.default_rng(m + n + s + 2).standard_normal((m, n)).astype(np.float32)
     Ad = torch.from_numpy(A).cuda()
     A64 = A.astype(np.float64)
