@@ -5,7 +5,7 @@ Every step follows the algorithm box in order, with the embeddings written out
 densely so that each product is a plain matrix product a reader can check:
 
   step 1  r~1 = round(1.1 r1)                         -> ``oversampled``
-  step 2  draw X (n x r~1): Gaussian G, SRTT D H S^T or HRTT D H C^T
+  step 2  draw X (n x r~1): Gaussian G, SRTT D H S^T, HRTT D H C^T or HRCT D F^T C^T
                                                        -> ``rng.gaussian_x`` / ``rng.srtt_x`` / ``rng.hrtt_x``
   step 3  form A X                                     -> ``A @ X``
   step 4  r2 = 2 r~1
@@ -62,6 +62,7 @@ GAUSSIAN = 0
 SRHT = 1
 HRTT = 2
 SRCT = 3        # left embedding only: subsampled randomized DCT (Sec. 4, eta = 2)
+HRCT = 4        # right embedding only: hashed randomized DCT (Sec. 3.4, the experiments' X)
 
 
 def round_half_away(num: int, den: int) -> int:
@@ -90,16 +91,17 @@ def embeddings(kind: int, n: int, m: int, s: int, seed: int,
         return rng.gaussian_x(n, s, seed, col0), rng.gaussian_y(r2, m, seed, row0)
     if kind == SRHT:
         return rng.srtt_x(n, s, seed, col0), rng.srtt_y(r2, m, seed, row0)
-    if kind == HRTT:
+    if kind in (HRTT, HRCT):
         if col0 != 0:
-            raise ValueError("HRTT columns depend on the width: col0 must be 0")
-        return rng.hrtt_x(n, s, seed), rng.gaussian_y(r2, m, seed, row0)
+            raise ValueError("hashed embeddings' columns depend on the width: col0 must be 0")
+        X = rng.hrtt_x(n, s, seed) if kind == HRTT else rng.hrct_x(n, s, seed)
+        return X, rng.gaussian_y(r2, m, seed, row0)
     raise ValueError(f"unknown sketch kind {kind}")
 
 
 def left_kind(kind: int) -> int:
     """Kind of the left embedding Y drawn with right embedding `kind`."""
-    return GAUSSIAN if kind == HRTT else kind
+    return GAUSSIAN if kind in (HRTT, HRCT) else kind
 
 
 def orient(A: np.ndarray) -> tuple[np.ndarray, bool]:
@@ -134,8 +136,8 @@ def left_sketch(AX: np.ndarray, r2: int, kind: int, seed: int, row0: int = 0, yk
 
 
 def sketch_scale(s: int, kind: int = GAUSSIAN, n: int = 0) -> float:
-    """1/sqrt(s * r2) with r2 = 2 s; for the HRTT 1/sqrt(n_pad * r2) (n columns)."""
-    if kind == HRTT:
+    """1/sqrt(s * r2) with r2 = 2 s; for the hashed embeddings 1/sqrt(n_pad * r2) (n columns)."""
+    if kind in (HRTT, HRCT):
         return 1.0 / math.sqrt(float(1 << rng.next_pow2_bits(n)) * float(2 * s))
     return 1.0 / math.sqrt(float(s) * float(2 * s))
 
@@ -222,7 +224,7 @@ def ladder_limits(m: int, n: int, kind: int, s_max: int, ykind: int | None = Non
         cap = min(cap, 1 << rng.next_pow2_bits(n))
     if yk in (SRHT, SRCT):
         cap = min(cap, (1 << rng.next_pow2_bits(m)) // 2)   # 2s sampled rows of the padded transform
-    if kind == HRTT:
+    if kind in (HRTT, HRCT):
         cap = min(cap, 1 << rng.next_pow2_bits(n))      # no empty bucket
     return cap
 

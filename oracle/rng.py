@@ -329,6 +329,30 @@ def srtt_y(r2: int, m: int, seed: int, row0: int = 0) -> np.ndarray:
     return hadamard_entries(rows, np.arange(m)) * d[None, :]
 
 
+def hrct_x(n: int, s: int, seed: int, rows=None) -> np.ndarray:
+    """Unscaled hashed randomized DCT right embedding, n x s: X = D F^T C^T with F
+    the DCT-II of order n_pad = 2^ceil(log2 n) scaled to entries of magnitude up to
+    sqrt(2) (sqrt(n_pad) times the orthonormal transform) and C the CountSketch of
+    hrtt_x (the same buckets {pi(k + t s)} and signs sigma_c) -- the hashed
+    randomized DCT the paper's experiments use for X (Sec. 3.4, Sec. 6).  Column k
+    of X is d * sum over its bucket of sigma_c F[c, :].  The orthonormal
+    transform's scale 1/sqrt(n_pad) is applied to the singular values afterwards."""
+    if s < 1:
+        raise ValueError("s must be positive")
+    b = next_pow2_bits(n)
+    n_pad = 1 << b
+    if s > n_pad:
+        raise ValueError("HRCT width exceeds the padded dimension (empty buckets)")
+    rows = np.arange(n) if rows is None else np.asarray(rows, dtype=np.int64)
+    d = signs(n, STREAM_DX, seed)[rows]
+    sigma = signs(n_pad, STREAM_SX, seed)
+    X = np.empty((rows.size, s), dtype=np.float64)
+    for k in range(s):
+        c = feistel_perm(np.arange(k, n_pad, s), b, STREAM_PX, seed)   # bucket k
+        X[:, k] = d * (dct_entries(c, rows, n_pad).T @ sigma[c])
+    return X
+
+
 def dct_entries(rows: np.ndarray, cols: np.ndarray, N: int) -> np.ndarray:
     """sqrt(N) times the orthonormal DCT-II matrix of order N, rows k x columns i:
     sqrt(2) w_k cos(pi (2 i + 1) k / (2 N)), w_0 = 1/sqrt(2), w_k = 1 otherwise.

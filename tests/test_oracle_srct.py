@@ -85,3 +85,45 @@ def test_rank_estimate_with_srct_left_embedding():
     A = (U * sig) @ V.T
     res = alg.rank_estimate(A, 1e-5, kind=alg.GAUSSIAN, seed=4, ykind=alg.SRCT)
     assert res.converged and res.rank == r and res.final_s == 32
+
+
+# ---- the hashed randomized DCT right embedding (Sec. 3.4; the paper's X in Sec. 6)
+
+@pytest.mark.parametrize("n,s", [(64, 8), (100, 16), (256, 32)])
+def test_hrct_columns_are_the_library_inverse_dct(n, s):
+    """Column k of X is d * sqrt(N) * (inverse orthonormal DCT-II of the bucket's
+    signed indicator): scipy's idct (type 2, orthonormal) of that vector."""
+    scipy_fft = pytest.importorskip("scipy.fft")
+    b = rng.next_pow2_bits(n)
+    N = 1 << b
+    X = rng.hrct_x(n, s, 23)
+    d = rng.signs(n, rng.STREAM_DX, 23)
+    sig = rng.signs(N, rng.STREAM_SX, 23)
+    for k in range(s):
+        v = np.zeros(N)
+        c = rng.feistel_perm(np.arange(k, N, s), b, rng.STREAM_PX, 23)
+        v[c] = sig[c]
+        ref = d * math.sqrt(N) * scipy_fft.idct(v, type=2, norm="ortho")[:n]
+        assert np.max(np.abs(X[:, k] - ref)) < 1e-10 * math.sqrt(N)
+
+
+def test_hrct_full_width_is_an_isometry_and_folds():
+    """s = n_pad (one coordinate per bucket): X^T X = n_pad I for n = n_pad.  Halving
+    the width merges bucket k with bucket k + s/2: X_{s/2}[:, k] = X_s[:, k] + X_s[:, k + s/2]."""
+    n = 128
+    X = rng.hrct_x(n, n, 4)
+    assert np.max(np.abs(X.T @ X - n * np.eye(n))) < 1e-9 * n
+    X16, X8 = rng.hrct_x(200, 16, 4), rng.hrct_x(200, 8, 4)
+    assert np.max(np.abs(X8 - (X16[:, :8] + X16[:, 8:]))) < 1e-12 * 16
+
+
+def test_hrct_rank_on_a_diagonal_matrix():
+    """Sec. 3.4 / Sec. 6: hashed embeddings keep the embedding on a diagonal (most
+    coherent) matrix: the exact rank of a gapped diagonal spectrum, with Gaussian
+    and with SRCT left embeddings."""
+    n, r = 1024, 60
+    sig = np.where(np.arange(n) < r, np.logspace(0, -1, n), 1e-10)
+    A = np.diag(sig)
+    for yk in (alg.GAUSSIAN, alg.SRCT):
+        res = alg.rank_estimate(A, 1e-6, kind=alg.HRCT, seed=3, ykind=yk)
+        assert res.converged and res.rank == r
