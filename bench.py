@@ -443,12 +443,15 @@ def main():
         # columns through the BF16x3 tensor-core contraction; hrtt_tc: the same for the
         # HRTT widths whose buckets hold at most 256 coordinates (the register transform
         # for the narrower ones); srct_y: the BF16x3 Gaussian
-        # right sketch with the DCT left embedding, the paper's pairing for the estimate
+        # right sketch with the DCT left embedding, the paper's pairing for the estimate;
+        # hrct_srct_y: the hashed randomized DCT X (FP32 entries as three BF16 terms on
+        # the tensor cores) with the SRCT Y, the pair of the paper's experiments
         variants = (("srht", rk.RE_SRHT, rk.make_opts(precision=rk.RE_PREC_FP32)),
                     ("srht_tc", rk.RE_SRHT, rk.make_opts(precision=rk.RE_PREC_BF16X3)),
                     ("hrtt", rk.RE_HRTT, rk.make_opts(precision=rk.RE_PREC_FP32)),
                     ("hrtt_tc", rk.RE_HRTT, rk.make_opts(precision=rk.RE_PREC_BF16X3)),
-                    ("srct_y", rk.RE_GAUSSIAN, rk.make_opts(precision=rk.RE_PREC_BF16X3, y_kind=rk.RE_SRCT)))
+                    ("srct_y", rk.RE_GAUSSIAN, rk.make_opts(precision=rk.RE_PREC_BF16X3, y_kind=rk.RE_SRCT)),
+                    ("hrct_srct_y", rk.RE_HRCT, rk.make_opts(precision=rk.RE_PREC_BF16X3, y_kind=rk.RE_SRCT)))
         for name, code, opts_v in variants:
             hs = rk.re_create(local, opts_v)
             rs, _ = rk.re_rank_estimate(hs, A, w["eps"], code, w["sketch_seed"], stream=stream)

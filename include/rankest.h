@@ -74,6 +74,16 @@ extern "C" {
  * sampled frequencies pi_Y(q), signs D.  Its rows are generated on the fly from a
  * cosine table (m_pad + 1 FP32 values) inside the CUDA-core left sketch. */
 #define RE_SRCT 3
+/* Hashed randomized DCT (Sec. 3.4 with F the DCT-II in place of the Hadamard
+ * transform; with the SRCT Y, the pair the paper's experiments use, Sec. 6): right
+ * embedding only, X = D (F/sqrt(n_pad)) C^T with the HRTT's CountSketch C (buckets
+ * {pi_X(k + t s)}, signs sigma_c) and D.  Every entry of X is an FP32 compensated
+ * sum of its bucket's scaled cosines, generated densely (n x s) each pass; under
+ * RE_PREC_BF16X3 the FP32 X enters the tensor cores as its three exact BF16 terms
+ * (six products, 128 columns per launch), under RE_PREC_FP32 the CUDA-core sketch.
+ * Like the HRTT it is not appendable (every doubling step sketches anew), its
+ * width is at most n_pad <= 2^15, and the left embedding defaults to Gaussian. */
+#define RE_HRCT 4
 
 /* arithmetic of the Gaussian right sketch */
 #define RE_PREC_FP32 0   /* FP32 FMA on CUDA cores */
@@ -116,8 +126,8 @@ typedef struct {
     int s0;          /* initial X width, multiple of 8 (default 8) */
     int s_max;       /* largest X width, <= 512 (default 512) */
     int precision;   /* RE_PREC_* for the Gaussian right sketch (default RE_PREC_FP32) */
-    int y_kind;      /* left embedding kind: -1 = same as the right one (Gaussian for RE_HRTT;
-                        default), RE_GAUSSIAN, RE_SRHT or RE_SRCT */
+    int y_kind;      /* left embedding kind: -1 = same as the right one (Gaussian for RE_HRTT
+                        and RE_HRCT; default), RE_GAUSSIAN, RE_SRHT or RE_SRCT */
     double norm_a;   /* > 0: use as ||A|| in the threshold; otherwise sigma^_1 (step 8) */
     int learned;     /* 1: let the sketch-size proposal network pick the next width (default 0) */
     /* Test hook for the failure path (default 0; no counterpart in the paper): when
@@ -216,10 +226,11 @@ int re_stats_get(re_handle h, re_stats* out);
  * Algorithm 1 with doubling (Sec. 5): estimate rank_eps(A).
  *   A          device pointer, m x n row-major, leading dimension ld.
  *   eps        relative tolerance in (0, 1) (Definition 1).
- *   sketch_kind RE_GAUSSIAN, RE_SRHT or RE_HRTT (right embedding; left per
- *              opts.y_kind, by default the same kind, Gaussian for RE_HRTT).
- *              RE_SRHT / RE_HRTT take min(m, n) <= 32768 (else RE_ERR_UNSUPPORTED);
- *              RE_HRTT with opts.learned is RE_ERR_UNSUPPORTED.
+ *   sketch_kind RE_GAUSSIAN, RE_SRHT, RE_HRTT or RE_HRCT (right embedding; left
+ *              per opts.y_kind, by default the same kind, Gaussian for the hashed
+ *              RE_HRTT and RE_HRCT).  RE_SRHT / RE_HRTT / RE_HRCT take min(m, n) <=
+ *              32768 (else RE_ERR_UNSUPPORTED); RE_HRTT or RE_HRCT with
+ *              opts.learned is RE_ERR_UNSUPPORTED.
  *   seed       generator key for X and Y.
  *   sigma_out  host buffer of sigma_cap doubles, receives the first
  *              min(n_sigma, sigma_cap) scaled sketched singular values
@@ -250,8 +261,9 @@ int re_rank_estimate_host(re_handle h, const void* A_host, int dtype, int64_t m,
  *        k0 .. k0+s-1 receive the UNSCALED right sketch A*G[:, k0:k0+s] (Gaussian G
  *        entries, or D H S^T entries +-1 for RE_SRHT).  Columns < k0 must hold
  *        earlier columns from the same seed when core is non-NULL.  RE_HRTT
- *        (col0 must be 0) writes the whole width-s sketch A D H C^T (unscaled:
- *        the caller applies 1/sqrt(N), N = 2^ceil(log2 min(m, n))).
+ *        (col0 must be 0) writes the whole width-s sketch A D H C^T, RE_HRCT
+ *        (col0 = 0) A D F^T C^T with F the DCT-II scaled to entries up to sqrt(2)
+ *        (both unscaled: the caller applies 1/sqrt(N), N = 2^ceil(log2 min(m, n))).
  *   core optional device FP64, (2 (k0+s)) x ld_core row-major: on entry its
  *        leading 2 k0 x k0 block holds the previous unscaled core; on return the
  *        leading 2(k0+s) x (k0+s) block holds Y[0:2(k0+s)] * A * X[:, 0:k0+s].
@@ -302,7 +314,8 @@ int re_core_sigma_exact(re_handle h, const double* core, int r2, int s, int64_t 
  * explicitly (the estimator never materialises them this way):
  *   re_embedding_x: out (device FP32, n x s row-major) = columns col0.. of the
  *                   unscaled X (n = number of columns of the oriented A); for
- *                   RE_HRTT col0 = 0 and the s columns of the width-s X.
+ *                   RE_HRTT and RE_HRCT col0 = 0 and the s columns of the
+ *                   width-s X.
  *   re_embedding_y: out (device FP32, r2 x m row-major) = rows row0.. of the
  *                   unscaled Y (m = number of rows of the oriented A).
  */

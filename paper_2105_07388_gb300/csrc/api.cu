@@ -55,6 +55,7 @@ struct re_handle_ {
     DevBuf x, xt, ax, part, core, sigma, sigma_scaled, svdws, acopy, dx, px, dy, py, ro, status, ht, fz;
     DevBuf qbws, qbsel;                 // Algorithm 3: factorization workspace, selection record
     DevBuf ctab;                        // cosine table of the SRCT left embedding
+    DevBuf ctabx;                       // cosine table of the HRCT right embedding
     // precision mode (exact-product sketches): row exponents of A, digit slices of X
     // and Y, int64 accumulators of the right and left sketches, A X as FP32 pair planes
     // (transposed) with column exponents, and the precise singular-value scratch
@@ -170,8 +171,12 @@ int r1_of_s(int s) {
 // coherent as A's, where a sampled Hadamard Y aliases).
 int left_kind(re_handle h, int kind) {
     if (h->opts.y_kind >= 0) return h->opts.y_kind;
-    return kind == RE_HRTT ? RE_GAUSSIAN : kind;
+    return kind == RE_HRTT || kind == RE_HRCT ? RE_GAUSSIAN : kind;
 }
+
+// Hashed right embeddings (HRTT, HRCT): every column depends on the width, so a
+// wider sketch is formed anew from column 0, and the width is at most n_pad.
+bool hashed(int kind) { return kind == RE_HRTT || kind == RE_HRCT; }
 
 struct Plan {
     re::MatView A;
@@ -189,7 +194,7 @@ int make_plan(const void* A, int dtype, int64_t m, int64_t n, int64_t ld, int ki
     if (m <= 0 || n <= 0) return fail(RE_ERR_ARG, "m and n must be positive");
     if (ld < n) return fail(RE_ERR_ARG, "ld < n");
     if (m > INT32_MAX || n > INT32_MAX) return fail(RE_ERR_ARG, "dimension too large");
-    if (kind != RE_GAUSSIAN && kind != RE_SRHT && kind != RE_HRTT) return fail(RE_ERR_ARG, "unknown sketch kind");
+    if (kind != RE_GAUSSIAN && kind != RE_SRHT && !hashed(kind)) return fail(RE_ERR_ARG, "unknown sketch kind");
     if (ykind != RE_GAUSSIAN && ykind != RE_SRHT && ykind != RE_SRCT) return fail(RE_ERR_ARG, "unknown left sketch kind");
     p->A.ptr = A;
     p->A.dtype = dtype;
@@ -204,9 +209,9 @@ int make_plan(const void* A, int dtype, int64_t m, int64_t n, int64_t ld, int ki
     p->n_pad = int64_t(1) << p->nbits;
     p->m_pad = int64_t(1) << p->mbits;
     if (kind != RE_GAUSSIAN && p->nbits > 15)
-        return fail(RE_ERR_UNSUPPORTED, "right Hadamard transforms of more than 2^15 points are not built");
+        return fail(RE_ERR_UNSUPPORTED, "right transforms of more than 2^15 points are not built");
     int64_t cap = s_max;
-    if (kind == RE_SRHT || kind == RE_HRTT) cap = std::min<int64_t>(cap, p->n_pad);   // HRTT: no empty bucket
+    if (kind == RE_SRHT || hashed(kind)) cap = std::min<int64_t>(cap, p->n_pad);   // hashed: no empty bucket
     if (ykind == RE_SRHT || ykind == RE_SRCT) cap = std::min<int64_t>(cap, p->m_pad / 2);
     p->cap = (int)cap;
     return RE_OK;
@@ -401,6 +406,66 @@ int right_columns(re_handle h, const Plan& P, uint64_t seed, int c0, int cnt, fl
         cudaEvent_t a = stage_begin(h, st);
         e = re::launch_right_simt(P.A, static_cast<const float*>(h->x.p), cnt, cnt, AX + c0, ld_ax, st);
         if (e != cudaSuccess) return cuda_fail(e, "right sketch (FP32)");
+        stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 4), 2.0 * P.A.rows * P.A.cols * cnt);
+        h->stats.launches += 2;
+        return RE_OK;
+    }
+    if (P.kind == RE_HRCT) {
+        // hashed randomized DCT of width cnt: X = D F^T C^T generated densely, each entry
+        // a compensated FP32 sum over its bucket's scaled cosines (columns depend on
+        // the width: c0 is where AX receives them)
+        if (int r = ensure(h->dx, sizeof(uint32_t) * (size_t)(P.n_pad / 32 + 1))) return r;
+        if (int r = ensure(h->ht, sizeof(uint16_t) * (size_t)P.n_pad)) return r;
+        if (int r = ensure(h->ctabx, sizeof(float) * (size_t)(P.n_pad + 1))) return r;
+        if (int r = ensure(h->status, 64)) return r;
+        cudaEvent_t g = stage_begin(h, st);
+        e = re::launch_sign_bits(seed, re::kStreamDX, P.A.cols, static_cast<uint32_t*>(h->dx.p), st);
+        if (e == cudaSuccess) e = re::launch_hrtt_table(seed, P.nbits, static_cast<uint16_t*>(h->ht.p), st);
+        if (e == cudaSuccess) e = re::launch_cos_table(P.nbits, static_cast<float*>(h->ctabx.p), st);
+        stage_end(h, st, g, kStageOther);
+        if (e != cudaSuccess) return cuda_fail(e, "generate X (HRCT)");
+        h->stats.launches += 3;
+        const uint32_t* dx = static_cast<const uint32_t*>(h->dx.p);
+        const uint16_t* tbl = static_cast<const uint16_t*>(h->ht.p);
+        const float* ctab = static_cast<const float*>(h->ctabx.p);
+        const bool tc = h->opts.precision == RE_PREC_BF16X3 && re::tc_supported(P.A) && (ld_ax % 4) == 0 &&
+                        (reinterpret_cast<uintptr_t>(AX + c0) & 15) == 0;
+        if (tc) {
+            // the FP32 X as its three exact BF16 terms: six products per K step, 128
+            // columns per launch (shared memory holds three planes of 128 rows)
+            const int64_t kpad = (P.A.cols + 63) / 64 * 64;
+            for (int j0 = 0; j0 < cnt; j0 += 128) {
+                const int w = std::min(128, cnt - j0);
+                const int nrows = re::tc_mma_n(w);
+                if (int r = ensure(h->xt, sizeof(uint16_t) * (size_t)kpad * nrows * 3)) return r;
+                cudaEvent_t g2 = stage_begin(h, st);
+                for (int pl = 0; pl < 3 && e == cudaSuccess && nrows > w; ++pl)
+                    e = cudaMemsetAsync(static_cast<uint16_t*>(h->xt.p) + (size_t)kpad * ((size_t)pl * nrows + w), 0,
+                                        sizeof(uint16_t) * (size_t)kpad * (nrows - w), st);
+                if (e == cudaSuccess)
+                    e = re::launch_hrct_x(P.A.cols, kpad, cnt, j0, w, P.nbits, dx, tbl, ctab, 3, nullptr,
+                                          static_cast<uint16_t*>(h->xt.p), kpad, nrows, st);
+                stage_end(h, st, g2, kStageOther);
+                if (e != cudaSuccess) return cuda_fail(e, "generate X (HRCT)");
+                cudaEvent_t a2 = stage_begin(h, st);
+                int nl = 0;
+                e = re::launch_right_tc(P.A, static_cast<const uint16_t*>(h->xt.p), kpad, w, AX + c0 + j0, ld_ax,
+                                        static_cast<int*>(h->status.p) + 1, st, &nl, h->opts.test_drop_load, 3);
+                if (e != cudaSuccess) return cuda_fail(e, "right sketch (HRCT, tensor cores)");
+                stage_end(h, st, a2, kStageRight, right_bytes(P, w, 6), 6.0 * 2.0 * P.A.rows * P.A.cols * w);
+                h->stats.launches += 1 + nl;
+            }
+            return RE_OK;
+        }
+        if (int r = ensure(h->x, sizeof(float) * (size_t)P.A.cols * cnt)) return r;
+        cudaEvent_t g2 = stage_begin(h, st);
+        e = re::launch_hrct_x(P.A.cols, 0, cnt, 0, cnt, P.nbits, dx, tbl, ctab, 0, static_cast<float*>(h->x.p),
+                              nullptr, cnt, 0, st);
+        stage_end(h, st, g2, kStageOther);
+        if (e != cudaSuccess) return cuda_fail(e, "generate X (HRCT)");
+        cudaEvent_t a = stage_begin(h, st);
+        e = re::launch_right_simt(P.A, static_cast<const float*>(h->x.p), cnt, cnt, AX + c0, ld_ax, st);
+        if (e != cudaSuccess) return cuda_fail(e, "right sketch (HRCT, FP32)");
         stage_end(h, st, a, kStageRight, right_bytes(P, cnt, 4), 2.0 * P.A.rows * P.A.cols * cnt);
         h->stats.launches += 2;
         return RE_OK;
@@ -618,8 +683,9 @@ int check_width(re_handle h, const Plan& P, int s, int smax, double eps, re::Dev
     const bool skip_ok = may_skip && h->opts.norm_a <= 0.0 && r1c < P.A.cols;
     const float ratio = (float)(4.0 * std::max(eps, 1e-5));
     const int r1 = std::min(r1_of_s(s), s);
-    // X = G/sqrt(s) or D H S^T/sqrt(s); the HRTT's D (H/sqrt(n_pad)) C^T; Y scaled by 1/sqrt(2s)
-    const double xs = P.kind == RE_HRTT ? (double)P.n_pad : (double)s;
+    // X = G/sqrt(s) or D H S^T/sqrt(s); the hashed forms' D (F/sqrt(n_pad)) C^T with F the
+    // Hadamard or the scaled DCT-II; Y scaled by 1/sqrt(2s)
+    const double xs = hashed(P.kind) ? (double)P.n_pad : (double)s;
     const double scale = 1.0 / std::sqrt(xs * (double)(2 * s));
     // the precision mode takes the preconditioned FP32 singular values (stage 1 is
     // the plain FP32 step, which may first certify that this width cannot succeed)
@@ -695,7 +761,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
     const re_opts& o = h->opts;
     if (o.s0 > P.cap) return fail(RE_ERR_ARG, "initial sketch width exceeds the admissible width");
     if (o.learned && !h->mlp_ready) return fail(RE_ERR_ARG, "learned proposal requested but no network is loaded");
-    if (o.learned && P.kind == RE_HRTT)
+    if (o.learned && hashed(P.kind))
         return fail(RE_ERR_UNSUPPORTED, "the proposal network needs an appendable embedding (Gaussian or SRHT)");
     int smax = o.s0;
     while (smax * 2 <= P.cap) smax *= 2;
@@ -795,7 +861,7 @@ int run_estimate(re_handle h, const Plan& P, double eps, uint64_t seed, double* 
         }
     }
     while (!done) {
-        if (int r = sketch_to(P.kind == RE_HRTT ? 0 : s_prev, s)) return r;
+        if (int r = sketch_to(hashed(P.kind) ? 0 : s_prev, s)) return r;
         ++passes;
         if (int r = check_width(h, P, s, smax, eps, &ro, &r1, st, 2 * s <= smax)) return r;
         if (ro.rank >= 0 || 2 * s > smax || r1 >= P.A.cols) break;
@@ -997,7 +1063,7 @@ int re_destroy(re_handle h) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&h->x, &h->xt, &h->ax, &h->part, &h->core, &h->sigma, &h->sigma_scaled,
                       &h->svdws, &h->acopy, &h->dx, &h->px, &h->dy, &h->py, &h->ro, &h->status, &h->ht, &h->fz,
-                      &h->qbws, &h->qbsel, &h->ctab,
+                      &h->qbws, &h->qbsel, &h->ctab, &h->ctabx,
                       &h->ex_rexp, &h->ex_xd, &h->ex_tr, &h->ex_hi, &h->ex_lo, &h->ex_cexp, &h->ex_yd, &h->ex_tc,
                       &h->ex_svd,
                       &h->mlp_P, &h->mlp_M, &h->mlp_V, &h->mlp_G, &h->mlp_X, &h->mlp_y,
@@ -1154,10 +1220,10 @@ int re_sketch_apply(re_handle h, const void* A, int dtype, int64_t m, int64_t n,
     const int ykind = left_kind(h, sketch_kind);
     Plan P;
     if (int r = make_plan(A, dtype, m, n, ld, sketch_kind, ykind, 1 << 30, &P)) return r;
-    if ((sketch_kind == RE_SRHT || sketch_kind == RE_HRTT) && col0 + s > P.n_pad)
-        return fail(RE_ERR_ARG, "SRHT/HRTT width exceeds the padded dimension");
-    if (sketch_kind == RE_HRTT && col0 != 0)
-        return fail(RE_ERR_ARG, "HRTT columns depend on the width: col0 must be 0");
+    if ((sketch_kind == RE_SRHT || hashed(sketch_kind)) && col0 + s > P.n_pad)
+        return fail(RE_ERR_ARG, "SRHT/HRTT/HRCT width exceeds the padded dimension");
+    if (hashed(sketch_kind) && col0 != 0)
+        return fail(RE_ERR_ARG, "HRTT/HRCT columns depend on the width: col0 must be 0");
     if (core && ykind == RE_SRHT && 2 * (int64_t)(col0 + s) > P.m_pad)
         return fail(RE_ERR_ARG, "SRHT left width exceeds the padded dimension");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1276,6 +1342,21 @@ int re_embedding_x(re_handle h, int kind, uint64_t seed, int64_t n, int col0, in
         if (e == cudaSuccess)
             e = re::launch_hrtt_x_dense(n, s, bits, static_cast<const uint32_t*>(h->dx.p),
                                         static_cast<const uint16_t*>(h->ht.p), out, s, st);
+    } else if (kind == RE_HRCT) {
+        const int bits = re::pow2_bits(n);
+        if (bits > 15) return fail(RE_ERR_UNSUPPORTED, "HRCT of more than 2^15 points");
+        if (col0 != 0) return fail(RE_ERR_ARG, "HRCT columns depend on the width: col0 must be 0");
+        if (s > (int64_t(1) << bits)) return fail(RE_ERR_ARG, "HRCT width exceeds the padded dimension");
+        if (int r = ensure(h->dx, sizeof(uint32_t) * (size_t)((int64_t(1) << bits) / 32 + 1))) return r;
+        if (int r = ensure(h->ht, sizeof(uint16_t) * (size_t)(int64_t(1) << bits))) return r;
+        if (int r = ensure(h->ctabx, sizeof(float) * (size_t)((int64_t(1) << bits) + 1))) return r;
+        e = re::launch_sign_bits(seed, re::kStreamDX, n, static_cast<uint32_t*>(h->dx.p), st);
+        if (e == cudaSuccess) e = re::launch_hrtt_table(seed, bits, static_cast<uint16_t*>(h->ht.p), st);
+        if (e == cudaSuccess) e = re::launch_cos_table(bits, static_cast<float*>(h->ctabx.p), st);
+        if (e == cudaSuccess)
+            e = re::launch_hrct_x(n, 0, s, 0, s, bits, static_cast<const uint32_t*>(h->dx.p),
+                                  static_cast<const uint16_t*>(h->ht.p), static_cast<const float*>(h->ctabx.p), 0,
+                                  out, nullptr, s, 0, st);
     } else {
         return fail(RE_ERR_ARG, "unknown kind");
     }

@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace re {
 
@@ -280,6 +281,123 @@ cudaError_t launch_hrtt_xt_bf16(int64_t n, int64_t kpad, int s, int j0, int cnt,
     cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(hrtt_xt_bf16_kernel));
     if (e != cudaSuccess) return e;
     hrtt_xt_bf16_kernel<<<cnt, 1024, smem, st>>>(n, kpad, s, j0, bits, dbits, tbl, Xt, ldt, planes, plane_rows);
+    return cudaGetLastError();
+}
+
+// Columns j0 .. j0+cnt-1 of the width-s hashed randomized DCT X (order N = 2^bits):
+// X[k][j] = d_k sum over bucket j of sigma_c sqrt(2) w_c cos(pi (2k+1) c / 2N)
+// (w_0 = 1/sqrt(2)).  The cosines come from the table cos(pi i / 2N), i in [0, N],
+// held in shared memory, after the phase (2k+1) c is reduced modulo 4N in integers
+// and folded onto [0, N].  Rows k and N-1-k take the same table entry: their
+// phases differ by c (2N) - (2k+1) c, so their cosines differ by the sign (-1)^c.
+// A thread forms both rows of one pair, each as an FP32 sum with a compensation
+// term (Kahan), so the value is close to the correctly rounded sum.  Work items
+// are (bucket, chunk of blockDim pairs), spread over a persistent grid.
+// planes = 0: FP32 X row-major (X[k * ldx + j - j0], rows k < n); planes = 3: the
+// three exact BF16 terms of the FP32 value as X^T planes (row j - j0 of plane t at
+// Xt + (t * plane_rows + j - j0) * ldx, columns k < kpad, zeros for n <= k).
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+__device__ __forceinline__ void hrct_store(int planes, float v, int64_t k, int jj, float* X, uint16_t* Xt,
+                                           int64_t ldx, int64_t plane_rows) {
+    if (planes == 0) {
+        X[k * ldx + jj] = v;
+    } else {
+        uint32_t hi, mid, lo;
+        tc::split3(v, 0.f, hi, mid, lo);       // the low halves hold the terms of v
+        Xt[(int64_t)jj * ldx + k] = (uint16_t)(hi & 0xffffu);
+        Xt[(plane_rows + jj) * ldx + k] = (uint16_t)(mid & 0xffffu);
+        Xt[(2 * plane_rows + jj) * ldx + k] = (uint16_t)(lo & 0xffffu);
+    }
+}
+
+__global__ void __launch_bounds__(512) hrct_x_kernel(int64_t n, int64_t kpad, int s, int j0, int cnt, int bits,
+                                                     const uint32_t* __restrict__ dbits,
+                                                     const uint16_t* __restrict__ tbl,
+                                                     const float* __restrict__ ctab, int planes,
+                                                     float* __restrict__ X, uint16_t* __restrict__ Xt, int64_t ldx,
+                                                     int64_t plane_rows) {
+    extern __shared__ float smf[];
+    const int N = 1 << bits;
+    float* ct = smf;                                              // N + 1 cosines
+    uint16_t* bucket = reinterpret_cast<uint16_t*>(smf + N + 1);  // ceil(N / s) entries
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) ct[i] = ctab[i];
+    const int64_t kend = planes == 0 ? n : kpad;
+    const int kcov = (int)(kend < (int64_t)N ? kend : (int64_t)N);  // rows below N
+    const int P = (N + 1) / 2 < kcov ? (N + 1) / 2 : kcov;           // pairs (k, N-1-k)
+    const int chunks = (P + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int items = cnt * chunks;
+    const uint32_t twoN = 2u * (uint32_t)N, fourN = 4u * (uint32_t)N, mask = fourN - 1u;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int jj = item / chunks, chunk = item - jj * chunks;
+        const int j = j0 + jj;
+        const int L = (N - j + s - 1) / s;                        // entries q = j + t s < N
+        __syncthreads();                                          // the previous bucket is no longer read
+        for (int t = threadIdx.x; t < L; t += blockDim.x) bucket[t] = tbl[j + t * s];
+        __syncthreads();
+        const int p = chunk * (int)blockDim.x + (int)threadIdx.x;
+        if (p >= P) continue;                                     // every thread runs the same items
+        const int k = p, km = N - 1 - p;
+        const bool vk = k < n, vm = km != k && km < n;
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+        if (vk || vm) {
+            const uint32_t odd = 2u * (uint32_t)k + 1u;           // < 2^16, c < 2^15: no overflow
+            for (int t = 0; t < L; ++t) {
+                const uint32_t e = bucket[t];
+                const uint32_t c = e & 0x7fffu;
+                uint32_t ph = (odd * c) & mask;
+                if (ph > twoN) ph = fourN - ph;
+                const float cv = ph <= (uint32_t)N ? ct[ph] : -ct[twoN - ph];
+                float term = c == 0 ? 1.f : 1.41421356237309515f * cv;
+                if (e >> 15) term = -term;
+                kahan_add(s0, c0, term);
+                kahan_add(s1, c1, (c & 1u) ? -term : term);
+            }
+        }
+        if (k < kend) {
+            const float v = vk ? (((dbits[k >> 5] >> (k & 31)) & 1u) ? -s0 : s0) : 0.f;
+            hrct_store(planes, v, k, jj, X, Xt, ldx, plane_rows);
+        }
+        if (km != k && km < kend) {
+            const float v = vm ? (((dbits[km >> 5] >> (km & 31)) & 1u) ? -s1 : s1) : 0.f;
+            hrct_store(planes, v, km, jj, X, Xt, ldx, plane_rows);
+        }
+    }
+    // rows N .. kend-1 (a padded X^T wider than the order): zeros
+    const int64_t extra = kend > (int64_t)N ? kend - N : 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < extra * cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        hrct_store(planes, 0.f, N + i % extra, (int)(i / extra), X, Xt, ldx, plane_rows);
+}
+
+cudaError_t launch_hrct_x(int64_t n, int64_t kpad, int s, int j0, int cnt, int bits, const uint32_t* dbits,
+                          const uint16_t* tbl, const float* ctab, int planes, float* X, uint16_t* Xt, int64_t ldx,
+                          int64_t plane_rows, cudaStream_t st) {
+    if (cnt <= 0) return cudaSuccess;
+    if (bits < 0 || bits > 15 || s <= 0 || j0 < 0 || j0 + cnt > s || n <= 0 || n > (int64_t(1) << bits) ||
+        (planes != 0 && planes != 3) || (planes == 0 && ldx < cnt) || (planes == 3 && (plane_rows < cnt || kpad < n ||
+        ldx < kpad)))
+        return cudaErrorInvalidValue;
+    const int N = 1 << bits;
+    const size_t smem = sizeof(float) * (size_t)(N + 1) + sizeof(uint16_t) * (size_t)((N + s - 1) / s) + 16;
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(hrct_x_kernel));
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hrct_x_kernel, 512, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t kend = planes == 0 ? n : kpad;
+    const int64_t P = std::min<int64_t>((N + 1) / 2, std::min<int64_t>(kend, N));
+    const int64_t items = (int64_t)cnt * ((P + 511) / 512);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * std::max(per_sm, 1)));
+    hrct_x_kernel<<<grid, 512, smem, st>>>(n, kpad, s, j0, cnt, bits, dbits, tbl, ctab, planes, X, Xt, ldx,
+                                           plane_rows);
     return cudaGetLastError();
 }
 

@@ -72,6 +72,14 @@ cudaError_t launch_srtt_y_dense(int64_t m, int r2, const uint32_t* dbits, const 
                                 int64_t ldy, cudaStream_t st);
 // HRTT hashing table of 2^bits entries (bits <= 15): entry q = pi_X(q) | (sigma < 0) << 15.
 cudaError_t launch_hrtt_table(uint64_t seed, int bits, uint16_t* tbl, cudaStream_t st);
+// Columns j0 .. j0+cnt-1 of the width-s hashed randomized DCT X (order 2^bits, the HRTT's
+// buckets and signs from tbl, cosines from ctab = launch_cos_table(bits)): planes = 0
+// writes FP32 X row-major (ldx, column j - j0); planes = 3 writes the three exact BF16
+// terms of the FP32 values as X^T planes of plane_rows rows (row pitch ldx, zeros for
+// n <= k < kpad).
+cudaError_t launch_hrct_x(int64_t n, int64_t kpad, int s, int j0, int cnt, int bits, const uint32_t* dbits,
+                          const uint16_t* tbl, const float* ctab, int planes, float* X, uint16_t* Xt, int64_t ldx,
+                          int64_t plane_rows, cudaStream_t st);
 // Rows j0 .. j0+cnt-1 of the width-s HRTT's X^T as BF16 bits (kpad per row, zero past
 // n): Xt[j - j0][k] = d_k sum over bucket j of sigma_c H[k, c].  planes = 1: exact when
 // every bucket holds at most 256 coordinates (2^bits <= 256 s); planes = 2: the

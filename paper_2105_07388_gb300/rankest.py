@@ -29,6 +29,7 @@ RE_GAUSSIAN = 0
 RE_SRHT = 1
 RE_HRTT = 2
 RE_SRCT = 3
+RE_HRCT = 4
 RE_PREC_FP32 = 0
 RE_PREC_BF16X3 = 1
 RE_PREC_EXACT = 2
