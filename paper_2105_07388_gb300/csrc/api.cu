@@ -624,8 +624,13 @@ int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const
         if (int r = ensure(h->dy, sizeof(uint32_t) * (size_t)(P.m_pad / 32 + 1))) return r;
         if (int r = ensure(h->py, sizeof(int) * (size_t)(2 * c1))) return r;
         if (int r = ensure(h->ctab, sizeof(float) * (size_t)(P.m_pad + 1))) return r;
-        const size_t needc = std::max(re::left_part_floats(M, 2 * (c1 - c0), c0), re::left_part_floats(M, 2 * c1, c1 - c0));
+        const size_t needc = std::max({re::left_part_floats(M, 2 * (c1 - c0), c0),
+                                       re::left_part_floats(M, 2 * c1, c1 - c0),
+                                       re::left_tc_part_floats(M, 2 * (c1 - c0), c0, true),
+                                       re::left_tc_part_floats(M, 2 * c1, c1 - c0, true)});
         if (int r = ensure(h->part, sizeof(float) * needc)) return r;
+        if (int r = ensure(h->status, 64)) return r;
+        int* tmo = static_cast<int*>(h->status.p) + 1;   // bounded-wait expiry flag of the tensor-core kernels
         cudaEvent_t g = stage_begin(h, st);
         cudaError_t e = re::launch_sign_bits(seed, re::kStreamDY, M, static_cast<uint32_t*>(h->dy.p), st);
         if (e == cudaSuccess)
@@ -638,9 +643,15 @@ int left_blocks(re_handle h, const Plan& P, uint64_t seed, int c0, int c1, const
         cudaEvent_t a = stage_begin(h, st);
         float* part = static_cast<float*>(h->part.p);
         const size_t cap = h->part.cap / sizeof(float);
-        if (c0 > 0) e = re::launch_left_dct(Yd, AX, ld_ax, M, 2 * c0, 2 * (c1 - c0), 0, c0, part, cap, core, ld_core, st);
+        // on the tensor cores when AX is aligned (Y and AX as three exact BF16 terms
+        // each, six products, FP32 accumulation: the numerics of an FP32 product, as
+        // for the Gaussian Y), else on CUDA cores
+        int* tflag = tmo;
+        if (c0 > 0)
+            e = re::launch_left_dct(Yd, AX, ld_ax, M, 2 * c0, 2 * (c1 - c0), 0, c0, part, cap, core, ld_core, st,
+                                    tflag);
         if (e == cudaSuccess)
-            e = re::launch_left_dct(Yd, AX, ld_ax, M, 0, 2 * c1, c0, c1 - c0, part, cap, core, ld_core, st);
+            e = re::launch_left_dct(Yd, AX, ld_ax, M, 0, 2 * c1, c0, c1 - c0, part, cap, core, ld_core, st, tflag);
         if (e != cudaSuccess) return cuda_fail(e, "left sketch (SRCT)");
         stage_end(h, st, a, kStageLeft);
         h->stats.launches += 3 + (c0 > 0 ? 4 : 2);

@@ -119,9 +119,12 @@ struct DctRows {
 // ctab[j] = cos(pi j / 2^(nbits+1)) for j in [0, 2^nbits] (FP32 from FP64 cospi).
 cudaError_t launch_cos_table(int nbits, float* ctab, cudaStream_t st);
 // core[row0+r][col0+c] (FP64) = sum_i Y[row0+r][i] AX[i][col0+c], Y the SRCT rows
-// above, on CUDA cores (FP32 split-K partials in `part`, summed as for launch_left).
+// above (FP32 split-K partials in `part`, summed as for launch_left).  With a
+// non-null err_flag, blocks of aligned AX run on the tensor cores (Y as three BF16
+// terms; left_tc.cu) when `part` holds that kernel's partials, else on CUDA cores.
 cudaError_t launch_left_dct(const DctRows& Y, const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0,
-                            int S, float* part, size_t part_cap, double* core, int64_t ld_core, cudaStream_t st);
+                            int S, float* part, size_t part_cap, double* core, int64_t ld_core, cudaStream_t st,
+                            int* err_flag = nullptr);
 
 // ---- left sketch with the SRTT Y by fast transforms (left_fwht.cu) ------------
 // Z[i][c] = (H D AX)[i][c] for c in [c0, c1) and i < 2^mbits (Z row-major, ldz >= c1,
@@ -134,11 +137,12 @@ cudaError_t launch_left_srtt_sample(const float* Z, int64_t ldz, const int* perm
 
 // ---- left sketch on the tensor cores (left_tc.cu) -----------------------------
 bool left_tc_supported(const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0, int S);
-size_t left_tc_part_floats(int64_t M, int R, int S);
+size_t left_tc_part_floats(int64_t M, int R, int S, bool dct = false);
 // FP32 split-K partials part[split][R][S] of the block; *splits_out = splits used.
+// dct non-null: Y is the SRCT of those rows (three BF16 terms, six products).
 cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0, int R,
                                     int col0, int S, float* part, size_t part_cap, int* err_flag, int* splits_out,
-                                    cudaStream_t st);
+                                    cudaStream_t st, const DctRows* dct = nullptr);
 
 // Batched right sketch on the tensor cores (batched_tc.cu), BF16x3 as in
 // right_tc_kernel: for every active block b and each of its 128-row tiles,

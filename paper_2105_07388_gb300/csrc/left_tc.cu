@@ -1,5 +1,5 @@
-// Left sketch on the tensor cores (Algorithm 1 steps 4-6 for a Gaussian Y): a
-// block of the core Y (AX), computed transposed so that AX is the MMA's A
+// Left sketch on the tensor cores (Algorithm 1 steps 4-6 for a Gaussian or an
+// SRCT Y): a block of the core Y (AX), computed transposed so that AX is the MMA's A
 // operand.  For an M tile of 128 AX columns c, an N tile of up to 256 Y rows q
 // and a range of AX rows i (split-K):
 //
@@ -11,6 +11,13 @@
 // (Y never exists in HBM).  Products are exact; the FP32 accumulation in TMEM is
 // the only rounding.  Each CTA writes its FP32 partial block, and the split-K
 // partials are summed in FP64 in a fixed order afterwards.
+//
+// SRCT Y (the DCT-II rows of the sampled frequencies, Sec. 4 with eta = 2): an
+// entry d_i sqrt(2) cos(pi (2i+1) k / 2N) is an FP32 value from the cosine table,
+// so it enters as its three exact BF16 terms (three B planes per stage) and six
+// products are issued per K step, the pairs of A and Y terms whose indices sum to
+// at most 2 (as the three-plane right sketch).  N is at most 128 there, so that
+// three planes of two stages fit in shared memory.
 //
 // Warp roles (576 threads, one CTA per SM):
 //   warps 0-15   workers: for each 64-row chunk, warp w first generates its
@@ -53,6 +60,7 @@ static_assert(kLAStageCol + 96 * kLStages <= kLTmemCols, "TMEM budget");
 
 struct LeftTcParams {
     uint64_t seed;
+    DctRows dct;        // SRCT rows (DCT mode only)
     int64_t M;          // AX rows
     int row0;           // first Y row of the block (a multiple of 4)
     int R;              // Y rows in the block
@@ -65,6 +73,19 @@ struct LeftTcParams {
     int* err;
 };
 
+// Entry (q, i) of the SRCT left embedding from its row frequency k and sign d: the
+// phase (2i+1) k is reduced modulo 4N (4N divides 2^32, so the wrapped 32-bit
+// product has the right residue) and folded onto [0, N].
+__device__ __forceinline__ float dct_y_entry(const DctRows& Y, uint32_t k, uint32_t i, float d) {
+    if (k == 0) return d;
+    const uint32_t N = 1u << Y.nbits, twoN = 2u * N, fourN = 4u * N;
+    uint32_t ph = ((2u * i + 1u) * k) & (fourN - 1u);
+    if (ph > twoN) ph = fourN - ph;
+    const float c = ph <= N ? __ldg(Y.ctab + ph) : -__ldg(Y.ctab + (twoN - ph));
+    return 1.41421356237309515f * c * d;
+}
+
+template <bool DCT>
 __global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_constant__ CUtensorMap amap,
                                                                const LeftTcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -83,7 +104,9 @@ __global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_cons
     const int64_t i_end = std::min<int64_t>(p.M, i_begin + p.chunk);
     const int64_t nchunks = i_end > i_begin ? (i_end - i_begin + kLBK - 1) / kLBK : 0;
     const uint32_t half_bytes = (uint32_t)p.boxw * 32u * 4u;
-    const uint32_t y_stage = ((uint32_t)p.N * 128u + 1023u) & ~1023u;
+    constexpr int kYTerms = DCT ? 3 : 1;
+    const uint32_t y_plane = ((uint32_t)p.N * 128u + 1023u) & ~1023u;
+    const uint32_t y_stage = y_plane * (uint32_t)kYTerms;
     unsigned char* abuf = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* ybuf = abuf + (size_t)kLAStages * ((kLBM * 32 * 4 + 1023) & ~1023);
@@ -132,25 +155,46 @@ __global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_cons
             // Y share: groups of 4 rows
             unsigned char* yb = ybuf + (size_t)s * y_stage;
             const int64_t i0 = i_begin + g * kLBK + 2 * lane;
-            for (int grp = warp; grp < p.N / 4; grp += kLWork) {
-                float z0[4], z1[4];
-                if (4 * grp < rows_here && i0 < p.M) {
-                    normals4((uint32_t)i0, q4_base + (uint32_t)grp, kStreamGY, p.seed, z0);
-                } else {
-                    z0[0] = z0[1] = z0[2] = z0[3] = 0.f;
+            if constexpr (DCT) {
+                // one row per step: lane l forms the entries i0 = 2l, 2l+1 of the chunk
+                const uint32_t db = i0 < p.M ? __ldg(p.dct.dbits + (i0 >> 5)) : 0u;   // i0 even: one word
+                const float d0 = ((db >> (i0 & 31)) & 1u) ? -1.f : 1.f;
+                const float d1 = ((db >> ((i0 + 1) & 31)) & 1u) ? -1.f : 1.f;
+                const int qrow = p.row0 + nt * p.N;
+                for (int ql = warp; ql < p.N; ql += kLWork) {
+                    uint32_t wh = 0u, wm = 0u, wl = 0u;
+                    if (ql < rows_here) {
+                        const uint32_t k = (uint32_t)__ldg(p.dct.krow + qrow + ql);
+                        const float e0 = i0 < p.M ? dct_y_entry(p.dct, k, (uint32_t)i0, d0) : 0.f;
+                        const float e1 = i0 + 1 < p.M ? dct_y_entry(p.dct, k, (uint32_t)(i0 + 1), d1) : 0.f;
+                        split3(e0, e1, wh, wm, wl);
+                    }
+                    const size_t off = (size_t)ql * 128 + ((chunk16 ^ (ql & 7)) << 4) + in_seg;
+                    *reinterpret_cast<uint32_t*>(yb + off) = wh;
+                    *reinterpret_cast<uint32_t*>(yb + y_plane + off) = wm;
+                    *reinterpret_cast<uint32_t*>(yb + 2 * (size_t)y_plane + off) = wl;
                 }
-                if (4 * grp < rows_here && i0 + 1 < p.M) {
-                    normals4((uint32_t)(i0 + 1), q4_base + (uint32_t)grp, kStreamGY, p.seed, z1);
-                } else {
-                    z1[0] = z1[1] = z1[2] = z1[3] = 0.f;
-                }
+            } else {
+                for (int grp = warp; grp < p.N / 4; grp += kLWork) {
+                    float z0[4], z1[4];
+                    if (4 * grp < rows_here && i0 < p.M) {
+                        normals4((uint32_t)i0, q4_base + (uint32_t)grp, kStreamGY, p.seed, z0);
+                    } else {
+                        z0[0] = z0[1] = z0[2] = z0[3] = 0.f;
+                    }
+                    if (4 * grp < rows_here && i0 + 1 < p.M) {
+                        normals4((uint32_t)(i0 + 1), q4_base + (uint32_t)grp, kStreamGY, p.seed, z1);
+                    } else {
+                        z1[0] = z1[1] = z1[2] = z1[3] = 0.f;
+                    }
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int ql = 4 * grp + e;
-                    const uint32_t w = ql < rows_here
-                                           ? ((__float_as_uint(z0[e]) >> 16) | (__float_as_uint(z1[e]) & 0xFFFF0000u))
-                                           : 0u;
-                    *reinterpret_cast<uint32_t*>(yb + (size_t)ql * 128 + ((chunk16 ^ (ql & 7)) << 4) + in_seg) = w;
+                    for (int e = 0; e < 4; ++e) {
+                        const int ql = 4 * grp + e;
+                        const uint32_t w = ql < rows_here
+                                               ? ((__float_as_uint(z0[e]) >> 16) | (__float_as_uint(z1[e]) & 0xFFFF0000u))
+                                               : 0u;
+                        *reinterpret_cast<uint32_t*>(yb + (size_t)ql * 128 + ((chunk16 ^ (ql & 7)) << 4) + in_seg) = w;
+                    }
                 }
             }
             fence_proxy_async();
@@ -231,10 +275,22 @@ __global__ void __launch_bounds__(kLThreads, 1) left_tc_kernel(const __grid_cons
                 const uint32_t ast = tmem_base + kLAStageCol + 96u * (uint32_t)s;
 #pragma unroll
                 for (int kk = 0; kk < kLBK / 16; ++kk) {
-                    const uint64_t bdesc = sw128_desc(bst + 32u * kk);
+                    if constexpr (DCT) {
+                        // AX term ta with Y term ty, ta + ty <= 2
+                        constexpr int kTa[6] = {0, 0, 1, 0, 1, 2}, kTy[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
-                    for (int term = 0; term < 3; ++term)
-                        mma_bf16_ts(tmem_base, ast + 32u * term + 8u * kk, bdesc, idesc, (g | kk | term) ? 1u : 0u);
+                        for (int pr = 0; pr < 6; ++pr) {
+                            const uint64_t bdesc = sw128_desc(bst + (uint32_t)kTy[pr] * y_plane + 32u * kk);
+                            mma_bf16_ts(tmem_base, ast + 32u * kTa[pr] + 8u * kk, bdesc, idesc,
+                                        (g | kk | pr) ? 1u : 0u);
+                        }
+                    } else {
+                        const uint64_t bdesc = sw128_desc(bst + 32u * kk);
+#pragma unroll
+                        for (int term = 0; term < 3; ++term)
+                            mma_bf16_ts(tmem_base, ast + 32u * term + 8u * kk, bdesc, idesc,
+                                        (g | kk | term) ? 1u : 0u);
+                    }
                 }
                 mma_commit(&empty[s]);
             }
@@ -270,9 +326,9 @@ struct LeftTcPlan {
     int64_t chunk;
 };
 
-LeftTcPlan left_tc_plan(int64_t M, int R, int S, size_t part_cap) {
+LeftTcPlan left_tc_plan(int64_t M, int R, int S, size_t part_cap, bool dct) {
     LeftTcPlan pl;
-    pl.N = std::min(256, (R + 15) / 16 * 16);
+    pl.N = std::min(dct ? 128 : 256, (R + 15) / 16 * 16);
     pl.n_tiles = (R + pl.N - 1) / pl.N;
     pl.m_tiles = (S + kLBM - 1) / kLBM;
     const int tiles = pl.n_tiles * pl.m_tiles;
@@ -293,15 +349,17 @@ bool left_tc_supported(const float* AX, int64_t ldax, int64_t M, int row0, int R
            (ldax % 4) == 0 && (reinterpret_cast<uintptr_t>(AX + col0) & 15) == 0;
 }
 
-size_t left_tc_part_floats(int64_t M, int R, int S) {
-    const LeftTcPlan pl = left_tc_plan(M, R, S, 0);
+size_t left_tc_part_floats(int64_t M, int R, int S, bool dct) {
+    const LeftTcPlan pl = left_tc_plan(M, R, S, 0, dct);
     return (size_t)pl.splits * R * S;
 }
 
 cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax, int64_t M, int row0, int R,
                                     int col0, int S, float* part, size_t part_cap, int* err_flag, int* splits_out,
-                                    cudaStream_t st) {
-    const LeftTcPlan pl = left_tc_plan(M, R, S, part_cap);
+                                    cudaStream_t st, const DctRows* dct) {
+    const bool is_dct = dct != nullptr;
+    if (is_dct && (dct->nbits < 0 || dct->nbits > 29 || (M > (int64_t(1) << dct->nbits)))) return cudaErrorInvalidValue;
+    const LeftTcPlan pl = left_tc_plan(M, R, S, part_cap, is_dct);
     if ((size_t)pl.splits * R * S > part_cap) return cudaErrorInvalidValue;
     EncodeTiled enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
@@ -317,6 +375,7 @@ cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     LeftTcParams p;
     p.seed = seed;
+    p.dct = is_dct ? *dct : DctRows{nullptr, nullptr, nullptr, 0};
     p.M = M;
     p.row0 = row0;
     p.R = R;
@@ -330,13 +389,18 @@ cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax
     p.part = part;
     p.err = err_flag;
     const size_t a_stage = (kLBM * 32 * 4 + 1023) & ~1023;
-    const size_t y_stage = ((size_t)pl.N * 128 + 1023) & ~(size_t)1023;
+    const size_t y_stage = (((size_t)pl.N * 128 + 1023) & ~(size_t)1023) * (is_dct ? 3 : 1);
     const size_t smem = a_stage * kLAStages + y_stage * kLStages + 1024;
-    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(left_tc_kernel));
+    const void* kern = is_dct ? reinterpret_cast<const void*>(left_tc_kernel<true>)
+                              : reinterpret_cast<const void*>(left_tc_kernel<false>);
+    cudaError_t e = allow_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
     const int64_t grid = (int64_t)pl.splits * pl.n_tiles * pl.m_tiles;
     if (grid > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    left_tc_kernel<<<(unsigned)grid, kLThreads, smem, st>>>(amap, p);
+    if (is_dct)
+        left_tc_kernel<true><<<(unsigned)grid, kLThreads, smem, st>>>(amap, p);
+    else
+        left_tc_kernel<false><<<(unsigned)grid, kLThreads, smem, st>>>(amap, p);
     *splits_out = pl.splits;
     return cudaGetLastError();
 }

@@ -529,8 +529,20 @@ cudaError_t launch_left(uint64_t seed, const float* AX, int64_t ldax, int64_t M,
 }
 
 cudaError_t launch_left_dct(const DctRows& Y, const float* AX, int64_t ldax, int64_t M, int row0, int R, int col0,
-                            int S, float* part, size_t part_cap, double* core, int64_t ld_core, cudaStream_t st) {
+                            int S, float* part, size_t part_cap, double* core, int64_t ld_core, cudaStream_t st,
+                            int* err_flag) {
     if (R <= 0 || S <= 0) return cudaSuccess;
+    if (err_flag && left_tc_supported(AX, ldax, M, row0, R, col0, S) &&
+        left_tc_part_floats(M, R, S, true) <= part_cap) {
+        int tsplits = 0;
+        cudaError_t e = launch_left_tc_partials(0, AX, ldax, M, row0, R, col0, S, part, part_cap, err_flag, &tsplits,
+                                                st, &Y);
+        if (e != cudaSuccess) return e;
+        const int64_t total = (int64_t)R * S;
+        left_reduce_kernel<<<(unsigned)((total + 31) / 32), 256, 0, st>>>(part, tsplits, R, S, row0, col0,
+                                                                                 core, ld_core);
+        return cudaGetLastError();
+    }
     int64_t chunk;
     const int splits = left_splits(M, R, S, &chunk);
     if ((size_t)splits * R * S > part_cap) return cudaErrorInvalidValue;

@@ -200,18 +200,21 @@ def test_core_blocks_parity(h, m, n, c0, c1):
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
 
 
-@pytest.mark.parametrize("m,n,steps", [
-    (3001, 700, ((0, 16), (16, 16), (32, 32))),   # m_pad 4096: appended columns and rows
-    (70000, 40, ((0, 8), (8, 24))),               # m_pad 2^17: phases reduced modulo 2^19
+@pytest.mark.parametrize("m,n,steps,pad", [
+    (3001, 700, ((0, 16), (16, 16), (32, 32)), 0),   # m_pad 4096: appended columns and rows
+    (70000, 40, ((0, 8), (8, 24)), 0),               # m_pad 2^17: phases reduced modulo 2^19
+    (5000, 300, ((0, 8), (8, 8), (16, 112)), 0),     # 2 c1 = 256 rows: two N tiles of 128
+    (3001, 700, ((0, 16), (16, 16)), 1),             # AX rows not 16-byte aligned: CUDA cores
 ])
-def test_srct_left_parity(m, n, steps):
+def test_srct_left_parity(m, n, steps, pad):
     """The SRCT left embedding (DCT-II rows generated from the cosine table):
     the whole core against the oracle's dense S F D (A X) on the GPU's own A X
-    after each appending step."""
+    after each appending step.  Aligned A X takes the tensor-core kernel (Y and
+    A X as three BF16 terms each), an odd row pitch the CUDA-core kernel."""
     A = np.random.default_rng(m + n).standard_normal((m, n)).astype(np.float32)
     Ad = dev(A)
     c1 = steps[-1][0] + steps[-1][1]
-    AX = torch.zeros(m, c1, dtype=torch.float32, device="cuda")
+    AX = torch.zeros(m, c1 + pad, dtype=torch.float32, device="cuda")[:, :c1]
     core = torch.zeros(2 * c1, c1, dtype=torch.float64, device="cuda")
     hd = rk.re_create(0, rk.make_opts(y_kind=rk.RE_SRCT))
     try:
