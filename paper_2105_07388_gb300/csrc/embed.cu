@@ -292,7 +292,9 @@ cudaError_t launch_hrtt_xt_bf16(int64_t n, int64_t kpad, int s, int j0, int cnt,
 // phases differ by c (2N) - (2k+1) c, so their cosines differ by the sign (-1)^c.
 // A thread forms both rows of one pair, each as an FP32 sum with a compensation
 // term (Kahan), so the value is close to the correctly rounded sum.  Work items
-// are (bucket, chunk of blockDim pairs), spread over a persistent grid.
+// are (bucket, chunk of blockDim pairs), spread over a persistent grid; each
+// item first stages its bucket as records (c, sigma_c sqrt(2) w_c, the same times
+// (-1)^c) so the inner loop reads one 16-byte broadcast per entry.
 // planes = 0: FP32 X row-major (X[k * ldx + j - j0], rows k < n); planes = 3: the
 // three exact BF16 terms of the FP32 value as X^T planes (row j - j0 of plane t at
 // Xt + (t * plane_rows + j - j0) * ldx, columns k < kpad, zeros for n <= k).
@@ -322,11 +324,15 @@ __global__ void __launch_bounds__(512) hrct_x_kernel(int64_t n, int64_t kpad, in
                                                      const float* __restrict__ ctab, int planes,
                                                      float* __restrict__ X, uint16_t* __restrict__ Xt, int64_t ldx,
                                                      int64_t plane_rows) {
-    extern __shared__ float smf[];
+    extern __shared__ __align__(16) float smf[];
     const int N = 1 << bits;
-    float* ct = smf;                                              // N + 1 cosines
-    uint16_t* bucket = reinterpret_cast<uint16_t*>(smf + N + 1);  // ceil(N / s) entries
-    for (int i = threadIdx.x; i <= N; i += blockDim.x) ct[i] = ctab[i];
+    // ceil(N / s) bucket records, then the N + 1 cosines with one padding word
+    // after every 32 (cosine i at i + i / 32): within a branch of the fold the lanes
+    // of a warp read indices 2c apart, and the padding spreads such power-of-two
+    // multiples over the banks
+    uint4* bucket = reinterpret_cast<uint4*>(smf);
+    float* ct = smf + 4 * ((N + s - 1) / s);
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) ct[i + (i >> 5)] = ctab[i];
     const int64_t kend = planes == 0 ? n : kpad;
     const int kcov = (int)(kend < (int64_t)N ? kend : (int64_t)N);  // rows below N
     const int P = (N + 1) / 2 < kcov ? (N + 1) / 2 : kcov;           // pairs (k, N-1-k)
@@ -338,7 +344,14 @@ __global__ void __launch_bounds__(512) hrct_x_kernel(int64_t n, int64_t kpad, in
         const int j = j0 + jj;
         const int L = (N - j + s - 1) / s;                        // entries q = j + t s < N
         __syncthreads();                                          // the previous bucket is no longer read
-        for (int t = threadIdx.x; t < L; t += blockDim.x) bucket[t] = tbl[j + t * s];
+        for (int t = threadIdx.x; t < L; t += blockDim.x) {
+            const uint32_t e = tbl[j + t * s];
+            const uint32_t c = e & 0x7fffu;
+            float coef = c == 0 ? 1.f : 1.41421356237309515f;     // sqrt(2) w_c
+            if (e >> 15) coef = -coef;                            // sigma_c
+            const float coef_m = (c & 1u) ? -coef : coef;         // row N-1-k: times (-1)^c
+            bucket[t] = make_uint4(c, __float_as_uint(coef), __float_as_uint(coef_m), 0u);
+        }
         __syncthreads();
         const int p = chunk * (int)blockDim.x + (int)threadIdx.x;
         if (p >= P) continue;                                     // every thread runs the same items
@@ -348,15 +361,15 @@ __global__ void __launch_bounds__(512) hrct_x_kernel(int64_t n, int64_t kpad, in
         if (vk || vm) {
             const uint32_t odd = 2u * (uint32_t)k + 1u;           // < 2^16, c < 2^15: no overflow
             for (int t = 0; t < L; ++t) {
-                const uint32_t e = bucket[t];
-                const uint32_t c = e & 0x7fffu;
-                uint32_t ph = (odd * c) & mask;
-                if (ph > twoN) ph = fourN - ph;
-                const float cv = ph <= (uint32_t)N ? ct[ph] : -ct[twoN - ph];
-                float term = c == 0 ? 1.f : 1.41421356237309515f * cv;
-                if (e >> 15) term = -term;
-                kahan_add(s0, c0, term);
-                kahan_add(s1, c1, (c & 1u) ? -term : term);
+                const uint4 b = bucket[t];
+                const uint32_t ph = (odd * b.x) & mask;
+                const uint32_t ph2 = min(ph, fourN - ph);         // cos(2 pi - x) = cos x: [0, 2N]
+                const uint32_t jx = min(ph2, twoN - ph2);         // cos(pi - x) = -cos x: [0, N]
+                const float cv = ct[jx + (jx >> 5)];
+                const bool neg = ph2 > (uint32_t)N;
+                const float ca = __uint_as_float(b.y), cm = __uint_as_float(b.z);
+                kahan_add(s0, c0, (neg ? -ca : ca) * cv);         // c = 0: ph = 0, cv = 1
+                kahan_add(s1, c1, (neg ? -cm : cm) * cv);
             }
         }
         if (k < kend) {
@@ -384,7 +397,7 @@ cudaError_t launch_hrct_x(int64_t n, int64_t kpad, int s, int j0, int cnt, int b
         ldx < kpad)))
         return cudaErrorInvalidValue;
     const int N = 1 << bits;
-    const size_t smem = sizeof(float) * (size_t)(N + 1) + sizeof(uint16_t) * (size_t)((N + s - 1) / s) + 16;
+    const size_t smem = sizeof(float) * (size_t)(N + 1 + (N >> 5) + 1) + sizeof(uint4) * (size_t)((N + s - 1) / s);
     cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(hrct_x_kernel));
     int dev = 0, sms = 0, per_sm = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
