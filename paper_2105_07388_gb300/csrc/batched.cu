@@ -279,6 +279,7 @@ struct BatchedState {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
     DBuf ax, x, xt, tcerr, actpre, core, sigma, sscaled, status, out, active, valid, descs, pre128, pre64, colpre, finals;
     DBuf tmaps;                       // tensor-core path: four row-class tensor maps per block
+    DBuf tileblk;                     // tensor-core path: block of each active 128-row tile
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned char> key;
     int bm_for[16] = {0};
@@ -290,7 +291,8 @@ void batched_destroy(BatchedState* st) {
     if (!st) return;
     if (st->exec) cudaGraphExecDestroy(st->exec);
     DBuf* bufs[] = {&st->ax, &st->x, &st->xt, &st->tcerr, &st->actpre, &st->core, &st->sigma, &st->sscaled, &st->status, &st->out,
-                    &st->active, &st->valid, &st->descs, &st->pre128, &st->pre64, &st->colpre, &st->finals, &st->tmaps};
+                    &st->active, &st->valid, &st->descs, &st->pre128, &st->pre64, &st->colpre, &st->finals, &st->tmaps,
+                    &st->tileblk};
     for (DBuf* b : bufs) b->release();
     if (st->ev_in) cudaEventDestroy(st->ev_in);
     if (st->ev_out) cudaEventDestroy(st->ev_out);
@@ -408,6 +410,7 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
         ens(st->xt, sizeof(uint16_t) * (size_t)std::max<int64_t>(xt_total, 1));
         ens(st->tcerr, sizeof(int));
         ens(st->actpre, sizeof(int64_t) * (size_t)(count + 1));
+        ens(st->tileblk, sizeof(int) * (size_t)std::max<int64_t>(pre128[count], 1));
     } else {
         ens(st->x, sizeof(float) * (size_t)std::max<int64_t>(x_total, 1));
     }
@@ -440,7 +443,7 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
     put(hd.data(), sizeof(BatchDesc) * hd.size());
     put(valid.data(), sizeof(int) * valid.size());
     const void* pools[] = {st->ax.p, st->x.p, st->xt.p, st->tcerr.p, st->actpre.p, st->core.p, st->sigma.p, st->sscaled.p,
-                           st->status.p, st->out.p, st->active.p, st->finals.p, st->tmaps.p};
+                           st->status.p, st->out.p, st->active.p, st->finals.p, st->tmaps.p, st->tileblk.p};
     put(pools, sizeof(pools));
 
     cudaStream_t bs = st->stream;
@@ -518,13 +521,16 @@ int batched_estimate(BatchedState** pst, const re_opts& o, const re_block* block
                         const int upto = covered == 0 ? std::max(s, w1) : s;
                         const int c0 = covered, cn = upto - covered;
                         el = launch_gauss_xt_batched(dd, count, active, c0, cn, tc_mma_n(cn), st->xt.as<uint16_t>(), bs);
-                        if (el == cudaSuccess) el = launch_compact_tiles(dd, count, active, st->actpre.as<int64_t>(), bs);
                         if (el == cudaSuccess)
-                            el = launch_right_tc_batched(dd, count, st->actpre.as<int64_t>(), pre128[count],
+                            el = launch_compact_tiles(dd, count, active, st->actpre.as<int64_t>(),
+                                                      st->tileblk.as<int>(), pre128[count], bs);
+                        if (el == cudaSuccess)
+                            el = launch_right_tc_batched(dd, count, st->actpre.as<int64_t>(), st->tileblk.as<int>(),
+                                                         pre128[count],
                                                          st->xt.as<uint16_t>(), cn, st->ax.as<float>(), S_MAX, c0, tcerr,
                                                          st->tmaps.p, bs);
                         covered = upto;
-                        nl += 3;
+                        nl += 4;
                     }
                 } else {
                     const int bm = st->bm_for[31 - __builtin_clz((unsigned)sn)] == 64 ? 64 : 128;

@@ -214,6 +214,7 @@ struct TcBatchParams {
     const BatchDesc* d;
     int count;
     const int64_t* pre;       // prefix of the active blocks' 128-row tiles (count + 1 entries)
+    const int* tb;            // block of each of those tiles (launch_compact_tiles)
     const uint16_t* xt;       // X^T pool
     int N;                    // MMA N (rows of each block's X^T)
     int S;                    // valid output columns
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
         int64_t g = 0;
         bool ok = true;
         for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
-            const int b = find_block(p.pre, p.count, it);
+            const int b = p.tb[it];
             const int64_t kch = p.d[b].kpad / kBK;
             const bool trans = p.d[b].trans != 0;
             const bool mfree = p.d[b].A == nullptr;
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
         int64_t hg = 0;
         bool ok = true;
         for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
-            const int b = find_block(p.pre, p.count, it);
+            const int b = p.tb[it];
             const BatchDesc& D = p.d[b];
             const BlockRef B{D.A, D.ld, D.rows, D.cols};   // in registers for the whole tile
             const bool tr = D.trans != 0;
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
         int64_t g = 0;
         bool ok = true;
         for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
-            const int b = find_block(p.pre, p.count, it);
+            const int b = p.tb[it];
             const BatchDesc& D = p.d[b];
             const uint16_t* xt = p.xt + D.xt_off;
             const int64_t kch = D.kpad / kBK;
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
             int64_t g = 0, j = 0;
             bool ok = true;
             for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
-                const int b = find_block(p.pre, p.count, it);
+                const int b = p.tb[it];
                 const int64_t kch = p.d[b].kpad / kBK;
                 const int a = (int)(j & 1);
                 if (!mbar_wait(&acce[a], (uint32_t)(((j >> 1) & 1) ^ 1), &s_abort, p.err)) break;
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
         const int q = warp & 3;
         int64_t j = 0;
         for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-            const int b = find_block(p.pre, p.count, it);
+            const int b = p.tb[it];
             const int a = (int)(j & 1);
             const bool ok = mbar_wait(&accf[a], (uint32_t)((j >> 1) & 1), &s_abort, p.err);
             if (!__all_sync(0xffffffffu, ok)) break;   // tcgen05.ld is warp-wide
@@ -647,14 +648,27 @@ __global__ void __launch_bounds__(1024) compact_tiles_kernel(const BatchDesc* __
     if (t == 1023) act_pre[count] = s_part[1023];
 }
 
+// tile_block[t] = the active block holding tile t (t < act_pre[count]): one search
+// per tile here instead of one per tile in every role of the sketch kernel
+__global__ void tile_block_kernel(const int64_t* __restrict__ act_pre, int count, int64_t max_items,
+                                  int* __restrict__ tile_block) {
+    const int64_t items = min(act_pre[count], max_items);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < items; t += (int64_t)gridDim.x * blockDim.x)
+        tile_block[t] = find_block(act_pre, count, t);
+}
+
 int g_bsms = 0;
 
 }  // namespace
 
 cudaError_t launch_compact_tiles(const BatchDesc* d, int count, const int* active, int64_t* act_pre,
-                                 cudaStream_t st) {
-    if (count <= 0) return cudaSuccess;
+                                 int* tile_block, int64_t max_items, cudaStream_t st) {
+    if (count <= 0 || max_items <= 0) return cudaSuccess;
     compact_tiles_kernel<<<1, 1024, 0, st>>>(d, count, active, act_pre);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::min<int64_t>((max_items + 255) / 256, 1024);
+    tile_block_kernel<<<(unsigned)blocks, 256, 0, st>>>(act_pre, count, max_items, tile_block);
     return cudaGetLastError();
 }
 
@@ -691,16 +705,18 @@ bool encode_row_class_maps(const float* A, int64_t ld, int64_t rows, int64_t col
     return true;
 }
 
-cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t* act_prefix, int64_t max_items,
-                                    const uint16_t* XTpool, int s, float* AXpool, int64_t ldax, int col0,
-                                    int* err_flag, const void* tmaps, cudaStream_t st) {
+cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t* act_prefix, const int* tile_block,
+                                    int64_t max_items, const uint16_t* XTpool, int s, float* AXpool, int64_t ldax,
+                                    int col0, int* err_flag, const void* tmaps, cudaStream_t st) {
     if (max_items <= 0 || s <= 0 || count <= 0) return cudaSuccess;
-    if (s > 256 || s % 8 != 0 || col0 % 4 != 0 || ldax % 4 != 0 || !err_flag) return cudaErrorInvalidValue;
+    if (s > 256 || s % 8 != 0 || col0 % 4 != 0 || ldax % 4 != 0 || !err_flag || !tile_block)
+        return cudaErrorInvalidValue;
     TcBatchParams p;
     p.tmaps = static_cast<const CUtensorMap*>(tmaps);
     p.d = d;
     p.count = count;
     p.pre = act_prefix;
+    p.tb = tile_block;
     p.xt = XTpool;
     p.N = tc_mma_n(s);
     p.S = s;

@@ -151,13 +151,14 @@ cudaError_t launch_left_tc_partials(uint64_t seed, const float* AX, int64_t ldax
 // from launch_compact_tiles) numbers the tiles of the active blocks; max_items
 // bounds their number.  A is loaded with asynchronous copies of 16, 8 or 4
 // bytes, so any row pitch works.
+// It also writes tile_block[t] (max_items entries), the block of each active tile.
 cudaError_t launch_compact_tiles(const BatchDesc* d, int count, const int* active, int64_t* act_prefix,
-                                 cudaStream_t st);
+                                 int* tile_block, int64_t max_items, cudaStream_t st);
 // tmaps: device array of 4 tensor maps per block (block b's at 4b .. 4b+3, used when
 // d[b].tmaps is set; see encode_row_class_maps).
-cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t* act_prefix, int64_t max_items,
-                                    const uint16_t* XTpool, int s, float* AXpool, int64_t ldax, int col0,
-                                    int* err_flag, const void* tmaps, cudaStream_t st);
+cudaError_t launch_right_tc_batched(const BatchDesc* d, int count, const int64_t* act_prefix, const int* tile_block,
+                                    int64_t max_items, const uint16_t* XTpool, int s, float* AXpool, int64_t ldax,
+                                    int col0, int* err_flag, const void* tmaps, cudaStream_t st);
 // Bytes of one tensor map (CUtensorMap) of the row-class fetch.
 size_t row_class_map_bytes();
 // Encodes into out (4 maps) the row classes of an FP32 matrix stored row-major with
