@@ -973,14 +973,15 @@ int run_qb(re_handle h, const Plan& P, double eps, int p, uint64_t seed, float* 
     if (int rr = ensure(h->qbws, re::qb_workspace_bytes(M, P.A.cols, k, tensor))) return rr;
     int nl = 0;
     cudaEvent_t a = stage_begin(h, st);
+    int* tmo_flag = static_cast<int*>(h->status.p) + 1;   // bounded-wait expiry of the tensor-core kernels
     e = exact ? re::launch_qb_precondition(static_cast<const float*>(h->ex_hi.p), 1, h->ex_ldp, M, P.A.cols, core,
-                                           smax, 2 * s, k, h->qbws.p, floored, st, &nl)
+                                           smax, 2 * s, k, h->qbws.p, floored, st, &nl, tensor, tmo_flag)
               : re::launch_qb_precondition(AX, smax, 1, M, P.A.cols, core, smax, 2 * s, k, h->qbws.p, floored, st,
-                                           &nl);
+                                           &nl, tensor, tmo_flag);
     stage_end(h, st, a, kStageQbPre);
     if (e == cudaSuccess) {
         a = stage_begin(h, st);
-        e = re::launch_qb_orthonormalise(M, P.A.cols, k, Q, ldq, h->qbws.p, floored, st, &nl);
+        e = re::launch_qb_orthonormalise(M, P.A.cols, k, Q, ldq, h->qbws.p, floored, st, &nl, tensor, tmo_flag);
         stage_end(h, st, a, kStageQbOrth);
     }
     if (e == cudaSuccess) {

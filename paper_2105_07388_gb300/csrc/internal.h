@@ -316,11 +316,15 @@ size_t qb_workspace_bytes(int64_t rows, int64_t cols, int k, bool tensor);
 // *floored (device) is set when a Cholesky pivot had to be raised (an exactly
 // singular Gram matrix).  launches (may be null) counts the kernels launched.
 // AX(r, l) at AX[r sar + l sak] (sak == 1: row-major; sar == 1: transposed planes)
+// tensor (with a non-null err_flag for the bounded waits): the Gram matrices V^T V
+// and the products by (L^-1)^T on the tensor cores (both factors in three BF16
+// terms, six products), where the operands suit those kernels; else CUDA cores.
 cudaError_t launch_qb_precondition(const float* AX, int64_t sar, int64_t sak, int64_t rows, int64_t cols,
                                    const double* core, int64_t ld_core, int r2, int k, void* ws, int* floored,
-                                   cudaStream_t st, int* launches);
+                                   cudaStream_t st, int* launches, bool tensor = false, int* err_flag = nullptr);
 cudaError_t launch_qb_orthonormalise(int64_t rows, int64_t cols, int k, float* Q, int64_t ldq, void* ws,
-                                     int* floored, cudaStream_t st, int* launches);
+                                     int* floored, cudaStream_t st, int* launches, bool tensor = false,
+                                     int* err_flag = nullptr);
 // tensor: B = Q^T A on the tensor cores (qb_tc.cu) when the view allows it (else
 // CUDA cores); err_flag receives a bounded wait's expiry.
 cudaError_t launch_qb_product(const MatView& A, const float* Q, int64_t ldq, int k, float* B, int64_t ldb, void* ws,
@@ -328,6 +332,8 @@ cudaError_t launch_qb_product(const MatView& A, const float* Q, int64_t ldq, int
 // out (M x N, pitch ldo) = the sum over `splits` FP32 partials (pitch N, M N apart),
 // added in FP64 in split order.
 cudaError_t reduce_parts_f32(const float* part, int splits, int64_t M, int64_t N, float* out, int64_t ldo,
+                             cudaStream_t st);
+cudaError_t reduce_parts_f64(const float* part, int splits, int64_t M, int64_t N, double* out, int64_t ldo,
                              cudaStream_t st);
 
 // ---- B = Q^T A on tcgen05 (qb_tc.cu) -------------------------------------------
@@ -338,9 +344,16 @@ int qb_tc_splits(int64_t tiles, int64_t kchunks, int cap);
 // Qt (3 x qb_tc_qt_rows(k) rows of pitch qb_tc_qt_ld(M), BF16 bits) = the three
 // BF16 terms of Q^T (Q: M x k FP32, pitch ldq)
 cudaError_t launch_qt_split(const float* Q, int64_t ldq, int64_t M, int k, uint16_t* Qt, cudaStream_t st);
-// rows [c0, c0 + kq) of Q^T A (kq <= 128) into out (pitch ldo); split partials in part
+// rows [c0, c0 + kq) of Q^T A (kq <= 128) into out (pitch ldo); split partials in
+// part.  With out64, the partials are summed into out64 (FP64, pitch ldo64) instead.
 cudaError_t launch_qb_product_tc(const MatView& A, const uint16_t* Qt, int k, int c0, int kq, float* out,
-                                 int64_t ldo, float* part, int splits, int* err_flag, cudaStream_t st);
+                                 int64_t ldo, float* part, int splits, int* err_flag, cudaStream_t st,
+                                 double* out64 = nullptr, int64_t ldo64 = 0);
+// Xt (3 planes of nrows rows, pitch ldt, BF16 bits) = the three BF16 terms of rows
+// c0 .. c0+w-1 of S (FP32, pitch lds, cols columns), zero elsewhere: the X^T
+// operand of launch_right_tc (xterms = 3) for X = S^T restricted to those columns.
+cudaError_t launch_rows_split3(const float* S, int64_t lds, int c0, int w, int cols, int nrows, int64_t ldt,
+                               uint16_t* Xt, cudaStream_t st);
 
 // ---- batched estimate (batched.cu) --------------------------------------------
 struct BatchedState;

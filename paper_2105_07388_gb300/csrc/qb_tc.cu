@@ -330,7 +330,8 @@ cudaError_t launch_qt_split(const float* Q, int64_t ldq, int64_t M, int k, uint1
 // Columns [c0, c0 + kq) of Q (kq <= 128): out (row c - c0 at out + (c - c0) ldo, or
 // the split partials at part + z zstride with pitch N) = (Q^T A)[c][:].
 cudaError_t launch_qb_product_tc(const MatView& A, const uint16_t* Qt, int k, int c0, int kq, float* out,
-                                 int64_t ldo, float* part, int splits, int* err_flag, cudaStream_t st) {
+                                 int64_t ldo, float* part, int splits, int* err_flag, cudaStream_t st,
+                                 double* out64, int64_t ldo64) {
     if (kq <= 0 || kq > kNQ) return cudaErrorInvalidValue;
     EncodeTiled enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
@@ -367,8 +368,10 @@ cudaError_t launch_qb_product_tc(const MatView& A, const uint16_t* Qt, int k, in
     const int used = (int)((p.kchunks + p.per - 1) / p.per);     // splits that own at least one chunk
     p.kq = kq;
     p.nmma = nmma;
-    p.out = splits > 1 ? part : out;
-    p.ldo = splits > 1 ? N : ldo;
+    // an FP64 output always takes the partials (one or more) and the FP64 reduction
+    const bool parts = splits > 1 || out64 != nullptr;
+    p.out = parts ? part : out;
+    p.ldo = parts ? N : ldo;
     p.zstride = (int64_t)kq * N;
     p.err = err_flag;
     const size_t smem = (size_t)kHalfBytes * kAStages + (size_t)3 * kTermBytes * kStages + 1024;
@@ -377,9 +380,39 @@ cudaError_t launch_qb_product_tc(const MatView& A, const uint16_t* Qt, int k, in
     const dim3 grid((unsigned)((N + kBM - 1) / kBM), (unsigned)used);
     qb_product_tc_kernel<<<grid, kThreads, smem, st>>>(amap, qmap, p);
     e = cudaGetLastError();
-    if (e != cudaSuccess || splits <= 1) return e;
+    if (e != cudaSuccess || !parts) return e;
     // splits that own no chunk leave their partial unwritten: the reduction covers `used`
+    if (out64) return reduce_parts_f64(part, used, (int64_t)kq, N, out64, ldo64, st);
     return reduce_parts_f32(part, used, (int64_t)kq, N, out, ldo, st);
+}
+
+namespace {
+// Plane t, row j (j < nrows), column l (l < ldt) of the X^T operand of the
+// tensor-core right sketch for X = S^T, S rows c0 .. c0+w-1 (FP32, pitch lds,
+// cols columns): term t of S[c0 + j][l], zero past w rows or cols columns.
+__global__ void rows_split3_kernel(const float* __restrict__ S, int64_t lds, int c0, int w, int cols, int nrows,
+                                   int64_t ldt, uint16_t* __restrict__ Xt) {
+    const int64_t total = (int64_t)nrows * ldt;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i / ldt);
+        const int l = (int)(i - (int64_t)j * ldt);
+        const float v = (j < w && l < cols) ? S[(int64_t)(c0 + j) * lds + l] : 0.f;
+        uint32_t hi, mid, lo;
+        split3(v, 0.f, hi, mid, lo);                   // the low halves hold the terms of v
+        Xt[i] = (uint16_t)(hi & 0xffffu);
+        Xt[total + i] = (uint16_t)(mid & 0xffffu);
+        Xt[2 * total + i] = (uint16_t)(lo & 0xffffu);
+    }
+}
+}  // namespace
+
+cudaError_t launch_rows_split3(const float* S, int64_t lds, int c0, int w, int cols, int nrows, int64_t ldt,
+                               uint16_t* Xt, cudaStream_t st) {
+    if (w <= 0 || w > nrows || cols <= 0 || cols > ldt) return cudaErrorInvalidValue;
+    const int64_t total = (int64_t)nrows * ldt;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 2048);
+    rows_split3_kernel<<<blocks, 256, 0, st>>>(S, lds, c0, w, cols, nrows, ldt, Xt);
+    return cudaGetLastError();
 }
 
 }  // namespace re

@@ -505,9 +505,19 @@ cudaError_t reduce_parts(const float* P, int splits, int64_t M, int64_t N, TO* o
 struct QbWs {
     double *G64, *Lp, *Xp, *T, *fl;
     int* defl;
-    float *Xinv, *W, *Q1, *part;
+    float *Xinv, *W, *Q1, *part;    // W and Q1: rows x vpitch(k), 16-byte aligned rows
     uint16_t* qt;                   // the Q^T terms of the tensor-core product
+    uint16_t* xt;                   // tensor cores: the three BF16 planes of L^-1 rows, per 128-row chunk
 };
+
+// Row pitch of W and Q1 (k rounded up to 8): 16-byte aligned rows for the tensor
+// maps, and whole 8-column groups for the right-sketch kernel's output widths.
+int64_t vpitch(int k) { return (k + 7) / 8 * 8; }
+// The L^-1 plane chunks of the tensor-core products V (L^-1)^T: 128 output
+// columns each, rows of xt_ld(k) contraction entries.
+int64_t xt_ld(int k) { return (k + 63) / 64 * 64; }
+size_t xt_chunk_elems(int k) { return (size_t)3 * 128 * (size_t)xt_ld(k); }
+int xt_chunks(int k) { return (k + 127) / 128; }
 
 constexpr int kPartCap = 128;       // largest split count of any CUDA-core product
 constexpr size_t kTcPartFloats = (size_t)16 << 20;   // tensor-core product partials: 64 MB
@@ -547,12 +557,14 @@ QbWs carve(void* ws, int64_t rows, int64_t cols, int k, bool tensor) {
     w.fl = w.T + kp * kp / 4;
     w.defl = reinterpret_cast<int*>(w.fl + 2);
     w.Xinv = reinterpret_cast<float*>(w.G64 + ws_doubles(k));
-    w.W = w.Xinv + (size_t)k * k;
-    w.Q1 = w.W + (size_t)rows * k;
-    w.part = w.Q1 + (size_t)rows * k;
+    const uintptr_t wa = reinterpret_cast<uintptr_t>(w.Xinv + (size_t)k * k);
+    w.W = reinterpret_cast<float*>((wa + 15) & ~(uintptr_t)15);
+    w.Q1 = w.W + (size_t)rows * vpitch(k);
+    w.part = w.Q1 + (size_t)rows * vpitch(k);
     // 16-byte aligned: the tensor maps of the product start here
     const uintptr_t q = reinterpret_cast<uintptr_t>(w.part + part_floats_needed(rows, cols, k, tensor));
     w.qt = reinterpret_cast<uint16_t*>((q + 15) & ~(uintptr_t)15);
+    w.xt = w.qt + (tensor ? (size_t)3 * qb_tc_qt_rows(k) * (size_t)qb_tc_qt_ld(rows) : 0);
     return w;
 }
 
@@ -568,8 +580,9 @@ size_t qb_workspace_bytes(int64_t rows, int64_t cols, int k, bool tensor) {
     // the FP64 factorization buffers, the FP32 inverse (k x k), W and Q1 (rows x k
     // FP32), the split partials, the Q^T terms (tensor cores)
     const size_t qt = tensor ? sizeof(uint16_t) * 3 * (size_t)qb_tc_qt_rows(k) * (size_t)qb_tc_qt_ld(rows) : 0;
-    return sizeof(double) * ws_doubles(k) + sizeof(float) * ((size_t)k * k + (size_t)2 * rows * k) +
-           sizeof(float) * part_floats_needed(rows, cols, k, tensor) + qt + 256;
+    const size_t xt = tensor ? sizeof(uint16_t) * xt_chunk_elems(k) * (size_t)xt_chunks(k) : 0;
+    return sizeof(double) * ws_doubles(k) + sizeof(float) * ((size_t)k * k + (size_t)2 * rows * vpitch(k)) +
+           sizeof(float) * part_floats_needed(rows, cols, k, tensor) + qt + xt + 256 + 32;
 }
 
 cudaError_t reduce_parts_f32(const float* part, int splits, int64_t M, int64_t N, float* out, int64_t ldo,
@@ -577,11 +590,51 @@ cudaError_t reduce_parts_f32(const float* part, int splits, int64_t M, int64_t N
     return reduce_parts<float>(part, splits, M, N, out, ldo, st);
 }
 
+cudaError_t reduce_parts_f64(const float* part, int splits, int64_t M, int64_t N, double* out, int64_t ldo,
+                             cudaStream_t st) {
+    return reduce_parts<double>(part, splits, M, N, out, ldo, st);
+}
+
+namespace {
+// out (rows x k, pitch ldo, a multiple of 8 at least vpitch(k), 16-byte aligned) =
+// V (rows x k, pitch ldv) (L^-1)^T on the tensor cores: the rows of L^-1 (Xinv, k x k)
+// as three BF16 planes per 128 output columns, six products per K step; the
+// columns [k, vpitch(k)) of out receive zeros.  Returns cudaErrorNotSupported when
+// V does not suit the kernel (the caller then uses the CUDA-core tiles).
+cudaError_t vlinv_tc(const float* V, int64_t ldv, int64_t rows, int k, const float* Xinv, uint16_t* xt, float* out,
+                     int64_t ldo, int* err_flag, cudaStream_t st, int* launches) {
+    MatView Vv;
+    Vv.ptr = V;
+    Vv.dtype = RE_F32;
+    Vv.trans = false;
+    Vv.rows = rows;
+    Vv.cols = k;
+    Vv.ld = ldv;
+    if (!err_flag || !tc_supported(Vv) || (ldo % 8) != 0 || ldo < vpitch(k) ||
+        (reinterpret_cast<uintptr_t>(out) & 15) != 0)
+        return cudaErrorNotSupported;
+    const int64_t ldt = xt_ld(k);
+    cudaError_t e = cudaSuccess;
+    for (int c0 = 0, ch = 0; c0 < k && e == cudaSuccess; c0 += 128, ++ch) {
+        const int w = std::min(128, k - c0);
+        const int s8 = (w + 7) / 8 * 8;                 // c0 + s8 <= vpitch(k) <= ldo
+        const int nrows = tc_mma_n(s8);
+        uint16_t* planes = xt + (size_t)ch * xt_chunk_elems(k);
+        e = launch_rows_split3(Xinv, k, c0, w, k, nrows, ldt, planes, st);
+        int nl = 0;
+        if (e == cudaSuccess)
+            e = launch_right_tc(Vv, planes, ldt, s8, out + c0, ldo, err_flag, st, &nl, 0, 3);
+        if (launches) *launches += 1 + nl;
+    }
+    return e;
+}
+}  // namespace
+
 cudaError_t launch_qb_precondition(const float* AX, int64_t sar, int64_t sak, int64_t rows, int64_t cols,
                                    const double* core, int64_t ld_core, int r2, int k, void* ws, int* floored,
-                                   cudaStream_t st, int* launches) {
+                                   cudaStream_t st, int* launches, bool tensor, int* err_flag) {
     if (k <= 0 || k > 1024) return cudaErrorInvalidValue;
-    QbWs w = carve(ws, rows, cols, k, false);
+    QbWs w = carve(ws, rows, cols, k, tensor);
     // R_s^T R_s = C_k^T C_k (C_k = the first k columns of the r2 x s core), L = R_s^T
     const dim3 g64((unsigned)((k + 31) / 32), (unsigned)((k + 31) / 32));
     gram64_kernel<<<g64, 256, 0, st>>>(core, ld_core, r2, k, w.G64);
@@ -591,30 +644,70 @@ cudaError_t launch_qb_precondition(const float* AX, int64_t sar, int64_t sak, in
     // W = (A X_k) R_s^{-1} = (A X_k) (L^{-1})^T: W(r, c) = sum_l AX(r, l) Xinv[c][l],
     // AX(r, l) at AX[r sar + l sak] (row-major, or the transposed planes of the
     // exact-product mode)
-    e = sak == 1 ? gemm<true, true>(AX, sar, 1, w.Xinv, 1, k, w.W, k, rows, k, k, 1, 0, st)
-                 : gemm<false, true>(AX, sar, sak, w.Xinv, 1, k, w.W, k, rows, k, k, 1, 0, st);
+    const int64_t kp = vpitch(k);
+    if (tensor && sak == 1) {
+        e = vlinv_tc(AX, sar, rows, k, w.Xinv, w.xt, w.W, kp, err_flag, st, launches);
+        if (e != cudaErrorNotSupported) return e;
+    }
+    e = sak == 1 ? gemm<true, true>(AX, sar, 1, w.Xinv, 1, k, w.W, kp, rows, k, k, 1, 0, st)
+                 : gemm<false, true>(AX, sar, sak, w.Xinv, 1, k, w.W, kp, rows, k, k, 1, 0, st);
     if (launches) *launches += 1;
     return e;
 }
 
 cudaError_t launch_qb_orthonormalise(int64_t rows, int64_t cols, int k, float* Q, int64_t ldq, void* ws,
-                                     int* floored, cudaStream_t st, int* launches) {
-    QbWs w = carve(ws, rows, cols, k, false);
+                                     int* floored, cudaStream_t st, int* launches, bool tensor, int* err_flag) {
+    QbWs w = carve(ws, rows, cols, k, tensor);
+    const int64_t kp = vpitch(k);
     // two Cholesky-QR passes: G = V^T V, V <- V (L^{-1})^T
-    const float* V = w.W;
+    float* V = w.W;
     const int splits = choose_splits(k, k, rows, kPartCap);
     cudaError_t e = cudaSuccess;
+    MatView Vv;
+    Vv.dtype = RE_F32;
+    Vv.trans = false;
+    Vv.rows = rows;
+    Vv.cols = k;
+    Vv.ld = kp;
     for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
-        float* out = pass == 0 ? w.Q1 : Q;
-        const int64_t ldo = pass == 0 ? k : ldq;
-        // partial Gram matrices over row ranges, summed in FP64
-        e = gemm<false, false>(V, 1, k, V, k, 1, w.part, k, k, k, rows, splits, (int64_t)k * k, st);
-        if (e == cudaSuccess) e = reduce_parts<double>(w.part, splits, k, k, w.G64, k, st);
-        if (launches) *launches += 2;
+        Vv.ptr = V;
+        // partial Gram matrices over row ranges, summed in FP64: on the tensor cores
+        // as the product V^T V (both factors in three BF16 terms, six products)
+        if (tensor && err_flag && qb_tc_supported(Vv)) {
+            e = launch_qt_split(V, kp, rows, k, w.qt, st);
+            int nl = 1;
+            const int64_t tiles = (k + 127) / 128, kchunks = (rows + 63) / 64;
+            const int ts = qb_tc_splits(tiles, kchunks, tc_part_cap(k));
+            for (int c0 = 0; c0 < k && e == cudaSuccess; c0 += 128) {
+                const int kq = std::min(128, k - c0);
+                e = launch_qb_product_tc(Vv, w.qt, k, c0, kq, nullptr, 0, w.part, ts, err_flag, st,
+                                         w.G64 + (size_t)c0 * k, k);
+                nl += 2;
+            }
+            if (launches) *launches += nl;
+        } else {
+            e = gemm<false, false>(V, 1, kp, V, kp, 1, w.part, k, k, k, rows, splits, (int64_t)k * k, st);
+            if (e == cudaSuccess) e = reduce_parts<double>(w.part, splits, k, k, w.G64, k, st);
+            if (launches) *launches += 2;
+        }
         if (e == cudaSuccess)
             e = chol_inverse(w.G64, k, k, kDeflPass, w.Lp, w.Xp, w.T, w.fl, w.defl, w.Xinv, floored, st, launches);
-        if (e == cudaSuccess) e = gemm<true, true>(V, k, 1, w.Xinv, 1, k, out, ldo, rows, k, k, 1, 0, st);
-        if (launches) *launches += 1;
+        if (e != cudaSuccess) break;
+        // V (L^-1)^T: pass 0 into Q1; pass 1 into Q, through W (free after pass 0) on
+        // the tensor cores, whose output rows are padded to whole 8-column groups
+        float* tout = pass == 0 ? w.Q1 : w.W;
+        cudaError_t et = tensor ? vlinv_tc(V, kp, rows, k, w.Xinv, w.xt, tout, kp, err_flag, st, launches)
+                                : cudaErrorNotSupported;
+        if (et == cudaSuccess && pass == 1) {
+            et = cudaMemcpy2DAsync(Q, sizeof(float) * ldq, w.W, sizeof(float) * kp, sizeof(float) * k, rows,
+                                   cudaMemcpyDeviceToDevice, st);
+        } else if (et == cudaErrorNotSupported) {
+            float* out = pass == 0 ? w.Q1 : Q;
+            const int64_t ldo = pass == 0 ? kp : ldq;
+            et = gemm<true, true>(V, kp, 1, w.Xinv, 1, k, out, ldo, rows, k, k, 1, 0, st);
+            if (launches) *launches += 1;
+        }
+        e = et;
         V = w.Q1;
     }
     return e;
