@@ -25,6 +25,7 @@
 //                      Gram matrices summed in FP64 in a fixed order;
 //   B = Q^T A          the same tiles (A read once per 128 columns of Q), split
 //                      over the rows of A when the output has few tiles.
+#include <climits>
 #include <cmath>
 #include <algorithm>
 
@@ -36,25 +37,52 @@ namespace re {
 namespace {
 
 
+// Steps 4-5 of Algorithm 3 (one warp): lane 0 accumulates the tail sums T(r) from
+// the end, in the order of the sequential definition; the lanes then test the
+// criterion for r = lane, lane + 32, ... (two square roots and a division each,
+// the costly part in FP64) and a warp minimum keeps the smallest r that meets it.
+constexpr int kSelMax = 1024;       // trusted values held in shared memory (r1 <= 465 at s = 512)
+
 __global__ void select_rank_kernel(const double* __restrict__ sig, int r1, int64_t n, double eps, double norm_a,
                                    int p, int s, QbSelect* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double Ts[kSelMax + 1];
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     const double ref = norm_a > 0.0 ? norm_a : (r1 > 0 ? sig[0] : 0.0);
     // A has only n singular values: a sketch wider than n trusts at most n of them
-    const int re = (int)(n < (int64_t)r1 ? n : (int64_t)r1);
-    const double last = re > 0 ? sig[re - 1] : 0.0;
-    // T(r) = sum_{j>r} sigma^_j^2, accumulated from the tail: T(re) = (n - re) sigma^_{re}^2
-    double T = (double)(n - re) * last * last;
-    int best = -1;
+    int re = (int)(n < (int64_t)r1 ? n : (int64_t)r1);
+    if (re > kSelMax) re = kSelMax;
+    if (lane == 0) {
+        const double last = re > 0 ? sig[re - 1] : 0.0;
+        // T(r) = sum_{j>r} sigma^_j^2, accumulated from the tail: T(re) = (n - re) sigma^_{re}^2
+        double T = (double)(n - re) * last * last;
+        Ts[re] = T;
+        for (int r = re - 1; r >= 0; --r) {
+            T += sig[r] * sig[r];
+            Ts[r] = T;
+        }
+    }
+    __syncwarp();
+    int best = INT_MAX;
     double best_bound = 0.0;
-    for (int r = re; r >= 0; --r) {
-        if (r < re) T += sig[r] * sig[r];
-        const double bound = sqrt(1.0 + (double)r / (p - 1.0)) * sqrt(T);
-        if (bound <= eps * ref) {
-            best = r;                     // walking down: the last hit is the smallest r
+    for (int r = lane; r <= re; r += 32) {
+        const double bound = sqrt(1.0 + (double)r / (p - 1.0)) * sqrt(Ts[r]);
+        if (bound <= eps * ref && r < best) {
+            best = r;
             best_bound = bound;
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int b2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const double v2 = __shfl_xor_sync(0xffffffffu, best_bound, o);
+        if (b2 < best) {
+            best = b2;
+            best_bound = v2;
+        }
+    }
+    if (lane != 0) return;
+    if (best == INT_MAX) best = -1;
     out->r = best;
     // k = min(r + p, n) columns factor A exactly once the sketch covers all n
     // singular values, so the criterion is met when those k columns are sketched
@@ -113,17 +141,24 @@ __global__ void blk_floor_kernel(const double* __restrict__ G, int ldg, int k, d
 // 32 x 32 lower Cholesky factorization of D (shared, row pitch kTB + 1) by the
 // 1024 threads of the block, thread (r, c) = (tid / 32, tid % 32).  thr[j] is
 // column j's deflation threshold; dfl[j] (shared) receives its mark.
+// The pivot's square root and the column's scaling come from one reciprocal square
+// root: L_jj = d rsqrt(d) and L_rj = D_rj rsqrt(d), so each of the 32 steps waits
+// for one long FP64 operation instead of a square root and then a division
+// (FP64 instructions issue at a small fraction of the FP32 rate on this GPU).
 __device__ void potrf32(double (*D)[kTB + 1], const double* thr, int* dfl) {
+    __shared__ double s_rinv;
     const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
     for (int j = 0; j < kTB; ++j) {
         if (r == j && c == j) {
             const double d = D[j][j];
             const bool dep = !(d > thr[j]);
             dfl[j] = dep ? 1 : 0;
-            D[j][j] = dep ? 1.0 : sqrt(d);
+            const double y = dep ? 1.0 : rsqrt(d);
+            D[j][j] = dep ? 1.0 : d * y;
+            s_rinv = y;
         }
         __syncthreads();
-        if (c == j && r > j) D[r][j] = dfl[j] ? 0.0 : D[r][j] / D[j][j];
+        if (c == j && r > j) D[r][j] = dfl[j] ? 0.0 : D[r][j] * s_rinv;
         __syncthreads();
         if (r > j && c > j && c <= r) D[r][c] -= D[r][j] * D[c][j];
         __syncthreads();
@@ -131,16 +166,20 @@ __device__ void potrf32(double (*D)[kTB + 1], const double* thr, int* dfl) {
 }
 
 // X (shared) = D^{-1} for the lower-triangular D: thread c of warp 0 owns column c.
+// The diagonal's reciprocals are formed once, in parallel, so the substitution
+// multiplies instead of dividing at each of its steps.
 __device__ void trinv32(const double (*D)[kTB + 1], double (*X)[kTB + 1]) {
+    __shared__ double rd[kTB];
     const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
     X[r][c] = 0.0;
+    if (threadIdx.x < kTB) rd[c] = 1.0 / D[c][c];
     __syncthreads();
     if (threadIdx.x < kTB) {
-        X[c][c] = 1.0 / D[c][c];
+        X[c][c] = rd[c];
         for (int i = c + 1; i < kTB; ++i) {
             double acc = 0.0;
             for (int l = c; l < i; ++l) acc = fma(D[i][l], X[l][c], acc);
-            X[i][c] = -acc / D[i][i];
+            X[i][c] = -acc * rd[i];
         }
     }
     __syncthreads();
