@@ -410,9 +410,28 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
             const int64_t kch = D.kpad / kBK;
             const bool mfree = B.A == nullptr;
             const int w = mfree ? 4 : copy_width(B.A, B.ld);
+            // matrix-free: this thread's row point (row t = 32 pw + lane of the tile) is the
+            // same for every K chunk, so it is loaded once per tile
+            float4 rp = make_float4(kFar, kFar, kFar, 0.f);
+            if (mfree && row0 + 32 * pw + lane < B.rows) {
+                const float* xp = D.px + 3 * (row0 + 32 * pw + lane);
+                rp = make_float4(xp[0], xp[1], xp[2], 0.f);
+            }
             for (int64_t kc = 0; kc < kch && ok; ++kc) {
                 for (int h = 0; h < 2; ++h, ++hg) {
                     const int as = (int)(hg % kAStages);
+                    // matrix-free: the half chunk's column point (k0 + lane, negated) is
+                    // loaded before the wait for the stage, so the load overlaps the wait
+                    float nx = kFar, ny = kFar, nz = kFar;
+                    if (mfree && pw == 0) {
+                        const int64_t k = kc * kBK + 32 * h + lane;
+                        if (k < B.cols) {
+                            const float* yp = D.py + 3 * k;
+                            nx = -yp[0];
+                            ny = -yp[1];
+                            nz = -yp[2];
+                        }
+                    }
                     ok = mbar_wait(&a_empty[as], (uint32_t)((hg / kAStages) & 1) ^ 1u, &s_abort, p.err);
                     if (!__all_sync(0xffffffffu, ok)) {
                         ok = false;
@@ -447,23 +466,8 @@ __global__ void __launch_bounds__(kThreads, 1) right_tc_batched_kernel(const TcB
                     }
                     if (mfree) {
                         unsigned char* stg = abuf + (size_t)as * kHalfBytes;
-                        const int t = 32 * pw + lane;          // row point t of the tile
-                        const int64_t row = row0 + t;
-                        float4 rp = make_float4(kFar, kFar, kFar, 0.f);
-                        if (row < B.rows) {
-                            const float* xp = D.px + 3 * row;
-                            rp = make_float4(xp[0], xp[1], xp[2], 0.f);
-                        }
-                        reinterpret_cast<float4*>(stg)[t] = rp;
+                        reinterpret_cast<float4*>(stg)[32 * pw + lane] = rp;   // row point t of the tile
                         if (pw == 0) {                          // column point k0 + lane, negated
-                            const int64_t k = k0 + lane;
-                            float nx = kFar, ny = kFar, nz = kFar;
-                            if (k < B.cols) {
-                                const float* yp = D.py + 3 * k;
-                                nx = -yp[0];
-                                ny = -yp[1];
-                                nz = -yp[2];
-                            }
                             float* cs = reinterpret_cast<float*>(stg + kColPts);
                             cs[lane] = nx;
                             cs[32 + lane] = ny;
