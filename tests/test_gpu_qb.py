@@ -90,6 +90,27 @@ def test_qb_parity(h, h_tc, tensor, fam, m, n, kw, eps, p):
     assert res.bound > 0 and res.bound <= eps * res.norm_a * (1 + 1e-12)
 
 
+def test_qb_caller_buffers_with_any_row_pitch(h_tc):
+    """Q and B given by the caller with row pitches that are not multiples of 4
+    floats: the tensor-core Cholesky-QR works on its own padded buffers and copies
+    the k columns of Q out, so the results equal those with the library's buffers
+    and nothing past column k of Q's rows is written."""
+    sig = wl.spectrum("step", 500, rank=150, tail_scale=1e-9)
+    A = wl.haar_matrix(1200, 500, sig, seed=1700).to(torch.float32).cuda()
+    res0, Q0, B0 = rk.re_rank_estimate_qb(h_tc, A, 1e-5, p=13, seed=21)
+    k_cap = 500
+    Qbuf = torch.full((1200, k_cap + 3), 7.0, dtype=torch.float32, device="cuda")
+    Bbuf = torch.full((k_cap, 500 + 1), 7.0, dtype=torch.float32, device="cuda")
+    res, Q, B = rk.re_rank_estimate_qb(h_tc, A, 1e-5, p=13, seed=21, Q=Qbuf[:, :k_cap], B=Bbuf[:, :500],
+                                       k_cap=k_cap)
+    assert (res.r, res.k, res.final_s, res.flags) == (res0.r, res0.k, res0.final_s, res0.flags)
+    # k = 163: the tensor-core products run (k >= 64) on rows padded to 168 columns
+    assert res.r == 150 and res.k == 163
+    assert torch.equal(Q, Q0) and torch.equal(B, B0)
+    # the columns past k of every row of Q, and the pitch padding, keep their contents
+    assert bool((Qbuf[:, res.k:] == 7.0).all()) and bool((Bbuf[:, 500:] == 7.0).all())
+
+
 def test_qb_exact_low_rank_and_zero(h):
     sig = wl.spectrum("step", 300, rank=12, tail_scale=0.0)
     A = wl.haar_matrix(700, 300, sig, seed=9).to(torch.float32).cuda()
